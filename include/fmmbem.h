@@ -1,0 +1,253 @@
+/*
+ * fmmbem.h — C ABI of the GB300 relaxed-p FMM-BEM library (libfmmbem.so).
+ *
+ * The library solves the collocation boundary-element systems of Wang, Layton
+ * & Barba, "Inexact Krylov iterations and relaxation strategies with
+ * fast-multipole boundary element method" (arXiv:1506.05957):
+ *   - Laplace, first kind (Sec. 2.1, eqs. laplace_bem_final, laplace_matrix):
+ *       V q = b,  V_ij = 1/(4 pi) int_{Gamma_j} 1/|c_i - y| dS_y,
+ *   - Stokes, single layer (Sec. 2.2, eqs. stokes_bem_discretized, stokeslet):
+ *       A t = u,  A_iJ = -1/(8 pi mu) int_{Gamma_J} (I/r + d d^T/r^3) dS_y,  d = c_i - y,
+ * on flat triangular panels with one unknown (Laplace) or three (Stokes) per
+ * panel, collocated at panel centroids. Integrals use K-point Gauss rules for
+ * far panels, a 20-point rule for panels within 2 sqrt(2 S_j) of the target
+ * and a semi-analytic self-panel integral (Sec. 2.3). The mat-vec is an
+ * N-body sum (eq. matvec-onerow) accelerated by a spherical-harmonic fast
+ * multipole method (Sec. 2.5) at a runtime expansion order p; GMRES
+ * (Sec. 2.4) lowers p as the residual falls (Sec. 2.6, eqs.
+ * matrix-perturbation and fmm_p).
+ *
+ * Conventions for every entry point:
+ *   - Return value: 0 on success, a negative FMMBEM_E* code on failure
+ *     (fmmbem_last_error() then describes it), FMMBEM_NOT_CONVERGED (1) from
+ *     fmmbem_solve when the iteration cap was reached (outputs still filled).
+ *   - "_dev" pointers are CUDA device memory of the current device; they are
+ *     read/written on the handle's stream. Host pointers are named "_host".
+ *   - The caller owns every buffer it passes; the library never frees them
+ *     and keeps no reference after the call returns. The handle owns all of
+ *     its own device state and frees it in fmmbem_destroy.
+ *   - Unknowns are in the caller's panel order: Laplace [n_panels] doubles,
+ *     Stokes [n_panels][3] doubles (x, y, z per panel).
+ *   - A handle is not thread-safe; distinct handles may be used from
+ *     distinct threads on distinct streams.
+ */
+#ifndef FMMBEM_H
+#define FMMBEM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Error codes. */
+#define FMMBEM_OK 0
+#define FMMBEM_NOT_CONVERGED 1
+#define FMMBEM_EINVAL (-1)   /* bad argument: sizes, p outside [1, p_max], theta outside (0,1), NULL */
+#define FMMBEM_ENOMEM (-2)   /* device allocation failed */
+#define FMMBEM_EDEVICE (-3)  /* CUDA error reported by a launch or a copy */
+#define FMMBEM_ENAN (-4)     /* NaN/Inf met in the Krylov recurrence */
+#define FMMBEM_ESTATE (-5)   /* call not valid for this handle (e.g. Stokes-only call on a Laplace handle) */
+
+/* Operators (Sec. 2.1-2.2). */
+#define FMMBEM_LAPLACE 0     /* Laplace single layer, 1 unknown per panel */
+#define FMMBEM_STOKES 1      /* Stokeslet single layer, 3 unknowns per panel */
+
+/* Arithmetic of the mat-vec (the Krylov recurrence is always FP64). */
+#define FMMBEM_FP64 0        /* every pass in FP64 */
+#define FMMBEM_MIXED 1       /* P2M/M2M/M2L/L2L/L2P and P2P in FP32 with FP64 tile sums;
+                                singular/near-singular corrections and the output in FP64 */
+
+/* Largest supported expansion order (degrees n = 0..p, (p+1)(p+2)/2 complex
+ * coefficients per expansion). */
+#define FMMBEM_P_MAX 16
+
+/* A surface triangulation in host memory. Triangles are counter-clockwise
+ * when seen from the side the normal should point to (outward for a closed
+ * body). Copied to the device by fmmbem_create; not referenced afterwards. */
+typedef struct {
+    int64_t n_vertices;
+    const double* vertices;   /* [n_vertices][3], host */
+    int64_t n_panels;
+    const int32_t* triangles; /* [n_panels][3] vertex indices, host */
+} fmmbem_mesh;
+
+/* Options; fmmbem_default_opts fills the defaults shown. */
+typedef struct {
+    int p_max;            /* 16: largest p any later call may request (<= FMMBEM_P_MAX) */
+    double near_factor;   /* 2.0: near-singular if |c_i - c_j| < near_factor * sqrt(2 S_j) (Sec. 2.3) */
+    double mu;            /* 1.0: viscosity (Stokes) */
+    int precision;        /* FMMBEM_MIXED */
+    int restart;          /* 50: GMRES restart length m */
+    int max_iter;         /* 100: cap on Arnoldi steps (the paper's cap, Table stokes_min_p) */
+    void* stream;         /* NULL: the legacy default stream; else a cudaStream_t for all work */
+} fmmbem_opts;
+
+typedef struct fmmbem_handle fmmbem_handle;
+
+/* Fill *opts with the defaults. Returns FMMBEM_EINVAL if opts is NULL. */
+int fmmbem_default_opts(fmmbem_opts* opts);
+
+/*
+ * Build everything the mat-vec needs (Sec. 2.3 and 2.5): panel geometry and
+ * K-point Gauss points, a Morton-sorted octree over panels whose leaves hold
+ * at most `ncrit` Gauss points, dual-tree-traversal interaction lists with the
+ * acceptance criterion (R_a + R_b) < theta |c_a - c_b| (R = box half-diagonal
+ * plus the largest panel extent), and the sparse table of near-singular and
+ * self-panel corrections (accurate integral minus the K-point sum), in FP64.
+ *   mesh      : host mesh (see fmmbem_mesh)
+ *   kernel    : FMMBEM_LAPLACE or FMMBEM_STOKES
+ *   gauss_k   : far-field rule, K in {1, 3, 4, 7}
+ *   ncrit     : leaf capacity in Gauss points, >= gauss_k
+ *   theta     : multipole acceptance parameter, 0 < theta < 1
+ *   opts      : NULL for defaults
+ *   out       : receives the handle
+ * Errors: FMMBEM_EINVAL on bad arguments or a degenerate (zero-area) panel,
+ * FMMBEM_ENOMEM, FMMBEM_EDEVICE. No handle is returned on failure.
+ */
+int fmmbem_create(const fmmbem_mesh* mesh, int kernel, int gauss_k, int ncrit, double theta,
+                  const fmmbem_opts* opts, fmmbem_handle** out);
+
+/* Release all device memory of the handle. NULL is ignored. */
+void fmmbem_destroy(fmmbem_handle* h);
+
+/* Number of unknowns: n_panels (Laplace) or 3 n_panels (Stokes). -1 for NULL. */
+int64_t fmmbem_n_unknowns(const fmmbem_handle* h);
+
+/* Switch the arithmetic of later mat-vecs and solves (FMMBEM_FP64 or FMMBEM_MIXED). */
+int fmmbem_set_precision(fmmbem_handle* h, int precision);
+
+/*
+ * y = A x through the FMM at expansion order p (eq. matvec-onerow with the
+ * far field by P2M, M2M, M2L, L2L, L2P and the near field by P2P plus the
+ * precomputed corrections).
+ *   p      : 1 <= p <= opts.p_max
+ *   x_dev  : [n_unknowns] doubles, device
+ *   y_dev  : [n_unknowns] doubles, device (must not alias x_dev)
+ * Asynchronous on the handle's stream. Errors: FMMBEM_EINVAL, FMMBEM_EDEVICE.
+ */
+int fmmbem_matvec(fmmbem_handle* h, int p, const double* x_dev, double* y_dev);
+
+/*
+ * y = A x by direct summation over every (collocation point, Gauss point)
+ * pair (the Appendix algorithm) plus the same corrections: the dense
+ * operator the FMM approximates. Same arguments as fmmbem_matvec without p.
+ */
+int fmmbem_matvec_direct(fmmbem_handle* h, const double* x_dev, double* y_dev);
+
+/*
+ * Right-hand side of the Laplace first-kind problem with Dirichlet data
+ * (Sec. 2.1, eqs. laplace_bem_final, laplace_matrix): b = phi/2 + K phi with
+ * K_ij = 1/(4 pi) int_j n_j.(c_i - y)/|c_i - y|^3 dS_y, by direct summation in
+ * FP64 with the same near-singular rule (the self term of a flat panel is 0).
+ *   known_dev : [n_panels] doubles, phi at the collocation points, device
+ *   b_dev     : [n_panels] doubles, device
+ * Errors: FMMBEM_ESTATE on a Stokes handle, FMMBEM_EINVAL, FMMBEM_EDEVICE.
+ */
+int fmmbem_rhs(fmmbem_handle* h, const double* known_dev, double* b_dev);
+
+/*
+ * Stokes double layer (eq. stresslet, T_ijk contracted once with the panel
+ * normal): y = B u with B_iJ = 1/(8 pi) int_J 6 e e^T (e.n_J)/|e|^5 dS_y,
+ * e = y - c_i, by direct summation in FP64 (the self term of a flat panel is
+ * 0). u_dev, y_dev: [n_panels][3] doubles, device. FMMBEM_ESTATE on a Laplace handle.
+ */
+int fmmbem_stokes_dl_apply(fmmbem_handle* h, const double* u_dev, double* y_dev);
+
+/*
+ * Relaxation rule (eqs. matrix-perturbation and fmm_p): with
+ * eps = min(eta / min(rho_prev, 1), 1), returns
+ * min(p_initial, max(p_min, ceil(-log2 eps))). ceil(-log2 eps) is evaluated
+ * exactly from the binary exponent of eps. Pure host function.
+ */
+int fmmbem_relaxed_p(double eta, double rho_prev, int p_initial, int p_min);
+
+/*
+ * Restarted GMRES(m) on A x = b (Sec. 2.4) with FP64 Arnoldi (classical
+ * Gram-Schmidt applied twice), Givens rotations and the residual estimate
+ * rho_k = |g_{k+1}| / ||b||. Step k uses the mat-vec at
+ *   p_k = fmmbem_relaxed_p(tol, rho_{k-1}, p_initial, p_min)  if relax != 0,
+ *   p_k = p_initial                                           otherwise.
+ * Restart residuals and the final true residual use p_initial.
+ *   rhs_dev   : [n] doubles, device
+ *   tol       : relative residual target (also eta of the relaxation rule)
+ *   x_dev     : [n] doubles, device; in: ignored (x0 = 0); out: solution
+ *   iters     : out, number of Arnoldi steps (mat-vecs inside GMRES)
+ *   p_hist    : out, [opts.max_iter] ints, host, p used at each step (may be NULL)
+ *   res_hist  : out, [opts.max_iter + 1] doubles, host, rho_0 = 1, rho_1.. (may be NULL)
+ *   true_res  : out, ||b - A_{p_initial} x|| / ||b|| after the solve (may be NULL)
+ * Returns 0 (converged), FMMBEM_NOT_CONVERGED, or a negative error.
+ */
+int fmmbem_solve(fmmbem_handle* h, const double* rhs_dev, double tol, int relax, int p_initial,
+                 int p_min, double* x_dev, int* iters, int* p_hist, double* res_hist,
+                 double* true_res);
+
+/*
+ * fmmbem_solve with host buffers: copies rhs_host to the device, solves,
+ * and copies the solution back into x_host before returning (synchronous).
+ * rhs_host, x_host: [n] doubles, host (pinned memory gives the fastest copies).
+ */
+int fmmbem_solve_host(fmmbem_handle* h, const double* rhs_host, double tol, int relax,
+                      int p_initial, int p_min, double* x_host, int* iters, int* p_hist,
+                      double* res_hist, double* true_res);
+
+/*
+ * Single expansions (Sec. 2.5, spherical-harmonic forms of M_n^m and L_n^m):
+ * form the multipole (kind 0) or local (kind 1) expansion of order p about
+ * `center` (host, 3 doubles) from n_src point charges, then evaluate it at
+ * n_tgt targets, all in FP64 on the device. Used to check eq. multipole_error.
+ *   src_dev : [n_src][4] doubles (x, y, z, q), device
+ *   tgt_dev : [n_tgt][3] doubles, device
+ *   out_dev : [n_tgt] doubles, device: sum_n sum_m M_n^m I_n^m(x - center) (kind 0)
+ *             or sum_n sum_m L_n^m R_n^m(x - center) (kind 1)
+ *   scale   : length used to scale the expansion (any positive number; the
+ *             result does not depend on it up to rounding)
+ */
+int fmmbem_expansion_eval(int kind, int p, const double* center, double scale, int n_src,
+                          const double* src_dev, int n_tgt, const double* tgt_dev, double* out_dev,
+                          void* stream);
+
+/* Sizes of the tree and lists built by fmmbem_create (algorithmic work counts). */
+typedef struct {
+    int64_t n_panels, n_sources, n_cells, n_leaves, n_levels;
+    int64_t n_m2l_pairs;          /* all M2L pairs */
+    int64_t n_m2l_same_level;     /* pairs whose cells have the same size */
+    int64_t n_p2p_pairs;          /* leaf-leaf near-field pairs */
+    int64_t n_p2p_interactions;   /* sum over P2P pairs of targets x Gauss points */
+    int64_t n_corrections;        /* entries of the near-singular/self correction table */
+    double setup_seconds;         /* wall time of fmmbem_create */
+} fmmbem_stats;
+
+int fmmbem_get_stats(const fmmbem_handle* h, fmmbem_stats* out);
+
+/* Per-pass device timing, measured with CUDA events recorded around each
+ * pass on the stream that launches it while profiling is enabled. */
+#define FMMBEM_PASS_P2M 0
+#define FMMBEM_PASS_M2M 1
+#define FMMBEM_PASS_M2L 2
+#define FMMBEM_PASS_L2L 3
+#define FMMBEM_PASS_L2P 4
+#define FMMBEM_PASS_P2P 5          /* near field + corrections */
+#define FMMBEM_PASS_KRYLOV 6       /* Arnoldi, Givens and updates */
+#define FMMBEM_PASS_MATVEC 7       /* whole mat-vec */
+#define FMMBEM_N_PASSES 8
+typedef struct {
+    double ms[FMMBEM_N_PASSES];       /* accumulated milliseconds */
+    int64_t launches[FMMBEM_N_PASSES]; /* kernel launches counted in each pass */
+    int64_t calls[FMMBEM_N_PASSES];    /* timed intervals */
+    double m2l_flops;                  /* accumulated algorithmic M2L flops (8 per complex MAC) */
+    double p2p_interactions;           /* accumulated P2P pair interactions */
+    int64_t kernel_launches;           /* every kernel launched by the handle since the reset */
+} fmmbem_profile;
+
+/* enable != 0 starts recording (and resets the counters); 0 stops. */
+int fmmbem_profile_enable(fmmbem_handle* h, int enable);
+int fmmbem_profile_get(fmmbem_handle* h, fmmbem_profile* out); /* synchronizes the stream */
+
+/* Message of the last failure in this thread ("" if none). */
+const char* fmmbem_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FMMBEM_H */

@@ -1,0 +1,10 @@
+"""GB300-native relaxed-p FMM-BEM (Wang, Layton & Barba, arXiv:1506.05957).
+
+The compute path is libfmmbem.so (hand-written sm_103a CUDA behind the C ABI in
+include/fmmbem.h); this package only builds and binds it.
+"""
+from .binding import (FmmBem, FmmBemError, fmmbem_default_opts, fmmbem_expansion_eval, fmmbem_relaxed_p, lib,
+                      FMMBEM_LAPLACE, FMMBEM_STOKES, FMMBEM_FP64, FMMBEM_MIXED, FMMBEM_P_MAX)
+
+__all__ = ["FmmBem", "FmmBemError", "fmmbem_default_opts", "fmmbem_expansion_eval", "fmmbem_relaxed_p", "lib",
+           "FMMBEM_LAPLACE", "FMMBEM_STOKES", "FMMBEM_FP64", "FMMBEM_MIXED", "FMMBEM_P_MAX"]

@@ -1,0 +1,217 @@
+"""ctypes binding of libfmmbem.so, the C ABI declared in include/fmmbem.h.
+
+Argument marshalling only: every step of the mat-vec and the solve runs in the
+library's CUDA kernels. Device buffers are passed as torch CUDA tensors (float64,
+contiguous); host buffers as numpy arrays. If the library has not been built,
+loading raises instead of falling back to anything else.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libfmmbem.so")
+
+FMMBEM_OK = 0
+FMMBEM_NOT_CONVERGED = 1
+FMMBEM_EINVAL = -1
+FMMBEM_ENOMEM = -2
+FMMBEM_EDEVICE = -3
+FMMBEM_ENAN = -4
+FMMBEM_ESTATE = -5
+FMMBEM_LAPLACE = 0
+FMMBEM_STOKES = 1
+FMMBEM_FP64 = 0
+FMMBEM_MIXED = 1
+FMMBEM_P_MAX = 16
+PASS_NAMES = ["p2m", "m2m", "m2l", "l2l", "l2p", "p2p", "krylov", "matvec"]
+
+
+class fmmbem_mesh(ctypes.Structure):
+    _fields_ = [("n_vertices", ctypes.c_int64), ("vertices", ctypes.POINTER(ctypes.c_double)),
+                ("n_panels", ctypes.c_int64), ("triangles", ctypes.POINTER(ctypes.c_int32))]
+
+
+class fmmbem_opts(ctypes.Structure):
+    _fields_ = [("p_max", ctypes.c_int), ("near_factor", ctypes.c_double), ("mu", ctypes.c_double),
+                ("precision", ctypes.c_int), ("restart", ctypes.c_int), ("max_iter", ctypes.c_int),
+                ("stream", ctypes.c_void_p)]
+
+
+class fmmbem_stats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int64) for n in ("n_panels", "n_sources", "n_cells", "n_leaves", "n_levels",
+                                               "n_m2l_pairs", "n_m2l_same_level", "n_p2p_pairs",
+                                               "n_p2p_interactions", "n_corrections")] + \
+               [("setup_seconds", ctypes.c_double)]
+
+
+class fmmbem_profile(ctypes.Structure):
+    _fields_ = [("ms", ctypes.c_double * 8), ("launches", ctypes.c_int64 * 8), ("calls", ctypes.c_int64 * 8),
+                ("m2l_flops", ctypes.c_double), ("p2p_interactions", ctypes.c_double),
+                ("kernel_launches", ctypes.c_int64)]
+
+
+_lib = None
+_dp = ctypes.POINTER(ctypes.c_double)
+_vp = ctypes.c_void_p
+
+
+def lib():
+    """The loaded library; raises if it was not built (no fallback path exists)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libfmmbem.so is not built (run __graft_entry__.build())")
+        L = ctypes.CDLL(LIB_PATH)
+        L.fmmbem_default_opts.argtypes = [ctypes.POINTER(fmmbem_opts)]
+        L.fmmbem_create.argtypes = [ctypes.POINTER(fmmbem_mesh), ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                    ctypes.c_double, ctypes.POINTER(fmmbem_opts), ctypes.POINTER(_vp)]
+        L.fmmbem_destroy.argtypes = [_vp]
+        L.fmmbem_destroy.restype = None
+        L.fmmbem_n_unknowns.argtypes = [_vp]
+        L.fmmbem_n_unknowns.restype = ctypes.c_int64
+        L.fmmbem_set_precision.argtypes = [_vp, ctypes.c_int]
+        L.fmmbem_matvec.argtypes = [_vp, ctypes.c_int, _vp, _vp]
+        L.fmmbem_matvec_direct.argtypes = [_vp, _vp, _vp]
+        L.fmmbem_rhs.argtypes = [_vp, _vp, _vp]
+        L.fmmbem_stokes_dl_apply.argtypes = [_vp, _vp, _vp]
+        L.fmmbem_relaxed_p.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_int]
+        L.fmmbem_solve.argtypes = [_vp, _vp, ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp,
+                                   ctypes.POINTER(ctypes.c_int), _vp, _vp, _dp]
+        L.fmmbem_solve_host.argtypes = [_vp, _vp, ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp,
+                                        ctypes.POINTER(ctypes.c_int), _vp, _vp, _dp]
+        L.fmmbem_expansion_eval.argtypes = [ctypes.c_int, ctypes.c_int, _dp, ctypes.c_double, ctypes.c_int, _vp,
+                                            ctypes.c_int, _vp, _vp, _vp]
+        L.fmmbem_get_stats.argtypes = [_vp, ctypes.POINTER(fmmbem_stats)]
+        L.fmmbem_profile_enable.argtypes = [_vp, ctypes.c_int]
+        L.fmmbem_profile_get.argtypes = [_vp, ctypes.POINTER(fmmbem_profile)]
+        L.fmmbem_last_error.restype = ctypes.c_char_p
+        _lib = L
+    return _lib
+
+
+class FmmBemError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("fmmbem error %d: %s" % (code, msg))
+        self.code = code
+
+
+def _check(rc):
+    if rc < 0:
+        raise FmmBemError(rc, lib().fmmbem_last_error().decode())
+    return rc
+
+
+def _dev(t, n=None):
+    """Device pointer of a contiguous float64 CUDA tensor."""
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+        raise TypeError("expected a contiguous float64 CUDA tensor")
+    if n is not None and t.numel() != n:
+        raise ValueError("expected %d elements, got %d" % (n, t.numel()))
+    return _vp(t.data_ptr())
+
+
+def _host(a, n):
+    if not (isinstance(a, np.ndarray) and a.dtype == np.float64 and a.flags.c_contiguous and a.size == n):
+        raise TypeError("expected a contiguous float64 numpy array of %d elements" % n)
+    return _vp(a.ctypes.data)
+
+
+def fmmbem_default_opts():
+    o = fmmbem_opts()
+    _check(lib().fmmbem_default_opts(ctypes.byref(o)))
+    return o
+
+
+def fmmbem_relaxed_p(eta, rho_prev, p_initial, p_min):
+    return int(lib().fmmbem_relaxed_p(float(eta), float(rho_prev), int(p_initial), int(p_min)))
+
+
+def fmmbem_expansion_eval(kind, p, center, scale, src, tgt, out, stream=None):
+    """src: [n,4] (x,y,z,q) CUDA float64; tgt: [m,3]; out: [m]."""
+    c = (ctypes.c_double * 3)(*[float(v) for v in center])
+    _check(lib().fmmbem_expansion_eval(int(kind), int(p), c, float(scale), int(src.shape[0]), _dev(src),
+                                       int(tgt.shape[0]), _dev(tgt), _dev(out), _vp(stream)))
+
+
+class FmmBem:
+    """One resident BEM problem: fmmbem_create ... fmmbem_destroy."""
+
+    def __init__(self, vertices, triangles, kernel=FMMBEM_LAPLACE, gauss_k=4, ncrit=150, theta=0.5, p_max=16,
+                 near_factor=2.0, mu=1.0, precision=FMMBEM_MIXED, restart=50, max_iter=100, stream=None):
+        v = np.ascontiguousarray(vertices, dtype=np.float64)
+        t = np.ascontiguousarray(triangles, dtype=np.int32)
+        mesh = fmmbem_mesh(len(v), v.ctypes.data_as(_dp), len(t), t.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)))
+        o = fmmbem_default_opts()
+        o.p_max, o.near_factor, o.mu, o.precision = p_max, near_factor, mu, precision
+        o.restart, o.max_iter = restart, max_iter
+        if stream is None:
+            import torch
+            stream = torch.cuda.current_stream().cuda_stream
+        o.stream = stream
+        h = _vp()
+        _check(lib().fmmbem_create(ctypes.byref(mesh), int(kernel), int(gauss_k), int(ncrit), float(theta),
+                                   ctypes.byref(o), ctypes.byref(h)))
+        self.h = h
+        self.kernel = kernel
+        self.max_iter = max_iter
+        self.n = int(lib().fmmbem_n_unknowns(h))
+        self.n_panels = len(t)
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().fmmbem_destroy(self.h)
+            self.h = None
+
+    __del__ = close
+
+    def set_precision(self, precision):
+        _check(lib().fmmbem_set_precision(self.h, int(precision)))
+
+    def matvec(self, p, x, y):
+        _check(lib().fmmbem_matvec(self.h, int(p), _dev(x, self.n), _dev(y, self.n)))
+
+    def matvec_direct(self, x, y):
+        _check(lib().fmmbem_matvec_direct(self.h, _dev(x, self.n), _dev(y, self.n)))
+
+    def rhs(self, known, b):
+        _check(lib().fmmbem_rhs(self.h, _dev(known, self.n_panels), _dev(b, self.n_panels)))
+
+    def stokes_dl_apply(self, u, y):
+        _check(lib().fmmbem_stokes_dl_apply(self.h, _dev(u, self.n), _dev(y, self.n)))
+
+    def _solve(self, fn, b, x, tol, relax, p_initial, p_min):
+        it = ctypes.c_int(0)
+        ph = np.zeros(self.max_iter + 1, dtype=np.int32)
+        rh = np.zeros(self.max_iter + 2, dtype=np.float64)
+        tr = ctypes.c_double(0.0)
+        rc = _check(fn(self.h, b, float(tol), int(bool(relax)), int(p_initial), int(p_min), x, ctypes.byref(it),
+                       _vp(ph.ctypes.data), _vp(rh.ctypes.data), ctypes.byref(tr)))
+        k = it.value
+        return dict(converged=(rc == 0), iters=k, p_hist=ph[:k].tolist(), res_hist=rh[:k + 1].tolist(),
+                    true_res=tr.value)
+
+    def solve(self, b, x, tol=1e-6, relax=True, p_initial=10, p_min=3):
+        return self._solve(lib().fmmbem_solve, _dev(b, self.n), _dev(x, self.n), tol, relax, p_initial, p_min)
+
+    def solve_host(self, b, x, tol=1e-6, relax=True, p_initial=10, p_min=3):
+        return self._solve(lib().fmmbem_solve_host, _host(b, self.n), _host(x, self.n), tol, relax, p_initial, p_min)
+
+    def stats(self):
+        s = fmmbem_stats()
+        _check(lib().fmmbem_get_stats(self.h, ctypes.byref(s)))
+        return {n: getattr(s, n) for n, _ in fmmbem_stats._fields_}
+
+    def profile_enable(self, on=True):
+        _check(lib().fmmbem_profile_enable(self.h, int(on)))
+
+    def profile(self):
+        pr = fmmbem_profile()
+        _check(lib().fmmbem_profile_get(self.h, ctypes.byref(pr)))
+        return dict(ms={PASS_NAMES[i]: pr.ms[i] for i in range(8)},
+                    launches={PASS_NAMES[i]: pr.launches[i] for i in range(8)},
+                    calls={PASS_NAMES[i]: pr.calls[i] for i in range(8)},
+                    m2l_flops=pr.m2l_flops, p2p_interactions=pr.p2p_interactions,
+                    kernel_launches=pr.kernel_launches)

@@ -1,0 +1,382 @@
+// C ABI of libfmmbem.so (declared in include/fmmbem.h): handle life cycle, the
+// mat-vec pipeline (near field, far field, evaluation) in Morton-sorted order,
+// permutations to and from the caller's panel order, solves and profiling.
+#include <stdarg.h>
+#include <string.h>
+#include <chrono>
+#include <vector>
+#include "handle.cuh"
+
+namespace {
+thread_local char g_err[1024] = "";
+}
+
+void fmmbem_set_error(const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+}
+
+namespace fmmbem {
+
+namespace {
+
+__global__ void k_perm_in(const double* x, const int* perm, int64_t n, int dof, double* xs) {
+    int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    const int64_t i = perm[s];
+    for (int a = 0; a < dof; ++a) xs[dof * s + a] = x[dof * i + a];
+}
+
+__global__ void k_perm_out(const double* ys, const int* perm, int64_t n, int dof, double* y) {
+    int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    const int64_t i = perm[s];
+    for (int a = 0; a < dof; ++a) y[dof * i + a] = ys[dof * s + a];
+}
+
+__global__ void k_axpy_half(double* y, const double* x, int64_t n) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) y[i] += 0.5 * x[i];
+}
+
+struct ProfRec {
+    int pass;
+    int launches;
+    cudaEvent_t a, b;
+};
+struct ProfState {
+    std::vector<cudaEvent_t> pool;
+    size_t used = 0;
+    std::vector<ProfRec> recs;
+    cudaEvent_t open[FMMBEM_N_PASSES] = {};
+};
+ProfState* prof_state(fmmbem_handle* h);
+
+double operator_scale(const fmmbem_handle* h) {
+    const double pi = 3.14159265358979323846;
+    return h->kernel == FMMBEM_LAPLACE ? 1.0 / (4.0 * pi) : -1.0 / (8.0 * pi * h->opts.mu);
+}
+
+int perm_in(fmmbem_handle* h, const double* x, double* xs) {
+    const int64_t n = h->N;
+    k_perm_in<<<(unsigned)((n + 255) / 256), 256, 0, h->stream>>>(x, h->perm, n, h->dof, xs);
+    FMM_LAUNCHED();
+    h->launches += 1;
+    return 0;
+}
+
+int perm_out(fmmbem_handle* h, const double* ys, double* y) {
+    const int64_t n = h->N;
+    k_perm_out<<<(unsigned)((n + 255) / 256), 256, 0, h->stream>>>(ys, h->perm, n, h->dof, y);
+    FMM_LAUNCHED();
+    h->launches += 1;
+    return 0;
+}
+
+template <typename P>
+int dalloc(P** p, size_t count) {
+    *p = nullptr;
+    FMM_CU(cudaMalloc((void**)p, (count ? count : 1) * sizeof(P)));
+    return 0;
+}
+
+}  // namespace
+
+// Profiling state lives beside the handle (allocated on first use).
+static std::vector<std::pair<fmmbem_handle*, ProfState*>> g_prof;
+
+namespace {
+ProfState* prof_state(fmmbem_handle* h) {
+    for (auto& e : g_prof)
+        if (e.first == h) return e.second;
+    ProfState* s = new ProfState();
+    g_prof.push_back({h, s});
+    return s;
+}
+void prof_free(fmmbem_handle* h) {
+    for (size_t i = 0; i < g_prof.size(); ++i)
+        if (g_prof[i].first == h) {
+            for (auto ev : g_prof[i].second->pool) cudaEventDestroy(ev);
+            delete g_prof[i].second;
+            g_prof.erase(g_prof.begin() + i);
+            return;
+        }
+}
+cudaEvent_t prof_event(ProfState* s) {
+    if (s->used == s->pool.size()) {
+        cudaEvent_t e;
+        cudaEventCreate(&e);
+        s->pool.push_back(e);
+    }
+    return s->pool[s->used++];
+}
+}  // namespace
+
+void prof_begin(fmmbem_handle* h, int pass) {
+    if (!h->prof_on) return;
+    ProfState* s = prof_state(h);
+    cudaEvent_t e = prof_event(s);
+    cudaEventRecord(e, h->stream);
+    s->open[pass] = e;
+}
+
+void prof_end(fmmbem_handle* h, int pass, int launches) {
+    if (!h->prof_on) return;
+    ProfState* s = prof_state(h);
+    if (!s->open[pass]) return;
+    cudaEvent_t e = prof_event(s);
+    cudaEventRecord(e, h->stream);
+    s->recs.push_back({pass, launches, s->open[pass], e});
+    s->open[pass] = nullptr;
+}
+
+int matvec_sorted(fmmbem_handle* h, int p, const double* xs, double* ys) {
+    const bool fp64 = h->precision == FMMBEM_FP64;
+    h->xin = xs;
+    prof_begin(h, FMMBEM_PASS_MATVEC);
+    FMM_TRY(near_field(h, fp64));
+    FMM_TRY(far_field(h, p, fp64));
+    FMM_TRY(far_eval_add(h, p, fp64, ys, operator_scale(h)));
+    prof_end(h, FMMBEM_PASS_MATVEC, 0);
+    if (h->prof_on) {
+        const double q = (double)(p + 1) * (p + 1);
+        h->prof.m2l_flops += 2.0 * q * q * h->ncomp * (double)h->n_m2l;
+        h->prof.p2p_interactions += (double)h->n_p2p_inter;
+    }
+    return 0;
+}
+
+}  // namespace fmmbem
+
+using namespace fmmbem;
+
+extern "C" {
+
+const char* fmmbem_last_error(void) { return g_err; }
+
+int fmmbem_default_opts(fmmbem_opts* o) {
+    if (!o) return FMMBEM_EINVAL;
+    o->p_max = FMMBEM_P_MAX;
+    o->near_factor = 2.0;
+    o->mu = 1.0;
+    o->precision = FMMBEM_MIXED;
+    o->restart = 50;
+    o->max_iter = 100;
+    o->stream = nullptr;
+    return 0;
+}
+
+int fmmbem_relaxed_p(double eta, double rho_prev, int p_initial, int p_min) {
+    return fmmbem::relaxed_p(eta, rho_prev, p_initial, p_min);
+}
+
+void fmmbem_destroy(fmmbem_handle* h) {
+    if (!h) return;
+    void* bufs[] = {h->perm, h->tgt_d, h->tgt_f, h->nrm_d, h->verts, h->src_d, h->src_f, h->cell_cs, h->cell_range,
+                    h->cell_child, h->cell_level, h->cell_parent, h->leaves, h->m2l_ptr, h->m2l_src, h->p2p_ptr,
+                    h->p2p_src, h->corr_ptr, h->corr_col, h->corr_sl, h->corr_dl, h->oct_d, h->oct_f, h->M, h->L,
+                    h->xs, h->ys, h->ynear, h->V, h->kw, h->kb, h->kx, h->kr, h->kpart, h->kh, h->kyv};
+    for (void* b : bufs)
+        if (b) cudaFree(b);
+    if (h->kh_host) cudaFreeHost(h->kh_host);
+    prof_free(h);
+    delete h;
+}
+
+int fmmbem_create(const fmmbem_mesh* mesh, int kernel, int gauss_k, int ncrit, double theta, const fmmbem_opts* opts,
+                  fmmbem_handle** out) {
+    const auto t0 = std::chrono::steady_clock::now();
+    if (!out) { fmmbem_set_error("out is NULL"); return FMMBEM_EINVAL; }
+    *out = nullptr;
+    if (!mesh || !mesh->vertices || !mesh->triangles || mesh->n_panels <= 0 || mesh->n_vertices < 3) {
+        fmmbem_set_error("empty or NULL mesh");
+        return FMMBEM_EINVAL;
+    }
+    if (mesh->n_panels > (int64_t)1 << 28) { fmmbem_set_error("too many panels"); return FMMBEM_EINVAL; }
+    if (kernel != FMMBEM_LAPLACE && kernel != FMMBEM_STOKES) { fmmbem_set_error("unknown kernel %d", kernel); return FMMBEM_EINVAL; }
+    if (!(theta > 0.0 && theta < 1.0)) { fmmbem_set_error("theta must lie in (0, 1)"); return FMMBEM_EINVAL; }
+    if (ncrit < gauss_k || ncrit < 1) { fmmbem_set_error("ncrit must be >= gauss_k"); return FMMBEM_EINVAL; }
+    fmmbem_opts o;
+    fmmbem_default_opts(&o);
+    if (opts) o = *opts;
+    if (o.p_max < 1 || o.p_max > FMMBEM_P_MAX) { fmmbem_set_error("p_max outside [1, %d]", FMMBEM_P_MAX); return FMMBEM_EINVAL; }
+    if (o.restart < 1 || o.restart > 60) { fmmbem_set_error("restart outside [1, 60]"); return FMMBEM_EINVAL; }
+    if (o.max_iter < 1) { fmmbem_set_error("max_iter < 1"); return FMMBEM_EINVAL; }
+    if (!(o.near_factor >= 0.0)) { fmmbem_set_error("near_factor < 0"); return FMMBEM_EINVAL; }
+    if (!(o.mu > 0.0)) { fmmbem_set_error("mu must be > 0"); return FMMBEM_EINVAL; }
+    if (o.precision != FMMBEM_FP64 && o.precision != FMMBEM_MIXED) { fmmbem_set_error("bad precision"); return FMMBEM_EINVAL; }
+
+    fmmbem_handle* h = new fmmbem_handle();
+    h->kernel = kernel;
+    h->dof = kernel == FMMBEM_STOKES ? 3 : 1;
+    h->ncomp = kernel == FMMBEM_STOKES ? 4 : 1;
+    h->K = gauss_k;
+    h->ncrit = ncrit;
+    h->theta = theta;
+    h->opts = o;
+    h->precision = o.precision;
+    h->stream = (cudaStream_t)o.stream;
+    auto fail = [&](int rc) { fmmbem_destroy(h); return rc; };
+    int rc = build_geometry_tree_lists(h, mesh);
+    if (rc < 0) return fail(rc);
+    rc = init_octant_tables(h);
+    if (rc < 0) return fail(rc);
+    const size_t ex = (size_t)h->n_cells * h->ncomp * NCOEF_MAX * 2;
+    const int64_t n = h->N * h->dof;
+    h->kr_m = o.restart;
+    if ((rc = dalloc((double**)&h->M, ex)) < 0) return fail(rc);
+    if ((rc = dalloc((double**)&h->L, ex)) < 0) return fail(rc);
+    if ((rc = dalloc(&h->xs, n)) < 0 || (rc = dalloc(&h->ys, n)) < 0 || (rc = dalloc(&h->ynear, n)) < 0) return fail(rc);
+    if ((rc = dalloc(&h->V, (size_t)(o.restart + 1) * n)) < 0) return fail(rc);
+    if ((rc = dalloc(&h->kw, n)) < 0 || (rc = dalloc(&h->kb, n)) < 0 || (rc = dalloc(&h->kx, n)) < 0 ||
+        (rc = dalloc(&h->kr, n)) < 0)
+        return fail(rc);
+    if ((rc = dalloc(&h->kpart, (size_t)96 * (o.restart + 2))) < 0) return fail(rc);
+    if ((rc = dalloc(&h->kh, (size_t)3 * (o.restart + 2))) < 0) return fail(rc);
+    if ((rc = dalloc(&h->kyv, (size_t)(o.restart + 2))) < 0) return fail(rc);
+    if (cudaMallocHost((void**)&h->kh_host, sizeof(double) * 3 * (o.restart + 2)) != cudaSuccess) {
+        fmmbem_set_error("pinned allocation failed");
+        return fail(FMMBEM_ENOMEM);
+    }
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess) {
+        fmmbem_set_error("create: %s", cudaGetErrorString(cudaGetLastError()));
+        return fail(FMMBEM_EDEVICE);
+    }
+    h->setup_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    *out = h;
+    return 0;
+}
+
+int64_t fmmbem_n_unknowns(const fmmbem_handle* h) { return h ? h->N * h->dof : -1; }
+
+int fmmbem_set_precision(fmmbem_handle* h, int precision) {
+    if (!h || (precision != FMMBEM_FP64 && precision != FMMBEM_MIXED)) { fmmbem_set_error("bad precision"); return FMMBEM_EINVAL; }
+    h->precision = precision;
+    return 0;
+}
+
+int fmmbem_matvec(fmmbem_handle* h, int p, const double* x_dev, double* y_dev) {
+    if (!h || !x_dev || !y_dev) { fmmbem_set_error("NULL argument"); return FMMBEM_EINVAL; }
+    if (p < 1 || p > h->opts.p_max) { fmmbem_set_error("p=%d outside [1, %d]", p, h->opts.p_max); return FMMBEM_EINVAL; }
+    if (x_dev == y_dev) { fmmbem_set_error("x and y alias"); return FMMBEM_EINVAL; }
+    FMM_TRY(perm_in(h, x_dev, h->xs));
+    FMM_TRY(matvec_sorted(h, p, h->xs, h->ys));
+    FMM_TRY(perm_out(h, h->ys, y_dev));
+    return 0;
+}
+
+int fmmbem_matvec_direct(fmmbem_handle* h, const double* x_dev, double* y_dev) {
+    if (!h || !x_dev || !y_dev || x_dev == y_dev) { fmmbem_set_error("bad argument"); return FMMBEM_EINVAL; }
+    FMM_TRY(perm_in(h, x_dev, h->xs));
+    FMM_TRY(direct_field(h, h->precision == FMMBEM_FP64, 0, h->xs, h->ys));
+    FMM_TRY(perm_out(h, h->ys, y_dev));
+    return 0;
+}
+
+int fmmbem_rhs(fmmbem_handle* h, const double* known_dev, double* b_dev) {
+    if (!h || !known_dev || !b_dev || known_dev == b_dev) { fmmbem_set_error("bad argument"); return FMMBEM_EINVAL; }
+    if (h->kernel != FMMBEM_LAPLACE) { fmmbem_set_error("fmmbem_rhs needs a Laplace handle"); return FMMBEM_ESTATE; }
+    FMM_TRY(perm_in(h, known_dev, h->xs));
+    FMM_TRY(direct_field(h, true, 1, h->xs, h->ys));
+    k_axpy_half<<<(unsigned)((h->N + 255) / 256), 256, 0, h->stream>>>(h->ys, h->xs, h->N);
+    FMM_LAUNCHED();
+    FMM_TRY(perm_out(h, h->ys, b_dev));
+    return 0;
+}
+
+int fmmbem_stokes_dl_apply(fmmbem_handle* h, const double* u_dev, double* y_dev) {
+    if (!h || !u_dev || !y_dev || u_dev == y_dev) { fmmbem_set_error("bad argument"); return FMMBEM_EINVAL; }
+    if (h->kernel != FMMBEM_STOKES) { fmmbem_set_error("needs a Stokes handle"); return FMMBEM_ESTATE; }
+    FMM_TRY(perm_in(h, u_dev, h->xs));
+    FMM_TRY(direct_field(h, true, 1, h->xs, h->ys));
+    FMM_TRY(perm_out(h, h->ys, y_dev));
+    return 0;
+}
+
+int fmmbem_solve(fmmbem_handle* h, const double* rhs_dev, double tol, int relax, int p_initial, int p_min,
+                 double* x_dev, int* iters, int* p_hist, double* res_hist, double* true_res) {
+    if (!h || !rhs_dev || !x_dev) { fmmbem_set_error("NULL argument"); return FMMBEM_EINVAL; }
+    if (p_initial < 1 || p_initial > h->opts.p_max || p_min < 1 || p_min > p_initial) {
+        fmmbem_set_error("need 1 <= p_min <= p_initial <= p_max");
+        return FMMBEM_EINVAL;
+    }
+    if (!(tol > 0.0 && tol < 1.0)) { fmmbem_set_error("tol must lie in (0, 1)"); return FMMBEM_EINVAL; }
+    FMM_TRY(perm_in(h, rhs_dev, h->kb));
+    int rc = gmres_solve(h, h->kb, tol, relax, p_initial, p_min, h->kx, iters, p_hist, res_hist, true_res);
+    if (rc < 0) return rc;
+    FMM_TRY(perm_out(h, h->kx, x_dev));
+    return rc;
+}
+
+int fmmbem_solve_host(fmmbem_handle* h, const double* rhs_host, double tol, int relax, int p_initial, int p_min,
+                      double* x_host, int* iters, int* p_hist, double* res_hist, double* true_res) {
+    if (!h || !rhs_host || !x_host) { fmmbem_set_error("NULL argument"); return FMMBEM_EINVAL; }
+    const int64_t n = h->N * h->dof;
+    FMM_CU(cudaMemcpyAsync(h->ys, rhs_host, sizeof(double) * n, cudaMemcpyHostToDevice, h->stream));
+    int rc = fmmbem_solve(h, h->ys, tol, relax, p_initial, p_min, h->xs, iters, p_hist, res_hist, true_res);
+    if (rc < 0) return rc;
+    FMM_CU(cudaMemcpyAsync(x_host, h->xs, sizeof(double) * n, cudaMemcpyDeviceToHost, h->stream));
+    FMM_CU(cudaStreamSynchronize(h->stream));
+    return rc;
+}
+
+int fmmbem_expansion_eval(int kind, int p, const double* center, double scale, int n_src, const double* src_dev,
+                          int n_tgt, const double* tgt_dev, double* out_dev, void* stream) {
+    if ((kind != 0 && kind != 1) || p < 0 || p > FMMBEM_P_MAX || !center || !(scale > 0.0) || n_src < 0 ||
+        n_tgt < 0 || (n_src && !src_dev) || (n_tgt && (!tgt_dev || !out_dev))) {
+        fmmbem_set_error("bad argument");
+        return FMMBEM_EINVAL;
+    }
+    return fmmbem::expansion_eval(kind, p, center, scale, n_src, src_dev, n_tgt, tgt_dev, out_dev, (cudaStream_t)stream);
+}
+
+int fmmbem_get_stats(const fmmbem_handle* h, fmmbem_stats* s) {
+    if (!h || !s) { fmmbem_set_error("NULL argument"); return FMMBEM_EINVAL; }
+    s->n_panels = h->N;
+    s->n_sources = h->NS;
+    s->n_cells = h->n_cells;
+    s->n_leaves = h->n_leaves;
+    s->n_levels = h->n_levels;
+    s->n_m2l_pairs = h->n_m2l;
+    s->n_m2l_same_level = h->n_m2l_same;
+    s->n_p2p_pairs = h->n_p2p;
+    s->n_p2p_interactions = h->n_p2p_inter;
+    s->n_corrections = h->n_corr;
+    s->setup_seconds = h->setup_seconds;
+    return 0;
+}
+
+int fmmbem_profile_enable(fmmbem_handle* h, int enable) {
+    if (!h) { fmmbem_set_error("NULL handle"); return FMMBEM_EINVAL; }
+    FMM_CU(cudaStreamSynchronize(h->stream));
+    ProfState* s = prof_state(h);
+    s->recs.clear();
+    s->used = 0;
+    for (auto& e : s->open) e = nullptr;
+    memset(&h->prof, 0, sizeof(h->prof));
+    h->launches = 0;
+    h->prof_on = enable != 0;
+    return 0;
+}
+
+int fmmbem_profile_get(fmmbem_handle* h, fmmbem_profile* out) {
+    if (!h || !out) { fmmbem_set_error("NULL argument"); return FMMBEM_EINVAL; }
+    FMM_CU(cudaStreamSynchronize(h->stream));
+    ProfState* s = prof_state(h);
+    for (const auto& r : s->recs) {
+        float ms = 0.f;
+        FMM_CU(cudaEventElapsedTime(&ms, r.a, r.b));
+        h->prof.ms[r.pass] += ms;
+        h->prof.launches[r.pass] += r.launches;
+        h->prof.calls[r.pass] += 1;
+    }
+    s->recs.clear();
+    s->used = 0;
+    h->prof.kernel_launches = h->launches;
+    *out = h->prof;
+    return 0;
+}
+
+}  // extern "C"

@@ -1,0 +1,92 @@
+// Shared definitions of the CUDA path: complex helpers, coefficient indexing,
+// error reporting and launch checks.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdio.h>
+#include "fmmbem.h"
+
+#define FMM_HD __host__ __device__ __forceinline__
+
+namespace fmmbem {
+
+constexpr int PMAX = FMMBEM_P_MAX;
+// Expansions keep degrees n = 0..p and orders m = 0..n (the m < 0 half follows
+// from X_n^{-m} = (-1)^m conj(X_n^m)): (p+1)(p+2)/2 complex coefficients.
+constexpr int NCOEF_MAX = (PMAX + 1) * (PMAX + 2) / 2;
+// Irregular harmonics needed by M2L reach degree 2p.
+constexpr int NI_MAX = (2 * PMAX + 1) * (2 * PMAX + 2) / 2;
+constexpr int MAX_LEVELS = 21;  // 63-bit Morton keys, 21 bits per axis
+
+FMM_HD int cidx(int n, int m) { return (n * (n + 1)) / 2 + m; }
+FMM_HD int ncoef(int p) { return (p + 1) * (p + 2) / 2; }
+
+template <typename T> struct cpx { T re, im; };
+template <typename T> FMM_HD cpx<T> mk(T r, T i) { cpx<T> z; z.re = r; z.im = i; return z; }
+template <typename T> FMM_HD cpx<T> operator+(cpx<T> a, cpx<T> b) { return mk(a.re + b.re, a.im + b.im); }
+template <typename T> FMM_HD cpx<T> operator-(cpx<T> a, cpx<T> b) { return mk(a.re - b.re, a.im - b.im); }
+template <typename T> FMM_HD cpx<T> operator*(cpx<T> a, cpx<T> b) {
+    return mk(a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re);
+}
+template <typename T> FMM_HD cpx<T> operator*(T s, cpx<T> a) { return mk(s * a.re, s * a.im); }
+template <typename T> FMM_HD cpx<T> conj(cpx<T> a) { return mk(a.re, -a.im); }
+// acc += a * b
+template <typename T> FMM_HD void cfma(cpx<T>& acc, cpx<T> a, cpx<T> b) {
+    acc.re += a.re * b.re - a.im * b.im;
+    acc.im += a.re * b.im + a.im * b.re;
+}
+// acc += conj(a) * b
+template <typename T> FMM_HD void cfma_conja(cpx<T>& acc, cpx<T> a, cpx<T> b) {
+    acc.re += a.re * b.re + a.im * b.im;
+    acc.im += a.re * b.im - a.im * b.re;
+}
+
+// 4-wide vector of the arithmetic type (positions + weight).
+template <typename T> struct V4;
+template <> struct V4<float> { typedef float4 type; };
+template <> struct V4<double> { typedef double4 type; };
+
+template <typename T> FMM_HD T rsqrt_t(T x);
+template <> FMM_HD float rsqrt_t<float>(float x) {
+#ifdef __CUDA_ARCH__
+    return rsqrtf(x);
+#else
+    return 1.0f / sqrtf(x);
+#endif
+}
+template <> FMM_HD double rsqrt_t<double>(double x) {
+#ifdef __CUDA_ARCH__
+    return rsqrt(x);
+#else
+    return 1.0 / sqrt(x);
+#endif
+}
+
+}  // namespace fmmbem
+
+// Thread-local message of the last failure (fmmbem_last_error).
+void fmmbem_set_error(const char* fmt, ...);
+
+#define FMM_CU(call)                                                                        \
+    do {                                                                                    \
+        cudaError_t e_ = (call);                                                            \
+        if (e_ != cudaSuccess) {                                                            \
+            fmmbem_set_error("%s:%d %s: %s", __FILE__, __LINE__, #call, cudaGetErrorString(e_)); \
+            return e_ == cudaErrorMemoryAllocation ? FMMBEM_ENOMEM : FMMBEM_EDEVICE;        \
+        }                                                                                   \
+    } while (0)
+
+#define FMM_LAUNCHED()                                                                      \
+    do {                                                                                    \
+        cudaError_t e_ = cudaGetLastError();                                                \
+        if (e_ != cudaSuccess) {                                                            \
+            fmmbem_set_error("%s:%d launch: %s", __FILE__, __LINE__, cudaGetErrorString(e_)); \
+            return FMMBEM_EDEVICE;                                                          \
+        }                                                                                   \
+    } while (0)
+
+#define FMM_TRY(expr)              \
+    do {                           \
+        int r_ = (expr);           \
+        if (r_ < 0) return r_;     \
+    } while (0)

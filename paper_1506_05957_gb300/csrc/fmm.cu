@@ -1,0 +1,522 @@
+// Far-field passes of the FMM mat-vec at a runtime expansion order p (Sec. 2.5):
+// P2M at the leaves, M2M up the tree, M2L over the dual-tree-traversal list,
+// L2L down the tree, L2P at the collocation points. Expansions are stored
+// scaled by the cell side s (M~_n = M_n / s^n, L^_n = L_n s^{n+1}) so that
+// magnitudes stay O(1) at every level in FP32 and the translation operators
+// between same-size cells depend only on the offset in units of s.
+//
+// Laplace uses one expansion per cell with strengths w = q_k S_j x_j (eq.
+// matvec-onerow). Stokes uses four (Sec. 3.2: "four Laplace expansions"):
+// strengths f_1, f_2, f_3 and y.f with f = q_k S_J t_J, and the Stokeslet sum
+// u_a = phi_a - x_b d_a phi_b + d_a phi_4 at each target.
+#include <type_traits>
+#include "handle.cuh"
+#include "harmonics.cuh"
+
+namespace fmmbem {
+
+namespace {
+
+__constant__ unsigned char c_deg[NCOEF_MAX];  // degree n of each stored coefficient index
+
+template <typename T> FMM_HD cpx<T> ld(const T* base, int q) { return mk(base[2 * q], base[2 * q + 1]); }
+template <typename T> FMM_HD void st(T* base, int q, cpx<T> v) { base[2 * q] = v.re; base[2 * q + 1] = v.im; }
+
+// any-order coefficient from a stored (m >= 0) complex array
+template <typename T> __device__ __forceinline__ cpx<T> ld_any(const T* base, int n, int m) {
+    if (m >= 0) return ld(base, cidx(n, m));
+    cpx<T> v = ld(base, cidx(n, -m));
+    return (m & 1) ? mk(-v.re, v.im) : mk(v.re, -v.im);
+}
+
+__device__ __forceinline__ void decode(int q, int& n, int& m) {
+    n = c_deg[q];
+    m = q - (n * (n + 1)) / 2;
+}
+
+template <typename T> __device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ int octant_of(double4 c, double4 par) {
+    return (c.x > par.x ? 1 : 0) | (c.y > par.y ? 2 : 0) | (c.z > par.z ? 4 : 0);
+}
+
+constexpr int P2M_WARPS = 4;
+
+// P2M: one block per leaf. Each lane of a warp takes one Gauss point; the solid
+// harmonics are generated column by column and every coefficient is reduced
+// across the warp by shuffles into a per-warp shared-memory accumulator.
+template <typename T, int NC>
+__global__ void __launch_bounds__(32 * P2M_WARPS) k_p2m(int p, const int* leaves, const double4* cs, const int2* range,
+                                                       const typename V4<T>::type* src, const double* xs, int K,
+                                                       double ox, double oy, double oz, T* M) {
+    extern __shared__ unsigned char smem_raw[];
+    T* acc = reinterpret_cast<T*>(smem_raw);  // [warps][NC][ncoef][2]
+    const int nco = ncoef(p);
+    const int cell = leaves[blockIdx.x];
+    const double4 cc = cs[cell];
+    const int2 r = range[cell];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int q = threadIdx.x; q < P2M_WARPS * NC * nco * 2; q += blockDim.x) acc[q] = T(0);
+    __syncthreads();
+    T* wacc = acc + warp * NC * nco * 2;
+    const double inv_s = 1.0 / cc.w;
+    const int s0 = r.x * K, s1 = r.y * K;
+    for (int base = s0 + warp * 32; base < s1; base += P2M_WARPS * 32) {
+        const int s = base + lane;
+        T vx = 0, vy = 0, vz = 0, q[NC];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) q[c] = 0;
+        if (s < s1) {
+            const auto y = src[s];
+            const int pj = s / K;
+            vx = T(((double)y.x - cc.x) * inv_s);
+            vy = T(((double)y.y - cc.y) * inv_s);
+            vz = T(((double)y.z - cc.z) * inv_s);
+            if (NC == 1) {
+                q[0] = T((double)y.w * xs[pj]);
+            } else {
+                const double t0 = xs[3 * pj], t1 = xs[3 * pj + 1], t2 = xs[3 * pj + 2];
+                const double w = (double)y.w;
+                q[0] = T(w * t0);
+                q[1] = T(w * t1);
+                q[2] = T(w * t2);
+                q[NC - 1] = T(w * (((double)y.x - ox) * t0 + ((double)y.y - oy) * t1 + ((double)y.z - oz) * t2));
+            }
+        }
+        const T r2 = vx * vx + vy * vy + vz * vz;
+        const cpx<T> xy = mk(vx, vy);
+        cpx<T> diag = mk(T(1), T(0));
+        auto emit = [&](int n, int m, cpx<T> R) {
+            const int qi = cidx(n, m);
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+                T re = warp_sum(q[c] * R.re), im = warp_sum(-q[c] * R.im);
+                if (lane == 0) {
+                    wacc[(c * nco + qi) * 2] += re;
+                    wacc[(c * nco + qi) * 2 + 1] += im;
+                }
+            }
+        };
+        for (int m = 0; m <= p; ++m) {
+            if (m > 0) diag = (T(-0.5) / T(m)) * (xy * diag);
+            emit(m, m, diag);
+            if (m + 1 > p) break;
+            cpx<T> prev2 = diag, prev1 = vz * diag;
+            emit(m + 1, m, prev1);
+            for (int n = m + 2; n <= p; ++n) {
+                const T inv = T(1) / T((n - m) * (n + m));
+                cpx<T> cur = mk((T(2 * n - 1) * vz * prev1.re - r2 * prev2.re) * inv,
+                                (T(2 * n - 1) * vz * prev1.im - r2 * prev2.im) * inv);
+                emit(n, m, cur);
+                prev2 = prev1;
+                prev1 = cur;
+            }
+        }
+    }
+    __syncthreads();
+    T* out = M + (size_t)cell * NC * NCOEF_MAX * 2;
+    for (int idx = threadIdx.x; idx < NC * nco * 2; idx += blockDim.x) {
+        const int c = idx / (nco * 2), rest = idx % (nco * 2);
+        T v = 0;
+#pragma unroll
+        for (int w = 0; w < P2M_WARPS; ++w) v += acc[w * NC * nco * 2 + idx];
+        out[c * NCOEF_MAX * 2 + rest] = v;
+    }
+}
+
+// M2M for the non-leaf cells of one level: M~_n^m(P) = sum_children sum_{j,k}
+// M~_j^k(c) 2^{-j} conj(R_{n-j}^{m-k}(d)), d = (c_child - c_parent)/s_parent.
+template <typename T, int NC>
+__global__ void k_m2m(int p, int lb, const double4* cs, const int2* child, const T* oct, T* M) {
+    const int cell = lb + blockIdx.x;
+    const int2 ch = child[cell];
+    if (ch.y == 0) return;
+    const int nco = ncoef(p);
+    const int t = threadIdx.x;
+    if (t >= nco) return;
+    int n, m;
+    decode(t, n, m);
+    const double4 pc = cs[cell];
+    cpx<T> acc[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) acc[c] = mk(T(0), T(0));
+    for (int x = 0; x < ch.y; ++x) {
+        const int cid = ch.x + x;
+        const T* Rt = oct + octant_of(cs[cid], pc) * NCOEF_MAX * 2;
+        const T* Mc = M + (size_t)cid * NC * NCOEF_MAX * 2;
+        T sc = T(1);
+        for (int j = 0; j <= n; ++j) {
+            const int klo = max(-j, m - (n - j)), khi = min(j, m + (n - j));
+            for (int k = klo; k <= khi; ++k) {
+                const cpx<T> R = conj(ld_any(Rt, n - j, m - k));
+#pragma unroll
+                for (int c = 0; c < NC; ++c) cfma(acc[c], sc * ld_any(Mc + c * NCOEF_MAX * 2, j, k), R);
+            }
+            sc *= T(0.5);
+        }
+    }
+    T* out = M + (size_t)cell * NC * NCOEF_MAX * 2;
+#pragma unroll
+    for (int c = 0; c < NC; ++c) st(out + c * NCOEF_MAX * 2, t, acc[c]);
+}
+
+// M2L, gathered per target cell over its interaction list:
+//   L^_j^k += (-1)^j conj( sum_{n,m} rho^n M~_n^m I_{n+j}^{m+k}(t / s_t) ),
+// t = c_target - c_source, rho = s_source / s_target (a power of two).
+// One thread per output coefficient (j, k); the irregular table of each pair is
+// built in shared memory, one column per thread.
+template <typename T, int NC>
+__global__ void k_m2l(int p, const int* ptr, const int* srcl, const double4* cs, const T* M, T* L) {
+    __shared__ T sI[NI_MAX * 2];
+    __shared__ T sM[NC * NCOEF_MAX * 2];
+    const int tc = blockIdx.x;
+    const int nco = ncoef(p);
+    const int t = threadIdx.x;
+    int j = 0, k = 0;
+    if (t < nco) decode(t, j, k);
+    const double4 ct = cs[tc];
+    cpx<T> acc[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) acc[c] = mk(T(0), T(0));
+    const int e0 = ptr[tc], e1 = ptr[tc + 1];
+    for (int e = e0; e < e1; ++e) {
+        const int sc = srcl[e];
+        const double4 cv = cs[sc];
+        const double is = 1.0 / ct.w;
+        const T vx = T((ct.x - cv.x) * is), vy = T((ct.y - cv.y) * is), vz = T((ct.z - cv.z) * is);
+        const int dl = ilogb(cv.w * is);  // log2(rho), exact for cells of the same tree
+        __syncthreads();
+        if (t <= 2 * p) irregular_column<T>(vx, vy, vz, t, 2 * p, reinterpret_cast<cpx<T>*>(sI));
+        const T* Ms = M + (size_t)sc * NC * NCOEF_MAX * 2;
+        for (int idx = t; idx < NC * nco; idx += blockDim.x) {
+            const int c = idx / nco, q = idx % nco;
+            const T f = (dl == 0) ? T(1) : T(ldexp(1.0, dl * (int)c_deg[q]));
+            sM[(c * NCOEF_MAX + q) * 2] = f * Ms[c * NCOEF_MAX * 2 + 2 * q];
+            sM[(c * NCOEF_MAX + q) * 2 + 1] = f * Ms[c * NCOEF_MAX * 2 + 2 * q + 1];
+        }
+        __syncthreads();
+        if (t < nco) {
+            for (int n = 0; n <= p; ++n) {
+                const int nj = n + j;
+                const int base = cidx(n, 0);
+                // m >= 0: M_n^m I_{n+j}^{m+k}
+                for (int m = 0; m <= n; ++m) {
+                    const cpx<T> I = ld(sI, cidx(nj, m + k));
+#pragma unroll
+                    for (int c = 0; c < NC; ++c) cfma(acc[c], ld(sM + c * NCOEF_MAX * 2, base + m), I);
+                }
+                // m = -mu, 1 <= mu <= min(n, k): (-1)^mu conj(M_n^mu) I_{n+j}^{k-mu}
+                const int mk1 = min(n, k);
+                for (int mu = 1; mu <= mk1; ++mu) {
+                    cpx<T> I = ld(sI, cidx(nj, k - mu));
+                    if (mu & 1) I = mk(-I.re, -I.im);
+#pragma unroll
+                    for (int c = 0; c < NC; ++c) cfma_conja(acc[c], ld(sM + c * NCOEF_MAX * 2, base + mu), I);
+                }
+                // m = -mu, k < mu <= n: (-1)^k conj(M_n^mu I_{n+j}^{mu-k})
+                for (int mu = k + 1; mu <= n; ++mu) {
+                    const cpx<T> I = ld(sI, cidx(nj, mu - k));
+#pragma unroll
+                    for (int c = 0; c < NC; ++c) {
+                        const cpx<T> v = ld(sM + c * NCOEF_MAX * 2, base + mu) * I;
+                        if (k & 1) { acc[c].re -= v.re; acc[c].im += v.im; }
+                        else { acc[c].re += v.re; acc[c].im -= v.im; }
+                    }
+                }
+            }
+        }
+    }
+    if (t < nco) {
+        T* out = L + (size_t)tc * NC * NCOEF_MAX * 2;
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            cpx<T> v = conj(acc[c]);
+            if (j & 1) v = mk(-v.re, -v.im);
+            st(out + c * NCOEF_MAX * 2, t, v);
+        }
+    }
+}
+
+// L2L for every cell of one level: L^_j^k(c) += sum_{n>=j, m} L^_n^m(P) R_{n-j}^{m-k}(d) 2^{-(j+1)}.
+template <typename T, int NC>
+__global__ void k_l2l(int p, int lb, const double4* cs, const int* parent, const T* oct, T* L) {
+    const int cell = lb + blockIdx.x;
+    const int par = parent[cell];
+    const int nco = ncoef(p);
+    const int t = threadIdx.x;
+    if (t >= nco || par < 0) return;
+    int j, k;
+    decode(t, j, k);
+    const T* Rt = oct + octant_of(cs[cell], cs[par]) * NCOEF_MAX * 2;
+    const T* Lp = L + (size_t)par * NC * NCOEF_MAX * 2;
+    cpx<T> acc[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) acc[c] = mk(T(0), T(0));
+    for (int n = j; n <= p; ++n) {
+        const int mlo = max(-n, k - (n - j)), mhi = min(n, k + (n - j));
+        for (int m = mlo; m <= mhi; ++m) {
+            const cpx<T> R = ld_any(Rt, n - j, m - k);
+#pragma unroll
+            for (int c = 0; c < NC; ++c) cfma(acc[c], ld_any(Lp + c * NCOEF_MAX * 2, n, m), R);
+        }
+    }
+    const T f = T(ldexp(1.0, -(j + 1)));
+    T* out = L + (size_t)cell * NC * NCOEF_MAX * 2;
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+        cpx<T> v = ld(out + c * NCOEF_MAX * 2, t);
+        st(out + c * NCOEF_MAX * 2, t, v + f * acc[c]);
+    }
+}
+
+// L2P at the collocation points of each leaf, plus the near-field sum, times the
+// operator's scale; written in the caller's order or in sorted order.
+//   phi(x) = (1/s) sum_{n,m} L^_n^m R_n^m(v), v = (x - c)/s
+//   grad phi = (1/s^2) sum L^_n^m grad R_n^m(v) with d_z R_n^m = R_{n-1}^m and
+//   (d_x + i d_y) R_n^m = R_{n-1}^{m+1}.
+template <typename T, int NC>
+__global__ void k_l2p(int p, const int* leaves, const double4* cs, const int2* range, const double4* tgt, const T* L,
+                      const double* ynear, double scale, double ox, double oy, double oz, double* yout) {
+    __shared__ T sL[NC * NCOEF_MAX * 2];
+    const int cell = leaves[blockIdx.x];
+    const double4 cc = cs[cell];
+    const int2 r = range[cell];
+    const int nco = ncoef(p);
+    const T* Lc = L + (size_t)cell * NC * NCOEF_MAX * 2;
+    for (int idx = threadIdx.x; idx < NC * nco; idx += blockDim.x) {
+        const int c = idx / nco, q = idx % nco;
+        sL[(c * NCOEF_MAX + q) * 2] = Lc[c * NCOEF_MAX * 2 + 2 * q];
+        sL[(c * NCOEF_MAX + q) * 2 + 1] = Lc[c * NCOEF_MAX * 2 + 2 * q + 1];
+    }
+    __syncthreads();
+    const double inv_s = 1.0 / cc.w;
+    for (int i = r.x + threadIdx.x; i < r.y; i += blockDim.x) {
+        const double4 x = tgt[i];
+        const T vx = T((x.x - cc.x) * inv_s), vy = T((x.y - cc.y) * inv_s), vz = T((x.z - cc.z) * inv_s);
+        const T r2 = vx * vx + vy * vy + vz * vz;
+        const cpx<T> xy = mk(vx, vy);
+        T phi[NC], gz[NC];
+        cpx<T> F[NC];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) { phi[c] = 0; gz[c] = 0; F[c] = mk(T(0), T(0)); }
+        cpx<T> diag = mk(T(1), T(0));
+        auto use = [&](int n, int m, cpx<T> R) {
+            const T wgt = m ? T(2) : T(1);
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+                const T* Lb = sL + c * NCOEF_MAX * 2;
+                const cpx<T> a = ld(Lb, cidx(n, m));
+                phi[c] += wgt * (a.re * R.re - a.im * R.im);
+                if (NC > 1 && n + 1 <= p) {
+                    const cpx<T> b = ld(Lb, cidx(n + 1, m));
+                    gz[c] += wgt * (b.re * R.re - b.im * R.im);
+                    if (m >= 1) cfma(F[c], ld(Lb, cidx(n + 1, m - 1)), R);
+                    const cpx<T> d = ld(Lb, cidx(n + 1, m + 1)) * R;
+                    F[c].re -= d.re;
+                    F[c].im += d.im;
+                }
+            }
+        };
+        for (int m = 0; m <= p; ++m) {
+            if (m > 0) diag = (T(-0.5) / T(m)) * (xy * diag);
+            use(m, m, diag);
+            if (m + 1 > p) break;
+            cpx<T> prev2 = diag, prev1 = vz * diag;
+            use(m + 1, m, prev1);
+            for (int n = m + 2; n <= p; ++n) {
+                const T inv = T(1) / T((n - m) * (n + m));
+                cpx<T> cur = mk((T(2 * n - 1) * vz * prev1.re - r2 * prev2.re) * inv,
+                                (T(2 * n - 1) * vz * prev1.im - r2 * prev2.im) * inv);
+                use(n, m, cur);
+                prev2 = prev1;
+                prev1 = cur;
+            }
+        }
+        if (NC == 1) {
+            const double far = (double)phi[0] * inv_s;
+            yout[i] = scale * (far + ynear[i]);
+        } else {
+            const double is2 = inv_s * inv_s;
+            const double px = x.x - ox, py = x.y - oy, pz = x.z - oz;
+            double g[NC][3];
+#pragma unroll
+            for (int c = 0; c < NC; ++c) { g[c][0] = (double)F[c].re * is2; g[c][1] = (double)F[c].im * is2; g[c][2] = (double)gz[c] * is2; }
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                const double u = (double)phi[a] * inv_s - (px * g[0][a] + py * g[1][a] + pz * g[2][a]) + g[NC - 1][a];
+                yout[3 * (int64_t)i + a] = scale * (u + ynear[3 * (int64_t)i + a]);
+            }
+        }
+    }
+}
+
+__global__ void k_octant_tables(double* od, float* of) {
+    const int o = threadIdx.x;
+    if (o >= 8) return;
+    cpx<double> tab[NCOEF_MAX];
+    regular_table<double>((o & 1) ? 0.25 : -0.25, (o & 2) ? 0.25 : -0.25, (o & 4) ? 0.25 : -0.25, PMAX, tab);
+    for (int q = 0; q < NCOEF_MAX; ++q) {
+        od[(o * NCOEF_MAX + q) * 2] = tab[q].re;
+        od[(o * NCOEF_MAX + q) * 2 + 1] = tab[q].im;
+        of[(o * NCOEF_MAX + q) * 2] = (float)tab[q].re;
+        of[(o * NCOEF_MAX + q) * 2 + 1] = (float)tab[q].im;
+    }
+}
+
+// Single expansions for fmmbem_expansion_eval (FP64): kind 0 multipole, 1 local.
+__global__ void k_form_expansion(int kind, int p, double cx, double cy, double cz, double s, int ns, const double4* src,
+                                 double* E) {
+    const int nco = ncoef(p);
+    const int t = threadIdx.x;
+    if (t >= nco) return;
+    int n, m;
+    decode(t, n, m);
+    cpx<double> acc = mk(0.0, 0.0);
+    cpx<double> tab[NCOEF_MAX];
+    for (int j = 0; j < ns; ++j) {
+        const double4 y = src[j];
+        const double vx = (y.x - cx) / s, vy = (y.y - cy) / s, vz = (y.z - cz) / s;
+        if (kind == 0) regular_table<double>(vx, vy, vz, n, tab);
+        else irregular_table<double>(vx, vy, vz, n, tab);
+        const cpx<double> v = tab[cidx(n, m)];
+        acc.re += y.w * v.re;
+        acc.im -= y.w * v.im;
+    }
+    E[2 * t] = acc.re;
+    E[2 * t + 1] = acc.im;
+}
+
+__global__ void k_eval_expansion(int kind, int p, double cx, double cy, double cz, double s, const double* E, int nt,
+                                 const double* tgt, double* out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nt) return;
+    const double vx = (tgt[3 * i] - cx) / s, vy = (tgt[3 * i + 1] - cy) / s, vz = (tgt[3 * i + 2] - cz) / s;
+    cpx<double> tab[NCOEF_MAX];
+    if (kind == 0) irregular_table<double>(vx, vy, vz, p, tab);
+    else regular_table<double>(vx, vy, vz, p, tab);
+    double phi = 0.0;
+    for (int n = 0; n <= p; ++n)
+        for (int m = 0; m <= n; ++m) {
+            const cpx<double> a = mk(E[2 * cidx(n, m)], E[2 * cidx(n, m) + 1]), b = tab[cidx(n, m)];
+            phi += (m ? 2.0 : 1.0) * (a.re * b.re - a.im * b.im);
+        }
+    out[i] = phi / s;
+}
+
+bool g_deg_ready = false;
+
+int ensure_degree_table() {
+    if (g_deg_ready) return 0;
+    unsigned char deg[NCOEF_MAX];
+    for (int n = 0; n <= PMAX; ++n)
+        for (int m = 0; m <= n; ++m) deg[cidx(n, m)] = (unsigned char)n;
+    FMM_CU(cudaMemcpyToSymbol(c_deg, deg, sizeof(deg)));
+    g_deg_ready = true;
+    return 0;
+}
+
+unsigned m2l_block(int p) { return (unsigned)((ncoef(p) > 2 * p + 1 ? ncoef(p) : 2 * p + 1) + 31) / 32 * 32; }
+unsigned coef_block(int p) { return (unsigned)(ncoef(p) + 31) / 32 * 32; }
+
+template <typename T, int NC>
+int far_field_t(fmmbem_handle* h, int p) {
+    cudaStream_t st = h->stream;
+    T* M = reinterpret_cast<T*>(h->M);
+    T* L = reinterpret_cast<T*>(h->L);
+    const T* oct = std::is_same<T, float>::value ? reinterpret_cast<const T*>(h->oct_f) : reinterpret_cast<const T*>(h->oct_d);
+    const typename V4<T>::type* src;
+    if (std::is_same<T, float>::value) src = reinterpret_cast<const typename V4<T>::type*>(h->src_f);
+    else src = reinterpret_cast<const typename V4<T>::type*>(h->src_d);
+    const int nco = ncoef(p);
+    // P2M
+    prof_begin(h, FMMBEM_PASS_P2M);
+    const size_t sm = (size_t)P2M_WARPS * NC * nco * 2 * sizeof(T);
+    k_p2m<T, NC><<<h->n_leaves, 32 * P2M_WARPS, sm, st>>>(p, h->leaves, h->cell_cs, h->cell_range, src, h->xin, h->K,
+                                                         h->origin[0], h->origin[1], h->origin[2], M);
+    FMM_LAUNCHED();
+    prof_end(h, FMMBEM_PASS_P2M, 1);
+    // M2M, deepest non-leaf level first
+    prof_begin(h, FMMBEM_PASS_M2M);
+    int nl = 0;
+    for (int l = h->n_levels - 2; l >= 0; --l) {
+        const int lb = h->level_start[l], le = h->level_start[l + 1];
+        k_m2m<T, NC><<<le - lb, coef_block(p), 0, st>>>(p, lb, h->cell_cs, h->cell_child, oct, M);
+        FMM_LAUNCHED();
+        ++nl;
+    }
+    prof_end(h, FMMBEM_PASS_M2M, nl);
+    // M2L
+    prof_begin(h, FMMBEM_PASS_M2L);
+    k_m2l<T, NC><<<h->n_cells, m2l_block(p), 0, st>>>(p, h->m2l_ptr, h->m2l_src, h->cell_cs, M, L);
+    FMM_LAUNCHED();
+    prof_end(h, FMMBEM_PASS_M2L, 1);
+    // L2L, top-down
+    prof_begin(h, FMMBEM_PASS_L2L);
+    nl = 0;
+    for (int l = 1; l < h->n_levels; ++l) {
+        const int lb = h->level_start[l], le = h->level_start[l + 1];
+        k_l2l<T, NC><<<le - lb, coef_block(p), 0, st>>>(p, lb, h->cell_cs, h->cell_parent, oct, L);
+        FMM_LAUNCHED();
+        ++nl;
+    }
+    prof_end(h, FMMBEM_PASS_L2L, nl);
+    h->launches += 2 + 2 * (h->n_levels - 1);
+    return 0;
+}
+
+template <typename T, int NC>
+int far_eval_t(fmmbem_handle* h, int p, double* y_sorted, double scale) {
+    prof_begin(h, FMMBEM_PASS_L2P);
+    k_l2p<T, NC><<<h->n_leaves, 128, 0, h->stream>>>(p, h->leaves, h->cell_cs, h->cell_range, h->tgt_d,
+                                                    reinterpret_cast<const T*>(h->L), h->ynear, scale, h->origin[0],
+                                                    h->origin[1], h->origin[2], y_sorted);
+    FMM_LAUNCHED();
+    prof_end(h, FMMBEM_PASS_L2P, 1);
+    h->launches += 1;
+    return 0;
+}
+
+}  // namespace
+
+int init_octant_tables(fmmbem_handle* h) {
+    FMM_TRY(ensure_degree_table());
+    FMM_CU(cudaMalloc((void**)&h->oct_d, sizeof(double) * 8 * NCOEF_MAX * 2));
+    FMM_CU(cudaMalloc((void**)&h->oct_f, sizeof(float) * 8 * NCOEF_MAX * 2));
+    k_octant_tables<<<1, 8, 0, h->stream>>>(h->oct_d, h->oct_f);
+    FMM_LAUNCHED();
+    return 0;
+}
+
+int far_field(fmmbem_handle* h, int p, bool fp64) {
+    if (h->ncomp == 1) return fp64 ? far_field_t<double, 1>(h, p) : far_field_t<float, 1>(h, p);
+    return fp64 ? far_field_t<double, 4>(h, p) : far_field_t<float, 4>(h, p);
+}
+
+int far_eval_add(fmmbem_handle* h, int p, bool fp64, double* y_sorted, double scale) {
+    if (h->ncomp == 1) return fp64 ? far_eval_t<double, 1>(h, p, y_sorted, scale) : far_eval_t<float, 1>(h, p, y_sorted, scale);
+    return fp64 ? far_eval_t<double, 4>(h, p, y_sorted, scale) : far_eval_t<float, 4>(h, p, y_sorted, scale);
+}
+
+int expansion_eval(int kind, int p, const double* center, double scale, int n_src, const double* src, int n_tgt,
+                   const double* tgt, double* out, cudaStream_t st) {
+    FMM_TRY(ensure_degree_table());
+    double* E = nullptr;
+    FMM_CU(cudaMalloc((void**)&E, sizeof(double) * NCOEF_MAX * 2));
+    k_form_expansion<<<1, coef_block(p), 0, st>>>(kind, p, center[0], center[1], center[2], scale, n_src,
+                                                  reinterpret_cast<const double4*>(src), E);
+    FMM_LAUNCHED();
+    if (n_tgt > 0) {
+        k_eval_expansion<<<(n_tgt + 127) / 128, 128, 0, st>>>(kind, p, center[0], center[1], center[2], scale, E, n_tgt,
+                                                             tgt, out);
+        FMM_LAUNCHED();
+    }
+    FMM_CU(cudaStreamSynchronize(st));
+    cudaFree(E);
+    return 0;
+}
+
+}  // namespace fmmbem

@@ -1,0 +1,113 @@
+// Internal state of an fmmbem_handle: geometry, octree, interaction lists,
+// correction table and work buffers, all resident in device memory.
+#pragma once
+#include <vector>
+#include "common.cuh"
+
+struct fmmbem_handle {
+    // problem
+    int kernel = FMMBEM_LAPLACE;  // FMMBEM_LAPLACE or FMMBEM_STOKES
+    int dof = 1;                  // unknowns per panel
+    int ncomp = 1;                // harmonic expansions per cell (1 Laplace, 4 Stokes)
+    int K = 4;                    // far-field Gauss points per panel
+    int ncrit = 150;
+    double theta = 0.5;
+    fmmbem_opts opts{};
+    int precision = FMMBEM_MIXED;
+    cudaStream_t stream = nullptr;
+    int64_t N = 0;   // panels
+    int64_t NS = 0;  // Gauss points = K * N
+
+    // geometry, in Morton-sorted panel order
+    int* perm = nullptr;          // [N] sorted index -> caller's index
+    double4* tgt_d = nullptr;     // [N] centroid (x,y,z, area)
+    float4* tgt_f = nullptr;
+    double4* nrm_d = nullptr;     // [N] unit normal (x,y,z, area)
+    double* verts = nullptr;      // [N][9] panel vertices
+    double4* src_d = nullptr;     // [NS] Gauss point (x,y,z, q_k S_j), panel-major
+    float4* src_f = nullptr;
+    double origin[3] = {0, 0, 0};  // root-box centre; Stokes y.f strengths use it
+    double half = 1.0;             // root-box half side
+    double spill = 0.0;            // largest centroid-to-vertex distance
+
+    // octree (cells in breadth-first order, levels contiguous)
+    int n_cells = 0, n_leaves = 0, n_levels = 0;
+    std::vector<int> level_start;  // host, [n_levels + 1]
+    double4* cell_cs = nullptr;    // [n_cells] centre (x,y,z) and side
+    int2* cell_range = nullptr;    // [n_cells] sorted panel range [begin, end)
+    int2* cell_child = nullptr;    // [n_cells] first child, number of children (0 = leaf)
+    int* cell_level = nullptr;
+    int* cell_parent = nullptr;
+    int* leaves = nullptr;         // [n_leaves] cell ids
+
+    // interaction lists (CSR by target cell)
+    int* m2l_ptr = nullptr;  // [n_cells + 1]
+    int* m2l_src = nullptr;
+    int64_t n_m2l = 0, n_m2l_same = 0;
+    int* p2p_ptr = nullptr;  // [n_cells + 1]
+    int* p2p_src = nullptr;
+    int64_t n_p2p = 0, n_p2p_inter = 0;
+    int max_leaf_panels = 0;
+
+    // near-singular / self corrections (CSR by sorted target panel), FP64
+    int* corr_ptr = nullptr;   // [N + 1]
+    int* corr_col = nullptr;
+    double* corr_sl = nullptr;  // single layer: 1 (Laplace) or 9 (Stokes) per entry
+    double* corr_dl = nullptr;  // double layer / stresslet
+    int64_t n_corr = 0;
+
+    // octant translation tables: R_n^m((+-1/4, +-1/4, +-1/4)) for the 8 children
+    double* oct_d = nullptr;  // [8][NCOEF_MAX][2]
+    float* oct_f = nullptr;
+
+    // expansions: [n_cells][ncomp][NCOEF_MAX] complex, FP32 or FP64 view
+    void* M = nullptr;
+    void* L = nullptr;
+
+    // mat-vec work, sorted order
+    const double* xin = nullptr;  // input of the mat-vec in flight (sorted order)
+    double* xs = nullptr;     // [N*dof]
+    double* ys = nullptr;     // [N*dof]
+    double* ynear = nullptr;  // [N*dof]
+
+    // Krylov work
+    int kr_m = 0;
+    double* V = nullptr;        // [(m+1) * n]
+    double* kw = nullptr;       // [n]
+    double* kb = nullptr;       // [n] sorted rhs
+    double* kx = nullptr;       // [n] sorted solution
+    double* kr = nullptr;       // [n] residual
+    double* kpart = nullptr;    // partial dots
+    double* kh = nullptr;       // [m+2] dot results
+    double* kh_host = nullptr;  // pinned
+    double* kyv = nullptr;      // [m] update coefficients
+
+    // timing
+    double setup_seconds = 0.0;
+    bool prof_on = false;
+    fmmbem_profile prof{};
+    cudaEvent_t ev[2 * FMMBEM_N_PASSES] = {};
+    int64_t launches = 0;
+};
+
+namespace fmmbem {
+// setup.cu
+int build_geometry_tree_lists(fmmbem_handle* h, const fmmbem_mesh* mesh);
+// fmm.cu
+int far_field(fmmbem_handle* h, int p, bool fp64);
+int far_eval_add(fmmbem_handle* h, int p, bool fp64, double* y_sorted, double scale);
+int expansion_eval(int kind, int p, const double* center, double scale, int n_src, const double* src,
+                   int n_tgt, const double* tgt, double* out, cudaStream_t st);
+int init_octant_tables(fmmbem_handle* h);
+// near.cu
+int near_field(fmmbem_handle* h, bool fp64);
+int direct_field(fmmbem_handle* h, bool fp64, int which, const double* x_sorted, double* y_sorted);
+// krylov.cu
+int relaxed_p(double eta, double rho_prev, int p_initial, int p_min);
+int gmres_solve(fmmbem_handle* h, const double* b_sorted, double tol, int relax, int p_initial, int p_min,
+                double* x_sorted, int* iters, int* p_hist, double* res_hist, double* true_res);
+// capi.cu
+int matvec_sorted(fmmbem_handle* h, int p, const double* xs, double* ys);
+void prof_begin(fmmbem_handle* h, int pass);
+void prof_end(fmmbem_handle* h, int pass, int launches);
+}  // namespace fmmbem

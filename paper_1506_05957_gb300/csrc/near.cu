@@ -1,0 +1,276 @@
+// Near field of the FMM mat-vec and the direct (all-pairs) operators.
+//
+// P2P (Sec. 2.5): for every target leaf, the K-point sums (eq. gauss:1st-kind) over
+// the Gauss points of the leaves in its P2P list, skipping the target's own panel;
+// then the FP64 correction row (near-singular 20-point rule minus K-point rule, and
+// the semi-analytic self integral, Sec. 2.3) is added. Sources are staged in
+// shared memory per tile; each target is shared by several threads ("slices")
+// that take interleaved sources, so small leaves still fill the block. Tile sums
+// run in the arithmetic type and are accumulated in FP64.
+//
+// Direct: the same sums over every Gauss point (the Appendix mat-vec algorithm),
+// for the single layers and for the double layers used by the right-hand side
+// (eq. laplace_bem_dGdn) and the stresslet operator (eq. stresslet).
+#include <type_traits>
+#include "handle.cuh"
+
+namespace fmmbem {
+
+namespace {
+
+constexpr int P2P_THREADS = 128;
+constexpr int P2P_TILE = 512;
+
+enum Op { LAP_SL = 0, LAP_DL = 1, STK_SL = 2, STK_DL = 3 };
+
+template <int OP> struct OpDof { static constexpr int v = (OP == STK_SL || OP == STK_DL) ? 3 : 1; };
+
+// Accumulate one source into acc (unscaled kernel sums).
+//   LAP_SL : w / r
+//   LAP_DL : w n.d / r^3                      (d = x - y)
+//   STK_SL : f / r + d (d.f) / r^3            (f = w t)
+//   STK_DL : 6 d (d.u)(e.n) / r^5, e = -d     (w folded into u)
+template <typename T, int OP>
+__device__ __forceinline__ void interact(T dx, T dy, T dz, const T* s, T* acc) {
+    const T r2 = dx * dx + dy * dy + dz * dz;
+    const T ir = rsqrt_t<T>(r2);
+    if (OP == LAP_SL) {
+        acc[0] += s[0] * ir;
+    } else if (OP == LAP_DL) {
+        const T ir3 = ir * ir * ir;
+        acc[0] += s[0] * (dx * s[1] + dy * s[2] + dz * s[3]) * ir3;
+    } else if (OP == STK_SL) {
+        const T ir3 = ir * ir * ir;
+        const T df = (dx * s[0] + dy * s[1] + dz * s[2]) * ir3;
+        acc[0] += s[0] * ir + dx * df;
+        acc[1] += s[1] * ir + dy * df;
+        acc[2] += s[2] * ir + dz * df;
+    } else {
+        const T ir2 = ir * ir;
+        const T ir5 = ir2 * ir2 * ir;
+        const T du = dx * s[0] + dy * s[1] + dz * s[2];
+        const T en = -(dx * s[3] + dy * s[4] + dz * s[5]);
+        const T f = T(6) * du * en * ir5;
+        acc[0] += dx * f;
+        acc[1] += dy * f;
+        acc[2] += dz * f;
+    }
+}
+
+template <int OP> struct SrcWidth { static constexpr int v = (OP == LAP_SL) ? 1 : (OP == LAP_DL ? 4 : (OP == STK_SL ? 3 : 6)); };
+
+// Stage source q (global Gauss-point index) into shared memory: position + strength terms.
+template <typename T, int OP>
+__device__ __forceinline__ void stage(int g, const typename V4<T>::type* src, const double* xs, const double4* nrm, int K,
+                                      T* spos, T* sval, int slot) {
+    const auto y = src[g];
+    const int pj = g / K;
+    spos[3 * slot] = y.x;
+    spos[3 * slot + 1] = y.y;
+    spos[3 * slot + 2] = y.z;
+    constexpr int W = SrcWidth<OP>::v;
+    T* v = sval + W * slot;
+    const double w = (double)y.w;
+    if (OP == LAP_SL) {
+        v[0] = T(w * xs[pj]);
+    } else if (OP == LAP_DL) {
+        const double4 n = nrm[pj];
+        v[0] = T(w * xs[pj]);
+        v[1] = T(n.x); v[2] = T(n.y); v[3] = T(n.z);
+    } else if (OP == STK_SL) {
+        v[0] = T(w * xs[3 * pj]); v[1] = T(w * xs[3 * pj + 1]); v[2] = T(w * xs[3 * pj + 2]);
+    } else {
+        const double4 n = nrm[pj];
+        v[0] = T(w * xs[3 * pj]); v[1] = T(w * xs[3 * pj + 1]); v[2] = T(w * xs[3 * pj + 2]);
+        v[3] = T(n.x); v[4] = T(n.y); v[5] = T(n.z);
+    }
+}
+
+// Add the correction row of target i: sum_e C_e x_{col_e} (1x1 or 3x3 blocks), FP64.
+template <int DOF>
+__device__ __forceinline__ void add_correction(int i, const int* cptr, const int* ccol, const double* cval,
+                                               const double* xs, double* out) {
+    for (int e = cptr[i]; e < cptr[i + 1]; ++e) {
+        const int j = ccol[e];
+        if (DOF == 1) {
+            out[0] += cval[e] * xs[j];
+        } else {
+            const double* B = cval + 9 * (int64_t)e;
+            const double x0 = xs[3 * j], x1 = xs[3 * j + 1], x2 = xs[3 * j + 2];
+            out[0] += B[0] * x0 + B[1] * x1 + B[2] * x2;
+            out[1] += B[3] * x0 + B[4] * x1 + B[5] * x2;
+            out[2] += B[6] * x0 + B[7] * x1 + B[8] * x2;
+        }
+    }
+}
+
+// Near field: one block per target leaf.
+template <typename T, int OP>
+__global__ void __launch_bounds__(P2P_THREADS) k_p2p(const int* leaves, const int2* range, const int* pptr,
+                                                     const int* psrc, const typename V4<T>::type* src,
+                                                     const double4* tgt, const double* xs, const double4* nrm, int K,
+                                                     const int* cptr, const int* ccol, const double* cval,
+                                                     double* ynear) {
+    constexpr int DOF = OpDof<OP>::v;
+    constexpr int W = SrcWidth<OP>::v;
+    __shared__ T spos[3 * P2P_TILE];
+    __shared__ T sval[W * P2P_TILE];
+    __shared__ double sred[P2P_THREADS * DOF];
+    const int cell = leaves[blockIdx.x];
+    const int2 r = range[cell];
+    const int tid = threadIdx.x;
+    for (int tb = r.x; tb < r.y; tb += P2P_THREADS) {
+        const int chunk = min(P2P_THREADS, r.y - tb);
+        const int nsl = max(1, P2P_THREADS / chunk);
+        const int ti = tid % chunk, sl = tid / chunk;
+        const bool active = sl < nsl;
+        const int i = tb + ti;
+        const double4 xi = tgt[i];
+        const T tx = T(xi.x), ty = T(xi.y), tz = T(xi.z);
+        double acc[DOF];
+#pragma unroll
+        for (int a = 0; a < DOF; ++a) acc[a] = 0.0;
+        for (int e = pptr[cell]; e < pptr[cell + 1]; ++e) {
+            const int sc = psrc[e];
+            const int2 sr = range[sc];
+            const int g0 = sr.x * K, g1 = sr.y * K;
+            const bool self_leaf = (sc == cell);
+            for (int gb = g0; gb < g1; gb += P2P_TILE) {
+                const int nt = min(P2P_TILE, g1 - gb);
+                __syncthreads();
+                for (int q = tid; q < nt; q += P2P_THREADS) stage<T, OP>(gb + q, src, xs, nrm, K, spos, sval, q);
+                __syncthreads();
+                if (active) {
+                    T part[DOF];
+#pragma unroll
+                    for (int a = 0; a < DOF; ++a) part[a] = T(0);
+                    if (!self_leaf) {
+                        for (int q = sl; q < nt; q += nsl)
+                            interact<T, OP>(tx - spos[3 * q], ty - spos[3 * q + 1], tz - spos[3 * q + 2], sval + W * q, part);
+                    } else {
+                        const int own0 = i * K - gb;  // the target's own Gauss points are skipped
+                        for (int q = sl; q < nt; q += nsl) {
+                            if ((unsigned)(q - own0) < (unsigned)K) continue;
+                            interact<T, OP>(tx - spos[3 * q], ty - spos[3 * q + 1], tz - spos[3 * q + 2], sval + W * q, part);
+                        }
+                    }
+#pragma unroll
+                    for (int a = 0; a < DOF; ++a) acc[a] += (double)part[a];
+                }
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int a = 0; a < DOF; ++a) sred[tid * DOF + a] = active ? acc[a] : 0.0;
+        __syncthreads();
+        if (sl == 0 && ti < chunk) {
+            double out[DOF];
+#pragma unroll
+            for (int a = 0; a < DOF; ++a) out[a] = 0.0;
+            for (int s = 0; s < nsl; ++s)
+#pragma unroll
+                for (int a = 0; a < DOF; ++a) out[a] += sred[(s * chunk + ti) * DOF + a];
+            add_correction<DOF>(i, cptr, ccol, cval, xs, out);
+#pragma unroll
+            for (int a = 0; a < DOF; ++a) ynear[(int64_t)DOF * i + a] = out[a];
+        }
+    }
+}
+
+// Direct: one thread per target, every Gauss point staged through shared memory.
+template <typename T, int OP>
+__global__ void __launch_bounds__(P2P_THREADS) k_direct(int n, int ns, const typename V4<T>::type* src,
+                                                        const double4* tgt, const double* xs, const double4* nrm, int K,
+                                                        const int* cptr, const int* ccol, const double* cval,
+                                                        double scale, double* y) {
+    constexpr int DOF = OpDof<OP>::v;
+    constexpr int W = SrcWidth<OP>::v;
+    __shared__ T spos[3 * P2P_TILE];
+    __shared__ T sval[W * P2P_TILE];
+    const int i = blockIdx.x * P2P_THREADS + threadIdx.x;
+    const bool active = i < n;
+    double4 xi = active ? tgt[i] : make_double4(0, 0, 0, 0);
+    const T tx = T(xi.x), ty = T(xi.y), tz = T(xi.z);
+    double acc[DOF];
+#pragma unroll
+    for (int a = 0; a < DOF; ++a) acc[a] = 0.0;
+    const int own0 = i * K;
+    for (int gb = 0; gb < ns; gb += P2P_TILE) {
+        const int nt = min(P2P_TILE, ns - gb);
+        __syncthreads();
+        for (int q = threadIdx.x; q < nt; q += P2P_THREADS) stage<T, OP>(gb + q, src, xs, nrm, K, spos, sval, q);
+        __syncthreads();
+        if (active) {
+            T part[DOF];
+#pragma unroll
+            for (int a = 0; a < DOF; ++a) part[a] = T(0);
+            for (int q = 0; q < nt; ++q) {
+                if ((unsigned)(gb + q - own0) < (unsigned)K) continue;
+                interact<T, OP>(tx - spos[3 * q], ty - spos[3 * q + 1], tz - spos[3 * q + 2], sval + W * q, part);
+            }
+#pragma unroll
+            for (int a = 0; a < DOF; ++a) acc[a] += (double)part[a];
+        }
+    }
+    if (!active) return;
+    add_correction<DOF>(i, cptr, ccol, cval, xs, acc);
+#pragma unroll
+    for (int a = 0; a < DOF; ++a) y[(int64_t)DOF * i + a] = scale * acc[a];
+}
+
+template <typename T, int OP>
+int launch_p2p(fmmbem_handle* h) {
+    const typename V4<T>::type* src = std::is_same<T, float>::value
+                                          ? reinterpret_cast<const typename V4<T>::type*>(h->src_f)
+                                          : reinterpret_cast<const typename V4<T>::type*>(h->src_d);
+    k_p2p<T, OP><<<h->n_leaves, P2P_THREADS, 0, h->stream>>>(h->leaves, h->cell_range, h->p2p_ptr, h->p2p_src, src,
+                                                             h->tgt_d, h->xin, h->nrm_d, h->K, h->corr_ptr, h->corr_col,
+                                                             h->corr_sl, h->ynear);
+    FMM_LAUNCHED();
+    return 0;
+}
+
+template <typename T, int OP>
+int launch_direct(fmmbem_handle* h, const double* xs, double* y, const double* cval, double scale) {
+    const typename V4<T>::type* src = std::is_same<T, float>::value
+                                          ? reinterpret_cast<const typename V4<T>::type*>(h->src_f)
+                                          : reinterpret_cast<const typename V4<T>::type*>(h->src_d);
+    const int n = (int)h->N;
+    k_direct<T, OP><<<(n + P2P_THREADS - 1) / P2P_THREADS, P2P_THREADS, 0, h->stream>>>(
+        n, (int)h->NS, src, h->tgt_d, xs, h->nrm_d, h->K, h->corr_ptr, h->corr_col, cval, scale, y);
+    FMM_LAUNCHED();
+    return 0;
+}
+
+}  // namespace
+
+int near_field(fmmbem_handle* h, bool fp64) {
+    prof_begin(h, FMMBEM_PASS_P2P);
+    int rc;
+    if (h->kernel == FMMBEM_LAPLACE) rc = fp64 ? launch_p2p<double, LAP_SL>(h) : launch_p2p<float, LAP_SL>(h);
+    else rc = fp64 ? launch_p2p<double, STK_SL>(h) : launch_p2p<float, STK_SL>(h);
+    prof_end(h, FMMBEM_PASS_P2P, 1);
+    h->launches += 1;
+    return rc;
+}
+
+// which: 0 single layer (scale of the operator), 1 double layer / stresslet.
+int direct_field(fmmbem_handle* h, bool fp64, int which, const double* xsorted, double* ysorted) {
+    const double pi = 3.14159265358979323846;
+    h->launches += 1;
+    if (h->kernel == FMMBEM_LAPLACE) {
+        const double sc = 1.0 / (4.0 * pi);
+        if (which == 0)
+            return fp64 ? launch_direct<double, LAP_SL>(h, xsorted, ysorted, h->corr_sl, sc)
+                        : launch_direct<float, LAP_SL>(h, xsorted, ysorted, h->corr_sl, sc);
+        return launch_direct<double, LAP_DL>(h, xsorted, ysorted, h->corr_dl, sc);
+    }
+    if (which == 0) {
+        const double sc = -1.0 / (8.0 * pi * h->opts.mu);
+        return fp64 ? launch_direct<double, STK_SL>(h, xsorted, ysorted, h->corr_sl, sc)
+                    : launch_direct<float, STK_SL>(h, xsorted, ysorted, h->corr_sl, sc);
+    }
+    return launch_direct<double, STK_DL>(h, xsorted, ysorted, h->corr_dl, 1.0 / (8.0 * pi));
+}
+
+}  // namespace fmmbem
