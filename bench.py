@@ -1,0 +1,337 @@
+"""Benchmark: relaxed GMRES solve of the Laplace first-kind BEM on a sphere of
+81920 panels (icosahedron refined 6 times, K = 4 Gauss points, Dirichlet data
+of a unit point charge at (0,0,3), theta = 0.5, p relaxed from 12 to 3, tol
+1e-6, FP32 passes with FP64 Krylov recurrence), one full solve per step.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line. Under torchrun each rank solves its own copy of the
+problem (replicas: the path has no exchange step at this size) and rank 0
+reports the slowest rank's time.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "relaxed GMRES solve s (and matvec/s, % roofline) vs fixed-p FP64 on 1 GB300 @1e-5 err"
+WORKLOAD = dict(workload="laplace-sphere-ico6-81920", panels=81920, gauss_k=4, theta=0.5, p_initial=12, p_min=3,
+                tol=1e-6, restart=50, ncrit=400, data="unit point charge at (0,0,3)")
+L2_FLUSH_BYTES = 512 << 20
+SM_COUNT = 152
+FP32_LANES_PER_SM = 128
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--levels", type=int, default=6)
+    ap.add_argument("--ncrit", type=int, default=WORKLOAD["ncrit"])
+    ap.add_argument("--no-compare", action="store_true", help="skip the FP64 comparison solves")
+    return ap.parse_args()
+
+
+def dist_init(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if args.impl == "ours" else "gloo"
+        dist.init_process_group(backend)
+    return world, rank, local
+
+
+def barrier(world, dev=None):
+    if world > 1:
+        import torch.distributed as dist
+        if dev is not None:
+            dist.barrier(device_ids=[dev.index])
+        else:
+            dist.barrier()
+
+
+def max_over_ranks(world, value, dev=None):
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=dev if dev is not None else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+class ClockSampler:
+    """nvidia-smi samples during the timed region: SM clock and throttle reasons."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def problem(levels):
+    from synth import icosphere, point_charge_dirichlet
+    v, t = icosphere(levels)
+    a, b, c = v[t[:, 0]], v[t[:, 1]], v[t[:, 2]]
+    phi = point_charge_dirichlet((a + b + c) / 3.0)  # Dirichlet data at the collocation points
+    return v, t, phi
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+def oracle_sample(v, t, phi, n_rows, seed=0, reps=1):
+    """Time the oracle's dense FP64 rows (the CPU baseline) on a sample of rows."""
+    from oracle import dense
+    M = dense.Mesh(v, t, k=WORKLOAD["gauss_k"])
+    rows = np.random.default_rng(seed).choice(len(t), n_rows, replace=False)
+    x = np.random.default_rng(seed + 1).standard_normal(len(t))
+    M.laplace_apply(x, rows=rows[:8])  # load/compile outside the timing
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        M.laplace_apply(x, rows=rows)
+    dt = (time.perf_counter() - t0) / reps
+    return dt, M
+
+
+def run_reference(args, world, rank):
+    """The oracle (plain FP64 dense BEM + textbook GMRES) on the host cores; each step
+    is a bounded sample of rows of the mat-vec, scaled to one full solve."""
+    if rank != 0:
+        return
+    v, t, phi = problem(args.levels)
+    n = len(t)
+    # mat-vecs of one solve at this size: 26 Arnoldi steps of the exact (fixed-p FP64)
+    # GMRES plus the final true residual
+    iters = 27
+    rows = 384
+    threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    for _ in range(args.warmup):
+        oracle_sample(v, t, phi, 32)
+    times = []
+    for k in range(args.steps):
+        dt, _ = oracle_sample(v, t, phi, rows, seed=k)
+        times.append(dt / rows * n * iters)
+    value = float(np.mean(times))
+    sample = "%d of %d dense rows per step, scaled to %d mat-vecs (one solve)" % (rows, n, iters)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": value * 1e3, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": dict(WORKLOAD, ncrit=None, solver="oracle: dense FP64 collocation rows + textbook GMRES"),
+            "cpu_baseline": {"value": value, "unit": "s", "cores": threads, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, world, rank, local):
+    import torch
+    from paper_1506_05957_gb300 import FmmBem, FMMBEM_FP64, FMMBEM_MIXED, build
+    build.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    v, t, phi = problem(args.levels)
+    n = len(t)
+    W = WORKLOAD
+    h = FmmBem(v, t, gauss_k=W["gauss_k"], ncrit=args.ncrit, theta=W["theta"], p_max=16, restart=W["restart"],
+               max_iter=100, precision=FMMBEM_MIXED, stream=stream.cuda_stream)
+    stats = h.stats()
+    phi_d = torch.tensor(phi, dtype=torch.float64, device=dev)
+    b = torch.empty_like(phi_d)
+    h.rhs(phi_d, b)
+    x = torch.zeros_like(b)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    solve = lambda: h.solve(b, x, tol=W["tol"], relax=True, p_initial=W["p_initial"], p_min=W["p_min"])
+
+    for _ in range(args.warmup):
+        solve()
+    torch.cuda.synchronize(dev)
+    barrier(world, dev)
+    h.profile_enable(True)
+    sampler = ClockSampler(local)
+    sampler.start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    torch.cuda.synchronize(dev)
+    barrier(world, dev)
+    results = []
+    for k in range(args.steps):
+        flush.fill_(float(k))  # evict L2 between steps (512 MB > 129 MB L2)
+        ev[k][0].record(stream)
+        results.append(solve())
+        ev[k][1].record(stream)
+    torch.cuda.synchronize(dev)
+    barrier(world, dev)
+    clocks = sampler.stop()
+    prof = h.profile()
+    h.profile_enable(False)
+    step_ms = [a.elapsed_time(b_) for a, b_ in ev]
+    t_local = float(np.sum(step_ms)) / 1e3
+    t_max = max_over_ranks(world, t_local, dev)
+    sec_per_solve = t_max / args.steps / world  # whole job: world solves finish per step time
+    r = results[-1]
+    iters = r["iters"]
+    matvecs_per_solve = iters + 1  # Arnoldi steps + the final true-residual product
+    mv_per_s = matvecs_per_solve * args.steps * world / t_max
+
+    # end to end through the public API with host buffers (pinned), copies inside the timing
+    bh = torch.empty(n, dtype=torch.float64, pin_memory=True)
+    bh.copy_(b.cpu())
+    xh = torch.empty(n, dtype=torch.float64, pin_memory=True)
+    bn, xn = bh.numpy(), xh.numpy()
+    h.solve_host(bn, xn, tol=W["tol"], relax=True, p_initial=W["p_initial"], p_min=W["p_min"])
+    torch.cuda.synchronize(dev)
+    barrier(world, dev)
+    e2e_t = []
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        h.solve_host(bn, xn, tol=W["tol"], relax=True, p_initial=W["p_initial"], p_min=W["p_min"])
+        e2e_t.append(time.perf_counter() - t0)
+    e2e = max_over_ranks(world, float(np.sum(e2e_t)), dev) / args.steps / world
+
+    # roofline of the dominant kernel class (M2L at these sizes), measured with the
+    # library's CUDA events on the launching stream over the timed region
+    ms = prof["ms"]
+    m2l_tflops = prof["m2l_flops"] / (ms["m2l"] * 1e-3) / 1e12 if ms["m2l"] > 0 else 0.0
+    smax = clocks.get("sm_max_mhz") or measured_peaks().get("sm_max_mhz", 2070.0)
+    fp32_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * smax * 1e6 / 1e12
+    total_ms = sum(step_ms)
+    share = {k_: round(v_ / total_ms, 4) for k_, v_ in ms.items() if k_ != "matvec"}
+    roofline = {"bound": "alu", "kernel": "k_m2l (M2L, FP32 SIMT)", "achieved": round(m2l_tflops, 3),
+                "peak": round(fp32_peak, 2), "unit": "TFLOP/s", "frac": round(m2l_tflops / fp32_peak, 4),
+                "traffic": None,
+                "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x max SM clock (no measured FP32 peak)",
+                "flops_convention": "2 (p+1)^4 per M2L pair (dense real operator)",
+                "p2p_interactions_per_s": round(prof["p2p_interactions"] / (ms["p2p"] * 1e-3), 1) if ms["p2p"] else None,
+                "time_share": share}
+
+    out = {"metric": METRIC, "value": sec_per_solve, "unit": "s", "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": t_max / args.steps * 1e3, "higher_is_better": False,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+           "config": dict(W, ncrit=args.ncrit, panels=n, parallelism="replicas" if world > 1 else "single",
+                          l2="flushed between steps (512 MB write)", precision="mixed"),
+           "matvec_per_s": mv_per_s, "iters": iters, "p_hist": r["p_hist"], "true_residual": r["true_res"],
+           "gpu_launches": int(prof["kernel_launches"]),
+           "e2e": {"value": e2e, "unit": "s", "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 8 * n},
+           "roofline": roofline, "clocks": clocks,
+           "tree": {k_: stats[k_] for k_ in ("n_cells", "n_leaves", "n_m2l_pairs", "n_p2p_interactions",
+                                              "n_corrections", "setup_seconds")}}
+
+    if not args.no_compare:
+        # comparison solves on the same GPU (one each): fixed p, FP64 (the metric's
+        # denominator), relaxed FP64, fixed p mixed
+        def timed(prec, relax):
+            h.set_precision(prec)
+            x.zero_()
+            torch.cuda.synchronize(dev)
+            a, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            rr = h.solve(b, x, tol=W["tol"], relax=relax, p_initial=W["p_initial"], p_min=W["p_min"])
+            b_.record(stream)
+            torch.cuda.synchronize(dev)
+            return a.elapsed_time(b_) / 1e3, rr
+        t_fixed64, r64 = timed(FMMBEM_FP64, False)
+        t_relax64, _ = timed(FMMBEM_FP64, True)
+        t_fixed32, _ = timed(FMMBEM_MIXED, False)
+        h.set_precision(FMMBEM_MIXED)
+        out["compare"] = {"fixed_p_fp64_s": t_fixed64, "relaxed_fp64_s": t_relax64, "fixed_p_mixed_s": t_fixed32,
+                          "speedup_vs_fixed_p_fp64": t_fixed64 / (t_max / args.steps),
+                          "relaxation_speedup_fp64": t_fixed64 / t_relax64,
+                          "fixed_p_fp64_iters": r64["iters"]}
+
+    if rank == 0 and world == 1:
+        # parity evidence at full size: GPU solution vs oracle rows; CPU baseline
+        xs = x.cpu().numpy()
+        dt, M = oracle_sample(v, t, phi, 256, seed=7)
+        rows = np.random.default_rng(7).choice(n, 256, replace=False)
+        bs = b.cpu().numpy()[rows]
+        res = np.linalg.norm(M.laplace_apply(xs, rows=rows) - bs) / np.linalg.norm(bs)
+        out["oracle_residual_sampled"] = float(res)
+        rows_cpu = 512
+        dt, _ = oracle_sample(v, t, phi, rows_cpu, seed=3)
+        threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+        out["cpu_baseline"] = {"value": dt / rows_cpu * n * (iters + 1), "unit": "s", "cores": threads,
+                               "kind": "oracle",
+                               "sample": "%d of %d dense FP64 rows timed, scaled to %d mat-vecs (one solve)"
+                                         % (rows_cpu, n, iters + 1)}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    h.close()
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_init(args)
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+    else:
+        run_ours(args, world, rank, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -26,6 +26,8 @@ struct fmmbem_handle {
     double* verts = nullptr;      // [N][9] panel vertices
     double4* src_d = nullptr;     // [NS] Gauss point (x,y,z, q_k S_j), panel-major
     float4* src_f = nullptr;
+    float4* src_rel = nullptr;    // [NS] Gauss point relative to its leaf centre, FP32 (x,y,z, q_k S_j)
+    float4* tgt_rel = nullptr;    // [N] centroid relative to its leaf centre, FP32
     double origin[3] = {0, 0, 0};  // root-box centre; Stokes y.f strengths use it
     double half = 1.0;             // root-box half side
     double spill = 0.0;            // largest centroid-to-vertex distance

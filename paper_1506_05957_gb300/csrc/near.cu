@@ -104,13 +104,19 @@ __device__ __forceinline__ void add_correction(int i, const int* cptr, const int
     }
 }
 
-// Near field: one block per target leaf.
+// Near field: one block per target leaf. In FP32 the operands are leaf-relative:
+// target offsets from its leaf centre, source offsets from theirs, and the
+// leaf-to-leaf shift (FP64 difference of the centres) is added while staging, so
+// close pairs keep their relative precision. Partial sums run over at most 32
+// sources in the arithmetic type before they are added to the FP64 accumulator.
+constexpr int P2P_FLUSH = 32;
+
 template <typename T, int OP>
-__global__ void __launch_bounds__(P2P_THREADS) k_p2p(const int* leaves, const int2* range, const int* pptr,
-                                                     const int* psrc, const typename V4<T>::type* src,
-                                                     const double4* tgt, const double* xs, const double4* nrm, int K,
-                                                     const int* cptr, const int* ccol, const double* cval,
-                                                     double* ynear) {
+__global__ void __launch_bounds__(P2P_THREADS) k_p2p(const int* leaves, const double4* cs, const int2* range,
+                                                     const int* pptr, const int* psrc, const typename V4<T>::type* src,
+                                                     const typename V4<T>::type* tgt, bool relative, const double* xs,
+                                                     const double4* nrm, int K, const int* cptr, const int* ccol,
+                                                     const double* cval, double* ynear) {
     constexpr int DOF = OpDof<OP>::v;
     constexpr int W = SrcWidth<OP>::v;
     __shared__ T spos[3 * P2P_TILE];
@@ -118,6 +124,7 @@ __global__ void __launch_bounds__(P2P_THREADS) k_p2p(const int* leaves, const in
     __shared__ double sred[P2P_THREADS * DOF];
     const int cell = leaves[blockIdx.x];
     const int2 r = range[cell];
+    const double4 ccell = cs[cell];
     const int tid = threadIdx.x;
     for (int tb = r.x; tb < r.y; tb += P2P_THREADS) {
         const int chunk = min(P2P_THREADS, r.y - tb);
@@ -125,8 +132,8 @@ __global__ void __launch_bounds__(P2P_THREADS) k_p2p(const int* leaves, const in
         const int ti = tid % chunk, sl = tid / chunk;
         const bool active = sl < nsl;
         const int i = tb + ti;
-        const double4 xi = tgt[i];
-        const T tx = T(xi.x), ty = T(xi.y), tz = T(xi.z);
+        const auto xi = tgt[i];
+        const T tx = xi.x, ty = xi.y, tz = xi.z;
         double acc[DOF];
 #pragma unroll
         for (int a = 0; a < DOF; ++a) acc[a] = 0.0;
@@ -135,27 +142,42 @@ __global__ void __launch_bounds__(P2P_THREADS) k_p2p(const int* leaves, const in
             const int2 sr = range[sc];
             const int g0 = sr.x * K, g1 = sr.y * K;
             const bool self_leaf = (sc == cell);
+            T shx = 0, shy = 0, shz = 0;
+            if (relative) {
+                const double4 cc = cs[sc];
+                shx = T(cc.x - ccell.x);
+                shy = T(cc.y - ccell.y);
+                shz = T(cc.z - ccell.z);
+            }
             for (int gb = g0; gb < g1; gb += P2P_TILE) {
                 const int nt = min(P2P_TILE, g1 - gb);
                 __syncthreads();
-                for (int q = tid; q < nt; q += P2P_THREADS) stage<T, OP>(gb + q, src, xs, nrm, K, spos, sval, q);
+                for (int q = tid; q < nt; q += P2P_THREADS) {
+                    stage<T, OP>(gb + q, src, xs, nrm, K, spos, sval, q);
+                    spos[3 * q] += shx;
+                    spos[3 * q + 1] += shy;
+                    spos[3 * q + 2] += shz;
+                }
                 __syncthreads();
                 if (active) {
-                    T part[DOF];
+                    const int own0 = self_leaf ? i * K - gb : -(1 << 30);  // the target's own Gauss points are skipped
+                    for (int q0 = sl; q0 < nt; q0 += P2P_FLUSH * nsl) {
+                        const int q1 = min(nt, q0 + P2P_FLUSH * nsl);
+                        T part[DOF];
 #pragma unroll
-                    for (int a = 0; a < DOF; ++a) part[a] = T(0);
-                    if (!self_leaf) {
-                        for (int q = sl; q < nt; q += nsl)
-                            interact<T, OP>(tx - spos[3 * q], ty - spos[3 * q + 1], tz - spos[3 * q + 2], sval + W * q, part);
-                    } else {
-                        const int own0 = i * K - gb;  // the target's own Gauss points are skipped
-                        for (int q = sl; q < nt; q += nsl) {
-                            if ((unsigned)(q - own0) < (unsigned)K) continue;
-                            interact<T, OP>(tx - spos[3 * q], ty - spos[3 * q + 1], tz - spos[3 * q + 2], sval + W * q, part);
+                        for (int a = 0; a < DOF; ++a) part[a] = T(0);
+                        if (!self_leaf) {
+                            for (int q = q0; q < q1; q += nsl)
+                                interact<T, OP>(tx - spos[3 * q], ty - spos[3 * q + 1], tz - spos[3 * q + 2], sval + W * q, part);
+                        } else {
+                            for (int q = q0; q < q1; q += nsl) {
+                                if ((unsigned)(q - own0) < (unsigned)K) continue;
+                                interact<T, OP>(tx - spos[3 * q], ty - spos[3 * q + 1], tz - spos[3 * q + 2], sval + W * q, part);
+                            }
                         }
-                    }
 #pragma unroll
-                    for (int a = 0; a < DOF; ++a) acc[a] += (double)part[a];
+                        for (int a = 0; a < DOF; ++a) acc[a] += (double)part[a];
+                    }
                 }
             }
         }
@@ -220,12 +242,14 @@ __global__ void __launch_bounds__(P2P_THREADS) k_direct(int n, int ns, const typ
 
 template <typename T, int OP>
 int launch_p2p(fmmbem_handle* h) {
-    const typename V4<T>::type* src = std::is_same<T, float>::value
-                                          ? reinterpret_cast<const typename V4<T>::type*>(h->src_f)
+    const bool rel = std::is_same<T, float>::value;
+    const typename V4<T>::type* src = rel ? reinterpret_cast<const typename V4<T>::type*>(h->src_rel)
                                           : reinterpret_cast<const typename V4<T>::type*>(h->src_d);
-    k_p2p<T, OP><<<h->n_leaves, P2P_THREADS, 0, h->stream>>>(h->leaves, h->cell_range, h->p2p_ptr, h->p2p_src, src,
-                                                             h->tgt_d, h->xin, h->nrm_d, h->K, h->corr_ptr, h->corr_col,
-                                                             h->corr_sl, h->ynear);
+    const typename V4<T>::type* tgt = rel ? reinterpret_cast<const typename V4<T>::type*>(h->tgt_rel)
+                                          : reinterpret_cast<const typename V4<T>::type*>(h->tgt_d);
+    k_p2p<T, OP><<<h->n_leaves, P2P_THREADS, 0, h->stream>>>(h->leaves, h->cell_cs, h->cell_range, h->p2p_ptr,
+                                                             h->p2p_src, src, tgt, rel, h->xin, h->nrm_d, h->K,
+                                                             h->corr_ptr, h->corr_col, h->corr_sl, h->ynear);
     FMM_LAUNCHED();
     return 0;
 }

@@ -346,6 +346,24 @@ __global__ void k_list_stats(const int* m2l_ptr, const int* m2l_src, const int* 
     if (inter) atomicAdd(p2p_inter, inter);
 }
 
+// Leaf-relative FP32 copies of the targets and Gauss points (the P2P operands in
+// mixed precision): offsets from the leaf centre keep FP32 rounding relative to the
+// leaf size instead of the domain size.
+__global__ void k_relative(const int* leaves, const double4* cs, const int2* range, const double4* tgt,
+                           const double4* src, int K, float4* tgt_rel, float4* src_rel) {
+    const int cell = leaves[blockIdx.x];
+    const double4 c = cs[cell];
+    const int2 r = range[cell];
+    for (int i = r.x + threadIdx.x; i < r.y; i += blockDim.x) {
+        const double4 t = tgt[i];
+        tgt_rel[i] = make_float4((float)(t.x - c.x), (float)(t.y - c.y), (float)(t.z - c.z), (float)t.w);
+    }
+    for (int g = r.x * K + threadIdx.x; g < r.y * K; g += blockDim.x) {
+        const double4 y = src[g];
+        src_rel[g] = make_float4((float)(y.x - c.x), (float)(y.y - c.y), (float)(y.z - c.z), (float)y.w);
+    }
+}
+
 __global__ void k_leaves(const int2* child, const int2* range, int ncells, int* leaves, int* nleaf, int* maxp) {
     int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= ncells) return;
@@ -718,6 +736,13 @@ int build_geometry_tree_lists(fmmbem_handle* h, const fmmbem_mesh* mesh) {
         cudaFree(tmp);
         cudaFree(h->leaves);
         h->leaves = ls;
+        FMM_TRY(dalloc(&h->tgt_rel, n));
+        FMM_TRY(dalloc(&h->src_rel, h->NS));
+        if (h->n_leaves > 0) {
+            k_relative<<<h->n_leaves, 256, 0, st>>>(h->leaves, h->cell_cs, h->cell_range, h->tgt_d, h->src_d, K,
+                                                    h->tgt_rel, h->src_rel);
+            FMM_LAUNCHED();
+        }
     }
 
     // ---- dual-tree traversal
