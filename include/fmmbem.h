@@ -117,6 +117,14 @@ int64_t fmmbem_n_unknowns(const fmmbem_handle* h);
 /* Switch the arithmetic of later mat-vecs and solves (FMMBEM_FP64 or FMMBEM_MIXED). */
 int fmmbem_set_precision(fmmbem_handle* h, int precision);
 
+/* M2L formulations: batched products against precomputed translation operators
+ * (default when they fit in memory), or a per-target gather that builds the
+ * irregular harmonics of each pair on the fly. Both compute the same sums. */
+#define FMMBEM_M2L_TABLES 0
+#define FMMBEM_M2L_GATHER 1
+/* Select the M2L formulation; FMMBEM_ESTATE if the operator tables were not built. */
+int fmmbem_set_m2l_mode(fmmbem_handle* h, int mode);
+
 /*
  * y = A x through the FMM at expansion order p (eq. matvec-onerow with the
  * far field by P2M, M2M, M2L, L2L, L2P and the near field by P2P plus the

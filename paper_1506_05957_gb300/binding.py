@@ -25,6 +25,8 @@ FMMBEM_STOKES = 1
 FMMBEM_FP64 = 0
 FMMBEM_MIXED = 1
 FMMBEM_P_MAX = 16
+FMMBEM_M2L_TABLES = 0
+FMMBEM_M2L_GATHER = 1
 PASS_NAMES = ["p2m", "m2m", "m2l", "l2l", "l2p", "p2p", "krylov", "matvec"]
 
 
@@ -73,6 +75,7 @@ def lib():
         L.fmmbem_n_unknowns.restype = ctypes.c_int64
         L.fmmbem_set_precision.argtypes = [_vp, ctypes.c_int]
         L.fmmbem_matvec.argtypes = [_vp, ctypes.c_int, _vp, _vp]
+        L.fmmbem_set_m2l_mode.argtypes = [_vp, ctypes.c_int]
         L.fmmbem_matvec_direct.argtypes = [_vp, _vp, _vp]
         L.fmmbem_rhs.argtypes = [_vp, _vp, _vp]
         L.fmmbem_stokes_dl_apply.argtypes = [_vp, _vp, _vp]
@@ -169,6 +172,9 @@ class FmmBem:
 
     def set_precision(self, precision):
         _check(lib().fmmbem_set_precision(self.h, int(precision)))
+
+    def set_m2l_mode(self, mode):
+        _check(lib().fmmbem_set_m2l_mode(self.h, int(mode)))
 
     def matvec(self, p, x, y):
         _check(lib().fmmbem_matvec(self.h, int(p), _dev(x, self.n), _dev(y, self.n)))

@@ -174,10 +174,10 @@ int fmmbem_relaxed_p(double eta, double rho_prev, int p_initial, int p_min) {
 
 void fmmbem_destroy(fmmbem_handle* h) {
     if (!h) return;
-    void* bufs[] = {h->perm, h->tgt_d, h->tgt_f, h->nrm_d, h->verts, h->src_d, h->src_f, h->src_rel, h->tgt_rel, h->cell_cs, h->cell_range,
+    void* bufs[] = {h->perm, h->tgt_d, h->tgt_f, h->nrm_d, h->verts, h->src_d, h->src_f, h->src_rel, h->tgt_rel, h->src_w, h->cell_cs, h->cell_range,
                     h->cell_child, h->cell_level, h->cell_parent, h->leaves, h->m2l_ptr, h->m2l_src, h->p2p_ptr,
                     h->p2p_src, h->corr_ptr, h->corr_col, h->corr_sl, h->corr_dl, h->oct_d, h->oct_f, h->M, h->L,
-                    h->xs, h->ys, h->ynear, h->V, h->kw, h->kb, h->kx, h->kr, h->kpart, h->kh, h->kyv};
+                    h->xs, h->ys, h->ynear, h->m2l_pt, h->m2l_ps, h->m2l_tiles, h->tab_d, h->tab_f, h->V, h->kw, h->kb, h->kx, h->kr, h->kpart, h->kh, h->kyv};
     for (void* b : bufs)
         if (b) cudaFree(b);
     if (h->kh_host) cudaFreeHost(h->kh_host);
@@ -223,11 +223,14 @@ int fmmbem_create(const fmmbem_mesh* mesh, int kernel, int gauss_k, int ncrit, d
     if (rc < 0) return fail(rc);
     rc = init_octant_tables(h);
     if (rc < 0) return fail(rc);
-    const size_t ex = (size_t)h->n_cells * h->ncomp * NCOEF_MAX * 2;
+    rc = build_m2l_tables(h);
+    if (rc < 0) return fail(rc);
+    const size_t ex = (size_t)h->n_cells * h->ncomp * ESTRIDE;
     const int64_t n = h->N * h->dof;
     h->kr_m = o.restart;
     if ((rc = dalloc((double**)&h->M, ex)) < 0) return fail(rc);
     if ((rc = dalloc((double**)&h->L, ex)) < 0) return fail(rc);
+    if ((rc = dalloc(&h->src_w, h->NS)) < 0) return fail(rc);
     if ((rc = dalloc(&h->xs, n)) < 0 || (rc = dalloc(&h->ys, n)) < 0 || (rc = dalloc(&h->ynear, n)) < 0) return fail(rc);
     if ((rc = dalloc(&h->V, (size_t)(o.restart + 1) * n)) < 0) return fail(rc);
     if ((rc = dalloc(&h->kw, n)) < 0 || (rc = dalloc(&h->kb, n)) < 0 || (rc = dalloc(&h->kx, n)) < 0 ||
@@ -254,6 +257,13 @@ int64_t fmmbem_n_unknowns(const fmmbem_handle* h) { return h ? h->N * h->dof : -
 int fmmbem_set_precision(fmmbem_handle* h, int precision) {
     if (!h || (precision != FMMBEM_FP64 && precision != FMMBEM_MIXED)) { fmmbem_set_error("bad precision"); return FMMBEM_EINVAL; }
     h->precision = precision;
+    return 0;
+}
+
+int fmmbem_set_m2l_mode(fmmbem_handle* h, int mode) {
+    if (!h || (mode != FMMBEM_M2L_TABLES && mode != FMMBEM_M2L_GATHER)) { fmmbem_set_error("bad M2L mode"); return FMMBEM_EINVAL; }
+    if (mode == FMMBEM_M2L_TABLES && !h->tab_f) { fmmbem_set_error("M2L operator tables were not built"); return FMMBEM_ESTATE; }
+    h->m2l_tables = mode == FMMBEM_M2L_TABLES;
     return 0;
 }
 

@@ -16,6 +16,9 @@ constexpr int PMAX = FMMBEM_P_MAX;
 constexpr int NCOEF_MAX = (PMAX + 1) * (PMAX + 2) / 2;
 // Irregular harmonics needed by M2L reach degree 2p.
 constexpr int NI_MAX = (2 * PMAX + 1) * (2 * PMAX + 2) / 2;
+// Stride, in reals, of one expansion in the global M and L arrays: 2 * NCOEF_MAX = 306
+// padded to a multiple of 32 so every expansion starts on a 128-byte boundary.
+constexpr int ESTRIDE = 320;
 constexpr int MAX_LEVELS = 21;  // 63-bit Morton keys, 21 bits per axis
 
 FMM_HD int cidx(int n, int m) { return (n * (n + 1)) / 2 + m; }

@@ -118,13 +118,13 @@ __global__ void __launch_bounds__(32 * P2M_WARPS) k_p2m(int p, const int* leaves
         }
     }
     __syncthreads();
-    T* out = M + (size_t)cell * NC * NCOEF_MAX * 2;
+    T* out = M + (size_t)cell * NC * ESTRIDE;
     for (int idx = threadIdx.x; idx < NC * nco * 2; idx += blockDim.x) {
         const int c = idx / (nco * 2), rest = idx % (nco * 2);
         T v = 0;
 #pragma unroll
         for (int w = 0; w < P2M_WARPS; ++w) v += acc[w * NC * nco * 2 + idx];
-        out[c * NCOEF_MAX * 2 + rest] = v;
+        out[c * ESTRIDE + rest] = v;
     }
 }
 
@@ -147,21 +147,21 @@ __global__ void k_m2m(int p, int lb, const double4* cs, const int2* child, const
     for (int x = 0; x < ch.y; ++x) {
         const int cid = ch.x + x;
         const T* Rt = oct + octant_of(cs[cid], pc) * NCOEF_MAX * 2;
-        const T* Mc = M + (size_t)cid * NC * NCOEF_MAX * 2;
+        const T* Mc = M + (size_t)cid * NC * ESTRIDE;
         T sc = T(1);
         for (int j = 0; j <= n; ++j) {
             const int klo = max(-j, m - (n - j)), khi = min(j, m + (n - j));
             for (int k = klo; k <= khi; ++k) {
                 const cpx<T> R = conj(ld_any(Rt, n - j, m - k));
 #pragma unroll
-                for (int c = 0; c < NC; ++c) cfma(acc[c], sc * ld_any(Mc + c * NCOEF_MAX * 2, j, k), R);
+                for (int c = 0; c < NC; ++c) cfma(acc[c], sc * ld_any(Mc + c * ESTRIDE, j, k), R);
             }
             sc *= T(0.5);
         }
     }
-    T* out = M + (size_t)cell * NC * NCOEF_MAX * 2;
+    T* out = M + (size_t)cell * NC * ESTRIDE;
 #pragma unroll
-    for (int c = 0; c < NC; ++c) st(out + c * NCOEF_MAX * 2, t, acc[c]);
+    for (int c = 0; c < NC; ++c) st(out + c * ESTRIDE, t, acc[c]);
 }
 
 // M2L, gathered per target cell over its interaction list:
@@ -191,12 +191,12 @@ __global__ void k_m2l(int p, const int* ptr, const int* srcl, const double4* cs,
         const int dl = ilogb(cv.w * is);  // log2(rho), exact for cells of the same tree
         __syncthreads();
         if (t <= 2 * p) irregular_column<T>(vx, vy, vz, t, 2 * p, reinterpret_cast<cpx<T>*>(sI));
-        const T* Ms = M + (size_t)sc * NC * NCOEF_MAX * 2;
+        const T* Ms = M + (size_t)sc * NC * ESTRIDE;
         for (int idx = t; idx < NC * nco; idx += blockDim.x) {
             const int c = idx / nco, q = idx % nco;
             const T f = (dl == 0) ? T(1) : T(ldexp(1.0, dl * (int)c_deg[q]));
-            sM[(c * NCOEF_MAX + q) * 2] = f * Ms[c * NCOEF_MAX * 2 + 2 * q];
-            sM[(c * NCOEF_MAX + q) * 2 + 1] = f * Ms[c * NCOEF_MAX * 2 + 2 * q + 1];
+            sM[(c * NCOEF_MAX + q) * 2] = f * Ms[c * ESTRIDE + 2 * q];
+            sM[(c * NCOEF_MAX + q) * 2 + 1] = f * Ms[c * ESTRIDE + 2 * q + 1];
         }
         __syncthreads();
         if (t < nco) {
@@ -231,12 +231,12 @@ __global__ void k_m2l(int p, const int* ptr, const int* srcl, const double4* cs,
         }
     }
     if (t < nco) {
-        T* out = L + (size_t)tc * NC * NCOEF_MAX * 2;
+        T* out = L + (size_t)tc * NC * ESTRIDE;
 #pragma unroll
         for (int c = 0; c < NC; ++c) {
             cpx<T> v = conj(acc[c]);
             if (j & 1) v = mk(-v.re, -v.im);
-            st(out + c * NCOEF_MAX * 2, t, v);
+            st(out + c * ESTRIDE, t, v);
         }
     }
 }
@@ -252,7 +252,7 @@ __global__ void k_l2l(int p, int lb, const double4* cs, const int* parent, const
     int j, k;
     decode(t, j, k);
     const T* Rt = oct + octant_of(cs[cell], cs[par]) * NCOEF_MAX * 2;
-    const T* Lp = L + (size_t)par * NC * NCOEF_MAX * 2;
+    const T* Lp = L + (size_t)par * NC * ESTRIDE;
     cpx<T> acc[NC];
 #pragma unroll
     for (int c = 0; c < NC; ++c) acc[c] = mk(T(0), T(0));
@@ -261,15 +261,15 @@ __global__ void k_l2l(int p, int lb, const double4* cs, const int* parent, const
         for (int m = mlo; m <= mhi; ++m) {
             const cpx<T> R = ld_any(Rt, n - j, m - k);
 #pragma unroll
-            for (int c = 0; c < NC; ++c) cfma(acc[c], ld_any(Lp + c * NCOEF_MAX * 2, n, m), R);
+            for (int c = 0; c < NC; ++c) cfma(acc[c], ld_any(Lp + c * ESTRIDE, n, m), R);
         }
     }
     const T f = T(ldexp(1.0, -(j + 1)));
-    T* out = L + (size_t)cell * NC * NCOEF_MAX * 2;
+    T* out = L + (size_t)cell * NC * ESTRIDE;
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
-        cpx<T> v = ld(out + c * NCOEF_MAX * 2, t);
-        st(out + c * NCOEF_MAX * 2, t, v + f * acc[c]);
+        cpx<T> v = ld(out + c * ESTRIDE, t);
+        st(out + c * ESTRIDE, t, v + f * acc[c]);
     }
 }
 
@@ -286,11 +286,11 @@ __global__ void k_l2p(int p, const int* leaves, const double4* cs, const int2* r
     const double4 cc = cs[cell];
     const int2 r = range[cell];
     const int nco = ncoef(p);
-    const T* Lc = L + (size_t)cell * NC * NCOEF_MAX * 2;
+    const T* Lc = L + (size_t)cell * NC * ESTRIDE;
     for (int idx = threadIdx.x; idx < NC * nco; idx += blockDim.x) {
         const int c = idx / nco, q = idx % nco;
-        sL[(c * NCOEF_MAX + q) * 2] = Lc[c * NCOEF_MAX * 2 + 2 * q];
-        sL[(c * NCOEF_MAX + q) * 2 + 1] = Lc[c * NCOEF_MAX * 2 + 2 * q + 1];
+        sL[(c * NCOEF_MAX + q) * 2] = Lc[c * ESTRIDE + 2 * q];
+        sL[(c * NCOEF_MAX + q) * 2 + 1] = Lc[c * ESTRIDE + 2 * q + 1];
     }
     __syncthreads();
     const double inv_s = 1.0 / cc.w;
@@ -451,8 +451,12 @@ int far_field_t(fmmbem_handle* h, int p) {
     prof_end(h, FMMBEM_PASS_M2M, nl);
     // M2L
     prof_begin(h, FMMBEM_PASS_M2L);
-    k_m2l<T, NC><<<h->n_cells, m2l_block(p), 0, st>>>(p, h->m2l_ptr, h->m2l_src, h->cell_cs, M, L);
-    FMM_LAUNCHED();
+    if (h->m2l_tables) {
+        FMM_TRY(m2l_gemm(h, p, !std::is_same<T, float>::value));
+    } else {
+        k_m2l<T, NC><<<h->n_cells, m2l_block(p), 0, st>>>(p, h->m2l_ptr, h->m2l_src, h->cell_cs, M, L);
+        FMM_LAUNCHED();
+    }
     prof_end(h, FMMBEM_PASS_M2L, 1);
     // L2L, top-down
     prof_begin(h, FMMBEM_PASS_L2L);

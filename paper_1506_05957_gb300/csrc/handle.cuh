@@ -28,6 +28,7 @@ struct fmmbem_handle {
     float4* src_f = nullptr;
     float4* src_rel = nullptr;    // [NS] Gauss point relative to its leaf centre, FP32 (x,y,z, q_k S_j)
     float4* tgt_rel = nullptr;    // [N] centroid relative to its leaf centre, FP32
+    float4* src_w = nullptr;      // [NS] per mat-vec: leaf-relative position and weight q_k S_j x_j
     double origin[3] = {0, 0, 0};  // root-box centre; Stokes y.f strengths use it
     double half = 1.0;             // root-box half side
     double spill = 0.0;            // largest centroid-to-vertex distance
@@ -46,6 +47,15 @@ struct fmmbem_handle {
     int* m2l_ptr = nullptr;  // [n_cells + 1]
     int* m2l_src = nullptr;
     int64_t n_m2l = 0, n_m2l_same = 0;
+    // M2L as batched products against precomputed operators (one per distinct pair geometry)
+    bool m2l_tables = false;
+    int* m2l_pt = nullptr;        // [n_m2l] target cell of each pair, grouped by operator
+    int* m2l_ps = nullptr;        // [n_m2l] source cell
+    int4* m2l_tiles = nullptr;    // (operator, first pair, pair count, -)
+    int n_tables = 0, n_tiles = 0, tab_ld = 0;
+    size_t tab_stride = 0;
+    double* tab_d = nullptr;      // [n_tables][2 ncoef(p_max)][tab_ld]
+    float* tab_f = nullptr;
     int* p2p_ptr = nullptr;  // [n_cells + 1]
     int* p2p_src = nullptr;
     int64_t n_p2p = 0, n_p2p_inter = 0;
@@ -95,6 +105,9 @@ struct fmmbem_handle {
 namespace fmmbem {
 // setup.cu
 int build_geometry_tree_lists(fmmbem_handle* h, const fmmbem_mesh* mesh);
+// m2l.cu
+int build_m2l_tables(fmmbem_handle* h);
+int m2l_gemm(fmmbem_handle* h, int p, bool fp64);
 // fmm.cu
 int far_field(fmmbem_handle* h, int p, bool fp64);
 int far_eval_add(fmmbem_handle* h, int p, bool fp64, double* y_sorted, double scale);

@@ -199,6 +199,133 @@ __global__ void __launch_bounds__(P2P_THREADS) k_p2p(const int* leaves, const do
     }
 }
 
+// Laplace single layer in FP32, the near-field pass of every mixed-precision mat-vec.
+// Per mat-vec each Gauss point is packed once as (leaf-relative position, w = q_k S_j x_j)
+// (k_pack_sources). A block takes one target leaf; each lane holds TPL targets in
+// registers (lane l: targets l, l+32, ...), the four warps split every staged source
+// tile into contiguous quarters, so one 128-bit broadcast shared load feeds TPL
+// interactions. FP32 partial sums over 32 sources are added to FP64 accumulators.
+constexpr int LAP_TILE = 1024;
+
+__global__ void k_pack_sources(const float4* src_rel, const double* xs, int K, int64_t ns, float4* out) {
+    const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (g >= ns) return;
+    const float4 y = src_rel[g];
+    out[g] = make_float4(y.x, y.y, y.z, (float)((double)y.w * xs[g / K]));
+}
+
+template <int TPL>
+__device__ __forceinline__ void lap_tile(const float4* s, int q0, int q1, const float* tx, const float* ty,
+                                         const float* tz, double* acc) {
+    for (int qb = q0; qb < q1; qb += 32) {
+        const int qe = min(q1, qb + 32);
+        float part[TPL];
+#pragma unroll
+        for (int t = 0; t < TPL; ++t) part[t] = 0.f;
+#pragma unroll 4
+        for (int q = qb; q < qe; ++q) {
+            const float4 v = s[q];
+#pragma unroll
+            for (int t = 0; t < TPL; ++t) {
+                const float dx = tx[t] - v.x, dy = ty[t] - v.y, dz = tz[t] - v.z;
+                part[t] = fmaf(v.w, rsqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz))), part[t]);
+            }
+        }
+#pragma unroll
+        for (int t = 0; t < TPL; ++t) acc[t] += (double)part[t];
+    }
+}
+
+template <int TPL>
+__device__ __forceinline__ void lap_tile_self(const float4* s, int q0, int q1, int gb, const int* own, int K,
+                                              const float* tx, const float* ty, const float* tz, double* acc) {
+    float part[TPL];
+#pragma unroll
+    for (int t = 0; t < TPL; ++t) part[t] = 0.f;
+    for (int q = q0; q < q1; ++q) {
+        const float4 v = s[q];
+#pragma unroll
+        for (int t = 0; t < TPL; ++t) {
+            if ((unsigned)(gb + q - own[t]) < (unsigned)K) continue;
+            const float dx = tx[t] - v.x, dy = ty[t] - v.y, dz = tz[t] - v.z;
+            part[t] = fmaf(v.w, rsqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz))), part[t]);
+        }
+    }
+#pragma unroll
+    for (int t = 0; t < TPL; ++t) acc[t] += (double)part[t];
+}
+
+template <int TPL>
+__device__ void lap_p2p_chunk(int cell, int tb, int nt, const double4* cs, const int2* range, const int* pptr,
+                              const int* psrc, const float4* srcw, const float4* tgt, int K, const int* cptr,
+                              const int* ccol, const double* cval, const double* xs, double* ynear, float4* sS,
+                              double* sred) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    float tx[TPL], ty[TPL], tz[TPL];
+    int own[TPL];
+    double acc[TPL];
+#pragma unroll
+    for (int t = 0; t < TPL; ++t) {
+        const int li = lane + 32 * t;
+        const float4 x = li < nt ? tgt[tb + li] : make_float4(1e30f, 0.f, 0.f, 0.f);
+        tx[t] = x.x; ty[t] = x.y; tz[t] = x.z;
+        own[t] = (tb + li) * K;
+        acc[t] = 0.0;
+    }
+    const double4 ccell = cs[cell];
+    for (int e = pptr[cell]; e < pptr[cell + 1]; ++e) {
+        const int sc = psrc[e];
+        const int2 sr = range[sc];
+        const double4 cc = cs[sc];
+        const float shx = (float)(cc.x - ccell.x), shy = (float)(cc.y - ccell.y), shz = (float)(cc.z - ccell.z);
+        const int g0 = sr.x * K, g1 = sr.y * K;
+        for (int gb = g0; gb < g1; gb += LAP_TILE) {
+            const int n = min(LAP_TILE, g1 - gb);
+            __syncthreads();
+            for (int q = threadIdx.x; q < n; q += blockDim.x) {
+                float4 v = srcw[gb + q];
+                v.x += shx; v.y += shy; v.z += shz;
+                sS[q] = v;
+            }
+            __syncthreads();
+            const int per = (n + 3) >> 2;
+            const int q0 = min(n, warp * per), q1 = min(n, q0 + per);
+            if (sc == cell) lap_tile_self<TPL>(sS, q0, q1, gb, own, K, tx, ty, tz, acc);
+            else lap_tile<TPL>(sS, q0, q1, tx, ty, tz, acc);
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int t = 0; t < TPL; ++t) sred[warp * 128 + lane + 32 * t] = acc[t];
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+        for (int t = 0; t < TPL; ++t) {
+            const int li = lane + 32 * t;
+            if (li >= nt) continue;
+            double out = sred[li] + sred[128 + li] + sred[256 + li] + sred[384 + li];
+            add_correction<1>(tb + li, cptr, ccol, cval, xs, &out);
+            ynear[tb + li] = out;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(128) k_p2p_lap(const int* leaves, const double4* cs, const int2* range,
+                                                 const int* pptr, const int* psrc, const float4* srcw,
+                                                 const float4* tgt, int K, const int* cptr, const int* ccol,
+                                                 const double* cval, const double* xs, double* ynear) {
+    __shared__ float4 sS[LAP_TILE];
+    __shared__ double sred[4 * 128];
+    const int cell = leaves[blockIdx.x];
+    const int2 r = range[cell];
+    for (int tb = r.x; tb < r.y; tb += 128) {
+        const int nt = min(128, r.y - tb);
+        if (nt <= 32) lap_p2p_chunk<1>(cell, tb, nt, cs, range, pptr, psrc, srcw, tgt, K, cptr, ccol, cval, xs, ynear, sS, sred);
+        else if (nt <= 64) lap_p2p_chunk<2>(cell, tb, nt, cs, range, pptr, psrc, srcw, tgt, K, cptr, ccol, cval, xs, ynear, sS, sred);
+        else lap_p2p_chunk<4>(cell, tb, nt, cs, range, pptr, psrc, srcw, tgt, K, cptr, ccol, cval, xs, ynear, sS, sred);
+    }
+}
+
 // Direct: one thread per target, every Gauss point staged through shared memory.
 template <typename T, int OP>
 __global__ void __launch_bounds__(P2P_THREADS) k_direct(int n, int ns, const typename V4<T>::type* src,
@@ -270,8 +397,16 @@ int launch_direct(fmmbem_handle* h, const double* xs, double* y, const double* c
 
 int near_field(fmmbem_handle* h, bool fp64) {
     prof_begin(h, FMMBEM_PASS_P2P);
-    int rc;
-    if (h->kernel == FMMBEM_LAPLACE) rc = fp64 ? launch_p2p<double, LAP_SL>(h) : launch_p2p<float, LAP_SL>(h);
+    int rc = 0;
+    if (h->kernel == FMMBEM_LAPLACE && !fp64) {
+        k_pack_sources<<<(unsigned)((h->NS + 255) / 256), 256, 0, h->stream>>>(h->src_rel, h->xin, h->K, h->NS, h->src_w);
+        FMM_LAUNCHED();
+        k_p2p_lap<<<h->n_leaves, 128, 0, h->stream>>>(h->leaves, h->cell_cs, h->cell_range, h->p2p_ptr, h->p2p_src,
+                                                     h->src_w, h->tgt_rel, h->K, h->corr_ptr, h->corr_col, h->corr_sl,
+                                                     h->xin, h->ynear);
+        FMM_LAUNCHED();
+        h->launches += 1;
+    } else if (h->kernel == FMMBEM_LAPLACE) rc = launch_p2p<double, LAP_SL>(h);
     else rc = fp64 ? launch_p2p<double, STK_SL>(h) : launch_p2p<float, STK_SL>(h);
     prof_end(h, FMMBEM_PASS_P2P, 1);
     h->launches += 1;
