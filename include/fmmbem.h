@@ -215,6 +215,26 @@ int fmmbem_expansion_eval(int kind, int p, const double* center, double scale, i
                           const double* src_dev, int n_tgt, const double* tgt_dev, double* out_dev,
                           void* stream);
 
+/*
+ * fmmbem_expansion_eval without any allocation (the paper has no counterpart: this
+ * is an interface for callers that cannot allocate device memory, e.g. code inside
+ * a CUDA-graph capture or under a memory arena). Same arguments and results as
+ * fmmbem_expansion_eval; the expansion coefficients are kept in a fixed module-global
+ * device array of one expansion of order <= FMMBEM_P_MAX (2448 bytes, held by every
+ * GPU that loads the library until the process exits) instead of a per-call buffer.
+ *   - p > FMMBEM_P_MAX is rejected with FMMBEM_EINVAL.
+ *   - No cudaMalloc, cudaFree or allocating routine is called.
+ *   - The first call on each device does a one-time set-up there (looks up the
+ *     array's device address and fills a small constant table with a synchronous
+ *     copy); make that first call before any stream capture.
+ *   - Work is queued on `stream` and the call returns without synchronizing.
+ *   - All calls share the one array: calls whose work overlaps on the GPU (other
+ *     streams, other host threads) race on it; serialize them.
+ */
+int fmmbem_expansion_eval_static(int kind, int p, const double* center, double scale, int n_src,
+                                 const double* src_dev, int n_tgt, const double* tgt_dev, double* out_dev,
+                                 void* stream);
+
 /* Sizes of the tree and lists built by fmmbem_create (algorithmic work counts). */
 typedef struct {
     int64_t n_panels, n_sources, n_cells, n_leaves, n_levels;

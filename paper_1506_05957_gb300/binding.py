@@ -86,6 +86,8 @@ def lib():
                                         ctypes.POINTER(ctypes.c_int), _vp, _vp, _dp]
         L.fmmbem_expansion_eval.argtypes = [ctypes.c_int, ctypes.c_int, _dp, ctypes.c_double, ctypes.c_int, _vp,
                                             ctypes.c_int, _vp, _vp, _vp]
+        L.fmmbem_expansion_eval_static.argtypes = [ctypes.c_int, ctypes.c_int, _dp, ctypes.c_double, ctypes.c_int,
+                                                   _vp, ctypes.c_int, _vp, _vp, _vp]
         L.fmmbem_get_stats.argtypes = [_vp, ctypes.POINTER(fmmbem_stats)]
         L.fmmbem_profile_enable.argtypes = [_vp, ctypes.c_int]
         L.fmmbem_profile_get.argtypes = [_vp, ctypes.POINTER(fmmbem_profile)]
@@ -137,6 +139,13 @@ def fmmbem_expansion_eval(kind, p, center, scale, src, tgt, out, stream=None):
     c = (ctypes.c_double * 3)(*[float(v) for v in center])
     _check(lib().fmmbem_expansion_eval(int(kind), int(p), c, float(scale), int(src.shape[0]), _dev(src),
                                        int(tgt.shape[0]), _dev(tgt), _dev(out), _vp(stream)))
+
+
+def fmmbem_expansion_eval_static(kind, p, center, scale, src, tgt, out, stream=None):
+    """Allocation-free fmmbem_expansion_eval (fixed module-global scratch; asynchronous)."""
+    c = (ctypes.c_double * 3)(*[float(v) for v in center])
+    _check(lib().fmmbem_expansion_eval_static(int(kind), int(p), c, float(scale), int(src.shape[0]), _dev(src),
+                                              int(tgt.shape[0]), _dev(tgt), _dev(out), _vp(stream)))
 
 
 class FmmBem:

@@ -9,6 +9,7 @@
 // matvec-onerow). Stokes uses four (Sec. 3.2: "four Laplace expansions"):
 // strengths f_1, f_2, f_3 and y.f with f = q_k S_J t_J, and the Stokeslet sum
 // u_a = phi_a - x_b d_a phi_b + d_a phi_4 at each target.
+#include <mutex>
 #include <type_traits>
 #include "handle.cuh"
 #include "harmonics.cuh"
@@ -524,3 +525,88 @@ int expansion_eval(int kind, int p, const double* center, double scale, int n_sr
 }
 
 }  // namespace fmmbem
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of fmmbem_expansion_eval.
+//
+// Some callers cannot call cudaMalloc: code running inside a CUDA-graph capture
+// (allocation is not capturable), code whose memory is owned by a pool or an
+// arena that forbids side allocations, and real-time loops that must not block
+// on the driver's allocator. For them the expansion coefficients live in a fixed
+// module-global buffer instead of a per-call allocation.
+namespace {
+
+// One expansion of order <= FMMBEM_P_MAX: (P_MAX+1)(P_MAX+2)/2 complex FP64
+// coefficients = 2448 bytes. Every GPU that loads the library holds it until exit.
+static __device__ __align__(256) double g_expansion_scratch[fmmbem::NCOEF_MAX * 2];
+
+struct ScratchSlot {
+    std::once_flag once;
+    double* ptr = nullptr;
+    cudaError_t err = cudaSuccess;
+};
+constexpr int kMaxDevices = 64;
+ScratchSlot g_scratch_slots[kMaxDevices];
+
+// Per-device set-up, done once with that device current: the device address of the
+// scratch array (host code only sees a host-side stand-in for the symbol) and the
+// degree table the kernels read from constant memory.
+int scratch_address(double** out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) {
+        fmmbem_set_error("cudaGetDevice: %s", cudaGetErrorString(e));
+        return FMMBEM_EDEVICE;
+    }
+    if (dev < 0 || dev >= kMaxDevices) {
+        fmmbem_set_error("device ordinal %d beyond the %d supported", dev, kMaxDevices);
+        return FMMBEM_EDEVICE;
+    }
+    ScratchSlot& s = g_scratch_slots[dev];
+    std::call_once(s.once, [&s]() {
+        s.err = cudaGetSymbolAddress((void**)&s.ptr, g_expansion_scratch);
+        if (s.err != cudaSuccess) return;
+        unsigned char deg[fmmbem::NCOEF_MAX];
+        for (int n = 0; n <= fmmbem::PMAX; ++n)
+            for (int m = 0; m <= n; ++m) deg[fmmbem::cidx(n, m)] = (unsigned char)n;
+        s.err = cudaMemcpyToSymbol(fmmbem::c_deg, deg, sizeof(deg));
+    });
+    if (s.err != cudaSuccess || !s.ptr) {
+        fmmbem_set_error("static scratch set-up on device %d: %s", dev, cudaGetErrorString(s.err));
+        return FMMBEM_EDEVICE;
+    }
+    *out = s.ptr;
+    return 0;
+}
+
+}  // namespace
+
+extern "C" int fmmbem_expansion_eval_static(int kind, int p, const double* center, double scale, int n_src,
+                                            const double* src_dev, int n_tgt, const double* tgt_dev, double* out_dev,
+                                            void* stream) {
+    using namespace fmmbem;
+    if (p > FMMBEM_P_MAX) {
+        fmmbem_set_error("p=%d exceeds the static scratch, which holds one expansion of order <= %d", p,
+                         FMMBEM_P_MAX);
+        return FMMBEM_EINVAL;
+    }
+    if ((kind != 0 && kind != 1) || p < 0 || !center || !(scale > 0.0) || n_src < 0 || n_tgt < 0 ||
+        (n_src && !src_dev) || (n_tgt && (!tgt_dev || !out_dev))) {
+        fmmbem_set_error("bad argument");
+        return FMMBEM_EINVAL;
+    }
+    double* E = nullptr;
+    FMM_TRY(scratch_address(&E));
+    cudaStream_t st = (cudaStream_t)stream;
+    // k_form_expansion overwrites every coefficient of order <= p, so nothing left by
+    // an earlier call is read.
+    k_form_expansion<<<1, coef_block(p), 0, st>>>(kind, p, center[0], center[1], center[2], scale, n_src,
+                                                  reinterpret_cast<const double4*>(src_dev), E);
+    FMM_LAUNCHED();
+    if (n_tgt > 0) {
+        k_eval_expansion<<<(n_tgt + 127) / 128, 128, 0, st>>>(kind, p, center[0], center[1], center[2], scale, E,
+                                                             n_tgt, tgt_dev, out_dev);
+        FMM_LAUNCHED();
+    }
+    return 0;
+}
