@@ -243,6 +243,8 @@ typedef struct {
     int64_t n_p2p_pairs;          /* leaf-leaf near-field pairs */
     int64_t n_p2p_interactions;   /* sum over P2P pairs of targets x Gauss points */
     int64_t n_corrections;        /* entries of the near-singular/self correction table */
+    int64_t n_m2l_tables;         /* distinct M2L operators (0: gather form only) */
+    int64_t n_m2l_tiles;          /* GEMM tiles over the M2L pairs */
     double setup_seconds;         /* wall time of fmmbem_create */
 } fmmbem_stats;
 

@@ -136,8 +136,13 @@ int matvec_sorted(fmmbem_handle* h, int p, const double* xs, double* ys) {
     const bool fp64 = h->precision == FMMBEM_FP64;
     h->xin = xs;
     prof_begin(h, FMMBEM_PASS_MATVEC);
-    FMM_TRY(near_field(h, fp64));
+    // near field on the second stream, far field on the handle's stream, joined before L2P
+    FMM_CU(cudaEventRecord(h->ev_fork, h->stream));
+    FMM_CU(cudaStreamWaitEvent(h->stream2, h->ev_fork, 0));
+    FMM_TRY(near_field(h, fp64, h->stream2));
     FMM_TRY(far_field(h, p, fp64));
+    FMM_CU(cudaEventRecord(h->ev_join, h->stream2));
+    FMM_CU(cudaStreamWaitEvent(h->stream, h->ev_join, 0));
     FMM_TRY(far_eval_add(h, p, fp64, ys, operator_scale(h)));
     prof_end(h, FMMBEM_PASS_MATVEC, 0);
     if (h->prof_on) {
@@ -181,6 +186,9 @@ void fmmbem_destroy(fmmbem_handle* h) {
     for (void* b : bufs)
         if (b) cudaFree(b);
     if (h->kh_host) cudaFreeHost(h->kh_host);
+    if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+    if (h->ev_join) cudaEventDestroy(h->ev_join);
+    if (h->stream2) cudaStreamDestroy(h->stream2);
     prof_free(h);
     delete h;
 }
@@ -219,6 +227,12 @@ int fmmbem_create(const fmmbem_mesh* mesh, int kernel, int gauss_k, int ncrit, d
     h->precision = o.precision;
     h->stream = (cudaStream_t)o.stream;
     auto fail = [&](int rc) { fmmbem_destroy(h); return rc; };
+    if (cudaStreamCreateWithFlags(&h->stream2, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+        fmmbem_set_error("stream/event creation failed: %s", cudaGetErrorString(cudaGetLastError()));
+        return fail(FMMBEM_EDEVICE);
+    }
     int rc = build_geometry_tree_lists(h, mesh);
     if (rc < 0) return fail(rc);
     rc = init_octant_tables(h);
@@ -354,6 +368,8 @@ int fmmbem_get_stats(const fmmbem_handle* h, fmmbem_stats* s) {
     s->n_p2p_pairs = h->n_p2p;
     s->n_p2p_interactions = h->n_p2p_inter;
     s->n_corrections = h->n_corr;
+    s->n_m2l_tables = h->n_tables;
+    s->n_m2l_tiles = h->n_tiles;
     s->setup_seconds = h->setup_seconds;
     return 0;
 }

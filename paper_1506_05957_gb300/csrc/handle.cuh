@@ -15,6 +15,8 @@ struct fmmbem_handle {
     fmmbem_opts opts{};
     int precision = FMMBEM_MIXED;
     cudaStream_t stream = nullptr;
+    cudaStream_t stream2 = nullptr;  // near field runs here, concurrently with the far field
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     int64_t N = 0;   // panels
     int64_t NS = 0;  // Gauss points = K * N
 
@@ -115,7 +117,7 @@ int expansion_eval(int kind, int p, const double* center, double scale, int n_sr
                    int n_tgt, const double* tgt, double* out, cudaStream_t st);
 int init_octant_tables(fmmbem_handle* h);
 // near.cu
-int near_field(fmmbem_handle* h, bool fp64);
+int near_field(fmmbem_handle* h, bool fp64, cudaStream_t st);
 int direct_field(fmmbem_handle* h, bool fp64, int which, const double* x_sorted, double* y_sorted);
 // krylov.cu
 int relaxed_p(double eta, double rho_prev, int p_initial, int p_min);

@@ -214,9 +214,24 @@ __global__ void k_pack_sources(const float4* src_rel, const double* xs, int K, i
     out[g] = make_float4(y.x, y.y, y.z, (float)((double)y.w * xs[g / K]));
 }
 
+__device__ __forceinline__ float rsqrt_approx(float x) {
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// Compensated (Kahan) FP32 accumulation: hi + lo carries the sum of the partials to
+// about FP64 accuracy without FP64 arithmetic in the interaction loop.
+__device__ __forceinline__ void kahan_add(float& hi, float& lo, float v) {
+    const float y = v - lo;
+    const float t = hi + y;
+    lo = (t - hi) - y;
+    hi = t;
+}
+
 template <int TPL>
 __device__ __forceinline__ void lap_tile(const float4* s, int q0, int q1, const float* tx, const float* ty,
-                                         const float* tz, double* acc) {
+                                         const float* tz, float* hi, float* lo) {
     for (int qb = q0; qb < q1; qb += 32) {
         const int qe = min(q1, qb + 32);
         float part[TPL];
@@ -228,31 +243,35 @@ __device__ __forceinline__ void lap_tile(const float4* s, int q0, int q1, const 
 #pragma unroll
             for (int t = 0; t < TPL; ++t) {
                 const float dx = tx[t] - v.x, dy = ty[t] - v.y, dz = tz[t] - v.z;
-                part[t] = fmaf(v.w, rsqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz))), part[t]);
+                part[t] = fmaf(v.w, rsqrt_approx(fmaf(dx, dx, fmaf(dy, dy, dz * dz))), part[t]);
             }
         }
 #pragma unroll
-        for (int t = 0; t < TPL; ++t) acc[t] += (double)part[t];
+        for (int t = 0; t < TPL; ++t) kahan_add(hi[t], lo[t], part[t]);
     }
 }
 
 template <int TPL>
 __device__ __forceinline__ void lap_tile_self(const float4* s, int q0, int q1, int gb, const int* own, int K,
-                                              const float* tx, const float* ty, const float* tz, double* acc) {
-    float part[TPL];
+                                              const float* tx, const float* ty, const float* tz, float* hi,
+                                              float* lo) {
+    for (int qb = q0; qb < q1; qb += 32) {
+        const int qe = min(q1, qb + 32);
+        float part[TPL];
 #pragma unroll
-    for (int t = 0; t < TPL; ++t) part[t] = 0.f;
-    for (int q = q0; q < q1; ++q) {
-        const float4 v = s[q];
+        for (int t = 0; t < TPL; ++t) part[t] = 0.f;
+        for (int q = qb; q < qe; ++q) {
+            const float4 v = s[q];
 #pragma unroll
-        for (int t = 0; t < TPL; ++t) {
-            if ((unsigned)(gb + q - own[t]) < (unsigned)K) continue;
-            const float dx = tx[t] - v.x, dy = ty[t] - v.y, dz = tz[t] - v.z;
-            part[t] = fmaf(v.w, rsqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz))), part[t]);
+            for (int t = 0; t < TPL; ++t) {
+                if ((unsigned)(gb + q - own[t]) < (unsigned)K) continue;
+                const float dx = tx[t] - v.x, dy = ty[t] - v.y, dz = tz[t] - v.z;
+                part[t] = fmaf(v.w, rsqrt_approx(fmaf(dx, dx, fmaf(dy, dy, dz * dz))), part[t]);
+            }
         }
-    }
 #pragma unroll
-    for (int t = 0; t < TPL; ++t) acc[t] += (double)part[t];
+        for (int t = 0; t < TPL; ++t) kahan_add(hi[t], lo[t], part[t]);
+    }
 }
 
 template <int TPL>
@@ -263,14 +282,15 @@ __device__ void lap_p2p_chunk(int cell, int tb, int nt, const double4* cs, const
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     float tx[TPL], ty[TPL], tz[TPL];
     int own[TPL];
-    double acc[TPL];
+    float hi[TPL], lo[TPL];
 #pragma unroll
     for (int t = 0; t < TPL; ++t) {
         const int li = lane + 32 * t;
         const float4 x = li < nt ? tgt[tb + li] : make_float4(1e30f, 0.f, 0.f, 0.f);
         tx[t] = x.x; ty[t] = x.y; tz[t] = x.z;
         own[t] = (tb + li) * K;
-        acc[t] = 0.0;
+        hi[t] = 0.f;
+        lo[t] = 0.f;
     }
     const double4 ccell = cs[cell];
     for (int e = pptr[cell]; e < pptr[cell + 1]; ++e) {
@@ -290,13 +310,13 @@ __device__ void lap_p2p_chunk(int cell, int tb, int nt, const double4* cs, const
             __syncthreads();
             const int per = (n + 3) >> 2;
             const int q0 = min(n, warp * per), q1 = min(n, q0 + per);
-            if (sc == cell) lap_tile_self<TPL>(sS, q0, q1, gb, own, K, tx, ty, tz, acc);
-            else lap_tile<TPL>(sS, q0, q1, tx, ty, tz, acc);
+            if (sc == cell) lap_tile_self<TPL>(sS, q0, q1, gb, own, K, tx, ty, tz, hi, lo);
+            else lap_tile<TPL>(sS, q0, q1, tx, ty, tz, hi, lo);
         }
     }
     __syncthreads();
 #pragma unroll
-    for (int t = 0; t < TPL; ++t) sred[warp * 128 + lane + 32 * t] = acc[t];
+    for (int t = 0; t < TPL; ++t) sred[warp * 128 + lane + 32 * t] = (double)hi[t] - (double)lo[t];
     __syncthreads();
     if (warp == 0) {
 #pragma unroll
@@ -395,7 +415,17 @@ int launch_direct(fmmbem_handle* h, const double* xs, double* y, const double* c
 
 }  // namespace
 
-int near_field(fmmbem_handle* h, bool fp64) {
+int near_field_on(fmmbem_handle* h, bool fp64);
+
+int near_field(fmmbem_handle* h, bool fp64, cudaStream_t st) {
+    cudaStream_t keep = h->stream;
+    h->stream = st;
+    const int rc = near_field_on(h, fp64);
+    h->stream = keep;
+    return rc;
+}
+
+int near_field_on(fmmbem_handle* h, bool fp64) {
     prof_begin(h, FMMBEM_PASS_P2P);
     int rc = 0;
     if (h->kernel == FMMBEM_LAPLACE && !fp64) {
