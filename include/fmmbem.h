@@ -117,11 +117,15 @@ int64_t fmmbem_n_unknowns(const fmmbem_handle* h);
 /* Switch the arithmetic of later mat-vecs and solves (FMMBEM_FP64 or FMMBEM_MIXED). */
 int fmmbem_set_precision(fmmbem_handle* h, int precision);
 
-/* M2L formulations: batched products against precomputed translation operators
- * (default when they fit in memory), or a per-target gather that builds the
- * irregular harmonics of each pair on the fly. Both compute the same sums. */
+/* M2L formulations, all computing the same sums:
+ *   TABLES : batched products against precomputed translation operators, SIMT FMA;
+ *   GATHER : per-target gather that builds the irregular harmonics of each pair on the fly;
+ *   TENSOR : the TABLES products on the tcgen05 tensor cores in 3xTF32 (FP32-level
+ *            accuracy) for FMMBEM_MIXED mat-vecs; FMMBEM_FP64 mat-vecs use TABLES.
+ * fmmbem_create selects TENSOR when the operator tables fit in memory. */
 #define FMMBEM_M2L_TABLES 0
 #define FMMBEM_M2L_GATHER 1
+#define FMMBEM_M2L_TENSOR 2
 /* Select the M2L formulation; FMMBEM_ESTATE if the operator tables were not built. */
 int fmmbem_set_m2l_mode(fmmbem_handle* h, int mode);
 

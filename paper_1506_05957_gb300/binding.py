@@ -27,6 +27,7 @@ FMMBEM_MIXED = 1
 FMMBEM_P_MAX = 16
 FMMBEM_M2L_TABLES = 0
 FMMBEM_M2L_GATHER = 1
+FMMBEM_M2L_TENSOR = 2
 PASS_NAMES = ["p2m", "m2m", "m2l", "l2l", "l2p", "p2p", "krylov", "matvec"]
 
 

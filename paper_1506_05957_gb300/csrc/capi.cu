@@ -182,7 +182,7 @@ void fmmbem_destroy(fmmbem_handle* h) {
     void* bufs[] = {h->perm, h->tgt_d, h->tgt_f, h->nrm_d, h->verts, h->src_d, h->src_f, h->src_rel, h->tgt_rel, h->src_w, h->cell_cs, h->cell_range,
                     h->cell_child, h->cell_level, h->cell_parent, h->leaves, h->m2l_ptr, h->m2l_src, h->p2p_ptr,
                     h->p2p_src, h->corr_ptr, h->corr_col, h->corr_sl, h->corr_dl, h->oct_d, h->oct_f, h->M, h->L,
-                    h->xs, h->ys, h->ynear, h->m2l_pt, h->m2l_ps, h->m2l_tiles, h->tab_d, h->tab_f, h->V, h->kw, h->kb, h->kx, h->kr, h->kpart, h->kh, h->kyv};
+                    h->xs, h->ys, h->ynear, h->m2l_pt, h->m2l_ps, h->m2l_tiles, h->tab_d, h->tab_f, h->tab_tc, h->m2l_tiles_tc, h->tc_err, h->V, h->kw, h->kb, h->kx, h->kr, h->kpart, h->kh, h->kyv};
     for (void* b : bufs)
         if (b) cudaFree(b);
     if (h->kh_host) cudaFreeHost(h->kh_host);
@@ -239,6 +239,9 @@ int fmmbem_create(const fmmbem_mesh* mesh, int kernel, int gauss_k, int ncrit, d
     if (rc < 0) return fail(rc);
     rc = build_m2l_tables(h);
     if (rc < 0) return fail(rc);
+    rc = build_m2l_tc(h);
+    if (rc < 0) return fail(rc);
+    h->m2l_mode = h->m2l_tc_ready ? FMMBEM_M2L_TENSOR : (h->m2l_tables ? FMMBEM_M2L_TABLES : FMMBEM_M2L_GATHER);
     const size_t ex = (size_t)h->n_cells * h->ncomp * ESTRIDE;
     const int64_t n = h->N * h->dof;
     h->kr_m = o.restart;
@@ -275,9 +278,13 @@ int fmmbem_set_precision(fmmbem_handle* h, int precision) {
 }
 
 int fmmbem_set_m2l_mode(fmmbem_handle* h, int mode) {
-    if (!h || (mode != FMMBEM_M2L_TABLES && mode != FMMBEM_M2L_GATHER)) { fmmbem_set_error("bad M2L mode"); return FMMBEM_EINVAL; }
-    if (mode == FMMBEM_M2L_TABLES && !h->tab_f) { fmmbem_set_error("M2L operator tables were not built"); return FMMBEM_ESTATE; }
-    h->m2l_tables = mode == FMMBEM_M2L_TABLES;
+    if (!h || (mode != FMMBEM_M2L_TABLES && mode != FMMBEM_M2L_GATHER && mode != FMMBEM_M2L_TENSOR)) {
+        fmmbem_set_error("bad M2L mode");
+        return FMMBEM_EINVAL;
+    }
+    if (mode == FMMBEM_M2L_TABLES && !h->m2l_tables) { fmmbem_set_error("M2L operator tables were not built"); return FMMBEM_ESTATE; }
+    if (mode == FMMBEM_M2L_TENSOR && !h->m2l_tc_ready) { fmmbem_set_error("tensor-core M2L tables were not built"); return FMMBEM_ESTATE; }
+    h->m2l_mode = mode;
     return 0;
 }
 

@@ -452,7 +452,9 @@ int far_field_t(fmmbem_handle* h, int p) {
     prof_end(h, FMMBEM_PASS_M2M, nl);
     // M2L
     prof_begin(h, FMMBEM_PASS_M2L);
-    if (h->m2l_tables) {
+    if (std::is_same<T, float>::value && h->m2l_mode == FMMBEM_M2L_TENSOR && h->m2l_tc_ready && p >= h->tc_min_p) {
+        FMM_TRY(m2l_tc(h, p));
+    } else if (h->m2l_mode != FMMBEM_M2L_GATHER && h->m2l_tables) {
         FMM_TRY(m2l_gemm(h, p, !std::is_same<T, float>::value));
     } else {
         k_m2l<T, NC><<<h->n_cells, m2l_block(p), 0, st>>>(p, h->m2l_ptr, h->m2l_src, h->cell_cs, M, L);

@@ -58,6 +58,16 @@ struct fmmbem_handle {
     size_t tab_stride = 0;
     double* tab_d = nullptr;      // [n_tables][2 ncoef(p_max)][tab_ld]
     float* tab_f = nullptr;
+    // tensor-core (tcgen05) path: operators split into TF32 hi/lo, K-chunked core-matrix layout
+    bool m2l_tc_ready = false;
+    int m2l_mode = FMMBEM_M2L_TABLES;
+    int tc_min_p = 1;             // mixed-precision mat-vecs at p >= tc_min_p use the tensor cores
+    float* tab_tc = nullptr;
+    size_t tc_stride = 0;
+    int tc_rows_max = 0;
+    int4* m2l_tiles_tc = nullptr;
+    int n_tiles_tc = 0;
+    int* tc_err = nullptr;        // set by the kernel if a bounded wait gives up
     int* p2p_ptr = nullptr;  // [n_cells + 1]
     int* p2p_src = nullptr;
     int64_t n_p2p = 0, n_p2p_inter = 0;
@@ -110,6 +120,9 @@ int build_geometry_tree_lists(fmmbem_handle* h, const fmmbem_mesh* mesh);
 // m2l.cu
 int build_m2l_tables(fmmbem_handle* h);
 int m2l_gemm(fmmbem_handle* h, int p, bool fp64);
+// m2l_tc.cu
+int build_m2l_tc(fmmbem_handle* h);
+int m2l_tc(fmmbem_handle* h, int p);
 // fmm.cu
 int far_field(fmmbem_handle* h, int p, bool fp64);
 int far_eval_add(fmmbem_handle* h, int p, bool fp64, double* y_sorted, double scale);

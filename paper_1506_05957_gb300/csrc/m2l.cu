@@ -294,6 +294,23 @@ int build_m2l_tables(fmmbem_handle* h) {
     FMM_TRY(dalloc(&h->m2l_tiles, ntiles));
     k_tile_emit<<<(ntab + T - 1) / T, T, 0, st>>>(tab_first, off, ntab, per_tile, h->m2l_tiles);
     FMM_LAUNCHED();
+    // tiles of 128 rows for the tensor-core path (128 pairs Laplace, 32 pairs x 4 Stokes)
+    {
+        const int per_tc = 128 / h->ncomp;
+        FMM_CU(cudaMemsetAsync(cnt, 0, sizeof(int) * (ntab + 1), st));
+        k_tile_counts<<<(ntab + T - 1) / T, T, 0, st>>>(tab_first, ntab, per_tc, cnt);
+        FMM_LAUNCHED();
+        FMM_CU(cudaMalloc(&tmp, tb ? tb : 1));
+        FMM_CU(cub::DeviceScan::ExclusiveSum(tmp, tb, cnt, off, ntab + 1, st));
+        int ntc = 0;
+        FMM_CU(cudaMemcpyAsync(&ntc, off + ntab, sizeof(int), cudaMemcpyDeviceToHost, st));
+        FMM_CU(cudaStreamSynchronize(st));
+        cudaFree(tmp);
+        FMM_TRY(dalloc(&h->m2l_tiles_tc, ntc));
+        k_tile_emit<<<(ntab + T - 1) / T, T, 0, st>>>(tab_first, off, ntab, per_tc, h->m2l_tiles_tc);
+        FMM_LAUNCHED();
+        h->n_tiles_tc = ntc;
+    }
     FMM_TRY(dalloc(&h->tab_d, (size_t)ntab * per));
     FMM_TRY(dalloc(&h->tab_f, (size_t)ntab * per));
     k_gen_tables<<<ntab, 256, 0, st>>>(tab_key, pmax, ld, h->tab_d, h->tab_f);

@@ -212,20 +212,23 @@ def test_invalid_arguments_are_errors(torch_cuda, sphere1280):
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
-def test_m2l_tables_and_gather_agree(torch_cuda, sphere1280, precision):
-    """The operator-table GEMM and the on-the-fly gather compute the same M2L sums."""
+def test_m2l_formulations_agree(torch_cuda, sphere1280, precision):
+    """Operator-table GEMM (SIMT), on-the-fly gather and, in mixed precision, the
+    tcgen05 3xTF32 path compute the same M2L sums."""
     torch = torch_cuda
     from paper_1506_05957_gb300 import FMMBEM_FP64, FMMBEM_MIXED
-    from paper_1506_05957_gb300.binding import FMMBEM_M2L_GATHER, FMMBEM_M2L_TABLES
+    from paper_1506_05957_gb300.binding import FMMBEM_M2L_GATHER, FMMBEM_M2L_TABLES, FMMBEM_M2L_TENSOR
     s = sphere1280
     h = _h(torch, s["v"], s["t"], ncrit=40, precision=FMMBEM_FP64 if precision == "fp64" else FMMBEM_MIXED)
     x = _dev(torch, np.random.default_rng(5).standard_normal(h.n))
-    ya = torch.zeros_like(x)
-    yb = torch.zeros_like(x)
-    for p in (1, 3, 7, 12, 16):
-        h.set_m2l_mode(FMMBEM_M2L_TABLES)
-        h.matvec(p, x, ya)
-        h.set_m2l_mode(FMMBEM_M2L_GATHER)
-        h.matvec(p, x, yb)
-        tol = 1e-13 if precision == "fp64" else 2e-6
-        assert rel(ya.cpu().numpy(), yb.cpu().numpy()) < tol, p
+    modes = [FMMBEM_M2L_TABLES, FMMBEM_M2L_GATHER] + ([FMMBEM_M2L_TENSOR] if precision == "mixed" else [])
+    tol = 1e-13 if precision == "fp64" else 2e-6
+    for p in (1, 3, 7, 12, 15, 16):
+        ys = []
+        for mode in modes:
+            h.set_m2l_mode(mode)
+            y = torch.zeros_like(x)
+            h.matvec(p, x, y)
+            ys.append(y.cpu().numpy())
+        for y in ys[1:]:
+            assert rel(y, ys[0]) < tol, p
