@@ -44,6 +44,8 @@ struct fmmbem_handle {
     int* cell_level = nullptr;
     int* cell_parent = nullptr;
     int* leaves = nullptr;         // [n_leaves] cell ids
+    int* leaf_class = nullptr;     // [n_leaves] leaves ordered by target count class (<=32, <=64, more)
+    int leaf_class_start[4] = {0, 0, 0, 0};
 
     // interaction lists (CSR by target cell)
     int* m2l_ptr = nullptr;  // [n_cells + 1]

@@ -229,25 +229,40 @@ __device__ __forceinline__ void kahan_add(float& hi, float& lo, float v) {
     hi = t;
 }
 
+// Each source of a staged tile carries its global Gauss-point index in .w of a
+// companion int array only for the target leaf's own sources (the own panel is
+// skipped there); other leaves are merged into shared tiles of up to LAP_TILE
+// sources, so one barrier pair serves many small leaves. Two partial sums per
+// target alternate between sources to break the FMA dependency chain.
 template <int TPL>
 __device__ __forceinline__ void lap_tile(const float4* s, int q0, int q1, const float* tx, const float* ty,
                                          const float* tz, float* hi, float* lo) {
-    for (int qb = q0; qb < q1; qb += 32) {
-        const int qe = min(q1, qb + 32);
-        float part[TPL];
+    for (int qb = q0; qb < q1; qb += 64) {
+        const int qe = min(q1, qb + 64);
+        float pa[TPL], pb[TPL];
 #pragma unroll
-        for (int t = 0; t < TPL; ++t) part[t] = 0.f;
-#pragma unroll 4
-        for (int q = qb; q < qe; ++q) {
-            const float4 v = s[q];
+        for (int t = 0; t < TPL; ++t) { pa[t] = 0.f; pb[t] = 0.f; }
+        int q = qb;
+        for (; q + 1 < qe; q += 2) {
+            const float4 u = s[q], v = s[q + 1];
 #pragma unroll
             for (int t = 0; t < TPL; ++t) {
-                const float dx = tx[t] - v.x, dy = ty[t] - v.y, dz = tz[t] - v.z;
-                part[t] = fmaf(v.w, rsqrt_approx(fmaf(dx, dx, fmaf(dy, dy, dz * dz))), part[t]);
+                const float ux = tx[t] - u.x, uy = ty[t] - u.y, uz = tz[t] - u.z;
+                const float vx = tx[t] - v.x, vy = ty[t] - v.y, vz = tz[t] - v.z;
+                pa[t] = fmaf(u.w, rsqrt_approx(fmaf(ux, ux, fmaf(uy, uy, uz * uz))), pa[t]);
+                pb[t] = fmaf(v.w, rsqrt_approx(fmaf(vx, vx, fmaf(vy, vy, vz * vz))), pb[t]);
+            }
+        }
+        if (q < qe) {
+            const float4 u = s[q];
+#pragma unroll
+            for (int t = 0; t < TPL; ++t) {
+                const float ux = tx[t] - u.x, uy = ty[t] - u.y, uz = tz[t] - u.z;
+                pa[t] = fmaf(u.w, rsqrt_approx(fmaf(ux, ux, fmaf(uy, uy, uz * uz))), pa[t]);
             }
         }
 #pragma unroll
-        for (int t = 0; t < TPL; ++t) kahan_add(hi[t], lo[t], part[t]);
+        for (int t = 0; t < TPL; ++t) kahan_add(hi[t], lo[t], pa[t] + pb[t]);
     }
 }
 
@@ -275,61 +290,6 @@ __device__ __forceinline__ void lap_tile_self(const float4* s, int q0, int q1, i
 }
 
 template <int TPL>
-__device__ void lap_p2p_chunk(int cell, int tb, int nt, const double4* cs, const int2* range, const int* pptr,
-                              const int* psrc, const float4* srcw, const float4* tgt, int K, const int* cptr,
-                              const int* ccol, const double* cval, const double* xs, double* ynear, float4* sS,
-                              double* sred) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    float tx[TPL], ty[TPL], tz[TPL];
-    int own[TPL];
-    float hi[TPL], lo[TPL];
-#pragma unroll
-    for (int t = 0; t < TPL; ++t) {
-        const int li = lane + 32 * t;
-        const float4 x = li < nt ? tgt[tb + li] : make_float4(1e30f, 0.f, 0.f, 0.f);
-        tx[t] = x.x; ty[t] = x.y; tz[t] = x.z;
-        own[t] = (tb + li) * K;
-        hi[t] = 0.f;
-        lo[t] = 0.f;
-    }
-    const double4 ccell = cs[cell];
-    for (int e = pptr[cell]; e < pptr[cell + 1]; ++e) {
-        const int sc = psrc[e];
-        const int2 sr = range[sc];
-        const double4 cc = cs[sc];
-        const float shx = (float)(cc.x - ccell.x), shy = (float)(cc.y - ccell.y), shz = (float)(cc.z - ccell.z);
-        const int g0 = sr.x * K, g1 = sr.y * K;
-        for (int gb = g0; gb < g1; gb += LAP_TILE) {
-            const int n = min(LAP_TILE, g1 - gb);
-            __syncthreads();
-            for (int q = threadIdx.x; q < n; q += blockDim.x) {
-                float4 v = srcw[gb + q];
-                v.x += shx; v.y += shy; v.z += shz;
-                sS[q] = v;
-            }
-            __syncthreads();
-            const int per = (n + 3) >> 2;
-            const int q0 = min(n, warp * per), q1 = min(n, q0 + per);
-            if (sc == cell) lap_tile_self<TPL>(sS, q0, q1, gb, own, K, tx, ty, tz, hi, lo);
-            else lap_tile<TPL>(sS, q0, q1, tx, ty, tz, hi, lo);
-        }
-    }
-    __syncthreads();
-#pragma unroll
-    for (int t = 0; t < TPL; ++t) sred[warp * 128 + lane + 32 * t] = (double)hi[t] - (double)lo[t];
-    __syncthreads();
-    if (warp == 0) {
-#pragma unroll
-        for (int t = 0; t < TPL; ++t) {
-            const int li = lane + 32 * t;
-            if (li >= nt) continue;
-            double out = sred[li] + sred[128 + li] + sred[256 + li] + sred[384 + li];
-            add_correction<1>(tb + li, cptr, ccol, cval, xs, &out);
-            ynear[tb + li] = out;
-        }
-    }
-}
-
 __global__ void __launch_bounds__(128) k_p2p_lap(const int* leaves, const double4* cs, const int2* range,
                                                  const int* pptr, const int* psrc, const float4* srcw,
                                                  const float4* tgt, int K, const int* cptr, const int* ccol,
@@ -338,11 +298,92 @@ __global__ void __launch_bounds__(128) k_p2p_lap(const int* leaves, const double
     __shared__ double sred[4 * 128];
     const int cell = leaves[blockIdx.x];
     const int2 r = range[cell];
-    for (int tb = r.x; tb < r.y; tb += 128) {
-        const int nt = min(128, r.y - tb);
-        if (nt <= 32) lap_p2p_chunk<1>(cell, tb, nt, cs, range, pptr, psrc, srcw, tgt, K, cptr, ccol, cval, xs, ynear, sS, sred);
-        else if (nt <= 64) lap_p2p_chunk<2>(cell, tb, nt, cs, range, pptr, psrc, srcw, tgt, K, cptr, ccol, cval, xs, ynear, sS, sred);
-        else lap_p2p_chunk<4>(cell, tb, nt, cs, range, pptr, psrc, srcw, tgt, K, cptr, ccol, cval, xs, ynear, sS, sred);
+    const double4 ccell = cs[cell];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int tb = r.x; tb < r.y; tb += 32 * TPL) {
+        const int nt = min(32 * TPL, r.y - tb);
+        float tx[TPL], ty[TPL], tz[TPL], hi[TPL], lo[TPL];
+        int own[TPL];
+#pragma unroll
+        for (int t = 0; t < TPL; ++t) {
+            const int li = lane + 32 * t;
+            const float4 x = li < nt ? tgt[tb + li] : make_float4(1e30f, 0.f, 0.f, 0.f);
+            tx[t] = x.x; ty[t] = x.y; tz[t] = x.z;
+            own[t] = (tb + li) * K;
+            hi[t] = 0.f;
+            lo[t] = 0.f;
+        }
+        // the target leaf's own sources, with the own-panel skip
+        {
+            const int g0 = r.x * K, g1 = r.y * K;
+            for (int gb = g0; gb < g1; gb += LAP_TILE) {
+                const int n = min(LAP_TILE, g1 - gb);
+                __syncthreads();
+                for (int q = threadIdx.x; q < n; q += blockDim.x) sS[q] = srcw[gb + q];
+                __syncthreads();
+                const int per = (n + 3) >> 2;
+                const int q0 = min(n, warp * per), q1 = min(n, q0 + per);
+                lap_tile_self<TPL>(sS, q0, q1, gb, own, K, tx, ty, tz, hi, lo);
+            }
+        }
+        __syncthreads();
+        // every other leaf of the list, merged into shared tiles
+        int fill = 0;
+        const int e1 = pptr[cell + 1];
+        for (int e = pptr[cell]; e <= e1; ++e) {
+            int sc = -1, g0 = 0, g1 = 0;
+            if (e < e1) {
+                sc = psrc[e];
+                if (sc == cell) continue;
+                const int2 sr = range[sc];
+                g0 = sr.x * K;
+                g1 = sr.y * K;
+            }
+            // flush when the next leaf does not fit, or at the end
+            if (e == e1 || fill + (g1 - g0) > LAP_TILE) {
+                __syncthreads();
+                const int per = (fill + 3) >> 2;
+                const int q0 = min(fill, warp * per), q1 = min(fill, q0 + per);
+                lap_tile<TPL>(sS, q0, q1, tx, ty, tz, hi, lo);
+                fill = 0;
+                if (e == e1) break;
+                __syncthreads();
+            }
+            const double4 cc = cs[sc];
+            const float shx = (float)(cc.x - ccell.x), shy = (float)(cc.y - ccell.y), shz = (float)(cc.z - ccell.z);
+            for (int gb = g0; gb < g1; gb += LAP_TILE) {
+                const int n = min(LAP_TILE, g1 - gb);
+                if (fill + n > LAP_TILE) {  // a leaf larger than a tile: process what is staged
+                    __syncthreads();
+                    const int per = (fill + 3) >> 2;
+                    const int q0 = min(fill, warp * per), q1 = min(fill, q0 + per);
+                    lap_tile<TPL>(sS, q0, q1, tx, ty, tz, hi, lo);
+                    fill = 0;
+                    __syncthreads();
+                }
+                for (int q = threadIdx.x; q < n; q += blockDim.x) {
+                    float4 v = srcw[gb + q];
+                    v.x += shx; v.y += shy; v.z += shz;
+                    sS[fill + q] = v;
+                }
+                fill += n;
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int t = 0; t < TPL; ++t) sred[warp * 128 + lane + 32 * t] = (double)hi[t] - (double)lo[t];
+        __syncthreads();
+        if (warp == 0) {
+#pragma unroll
+            for (int t = 0; t < TPL; ++t) {
+                const int li = lane + 32 * t;
+                if (li >= nt) continue;
+                double out = sred[li] + sred[128 + li] + sred[256 + li] + sred[384 + li];
+                add_correction<1>(tb + li, cptr, ccol, cval, xs, &out);
+                ynear[tb + li] = out;
+            }
+        }
+        __syncthreads();
     }
 }
 
@@ -431,11 +472,23 @@ int near_field_on(fmmbem_handle* h, bool fp64) {
     if (h->kernel == FMMBEM_LAPLACE && !fp64) {
         k_pack_sources<<<(unsigned)((h->NS + 255) / 256), 256, 0, h->stream>>>(h->src_rel, h->xin, h->K, h->NS, h->src_w);
         FMM_LAUNCHED();
-        k_p2p_lap<<<h->n_leaves, 128, 0, h->stream>>>(h->leaves, h->cell_cs, h->cell_range, h->p2p_ptr, h->p2p_src,
-                                                     h->src_w, h->tgt_rel, h->K, h->corr_ptr, h->corr_col, h->corr_sl,
-                                                     h->xin, h->ynear);
+        // leaves grouped by target count: <= 32, <= 64, more (targets per lane 1, 2, 4)
+        const int* cls = h->leaf_class;
+        const int n1 = h->leaf_class_start[1], n2 = h->leaf_class_start[2] - n1, n3 = h->n_leaves - n1 - n2;
+        if (n1 > 0)
+            k_p2p_lap<1><<<n1, 128, 0, h->stream>>>(cls, h->cell_cs, h->cell_range, h->p2p_ptr, h->p2p_src, h->src_w,
+                                                    h->tgt_rel, h->K, h->corr_ptr, h->corr_col, h->corr_sl, h->xin,
+                                                    h->ynear);
+        if (n2 > 0)
+            k_p2p_lap<2><<<n2, 128, 0, h->stream>>>(cls + n1, h->cell_cs, h->cell_range, h->p2p_ptr, h->p2p_src,
+                                                    h->src_w, h->tgt_rel, h->K, h->corr_ptr, h->corr_col, h->corr_sl,
+                                                    h->xin, h->ynear);
+        if (n3 > 0)
+            k_p2p_lap<4><<<n3, 128, 0, h->stream>>>(cls + n1 + n2, h->cell_cs, h->cell_range, h->p2p_ptr, h->p2p_src,
+                                                    h->src_w, h->tgt_rel, h->K, h->corr_ptr, h->corr_col, h->corr_sl,
+                                                    h->xin, h->ynear);
         FMM_LAUNCHED();
-        h->launches += 1;
+        h->launches += (n1 > 0) + (n2 > 0) + (n3 > 0);
     } else if (h->kernel == FMMBEM_LAPLACE) rc = launch_p2p<double, LAP_SL>(h);
     else rc = fp64 ? launch_p2p<double, STK_SL>(h) : launch_p2p<float, STK_SL>(h);
     prof_end(h, FMMBEM_PASS_P2P, 1);

@@ -364,6 +364,16 @@ __global__ void k_relative(const int* leaves, const double4* cs, const int2* ran
     }
 }
 
+__global__ void k_leaf_class_key(const int* leaves, const int2* range, int n, int* key, int* counts) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int2 r = range[leaves[i]];
+    const int nt = r.y - r.x;
+    const int c = nt <= 32 ? 0 : (nt <= 64 ? 1 : 2);
+    key[i] = c;
+    atomicAdd(&counts[c], 1);
+}
+
 __global__ void k_leaves(const int2* child, const int2* range, int ncells, int* leaves, int* nleaf, int* maxp) {
     int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= ncells) return;
@@ -736,6 +746,30 @@ int build_geometry_tree_lists(fmmbem_handle* h, const fmmbem_mesh* mesh) {
         cudaFree(tmp);
         cudaFree(h->leaves);
         h->leaves = ls;
+        // leaves ordered by target-count class for the near-field kernels
+        {
+            int *ckey = nullptr, *ckey_s = nullptr, *counts = nullptr;
+            FMM_TRY(dalloc(&ckey, h->n_leaves));
+            FMM_TRY(dalloc(&ckey_s, h->n_leaves));
+            FMM_TRY(dalloc(&counts, 3));
+            FMM_TRY(dalloc(&h->leaf_class, h->n_leaves));
+            FMM_CU(cudaMemsetAsync(counts, 0, 3 * sizeof(int), st));
+            k_leaf_class_key<<<(h->n_leaves + T - 1) / T, T, 0, st>>>(h->leaves, h->cell_range, h->n_leaves, ckey, counts);
+            FMM_LAUNCHED();
+            size_t tb2 = 0;
+            FMM_CU(cub::DeviceRadixSort::SortPairs(nullptr, tb2, ckey, ckey_s, h->leaves, h->leaf_class, h->n_leaves, 0, 2, st));
+            void* tmp2 = nullptr;
+            FMM_CU(cudaMalloc(&tmp2, tb2 ? tb2 : 1));
+            FMM_CU(cub::DeviceRadixSort::SortPairs(tmp2, tb2, ckey, ckey_s, h->leaves, h->leaf_class, h->n_leaves, 0, 2, st));
+            int c_h[3];
+            FMM_CU(cudaMemcpyAsync(c_h, counts, sizeof(c_h), cudaMemcpyDeviceToHost, st));
+            FMM_CU(cudaStreamSynchronize(st));
+            cudaFree(tmp2); cudaFree(ckey); cudaFree(ckey_s); cudaFree(counts);
+            h->leaf_class_start[0] = 0;
+            h->leaf_class_start[1] = c_h[0];
+            h->leaf_class_start[2] = c_h[0] + c_h[1];
+            h->leaf_class_start[3] = h->n_leaves;
+        }
         FMM_TRY(dalloc(&h->tgt_rel, n));
         FMM_TRY(dalloc(&h->src_rel, h->NS));
         if (h->n_leaves > 0) {
