@@ -73,6 +73,9 @@ struct fmmbem_handle {
     int* p2p_ptr = nullptr;  // [n_cells + 1]
     int* p2p_src = nullptr;
     int64_t n_p2p = 0, n_p2p_inter = 0;
+    float4* p2p_rec = nullptr;  // [n_p2p] FP32 shift c_source - c_target (x,y,z) and first Gauss point (int bits)
+    int* p2p_off = nullptr;     // [n_p2p] offset of the pair in its target leaf's source stream (self pair: empty)
+    int* p2p_len = nullptr;     // [n_cells] length of each target leaf's source stream
     int max_leaf_panels = 0;
 
     // near-singular / self corrections (CSR by sorted target panel), FP64

@@ -289,17 +289,28 @@ __device__ __forceinline__ void lap_tile_self(const float4* s, int q0, int q1, i
     }
 }
 
+// Per target leaf the sources of every other leaf of its P2P list form one
+// concatenated stream; the static per-pair records (leaf-to-leaf FP32 shift, first
+// Gauss point, offset in the stream) are loaded into shared memory once, and each
+// slot of a staged tile finds its pair by a binary search over the offsets, so
+// staging runs in parallel with no dependent global-load chains.
+constexpr int LAP_MAXE = 512;
+
 template <int TPL>
-__global__ void __launch_bounds__(128) k_p2p_lap(const int* leaves, const double4* cs, const int2* range,
-                                                 const int* pptr, const int* psrc, const float4* srcw,
-                                                 const float4* tgt, int K, const int* cptr, const int* ccol,
-                                                 const double* cval, const double* xs, double* ynear) {
+__global__ void __launch_bounds__(128) k_p2p_lap(const int* leaves, const int2* range, const int* pptr,
+                                                 const float4* prec, const int* poff, const int* plen,
+                                                 const float4* srcw, const float4* tgt, int K, const int* cptr,
+                                                 const int* ccol, const double* cval, const double* xs,
+                                                 double* ynear) {
     __shared__ float4 sS[LAP_TILE];
+    __shared__ float4 sRec[LAP_MAXE];
+    __shared__ int sOff[LAP_MAXE];
     __shared__ double sred[4 * 128];
     const int cell = leaves[blockIdx.x];
     const int2 r = range[cell];
-    const double4 ccell = cs[cell];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int e0 = pptr[cell], e1 = pptr[cell + 1];
+    const int total = plen[cell];
     for (int tb = r.x; tb < r.y; tb += 32 * TPL) {
         const int nt = min(32 * TPL, r.y - tb);
         float tx[TPL], ty[TPL], tz[TPL], hi[TPL], lo[TPL];
@@ -326,47 +337,36 @@ __global__ void __launch_bounds__(128) k_p2p_lap(const int* leaves, const double
                 lap_tile_self<TPL>(sS, q0, q1, gb, own, K, tx, ty, tz, hi, lo);
             }
         }
-        __syncthreads();
-        // every other leaf of the list, merged into shared tiles
-        int fill = 0;
-        const int e1 = pptr[cell + 1];
-        for (int e = pptr[cell]; e <= e1; ++e) {
-            int sc = -1, g0 = 0, g1 = 0;
-            if (e < e1) {
-                sc = psrc[e];
-                if (sc == cell) continue;
-                const int2 sr = range[sc];
-                g0 = sr.x * K;
-                g1 = sr.y * K;
+        // the other leaves, as one stream of Gauss points
+        for (int eb = e0; eb < e1; eb += LAP_MAXE) {
+            const int ne = min(LAP_MAXE, e1 - eb);
+            __syncthreads();
+            for (int j = threadIdx.x; j < ne; j += blockDim.x) {
+                sRec[j] = prec[eb + j];
+                sOff[j] = poff[eb + j];
             }
-            // flush when the next leaf does not fit, or at the end
-            if (e == e1 || fill + (g1 - g0) > LAP_TILE) {
-                __syncthreads();
-                const int per = (fill + 3) >> 2;
-                const int q0 = min(fill, warp * per), q1 = min(fill, q0 + per);
-                lap_tile<TPL>(sS, q0, q1, tx, ty, tz, hi, lo);
-                fill = 0;
-                if (e == e1) break;
-                __syncthreads();
-            }
-            const double4 cc = cs[sc];
-            const float shx = (float)(cc.x - ccell.x), shy = (float)(cc.y - ccell.y), shz = (float)(cc.z - ccell.z);
-            for (int gb = g0; gb < g1; gb += LAP_TILE) {
-                const int n = min(LAP_TILE, g1 - gb);
-                if (fill + n > LAP_TILE) {  // a leaf larger than a tile: process what is staged
-                    __syncthreads();
-                    const int per = (fill + 3) >> 2;
-                    const int q0 = min(fill, warp * per), q1 = min(fill, q0 + per);
-                    lap_tile<TPL>(sS, q0, q1, tx, ty, tz, hi, lo);
-                    fill = 0;
-                    __syncthreads();
-                }
+            __syncthreads();
+            const int s_beg = sOff[0];
+            const int s_end = (eb + LAP_MAXE < e1) ? poff[eb + LAP_MAXE] : total;
+            for (int s0 = s_beg; s0 < s_end; s0 += LAP_TILE) {
+                const int n = min(LAP_TILE, s_end - s0);
                 for (int q = threadIdx.x; q < n; q += blockDim.x) {
-                    float4 v = srcw[gb + q];
-                    v.x += shx; v.y += shy; v.z += shz;
-                    sS[fill + q] = v;
+                    const int sp = s0 + q;
+                    int lo_i = 0, hi_i = ne;  // last j with sOff[j] <= sp
+                    while (hi_i - lo_i > 1) {
+                        const int mid = (lo_i + hi_i) >> 1;
+                        if (sOff[mid] <= sp) lo_i = mid; else hi_i = mid;
+                    }
+                    const float4 rc = sRec[lo_i];
+                    float4 v = srcw[__float_as_int(rc.w) + (sp - sOff[lo_i])];
+                    v.x += rc.x; v.y += rc.y; v.z += rc.z;
+                    sS[q] = v;
                 }
-                fill += n;
+                __syncthreads();
+                const int per = (n + 3) >> 2;
+                const int q0 = min(n, warp * per), q1 = min(n, q0 + per);
+                lap_tile<TPL>(sS, q0, q1, tx, ty, tz, hi, lo);
+                __syncthreads();
             }
         }
         __syncthreads();
@@ -476,17 +476,17 @@ int near_field_on(fmmbem_handle* h, bool fp64) {
         const int* cls = h->leaf_class;
         const int n1 = h->leaf_class_start[1], n2 = h->leaf_class_start[2] - n1, n3 = h->n_leaves - n1 - n2;
         if (n1 > 0)
-            k_p2p_lap<1><<<n1, 128, 0, h->stream>>>(cls, h->cell_cs, h->cell_range, h->p2p_ptr, h->p2p_src, h->src_w,
-                                                    h->tgt_rel, h->K, h->corr_ptr, h->corr_col, h->corr_sl, h->xin,
-                                                    h->ynear);
+            k_p2p_lap<1><<<n1, 128, 0, h->stream>>>(cls, h->cell_range, h->p2p_ptr, h->p2p_rec, h->p2p_off, h->p2p_len,
+                                                    h->src_w, h->tgt_rel, h->K, h->corr_ptr, h->corr_col, h->corr_sl,
+                                                    h->xin, h->ynear);
         if (n2 > 0)
-            k_p2p_lap<2><<<n2, 128, 0, h->stream>>>(cls + n1, h->cell_cs, h->cell_range, h->p2p_ptr, h->p2p_src,
-                                                    h->src_w, h->tgt_rel, h->K, h->corr_ptr, h->corr_col, h->corr_sl,
-                                                    h->xin, h->ynear);
+            k_p2p_lap<2><<<n2, 128, 0, h->stream>>>(cls + n1, h->cell_range, h->p2p_ptr, h->p2p_rec, h->p2p_off,
+                                                    h->p2p_len, h->src_w, h->tgt_rel, h->K, h->corr_ptr, h->corr_col,
+                                                    h->corr_sl, h->xin, h->ynear);
         if (n3 > 0)
-            k_p2p_lap<4><<<n3, 128, 0, h->stream>>>(cls + n1 + n2, h->cell_cs, h->cell_range, h->p2p_ptr, h->p2p_src,
-                                                    h->src_w, h->tgt_rel, h->K, h->corr_ptr, h->corr_col, h->corr_sl,
-                                                    h->xin, h->ynear);
+            k_p2p_lap<4><<<n3, 128, 0, h->stream>>>(cls + n1 + n2, h->cell_range, h->p2p_ptr, h->p2p_rec,
+                                                    h->p2p_off, h->p2p_len, h->src_w, h->tgt_rel, h->K, h->corr_ptr,
+                                                    h->corr_col, h->corr_sl, h->xin, h->ynear);
         FMM_LAUNCHED();
         h->launches += (n1 > 0) + (n2 > 0) + (n3 > 0);
     } else if (h->kernel == FMMBEM_LAPLACE) rc = launch_p2p<double, LAP_SL>(h);

@@ -364,6 +364,26 @@ __global__ void k_relative(const int* leaves, const double4* cs, const int2* ran
     }
 }
 
+// Static P2P records per target leaf: the other leaves of its list form one stream
+// of Gauss points; each pair stores its FP32 leaf-to-leaf shift, first Gauss point and
+// offset in the stream (the self pair contributes nothing to the stream).
+__global__ void k_p2p_records(const int* pptr, const int* psrc, const double4* cs, const int2* range, int ncells,
+                              int K, float4* rec, int* off, int* len) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ncells) return;
+    const double4 ct = cs[c];
+    int acc = 0;
+    for (int e = pptr[c]; e < pptr[c + 1]; ++e) {
+        const int s = psrc[e];
+        const double4 cv = cs[s];
+        const int2 r = range[s];
+        rec[e] = make_float4((float)(cv.x - ct.x), (float)(cv.y - ct.y), (float)(cv.z - ct.z), __int_as_float(r.x * K));
+        off[e] = acc;
+        if (s != c) acc += K * (r.y - r.x);
+    }
+    len[c] = acc;
+}
+
 __global__ void k_leaf_class_key(const int* leaves, const int2* range, int n, int* key, int* counts) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -856,6 +876,12 @@ int build_geometry_tree_lists(fmmbem_handle* h, const fmmbem_mesh* mesh) {
         h->n_m2l_same = (int64_t)s_h[0];
         h->n_p2p_inter = (int64_t)s_h[1];
         cudaFree(cnt);
+        FMM_TRY(dalloc(&h->p2p_rec, h->n_p2p));
+        FMM_TRY(dalloc(&h->p2p_off, h->n_p2p));
+        FMM_TRY(dalloc(&h->p2p_len, nc));
+        k_p2p_records<<<(nc + T - 1) / T, T, 0, st>>>(h->p2p_ptr, h->p2p_src, h->cell_cs, h->cell_range, nc, K,
+                                                     h->p2p_rec, h->p2p_off, h->p2p_len);
+        FMM_LAUNCHED();
     }
 
     // ---- near-singular table
