@@ -129,6 +129,11 @@ int fmmbem_set_precision(fmmbem_handle* h, int precision);
 /* Select the M2L formulation; FMMBEM_ESTATE if the operator tables were not built. */
 int fmmbem_set_m2l_mode(fmmbem_handle* h, int mode);
 
+/* Near-field kernel of FMMBEM_MIXED Laplace mat-vecs (same sums, different schedules):
+ * 0 = source tiles staged in shared memory, targets held per lane;
+ * 1 = (target, source slice) per thread, sources read through L1 (default). */
+int fmmbem_set_p2p_variant(fmmbem_handle* h, int variant);
+
 /*
  * y = A x through the FMM at expansion order p (eq. matvec-onerow with the
  * far field by P2M, M2M, M2L, L2L, L2P and the near field by P2P plus the

@@ -77,6 +77,7 @@ def lib():
         L.fmmbem_set_precision.argtypes = [_vp, ctypes.c_int]
         L.fmmbem_matvec.argtypes = [_vp, ctypes.c_int, _vp, _vp]
         L.fmmbem_set_m2l_mode.argtypes = [_vp, ctypes.c_int]
+        L.fmmbem_set_p2p_variant.argtypes = [_vp, ctypes.c_int]
         L.fmmbem_matvec_direct.argtypes = [_vp, _vp, _vp]
         L.fmmbem_rhs.argtypes = [_vp, _vp, _vp]
         L.fmmbem_stokes_dl_apply.argtypes = [_vp, _vp, _vp]
@@ -182,6 +183,9 @@ class FmmBem:
 
     def set_precision(self, precision):
         _check(lib().fmmbem_set_precision(self.h, int(precision)))
+
+    def set_p2p_variant(self, variant):
+        _check(lib().fmmbem_set_p2p_variant(self.h, int(variant)))
 
     def set_m2l_mode(self, mode):
         _check(lib().fmmbem_set_m2l_mode(self.h, int(mode)))

@@ -277,6 +277,12 @@ int fmmbem_set_precision(fmmbem_handle* h, int precision) {
     return 0;
 }
 
+int fmmbem_set_p2p_variant(fmmbem_handle* h, int variant) {
+    if (!h || (variant != 0 && variant != 1)) { fmmbem_set_error("bad P2P variant"); return FMMBEM_EINVAL; }
+    h->p2p_variant = variant;
+    return 0;
+}
+
 int fmmbem_set_m2l_mode(fmmbem_handle* h, int mode) {
     if (!h || (mode != FMMBEM_M2L_TABLES && mode != FMMBEM_M2L_GATHER && mode != FMMBEM_M2L_TENSOR)) {
         fmmbem_set_error("bad M2L mode");

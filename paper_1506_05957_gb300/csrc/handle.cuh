@@ -77,6 +77,7 @@ struct fmmbem_handle {
     int* p2p_off = nullptr;     // [n_p2p] offset of the pair in its target leaf's source stream (self pair: empty)
     int* p2p_len = nullptr;     // [n_cells] length of each target leaf's source stream
     int max_leaf_panels = 0;
+    int p2p_variant = 1;        // 0: shared-memory stream tiles, 1: sliced L1 broadcast
 
     // near-singular / self corrections (CSR by sorted target panel), FP64
     int* corr_ptr = nullptr;   // [N + 1]

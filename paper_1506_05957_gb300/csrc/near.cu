@@ -387,6 +387,78 @@ __global__ void __launch_bounds__(128) k_p2p_lap(const int* leaves, const int2* 
     }
 }
 
+// Sliced variant: thread tid of the block takes target tid % nt and source slice
+// tid / nt (S = 128 / nt slices), so small leaves still keep every lane busy. Each
+// slice walks whole P2P pairs (pair e goes to slice (e - e0) % S) and reads the Gauss
+// points straight through L1: all lanes of a slice read the same address, so every
+// load is a broadcast. No shared staging, no barriers inside the sums.
+__device__ __forceinline__ void lap_run(const float4* __restrict__ srcw, int g0, int n, float shx, float shy,
+                                        float shz, float tx, float ty, float tz, int skip0, int K, float& hi,
+                                        float& lo) {
+    const float px = tx - shx, py = ty - shy, pz = tz - shz;
+    for (int qb = 0; qb < n; qb += 64) {
+        const int qe = min(n, qb + 64);
+        float pa = 0.f, pb = 0.f;
+        int q = qb;
+        if (skip0 < 0) {
+#pragma unroll 2
+            for (; q + 1 < qe; q += 2) {
+                const float4 u = __ldg(srcw + g0 + q), v = __ldg(srcw + g0 + q + 1);
+                const float ux = px - u.x, uy = py - u.y, uz = pz - u.z;
+                const float vx = px - v.x, vy = py - v.y, vz = pz - v.z;
+                pa = fmaf(u.w, rsqrt_approx(fmaf(ux, ux, fmaf(uy, uy, uz * uz))), pa);
+                pb = fmaf(v.w, rsqrt_approx(fmaf(vx, vx, fmaf(vy, vy, vz * vz))), pb);
+            }
+        }
+        for (; q < qe; ++q) {
+            if ((unsigned)(q - skip0) < (unsigned)K) continue;
+            const float4 u = __ldg(srcw + g0 + q);
+            const float ux = px - u.x, uy = py - u.y, uz = pz - u.z;
+            pa = fmaf(u.w, rsqrt_approx(fmaf(ux, ux, fmaf(uy, uy, uz * uz))), pa);
+        }
+        kahan_add(hi, lo, pa + pb);
+    }
+}
+
+__global__ void __launch_bounds__(128) k_p2p_lap_sliced(const int* leaves, const int2* range, const int* pptr,
+                                                        const int* psrc, const float4* prec, const float4* srcw,
+                                                        const float4* tgt, int K, const int* cptr, const int* ccol,
+                                                        const double* cval, const double* xs, double* ynear) {
+    __shared__ double sred[128];
+    const int cell = leaves[blockIdx.x];
+    const int2 r = range[cell];
+    const int e0 = pptr[cell], e1 = pptr[cell + 1];
+    const int tid = threadIdx.x;
+    for (int tb = r.x; tb < r.y; tb += 128) {
+        const int nt = min(128, r.y - tb);
+        const int S = 128 / nt;
+        const int t = tid % nt, slice = tid / nt;
+        const bool active = slice < S;
+        float hi = 0.f, lo = 0.f;
+        if (active) {
+            const float4 x = tgt[tb + t];
+            for (int e = e0 + slice; e < e1; e += S) {
+                const int sc = psrc[e];
+                const float4 rc = prec[e];
+                const int2 sr = range[sc];
+                const int g0 = __float_as_int(rc.w), n = K * (sr.y - sr.x);
+                const int skip0 = (sc == cell) ? (tb + t) * K - g0 : -(1 << 30);
+                lap_run(srcw, g0, n, rc.x, rc.y, rc.z, x.x, x.y, x.z, skip0, K, hi, lo);
+            }
+        }
+        __syncthreads();
+        sred[tid] = active ? (double)hi - (double)lo : 0.0;
+        __syncthreads();
+        if (slice == 0) {
+            double out = 0.0;
+            for (int sl = 0; sl < S; ++sl) out += sred[sl * nt + t];
+            add_correction<1>(tb + t, cptr, ccol, cval, xs, &out);
+            ynear[tb + t] = out;
+        }
+        __syncthreads();
+    }
+}
+
 // Direct: one thread per target, every Gauss point staged through shared memory.
 template <typename T, int OP>
 __global__ void __launch_bounds__(P2P_THREADS) k_direct(int n, int ns, const typename V4<T>::type* src,
@@ -472,6 +544,16 @@ int near_field_on(fmmbem_handle* h, bool fp64) {
     if (h->kernel == FMMBEM_LAPLACE && !fp64) {
         k_pack_sources<<<(unsigned)((h->NS + 255) / 256), 256, 0, h->stream>>>(h->src_rel, h->xin, h->K, h->NS, h->src_w);
         FMM_LAUNCHED();
+        if (h->p2p_variant == 1) {
+            k_p2p_lap_sliced<<<h->n_leaves, 128, 0, h->stream>>>(h->leaves, h->cell_range, h->p2p_ptr, h->p2p_src,
+                                                                h->p2p_rec, h->src_w, h->tgt_rel, h->K, h->corr_ptr,
+                                                                h->corr_col, h->corr_sl, h->xin, h->ynear);
+            FMM_LAUNCHED();
+            h->launches += 1;
+            prof_end(h, FMMBEM_PASS_P2P, 2);
+            h->launches += 1;
+            return 0;
+        }
         // leaves grouped by target count: <= 32, <= 64, more (targets per lane 1, 2, 4)
         const int* cls = h->leaf_class;
         const int n1 = h->leaf_class_start[1], n2 = h->leaf_class_start[2] - n1, n3 = h->n_leaves - n1 - n2;
