@@ -114,8 +114,17 @@ cudaEvent_t prof_event(ProfState* s) {
 }
 }  // namespace
 
+// While a mat-vec graph is being captured with profiling on, pass boundaries become
+// external event-record nodes of that graph (one event pair per pass, owned by the
+// graph); prof_harvest reads them after each replay, once the stream has synchronized.
 void prof_begin(fmmbem_handle* h, int pass) {
     if (!h->prof_on) return;
+    if (h->capturing >= 0) {
+        cudaEvent_t& e = h->gev[h->capturing][2 * pass];
+        if (!e) cudaEventCreate(&e);
+        cudaEventRecordWithFlags(e, h->stream, cudaEventRecordExternal);
+        return;
+    }
     ProfState* s = prof_state(h);
     cudaEvent_t e = prof_event(s);
     cudaEventRecord(e, h->stream);
@@ -124,6 +133,13 @@ void prof_begin(fmmbem_handle* h, int pass) {
 
 void prof_end(fmmbem_handle* h, int pass, int launches) {
     if (!h->prof_on) return;
+    if (h->capturing >= 0) {
+        cudaEvent_t& e = h->gev[h->capturing][2 * pass + 1];
+        if (!e) cudaEventCreate(&e);
+        cudaEventRecordWithFlags(e, h->stream, cudaEventRecordExternal);
+        h->gev_launches[h->capturing][pass] = launches;
+        return;
+    }
     ProfState* s = prof_state(h);
     if (!s->open[pass]) return;
     cudaEvent_t e = prof_event(s);
@@ -132,7 +148,63 @@ void prof_end(fmmbem_handle* h, int pass, int launches) {
     s->open[pass] = nullptr;
 }
 
+void prof_harvest(fmmbem_handle* h) {
+    const int p = h->pending_graph;
+    if (p < 0) return;
+    h->pending_graph = -1;
+    for (int pass = 0; pass < FMMBEM_N_PASSES; ++pass) {
+        cudaEvent_t a = h->gev[p][2 * pass], b = h->gev[p][2 * pass + 1];
+        if (!a || !b) continue;
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, a, b) != cudaSuccess) continue;
+        h->prof.ms[pass] += ms;
+        h->prof.launches[pass] += h->gev_launches[p][pass];
+        h->prof.calls[pass] += 1;
+    }
+}
+
+static int matvec_launch(fmmbem_handle* h, int p, const double* xs, double* ys);
+
+// Mat-vecs of the solver (fixed buffers xfix -> kw, not profiling) replay one CUDA graph
+// per order p; the graph is recaptured when the arithmetic or kernel selection changed.
 int matvec_sorted(fmmbem_handle* h, int p, const double* xs, double* ys) {
+    const int mode = h->precision * 16 + h->m2l_mode + 4 * h->p2p_variant + 64 * (h->prof_on ? 1 : 0);
+    if (!h->use_graphs || xs != h->xfix || ys != h->kw || h->stream == nullptr)
+        return matvec_launch(h, p, xs, ys);
+    prof_harvest(h);
+    if (h->mv_graph[p] && h->mv_graph_mode[p] != mode) {
+        cudaGraphExecDestroy(h->mv_graph[p]);
+        h->mv_graph[p] = nullptr;
+    }
+    if (!h->mv_graph[p]) {
+        cudaGraph_t g = nullptr;
+        const int64_t keep = h->launches;
+        FMM_CU(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+        h->capturing = p;
+        const int rc = matvec_launch(h, p, xs, ys);
+        h->capturing = -1;
+        cudaError_t e = cudaStreamEndCapture(h->stream, &g);
+        if (rc < 0) { if (g) cudaGraphDestroy(g); return rc; }
+        FMM_CU(e);
+        e = cudaGraphInstantiate(&h->mv_graph[p], g, 0);
+        cudaGraphDestroy(g);
+        FMM_CU(e);
+        h->mv_graph_mode[p] = mode;
+        h->graph_launches[p] = h->launches - keep;
+        h->launches = keep;
+    }
+    FMM_CU(cudaGraphLaunch(h->mv_graph[p], h->stream));
+    h->launches += h->graph_launches[p];
+    if (h->prof_on) h->pending_graph = p;
+    if (h->prof_on) {
+        const double q = (double)(p + 1) * (p + 1);
+        h->prof.m2l_flops += 2.0 * q * q * h->ncomp * (double)h->n_m2l;
+        h->prof.p2p_interactions += (double)h->n_p2p_inter;
+    }
+    return 0;
+}
+
+static int matvec_launch(fmmbem_handle* h, int p, const double* xs, double* ys) {
     const bool fp64 = h->precision == FMMBEM_FP64;
     h->xin = xs;
     prof_begin(h, FMMBEM_PASS_MATVEC);
@@ -182,10 +254,18 @@ void fmmbem_destroy(fmmbem_handle* h) {
     void* bufs[] = {h->perm, h->tgt_d, h->tgt_f, h->nrm_d, h->verts, h->src_d, h->src_f, h->src_rel, h->tgt_rel, h->src_w, h->cell_cs, h->cell_range,
                     h->cell_child, h->cell_level, h->cell_parent, h->leaves, h->leaf_class, h->m2l_ptr, h->m2l_src, h->p2p_ptr,
                     h->p2p_src, h->p2p_rec, h->p2p_off, h->p2p_len, h->corr_ptr, h->corr_col, h->corr_sl, h->corr_dl, h->oct_d, h->oct_f, h->M, h->L,
-                    h->xs, h->ys, h->ynear, h->m2l_pt, h->m2l_ps, h->m2l_tiles, h->tab_d, h->tab_f, h->tab_tc, h->m2l_tiles_tc, h->tc_err, h->V, h->kw, h->kb, h->kx, h->kr, h->kpart, h->kh, h->kyv};
+                    h->xs, h->ys, h->ynear, h->m2l_pt, h->m2l_ps, h->m2l_tiles, h->tab_d, h->tab_f, h->tab_tc, h->m2l_tiles_tc, h->tc_err, h->V, h->kw, h->xfix, h->kb, h->kx, h->kr, h->kpart, h->kh, h->kyv};
     for (void* b : bufs)
         if (b) cudaFree(b);
     if (h->kh_host) cudaFreeHost(h->kh_host);
+    for (int q = 0; q <= FMMBEM_P_MAX; ++q) {
+        if (h->mv_graph[q]) cudaGraphExecDestroy(h->mv_graph[q]);
+        for (int e = 0; e < 2 * FMMBEM_N_PASSES; ++e)
+            if (h->gev[q][e]) cudaEventDestroy(h->gev[q][e]);
+    }
+    if (h->ev_in) cudaEventDestroy(h->ev_in);
+    if (h->ev_out) cudaEventDestroy(h->ev_out);
+    if (h->istream) cudaStreamDestroy(h->istream);
     if (h->ev_fork) cudaEventDestroy(h->ev_fork);
     if (h->ev_join) cudaEventDestroy(h->ev_join);
     if (h->stream2) cudaStreamDestroy(h->stream2);
@@ -228,6 +308,9 @@ int fmmbem_create(const fmmbem_mesh* mesh, int kernel, int gauss_k, int ncrit, d
     h->stream = (cudaStream_t)o.stream;
     auto fail = [&](int rc) { fmmbem_destroy(h); return rc; };
     if (cudaStreamCreateWithFlags(&h->stream2, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&h->istream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->ev_out, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming) != cudaSuccess) {
         fmmbem_set_error("stream/event creation failed: %s", cudaGetErrorString(cudaGetLastError()));
@@ -250,6 +333,7 @@ int fmmbem_create(const fmmbem_mesh* mesh, int kernel, int gauss_k, int ncrit, d
     if ((rc = dalloc(&h->src_w, h->NS)) < 0) return fail(rc);
     if ((rc = dalloc(&h->xs, n)) < 0 || (rc = dalloc(&h->ys, n)) < 0 || (rc = dalloc(&h->ynear, n)) < 0) return fail(rc);
     if ((rc = dalloc(&h->V, (size_t)(o.restart + 1) * n)) < 0) return fail(rc);
+    if ((rc = dalloc(&h->xfix, n)) < 0) return fail(rc);
     if ((rc = dalloc(&h->kw, n)) < 0 || (rc = dalloc(&h->kb, n)) < 0 || (rc = dalloc(&h->kx, n)) < 0 ||
         (rc = dalloc(&h->kr, n)) < 0)
         return fail(rc);
@@ -396,6 +480,7 @@ int fmmbem_profile_enable(fmmbem_handle* h, int enable) {
     for (auto& e : s->open) e = nullptr;
     memset(&h->prof, 0, sizeof(h->prof));
     h->launches = 0;
+    h->pending_graph = -1;
     h->prof_on = enable != 0;
     return 0;
 }
@@ -403,6 +488,8 @@ int fmmbem_profile_enable(fmmbem_handle* h, int enable) {
 int fmmbem_profile_get(fmmbem_handle* h, fmmbem_profile* out) {
     if (!h || !out) { fmmbem_set_error("NULL argument"); return FMMBEM_EINVAL; }
     FMM_CU(cudaStreamSynchronize(h->stream));
+    FMM_CU(cudaStreamSynchronize(h->istream));
+    prof_harvest(h);
     ProfState* s = prof_state(h);
     for (const auto& r : s->recs) {
         float ms = 0.f;

@@ -17,6 +17,17 @@ struct fmmbem_handle {
     cudaStream_t stream = nullptr;
     cudaStream_t stream2 = nullptr;  // near field runs here, concurrently with the far field
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    cudaStream_t istream = nullptr;  // internal stream of fmmbem_solve
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    // one captured mat-vec per order p (input xfix, output kw), instantiated on first use
+    bool use_graphs = true;
+    cudaGraphExec_t mv_graph[FMMBEM_P_MAX + 1] = {};
+    int mv_graph_mode[FMMBEM_P_MAX + 1] = {};
+    int64_t graph_launches[FMMBEM_P_MAX + 1] = {};
+    int capturing = -1;          // order p of the graph being captured, else -1
+    int pending_graph = -1;      // last replayed graph whose pass events await harvesting
+    cudaEvent_t gev[FMMBEM_P_MAX + 1][2 * FMMBEM_N_PASSES] = {};
+    int gev_launches[FMMBEM_P_MAX + 1][FMMBEM_N_PASSES] = {};  // precision * 16 + m2l mode + 4 * p2p variant at capture
     int64_t N = 0;   // panels
     int64_t NS = 0;  // Gauss points = K * N
 
@@ -104,6 +115,7 @@ struct fmmbem_handle {
     int kr_m = 0;
     double* V = nullptr;        // [(m+1) * n]
     double* kw = nullptr;       // [n]
+    double* xfix = nullptr;     // [n] input of the captured mat-vecs
     double* kb = nullptr;       // [n] sorted rhs
     double* kx = nullptr;       // [n] sorted solution
     double* kr = nullptr;       // [n] residual
@@ -146,4 +158,5 @@ int gmres_solve(fmmbem_handle* h, const double* b_sorted, double tol, int relax,
 int matvec_sorted(fmmbem_handle* h, int p, const double* xs, double* ys);
 void prof_begin(fmmbem_handle* h, int pass);
 void prof_end(fmmbem_handle* h, int pass, int launches);
+void prof_harvest(fmmbem_handle* h);
 }  // namespace fmmbem

@@ -70,9 +70,13 @@ __global__ void k_add_combo(double* x, const double* V, int64_t ldv, int nv, con
     }
 }
 
-__global__ void k_scale(double* dst, const double* src, double a, int64_t n) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        dst[i] = a * src[i];
+// dst = a src, and a second copy in dst2 (the fixed input buffer of the next mat-vec)
+__global__ void k_scale(double* dst, double* dst2, const double* src, double a, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double v = a * src[i];
+        dst[i] = v;
+        dst2[i] = v;
+    }
 }
 
 __global__ void k_sub(double* r, const double* b, const double* ax, int64_t n) {
@@ -123,8 +127,27 @@ int relaxed_p(double eta, double rho_prev, int p_initial, int p_min) {
     return relaxed_p_int(eta, rho_prev, p_initial, p_min);
 }
 
+static int gmres_solve_on(fmmbem_handle* h, const double* b, double tol, int relax, int p_initial, int p_min, double* x,
+                          int* iters, int* p_hist, double* res_hist, double* true_res);
+
+// The solve runs on the handle's internal stream (capturable, so the mat-vec graphs can
+// be recorded), ordered after the caller's stream on entry and before it on exit.
 int gmres_solve(fmmbem_handle* h, const double* b, double tol, int relax, int p_initial, int p_min, double* x,
                 int* iters, int* p_hist, double* res_hist, double* true_res) {
+    cudaStream_t user = h->stream;
+    FMM_CU(cudaEventRecord(h->ev_in, user));
+    FMM_CU(cudaStreamWaitEvent(h->istream, h->ev_in, 0));
+    h->stream = h->istream;
+    const int rc = gmres_solve_on(h, b, tol, relax, p_initial, p_min, x, iters, p_hist, res_hist, true_res);
+    h->stream = user;
+    if (rc < 0) return rc;
+    FMM_CU(cudaEventRecord(h->ev_out, h->istream));
+    FMM_CU(cudaStreamWaitEvent(user, h->ev_out, 0));
+    return rc;
+}
+
+static int gmres_solve_on(fmmbem_handle* h, const double* b, double tol, int relax, int p_initial, int p_min, double* x,
+                          int* iters, int* p_hist, double* res_hist, double* true_res) {
     const int64_t n = h->N * h->dof;
     const int m_max = h->kr_m;
     const int max_iter = h->opts.max_iter;
@@ -139,6 +162,7 @@ int gmres_solve(fmmbem_handle* h, const double* b, double tol, int relax, int p_
     FMM_TRY(kr.dots(b, 1, b, knr));
     FMM_CU(cudaMemcpyAsync(hb, knr, sizeof(double), cudaMemcpyDeviceToHost, st));
     FMM_CU(cudaStreamSynchronize(st));
+        prof_harvest(h);
     const double bnorm = sqrt(hb[0]);
     if (iters) *iters = 0;
     if (res_hist) res_hist[0] = 1.0;
@@ -158,7 +182,7 @@ int gmres_solve(fmmbem_handle* h, const double* b, double tol, int relax, int p_
     while (true) {
         const int m = std::min(m_max, max_iter - it);
         if (m <= 0) break;
-        k_scale<<<kr.gs, 256, 0, st>>>(h->V, h->kr, 1.0 / beta, n);
+        k_scale<<<kr.gs, 256, 0, st>>>(h->V, h->xfix, h->kr, 1.0 / beta, n);
         FMM_LAUNCHED();
         h->launches += 1;
         std::fill(H.begin(), H.end(), 0.0);
@@ -168,8 +192,8 @@ int gmres_solve(fmmbem_handle* h, const double* b, double tol, int relax, int p_
         bool stop = false;
         for (int k = 0; k < m; ++k) {
             const int p = relax ? relaxed_p_int(tol, rho, p_initial, p_min) : p_initial;
-            double* vk = h->V + (int64_t)k * n;
-            FMM_TRY(matvec_sorted(h, p, vk, h->kw));
+            // v_k is also in xfix, the fixed input of the per-order mat-vec graphs
+            FMM_TRY(matvec_sorted(h, p, h->xfix, h->kw));
             if (p_hist) p_hist[it] = p;
             ++it;
             prof_begin(h, FMMBEM_PASS_KRYLOV);
@@ -180,12 +204,13 @@ int gmres_solve(fmmbem_handle* h, const double* b, double tol, int relax, int p_
             FMM_TRY(kr.dots(h->kw, 1, h->kw, knr));
             FMM_CU(cudaMemcpyAsync(hb, h->kh, sizeof(double) * 3 * (m_max + 2), cudaMemcpyDeviceToHost, st));
             FMM_CU(cudaStreamSynchronize(st));
+        prof_harvest(h);
             for (int i = 0; i <= k; ++i) Hc(i, k) = hb[i] + hb[(m_max + 2) + i];
             const double hn = sqrt(hb[2 * (m_max + 2)]);
             Hc(k + 1, k) = hn;
             if (!std::isfinite(hn)) { status = FMMBEM_ENAN; stop = true; k_done = k; prof_end(h, FMMBEM_PASS_KRYLOV, 9); break; }
             if (hn > 0.0) {
-                k_scale<<<kr.gs, 256, 0, st>>>(h->V + (int64_t)(k + 1) * n, h->kw, 1.0 / hn, n);
+                k_scale<<<kr.gs, 256, 0, st>>>(h->V + (int64_t)(k + 1) * n, h->xfix, h->kw, 1.0 / hn, n);
                 FMM_LAUNCHED();
                 h->launches += 1;
             }
@@ -225,13 +250,15 @@ int gmres_solve(fmmbem_handle* h, const double* b, double tol, int relax, int p_
         }
         if (converged || it >= max_iter || stop) break;
         // restart: r = b - A x at p_initial
-        FMM_TRY(matvec_sorted(h, p_initial, x, h->kw));
+        FMM_CU(cudaMemcpyAsync(h->xfix, x, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+        FMM_TRY(matvec_sorted(h, p_initial, h->xfix, h->kw));
         k_sub<<<kr.gs, 256, 0, st>>>(h->kr, b, h->kw, n);
         FMM_LAUNCHED();
         h->launches += 1;
         FMM_TRY(kr.dots(h->kr, 1, h->kr, knr));
         FMM_CU(cudaMemcpyAsync(hb, knr, sizeof(double), cudaMemcpyDeviceToHost, st));
         FMM_CU(cudaStreamSynchronize(st));
+        prof_harvest(h);
         beta = sqrt(hb[0]);
         rho = beta / bnorm;
         if (res_hist) res_hist[it] = rho;
@@ -241,13 +268,15 @@ int gmres_solve(fmmbem_handle* h, const double* b, double tol, int relax, int p_
     if (iters) *iters = it;
     if (status < 0) return status;
     if (true_res) {
-        FMM_TRY(matvec_sorted(h, p_initial, x, h->kw));
+        FMM_CU(cudaMemcpyAsync(h->xfix, x, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+        FMM_TRY(matvec_sorted(h, p_initial, h->xfix, h->kw));
         k_sub<<<kr.gs, 256, 0, st>>>(h->kr, b, h->kw, n);
         FMM_LAUNCHED();
         h->launches += 1;
         FMM_TRY(kr.dots(h->kr, 1, h->kr, knr));
         FMM_CU(cudaMemcpyAsync(hb, knr, sizeof(double), cudaMemcpyDeviceToHost, st));
         FMM_CU(cudaStreamSynchronize(st));
+        prof_harvest(h);
         *true_res = sqrt(hb[0]) / bnorm;
     }
     return converged ? 0 : FMMBEM_NOT_CONVERGED;

@@ -392,29 +392,38 @@ __global__ void __launch_bounds__(128) k_p2p_lap(const int* leaves, const int2* 
 // slice walks whole P2P pairs (pair e goes to slice (e - e0) % S) and reads the Gauss
 // points straight through L1: all lanes of a slice read the same address, so every
 // load is a broadcast. No shared staging, no barriers inside the sums.
+__device__ __forceinline__ float lap_pair(float px, float py, float pz, float4 u) {
+    const float ux = px - u.x, uy = py - u.y, uz = pz - u.z;
+    return u.w * rsqrt_approx(fmaf(ux, ux, fmaf(uy, uy, uz * uz)));
+}
+
+// One pair's Gauss points for one target: loads are issued 8 at a time ahead of the
+// arithmetic (8 independent 128-bit requests in flight per thread), partial sums of
+// at most 64 sources are folded into the compensated accumulator.
 __device__ __forceinline__ void lap_run(const float4* __restrict__ srcw, int g0, int n, float shx, float shy,
                                         float shz, float tx, float ty, float tz, int skip0, int K, float& hi,
                                         float& lo) {
     const float px = tx - shx, py = ty - shy, pz = tz - shz;
+    const float4* p = srcw + g0;
     for (int qb = 0; qb < n; qb += 64) {
         const int qe = min(n, qb + 64);
         float pa = 0.f, pb = 0.f;
         int q = qb;
         if (skip0 < 0) {
-#pragma unroll 2
-            for (; q + 1 < qe; q += 2) {
-                const float4 u = __ldg(srcw + g0 + q), v = __ldg(srcw + g0 + q + 1);
-                const float ux = px - u.x, uy = py - u.y, uz = pz - u.z;
-                const float vx = px - v.x, vy = py - v.y, vz = pz - v.z;
-                pa = fmaf(u.w, rsqrt_approx(fmaf(ux, ux, fmaf(uy, uy, uz * uz))), pa);
-                pb = fmaf(v.w, rsqrt_approx(fmaf(vx, vx, fmaf(vy, vy, vz * vz))), pb);
+            for (; q + 7 < qe; q += 8) {
+                float4 u[8];
+#pragma unroll
+                for (int j = 0; j < 8; ++j) u[j] = __ldg(p + q + j);
+#pragma unroll
+                for (int j = 0; j < 8; j += 2) {
+                    pa += lap_pair(px, py, pz, u[j]);
+                    pb += lap_pair(px, py, pz, u[j + 1]);
+                }
             }
         }
         for (; q < qe; ++q) {
             if ((unsigned)(q - skip0) < (unsigned)K) continue;
-            const float4 u = __ldg(srcw + g0 + q);
-            const float ux = px - u.x, uy = py - u.y, uz = pz - u.z;
-            pa = fmaf(u.w, rsqrt_approx(fmaf(ux, ux, fmaf(uy, uy, uz * uz))), pa);
+            pa += lap_pair(px, py, pz, __ldg(p + q));
         }
         kahan_add(hi, lo, pa + pb);
     }
