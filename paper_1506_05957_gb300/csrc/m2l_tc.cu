@@ -91,10 +91,6 @@ __global__ void k_tc_tables(const double* Td, int ntab, int nr, int ld, int nch,
     }
 }
 
-// Two-stage pipeline: while the tensor core multiplies chunk c (stage c & 1), the
-// threads gather chunk c + 1 into the other stage and one thread bulk-copies its
-// operator chunk; each stage has a load barrier (bulk-copy bytes) and an MMA barrier
-// (tcgen05.commit). Use k of stage s is chunk 2k + s, so its barrier parity is k & 1.
 template <int NC>
 __global__ void __launch_bounds__(128) k_m2l_tc(int p, const int4* tiles, const int* pt, const int* ps,
                                                const float* tab, size_t tab_stride, int rows_max, const float* M,
@@ -103,17 +99,21 @@ __global__ void __launch_bounds__(128) k_m2l_tc(int p, const int4* tiles, const 
     const int R = 2 * ncoef(p);                // outputs = inputs
     const int Np = (R + 15) & ~15;             // MMA N (multiple of 16)
     const int nch = (R + TC_KC - 1) / TC_KC;   // K chunks
-    const int stage_floats = 2 * TC_ROWS * TC_KC + 2 * Np * TC_KC;
-    float* stg[2] = {reinterpret_cast<float*>(smem), reinterpret_cast<float*>(smem) + stage_floats};
-    uint64_t* bars = reinterpret_cast<uint64_t*>(stg[1] + stage_floats);  // load[2], mma[2]
-    uint32_t* taddr_slot = reinterpret_cast<uint32_t*>(bars + 4);
+    float* sX_hi = reinterpret_cast<float*>(smem);
+    float* sX_lo = sX_hi + TC_ROWS * TC_KC;
+    float* sT_hi = sX_lo + TC_ROWS * TC_KC;
+    float* sT_lo = sT_hi + Np * TC_KC;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(sT_lo + Np * TC_KC);
+    uint32_t* taddr_slot = reinterpret_cast<uint32_t*>(bars + 2);
+    const uint32_t mbar_load = smem_u32(&bars[0]), mbar_mma = smem_u32(&bars[1]);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int4 tile = tiles[blockIdx.x];
     const int nrows = tile.z * NC;
     const uint32_t tcols = Np <= 32 ? 32 : (Np <= 64 ? 64 : (Np <= 128 ? 128 : (Np <= 256 ? 256 : 512)));
 
     if (tid == 0) {
-        for (int i = 0; i < 4; ++i) asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&bars[i])), "r"(1));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mbar_load), "r"(1));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mbar_mma), "r"(1));
         asm volatile("fence.mbarrier_init.release.cluster;");
     }
     if (warp == 0) {
@@ -121,7 +121,11 @@ __global__ void __launch_bounds__(128) k_m2l_tc(int p, const int4* tiles, const 
                      "r"(tcols));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
-    // source expansion of each of this thread's 16 gather rows (row = tid/8 + 16 i)
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t taddr = *taddr_slot;
+    // source expansion of each of this thread's gather rows (row = tid/8 + 16 i), read once
     const float* rowsrc[8];
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
@@ -129,35 +133,28 @@ __global__ void __launch_bounds__(128) k_m2l_tc(int p, const int4* tiles, const 
         rowsrc[i] = nullptr;
         if (row < nrows) rowsrc[i] = M + ((size_t)ps[tile.y + row / NC] * NC + row % NC) * ESTRIDE + (tid & 7) * 4;
     }
-    asm volatile("tcgen05.fence::before_thread_sync;");
-    __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;");
-    const uint32_t taddr = *taddr_slot;
     const float* Tg = tab + (size_t)tile.x * tab_stride;
     const uint32_t chunk_bytes = (uint32_t)Np * TC_KC * 4;
-
-    auto issue_loads = [&](int c) {
-        float* sx_hi = stg[c & 1];
-        float* sx_lo = sx_hi + TC_ROWS * TC_KC;
-        float* st_hi = sx_lo + TC_ROWS * TC_KC;
-        float* st_lo = st_hi + Np * TC_KC;
+    bool ok = true;
+    for (int c = 0; c < nch && ok; ++c) {
+        // operator chunk (hi, lo) by bulk copy
         if (tid == 0) {
-            const uint32_t mb = smem_u32(&bars[c & 1]);
-            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mb), "r"(2 * chunk_bytes)
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar_load), "r"(2 * chunk_bytes)
                          : "memory");
             const float* src = Tg + (size_t)c * 2 * rows_max * TC_KC;
             asm volatile(
                 "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                    smem_u32(st_hi)),
-                "l"(src), "r"(chunk_bytes), "r"(mb)
+                    smem_u32(sT_hi)),
+                "l"(src), "r"(chunk_bytes), "r"(mbar_load)
                 : "memory");
             asm volatile(
                 "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                    smem_u32(st_lo)),
-                "l"(src + (size_t)rows_max * TC_KC), "r"(chunk_bytes), "r"(mb)
+                    smem_u32(sT_lo)),
+                "l"(src + (size_t)rows_max * TC_KC), "r"(chunk_bytes), "r"(mbar_load)
                 : "memory");
         }
-        const int k0 = c * TC_KC + (tid & 7) * 4;
+        // gathered source expansions, split into TF32 hi/lo (8 independent loads per thread)
+        const int kq = (tid & 7) * 4, k = c * TC_KC + kq;
         float4 v[8];
 #pragma unroll
         for (int i = 0; i < 8; ++i)
@@ -165,29 +162,21 @@ __global__ void __launch_bounds__(128) k_m2l_tc(int p, const int4* tiles, const 
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
             const int row = (tid >> 3) + 16 * i;
-            if (k0 + 0 >= R) v[i].x = 0.f;
-            if (k0 + 1 >= R) v[i].y = 0.f;
-            if (k0 + 2 >= R) v[i].z = 0.f;
-            if (k0 + 3 >= R) v[i].w = 0.f;
+            if (k + 0 >= R) v[i].x = 0.f;
+            if (k + 1 >= R) v[i].y = 0.f;
+            if (k + 2 >= R) v[i].z = 0.f;
+            if (k + 3 >= R) v[i].w = 0.f;
             const float4 hi = make_float4(tf32_hi(v[i].x), tf32_hi(v[i].y), tf32_hi(v[i].z), tf32_hi(v[i].w));
             const float4 lo = make_float4(v[i].x - hi.x, v[i].y - hi.y, v[i].z - hi.z, v[i].w - hi.w);
-            *reinterpret_cast<float4*>(sx_hi + cm_index(row, (tid & 7) * 4)) = hi;
-            *reinterpret_cast<float4*>(sx_lo + cm_index(row, (tid & 7) * 4)) = lo;
+            *reinterpret_cast<float4*>(sX_hi + cm_index(row, kq)) = hi;
+            *reinterpret_cast<float4*>(sX_lo + cm_index(row, kq)) = lo;
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    };
-
-    bool ok = true;
-    issue_loads(0);
-    for (int c = 0; c < nch; ++c) {
-        const int s = c & 1;
-        const uint32_t par = (uint32_t)((c >> 1) & 1);
-        if (ok && !mbar_wait(smem_u32(&bars[s]), par)) { atomicExch(err, 1); ok = false; }
-        __syncthreads();  // every thread's gathered rows of chunk c are in place
+        if (!mbar_wait(mbar_load, c & 1)) { atomicExch(err, 1); ok = false; }
+        __syncthreads();
         asm volatile("tcgen05.fence::after_thread_sync;");
         if (tid == 0 && ok) {
-            const uint32_t xh = smem_u32(stg[s]), xl = xh + TC_ROWS * TC_KC * 4;
-            const uint32_t th = xl + TC_ROWS * TC_KC * 4, tl = th + (uint32_t)Np * TC_KC * 4;
+            const uint32_t xh = smem_u32(sX_hi), xl = smem_u32(sX_lo), th = smem_u32(sT_hi), tl = smem_u32(sT_lo);
             const int n1 = Np <= 256 ? Np : 256;
             const uint32_t id1 = idesc_tf32(TC_ROWS, n1);
             const uint32_t id2 = Np > 256 ? idesc_tf32(TC_ROWS, Np - 256) : 0u;
@@ -207,26 +196,13 @@ __global__ void __launch_bounds__(128) k_m2l_tc(int p, const int4* tiles, const 
                     mma_tf32(taddr + 256, a_lo, b2_hi, id2, 1u);
                 }
             }
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                             smem_u32(&bars[2 + s]))
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar_mma)
                          : "memory");
         }
-        if (c + 1 < nch) {
-            // the other stage was read by the MMAs of chunk c - 1
-            if (c >= 1 && ok && !mbar_wait(smem_u32(&bars[2 + (s ^ 1)]), (uint32_t)(((c - 1) >> 1) & 1))) {
-                atomicExch(err, 2);
-                ok = false;
-            }
-            if (ok) issue_loads(c + 1);
-        }
+        if (ok && !mbar_wait(mbar_mma, c & 1)) { atomicExch(err, 2); ok = false; }
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        __syncthreads();
     }
-    // the last commit covers every MMA issued before it
-    if (ok && !mbar_wait(smem_u32(&bars[2 + ((nch - 1) & 1)]), (uint32_t)(((nch - 1) >> 1) & 1))) {
-        atomicExch(err, 3);
-        ok = false;
-    }
-    asm volatile("tcgen05.fence::after_thread_sync;");
-    __syncthreads();
     if (ok) {
         const int row = 32 * warp + lane;
         float* dst = nullptr;
@@ -259,7 +235,7 @@ __global__ void __launch_bounds__(128) k_m2l_tc(int p, const int4* tiles, const 
 size_t m2l_tc_smem(int p) {
     const int R = 2 * ncoef(p);
     const int Np = (R + 15) & ~15;
-    return 2 * (size_t)(2 * TC_ROWS * TC_KC + 2 * Np * TC_KC) * sizeof(float) + 64;
+    return (size_t)(2 * TC_ROWS * TC_KC + 2 * Np * TC_KC) * sizeof(float) + 64;
 }
 
 int build_m2l_tc(fmmbem_handle* h) {

@@ -420,6 +420,13 @@ __device__ __forceinline__ void lap_run(const float4* __restrict__ srcw, int g0,
                     pb += lap_pair(px, py, pz, u[j + 1]);
                 }
             }
+            for (; q + 1 < qe; q += 2) {
+                const float4 u = __ldg(p + q), v = __ldg(p + q + 1);
+                pa += lap_pair(px, py, pz, u);
+                pb += lap_pair(px, py, pz, v);
+            }
+            if (q < qe) pa += lap_pair(px, py, pz, __ldg(p + q));
+            q = qe;
         }
         for (; q < qe; ++q) {
             if ((unsigned)(q - skip0) < (unsigned)K) continue;
