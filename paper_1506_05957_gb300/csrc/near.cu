@@ -475,6 +475,145 @@ __global__ void __launch_bounds__(128) k_p2p_lap_sliced(const int* leaves, const
     }
 }
 
+// Bulk-copy variant: the Gauss points of each P2P pair are one contiguous range, so a
+// stage of up to BK_TILE sources is filled by one cp.async.bulk per pair (issued by
+// thread 0, completing on the stage's mbarrier) while the block computes the other
+// stage. Within a stage, pair j goes to slice j % S; every thread of a slice reads the
+// same shared-memory source (broadcast). Thread = (target, slice) as in the sliced
+// variant.
+constexpr int BK_TILE = 1024;
+constexpr int BK_MAXP = 64;  // pairs per stage
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ bool bk_wait(uint32_t mbar, uint32_t parity) {
+    for (uint32_t it = 0; it < (1u << 24); ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred q;\n\tmbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2;\n\tselp.u32 %0, 1, 0, q;\n\t}\n"
+            : "=r"(done)
+            : "r"(mbar), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+__global__ void __launch_bounds__(128) k_p2p_lap_bulk(const int* leaves, const int2* range, const int* pptr,
+                                                      const int* psrc, const float4* prec, const float4* srcw,
+                                                      const float4* tgt, int K, const int* cptr, const int* ccol,
+                                                      const double* cval, const double* xs, double* ynear,
+                                                      int* err) {
+    __shared__ __align__(128) float4 sS[2][BK_TILE];
+    __shared__ float4 sRec[2][BK_MAXP];   // shift (x,y,z), offset in the stage (int bits)
+    __shared__ int sCnt[2][BK_MAXP];
+    __shared__ int sG0[2][BK_MAXP];       // first Gauss point of the pair
+    __shared__ int sSelf[2][BK_MAXP];     // 1 if the pair is the target leaf itself
+    __shared__ int sNp[2], sEnd[2];
+    __shared__ __align__(8) uint64_t bar[2];
+    __shared__ double sred[128];
+    const int cell = leaves[blockIdx.x];
+    const int2 r = range[cell];
+    const int e0 = pptr[cell], e1 = pptr[cell + 1];
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        for (int i = 0; i < 2; ++i) asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(&bar[i])), "r"(1));
+        asm volatile("fence.mbarrier_init.release.cluster;");
+    }
+    __syncthreads();
+    int uses[2] = {0, 0};
+    bool ok = true;
+    // thread 0: plan stage st from pair e (whole pairs, at most BK_TILE sources and
+    // BK_MAXP pairs), announce the bytes on the stage barrier, then issue the copies
+    auto issue = [&](int st, int e) {
+        int np = 0, fill = 0;
+        while (e < e1 && np < BK_MAXP) {
+            const int sc = psrc[e];
+            const int2 sr = range[sc];
+            const int cnt = K * (sr.y - sr.x);
+            if (fill + cnt > BK_TILE) break;
+            const float4 rc = prec[e];
+            sRec[st][np] = make_float4(rc.x, rc.y, rc.z, __int_as_float(fill));
+            sCnt[st][np] = cnt;
+            sG0[st][np] = __float_as_int(rc.w);
+            sSelf[st][np] = (sc == cell);
+            fill += cnt;
+            ++np;
+            ++e;
+        }
+        sNp[st] = np;
+        sEnd[st] = e;
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(&bar[st])),
+                     "r"((uint32_t)fill * 16u)
+                     : "memory");
+        for (int j = 0; j < np; ++j)
+            asm volatile(
+                "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                    smem_addr(&sS[st][__float_as_int(sRec[st][j].w)])),
+                "l"(srcw + sG0[st][j]), "r"((uint32_t)sCnt[st][j] * 16u), "r"(smem_addr(&bar[st]))
+                : "memory");
+    };
+    for (int tb = r.x; tb < r.y; tb += 128) {
+        const int nt = min(128, r.y - tb);
+        const int S = 128 / nt;
+        const int t = tid % nt, slice = tid / nt;
+        const bool active = slice < S;
+        float tx = 0.f, ty = 0.f, tz = 0.f;
+        if (active) {
+            const float4 x = tgt[tb + t];
+            tx = x.x; ty = x.y; tz = x.z;
+        }
+        float hi = 0.f, lo = 0.f;
+        if (tid == 0) issue(0, e0);
+        __syncthreads();
+        int st = 0;
+        while (true) {
+            const int eend = sEnd[st];
+            if (tid == 0 && eend < e1) issue(st ^ 1, eend);  // the other buffer was released by the last barrier
+            if (ok && !bk_wait(smem_addr(&bar[st]), (uint32_t)(uses[st] & 1))) { atomicExch(err, 4); ok = false; }
+            uses[st]++;
+            if (active && ok) {
+                const int np = sNp[st];
+                for (int j = slice; j < np; j += S) {
+                    const float4 rc = sRec[st][j];
+                    const int cnt = sCnt[st][j];
+                    const float px = tx - rc.x, py = ty - rc.y, pz = tz - rc.z;
+                    const float4* sp = &sS[st][__float_as_int(rc.w)];
+                    const int skip = sSelf[st][j] ? (tb + t) * K - sG0[st][j] : -(1 << 30);
+                    for (int qb = 0; qb < cnt; qb += 64) {
+                        const int qe = min(cnt, qb + 64);
+                        float pa = 0.f, pb = 0.f;
+                        int q = qb;
+                        if (skip < 0) {
+                            for (; q + 1 < qe; q += 2) {
+                                pa += lap_pair(px, py, pz, sp[q]);
+                                pb += lap_pair(px, py, pz, sp[q + 1]);
+                            }
+                        }
+                        for (; q < qe; ++q) {
+                            if ((unsigned)(q - skip) < (unsigned)K) continue;
+                            pa += lap_pair(px, py, pz, sp[q]);
+                        }
+                        kahan_add(hi, lo, pa + pb);
+                    }
+                }
+            }
+            __syncthreads();
+            if (eend >= e1) break;
+            st ^= 1;
+        }
+        sred[tid] = active ? (double)hi - (double)lo : 0.0;
+        __syncthreads();
+        if (slice == 0) {
+            double out = 0.0;
+            for (int sl = 0; sl < S; ++sl) out += sred[sl * nt + t];
+            add_correction<1>(tb + t, cptr, ccol, cval, xs, &out);
+            ynear[tb + t] = out;
+        }
+        __syncthreads();
+    }
+}
+
 // Direct: one thread per target, every Gauss point staged through shared memory.
 template <typename T, int OP>
 __global__ void __launch_bounds__(P2P_THREADS) k_direct(int n, int ns, const typename V4<T>::type* src,
@@ -560,6 +699,16 @@ int near_field_on(fmmbem_handle* h, bool fp64) {
     if (h->kernel == FMMBEM_LAPLACE && !fp64) {
         k_pack_sources<<<(unsigned)((h->NS + 255) / 256), 256, 0, h->stream>>>(h->src_rel, h->xin, h->K, h->NS, h->src_w);
         FMM_LAUNCHED();
+        if (h->p2p_variant == 2 && (int64_t)h->K * h->max_leaf_panels <= BK_TILE) {
+            k_p2p_lap_bulk<<<h->n_leaves, 128, 0, h->stream>>>(h->leaves, h->cell_range, h->p2p_ptr, h->p2p_src,
+                                                              h->p2p_rec, h->src_w, h->tgt_rel, h->K, h->corr_ptr,
+                                                              h->corr_col, h->corr_sl, h->xin, h->ynear, h->kerr);
+            FMM_LAUNCHED();
+            h->launches += 1;
+            prof_end(h, FMMBEM_PASS_P2P, 2);
+            h->launches += 1;
+            return 0;
+        }
         if (h->p2p_variant == 1) {
             k_p2p_lap_sliced<<<h->n_leaves, 128, 0, h->stream>>>(h->leaves, h->cell_range, h->p2p_ptr, h->p2p_src,
                                                                 h->p2p_rec, h->src_w, h->tgt_rel, h->K, h->corr_ptr,
