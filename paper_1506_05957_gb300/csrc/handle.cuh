@@ -88,6 +88,12 @@ struct fmmbem_handle {
     float4* p2p_rec = nullptr;  // [n_p2p] FP32 shift c_source - c_target (x,y,z) and first Gauss point (int bits)
     int* p2p_off = nullptr;     // [n_p2p] offset of the pair in its target leaf's source stream (self pair: empty)
     int* p2p_len = nullptr;     // [n_cells] length of each target leaf's source stream
+    int* p2p_cnt = nullptr;     // [n_p2p] Gauss points of the source leaf
+    int* p2p_toff = nullptr;    // [n_p2p] offset of the pair in its shared-memory stage
+    int* stage_ptr = nullptr;   // [n_cells + 1] stages of each target leaf (bulk-copy P2P)
+    int* stage_first = nullptr; // first pair of each stage
+    int* stage_bytes = nullptr; // bytes of each stage
+    int64_t n_stages = 0;
     int max_leaf_panels = 0;
     int p2p_variant = 1;        // 0: shared-memory stream tiles, 1: sliced L1 broadcast
 

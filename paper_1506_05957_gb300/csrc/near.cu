@@ -499,58 +499,43 @@ __device__ __forceinline__ bool bk_wait(uint32_t mbar, uint32_t parity) {
     return false;
 }
 
-__global__ void __launch_bounds__(128) k_p2p_lap_bulk(const int* leaves, const int2* range, const int* pptr,
-                                                      const int* psrc, const float4* prec, const float4* srcw,
-                                                      const float4* tgt, int K, const int* cptr, const int* ccol,
-                                                      const double* cval, const double* xs, double* ynear,
-                                                      int* err) {
+// Stage plans are static (create time): stage k of a target leaf covers pairs
+// [first_k, first_{k+1}) with at most BK_TILE Gauss points; pair e sits at offset
+// toff[e] of its stage and holds cnt[e] points. Warp 0 arms the stage barrier with the
+// stage's byte count, then its lanes issue one bulk copy per pair in parallel.
+__global__ void __launch_bounds__(128, 8) k_p2p_lap_bulk(const int* leaves, const int2* range, const int* pptr,
+                                                      const int* psrc, const float4* prec, const int* pcnt,
+                                                      const int* ptoff, const int* sptr, const int* sfirst,
+                                                      const int* sbytes, const float4* srcw, const float4* tgt, int K,
+                                                      const int* cptr, const int* ccol, const double* cval,
+                                                      const double* xs, double* ynear, int* err) {
     __shared__ __align__(128) float4 sS[2][BK_TILE];
-    __shared__ float4 sRec[2][BK_MAXP];   // shift (x,y,z), offset in the stage (int bits)
-    __shared__ int sCnt[2][BK_MAXP];
-    __shared__ int sG0[2][BK_MAXP];       // first Gauss point of the pair
-    __shared__ int sSelf[2][BK_MAXP];     // 1 if the pair is the target leaf itself
-    __shared__ int sNp[2], sEnd[2];
     __shared__ __align__(8) uint64_t bar[2];
     __shared__ double sred[128];
     const int cell = leaves[blockIdx.x];
     const int2 r = range[cell];
-    const int e0 = pptr[cell], e1 = pptr[cell + 1];
-    const int tid = threadIdx.x;
+    const int e1 = pptr[cell + 1];
+    const int s0 = sptr[cell], s1 = sptr[cell + 1];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (tid == 0) {
         for (int i = 0; i < 2; ++i) asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(&bar[i])), "r"(1));
         asm volatile("fence.mbarrier_init.release.cluster;");
     }
     __syncthreads();
-    int uses[2] = {0, 0};
+    int use0 = 0, use1 = 0;  // completed phases of each stage barrier
     bool ok = true;
-    // thread 0: plan stage st from pair e (whole pairs, at most BK_TILE sources and
-    // BK_MAXP pairs), announce the bytes on the stage barrier, then issue the copies
-    auto issue = [&](int st, int e) {
-        int np = 0, fill = 0;
-        while (e < e1 && np < BK_MAXP) {
-            const int sc = psrc[e];
-            const int2 sr = range[sc];
-            const int cnt = K * (sr.y - sr.x);
-            if (fill + cnt > BK_TILE) break;
-            const float4 rc = prec[e];
-            sRec[st][np] = make_float4(rc.x, rc.y, rc.z, __int_as_float(fill));
-            sCnt[st][np] = cnt;
-            sG0[st][np] = __float_as_int(rc.w);
-            sSelf[st][np] = (sc == cell);
-            fill += cnt;
-            ++np;
-            ++e;
-        }
-        sNp[st] = np;
-        sEnd[st] = e;
-        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(&bar[st])),
-                     "r"((uint32_t)fill * 16u)
-                     : "memory");
-        for (int j = 0; j < np; ++j)
+    auto issue = [&](int k, int buf) {  // executed by warp 0
+        const int fa = sfirst[k], fb = (k + 1 < s1) ? sfirst[k + 1] : e1;
+        if (lane == 0)
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(&bar[buf])),
+                         "r"((uint32_t)sbytes[k])
+                         : "memory");
+        __syncwarp();
+        for (int e = fa + lane; e < fb; e += 32)
             asm volatile(
                 "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                    smem_addr(&sS[st][__float_as_int(sRec[st][j].w)])),
-                "l"(srcw + sG0[st][j]), "r"((uint32_t)sCnt[st][j] * 16u), "r"(smem_addr(&bar[st]))
+                    smem_addr(&sS[buf][ptoff[e]])),
+                "l"(srcw + __float_as_int(prec[e].w)), "r"((uint32_t)pcnt[e] * 16u), "r"(smem_addr(&bar[buf]))
                 : "memory");
     };
     for (int tb = r.x; tb < r.y; tb += 128) {
@@ -564,22 +549,21 @@ __global__ void __launch_bounds__(128) k_p2p_lap_bulk(const int* leaves, const i
             tx = x.x; ty = x.y; tz = x.z;
         }
         float hi = 0.f, lo = 0.f;
-        if (tid == 0) issue(0, e0);
-        __syncthreads();
-        int st = 0;
-        while (true) {
-            const int eend = sEnd[st];
-            if (tid == 0 && eend < e1) issue(st ^ 1, eend);  // the other buffer was released by the last barrier
-            if (ok && !bk_wait(smem_addr(&bar[st]), (uint32_t)(uses[st] & 1))) { atomicExch(err, 4); ok = false; }
-            uses[st]++;
+        if (warp == 0 && s0 < s1) issue(s0, 0);
+        for (int k = s0; k < s1; ++k) {
+            const int buf = (k - s0) & 1;
+            if (warp == 0 && k + 1 < s1) issue(k + 1, buf ^ 1);  // released by the previous barrier
+            const uint32_t par = (uint32_t)((buf ? use1 : use0) & 1);
+            if (ok && !bk_wait(smem_addr(&bar[buf]), par)) { atomicExch(err, 4); ok = false; }
+            if (buf) ++use1; else ++use0;
             if (active && ok) {
-                const int np = sNp[st];
-                for (int j = slice; j < np; j += S) {
-                    const float4 rc = sRec[st][j];
-                    const int cnt = sCnt[st][j];
+                const int fa = sfirst[k], fb = (k + 1 < s1) ? sfirst[k + 1] : e1;
+                for (int e = fa + slice; e < fb; e += S) {
+                    const float4 rc = prec[e];
+                    const int cnt = pcnt[e];
                     const float px = tx - rc.x, py = ty - rc.y, pz = tz - rc.z;
-                    const float4* sp = &sS[st][__float_as_int(rc.w)];
-                    const int skip = sSelf[st][j] ? (tb + t) * K - sG0[st][j] : -(1 << 30);
+                    const float4* sp = &sS[buf][ptoff[e]];
+                    const int skip = (psrc[e] == cell) ? (tb + t) * K - __float_as_int(rc.w) : -(1 << 30);
                     for (int qb = 0; qb < cnt; qb += 64) {
                         const int qe = min(cnt, qb + 64);
                         float pa = 0.f, pb = 0.f;
@@ -599,8 +583,6 @@ __global__ void __launch_bounds__(128) k_p2p_lap_bulk(const int* leaves, const i
                 }
             }
             __syncthreads();
-            if (eend >= e1) break;
-            st ^= 1;
         }
         sred[tid] = active ? (double)hi - (double)lo : 0.0;
         __syncthreads();
@@ -699,10 +681,11 @@ int near_field_on(fmmbem_handle* h, bool fp64) {
     if (h->kernel == FMMBEM_LAPLACE && !fp64) {
         k_pack_sources<<<(unsigned)((h->NS + 255) / 256), 256, 0, h->stream>>>(h->src_rel, h->xin, h->K, h->NS, h->src_w);
         FMM_LAUNCHED();
-        if (h->p2p_variant == 2 && (int64_t)h->K * h->max_leaf_panels <= BK_TILE) {
-            k_p2p_lap_bulk<<<h->n_leaves, 128, 0, h->stream>>>(h->leaves, h->cell_range, h->p2p_ptr, h->p2p_src,
-                                                              h->p2p_rec, h->src_w, h->tgt_rel, h->K, h->corr_ptr,
-                                                              h->corr_col, h->corr_sl, h->xin, h->ynear, h->kerr);
+        if (h->p2p_variant == 2 && h->stage_ptr) {
+            k_p2p_lap_bulk<<<h->n_leaves, 128, 0, h->stream>>>(
+                h->leaves, h->cell_range, h->p2p_ptr, h->p2p_src, h->p2p_rec, h->p2p_cnt, h->p2p_toff, h->stage_ptr,
+                h->stage_first, h->stage_bytes, h->src_w, h->tgt_rel, h->K, h->corr_ptr, h->corr_col, h->corr_sl,
+                h->xin, h->ynear, h->kerr);
             FMM_LAUNCHED();
             h->launches += 1;
             prof_end(h, FMMBEM_PASS_P2P, 2);

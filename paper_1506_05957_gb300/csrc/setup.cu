@@ -384,6 +384,32 @@ __global__ void k_p2p_records(const int* pptr, const int* psrc, const double4* c
     len[c] = acc;
 }
 
+// Static stage plans of the bulk-copy near field: whole pairs, at most `tile` Gauss
+// points per stage, in list order. COUNT pass counts stages; FILL pass writes them.
+template <bool FILL>
+__global__ void k_p2p_plan(const int* pptr, const int* psrc, const int2* range, int ncells, int K, int tile,
+                           int* nst, const int* sptr, int* cnt, int* toff, int* sfirst, int* sbytes) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ncells) return;
+    int ns = 0, fill = 0, out = FILL ? sptr[c] : 0;
+    for (int e = pptr[c]; e < pptr[c + 1]; ++e) {
+        const int2 r = range[psrc[e]];
+        const int n = K * (r.y - r.x);
+        if (ns == 0 || fill + n > tile) {
+            if (FILL) {
+                if (ns > 0) sbytes[out + ns - 1] = fill * 16;
+                sfirst[out + ns] = e;
+            }
+            ++ns;
+            fill = 0;
+        }
+        if (FILL) { cnt[e] = n; toff[e] = fill; }
+        fill += n;
+    }
+    if (FILL && ns > 0) sbytes[out + ns - 1] = fill * 16;
+    if (!FILL) nst[c] = ns;
+}
+
 __global__ void k_leaf_class_key(const int* leaves, const int2* range, int n, int* key, int* counts) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -882,6 +908,35 @@ int build_geometry_tree_lists(fmmbem_handle* h, const fmmbem_mesh* mesh) {
         k_p2p_records<<<(nc + T - 1) / T, T, 0, st>>>(h->p2p_ptr, h->p2p_src, h->cell_cs, h->cell_range, nc, K,
                                                      h->p2p_rec, h->p2p_off, h->p2p_len);
         FMM_LAUNCHED();
+        // stage plans of the bulk-copy near field (leaves of at most 1024 Gauss points)
+        if ((int64_t)K * h->max_leaf_panels <= 1024) {
+            int* nst = nullptr;
+            FMM_TRY(dalloc(&nst, nc + 1));
+            FMM_CU(cudaMemsetAsync(nst, 0, sizeof(int) * (nc + 1), st));
+            k_p2p_plan<false><<<(nc + T - 1) / T, T, 0, st>>>(h->p2p_ptr, h->p2p_src, h->cell_range, nc, K, 1024, nst,
+                                                            nullptr, nullptr, nullptr, nullptr, nullptr);
+            FMM_LAUNCHED();
+            FMM_TRY(dalloc(&h->stage_ptr, nc + 1));
+            size_t tb3 = 0;
+            FMM_CU(cub::DeviceScan::ExclusiveSum(nullptr, tb3, nst, h->stage_ptr, nc + 1, st));
+            void* tmp3 = nullptr;
+            FMM_CU(cudaMalloc(&tmp3, tb3 ? tb3 : 1));
+            FMM_CU(cub::DeviceScan::ExclusiveSum(tmp3, tb3, nst, h->stage_ptr, nc + 1, st));
+            int nstages = 0;
+            FMM_CU(cudaMemcpyAsync(&nstages, h->stage_ptr + nc, sizeof(int), cudaMemcpyDeviceToHost, st));
+            FMM_CU(cudaStreamSynchronize(st));
+            cudaFree(tmp3);
+            cudaFree(nst);
+            h->n_stages = nstages;
+            FMM_TRY(dalloc(&h->stage_first, nstages));
+            FMM_TRY(dalloc(&h->stage_bytes, nstages));
+            FMM_TRY(dalloc(&h->p2p_cnt, h->n_p2p));
+            FMM_TRY(dalloc(&h->p2p_toff, h->n_p2p));
+            k_p2p_plan<true><<<(nc + T - 1) / T, T, 0, st>>>(h->p2p_ptr, h->p2p_src, h->cell_range, nc, K, 1024, nullptr,
+                                                           h->stage_ptr, h->p2p_cnt, h->p2p_toff, h->stage_first,
+                                                           h->stage_bytes);
+            FMM_LAUNCHED();
+        }
     }
 
     // ---- near-singular table
