@@ -131,9 +131,9 @@ int fmmbem_set_m2l_mode(fmmbem_handle* h, int mode);
 
 /* Near-field kernel of FMMBEM_MIXED Laplace mat-vecs (same sums, different schedules):
  * 0 = source tiles staged in shared memory, targets held per lane;
- * 1 = (target, source slice) per thread, sources read through L1 (default);
+ * 1 = (target, source slice) per thread, sources read through L1;
  * 2 = as 1, with each pair's sources bulk-copied into double-buffered shared memory
- *     (used when a leaf holds at most 1024 Gauss points, else 1). */
+ *     (default; used when a leaf holds at most 1024 Gauss points, else 1). */
 int fmmbem_set_p2p_variant(fmmbem_handle* h, int variant);
 
 /*

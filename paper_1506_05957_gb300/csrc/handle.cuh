@@ -66,6 +66,9 @@ struct fmmbem_handle {
     bool m2l_tables = false;
     int* m2l_pt = nullptr;        // [n_m2l] target cell of each pair, grouped by operator
     int* m2l_ps = nullptr;        // [n_m2l] source cell
+    int* m2l_refl = nullptr;      // [n_m2l] axis reflection mapping the pair's offset to its stored operator
+    float* sign_f = nullptr;      // [8][ESTRIDE] coefficient signs of each reflection
+    double* sign_d = nullptr;
     int4* m2l_tiles = nullptr;    // (operator, first pair, pair count, -)
     int n_tables = 0, n_tiles = 0, tab_ld = 0;
     size_t tab_stride = 0;
@@ -95,7 +98,7 @@ struct fmmbem_handle {
     int* stage_bytes = nullptr; // bytes of each stage
     int64_t n_stages = 0;
     int max_leaf_panels = 0;
-    int p2p_variant = 1;        // 0: shared-memory stream tiles, 1: sliced L1 broadcast
+    int p2p_variant = 2;        // 0: shared stream tiles, 1: sliced L1 broadcast, 2: bulk-copied stages
 
     // near-singular / self corrections (CSR by sorted target panel), FP64
     int* corr_ptr = nullptr;   // [N + 1]

@@ -10,6 +10,11 @@
 // matrix acting on the interleaved (Re, Im) coefficients, ordered by degree so that the
 // leading 2 ncoef(p) x 2 ncoef(p) block is the order-p operator for every p <= p_max.
 // The pairs of one operator form a GEMM: L[t_i] += T X[s_i] over the pairs i of the group.
+// Reflections of the coordinate axes map solid harmonics to themselves up to signs and
+// conjugation (z -> -z: (-1)^{n+m}; y -> -y: conj; x -> -x: (-1)^m conj), so in real
+// form T_v = D_Q T_{Qv} D_Q with D_Q diagonal +-1. Operators are stored only for
+// v with non-negative components; each pair carries the reflection Q (3 bits) that maps
+// its v there, and the products apply D_Q to the gathered input and to the output.
 #include <cub/cub.cuh>
 #include <algorithm>
 #include <type_traits>
@@ -49,18 +54,23 @@ __global__ void k_expand_pairs(const int* ptr, const int* src, int ncells, int* 
 }
 
 __global__ void k_pair_keys(const int* pt, const int* ps, long long n, const double4* cs, const int* lev,
-                            unsigned long long* key, int* idx, int* bad) {
+                            unsigned long long* key, int* idx, int* refl, int* bad) {
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int t = pt[i], s = ps[i];
     const double4 ct = cs[t], cv = cs[s];
     const int dl = lev[t] - lev[s];
     const double is = 16.0 / ct.w;
-    const long long kx = llrint((ct.x - cv.x) * is), ky = llrint((ct.y - cv.y) * is), kz = llrint((ct.z - cv.z) * is);
-    if (dl < -3 || dl > 3 || llabs(kx) >= KEY_BIAS || llabs(ky) >= KEY_BIAS || llabs(kz) >= KEY_BIAS) atomicExch(bad, 1);
+    long long kx = llrint((ct.x - cv.x) * is), ky = llrint((ct.y - cv.y) * is), kz = llrint((ct.z - cv.z) * is);
+    const int q = (kx < 0 ? 1 : 0) | (ky < 0 ? 2 : 0) | (kz < 0 ? 4 : 0);  // reflection to the canonical octant
+    kx = llabs(kx);
+    ky = llabs(ky);
+    kz = llabs(kz);
+    if (dl < -3 || dl > 3 || kx >= KEY_BIAS || ky >= KEY_BIAS || kz >= KEY_BIAS) atomicExch(bad, 1);
     key[i] = ((unsigned long long)(dl + 8) << (3 * KEY_BITS)) | ((unsigned long long)(kx + KEY_BIAS) << (2 * KEY_BITS)) |
              ((unsigned long long)(ky + KEY_BIAS) << KEY_BITS) | (unsigned long long)(kz + KEY_BIAS);
     idx[i] = (int)i;
+    refl[i] = q;
 }
 
 __global__ void k_mark_heads(const unsigned long long* key, long long n, int* head) {
@@ -72,7 +82,7 @@ __global__ void k_mark_heads(const unsigned long long* key, long long n, int* he
 // After an inclusive scan of the head flags: table id of each sorted pair, the
 // permuted pair arrays, and the first pair / key of each table.
 __global__ void k_assign_tables(const unsigned long long* key, const int* idx, const int* scan, long long n,
-                                const int* pt, const int* ps, int* st, int* ss, int* tab_first,
+                                const int* pt, const int* ps, const int* refl, int* st, int* ss, int* sr, int* tab_first,
                                 unsigned long long* tab_key) {
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i > n) return;
@@ -80,6 +90,7 @@ __global__ void k_assign_tables(const unsigned long long* key, const int* idx, c
     const int id = scan[i] - 1;
     st[i] = pt[idx[i]];
     ss[i] = ps[idx[i]];
+    sr[i] = refl[idx[i]];
     if (i == 0 || key[i] != key[i - 1]) { tab_first[id] = (int)i; tab_key[id] = key[i]; }
 }
 
@@ -142,6 +153,30 @@ __global__ void k_gen_tables(const unsigned long long* tab_key, int pmax, int ld
     }
 }
 
+// sign[q][k] of real coefficient k = 2 cidx(n, m) + part under reflection q (bit 0: x,
+// bit 1: y, bit 2: z): z -> (-1)^{n+m}; y -> conj (Im negated); x -> (-1)^m conj.
+__global__ void k_refl_signs(float* sf, double* sd) {
+    const int q = blockIdx.x;
+    for (int k = threadIdx.x; k < ESTRIDE; k += blockDim.x) {
+        double v = 0.0;
+        if (k < 2 * NCOEF_MAX) {
+            const int c = k >> 1, part = k & 1;
+            int n = 0;
+            while ((n + 1) * (n + 2) / 2 <= c) ++n;
+            const int m = c - n * (n + 1) / 2;
+            v = 1.0;
+            if (q & 4) v *= ((n + m) & 1) ? -1.0 : 1.0;
+            if ((q & 2) && part) v = -v;
+            if (q & 1) {
+                if (m & 1) v = -v;
+                if (part) v = -v;
+            }
+        }
+        sf[q * ESTRIDE + k] = (float)v;
+        sd[q * ESTRIDE + k] = v;
+    }
+}
+
 template <typename T> struct Vec4;
 template <> struct Vec4<float> { typedef float4 type; };
 template <> struct Vec4<double> { typedef double4 type; };
@@ -152,8 +187,8 @@ template <> struct Vec4<double> { typedef double4 type; };
 // stale higher degrees from earlier calls at larger p).
 template <typename T, int RPT, int NC>
 __global__ void __launch_bounds__(GEMM_THREADS) k_m2l_gemm(int p, const int4* tiles, const int* pt, const int* ps,
-                                                          const T* tables, size_t tab_stride, int ld, const T* M,
-                                                          T* L) {
+                                                          const int* prefl, const T* sign, const T* tables,
+                                                          size_t tab_stride, int ld, const T* M, T* L) {
     constexpr int RP = 16 * RPT;
     __shared__ __align__(16) T sA[GEMM_KC][RP];
     __shared__ __align__(16) T sB[GEMM_KC][GEMM_COLS];
@@ -180,7 +215,7 @@ __global__ void __launch_bounds__(GEMM_THREADS) k_m2l_gemm(int p, const int4* ti
             T v = T(0);
             if (col < ncols && k < kmax) {
                 const int pr = tile.y + col / NC, c = col % NC;
-                v = M[((size_t)ps[pr] * NC + c) * ESTRIDE + k];
+                v = M[((size_t)ps[pr] * NC + c) * ESTRIDE + k] * sign[prefl[pr] * ESTRIDE + k];
             }
             sB[kk][col] = v;
         }
@@ -205,6 +240,9 @@ __global__ void __launch_bounds__(GEMM_THREADS) k_m2l_gemm(int p, const int4* ti
         const int pr = tile.y + col / NC, c = col % NC;
         T* dst = L + ((size_t)pt[pr] * NC + c) * ESTRIDE;
         const int r0 = ty * RPT;
+        const T* sg = sign + prefl[pr] * ESTRIDE;
+#pragma unroll
+        for (int i = 0; i < RPT; ++i) acc[i][j] *= sg[r0 + i];
         if (std::is_same<T, float>::value && (RPT % 4) == 0) {
 #pragma unroll
             for (int i = 0; i < RPT; i += 4) {
@@ -230,14 +268,15 @@ int build_m2l_tables(fmmbem_handle* h) {
     const int T = 256;
     const unsigned gp = (unsigned)((n + T - 1) / T);
     int *pt = nullptr, *ps = nullptr, *idx = nullptr, *idx_s = nullptr, *head = nullptr, *scan = nullptr, *bad = nullptr;
+    int* refl = nullptr;
     unsigned long long *key = nullptr, *key_s = nullptr;
     FMM_TRY(dalloc(&pt, n)); FMM_TRY(dalloc(&ps, n)); FMM_TRY(dalloc(&idx, n)); FMM_TRY(dalloc(&idx_s, n));
     FMM_TRY(dalloc(&head, n)); FMM_TRY(dalloc(&scan, n)); FMM_TRY(dalloc(&bad, 1));
-    FMM_TRY(dalloc(&key, n)); FMM_TRY(dalloc(&key_s, n));
+    FMM_TRY(dalloc(&key, n)); FMM_TRY(dalloc(&key_s, n)); FMM_TRY(dalloc(&refl, n));
     FMM_CU(cudaMemsetAsync(bad, 0, sizeof(int), st));
     k_expand_pairs<<<(h->n_cells + T - 1) / T, T, 0, st>>>(h->m2l_ptr, h->m2l_src, h->n_cells, pt, ps);
     FMM_LAUNCHED();
-    k_pair_keys<<<gp, T, 0, st>>>(pt, ps, n, h->cell_cs, h->cell_level, key, idx, bad);
+    k_pair_keys<<<gp, T, 0, st>>>(pt, ps, n, h->cell_cs, h->cell_level, key, idx, refl, bad);
     FMM_LAUNCHED();
     size_t tb = 0;
     FMM_CU(cub::DeviceRadixSort::SortPairs(nullptr, tb, key, key_s, idx, idx_s, (int)n, 0, 3 * KEY_BITS + 4, st));
@@ -263,17 +302,22 @@ int build_m2l_tables(fmmbem_handle* h) {
     if (bad_h || bytes > ((size_t)16 << 30)) {
         // keys out of range or tables too large: the gather kernel (k_m2l) handles M2L
         cudaFree(pt); cudaFree(ps); cudaFree(idx); cudaFree(idx_s); cudaFree(head); cudaFree(scan); cudaFree(bad);
-        cudaFree(key); cudaFree(key_s);
+        cudaFree(key); cudaFree(key_s); cudaFree(refl);
         return 0;
     }
     int* tab_first = nullptr;
     unsigned long long* tab_key = nullptr;
     FMM_TRY(dalloc(&h->m2l_pt, n));
     FMM_TRY(dalloc(&h->m2l_ps, n));
+    FMM_TRY(dalloc(&h->m2l_refl, n));
+    FMM_TRY(dalloc(&h->sign_f, 8 * ESTRIDE));
+    FMM_TRY(dalloc(&h->sign_d, 8 * ESTRIDE));
+    k_refl_signs<<<8, 128, 0, st>>>(h->sign_f, h->sign_d);
+    FMM_LAUNCHED();
     FMM_TRY(dalloc(&tab_first, ntab + 1));
     FMM_TRY(dalloc(&tab_key, ntab));
-    k_assign_tables<<<(unsigned)((n + 1 + T - 1) / T), T, 0, st>>>(key_s, idx_s, scan, n, pt, ps, h->m2l_pt, h->m2l_ps,
-                                                                  tab_first, tab_key);
+    k_assign_tables<<<(unsigned)((n + 1 + T - 1) / T), T, 0, st>>>(key_s, idx_s, scan, n, pt, ps, refl, h->m2l_pt,
+                                                                  h->m2l_ps, h->m2l_refl, tab_first, tab_key);
     FMM_LAUNCHED();
     // tiles for Laplace (64 pairs) and Stokes (16 pairs x 4 expansions)
     const int per_tile = GEMM_COLS / h->ncomp;
@@ -322,7 +366,7 @@ int build_m2l_tables(fmmbem_handle* h) {
     h->tab_stride = per;
     h->m2l_tables = true;
     cudaFree(pt); cudaFree(ps); cudaFree(idx); cudaFree(idx_s); cudaFree(head); cudaFree(scan); cudaFree(bad);
-    cudaFree(key); cudaFree(key_s); cudaFree(tab_first); cudaFree(tab_key); cudaFree(cnt); cudaFree(off);
+    cudaFree(key); cudaFree(key_s); cudaFree(refl); cudaFree(tab_first); cudaFree(tab_key); cudaFree(cnt); cudaFree(off);
     return 0;
 }
 
@@ -331,11 +375,12 @@ int m2l_gemm_t(fmmbem_handle* h, int p) {
     T* L = reinterpret_cast<T*>(h->L);
     const T* M = reinterpret_cast<const T*>(h->M);
     const T* tab = std::is_same<T, float>::value ? reinterpret_cast<const T*>(h->tab_f) : reinterpret_cast<const T*>(h->tab_d);
+    const T* sign = std::is_same<T, float>::value ? reinterpret_cast<const T*>(h->sign_f) : reinterpret_cast<const T*>(h->sign_d);
     FMM_CU(cudaMemsetAsync(L, 0, sizeof(T) * (size_t)h->n_cells * NC * ESTRIDE, h->stream));
     const int rpt = rpt_for(p);
     const dim3 g(h->n_tiles), b(GEMM_THREADS);
 #define M2L_CASE(R) \
-    case R: k_m2l_gemm<T, R, NC><<<g, b, 0, h->stream>>>(p, h->m2l_tiles, h->m2l_pt, h->m2l_ps, tab, h->tab_stride, h->tab_ld, M, L); break;
+    case R: k_m2l_gemm<T, R, NC><<<g, b, 0, h->stream>>>(p, h->m2l_tiles, h->m2l_pt, h->m2l_ps, h->m2l_refl, sign, tab, h->tab_stride, h->tab_ld, M, L); break;
     switch (rpt) {
         M2L_CASE(1) M2L_CASE(2) M2L_CASE(4) M2L_CASE(8) M2L_CASE(12) M2L_CASE(16) M2L_CASE(20)
         default: fmmbem_set_error("no M2L kernel for p=%d", p); return FMMBEM_EINVAL;

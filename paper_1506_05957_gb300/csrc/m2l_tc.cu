@@ -93,8 +93,8 @@ __global__ void k_tc_tables(const double* Td, int ntab, int nr, int ld, int nch,
 
 template <int NC>
 __global__ void __launch_bounds__(128) k_m2l_tc(int p, const int4* tiles, const int* pt, const int* ps,
-                                               const float* tab, size_t tab_stride, int rows_max, const float* M,
-                                               float* L, int* err) {
+                                               const int* prefl, const float* sign, const float* tab,
+                                               size_t tab_stride, int rows_max, const float* M, float* L, int* err) {
     extern __shared__ __align__(1024) unsigned char smem[];
     const int R = 2 * ncoef(p);                // outputs = inputs
     const int Np = (R + 15) & ~15;             // MMA N (multiple of 16)
@@ -127,11 +127,17 @@ __global__ void __launch_bounds__(128) k_m2l_tc(int p, const int4* tiles, const 
     const uint32_t taddr = *taddr_slot;
     // source expansion of each of this thread's gather rows (row = tid/8 + 16 i), read once
     const float* rowsrc[8];
+    const float* rowsgn[8];  // reflection signs of the row's pair (see m2l.cu)
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
         const int row = (tid >> 3) + 16 * i;
         rowsrc[i] = nullptr;
-        if (row < nrows) rowsrc[i] = M + ((size_t)ps[tile.y + row / NC] * NC + row % NC) * ESTRIDE + (tid & 7) * 4;
+        rowsgn[i] = sign + (tid & 7) * 4;
+        if (row < nrows) {
+            const int pr = tile.y + row / NC;
+            rowsrc[i] = M + ((size_t)ps[pr] * NC + row % NC) * ESTRIDE + (tid & 7) * 4;
+            rowsgn[i] = sign + prefl[pr] * ESTRIDE + (tid & 7) * 4;
+        }
     }
     const float* Tg = tab + (size_t)tile.x * tab_stride;
     const uint32_t chunk_bytes = (uint32_t)Np * TC_KC * 4;
@@ -157,8 +163,11 @@ __global__ void __launch_bounds__(128) k_m2l_tc(int p, const int4* tiles, const 
         const int kq = (tid & 7) * 4, k = c * TC_KC + kq;
         float4 v[8];
 #pragma unroll
-        for (int i = 0; i < 8; ++i)
+        for (int i = 0; i < 8; ++i) {
             v[i] = rowsrc[i] ? *reinterpret_cast<const float4*>(rowsrc[i] + c * TC_KC) : make_float4(0.f, 0.f, 0.f, 0.f);
+            const float4 sg = *reinterpret_cast<const float4*>(rowsgn[i] + c * TC_KC);
+            v[i].x *= sg.x; v[i].y *= sg.y; v[i].z *= sg.z; v[i].w *= sg.w;
+        }
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
             const int row = (tid >> 3) + 16 * i;
@@ -206,7 +215,11 @@ __global__ void __launch_bounds__(128) k_m2l_tc(int p, const int4* tiles, const 
     if (ok) {
         const int row = 32 * warp + lane;
         float* dst = nullptr;
-        if (row < nrows) dst = L + ((size_t)pt[tile.y + row / NC] * NC + row % NC) * ESTRIDE;
+        const float* sg = sign;
+        if (row < nrows) {
+            dst = L + ((size_t)pt[tile.y + row / NC] * NC + row % NC) * ESTRIDE;
+            sg = sign + prefl[tile.y + row / NC] * ESTRIDE;
+        }
         for (int col0 = 0; col0 < R; col0 += 16) {
             uint32_t r[16];
             const uint32_t a = taddr + ((uint32_t)(32 * warp) << 16) + (uint32_t)col0;
@@ -220,8 +233,9 @@ __global__ void __launch_bounds__(128) k_m2l_tc(int p, const int4* tiles, const 
 #pragma unroll
                 for (int j = 0; j < 16; j += 4)
                     atomicAdd(reinterpret_cast<float4*>(dst + col0 + j),
-                              make_float4(__uint_as_float(r[j]), __uint_as_float(r[j + 1]), __uint_as_float(r[j + 2]),
-                                          __uint_as_float(r[j + 3])));
+                              make_float4(__uint_as_float(r[j]) * sg[col0 + j], __uint_as_float(r[j + 1]) * sg[col0 + j + 1],
+                                          __uint_as_float(r[j + 2]) * sg[col0 + j + 2],
+                                          __uint_as_float(r[j + 3]) * sg[col0 + j + 3]));
             }
         }
     }
@@ -265,10 +279,10 @@ int m2l_tc(fmmbem_handle* h, int p) {
     FMM_CU(cudaMemsetAsync(L, 0, sizeof(float) * (size_t)h->n_cells * h->ncomp * ESTRIDE, h->stream));
     const size_t sm = m2l_tc_smem(p);
     if (h->ncomp == 1)
-        k_m2l_tc<1><<<h->n_tiles_tc, 128, sm, h->stream>>>(p, h->m2l_tiles_tc, h->m2l_pt, h->m2l_ps, h->tab_tc,
+        k_m2l_tc<1><<<h->n_tiles_tc, 128, sm, h->stream>>>(p, h->m2l_tiles_tc, h->m2l_pt, h->m2l_ps, h->m2l_refl, h->sign_f, h->tab_tc,
                                                            h->tc_stride, h->tc_rows_max, M, L, h->tc_err);
     else
-        k_m2l_tc<4><<<h->n_tiles_tc, 128, sm, h->stream>>>(p, h->m2l_tiles_tc, h->m2l_pt, h->m2l_ps, h->tab_tc,
+        k_m2l_tc<4><<<h->n_tiles_tc, 128, sm, h->stream>>>(p, h->m2l_tiles_tc, h->m2l_pt, h->m2l_ps, h->m2l_refl, h->sign_f, h->tab_tc,
                                                            h->tc_stride, h->tc_rows_max, M, L, h->tc_err);
     FMM_LAUNCHED();
     return 0;

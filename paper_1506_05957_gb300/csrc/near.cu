@@ -499,11 +499,28 @@ __device__ __forceinline__ bool bk_wait(uint32_t mbar, uint32_t parity) {
     return false;
 }
 
+// Warp 0: arm stage buffer `buf` with stage k's byte count, then one bulk copy per pair.
+__device__ __forceinline__ void bk_issue(int k, int s1, int e1, const int* sfirst, const int* sbytes, const int* ptoff,
+                                         const int* pcnt, const float4* prec, const float4* srcw, float4* dst,
+                                         uint32_t bar, int lane) {
+    const int fa = sfirst[k], fb = (k + 1 < s1) ? sfirst[k + 1] : e1;
+    if (lane == 0)
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"((uint32_t)sbytes[k])
+                     : "memory");
+    __syncwarp();
+    for (int e = fa + lane; e < fb; e += 32)
+        asm volatile(
+            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                smem_addr(dst + ptoff[e])),
+            "l"(srcw + __float_as_int(prec[e].w)), "r"((uint32_t)pcnt[e] * 16u), "r"(bar)
+            : "memory");
+}
+
 // Stage plans are static (create time): stage k of a target leaf covers pairs
 // [first_k, first_{k+1}) with at most BK_TILE Gauss points; pair e sits at offset
 // toff[e] of its stage and holds cnt[e] points. Warp 0 arms the stage barrier with the
 // stage's byte count, then its lanes issue one bulk copy per pair in parallel.
-__global__ void __launch_bounds__(128, 8) k_p2p_lap_bulk(const int* leaves, const int2* range, const int* pptr,
+__global__ void __launch_bounds__(128) k_p2p_lap_bulk(const int* leaves, const int2* range, const int* pptr,
                                                       const int* psrc, const float4* prec, const int* pcnt,
                                                       const int* ptoff, const int* sptr, const int* sfirst,
                                                       const int* sbytes, const float4* srcw, const float4* tgt, int K,
@@ -524,20 +541,6 @@ __global__ void __launch_bounds__(128, 8) k_p2p_lap_bulk(const int* leaves, cons
     __syncthreads();
     int use0 = 0, use1 = 0;  // completed phases of each stage barrier
     bool ok = true;
-    auto issue = [&](int k, int buf) {  // executed by warp 0
-        const int fa = sfirst[k], fb = (k + 1 < s1) ? sfirst[k + 1] : e1;
-        if (lane == 0)
-            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(&bar[buf])),
-                         "r"((uint32_t)sbytes[k])
-                         : "memory");
-        __syncwarp();
-        for (int e = fa + lane; e < fb; e += 32)
-            asm volatile(
-                "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                    smem_addr(&sS[buf][ptoff[e]])),
-                "l"(srcw + __float_as_int(prec[e].w)), "r"((uint32_t)pcnt[e] * 16u), "r"(smem_addr(&bar[buf]))
-                : "memory");
-    };
     for (int tb = r.x; tb < r.y; tb += 128) {
         const int nt = min(128, r.y - tb);
         const int S = 128 / nt;
@@ -549,10 +552,12 @@ __global__ void __launch_bounds__(128, 8) k_p2p_lap_bulk(const int* leaves, cons
             tx = x.x; ty = x.y; tz = x.z;
         }
         float hi = 0.f, lo = 0.f;
-        if (warp == 0 && s0 < s1) issue(s0, 0);
+        if (warp == 0 && s0 < s1)
+            bk_issue(s0, s1, e1, sfirst, sbytes, ptoff, pcnt, prec, srcw, sS[0], smem_addr(&bar[0]), lane);
         for (int k = s0; k < s1; ++k) {
             const int buf = (k - s0) & 1;
-            if (warp == 0 && k + 1 < s1) issue(k + 1, buf ^ 1);  // released by the previous barrier
+            if (warp == 0 && k + 1 < s1)  // the other buffer was released by the previous barrier
+                bk_issue(k + 1, s1, e1, sfirst, sbytes, ptoff, pcnt, prec, srcw, sS[buf ^ 1], smem_addr(&bar[buf ^ 1]), lane);
             const uint32_t par = (uint32_t)((buf ? use1 : use0) & 1);
             if (ok && !bk_wait(smem_addr(&bar[buf]), par)) { atomicExch(err, 4); ok = false; }
             if (buf) ++use1; else ++use0;
