@@ -3,6 +3,7 @@
 // permutations to and from the caller's panel order, solves and profiling.
 #include <stdarg.h>
 #include <string.h>
+#include <algorithm>
 #include <chrono>
 #include <vector>
 #include "handle.cuh"
@@ -254,10 +255,11 @@ void fmmbem_destroy(fmmbem_handle* h) {
     void* bufs[] = {h->perm, h->tgt_d, h->tgt_f, h->nrm_d, h->verts, h->src_d, h->src_f, h->src_rel, h->tgt_rel, h->src_w, h->cell_cs, h->cell_range,
                     h->cell_child, h->cell_level, h->cell_parent, h->leaves, h->leaf_class, h->m2l_ptr, h->m2l_src, h->p2p_ptr,
                     h->p2p_src, h->p2p_rec, h->p2p_off, h->p2p_len, h->p2p_cnt, h->p2p_toff, h->stage_ptr, h->stage_first, h->stage_bytes, h->corr_ptr, h->corr_col, h->corr_sl, h->corr_dl, h->oct_d, h->oct_f, h->M, h->L,
-                    h->xs, h->ys, h->ynear, h->m2l_pt, h->m2l_ps, h->m2l_refl, h->sign_f, h->sign_d, h->m2l_tiles, h->tab_d, h->tab_f, h->tab_tc, h->m2l_tiles_tc, h->tc_err, h->kerr, h->V, h->kw, h->xfix, h->kb, h->kx, h->kr, h->kpart, h->kh, h->kyv};
+                    h->xs, h->ys, h->ynear, h->m2l_pt, h->m2l_ps, h->m2l_refl, h->sign_f, h->sign_d, h->m2l_tiles, h->tab_d, h->tab_f, h->tab_tc, h->m2l_tiles_tc, h->tc_err, h->kerr, h->V, h->kw, h->xfix, h->kb, h->kx, h->kr, h->kpart, h->kh, h->kyv, h->arn_bar};
     for (void* b : bufs)
         if (b) cudaFree(b);
     if (h->kh_host) cudaFreeHost(h->kh_host);
+    if (h->arn_out_host) cudaFreeHost(h->arn_out_host);
     for (int q = 0; q <= FMMBEM_P_MAX; ++q) {
         if (h->mv_graph[q]) cudaGraphExecDestroy(h->mv_graph[q]);
         for (int e = 0; e < 2 * FMMBEM_N_PASSES; ++e)
@@ -339,7 +341,16 @@ int fmmbem_create(const fmmbem_mesh* mesh, int kernel, int gauss_k, int ncrit, d
     if ((rc = dalloc(&h->kw, n)) < 0 || (rc = dalloc(&h->kb, n)) < 0 || (rc = dalloc(&h->kx, n)) < 0 ||
         (rc = dalloc(&h->kr, n)) < 0)
         return fail(rc);
-    if ((rc = dalloc(&h->kpart, (size_t)96 * (o.restart + 2))) < 0) return fail(rc);
+    h->arn_blocks = arnoldi_blocks();
+    if (h->arn_blocks < 1) { fmmbem_set_error("cooperative Arnoldi kernel cannot be resident"); return fail(FMMBEM_EDEVICE); }
+    if ((rc = dalloc(&h->kpart, (size_t)std::max(96, h->arn_blocks) * (o.restart + 2))) < 0) return fail(rc);
+    if ((rc = dalloc(&h->arn_bar, 2)) < 0) return fail(rc);
+    if (cudaMemsetAsync(h->arn_bar, 0, 2 * sizeof(unsigned), h->stream) != cudaSuccess) return fail(FMMBEM_EDEVICE);
+    if (cudaHostAlloc((void**)&h->arn_out_host, sizeof(double) * (2 * 65 + 1), cudaHostAllocMapped) != cudaSuccess ||
+        cudaHostGetDevicePointer((void**)&h->arn_out_dev, h->arn_out_host, 0) != cudaSuccess) {
+        fmmbem_set_error("mapped pinned allocation failed");
+        return fail(FMMBEM_ENOMEM);
+    }
     if ((rc = dalloc(&h->kh, (size_t)3 * (o.restart + 2))) < 0) return fail(rc);
     if ((rc = dalloc(&h->kyv, (size_t)(o.restart + 2))) < 0) return fail(rc);
     if (cudaMallocHost((void**)&h->kh_host, sizeof(double) * 3 * (o.restart + 2)) != cudaSuccess) {

@@ -133,6 +133,11 @@ struct fmmbem_handle {
     double* kh = nullptr;       // [m+2] dot results
     double* kh_host = nullptr;  // pinned
     double* kyv = nullptr;      // [m] update coefficients
+    // fused Arnoldi step (cooperative launch)
+    int arn_blocks = 0;
+    unsigned* arn_bar = nullptr;       // grid barrier counter and generation
+    double* arn_out_host = nullptr;    // mapped pinned: h1[65], h2[65], ||w||^2
+    double* arn_out_dev = nullptr;
 
     // timing
     double setup_seconds = 0.0;
@@ -162,6 +167,7 @@ int near_field(fmmbem_handle* h, bool fp64, cudaStream_t st);
 int direct_field(fmmbem_handle* h, bool fp64, int which, const double* x_sorted, double* y_sorted);
 // krylov.cu
 int relaxed_p(double eta, double rho_prev, int p_initial, int p_min);
+int arnoldi_blocks();
 int gmres_solve(fmmbem_handle* h, const double* b_sorted, double tol, int relax, int p_initial, int p_min,
                 double* x_sorted, int* iters, int* p_hist, double* res_hist, double* true_res);
 // capi.cu

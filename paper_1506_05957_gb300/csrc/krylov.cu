@@ -84,6 +84,110 @@ __global__ void k_sub(double* r, const double* b, const double* ax, int64_t n) {
         r[i] = b[i] - ax[i];
 }
 
+// ---- fused Arnoldi step: classical Gram-Schmidt twice, the norm and the new basis
+// vector in one cooperative launch (all blocks co-resident). Between phases the blocks
+// meet at a sense-reversal grid barrier whose wait is bounded: on timeout the kernel
+// flags an error and stops. Each block reduces the per-block partial dots itself in a
+// fixed order (results are deterministic); block 0 writes h1, h2 and ||w||^2 to out
+// (mapped pinned host memory).
+constexpr int ARN_THREADS = 256;
+constexpr int ARN_MAXV = 64;
+
+__device__ __forceinline__ bool grid_barrier(unsigned* count, volatile unsigned* gen, unsigned nb, int* err) {
+    __syncthreads();
+    bool ok = true;
+    if (threadIdx.x == 0) {
+        const unsigned g = *gen;
+        __threadfence();
+        if (atomicAdd(count, 1u) == nb - 1) {
+            *count = 0;
+            __threadfence();
+            atomicAdd((unsigned*)gen, 1u);
+        } else {
+            unsigned it = 0;
+            while (*gen == g) {
+                if (++it > (1u << 26)) { atomicExch(err, 5); ok = false; break; }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+    }
+    __shared__ int s_ok;
+    if (threadIdx.x == 0) s_ok = ok;
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// partial[j * gridDim.x + block] = sum over the block's rows of V_j w
+__device__ void arn_partials(const double* V, int64_t ldv, int nv, const double* w, int64_t i0, int64_t i1,
+                             double* partial) {
+    __shared__ double red[ARN_THREADS / 32];
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+    for (int j = 0; j < nv; ++j) {
+        const double* v = V + (int64_t)j * ldv;
+        double s = 0.0;
+        for (int64_t i = i0 + threadIdx.x; i < i1; i += ARN_THREADS) s += v[i] * w[i];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) red[wp] = s;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double t = 0.0;
+            for (int q = 0; q < ARN_THREADS / 32; ++q) t += red[q];
+            partial[(int64_t)j * gridDim.x + blockIdx.x] = t;
+        }
+        __syncthreads();
+    }
+}
+
+__device__ void arn_reduce(const double* partial, int nv, double* hs) {
+    for (int j = threadIdx.x; j < nv; j += ARN_THREADS) {
+        double t = 0.0;
+        for (int b = 0; b < (int)gridDim.x; ++b) t += partial[(int64_t)j * gridDim.x + b];
+        hs[j] = t;
+    }
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(ARN_THREADS) k_arnoldi(double* V, int64_t n, int k, double* w, double* xfix,
+                                                         double* partial, unsigned* bar_count, unsigned* bar_gen,
+                                                         double* out, int* err) {
+    __shared__ double hs[ARN_MAXV];
+    const int nv = k + 1;
+    const int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
+    const int64_t i0 = (int64_t)blockIdx.x * chunk, i1 = min(n, i0 + chunk);
+    const unsigned nb = gridDim.x;
+    for (int pass = 0; pass < 2; ++pass) {
+        arn_partials(V, n, nv, w, i0, i1, partial);
+        if (!grid_barrier(bar_count, bar_gen, nb, err)) return;
+        arn_reduce(partial, nv, hs);
+        if (blockIdx.x == 0)
+            for (int j = threadIdx.x; j < nv; j += ARN_THREADS) out[pass * (ARN_MAXV + 1) + j] = hs[j];
+        for (int64_t i = i0 + threadIdx.x; i < i1; i += ARN_THREADS) {
+            double t = 0.0;
+            for (int j = 0; j < nv; ++j) t += hs[j] * V[(int64_t)j * n + i];
+            w[i] -= t;
+        }
+        // the next pass reads partial[] again: every block must have finished reducing
+        if (!grid_barrier(bar_count, bar_gen, nb, err)) return;
+    }
+    arn_partials(w, n, 1, w, i0, i1, partial);
+    if (!grid_barrier(bar_count, bar_gen, nb, err)) return;
+    arn_reduce(partial, 1, hs);
+    const double nrm2 = hs[0];
+    if (blockIdx.x == 0 && threadIdx.x == 0) out[2 * (ARN_MAXV + 1)] = nrm2;
+    const double hn = sqrt(nrm2);
+    if (hn > 0.0 && isfinite(hn)) {
+        const double inv = 1.0 / hn;
+        double* vk1 = V + (int64_t)(k + 1) * n;
+        for (int64_t i = i0 + threadIdx.x; i < i1; i += ARN_THREADS) {
+            const double v = w[i] * inv;
+            vk1[i] = v;
+            xfix[i] = v;
+        }
+    }
+}
+
 struct Kr {
     fmmbem_handle* h;
     int64_t n;
@@ -123,6 +227,14 @@ int relaxed_p_int(double eta, double rho_prev, int p_initial, int p_min) {
 
 }  // namespace
 
+int arnoldi_blocks() {
+    int dev = 0, sms = 0, per = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_arnoldi, ARN_THREADS, 0) != cudaSuccess || per < 1) return 0;
+    return sms;  // one block per SM: co-resident for the cooperative launch
+}
+
 int relaxed_p(double eta, double rho_prev, int p_initial, int p_min) {
     return relaxed_p_int(eta, rho_prev, p_initial, p_min);
 }
@@ -141,6 +253,19 @@ int gmres_solve(fmmbem_handle* h, const double* b, double tol, int relax, int p_
     const int rc = gmres_solve_on(h, b, tol, relax, p_initial, p_min, x, iters, p_hist, res_hist, true_res);
     h->stream = user;
     if (rc < 0) return rc;
+    // bounded device waits (grid barrier, bulk-copy and tensor-core barriers) report here
+    int flags[2] = {0, 0};
+    FMM_CU(cudaMemcpyAsync(&flags[0], h->kerr, sizeof(int), cudaMemcpyDeviceToHost, h->istream));
+    if (h->tc_err) FMM_CU(cudaMemcpyAsync(&flags[1], h->tc_err, sizeof(int), cudaMemcpyDeviceToHost, h->istream));
+    FMM_CU(cudaStreamSynchronize(h->istream));
+    if (flags[0] || flags[1]) {
+        fmmbem_set_error("a bounded device wait gave up (code %d/%d); results are invalid", flags[0], flags[1]);
+        cudaMemsetAsync(h->kerr, 0, sizeof(int), h->istream);
+        if (h->tc_err) cudaMemsetAsync(h->tc_err, 0, sizeof(int), h->istream);
+        cudaMemsetAsync(h->arn_bar, 0, 2 * sizeof(unsigned), h->istream);
+        cudaStreamSynchronize(h->istream);
+        return FMMBEM_EDEVICE;
+    }
     FMM_CU(cudaEventRecord(h->ev_out, h->istream));
     FMM_CU(cudaStreamWaitEvent(user, h->ev_out, 0));
     return rc;
@@ -197,23 +322,30 @@ static int gmres_solve_on(fmmbem_handle* h, const double* b, double tol, int rel
             if (p_hist) p_hist[it] = p;
             ++it;
             prof_begin(h, FMMBEM_PASS_KRYLOV);
-            FMM_TRY(kr.dots(h->V, k + 1, h->kw, kh1));
-            FMM_TRY(kr.sub(h->kw, h->V, k + 1, kh1));
-            FMM_TRY(kr.dots(h->V, k + 1, h->kw, kh2));
-            FMM_TRY(kr.sub(h->kw, h->V, k + 1, kh2));
-            FMM_TRY(kr.dots(h->kw, 1, h->kw, knr));
-            FMM_CU(cudaMemcpyAsync(hb, h->kh, sizeof(double) * 3 * (m_max + 2), cudaMemcpyDeviceToHost, st));
-            FMM_CU(cudaStreamSynchronize(st));
-        prof_harvest(h);
-            for (int i = 0; i <= k; ++i) Hc(i, k) = hb[i] + hb[(m_max + 2) + i];
-            const double hn = sqrt(hb[2 * (m_max + 2)]);
-            Hc(k + 1, k) = hn;
-            if (!std::isfinite(hn)) { status = FMMBEM_ENAN; stop = true; k_done = k; prof_end(h, FMMBEM_PASS_KRYLOV, 9); break; }
-            if (hn > 0.0) {
-                k_scale<<<kr.gs, 256, 0, st>>>(h->V + (int64_t)(k + 1) * n, h->xfix, h->kw, 1.0 / hn, n);
-                FMM_LAUNCHED();
+            {
+                // fused CGS2 step; results in mapped pinned memory
+                double* dV = h->V;
+                int64_t nn = n;
+                int kk = k;
+                double* dw = h->kw;
+                double* dx = h->xfix;
+                double* dp = h->kpart;
+                unsigned* bc = h->arn_bar;
+                unsigned* bg = h->arn_bar + 1;
+                double* dout = h->arn_out_dev;
+                int* de = h->kerr;
+                void* args[] = {&dV, &nn, &kk, &dw, &dx, &dp, &bc, &bg, &dout, &de};
+                FMM_CU(cudaLaunchCooperativeKernel((const void*)k_arnoldi, dim3(h->arn_blocks), dim3(ARN_THREADS), args, 0,
+                                                   st));
                 h->launches += 1;
             }
+            FMM_CU(cudaStreamSynchronize(st));
+            prof_harvest(h);
+            const volatile double* ao = h->arn_out_host;
+            for (int i = 0; i <= k; ++i) Hc(i, k) = ao[i] + ao[(ARN_MAXV + 1) + i];
+            const double hn = sqrt(ao[2 * (ARN_MAXV + 1)]);
+            Hc(k + 1, k) = hn;
+            if (!std::isfinite(hn)) { status = FMMBEM_ENAN; stop = true; k_done = k; prof_end(h, FMMBEM_PASS_KRYLOV, 1); break; }
             for (int i = 0; i < k; ++i) {
                 const double t = cs[i] * Hc(i, k) + sn[i] * Hc(i + 1, k);
                 Hc(i + 1, k) = -sn[i] * Hc(i, k) + cs[i] * Hc(i + 1, k);
@@ -228,7 +360,7 @@ static int gmres_solve_on(fmmbem_handle* h, const double* b, double tol, int rel
             g[k] = cs[k] * g[k];
             rho = fabs(g[k + 1]) / bnorm;
             if (res_hist) res_hist[it] = rho;
-            prof_end(h, FMMBEM_PASS_KRYLOV, 9);
+            prof_end(h, FMMBEM_PASS_KRYLOV, 1);
             k_done = k + 1;
             if (!std::isfinite(rho)) { status = FMMBEM_ENAN; stop = true; break; }
             if (rho <= tol) { converged = true; break; }

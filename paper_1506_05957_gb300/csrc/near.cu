@@ -499,21 +499,31 @@ __device__ __forceinline__ bool bk_wait(uint32_t mbar, uint32_t parity) {
     return false;
 }
 
-// Warp 0: arm stage buffer `buf` with stage k's byte count, then one bulk copy per pair.
-__device__ __forceinline__ void bk_issue(int k, int s1, int e1, const int* sfirst, const int* sbytes, const int* ptoff,
-                                         const int* pcnt, const float4* prec, const float4* srcw, float4* dst,
+// Warp 0: arm stage buffer `buf` with stage k's byte count, issue one bulk copy per
+// pair, and leave the pairs' records (shift, stage offset, count, own-leaf flag) in
+// shared memory for the consumers (visible to them after the next block barrier).
+__device__ __forceinline__ void bk_issue(int k, int s1, int e1, int cell, const int* sfirst, const int* sbytes,
+                                         const int* ptoff, const int* pcnt, const int* psrc, const float4* prec,
+                                         const float4* srcw, float4* dst, float4* rec, int2* info, int* np_out,
                                          uint32_t bar, int lane) {
     const int fa = sfirst[k], fb = (k + 1 < s1) ? sfirst[k + 1] : e1;
-    if (lane == 0)
+    if (lane == 0) {
         asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"((uint32_t)sbytes[k])
                      : "memory");
+        *np_out = fb - fa;
+    }
     __syncwarp();
-    for (int e = fa + lane; e < fb; e += 32)
+    for (int e = fa + lane; e < fb; e += 32) {
+        const float4 rc = prec[e];
+        const int to = ptoff[e], n = pcnt[e];
         asm volatile(
             "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                smem_addr(dst + ptoff[e])),
-            "l"(srcw + __float_as_int(prec[e].w)), "r"((uint32_t)pcnt[e] * 16u), "r"(bar)
+                smem_addr(dst + to)),
+            "l"(srcw + __float_as_int(rc.w)), "r"((uint32_t)n * 16u), "r"(bar)
             : "memory");
+        rec[e - fa] = rc;
+        info[e - fa] = make_int2(to | (psrc[e] == cell ? (1 << 30) : 0), n);
+    }
 }
 
 // Stage plans are static (create time): stage k of a target leaf covers pairs
@@ -527,6 +537,9 @@ __global__ void __launch_bounds__(128) k_p2p_lap_bulk(const int* leaves, const i
                                                       const int* cptr, const int* ccol, const double* cval,
                                                       const double* xs, double* ynear, int* err) {
     __shared__ __align__(128) float4 sS[2][BK_TILE];
+    __shared__ float4 sRec[2][BK_MAXP];
+    __shared__ int2 sInfo[2][BK_MAXP];
+    __shared__ int sNp[2];
     __shared__ __align__(8) uint64_t bar[2];
     __shared__ double sred[128];
     const int cell = leaves[blockIdx.x];
@@ -551,24 +564,29 @@ __global__ void __launch_bounds__(128) k_p2p_lap_bulk(const int* leaves, const i
             const float4 x = tgt[tb + t];
             tx = x.x; ty = x.y; tz = x.z;
         }
+        const int own = (tb + t) * K;
         float hi = 0.f, lo = 0.f;
         if (warp == 0 && s0 < s1)
-            bk_issue(s0, s1, e1, sfirst, sbytes, ptoff, pcnt, prec, srcw, sS[0], smem_addr(&bar[0]), lane);
+            bk_issue(s0, s1, e1, cell, sfirst, sbytes, ptoff, pcnt, psrc, prec, srcw, sS[0], sRec[0], sInfo[0], &sNp[0],
+                     smem_addr(&bar[0]), lane);
+        __syncthreads();
         for (int k = s0; k < s1; ++k) {
             const int buf = (k - s0) & 1;
             if (warp == 0 && k + 1 < s1)  // the other buffer was released by the previous barrier
-                bk_issue(k + 1, s1, e1, sfirst, sbytes, ptoff, pcnt, prec, srcw, sS[buf ^ 1], smem_addr(&bar[buf ^ 1]), lane);
+                bk_issue(k + 1, s1, e1, cell, sfirst, sbytes, ptoff, pcnt, psrc, prec, srcw, sS[buf ^ 1], sRec[buf ^ 1],
+                         sInfo[buf ^ 1], &sNp[buf ^ 1], smem_addr(&bar[buf ^ 1]), lane);
             const uint32_t par = (uint32_t)((buf ? use1 : use0) & 1);
             if (ok && !bk_wait(smem_addr(&bar[buf]), par)) { atomicExch(err, 4); ok = false; }
             if (buf) ++use1; else ++use0;
             if (active && ok) {
-                const int fa = sfirst[k], fb = (k + 1 < s1) ? sfirst[k + 1] : e1;
-                for (int e = fa + slice; e < fb; e += S) {
-                    const float4 rc = prec[e];
-                    const int cnt = pcnt[e];
+                const int np = sNp[buf];
+                for (int j = slice; j < np; j += S) {
+                    const float4 rc = sRec[buf][j];
+                    const int2 in = sInfo[buf][j];
+                    const int to = in.x & ((1 << 30) - 1), cnt = in.y;
                     const float px = tx - rc.x, py = ty - rc.y, pz = tz - rc.z;
-                    const float4* sp = &sS[buf][ptoff[e]];
-                    const int skip = (psrc[e] == cell) ? (tb + t) * K - __float_as_int(rc.w) : -(1 << 30);
+                    const float4* sp = &sS[buf][to];
+                    const int skip = (in.x >> 30) ? own - __float_as_int(rc.w) : -(1 << 30);
                     for (int qb = 0; qb < cnt; qb += 64) {
                         const int qe = min(cnt, qb + 64);
                         float pa = 0.f, pb = 0.f;

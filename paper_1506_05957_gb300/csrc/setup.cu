@@ -385,26 +385,28 @@ __global__ void k_p2p_records(const int* pptr, const int* psrc, const double4* c
 }
 
 // Static stage plans of the bulk-copy near field: whole pairs, at most `tile` Gauss
-// points per stage, in list order. COUNT pass counts stages; FILL pass writes them.
+// points and 64 pairs per stage, in list order. COUNT pass counts stages; FILL pass writes them.
 template <bool FILL>
 __global__ void k_p2p_plan(const int* pptr, const int* psrc, const int2* range, int ncells, int K, int tile,
                            int* nst, const int* sptr, int* cnt, int* toff, int* sfirst, int* sbytes) {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= ncells) return;
-    int ns = 0, fill = 0, out = FILL ? sptr[c] : 0;
+    int ns = 0, fill = 0, npair = 0, out = FILL ? sptr[c] : 0;
     for (int e = pptr[c]; e < pptr[c + 1]; ++e) {
         const int2 r = range[psrc[e]];
         const int n = K * (r.y - r.x);
-        if (ns == 0 || fill + n > tile) {
+        if (ns == 0 || fill + n > tile || npair == 64) {
             if (FILL) {
                 if (ns > 0) sbytes[out + ns - 1] = fill * 16;
                 sfirst[out + ns] = e;
             }
             ++ns;
             fill = 0;
+            npair = 0;
         }
         if (FILL) { cnt[e] = n; toff[e] = fill; }
         fill += n;
+        ++npair;
     }
     if (FILL && ns > 0) sbytes[out + ns - 1] = fill * 16;
     if (!FILL) nst[c] = ns;
