@@ -84,6 +84,7 @@ struct fmmbem_handle {
     int4* m2l_tiles_tc = nullptr;
     int n_tiles_tc = 0;
     int* tc_err = nullptr;        // set by the kernel if a bounded wait gives up
+    int n_sm = 152;
     int* kerr = nullptr;          // same, for the near-field bulk-copy kernel
     int* p2p_ptr = nullptr;  // [n_cells + 1]
     int* p2p_src = nullptr;

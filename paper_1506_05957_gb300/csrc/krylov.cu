@@ -118,33 +118,30 @@ __device__ __forceinline__ bool grid_barrier(unsigned* count, volatile unsigned*
     return s_ok != 0;
 }
 
-// partial[j * gridDim.x + block] = sum over the block's rows of V_j w
+// partial[j * gridDim.x + block] = sum over the block's rows of V_j w. Warp q takes the
+// vectors j = q, q + 8, ...; its lanes stride the rows; no block barrier between dots.
 __device__ void arn_partials(const double* V, int64_t ldv, int nv, const double* w, int64_t i0, int64_t i1,
                              double* partial) {
-    __shared__ double red[ARN_THREADS / 32];
     const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
-    for (int j = 0; j < nv; ++j) {
+    for (int j = wp; j < nv; j += ARN_THREADS / 32) {
         const double* v = V + (int64_t)j * ldv;
         double s = 0.0;
-        for (int64_t i = i0 + threadIdx.x; i < i1; i += ARN_THREADS) s += v[i] * w[i];
+        for (int64_t i = i0 + lane; i < i1; i += 32) s += v[i] * w[i];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if (lane == 0) red[wp] = s;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            double t = 0.0;
-            for (int q = 0; q < ARN_THREADS / 32; ++q) t += red[q];
-            partial[(int64_t)j * gridDim.x + blockIdx.x] = t;
-        }
-        __syncthreads();
+        if (lane == 0) partial[(int64_t)j * gridDim.x + blockIdx.x] = s;
     }
 }
 
+// hs[j] = sum over blocks of partial[j][.], one warp per j, fixed order per lane and tree
 __device__ void arn_reduce(const double* partial, int nv, double* hs) {
-    for (int j = threadIdx.x; j < nv; j += ARN_THREADS) {
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+    for (int j = wp; j < nv; j += ARN_THREADS / 32) {
         double t = 0.0;
-        for (int b = 0; b < (int)gridDim.x; ++b) t += partial[(int64_t)j * gridDim.x + b];
-        hs[j] = t;
+        for (int b = lane; b < (int)gridDim.x; b += 32) t += partial[(int64_t)j * gridDim.x + b];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        if (lane == 0) hs[j] = t;
     }
     __syncthreads();
 }

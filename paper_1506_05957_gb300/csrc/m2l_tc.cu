@@ -12,6 +12,7 @@
 // rounding). T_hi/T_lo are precomputed; X is split while it is staged.
 // The accumulator rows are read back with tcgen05.ld (warp w owns TMEM lanes
 // 32w..32w+31) and added to the target expansions with vector atomics.
+#include <algorithm>
 #include <type_traits>
 #include "handle.cuh"
 
@@ -91,8 +92,11 @@ __global__ void k_tc_tables(const double* Td, int ntab, int nr, int ld, int nch,
     }
 }
 
+// Persistent: each CTA allocates its TMEM columns and initializes its barriers once,
+// then takes tiles blockIdx.x, blockIdx.x + gridDim.x, ...; the barrier parities run
+// on across tiles (one load phase and one MMA phase per chunk).
 template <int NC>
-__global__ void __launch_bounds__(128) k_m2l_tc(int p, const int4* tiles, const int* pt, const int* ps,
+__global__ void __launch_bounds__(128) k_m2l_tc(int p, const int4* tiles, int ntiles, const int* pt, const int* ps,
                                                const int* prefl, const float* sign, const float* tab,
                                                size_t tab_stride, int rows_max, const float* M, float* L, int* err) {
     extern __shared__ __align__(1024) unsigned char smem[];
@@ -107,8 +111,6 @@ __global__ void __launch_bounds__(128) k_m2l_tc(int p, const int4* tiles, const 
     uint32_t* taddr_slot = reinterpret_cast<uint32_t*>(bars + 2);
     const uint32_t mbar_load = smem_u32(&bars[0]), mbar_mma = smem_u32(&bars[1]);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int4 tile = tiles[blockIdx.x];
-    const int nrows = tile.z * NC;
     const uint32_t tcols = Np <= 32 ? 32 : (Np <= 64 ? 64 : (Np <= 128 ? 128 : (Np <= 256 ? 256 : 512)));
 
     if (tid == 0) {
@@ -125,6 +127,11 @@ __global__ void __launch_bounds__(128) k_m2l_tc(int p, const int4* tiles, const 
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
     const uint32_t taddr = *taddr_slot;
+    uint32_t ph = 0;  // completed phases of each barrier (both advance once per chunk)
+    bool ok = true;
+    for (int ti = blockIdx.x; ti < ntiles && ok; ti += gridDim.x) {
+    const int4 tile = tiles[ti];
+    const int nrows = tile.z * NC;
     // source expansion of each of this thread's gather rows (row = tid/8 + 16 i), read once
     const float* rowsrc[8];
     const float* rowsgn[8];  // reflection signs of the row's pair (see m2l.cu)
@@ -141,7 +148,6 @@ __global__ void __launch_bounds__(128) k_m2l_tc(int p, const int4* tiles, const 
     }
     const float* Tg = tab + (size_t)tile.x * tab_stride;
     const uint32_t chunk_bytes = (uint32_t)Np * TC_KC * 4;
-    bool ok = true;
     for (int c = 0; c < nch && ok; ++c) {
         // operator chunk (hi, lo) by bulk copy
         if (tid == 0) {
@@ -181,7 +187,7 @@ __global__ void __launch_bounds__(128) k_m2l_tc(int p, const int4* tiles, const 
             *reinterpret_cast<float4*>(sX_lo + cm_index(row, kq)) = lo;
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        if (!mbar_wait(mbar_load, c & 1)) { atomicExch(err, 1); ok = false; }
+        if (!mbar_wait(mbar_load, ph & 1)) { atomicExch(err, 1); ok = false; }
         __syncthreads();
         asm volatile("tcgen05.fence::after_thread_sync;");
         if (tid == 0 && ok) {
@@ -208,7 +214,8 @@ __global__ void __launch_bounds__(128) k_m2l_tc(int p, const int4* tiles, const 
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar_mma)
                          : "memory");
         }
-        if (ok && !mbar_wait(mbar_mma, c & 1)) { atomicExch(err, 2); ok = false; }
+        if (ok && !mbar_wait(mbar_mma, ph & 1)) { atomicExch(err, 2); ok = false; }
+        ++ph;
         asm volatile("tcgen05.fence::after_thread_sync;");
         __syncthreads();
     }
@@ -238,6 +245,11 @@ __global__ void __launch_bounds__(128) k_m2l_tc(int p, const int4* tiles, const 
                                           __uint_as_float(r[j + 3]) * sg[col0 + j + 3]));
             }
         }
+    }
+    // the epilogue's TMEM reads finish before the next tile's MMAs overwrite the accumulator
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
@@ -269,6 +281,9 @@ int build_m2l_tc(fmmbem_handle* h) {
     const size_t smax = m2l_tc_smem(pmax);
     FMM_CU(cudaFuncSetAttribute(k_m2l_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smax));
     FMM_CU(cudaFuncSetAttribute(k_m2l_tc<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smax));
+    int dev = 0;
+    FMM_CU(cudaGetDevice(&dev));
+    FMM_CU(cudaDeviceGetAttribute(&h->n_sm, cudaDevAttrMultiProcessorCount, dev));
     h->m2l_tc_ready = true;
     return 0;
 }
@@ -278,11 +293,15 @@ int m2l_tc(fmmbem_handle* h, int p) {
     const float* M = reinterpret_cast<const float*>(h->M);
     FMM_CU(cudaMemsetAsync(L, 0, sizeof(float) * (size_t)h->n_cells * h->ncomp * ESTRIDE, h->stream));
     const size_t sm = m2l_tc_smem(p);
+    const int R = 2 * ncoef(p), Np = (R + 15) & ~15;
+    const int tcols = Np <= 32 ? 32 : (Np <= 64 ? 64 : (Np <= 128 ? 128 : (Np <= 256 ? 256 : 512)));
+    const int per_sm = std::max(1, std::min({4, (int)((220u << 10) / sm), 512 / tcols}));
+    const int grid = std::min(h->n_tiles_tc, h->n_sm * per_sm);
     if (h->ncomp == 1)
-        k_m2l_tc<1><<<h->n_tiles_tc, 128, sm, h->stream>>>(p, h->m2l_tiles_tc, h->m2l_pt, h->m2l_ps, h->m2l_refl, h->sign_f, h->tab_tc,
+        k_m2l_tc<1><<<grid, 128, sm, h->stream>>>(p, h->m2l_tiles_tc, h->n_tiles_tc, h->m2l_pt, h->m2l_ps, h->m2l_refl, h->sign_f, h->tab_tc,
                                                            h->tc_stride, h->tc_rows_max, M, L, h->tc_err);
     else
-        k_m2l_tc<4><<<h->n_tiles_tc, 128, sm, h->stream>>>(p, h->m2l_tiles_tc, h->m2l_pt, h->m2l_ps, h->m2l_refl, h->sign_f, h->tab_tc,
+        k_m2l_tc<4><<<grid, 128, sm, h->stream>>>(p, h->m2l_tiles_tc, h->n_tiles_tc, h->m2l_pt, h->m2l_ps, h->m2l_refl, h->sign_f, h->tab_tc,
                                                            h->tc_stride, h->tc_rows_max, M, L, h->tc_err);
     FMM_LAUNCHED();
     return 0;
