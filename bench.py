@@ -37,7 +37,7 @@ TF32_PER_BF16 = 1.1 / 2.25    # nominal dense tensor-core ratio
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--levels", type=int, default=6)
@@ -91,7 +91,7 @@ class ClockSampler:
     def start(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
@@ -148,6 +148,7 @@ def oracle_sample(v, t, phi, n_rows, seed=0, reps=1):
     """Time the oracle's dense FP64 rows (the CPU baseline) on a sample of rows."""
     from oracle import dense
     M = dense.Mesh(v, t, k=WORKLOAD["gauss_k"])
+    n_rows = min(n_rows, len(t))
     rows = np.random.default_rng(seed).choice(len(t), n_rows, replace=False)
     x = np.random.default_rng(seed + 1).standard_normal(len(t))
     M.laplace_apply(x, rows=rows[:8])  # load/compile outside the timing
@@ -168,10 +169,10 @@ def run_reference(args, world, rank):
     # mat-vecs of one solve at this size: 26 Arnoldi steps of the exact (fixed-p FP64)
     # GMRES plus the final true residual
     iters = 27
-    rows = 384
+    rows = min(384, n)
     threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
     for _ in range(args.warmup):
-        oracle_sample(v, t, phi, 32)
+        oracle_sample(v, t, phi, min(32, n))
     times = []
     for k in range(args.steps):
         dt, _ = oracle_sample(v, t, phi, rows, seed=k)
@@ -288,8 +289,9 @@ def run_ours(args, world, rank, local):
            "gpu_launches": int(prof["kernel_launches"]),
            "e2e": {"value": e2e, "unit": "s", "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 8 * n},
            "roofline": roofline, "clocks": clocks,
-           "tree": {k_: stats[k_] for k_ in ("n_cells", "n_leaves", "n_m2l_pairs", "n_p2p_interactions",
-                                              "n_corrections", "setup_seconds")}}
+           "tree": {k_: stats[k_] for k_ in ("n_cells", "n_leaves", "n_levels", "n_m2l_pairs", "n_m2l_tables",
+                                              "n_m2l_tiles", "n_p2p_pairs", "n_p2p_interactions", "n_corrections",
+                                              "setup_seconds")}}
 
     if not args.no_compare:
         # comparison solves on the same GPU (one each): fixed p, FP64 (the metric's

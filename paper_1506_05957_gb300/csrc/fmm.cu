@@ -131,38 +131,62 @@ __global__ void __launch_bounds__(32 * P2M_WARPS) k_p2m(int p, const int* leaves
 
 // M2M for the non-leaf cells of one level: M~_n^m(P) = sum_children sum_{j,k}
 // M~_j^k(c) 2^{-j} conj(R_{n-j}^{m-k}(d)), d = (c_child - c_parent)/s_parent.
+// One block per parent. The children's expansions and octant tables are staged in
+// shared memory; thread (child x, coefficient q) forms one child's contribution and
+// the children are summed in a fixed order, so the result is deterministic.
+constexpr int TREE_THREADS = 256;
+
 template <typename T, int NC>
-__global__ void k_m2m(int p, int lb, const double4* cs, const int2* child, const T* oct, T* M) {
-    const int cell = lb + blockIdx.x;
-    const int2 ch = child[cell];
-    if (ch.y == 0) return;
+__global__ void __launch_bounds__(TREE_THREADS) k_m2m(int p, const int* parents, const double4* cs, const int2* child,
+                                                      const T* oct, T* M) {
+    extern __shared__ unsigned char smem_raw[];
     const int nco = ncoef(p);
-    const int t = threadIdx.x;
-    if (t >= nco) return;
-    int n, m;
-    decode(t, n, m);
+    const int cell = parents[blockIdx.x];
+    const int2 ch = child[cell];
+    const int per = NC * nco * 2;  // reals of one cell's expansions
+    T* sM = reinterpret_cast<T*>(smem_raw);  // [8][NC][nco][2]
+    T* sR = sM + 8 * per;                    // [8][nco][2]
+    T* sP = sR + 8 * nco * 2;                // [8][NC][nco][2] per-child contributions
     const double4 pc = cs[cell];
-    cpx<T> acc[NC];
+    for (int idx = threadIdx.x; idx < ch.y * per; idx += blockDim.x) {
+        const int x = idx / per, rem = idx % per, c = rem / (2 * nco), q2 = rem % (2 * nco);
+        sM[idx] = M[(size_t)(ch.x + x) * NC * ESTRIDE + c * ESTRIDE + q2];
+    }
+    for (int idx = threadIdx.x; idx < ch.y * nco * 2; idx += blockDim.x) {
+        const int x = idx / (2 * nco), q2 = idx % (2 * nco);
+        sR[idx] = oct[octant_of(cs[ch.x + x], pc) * NCOEF_MAX * 2 + q2];
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < ch.y * nco; idx += blockDim.x) {
+        const int x = idx / nco, q = idx % nco;
+        int n, m;
+        decode(q, n, m);
+        const T* Rt = sR + x * nco * 2;
+        const T* Mc = sM + x * per;
+        cpx<T> acc[NC];
 #pragma unroll
-    for (int c = 0; c < NC; ++c) acc[c] = mk(T(0), T(0));
-    for (int x = 0; x < ch.y; ++x) {
-        const int cid = ch.x + x;
-        const T* Rt = oct + octant_of(cs[cid], pc) * NCOEF_MAX * 2;
-        const T* Mc = M + (size_t)cid * NC * ESTRIDE;
+        for (int c = 0; c < NC; ++c) acc[c] = mk(T(0), T(0));
         T sc = T(1);
         for (int j = 0; j <= n; ++j) {
             const int klo = max(-j, m - (n - j)), khi = min(j, m + (n - j));
             for (int k = klo; k <= khi; ++k) {
                 const cpx<T> R = conj(ld_any(Rt, n - j, m - k));
 #pragma unroll
-                for (int c = 0; c < NC; ++c) cfma(acc[c], sc * ld_any(Mc + c * ESTRIDE, j, k), R);
+                for (int c = 0; c < NC; ++c) cfma(acc[c], sc * ld_any(Mc + c * nco * 2, j, k), R);
             }
             sc *= T(0.5);
         }
-    }
-    T* out = M + (size_t)cell * NC * ESTRIDE;
 #pragma unroll
-    for (int c = 0; c < NC; ++c) st(out + c * ESTRIDE, t, acc[c]);
+        for (int c = 0; c < NC; ++c) st(sP + x * per + c * nco * 2, q, acc[c]);
+    }
+    __syncthreads();
+    T* out = M + (size_t)cell * NC * ESTRIDE;
+    for (int idx = threadIdx.x; idx < per; idx += blockDim.x) {
+        T v = T(0);
+        for (int x = 0; x < ch.y; ++x) v += sP[x * per + idx];
+        const int c = idx / (2 * nco), q2 = idx % (2 * nco);
+        out[c * ESTRIDE + q2] = v;
+    }
 }
 
 // M2L, gathered per target cell over its interaction list:
@@ -242,35 +266,54 @@ __global__ void k_m2l(int p, const int* ptr, const int* srcl, const double4* cs,
     }
 }
 
-// L2L for every cell of one level: L^_j^k(c) += sum_{n>=j, m} L^_n^m(P) R_{n-j}^{m-k}(d) 2^{-(j+1)}.
+// L2L from the non-leaf cells of one level to their children:
+//   L^_j^k(c) += sum_{n>=j, m} L^_n^m(P) R_{n-j}^{m-k}(d) 2^{-(j+1)}.
+// One block per parent: the parent's expansions and the children's octant tables are
+// staged in shared memory; thread (child x, coefficient q) writes one output.
 template <typename T, int NC>
-__global__ void k_l2l(int p, int lb, const double4* cs, const int* parent, const T* oct, T* L) {
-    const int cell = lb + blockIdx.x;
-    const int par = parent[cell];
+__global__ void __launch_bounds__(TREE_THREADS) k_l2l(int p, const int* parents, const double4* cs, const int2* child,
+                                                      const T* oct, T* L) {
+    extern __shared__ unsigned char smem_raw[];
     const int nco = ncoef(p);
-    const int t = threadIdx.x;
-    if (t >= nco || par < 0) return;
-    int j, k;
-    decode(t, j, k);
-    const T* Rt = oct + octant_of(cs[cell], cs[par]) * NCOEF_MAX * 2;
-    const T* Lp = L + (size_t)par * NC * ESTRIDE;
-    cpx<T> acc[NC];
-#pragma unroll
-    for (int c = 0; c < NC; ++c) acc[c] = mk(T(0), T(0));
-    for (int n = j; n <= p; ++n) {
-        const int mlo = max(-n, k - (n - j)), mhi = min(n, k + (n - j));
-        for (int m = mlo; m <= mhi; ++m) {
-            const cpx<T> R = ld_any(Rt, n - j, m - k);
-#pragma unroll
-            for (int c = 0; c < NC; ++c) cfma(acc[c], ld_any(Lp + c * ESTRIDE, n, m), R);
-        }
+    const int cell = parents[blockIdx.x];
+    const int2 ch = child[cell];
+    const int per = NC * nco * 2;
+    T* sL = reinterpret_cast<T*>(smem_raw);  // [NC][nco][2]
+    T* sR = sL + per;                        // [8][nco][2]
+    const double4 pc = cs[cell];
+    const T* Lp = L + (size_t)cell * NC * ESTRIDE;
+    for (int idx = threadIdx.x; idx < per; idx += blockDim.x) {
+        const int c = idx / (2 * nco), q2 = idx % (2 * nco);
+        sL[idx] = Lp[c * ESTRIDE + q2];
     }
-    const T f = T(ldexp(1.0, -(j + 1)));
-    T* out = L + (size_t)cell * NC * ESTRIDE;
+    for (int idx = threadIdx.x; idx < ch.y * nco * 2; idx += blockDim.x) {
+        const int x = idx / (2 * nco), q2 = idx % (2 * nco);
+        sR[idx] = oct[octant_of(cs[ch.x + x], pc) * NCOEF_MAX * 2 + q2];
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < ch.y * nco; idx += blockDim.x) {
+        const int x = idx / nco, q = idx % nco;
+        int j, k;
+        decode(q, j, k);
+        const T* Rt = sR + x * nco * 2;
+        cpx<T> acc[NC];
 #pragma unroll
-    for (int c = 0; c < NC; ++c) {
-        cpx<T> v = ld(out + c * ESTRIDE, t);
-        st(out + c * ESTRIDE, t, v + f * acc[c]);
+        for (int c = 0; c < NC; ++c) acc[c] = mk(T(0), T(0));
+        for (int n = j; n <= p; ++n) {
+            const int mlo = max(-n, k - (n - j)), mhi = min(n, k + (n - j));
+            for (int m = mlo; m <= mhi; ++m) {
+                const cpx<T> R = ld_any(Rt, n - j, m - k);
+#pragma unroll
+                for (int c = 0; c < NC; ++c) cfma(acc[c], ld_any(sL + c * nco * 2, n, m), R);
+            }
+        }
+        const T f = T(ldexp(1.0, -(j + 1)));
+        T* out = L + (size_t)(ch.x + x) * NC * ESTRIDE;
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            cpx<T> v = ld(out + c * ESTRIDE, q);
+            st(out + c * ESTRIDE, q, v + f * acc[c]);
+        }
     }
 }
 
@@ -443,9 +486,11 @@ int far_field_t(fmmbem_handle* h, int p) {
     // M2M, deepest non-leaf level first
     prof_begin(h, FMMBEM_PASS_M2M);
     int nl = 0;
+    const size_t sm_m2m = (size_t)(16 * NC + 8) * nco * 2 * sizeof(T);
     for (int l = h->n_levels - 2; l >= 0; --l) {
-        const int lb = h->level_start[l], le = h->level_start[l + 1];
-        k_m2m<T, NC><<<le - lb, coef_block(p), 0, st>>>(p, lb, h->cell_cs, h->cell_child, oct, M);
+        const int pb = h->parent_start[l], pe = h->parent_start[l + 1];
+        if (pe == pb) continue;
+        k_m2m<T, NC><<<pe - pb, TREE_THREADS, sm_m2m, st>>>(p, h->parents + pb, h->cell_cs, h->cell_child, oct, M);
         FMM_LAUNCHED();
         ++nl;
     }
@@ -463,15 +508,17 @@ int far_field_t(fmmbem_handle* h, int p) {
     prof_end(h, FMMBEM_PASS_M2L, 1);
     // L2L, top-down
     prof_begin(h, FMMBEM_PASS_L2L);
-    nl = 0;
-    for (int l = 1; l < h->n_levels; ++l) {
-        const int lb = h->level_start[l], le = h->level_start[l + 1];
-        k_l2l<T, NC><<<le - lb, coef_block(p), 0, st>>>(p, lb, h->cell_cs, h->cell_parent, oct, L);
+    int nl2 = 0;
+    const size_t sm_l2l = (size_t)(NC + 8) * nco * 2 * sizeof(T);
+    for (int l = 0; l + 1 < h->n_levels; ++l) {
+        const int pb = h->parent_start[l], pe = h->parent_start[l + 1];
+        if (pe == pb) continue;
+        k_l2l<T, NC><<<pe - pb, TREE_THREADS, sm_l2l, st>>>(p, h->parents + pb, h->cell_cs, h->cell_child, oct, L);
         FMM_LAUNCHED();
-        ++nl;
+        ++nl2;
     }
-    prof_end(h, FMMBEM_PASS_L2L, nl);
-    h->launches += 2 + 2 * (h->n_levels - 1);
+    prof_end(h, FMMBEM_PASS_L2L, nl2);
+    h->launches += 2 + nl + nl2;
     return 0;
 }
 
@@ -491,6 +538,13 @@ int far_eval_t(fmmbem_handle* h, int p, double* y_sorted, double scale) {
 
 int init_octant_tables(fmmbem_handle* h) {
     FMM_TRY(ensure_degree_table());
+    // dynamic shared memory of the tree passes at p = PMAX (above the 48 KB default for FP64 and Stokes)
+    const int nmax = NCOEF_MAX * 2;
+    FMM_CU(cudaFuncSetAttribute(k_m2m<float, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 24 * nmax * (int)sizeof(float)));
+    FMM_CU(cudaFuncSetAttribute(k_m2m<float, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 72 * nmax * (int)sizeof(float)));
+    FMM_CU(cudaFuncSetAttribute(k_m2m<double, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 24 * nmax * (int)sizeof(double)));
+    FMM_CU(cudaFuncSetAttribute(k_m2m<double, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 72 * nmax * (int)sizeof(double)));
+    FMM_CU(cudaFuncSetAttribute(k_l2l<double, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 12 * nmax * (int)sizeof(double)));
     FMM_CU(cudaMalloc((void**)&h->oct_d, sizeof(double) * 8 * NCOEF_MAX * 2));
     FMM_CU(cudaMalloc((void**)&h->oct_f, sizeof(float) * 8 * NCOEF_MAX * 2));
     k_octant_tables<<<1, 8, 0, h->stream>>>(h->oct_d, h->oct_f);

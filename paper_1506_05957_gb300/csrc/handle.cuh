@@ -55,6 +55,8 @@ struct fmmbem_handle {
     int* cell_level = nullptr;
     int* cell_parent = nullptr;
     int* leaves = nullptr;         // [n_leaves] cell ids
+    int* parents = nullptr;        // non-leaf cells grouped by level (M2M and L2L blocks)
+    std::vector<int> parent_start; // host, [n_levels + 1]: parents of level l are [parent_start[l], parent_start[l+1])
     int* leaf_class = nullptr;     // [n_leaves] leaves ordered by target count class (<=32, <=64, more)
     int leaf_class_start[4] = {0, 0, 0, 0};
 

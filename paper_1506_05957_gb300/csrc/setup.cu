@@ -768,6 +768,23 @@ int build_geometry_tree_lists(fmmbem_handle* h, const fmmbem_mesh* mesh) {
         h->n_levels = level;  // level_start has n_levels + 1 entries
         h->cell_cs = cs; h->cell_range = range; h->cell_child = child; h->cell_level = clevel; h->cell_parent = parent;
     }
+    {
+        // non-leaf cells by level: one M2M / L2L block each
+        std::vector<int2> ch_h(h->n_cells);
+        FMM_CU(cudaMemcpyAsync(ch_h.data(), h->cell_child, sizeof(int2) * h->n_cells, cudaMemcpyDeviceToHost, st));
+        FMM_CU(cudaStreamSynchronize(st));
+        std::vector<int> par;
+        h->parent_start.assign(1, 0);
+        for (int l = 0; l < h->n_levels; ++l) {
+            for (int c = h->level_start[l]; c < h->level_start[l + 1]; ++c)
+                if (ch_h[c].y > 0) par.push_back(c);
+            h->parent_start.push_back((int)par.size());
+        }
+        FMM_TRY(dalloc(&h->parents, par.size()));
+        if (!par.empty())
+            FMM_CU(cudaMemcpyAsync(h->parents, par.data(), sizeof(int) * par.size(), cudaMemcpyHostToDevice, st));
+        FMM_CU(cudaStreamSynchronize(st));
+    }
     const int nc = h->n_cells;
     {
         int* cnt = nullptr;

@@ -65,6 +65,10 @@ def test_create_rejects_bad_arguments_without_touching_the_gpu(libfmm):
     t = np.array([[0, 1, 2]], dtype=np.int32)
     mesh = binding.fmmbem_mesh(3, v.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), 1,
                                t.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)))
+    empty = binding.fmmbem_mesh(3, v.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), 0,
+                                t.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)))
+    rc = binding.lib().fmmbem_create(ctypes.byref(empty), 0, 4, 150, 0.5, None, ctypes.byref(h))
+    assert rc == binding.FMMBEM_EINVAL and not h.value  # an empty mesh is refused
     for kernel, k, ncrit, theta in ((7, 4, 150, 0.5), (0, 4, 150, 1.5), (0, 4, 150, 0.0), (0, 4, 2, 0.5)):
         rc = binding.lib().fmmbem_create(ctypes.byref(mesh), kernel, k, ncrit, theta, None, ctypes.byref(h))
         assert rc == binding.FMMBEM_EINVAL

@@ -161,3 +161,25 @@ def test_stokes_drag_matches_stokes_law():
     # the paper's printed value for mu = 1e-3
     F3, _, _ = _stokes_drag(3, 1e-3)
     assert abs(abs(F3) - paper_values()["stokes_drag_mu1e-3"]) < 1e-2 * 0.01885
+
+
+def test_nbody_sums_octahedral_charges_closed_form():
+    """Six unit charges at +-e_x, +-e_y, +-e_z: potential and gradient on the z axis
+    and at the centre have closed forms."""
+    from oracle.dense import nbody_laplace
+    src = np.array([[1, 0, 0], [-1, 0, 0], [0, 1, 0], [0, -1, 0], [0, 0, 1], [0, 0, -1]], dtype=np.float64)
+    q = np.array([1.0, 1.0, 1.0, 1.0, 2.0, 0.5])
+    d = np.array([0.0, 0.3, 2.5, 7.0])
+    tgt = np.column_stack([np.zeros_like(d), np.zeros_like(d), d])
+    phi, g = nbody_laplace(tgt, src, q, grad=True)
+    s2 = np.sqrt(d * d + 1.0)
+    exact = 4.0 / s2 + 2.0 / np.abs(d - 1.0) + 0.5 / np.abs(d + 1.0)
+    # gradient of 1/|x - y| is -(x - y)/|x - y|^3
+    gz = -4.0 * d / s2 ** 3 - 2.0 * (d - 1.0) / np.abs(d - 1.0) ** 3 - 0.5 * (d + 1.0) / np.abs(d + 1.0) ** 3
+    assert np.allclose(phi, exact, rtol=1e-14, atol=0)
+    assert np.allclose(g[:, 2], gz, rtol=1e-13, atol=1e-15)
+    assert np.all(np.abs(g[:, :2]) < 1e-15)
+    # translation invariance of the sums
+    sh = np.array([0.7, -1.3, 2.2])
+    phi2 = nbody_laplace(tgt + sh, src + sh, q)
+    assert np.allclose(phi2, phi, rtol=1e-13)
