@@ -133,7 +133,10 @@ int fmmbem_set_m2l_mode(fmmbem_handle* h, int mode);
  * 0 = source tiles staged in shared memory, targets held per lane;
  * 1 = (target, source slice) per thread, sources read through L1;
  * 2 = as 1, with each pair's sources bulk-copied into double-buffered shared memory
- *     (default; used when a leaf holds at most 1024 Gauss points, else 1). */
+ *     (default; used when a leaf holds at most 1024 Gauss points, else 1);
+ * 3 = one warp per target leaf with the lanes over its source stream and the targets
+ *     looped in registers.
+ * Returns FMMBEM_EINVAL for any other value. */
 int fmmbem_set_p2p_variant(fmmbem_handle* h, int variant);
 
 /*

@@ -254,8 +254,8 @@ void fmmbem_destroy(fmmbem_handle* h) {
     if (!h) return;
     void* bufs[] = {h->perm, h->tgt_d, h->tgt_f, h->nrm_d, h->verts, h->src_d, h->src_f, h->src_rel, h->tgt_rel, h->src_w, h->cell_cs, h->cell_range,
                     h->cell_child, h->cell_level, h->cell_parent, h->leaves, h->parents, h->leaf_class, h->m2l_ptr, h->m2l_src, h->p2p_ptr,
-                    h->p2p_src, h->p2p_rec, h->p2p_off, h->p2p_len, h->p2p_cnt, h->p2p_toff, h->stage_ptr, h->stage_first, h->stage_bytes, h->corr_ptr, h->corr_col, h->corr_sl, h->corr_dl, h->oct_d, h->oct_f, h->M, h->L,
-                    h->xs, h->ys, h->ynear, h->m2l_pt, h->m2l_ps, h->m2l_refl, h->sign_f, h->sign_d, h->m2l_tiles, h->tab_d, h->tab_f, h->tab_tc, h->m2l_tiles_tc, h->tc_err, h->kerr, h->V, h->kw, h->xfix, h->kb, h->kx, h->kr, h->kpart, h->kh, h->kyv, h->arn_bar};
+                    h->p2p_src, h->p2p_rec, h->p2p_off, h->p2p_len, h->p2p_order, h->p2p_cnt, h->p2p_toff, h->stage_ptr, h->stage_first, h->stage_bytes, h->corr_ptr, h->corr_col, h->corr_sl, h->corr_dl, h->oct_d, h->oct_f, h->M, h->L,
+                    h->xs, h->ys, h->ynear, h->m2l_pt, h->m2l_ps, h->m2l_refl, h->sign_f, h->sign_d, h->m2l_tiles, h->tab_d, h->tab_f, h->tab_tc, h->m2l_tiles_tc, h->tc_src_info, h->tc_dst_info, h->tc_err, h->kerr, h->V, h->kw, h->xfix, h->kb, h->kx, h->kr, h->kpart, h->kh, h->kyv, h->arn_bar};
     for (void* b : bufs)
         if (b) cudaFree(b);
     if (h->kh_host) cudaFreeHost(h->kh_host);
@@ -375,7 +375,7 @@ int fmmbem_set_precision(fmmbem_handle* h, int precision) {
 }
 
 int fmmbem_set_p2p_variant(fmmbem_handle* h, int variant) {
-    if (!h || variant < 0 || variant > 2) { fmmbem_set_error("bad P2P variant"); return FMMBEM_EINVAL; }
+    if (!h || variant < 0 || variant > 3) { fmmbem_set_error("bad P2P variant"); return FMMBEM_EINVAL; }
     h->p2p_variant = variant;
     return 0;
 }

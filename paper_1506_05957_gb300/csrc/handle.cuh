@@ -85,6 +85,8 @@ struct fmmbem_handle {
     int tc_rows_max = 0;
     int4* m2l_tiles_tc = nullptr;
     int n_tiles_tc = 0;
+    int* tc_src_info = nullptr;   // [n_tiles_tc][128]: source row offset * 8 + reflection (-1: empty row)
+    int* tc_dst_info = nullptr;   // [n_tiles_tc][128]: target row offset * 8 + reflection
     int* tc_err = nullptr;        // set by the kernel if a bounded wait gives up
     int n_sm = 152;
     int* kerr = nullptr;          // same, for the near-field bulk-copy kernel
@@ -101,7 +103,8 @@ struct fmmbem_handle {
     int* stage_bytes = nullptr; // bytes of each stage
     int64_t n_stages = 0;
     int max_leaf_panels = 0;
-    int p2p_variant = 2;        // 0: shared stream tiles, 1: sliced L1 broadcast, 2: bulk-copied stages
+    int* p2p_order = nullptr;   // [n_leaves] leaves by decreasing near-field work (source-lane kernel order)
+    int p2p_variant = 2;        // 0: shared stream tiles, 1: sliced L1 broadcast, 2: bulk-copied stages, 3: source lanes
 
     // near-singular / self corrections (CSR by sorted target panel), FP64
     int* corr_ptr = nullptr;   // [N + 1]

@@ -10,8 +10,9 @@
 // FP32 accuracy comes from the 3xTF32 split: x = x_hi + x_lo with x_hi rounded to
 // TF32, D = X_hi T_hi + X_hi T_lo + X_lo T_hi (the X_lo T_lo term is below FP32
 // rounding). T_hi/T_lo are precomputed; X is split while it is staged.
-// The accumulator rows are read back with tcgen05.ld (warp w owns TMEM lanes
-// 32w..32w+31) and added to the target expansions with vector atomics.
+// The accumulator rows are read back with tcgen05.ld (warps w and w + 4 own TMEM lanes
+// 32 (w mod 4) .. +31 and split the columns), transposed through padded shared memory
+// and added to the target expansions with row-contiguous float4 atomics.
 #include <algorithm>
 #include <type_traits>
 #include "handle.cuh"
@@ -92,180 +93,391 @@ __global__ void k_tc_tables(const double* Td, int ntab, int nr, int ld, int nch,
     }
 }
 
-// Persistent: each CTA allocates its TMEM columns and initializes its barriers once,
-// then takes tiles blockIdx.x, blockIdx.x + gridDim.x, ...; the barrier parities run
-// on across tiles (one load phase and one MMA phase per chunk).
-template <int NC>
-__global__ void __launch_bounds__(128) k_m2l_tc(int p, const int4* tiles, int ntiles, const int* pt, const int* ps,
-                                               const int* prefl, const float* sign, const float* tab,
-                                               size_t tab_stride, int rows_max, const float* M, float* L, int* err) {
-    extern __shared__ __align__(1024) unsigned char smem[];
-    const int R = 2 * ncoef(p);                // outputs = inputs
-    const int Np = (R + 15) & ~15;             // MMA N (multiple of 16)
-    const int nch = (R + TC_KC - 1) / TC_KC;   // K chunks
-    float* sX_hi = reinterpret_cast<float*>(smem);
-    float* sX_lo = sX_hi + TC_ROWS * TC_KC;
-    float* sT_hi = sX_lo + TC_ROWS * TC_KC;
-    float* sT_lo = sT_hi + Np * TC_KC;
-    uint64_t* bars = reinterpret_cast<uint64_t*>(sT_lo + Np * TC_KC);
-    uint32_t* taddr_slot = reinterpret_cast<uint32_t*>(bars + 2);
-    const uint32_t mbar_load = smem_u32(&bars[0]), mbar_mma = smem_u32(&bars[1]);
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const uint32_t tcols = Np <= 32 ? 32 : (Np <= 64 ? 64 : (Np <= 128 ? 128 : (Np <= 256 ? 256 : 512)));
+// Persistent and warp-specialized: one CTA per SM takes tiles blockIdx.x, blockIdx.x +
+// gridDim.x, ...; its work items are (tile, K chunk) pairs in that order. Roles:
+//   warp 0      : bulk-copies the operator chunk of item i into smem stage i % NST;
+//   warp 1      : issues the MMAs of item i into TMEM accumulator (tile) % NB and commits;
+//   warps 2-9   : gather producers; each stages 16 rows of every item (rows of the
+//                 tile's pairs, reflection signs applied, split into TF32 hi/lo),
+//                 keeping the loads of the next item in flight while storing this one;
+//   warps 10-17 : two epilogue groups of four (one per TMEM lane quadrant); group g
+//                 drains the accumulators of tiles j = g mod 2 (all tiles by group 0
+//                 when there is one accumulator) through a padded smem transpose into
+//                 row-contiguous float4 atomics.
+// mbarriers: full[s] (8 producer arrivals + the copy's transaction bytes), empty[s]
+// (MMA commit), acc_full[b] (commit after a tile's last chunk), acc_empty[b] (the
+// four warps of the draining group). Use k of a barrier completes phase k; a role
+// waits on phase k only before the use k + 1 that it gates can begin, so parities
+// never alias. Every wait is bounded: on timeout the CTA records an error code,
+// raises an abort flag that the other roles' waits observe, drains what it
+// issued (bounded again), frees TMEM and returns.
+constexpr int TC_WARPS = 18;
+constexpr int TC_THREADS = 32 * TC_WARPS;
+constexpr int TC_PROD0 = 2, TC_NPROD = 8, TC_EPI0 = 10;
+constexpr int EPI_LD = 33;  // padded row length of the epilogue transpose buffer
+constexpr int TC_SMEM_BUDGET = 222 * 1024;
 
+struct TcLayout {
+    int nst, nb, np;
+    __host__ __device__ int stage_floats() const { return 2 * TC_ROWS * TC_KC + 2 * np * TC_KC; }
+    __host__ __device__ int epi_floats() const { return 8 * 32 * EPI_LD; }
+    __host__ __device__ size_t bytes() const {
+        return (size_t)(nst * stage_floats() + epi_floats()) * sizeof(float) + 16 * 8 + 64;
+    }
+};
+
+__host__ __device__ inline TcLayout tc_layout(int p) {
+    TcLayout t;
+    const int R = 2 * ncoef(p);
+    t.np = (R + 15) & ~15;
+    t.nb = t.np <= 128 ? 4 : (t.np <= 256 ? 2 : 1);
+    t.nst = 1;
+    for (int n = 4; n >= 1; --n) {
+        t.nst = n;
+        if ((size_t)(n * t.stage_floats() + t.epi_floats()) * sizeof(float) + 16 * 8 + 64 <= (size_t)TC_SMEM_BUDGET) break;
+    }
+    return t;
+}
+
+// Reflection sign bits of a float4 of real coefficients (re_a, im_a, re_b, im_b),
+// coefficients a and a + 1: bit e set = element e changes sign under reflection q
+// (bit 0: x, bit 1: y, bit 2: z). z -> (-1)^{n+m}; y -> conj; x -> (-1)^m conj.
+__device__ __forceinline__ uint32_t coef_nm_bits(int c) {
+    int n = (int)((sqrtf(8.f * c + 1.f) - 1.f) * 0.5f);
+    if ((n + 1) * (n + 2) / 2 <= c) ++n;
+    if (n * (n + 1) / 2 > c) --n;
+    const int m = c - n * (n + 1) / 2;
+    return (uint32_t)(((n + m) & 1) | ((m & 1) << 1));  // bit 0: z parity, bit 1: x parity
+}
+__device__ __forceinline__ uint32_t sign_bits(uint32_t nm_a, uint32_t nm_b, int q) {
+    const uint32_t z = (q >> 2) & 1, y = (q >> 1) & 1, x = q & 1;
+    const uint32_t ra = (z & nm_a) ^ (x & (nm_a >> 1)), rb = (z & nm_b) ^ (x & (nm_b >> 1));
+    const uint32_t ia = ra ^ y ^ x, ib = rb ^ y ^ x;
+    return ra | (ia << 1) | (rb << 2) | (ib << 3);
+}
+__device__ __forceinline__ float4 apply_signs(float4 v, uint32_t b) {
+    v.x = __uint_as_float(__float_as_uint(v.x) ^ ((b & 1u) << 31));
+    v.y = __uint_as_float(__float_as_uint(v.y) ^ (((b >> 1) & 1u) << 31));
+    v.z = __uint_as_float(__float_as_uint(v.z) ^ (((b >> 2) & 1u) << 31));
+    v.w = __uint_as_float(__float_as_uint(v.w) ^ (((b >> 3) & 1u) << 31));
+    return v;
+}
+
+// Bounded wait that also gives up once another role has raised the abort flag.
+__device__ __forceinline__ bool mbar_wait_ab(uint32_t mbar, uint32_t parity, volatile int* abort_flag) {
+    for (uint32_t it = 0; it < WAIT_LIMIT; ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred q;\n\tmbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2;\n\tselp.u32 %0, 1, 0, q;\n\t}\n"
+            : "=r"(done)
+            : "r"(mbar), "r"(parity)
+            : "memory");
+        if (done) return true;
+        if ((it & 255) == 255 && *abort_flag) return false;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(mbar) : "memory");
+}
+
+// rinfo[t * 128 + r] = (row offset of pair row r of tile t in the expansion array) * 8 + reflection,
+// -1 past the tile's rows; one table for the sources (gather) and one for the targets (epilogue).
+template <int NC>
+__global__ void __launch_bounds__(TC_THREADS, 1) k_m2l_tc(int p, int prods, const int4* tiles, int ntiles,
+                                                         const int* src_info, const int* dst_info, const float* tab,
+                                                         size_t tab_stride, int rows_max, const float* M, float* L,
+                                                         int* err) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    const TcLayout lay = tc_layout(p);
+    const int R = 2 * ncoef(p);
+    const int Np = lay.np, NST = lay.nst, NB = lay.nb;
+    const int nch = (R + TC_KC - 1) / TC_KC;
+    const uint32_t chunk_bytes = (uint32_t)Np * TC_KC * 4;
+    float* stage0 = reinterpret_cast<float*>(smem);
+    const int sf = lay.stage_floats();
+    float* epi = stage0 + NST * sf;
+    uint64_t* bar = reinterpret_cast<uint64_t*>(epi + lay.epi_floats());  // full[4], empty[4], acc_full[4], acc_empty[4]
+    uint32_t* taddr_slot = reinterpret_cast<uint32_t*>(bar + 16);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(taddr_slot + 1);
+    auto full = [&](int st) { return smem_u32(&bar[st]); };
+    auto empty = [&](int st) { return smem_u32(&bar[4 + st]); };
+    auto acc_full = [&](int b) { return smem_u32(&bar[8 + b]); };
+    auto acc_empty = [&](int b) { return smem_u32(&bar[12 + b]); };
+    auto xh = [&](int st) { return stage0 + st * sf; };
+    auto xl = [&](int st) { return stage0 + st * sf + TC_ROWS * TC_KC; };
+    auto th = [&](int st) { return stage0 + st * sf + 2 * TC_ROWS * TC_KC; };
+    auto tl = [&](int st) { return stage0 + st * sf + 2 * TC_ROWS * TC_KC + Np * TC_KC; };
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mbar_load), "r"(1));
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mbar_mma), "r"(1));
+        for (int st = 0; st < 4; ++st) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(full(st)), "r"(TC_NPROD + 1));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(empty(st)), "r"(1));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(acc_full(st)), "r"(1));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(acc_empty(st)), "r"(4));
+        }
         asm volatile("fence.mbarrier_init.release.cluster;");
+        *abort_flag = 0;
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(taddr_slot)),
-                     "r"(tcols));
+                     "r"(512));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
     const uint32_t taddr = *taddr_slot;
-    uint32_t ph = 0;  // completed phases of each barrier (both advance once per chunk)
-    bool ok = true;
-    for (int ti = blockIdx.x; ti < ntiles && ok; ti += gridDim.x) {
-    const int4 tile = tiles[ti];
-    const int nrows = tile.z * NC;
-    // source expansion of each of this thread's gather rows (row = tid/8 + 16 i), read once
-    const float* rowsrc[8];
-    const float* rowsgn[8];  // reflection signs of the row's pair (see m2l.cu)
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-        const int row = (tid >> 3) + 16 * i;
-        rowsrc[i] = nullptr;
-        rowsgn[i] = sign + (tid & 7) * 4;
-        if (row < nrows) {
-            const int pr = tile.y + row / NC;
-            rowsrc[i] = M + ((size_t)ps[pr] * NC + row % NC) * ESTRIDE + (tid & 7) * 4;
-            rowsgn[i] = sign + prefl[pr] * ESTRIDE + (tid & 7) * 4;
+    const uint32_t buf_cols = (uint32_t)(512 / NB);
+    const int my_tiles = (int)blockIdx.x < ntiles ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+    const int n_items = my_tiles * nch;
+    auto tile_of = [&](int j) { return (int)blockIdx.x + j * (int)gridDim.x; };
+    auto fail = [&](int code) {
+        atomicExch(err, code);
+        *abort_flag = 1;
+    };
+    int issued_tma = 0, issued_mma = 0;  // items issued by the copy and MMA roles (for the final drain)
+
+    if (warp == 0) {
+        // ---------------- operator copies
+        if (lane == 0) {
+            for (int i = 0; i < n_items; ++i) {
+                const int st = i % NST, k = i / NST;
+                if (k > 0 && !mbar_wait_ab(empty(st), (uint32_t)((k - 1) & 1), abort_flag)) { fail(1); break; }
+                if (*abort_flag) break;
+                const int4 tile = tiles[tile_of(i / nch)];
+                const int c = i % nch;
+                const uint32_t bytes = prods == 3 ? 2 * chunk_bytes : chunk_bytes;
+                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(full(st)), "r"(bytes) : "memory");
+                const float* src = tab + (size_t)tile.x * tab_stride + (size_t)c * 2 * rows_max * TC_KC;
+                asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                                 smem_u32(th(st))),
+                             "l"(src), "r"(chunk_bytes), "r"(full(st))
+                             : "memory");
+                if (prods == 3)
+                    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                                     smem_u32(tl(st))),
+                                 "l"(src + (size_t)rows_max * TC_KC), "r"(chunk_bytes), "r"(full(st))
+                                 : "memory");
+                issued_tma = i + 1;
+            }
         }
-    }
-    const float* Tg = tab + (size_t)tile.x * tab_stride;
-    const uint32_t chunk_bytes = (uint32_t)Np * TC_KC * 4;
-    for (int c = 0; c < nch && ok; ++c) {
-        // operator chunk (hi, lo) by bulk copy
-        if (tid == 0) {
-            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar_load), "r"(2 * chunk_bytes)
-                         : "memory");
-            const float* src = Tg + (size_t)c * 2 * rows_max * TC_KC;
-            asm volatile(
-                "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                    smem_u32(sT_hi)),
-                "l"(src), "r"(chunk_bytes), "r"(mbar_load)
-                : "memory");
-            asm volatile(
-                "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                    smem_u32(sT_lo)),
-                "l"(src + (size_t)rows_max * TC_KC), "r"(chunk_bytes), "r"(mbar_load)
-                : "memory");
-        }
-        // gathered source expansions, split into TF32 hi/lo (8 independent loads per thread)
-        const int kq = (tid & 7) * 4, k = c * TC_KC + kq;
-        float4 v[8];
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            v[i] = rowsrc[i] ? *reinterpret_cast<const float4*>(rowsrc[i] + c * TC_KC) : make_float4(0.f, 0.f, 0.f, 0.f);
-            const float4 sg = *reinterpret_cast<const float4*>(rowsgn[i] + c * TC_KC);
-            v[i].x *= sg.x; v[i].y *= sg.y; v[i].z *= sg.z; v[i].w *= sg.w;
-        }
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            const int row = (tid >> 3) + 16 * i;
-            if (k + 0 >= R) v[i].x = 0.f;
-            if (k + 1 >= R) v[i].y = 0.f;
-            if (k + 2 >= R) v[i].z = 0.f;
-            if (k + 3 >= R) v[i].w = 0.f;
-            const float4 hi = make_float4(tf32_hi(v[i].x), tf32_hi(v[i].y), tf32_hi(v[i].z), tf32_hi(v[i].w));
-            const float4 lo = make_float4(v[i].x - hi.x, v[i].y - hi.y, v[i].z - hi.z, v[i].w - hi.w);
-            *reinterpret_cast<float4*>(sX_hi + cm_index(row, kq)) = hi;
-            *reinterpret_cast<float4*>(sX_lo + cm_index(row, kq)) = lo;
-        }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        if (!mbar_wait(mbar_load, ph & 1)) { atomicExch(err, 1); ok = false; }
-        __syncthreads();
-        asm volatile("tcgen05.fence::after_thread_sync;");
-        if (tid == 0 && ok) {
-            const uint32_t xh = smem_u32(sX_hi), xl = smem_u32(sX_lo), th = smem_u32(sT_hi), tl = smem_u32(sT_lo);
+    } else if (warp == 1) {
+        // ---------------- MMA issue
+        if (lane == 0) {
             const int n1 = Np <= 256 ? Np : 256;
             const uint32_t id1 = idesc_tf32(TC_ROWS, n1);
             const uint32_t id2 = Np > 256 ? idesc_tf32(TC_ROWS, Np - 256) : 0u;
-            for (int ks = 0; ks < TC_KC / 8; ++ks) {
-                const uint32_t off = 256u * ks;
-                const uint64_t a_hi = smem_desc(xh + off, 128, 1024), a_lo = smem_desc(xl + off, 128, 1024);
-                const uint64_t b_hi = smem_desc(th + off, 128, 1024), b_lo = smem_desc(tl + off, 128, 1024);
-                const uint32_t first = (c == 0 && ks == 0) ? 0u : 1u;
-                mma_tf32(taddr, a_hi, b_hi, id1, first);
-                mma_tf32(taddr, a_hi, b_lo, id1, 1u);
-                mma_tf32(taddr, a_lo, b_hi, id1, 1u);
-                if (Np > 256) {
-                    const uint32_t boff = 32u * 1024u;  // rows 256.. start 32 row groups later
-                    const uint64_t b2_hi = smem_desc(th + off + boff, 128, 1024), b2_lo = smem_desc(tl + off + boff, 128, 1024);
-                    mma_tf32(taddr + 256, a_hi, b2_hi, id2, first);
-                    mma_tf32(taddr + 256, a_hi, b2_lo, id2, 1u);
-                    mma_tf32(taddr + 256, a_lo, b2_hi, id2, 1u);
+            for (int i = 0; i < n_items; ++i) {
+                const int st = i % NST, k = i / NST;
+                const int j = i / nch, c = i % nch, b = j % NB, u = j / NB;
+                if (c == 0 && u > 0 && !mbar_wait_ab(acc_empty(b), (uint32_t)((u - 1) & 1), abort_flag)) { fail(3); break; }
+                if (!mbar_wait_ab(full(st), (uint32_t)(k & 1), abort_flag)) { fail(4); break; }
+                asm volatile("tcgen05.fence::after_thread_sync;");
+                const uint32_t acc = taddr + (uint32_t)b * buf_cols;
+                const uint32_t ah = smem_u32(xh(st)), al = smem_u32(xl(st)), bh = smem_u32(th(st)), bl = smem_u32(tl(st));
+                for (int ks = 0; ks < TC_KC / 8; ++ks) {
+                    const uint32_t off = 256u * ks;
+                    const uint64_t a_hi = smem_desc(ah + off, 128, 1024), b_hi = smem_desc(bh + off, 128, 1024);
+                    const uint32_t first = (c == 0 && ks == 0) ? 0u : 1u;
+                    mma_tf32(acc, a_hi, b_hi, id1, first);
+                    if (prods == 3) {
+                        mma_tf32(acc, a_hi, smem_desc(bl + off, 128, 1024), id1, 1u);
+                        mma_tf32(acc, smem_desc(al + off, 128, 1024), b_hi, id1, 1u);
+                    }
+                    if (Np > 256) {
+                        const uint32_t boff = 32u * 1024u;  // operator rows 256.. start 32 row groups later
+                        const uint64_t b2_hi = smem_desc(bh + off + boff, 128, 1024);
+                        mma_tf32(acc + 256, a_hi, b2_hi, id2, first);
+                        if (prods == 3) {
+                            mma_tf32(acc + 256, a_hi, smem_desc(bl + off + boff, 128, 1024), id2, 1u);
+                            mma_tf32(acc + 256, smem_desc(al + off, 128, 1024), b2_hi, id2, 1u);
+                        }
+                    }
                 }
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(empty(st))
+                             : "memory");
+                if (c == nch - 1)
+                    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                                     acc_full(b))
+                                 : "memory");
+                issued_mma = i + 1;
             }
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar_mma)
-                         : "memory");
         }
-        if (ok && !mbar_wait(mbar_mma, ph & 1)) { atomicExch(err, 2); ok = false; }
-        ++ph;
-        asm volatile("tcgen05.fence::after_thread_sync;");
-        __syncthreads();
-    }
-    if (ok) {
-        const int row = 32 * warp + lane;
-        float* dst = nullptr;
-        const float* sg = sign;
-        if (row < nrows) {
-            dst = L + ((size_t)pt[tile.y + row / NC] * NC + row % NC) * ESTRIDE;
-            sg = sign + prefl[tile.y + row / NC] * ESTRIDE;
-        }
-        for (int col0 = 0; col0 < R; col0 += 16) {
-            uint32_t r[16];
-            const uint32_t a = taddr + ((uint32_t)(32 * warp) << 16) + (uint32_t)col0;
-            asm volatile(
-                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-                  "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-                : "r"(a));
-            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-            if (dst) {
+    } else if (warp < TC_EPI0) {
+        // ---------------- gather producers: rows 16 pw + 8 h + (lane & 7), k-quads (lane >> 3) + 4 e.
+        // Software pipeline over three register slots (the loop is unrolled by three so the
+        // slot indices are constants): while item i is stored from slot i % 3, the inputs of
+        // item i + 1 are in flight in slot (i + 1) % 3, the inputs of item i + 2 are issued into
+        // slot (i + 2) % 3 from its row tables (loaded one item earlier), and the row tables
+        // of item i + 3 then go into the freed slot i % 3.
+        const int pw = warp - TC_PROD0, r7 = lane & 7, kq0 = lane >> 3;
+        float4 d[3][2][2];
+        int f[3][2];
+        auto load_info = [&](int i, int (&info)[2]) {
 #pragma unroll
-                for (int j = 0; j < 16; j += 4)
-                    atomicAdd(reinterpret_cast<float4*>(dst + col0 + j),
-                              make_float4(__uint_as_float(r[j]) * sg[col0 + j], __uint_as_float(r[j + 1]) * sg[col0 + j + 1],
-                                          __uint_as_float(r[j + 2]) * sg[col0 + j + 2],
-                                          __uint_as_float(r[j + 3]) * sg[col0 + j + 3]));
+            for (int h = 0; h < 2; ++h)
+                info[h] = i < n_items ? src_info[(size_t)tile_of(i / nch) * TC_ROWS + 16 * pw + 8 * h + r7] : -1;
+        };
+        auto load_data = [&](int i, const int (&info)[2], float4 (&v)[2][2]) {
+            const int c = i % nch;
+#pragma unroll
+            for (int h = 0; h < 2; ++h)
+#pragma unroll
+                for (int e = 0; e < 2; ++e) {
+                    const int k = c * TC_KC + 4 * (kq0 + 4 * e);
+                    v[h][e] = (i < n_items && info[h] >= 0)
+                                  ? *reinterpret_cast<const float4*>(M + (size_t)(info[h] >> 3) + k)
+                                  : make_float4(0.f, 0.f, 0.f, 0.f);
+                }
+        };
+        load_info(0, f[0]);
+        load_info(1, f[1]);
+        load_info(2, f[2]);
+        load_data(0, f[0], d[0]);
+        load_data(1, f[1], d[1]);
+        bool stop = false;
+        for (int base = 0; base < n_items && !stop; base += 3) {
+#pragma unroll
+            for (int u = 0; u < 3; ++u) {
+                const int i = base + u;
+                if (i >= n_items || stop) break;
+                const int sa = u, sc = (u + 2) % 3;
+                const int st = i % NST, k = i / NST, c = i % nch;
+                load_data(i + 2, f[sc], d[sc]);
+                // warp-uniform decisions: the warp's lanes take every branch together
+                const bool okw = k == 0 || mbar_wait_ab(empty(st), (uint32_t)((k - 1) & 1), abort_flag);
+                if (!__all_sync(0xffffffffu, okw)) {
+                    if (lane == 0) fail(2);
+                    stop = true;
+                    break;
+                }
+                if (__any_sync(0xffffffffu, *abort_flag != 0)) { stop = true; break; }
+#pragma unroll
+                for (int e = 0; e < 2; ++e) {
+                    const int kq = 4 * (kq0 + 4 * e);
+                    const int k0 = c * TC_KC + kq;
+                    const uint32_t nm_a = coef_nm_bits(k0 >> 1), nm_b = coef_nm_bits((k0 >> 1) + 1);
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const int row = 16 * pw + 8 * h + r7;
+                        float4 x = f[sa][h] >= 0 ? apply_signs(d[sa][h][e], sign_bits(nm_a, nm_b, f[sa][h] & 7))
+                                                 : d[sa][h][e];
+                        if (k0 + 0 >= R) x.x = 0.f;
+                        if (k0 + 1 >= R) x.y = 0.f;
+                        if (k0 + 2 >= R) x.z = 0.f;
+                        if (k0 + 3 >= R) x.w = 0.f;
+                        const float4 hi = make_float4(tf32_hi(x.x), tf32_hi(x.y), tf32_hi(x.z), tf32_hi(x.w));
+                        *reinterpret_cast<float4*>(xh(st) + cm_index(row, kq)) = hi;
+                        if (prods == 3)
+                            *reinterpret_cast<float4*>(xl(st) + cm_index(row, kq)) =
+                                make_float4(x.x - hi.x, x.y - hi.y, x.z - hi.z, x.w - hi.w);
+                    }
+                }
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                __syncwarp();
+                if (lane == 0) mbar_arrive(full(st));
+                load_info(i + 3, f[sa]);
             }
         }
+    } else {
+        // ---------------- epilogue groups
+        // with one accumulator a single group drains every tile, so that each group waits
+        // on the phases of its buffers in order
+        const int EG = NB >= 2 ? 2 : 1;
+        const int eg = (warp - TC_EPI0) >> 2;  // group 0 or 1
+        const int quad = warp & 3;             // TMEM lane quadrant of this warp
+        float* E = epi + (warp - TC_EPI0) * 32 * EPI_LD;
+        for (int j = eg; eg < EG && j < my_tiles; j += EG) {
+            const int b = j % NB, u = j / NB;
+            const bool okw = mbar_wait_ab(acc_full(b), (uint32_t)(u & 1), abort_flag);
+            if (!__all_sync(0xffffffffu, okw)) {
+                if (lane == 0) fail(5);
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            const int t = tile_of(j);
+            // destination row info of the 4 rows (lane >> 3) + 4 pass this lane writes, per pass
+            for (int cb = 0; cb < R; cb += 32) {
+                uint32_t v[32];
+                const uint32_t a = taddr + (uint32_t)b * buf_cols + ((uint32_t)(32 * quad) << 16) + (uint32_t)cb;
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                    "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                    : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                      "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
+                      "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]),
+                      "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]),
+                      "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+                    : "r"(a));
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+                for (int q = 0; q < 32; ++q) E[lane * EPI_LD + q] = __uint_as_float(v[q]);
+                __syncwarp();
+                const int col = cb + 4 * (lane & 7);
+                const uint32_t nm_a = coef_nm_bits(col >> 1), nm_b = coef_nm_bits((col >> 1) + 1);
+#pragma unroll
+                for (int pass = 0; pass < 8; ++pass) {
+                    const int rr = 4 * pass + (lane >> 3);
+                    const int info = dst_info[(size_t)t * TC_ROWS + 32 * quad + rr];
+                    if (info >= 0 && col < R) {
+                        const float* e = E + rr * EPI_LD + 4 * (lane & 7);
+                        float4 w = apply_signs(make_float4(e[0], e[1], e[2], e[3]), sign_bits(nm_a, nm_b, info & 7));
+                        if (col + 1 >= R) w.y = 0.f;
+                        if (col + 2 >= R) w.z = 0.f;
+                        if (col + 3 >= R) w.w = 0.f;
+                        atomicAdd(reinterpret_cast<float4*>(L + (size_t)(info >> 3) + col), w);
+                    }
+                }
+                __syncwarp();
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;");
+            __syncwarp();
+            if (lane == 0) mbar_arrive(acc_empty(b));
+        }
     }
-    // the epilogue's TMEM reads finish before the next tile's MMAs overwrite the accumulator
+    __syncthreads();
+    // drain what this CTA issued before TMEM is released (waits on completed phases return at once)
+    if (tid == 0) {
+        for (int i = issued_tma - NST > 0 ? issued_tma - NST : 0; i < issued_tma; ++i)
+            mbar_wait(full(i % NST), (uint32_t)((i / NST) & 1));
+    }
+    if (tid == 32) {
+        for (int i = issued_mma - NST > 0 ? issued_mma - NST : 0; i < issued_mma; ++i)
+            mbar_wait(empty(i % NST), (uint32_t)((i / NST) & 1));
+    }
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;");
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(512));
+}
+
+// Row tables of the tensor-core tiles (see k_m2l_tc).
+template <int NC>
+__global__ void k_tc_rowinfo(const int4* tiles, int ntiles, const int* pt, const int* ps, const int* prefl, int* src_info,
+                             int* dst_info) {
+    const int t = blockIdx.x, r = threadIdx.x;
+    if (t >= ntiles || r >= TC_ROWS) return;
+    const int4 tile = tiles[t];
+    int si = -1, di = -1;
+    if (r < tile.z * NC) {
+        const int pr = tile.y + r / NC, comp = r % NC;
+        si = (int)(((size_t)ps[pr] * NC + comp) * ESTRIDE) * 8 + prefl[pr];
+        di = (int)(((size_t)pt[pr] * NC + comp) * ESTRIDE) * 8 + prefl[pr];
     }
-    asm volatile("tcgen05.fence::before_thread_sync;");
-    __syncthreads();
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(tcols));
+    src_info[(size_t)t * TC_ROWS + r] = si;
+    dst_info[(size_t)t * TC_ROWS + r] = di;
 }
 
 }  // namespace
 
-size_t m2l_tc_smem(int p) {
-    const int R = 2 * ncoef(p);
-    const int Np = (R + 15) & ~15;
-    return (size_t)(2 * TC_ROWS * TC_KC + 2 * Np * TC_KC) * sizeof(float) + 64;
-}
+size_t m2l_tc_smem(int p) { return tc_layout(p).bytes(); }
 
 int build_m2l_tc(fmmbem_handle* h) {
     if (!h->m2l_tables) return 0;
+    // row tables pack (offset * 8 + reflection) into an int
+    if ((double)h->n_cells * h->ncomp * ESTRIDE * 8.0 >= 2147483647.0) return 0;
     const int pmax = h->opts.p_max;
     const int nr = 2 * ncoef(pmax);
     const int rows_max = (nr + 15) & ~15;
@@ -276,9 +488,21 @@ int build_m2l_tc(fmmbem_handle* h) {
     FMM_LAUNCHED();
     h->tc_stride = per_tab;
     h->tc_rows_max = rows_max;
+    FMM_CU(cudaMalloc((void**)&h->tc_src_info, sizeof(int) * (size_t)h->n_tiles_tc * TC_ROWS));
+    FMM_CU(cudaMalloc((void**)&h->tc_dst_info, sizeof(int) * (size_t)h->n_tiles_tc * TC_ROWS));
+    if (h->n_tiles_tc > 0) {
+        if (h->ncomp == 1)
+            k_tc_rowinfo<1><<<h->n_tiles_tc, TC_ROWS, 0, h->stream>>>(h->m2l_tiles_tc, h->n_tiles_tc, h->m2l_pt, h->m2l_ps,
+                                                                     h->m2l_refl, h->tc_src_info, h->tc_dst_info);
+        else
+            k_tc_rowinfo<4><<<h->n_tiles_tc, TC_ROWS, 0, h->stream>>>(h->m2l_tiles_tc, h->n_tiles_tc, h->m2l_pt, h->m2l_ps,
+                                                                     h->m2l_refl, h->tc_src_info, h->tc_dst_info);
+        FMM_LAUNCHED();
+    }
     FMM_CU(cudaMalloc((void**)&h->tc_err, sizeof(int)));
     FMM_CU(cudaMemsetAsync(h->tc_err, 0, sizeof(int), h->stream));
-    const size_t smax = m2l_tc_smem(pmax);
+    size_t smax = 0;
+    for (int q = 1; q <= pmax; ++q) smax = std::max(smax, m2l_tc_smem(q));
     FMM_CU(cudaFuncSetAttribute(k_m2l_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smax));
     FMM_CU(cudaFuncSetAttribute(k_m2l_tc<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smax));
     int dev = 0;
@@ -293,16 +517,17 @@ int m2l_tc(fmmbem_handle* h, int p) {
     const float* M = reinterpret_cast<const float*>(h->M);
     FMM_CU(cudaMemsetAsync(L, 0, sizeof(float) * (size_t)h->n_cells * h->ncomp * ESTRIDE, h->stream));
     const size_t sm = m2l_tc_smem(p);
-    const int R = 2 * ncoef(p), Np = (R + 15) & ~15;
-    const int tcols = Np <= 32 ? 32 : (Np <= 64 ? 64 : (Np <= 128 ? 128 : (Np <= 256 ? 256 : 512)));
-    const int per_sm = std::max(1, std::min({4, (int)((220u << 10) / sm), 512 / tcols}));
-    const int grid = std::min(h->n_tiles_tc, h->n_sm * per_sm);
+    const int grid = std::min(h->n_tiles_tc, h->n_sm);  // persistent: one CTA per SM (512 TMEM columns each)
+    const int prods = 3;
+    if (grid <= 0) return 0;
     if (h->ncomp == 1)
-        k_m2l_tc<1><<<grid, 128, sm, h->stream>>>(p, h->m2l_tiles_tc, h->n_tiles_tc, h->m2l_pt, h->m2l_ps, h->m2l_refl, h->sign_f, h->tab_tc,
-                                                           h->tc_stride, h->tc_rows_max, M, L, h->tc_err);
+        k_m2l_tc<1><<<grid, TC_THREADS, sm, h->stream>>>(p, prods, h->m2l_tiles_tc, h->n_tiles_tc, h->tc_src_info,
+                                                        h->tc_dst_info, h->tab_tc, h->tc_stride, h->tc_rows_max, M, L,
+                                                        h->tc_err);
     else
-        k_m2l_tc<4><<<grid, 128, sm, h->stream>>>(p, h->m2l_tiles_tc, h->n_tiles_tc, h->m2l_pt, h->m2l_ps, h->m2l_refl, h->sign_f, h->tab_tc,
-                                                           h->tc_stride, h->tc_rows_max, M, L, h->tc_err);
+        k_m2l_tc<4><<<grid, TC_THREADS, sm, h->stream>>>(p, prods, h->m2l_tiles_tc, h->n_tiles_tc, h->tc_src_info,
+                                                        h->tc_dst_info, h->tab_tc, h->tc_stride, h->tc_rows_max, M, L,
+                                                        h->tc_err);
     FMM_LAUNCHED();
     return 0;
 }

@@ -927,6 +927,26 @@ int build_geometry_tree_lists(fmmbem_handle* h, const fmmbem_mesh* mesh) {
         k_p2p_records<<<(nc + T - 1) / T, T, 0, st>>>(h->p2p_ptr, h->p2p_src, h->cell_cs, h->cell_range, nc, K,
                                                      h->p2p_rec, h->p2p_off, h->p2p_len);
         FMM_LAUNCHED();
+        {
+            // leaves by decreasing near-field work (targets x stream length), so that the
+            // source-lane kernel's blocks, issued in order, finish together
+            const int nl = h->n_leaves;
+            std::vector<int> lv(nl), len(nc);
+            std::vector<int2> rg(nc);
+            FMM_CU(cudaMemcpyAsync(lv.data(), h->leaves, sizeof(int) * nl, cudaMemcpyDeviceToHost, st));
+            FMM_CU(cudaMemcpyAsync(len.data(), h->p2p_len, sizeof(int) * nc, cudaMemcpyDeviceToHost, st));
+            FMM_CU(cudaMemcpyAsync(rg.data(), h->cell_range, sizeof(int2) * nc, cudaMemcpyDeviceToHost, st));
+            FMM_CU(cudaStreamSynchronize(st));
+            std::vector<long long> cost(nc, 0);
+            for (int c : lv) {
+                const long long t = rg[c].y - rg[c].x;
+                cost[c] = t * ((long long)len[c] + t * K);
+            }
+            std::stable_sort(lv.begin(), lv.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+            FMM_TRY(dalloc(&h->p2p_order, nl));
+            FMM_CU(cudaMemcpyAsync(h->p2p_order, lv.data(), sizeof(int) * nl, cudaMemcpyHostToDevice, st));
+            FMM_CU(cudaStreamSynchronize(st));
+        }
         // stage plans of the bulk-copy near field (leaves of at most 1024 Gauss points)
         if ((int64_t)K * h->max_leaf_panels <= 1024) {
             int* nst = nullptr;

@@ -232,3 +232,28 @@ def test_m2l_formulations_agree(torch_cuda, sphere1280, precision):
             ys.append(y.cpu().numpy())
         for y in ys[1:]:
             assert rel(y, ys[0]) < tol, p
+
+
+@pytest.mark.parametrize("ncrit", [40, 150, 600])
+def test_p2p_variants_agree(torch_cuda, sphere1280, ncrit):
+    """The four near-field schedules compute the same FP32 sums (summation order differs):
+    shared tiles, sliced L1, bulk-copied stages and source lanes. ncrit 600 puts up to
+    150 targets in a leaf (several target passes), ncrit 40 gives leaves with more P2P
+    pairs than one shared-memory chunk of records holds."""
+    torch = torch_cuda
+    from paper_1506_05957_gb300 import FMMBEM_MIXED
+    s = sphere1280
+    h = _h(torch, s["v"], s["t"], ncrit=ncrit, precision=FMMBEM_MIXED)
+    x = _dev(torch, np.random.default_rng(9).standard_normal(h.n))
+    ref = s["A"] @ x.cpu().numpy()
+    ys = []
+    for variant in (0, 1, 2, 3):
+        h.set_p2p_variant(variant)
+        y = torch.zeros_like(x)
+        h.matvec(16, x, y)
+        ys.append(y.cpu().numpy())
+    for v, y in enumerate(ys):
+        assert rel(y, ys[0]) < 2e-6, v
+        assert rel(y, ref) < 1e-5, v
+    with pytest.raises(Exception):
+        h.set_p2p_variant(4)
