@@ -92,8 +92,10 @@ int fmmbem_default_opts(fmmbem_opts* opts);
  * Build everything the mat-vec needs (Sec. 2.3 and 2.5): panel geometry and
  * K-point Gauss points, a Morton-sorted octree over panels whose leaves hold
  * at most `ncrit` Gauss points, dual-tree-traversal interaction lists with the
- * acceptance criterion (R_a + R_b) < theta |c_a - c_b| (R = box half-diagonal
- * plus the largest panel extent), and the sparse table of near-singular and
+ * acceptance criterion (R_a + R_b) < theta |c_a - c_b| (c = box centre; R_a = the
+ * largest distance from c_a to a collocation point of the target cell a, R_b = the
+ * largest distance from c_b to a Gauss point of the source cell b: the cluster
+ * sizes of eq. multipole_error), and the sparse table of near-singular and
  * self-panel corrections (accurate integral minus the K-point sum), in FP64.
  *   mesh      : host mesh (see fmmbem_mesh)
  *   kernel    : FMMBEM_LAPLACE or FMMBEM_STOKES
@@ -133,9 +135,9 @@ int fmmbem_set_m2l_mode(fmmbem_handle* h, int mode);
  * 0 = source tiles staged in shared memory, targets held per lane;
  * 1 = (target, source slice) per thread, sources read through L1;
  * 2 = as 1, with each pair's sources bulk-copied into double-buffered shared memory
- *     (default; used when a leaf holds at most 1024 Gauss points, else 1);
- * 3 = one warp per target leaf with the lanes over its source stream and the targets
- *     looped in registers.
+ *     (used when a leaf holds at most 1024 Gauss points, else 1);
+ * 3 = one block per target leaf, its warps' lanes over the leaf's source stream and the
+ *     targets looped in registers (default).
  * Returns FMMBEM_EINVAL for any other value. */
 int fmmbem_set_p2p_variant(fmmbem_handle* h, int variant);
 

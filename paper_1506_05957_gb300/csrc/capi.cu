@@ -252,10 +252,10 @@ int fmmbem_relaxed_p(double eta, double rho_prev, int p_initial, int p_min) {
 
 void fmmbem_destroy(fmmbem_handle* h) {
     if (!h) return;
-    void* bufs[] = {h->perm, h->tgt_d, h->tgt_f, h->nrm_d, h->verts, h->src_d, h->src_f, h->src_rel, h->tgt_rel, h->src_w, h->cell_cs, h->cell_range,
+    void* bufs[] = {h->perm, h->tgt_d, h->tgt_f, h->nrm_d, h->verts, h->src_d, h->src_f, h->src_rel, h->tgt_rel, h->src_w, h->cell_cs, h->cell_range, h->cell_rad,
                     h->cell_child, h->cell_level, h->cell_parent, h->leaves, h->parents, h->leaf_class, h->m2l_ptr, h->m2l_src, h->p2p_ptr,
                     h->p2p_src, h->p2p_rec, h->p2p_off, h->p2p_len, h->p2p_order, h->p2p_cnt, h->p2p_toff, h->stage_ptr, h->stage_first, h->stage_bytes, h->corr_ptr, h->corr_col, h->corr_sl, h->corr_dl, h->oct_d, h->oct_f, h->M, h->L,
-                    h->xs, h->ys, h->ynear, h->m2l_pt, h->m2l_ps, h->m2l_refl, h->sign_f, h->sign_d, h->m2l_tiles, h->tab_d, h->tab_f, h->tab_tc, h->m2l_tiles_tc, h->tc_src_info, h->tc_dst_info, h->tc_err, h->kerr, h->V, h->kw, h->xfix, h->kb, h->kx, h->kr, h->kpart, h->kh, h->kyv, h->arn_bar};
+                    h->xs, h->ys, h->ynear, h->m2l_pt, h->m2l_ps, h->m2l_refl, h->sign_f, h->sign_d, h->m2l_tiles, h->tab_d, h->tab_f, h->tab_tc, h->m2l_tiles_tc, h->tc_src_info, h->tc_dst_info, h->tree_tab_tc, h->tree_tiles, h->tree_info, h->tc_err, h->kerr, h->V, h->kw, h->xfix, h->kb, h->kx, h->kr, h->kpart, h->kh, h->kyv, h->arn_bar};
     for (void* b : bufs)
         if (b) cudaFree(b);
     if (h->kh_host) cudaFreeHost(h->kh_host);
@@ -343,7 +343,8 @@ int fmmbem_create(const fmmbem_mesh* mesh, int kernel, int gauss_k, int ncrit, d
         return fail(rc);
     h->arn_blocks = arnoldi_blocks();
     if (h->arn_blocks < 1) { fmmbem_set_error("cooperative Arnoldi kernel cannot be resident"); return fail(FMMBEM_EDEVICE); }
-    if ((rc = dalloc(&h->kpart, (size_t)std::max(96, h->arn_blocks) * (o.restart + 2))) < 0) return fail(rc);
+    // partial dots: the fused Arnoldi step uses three areas of [64][blocks]; the restart dots [m+2][96]
+    if ((rc = dalloc(&h->kpart, std::max((size_t)96 * (o.restart + 2), (size_t)3 * 64 * h->arn_blocks))) < 0) return fail(rc);
     if ((rc = dalloc(&h->arn_bar, 2)) < 0) return fail(rc);
     if (cudaMemsetAsync(h->arn_bar, 0, 2 * sizeof(unsigned), h->stream) != cudaSuccess) return fail(FMMBEM_EDEVICE);
     if (cudaHostAlloc((void**)&h->arn_out_host, sizeof(double) * (2 * 65 + 1), cudaHostAllocMapped) != cudaSuccess ||

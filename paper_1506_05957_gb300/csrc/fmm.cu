@@ -483,6 +483,9 @@ int far_field_t(fmmbem_handle* h, int p) {
                                                          h->origin[0], h->origin[1], h->origin[2], M);
     FMM_LAUNCHED();
     prof_end(h, FMMBEM_PASS_P2M, 1);
+    // tensor-core tree translations in the mixed-precision M2L-TENSOR mode
+    const bool tree_tc_on = std::is_same<T, float>::value && h->m2l_mode == FMMBEM_M2L_TENSOR && h->m2l_tc_ready &&
+                            h->tree_tiles != nullptr;
     // M2M, deepest non-leaf level first
     prof_begin(h, FMMBEM_PASS_M2M);
     int nl = 0;
@@ -490,9 +493,14 @@ int far_field_t(fmmbem_handle* h, int p) {
     for (int l = h->n_levels - 2; l >= 0; --l) {
         const int pb = h->parent_start[l], pe = h->parent_start[l + 1];
         if (pe == pb) continue;
-        k_m2m<T, NC><<<pe - pb, TREE_THREADS, sm_m2m, st>>>(p, h->parents + pb, h->cell_cs, h->cell_child, oct, M);
-        FMM_LAUNCHED();
-        ++nl;
+        if (tree_tc_on) {
+            FMM_TRY(tree_tc(h, p, l, 0));
+            nl += 2;
+        } else {
+            k_m2m<T, NC><<<pe - pb, TREE_THREADS, sm_m2m, st>>>(p, h->parents + pb, h->cell_cs, h->cell_child, oct, M);
+            FMM_LAUNCHED();
+            ++nl;
+        }
     }
     prof_end(h, FMMBEM_PASS_M2M, nl);
     // M2L
@@ -513,8 +521,12 @@ int far_field_t(fmmbem_handle* h, int p) {
     for (int l = 0; l + 1 < h->n_levels; ++l) {
         const int pb = h->parent_start[l], pe = h->parent_start[l + 1];
         if (pe == pb) continue;
-        k_l2l<T, NC><<<pe - pb, TREE_THREADS, sm_l2l, st>>>(p, h->parents + pb, h->cell_cs, h->cell_child, oct, L);
-        FMM_LAUNCHED();
+        if (tree_tc_on) {
+            FMM_TRY(tree_tc(h, p, l, 1));
+        } else {
+            k_l2l<T, NC><<<pe - pb, TREE_THREADS, sm_l2l, st>>>(p, h->parents + pb, h->cell_cs, h->cell_child, oct, L);
+            FMM_LAUNCHED();
+        }
         ++nl2;
     }
     prof_end(h, FMMBEM_PASS_L2L, nl2);

@@ -51,6 +51,7 @@ struct fmmbem_handle {
     std::vector<int> level_start;  // host, [n_levels + 1]
     double4* cell_cs = nullptr;    // [n_cells] centre (x,y,z) and side
     int2* cell_range = nullptr;    // [n_cells] sorted panel range [begin, end)
+    double2* cell_rad = nullptr;   // [n_cells] cluster radii about the centre: (targets, Gauss points)
     int2* cell_child = nullptr;    // [n_cells] first child, number of children (0 = leaf)
     int* cell_level = nullptr;
     int* cell_parent = nullptr;
@@ -88,6 +89,12 @@ struct fmmbem_handle {
     int* tc_src_info = nullptr;   // [n_tiles_tc][128]: source row offset * 8 + reflection (-1: empty row)
     int* tc_dst_info = nullptr;   // [n_tiles_tc][128]: target row offset * 8 + reflection
     int* tc_err = nullptr;        // set by the kernel if a bounded wait gives up
+    // M2M / L2L on the tensor cores: one canonical operator each (TC layout), per-level tiles
+    float* tree_tab_tc = nullptr;  // [2][tc_stride]: op 0 M2M, op 1 L2L
+    int4* tree_tiles = nullptr;    // [2][n_tree_tiles]: operator index per tile (M2M tiles, then L2L tiles)
+    int* tree_info = nullptr;      // [4][n_tree_tiles][128]: M2M src, M2M dst, L2L src, L2L dst row tables
+    int n_tree_tiles = 0;
+    std::vector<int> tree_tile_start;  // host, tiles of parent level l: [start[l], start[l+1])
     int n_sm = 152;
     int* kerr = nullptr;          // same, for the near-field bulk-copy kernel
     int* p2p_ptr = nullptr;  // [n_cells + 1]
@@ -104,7 +111,7 @@ struct fmmbem_handle {
     int64_t n_stages = 0;
     int max_leaf_panels = 0;
     int* p2p_order = nullptr;   // [n_leaves] leaves by decreasing near-field work (source-lane kernel order)
-    int p2p_variant = 2;        // 0: shared stream tiles, 1: sliced L1 broadcast, 2: bulk-copied stages, 3: source lanes
+    int p2p_variant = 3;        // 0: shared stream tiles, 1: sliced L1 broadcast, 2: bulk-copied stages, 3: source lanes
 
     // near-singular / self corrections (CSR by sorted target panel), FP64
     int* corr_ptr = nullptr;   // [N + 1]
@@ -162,6 +169,7 @@ int m2l_gemm(fmmbem_handle* h, int p, bool fp64);
 // m2l_tc.cu
 int build_m2l_tc(fmmbem_handle* h);
 int m2l_tc(fmmbem_handle* h, int p);
+int tree_tc(fmmbem_handle* h, int p, int level, int which);
 // fmm.cu
 int far_field(fmmbem_handle* h, int p, bool fp64);
 int far_eval_add(fmmbem_handle* h, int p, bool fp64, double* y_sorted, double scale);

@@ -154,10 +154,14 @@ __global__ void __launch_bounds__(ARN_THREADS) k_arnoldi(double* V, int64_t n, i
     const int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
     const int64_t i0 = (int64_t)blockIdx.x * chunk, i1 = min(n, i0 + chunk);
     const unsigned nb = gridDim.x;
+    // each phase has its own partial-sum area, so one grid barrier per phase suffices:
+    // a block's w rows are read and written by that block alone
+    const size_t parea = (size_t)ARN_MAXV * gridDim.x;
     for (int pass = 0; pass < 2; ++pass) {
-        arn_partials(V, n, nv, w, i0, i1, partial);
+        double* part = partial + pass * parea;
+        arn_partials(V, n, nv, w, i0, i1, part);
         if (!grid_barrier(bar_count, bar_gen, nb, err)) return;
-        arn_reduce(partial, nv, hs);
+        arn_reduce(part, nv, hs);
         if (blockIdx.x == 0)
             for (int j = threadIdx.x; j < nv; j += ARN_THREADS) out[pass * (ARN_MAXV + 1) + j] = hs[j];
         for (int64_t i = i0 + threadIdx.x; i < i1; i += ARN_THREADS) {
@@ -165,12 +169,12 @@ __global__ void __launch_bounds__(ARN_THREADS) k_arnoldi(double* V, int64_t n, i
             for (int j = 0; j < nv; ++j) t += hs[j] * V[(int64_t)j * n + i];
             w[i] -= t;
         }
-        // the next pass reads partial[] again: every block must have finished reducing
-        if (!grid_barrier(bar_count, bar_gen, nb, err)) return;
+        __syncthreads();  // hs is rewritten by the next phase's reduction
     }
-    arn_partials(w, n, 1, w, i0, i1, partial);
+    double* part = partial + 2 * parea;
+    arn_partials(w, n, 1, w, i0, i1, part);
     if (!grid_barrier(bar_count, bar_gen, nb, err)) return;
-    arn_reduce(partial, 1, hs);
+    arn_reduce(part, 1, hs);
     const double nrm2 = hs[0];
     if (blockIdx.x == 0 && threadIdx.x == 0) out[2 * (ARN_MAXV + 1)] = nrm2;
     const double hn = sqrt(nrm2);

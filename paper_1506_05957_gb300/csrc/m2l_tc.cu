@@ -15,7 +15,9 @@
 // and added to the target expansions with row-contiguous float4 atomics.
 #include <algorithm>
 #include <type_traits>
+#include <vector>
 #include "handle.cuh"
+#include "harmonics.cuh"
 
 namespace fmmbem {
 
@@ -116,13 +118,14 @@ constexpr int TC_THREADS = 32 * TC_WARPS;
 constexpr int TC_PROD0 = 2, TC_NPROD = 8, TC_EPI0 = 10;
 constexpr int EPI_LD = 33;  // padded row length of the epilogue transpose buffer
 constexpr int TC_SMEM_BUDGET = 222 * 1024;
+constexpr int TC_SIGN_TAB = 16 * 8;  // (K chunk, k-quad) entries: chunks of 32 reals up to 2 ncoef(P_MAX) <= 320
 
 struct TcLayout {
     int nst, nb, np;
     __host__ __device__ int stage_floats() const { return 2 * TC_ROWS * TC_KC + 2 * np * TC_KC; }
     __host__ __device__ int epi_floats() const { return 8 * 32 * EPI_LD; }
     __host__ __device__ size_t bytes() const {
-        return (size_t)(nst * stage_floats() + epi_floats()) * sizeof(float) + 16 * 8 + 64;
+        return (size_t)(nst * stage_floats() + epi_floats()) * sizeof(float) + 16 * 8 + 64 + 2 * TC_SIGN_TAB * 4;
     }
 };
 
@@ -134,7 +137,9 @@ __host__ __device__ inline TcLayout tc_layout(int p) {
     t.nst = 1;
     for (int n = 4; n >= 1; --n) {
         t.nst = n;
-        if ((size_t)(n * t.stage_floats() + t.epi_floats()) * sizeof(float) + 16 * 8 + 64 <= (size_t)TC_SMEM_BUDGET) break;
+        if ((size_t)(n * t.stage_floats() + t.epi_floats()) * sizeof(float) + 16 * 8 + 64 + 2 * TC_SIGN_TAB * 4 <=
+            (size_t)TC_SMEM_BUDGET)
+            break;
     }
     return t;
 }
@@ -154,6 +159,13 @@ __device__ __forceinline__ uint32_t sign_bits(uint32_t nm_a, uint32_t nm_b, int 
     const uint32_t ra = (z & nm_a) ^ (x & (nm_a >> 1)), rb = (z & nm_b) ^ (x & (nm_b >> 1));
     const uint32_t ia = ra ^ y ^ x, ib = rb ^ y ^ x;
     return ra | (ia << 1) | (rb << 2) | (ib << 3);
+}
+__device__ __forceinline__ float4 apply_zero(float4 v, uint32_t z) {
+    if (z & 1u) v.x = 0.f;
+    if (z & 2u) v.y = 0.f;
+    if (z & 4u) v.z = 0.f;
+    if (z & 8u) v.w = 0.f;
+    return v;
 }
 __device__ __forceinline__ float4 apply_signs(float4 v, uint32_t b) {
     v.x = __uint_as_float(__float_as_uint(v.x) ^ ((b & 1u) << 31));
@@ -201,6 +213,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_m2l_tc(int p, int prods, cons
     uint64_t* bar = reinterpret_cast<uint64_t*>(epi + lay.epi_floats());  // full[4], empty[4], acc_full[4], acc_empty[4]
     uint32_t* taddr_slot = reinterpret_cast<uint32_t*>(bar + 16);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(taddr_slot + 1);
+    // sgn_tab[c * 8 + kq]: bits 4q..4q+3 = sign flips of the 4 reals at k = 32 c + 4 kq under
+    // reflection q; zm_tab: bit e set when k + e >= R (coefficient of degree > p, zeroed)
+    uint32_t* sgn_tab = reinterpret_cast<uint32_t*>(smem) + (lay.bytes() - 2 * TC_SIGN_TAB * 4) / 4;
+    uint32_t* zm_tab = sgn_tab + TC_SIGN_TAB;
     auto full = [&](int st) { return smem_u32(&bar[st]); };
     auto empty = [&](int st) { return smem_u32(&bar[4 + st]); };
     auto acc_full = [&](int b) { return smem_u32(&bar[8 + b]); };
@@ -211,6 +227,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_m2l_tc(int p, int prods, cons
     auto tl = [&](int st) { return stage0 + st * sf + 2 * TC_ROWS * TC_KC + Np * TC_KC; };
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    for (int e = tid; e < TC_SIGN_TAB; e += blockDim.x) {
+        const int k0 = 4 * e;  // e = c * 8 + kq  ->  k0 = 32 c + 4 kq
+        const uint32_t nm_a = coef_nm_bits(k0 >> 1), nm_b = coef_nm_bits((k0 >> 1) + 1);
+        uint32_t sg = 0;
+        for (int q = 0; q < 8; ++q) sg |= sign_bits(nm_a, nm_b, q) << (4 * q);
+        sgn_tab[e] = sg;
+        zm_tab[e] = (k0 >= R ? 1u : 0u) | (k0 + 1 >= R ? 2u : 0u) | (k0 + 2 >= R ? 4u : 0u) | (k0 + 3 >= R ? 8u : 0u);
+    }
     if (tid == 0) {
         for (int st = 0; st < 4; ++st) {
             asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(full(st)), "r"(TC_NPROD + 1));
@@ -243,13 +267,28 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_m2l_tc(int p, int prods, cons
     if (warp == 0) {
         // ---------------- operator copies
         if (lane == 0) {
+            // the tile record of the next tile is loaded one tile ahead, and the next tile's
+            // operator chunks are prefetched into L2 when this tile starts, so neither the
+            // record load nor a DRAM miss sits between a free stage and its refill
+            const uint32_t bytes = prods == 3 ? 2 * chunk_bytes : chunk_bytes;
+            int4 tile = my_tiles > 0 ? tiles[tile_of(0)] : make_int4(0, 0, 0, 0);
+            int4 next_tile = my_tiles > 1 ? tiles[tile_of(1)] : tile;
+            int4 next2_tile = my_tiles > 2 ? tiles[tile_of(2)] : next_tile;
+            int c = 0, st = 0, k = 0, j = 0;
             for (int i = 0; i < n_items; ++i) {
-                const int st = i % NST, k = i / NST;
+                if (c == 0 && j + 1 < my_tiles) {
+                    const float* nt = tab + (size_t)next_tile.x * tab_stride;
+                    for (int cc = 0; cc < nch; ++cc) {
+                        const float* q = nt + (size_t)cc * 2 * rows_max * TC_KC;
+                        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(q), "r"(chunk_bytes) : "memory");
+                        if (prods == 3)
+                            asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(q + (size_t)rows_max * TC_KC),
+                                         "r"(chunk_bytes)
+                                         : "memory");
+                    }
+                }
                 if (k > 0 && !mbar_wait_ab(empty(st), (uint32_t)((k - 1) & 1), abort_flag)) { fail(1); break; }
                 if (*abort_flag) break;
-                const int4 tile = tiles[tile_of(i / nch)];
-                const int c = i % nch;
-                const uint32_t bytes = prods == 3 ? 2 * chunk_bytes : chunk_bytes;
                 asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(full(st)), "r"(bytes) : "memory");
                 const float* src = tab + (size_t)tile.x * tab_stride + (size_t)c * 2 * rows_max * TC_KC;
                 asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
@@ -262,6 +301,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_m2l_tc(int p, int prods, cons
                                  "l"(src + (size_t)rows_max * TC_KC), "r"(chunk_bytes), "r"(full(st))
                                  : "memory");
                 issued_tma = i + 1;
+                if (++st == NST) { st = 0; ++k; }
+                if (++c == nch) {
+                    c = 0;
+                    ++j;
+                    tile = next_tile;
+                    next_tile = next2_tile;
+                    if (j + 2 < my_tiles) next2_tile = tiles[tile_of(j + 2)];
+                }
             }
         }
     } else if (warp == 1) {
@@ -270,9 +317,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_m2l_tc(int p, int prods, cons
             const int n1 = Np <= 256 ? Np : 256;
             const uint32_t id1 = idesc_tf32(TC_ROWS, n1);
             const uint32_t id2 = Np > 256 ? idesc_tf32(TC_ROWS, Np - 256) : 0u;
+            int st = 0, k = 0, c = 0, b = 0, u = 0;  // stage, stage use, chunk, accumulator, accumulator use
             for (int i = 0; i < n_items; ++i) {
-                const int st = i % NST, k = i / NST;
-                const int j = i / nch, c = i % nch, b = j % NB, u = j / NB;
                 if (c == 0 && u > 0 && !mbar_wait_ab(acc_empty(b), (uint32_t)((u - 1) & 1), abort_flag)) { fail(3); break; }
                 if (!mbar_wait_ab(full(st), (uint32_t)(k & 1), abort_flag)) { fail(4); break; }
                 asm volatile("tcgen05.fence::after_thread_sync;");
@@ -304,6 +350,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_m2l_tc(int p, int prods, cons
                                      acc_full(b))
                                  : "memory");
                 issued_mma = i + 1;
+                if (++st == NST) { st = 0; ++k; }
+                if (++c == nch) {
+                    c = 0;
+                    if (++b == NB) { b = 0; ++u; }
+                }
             }
         }
     } else if (warp < TC_EPI0) {
@@ -312,32 +363,47 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_m2l_tc(int p, int prods, cons
         // slot indices are constants): while item i is stored from slot i % 3, the inputs of
         // item i + 1 are in flight in slot (i + 1) % 3, the inputs of item i + 2 are issued into
         // slot (i + 2) % 3 from its row tables (loaded one item earlier), and the row tables
-        // of item i + 3 then go into the freed slot i % 3.
+        // of item i + 3 then go into the freed slot i % 3. Item counters (tile, chunk, stage,
+        // phase) advance incrementally; signs and the order-p mask come from the CTA's tables.
         const int pw = warp - TC_PROD0, r7 = lane & 7, kq0 = lane >> 3;
+        const int row0 = 16 * pw + r7;
         float4 d[3][2][2];
         int f[3][2];
-        auto load_info = [&](int i, int (&info)[2]) {
+        struct Ctr {
+            int j, c;
+            __device__ void next(int nch_) { if (++c == nch_) { c = 0; ++j; } }
+        };
+        auto load_info = [&](const Ctr& t, int (&info)[2]) {
 #pragma unroll
             for (int h = 0; h < 2; ++h)
-                info[h] = i < n_items ? src_info[(size_t)tile_of(i / nch) * TC_ROWS + 16 * pw + 8 * h + r7] : -1;
+                info[h] = t.j < my_tiles ? src_info[(size_t)tile_of(t.j) * TC_ROWS + row0 + 8 * h] : -1;
         };
-        auto load_data = [&](int i, const int (&info)[2], float4 (&v)[2][2]) {
-            const int c = i % nch;
+        auto load_data = [&](const Ctr& t, const int (&info)[2], float4 (&v)[2][2]) {
 #pragma unroll
             for (int h = 0; h < 2; ++h)
 #pragma unroll
                 for (int e = 0; e < 2; ++e) {
-                    const int k = c * TC_KC + 4 * (kq0 + 4 * e);
-                    v[h][e] = (i < n_items && info[h] >= 0)
+                    const int k = t.c * TC_KC + 4 * (kq0 + 4 * e);
+                    v[h][e] = (t.j < my_tiles && info[h] >= 0)
                                   ? *reinterpret_cast<const float4*>(M + (size_t)(info[h] >> 3) + k)
                                   : make_float4(0.f, 0.f, 0.f, 0.f);
                 }
         };
-        load_info(0, f[0]);
-        load_info(1, f[1]);
-        load_info(2, f[2]);
-        load_data(0, f[0], d[0]);
-        load_data(1, f[1], d[1]);
+        Ctr ci{0, 0}, c2{0, 0}, c3{0, 0};  // items i, i + 2, i + 3
+        load_info(c2, f[0]);
+        c2.next(nch);
+        load_info(c2, f[1]);
+        c2.next(nch);
+        load_info(c2, f[2]);
+        c3 = c2;
+        c3.next(nch);
+        {
+            Ctr c0{0, 0}, c1{0, 0};
+            c1.next(nch);
+            load_data(c0, f[0], d[0]);
+            load_data(c1, f[1], d[1]);
+        }
+        int st = 0, ph = 0;  // stage of item i and the number of earlier uses of that stage
         bool stop = false;
         for (int base = 0; base < n_items && !stop; base += 3) {
 #pragma unroll
@@ -345,41 +411,41 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_m2l_tc(int p, int prods, cons
                 const int i = base + u;
                 if (i >= n_items || stop) break;
                 const int sa = u, sc = (u + 2) % 3;
-                const int st = i % NST, k = i / NST, c = i % nch;
-                load_data(i + 2, f[sc], d[sc]);
+                load_data(c2, f[sc], d[sc]);
                 // warp-uniform decisions: the warp's lanes take every branch together
-                const bool okw = k == 0 || mbar_wait_ab(empty(st), (uint32_t)((k - 1) & 1), abort_flag);
+                const bool okw = ph == 0 || mbar_wait_ab(empty(st), (uint32_t)((ph - 1) & 1), abort_flag);
                 if (!__all_sync(0xffffffffu, okw)) {
                     if (lane == 0) fail(2);
                     stop = true;
                     break;
                 }
                 if (__any_sync(0xffffffffu, *abort_flag != 0)) { stop = true; break; }
+                float* xh_s = xh(st);
+                float* xl_s = xl(st);
 #pragma unroll
                 for (int e = 0; e < 2; ++e) {
                     const int kq = 4 * (kq0 + 4 * e);
-                    const int k0 = c * TC_KC + kq;
-                    const uint32_t nm_a = coef_nm_bits(k0 >> 1), nm_b = coef_nm_bits((k0 >> 1) + 1);
+                    const int te = ci.c * 8 + kq0 + 4 * e;
+                    const uint32_t sg = sgn_tab[te], zm = zm_tab[te];
 #pragma unroll
                     for (int h = 0; h < 2; ++h) {
-                        const int row = 16 * pw + 8 * h + r7;
-                        float4 x = f[sa][h] >= 0 ? apply_signs(d[sa][h][e], sign_bits(nm_a, nm_b, f[sa][h] & 7))
-                                                 : d[sa][h][e];
-                        if (k0 + 0 >= R) x.x = 0.f;
-                        if (k0 + 1 >= R) x.y = 0.f;
-                        if (k0 + 2 >= R) x.z = 0.f;
-                        if (k0 + 3 >= R) x.w = 0.f;
+                        const int row = row0 + 8 * h;
+                        const float4 x = apply_zero(apply_signs(d[sa][h][e], (sg >> (4 * (f[sa][h] & 7))) & 15u), zm);
                         const float4 hi = make_float4(tf32_hi(x.x), tf32_hi(x.y), tf32_hi(x.z), tf32_hi(x.w));
-                        *reinterpret_cast<float4*>(xh(st) + cm_index(row, kq)) = hi;
+                        *reinterpret_cast<float4*>(xh_s + cm_index(row, kq)) = hi;
                         if (prods == 3)
-                            *reinterpret_cast<float4*>(xl(st) + cm_index(row, kq)) =
+                            *reinterpret_cast<float4*>(xl_s + cm_index(row, kq)) =
                                 make_float4(x.x - hi.x, x.y - hi.y, x.z - hi.z, x.w - hi.w);
                     }
                 }
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 __syncwarp();
                 if (lane == 0) mbar_arrive(full(st));
-                load_info(i + 3, f[sa]);
+                load_info(c3, f[sa]);
+                ci.next(nch);
+                c2.next(nch);
+                c3.next(nch);
+                if (++st == NST) { st = 0; ++ph; }
             }
         }
     } else {
@@ -399,7 +465,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_m2l_tc(int p, int prods, cons
             }
             asm volatile("tcgen05.fence::after_thread_sync;");
             const int t = tile_of(j);
-            // destination row info of the 4 rows (lane >> 3) + 4 pass this lane writes, per pass
+            // destination row table of this warp's 32 accumulator rows, one per lane, shuffled per pass
+            const int my_info = dst_info[(size_t)t * TC_ROWS + 32 * quad + lane];
             for (int cb = 0; cb < R; cb += 32) {
                 uint32_t v[32];
                 const uint32_t a = taddr + (uint32_t)b * buf_cols + ((uint32_t)(32 * quad) << 16) + (uint32_t)cb;
@@ -417,17 +484,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_m2l_tc(int p, int prods, cons
                 for (int q = 0; q < 32; ++q) E[lane * EPI_LD + q] = __uint_as_float(v[q]);
                 __syncwarp();
                 const int col = cb + 4 * (lane & 7);
-                const uint32_t nm_a = coef_nm_bits(col >> 1), nm_b = coef_nm_bits((col >> 1) + 1);
+                const int te = (cb >> 5) * 8 + (lane & 7);
+                const uint32_t sg = sgn_tab[te], zm = zm_tab[te];
 #pragma unroll
                 for (int pass = 0; pass < 8; ++pass) {
                     const int rr = 4 * pass + (lane >> 3);
-                    const int info = dst_info[(size_t)t * TC_ROWS + 32 * quad + rr];
+                    const int info = __shfl_sync(0xffffffffu, my_info, rr);
                     if (info >= 0 && col < R) {
                         const float* e = E + rr * EPI_LD + 4 * (lane & 7);
-                        float4 w = apply_signs(make_float4(e[0], e[1], e[2], e[3]), sign_bits(nm_a, nm_b, info & 7));
-                        if (col + 1 >= R) w.y = 0.f;
-                        if (col + 2 >= R) w.z = 0.f;
-                        if (col + 3 >= R) w.w = 0.f;
+                        const float4 w =
+                            apply_zero(apply_signs(make_float4(e[0], e[1], e[2], e[3]), (sg >> (4 * (info & 7))) & 15u), zm);
                         atomicAdd(reinterpret_cast<float4*>(L + (size_t)(info >> 3) + col), w);
                     }
                 }
@@ -470,9 +536,141 @@ __global__ void k_tc_rowinfo(const int4* tiles, int ntiles, const int* pt, const
     dst_info[(size_t)t * TC_ROWS + r] = di;
 }
 
+// Real operators of the tree translations between a cell and a child in the canonical
+// octant, in the layout of the M2L operators (input-major [nr][nr], nr = 2 ncoef(pmax)):
+//   op 0, M2M (child -> parent), d = c_child - c_parent = (-1/4, -1/4, -1/4) s_parent:
+//     M~_n^m(P) = sum_{j,k} 2^{-j} M~_j^k(c) conj(R_{n-j}^{m-k}(d / s_parent));
+//   op 1, L2L (parent -> child), d = (+1/4, +1/4, +1/4) s_parent:
+//     L^_j^k(c) = 2^{-(j+1)} sum_{n >= j, m} L^_n^m(P) R_{n-j}^{m-k}(d / s_parent).
+// Column kin is the image of the unit input (Re or Im of one m >= 0 coefficient; its
+// m < 0 partner follows from X_n^{-m} = (-1)^m conj(X_n^m)). Other octants are reached by
+// the axis reflections of the M2L path (target - source >= 0 in the canonical octant).
+__global__ void k_tree_ops(int pmax, double* Td) {
+    __shared__ cpx<double> R[NCOEF_MAX];
+    const int op = blockIdx.y, kin = blockIdx.x;
+    const int nr = 2 * ncoef(pmax);
+    if (threadIdx.x == 0) {
+        const double d = op == 0 ? -0.25 : 0.25;
+        regular_table<double>(d, d, d, pmax, R);
+    }
+    __syncthreads();
+    auto rnm = [&](int n, int m) -> cpx<double> {  // R_n^m for any m, |m| <= n
+        if (m >= 0) return R[cidx(n, m)];
+        const cpx<double> v = R[cidx(n, -m)];
+        return (m & 1) ? mk(-v.re, v.im) : mk(v.re, -v.im);
+    };
+    const int cin = kin >> 1, pin = kin & 1;
+    int n0 = 0;
+    while ((n0 + 1) * (n0 + 2) / 2 <= cin) ++n0;
+    const int m0 = cin - n0 * (n0 + 1) / 2;
+    // the unit input at m0 and, for m0 > 0, its partner at -m0
+    const cpx<double> v_pos = pin == 0 ? mk(1.0, 0.0) : mk(0.0, 1.0);
+    const cpx<double> v_neg = (m0 & 1) ? mk(-v_pos.re, v_pos.im) : mk(v_pos.re, -v_pos.im);
+    for (int rout = threadIdx.x; rout < nr; rout += blockDim.x) {
+        const int cout = rout >> 1, pout = rout & 1;
+        int n = 0;
+        while ((n + 1) * (n + 2) / 2 <= cout) ++n;
+        const int m = cout - n * (n + 1) / 2;
+        cpx<double> acc = mk(0.0, 0.0);
+        for (int sgn = 0; sgn < (m0 > 0 ? 2 : 1); ++sgn) {
+            const int mi = sgn ? -m0 : m0;
+            const cpx<double> v = sgn ? v_neg : v_pos;
+            if (op == 0) {  // input degree j = n0 feeds output degree n >= n0
+                if (n0 <= n && abs(m - mi) <= n - n0) acc = acc + ldexp(1.0, -n0) * (v * conj(rnm(n - n0, m - mi)));
+            } else {        // input degree n0 feeds output degree j = n <= n0
+                if (n <= n0 && abs(mi - m) <= n0 - n) acc = acc + ldexp(1.0, -(n + 1)) * (v * rnm(n0 - n, mi - m));
+            }
+        }
+        Td[(size_t)op * nr * nr + (size_t)kin * nr + rout] = pout == 0 ? acc.re : acc.im;
+    }
+}
+
+// Zero the first R reals of every expansion of the listed cells (M2M accumulates into them).
+__global__ void k_zero_cells(const int* cells, int n, int nc, int R, float* X) {
+    const int c = blockIdx.x;
+    if (c >= n) return;
+    float* row = X + (size_t)cells[c] * nc * ESTRIDE;
+    for (int e = threadIdx.x; e < nc * R; e += blockDim.x) row[(e / R) * ESTRIDE + e % R] = 0.f;
+}
+
 }  // namespace
 
 size_t m2l_tc_smem(int p) { return tc_layout(p).bytes(); }
+
+// M2M and L2L of each level as tensor-core products: the pairs (parent at level l, child)
+// in tiles of 128 rows with the row tables of the M2L path; op 0 (M2M) reads the children
+// and accumulates into the parents, op 1 (L2L) reads the parents and accumulates into the
+// children.
+static int build_tree_tc(fmmbem_handle* h, int nr, int rows_max, int nch) {
+    cudaStream_t st = h->stream;
+    const int nc = h->n_cells, NC = h->ncomp;
+    double* Td = nullptr;
+    FMM_CU(cudaMalloc((void**)&Td, sizeof(double) * 2 * (size_t)nr * nr));
+    k_tree_ops<<<dim3(nr, 2), 128, 0, st>>>(h->opts.p_max, Td);
+    FMM_LAUNCHED();
+    const size_t per_tab = (size_t)nch * 2 * rows_max * TC_KC;
+    FMM_CU(cudaMalloc((void**)&h->tree_tab_tc, sizeof(float) * 2 * per_tab));
+    k_tc_tables<<<256, 256, 0, st>>>(Td, 2, nr, nr, nch, rows_max, h->tree_tab_tc);
+    FMM_LAUNCHED();
+    std::vector<double4> cs(nc);
+    std::vector<int2> ch(nc);
+    std::vector<int> par(h->parent_start.back());
+    FMM_CU(cudaMemcpyAsync(cs.data(), h->cell_cs, sizeof(double4) * nc, cudaMemcpyDeviceToHost, st));
+    FMM_CU(cudaMemcpyAsync(ch.data(), h->cell_child, sizeof(int2) * nc, cudaMemcpyDeviceToHost, st));
+    if (!par.empty())
+        FMM_CU(cudaMemcpyAsync(par.data(), h->parents, sizeof(int) * par.size(), cudaMemcpyDeviceToHost, st));
+    FMM_CU(cudaStreamSynchronize(st));
+    cudaFree(Td);
+    std::vector<int4> tiles;
+    std::vector<int> m_src, m_dst, l_src, l_dst;
+    h->tree_tile_start.assign(1, 0);
+    for (int l = 0; l + 1 < h->n_levels; ++l) {
+        std::vector<int> rows_ms, rows_md, rows_ls, rows_ld;
+        for (int pi = h->parent_start[l]; pi < h->parent_start[l + 1]; ++pi) {
+            const int pc = par[pi];
+            for (int x = 0; x < ch[pc].y; ++x) {
+                const int cc = ch[pc].x + x;
+                const int o = (cs[cc].x > cs[pc].x ? 1 : 0) | (cs[cc].y > cs[pc].y ? 2 : 0) | (cs[cc].z > cs[pc].z ? 4 : 0);
+                for (int comp = 0; comp < NC; ++comp) {
+                    const int prow = (pc * NC + comp) * ESTRIDE, crow = (cc * NC + comp) * ESTRIDE;
+                    rows_ms.push_back(crow * 8 + o);
+                    rows_md.push_back(prow * 8 + o);
+                    rows_ls.push_back(prow * 8 + (7 - o));
+                    rows_ld.push_back(crow * 8 + (7 - o));
+                }
+            }
+        }
+        const int nt = ((int)rows_ms.size() + TC_ROWS - 1) / TC_ROWS;
+        for (int t = 0; t < nt; ++t) {
+            tiles.push_back(make_int4(0, 0, 0, 0));
+            for (int r = 0; r < TC_ROWS; ++r) {
+                const size_t e = (size_t)t * TC_ROWS + r;
+                const bool in = e < rows_ms.size();
+                m_src.push_back(in ? rows_ms[e] : -1);
+                m_dst.push_back(in ? rows_md[e] : -1);
+                l_src.push_back(in ? rows_ls[e] : -1);
+                l_dst.push_back(in ? rows_ld[e] : -1);
+            }
+        }
+        h->tree_tile_start.push_back((int)tiles.size());
+    }
+    const size_t ntl = tiles.size();
+    FMM_CU(cudaMalloc((void**)&h->tree_tiles, sizeof(int4) * (ntl ? 2 * ntl : 1)));
+    FMM_CU(cudaMalloc((void**)&h->tree_info, sizeof(int) * (ntl ? 4 * ntl * TC_ROWS : 1)));
+    if (ntl) {
+        std::vector<int4> both(tiles);
+        for (auto& t : tiles) both.push_back(make_int4(1, 0, 0, 0));  // L2L tiles use op 1
+        FMM_CU(cudaMemcpyAsync(h->tree_tiles, both.data(), sizeof(int4) * 2 * ntl, cudaMemcpyHostToDevice, st));
+        const size_t rw = ntl * TC_ROWS;
+        FMM_CU(cudaMemcpyAsync(h->tree_info, m_src.data(), sizeof(int) * rw, cudaMemcpyHostToDevice, st));
+        FMM_CU(cudaMemcpyAsync(h->tree_info + rw, m_dst.data(), sizeof(int) * rw, cudaMemcpyHostToDevice, st));
+        FMM_CU(cudaMemcpyAsync(h->tree_info + 2 * rw, l_src.data(), sizeof(int) * rw, cudaMemcpyHostToDevice, st));
+        FMM_CU(cudaMemcpyAsync(h->tree_info + 3 * rw, l_dst.data(), sizeof(int) * rw, cudaMemcpyHostToDevice, st));
+        FMM_CU(cudaStreamSynchronize(st));  // the host vectors go out of scope
+    }
+    h->n_tree_tiles = (int)ntl;
+    return 0;
+}
 
 int build_m2l_tc(fmmbem_handle* h) {
     if (!h->m2l_tables) return 0;
@@ -501,6 +699,7 @@ int build_m2l_tc(fmmbem_handle* h) {
     }
     FMM_CU(cudaMalloc((void**)&h->tc_err, sizeof(int)));
     FMM_CU(cudaMemsetAsync(h->tc_err, 0, sizeof(int), h->stream));
+    FMM_TRY(build_tree_tc(h, nr, rows_max, nch));
     size_t smax = 0;
     for (int q = 1; q <= pmax; ++q) smax = std::max(smax, m2l_tc_smem(q));
     FMM_CU(cudaFuncSetAttribute(k_m2l_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smax));
@@ -509,6 +708,35 @@ int build_m2l_tc(fmmbem_handle* h) {
     FMM_CU(cudaGetDevice(&dev));
     FMM_CU(cudaDeviceGetAttribute(&h->n_sm, cudaDevAttrMultiProcessorCount, dev));
     h->m2l_tc_ready = true;
+    return 0;
+}
+
+// One level of M2M (which = 0: children of level l into their parents) or L2L (which = 1:
+// parents of level l into their children) on the tensor cores. M2M first zeroes the
+// parents it accumulates into.
+int tree_tc(fmmbem_handle* h, int p, int level, int which) {
+    const int t0 = h->tree_tile_start[level], t1 = h->tree_tile_start[level + 1];
+    const int nt = t1 - t0;
+    if (nt <= 0) return 0;
+    float* X = reinterpret_cast<float*>(which == 0 ? h->M : h->L);
+    if (which == 0) {
+        const int pb = h->parent_start[level], pe = h->parent_start[level + 1];
+        k_zero_cells<<<pe - pb, 128, 0, h->stream>>>(h->parents + pb, pe - pb, h->ncomp, 2 * ncoef(p), X);
+        FMM_LAUNCHED();
+    }
+    const size_t rw = (size_t)h->n_tree_tiles * TC_ROWS;
+    const int* src = h->tree_info + (which == 0 ? 0 : 2 * rw) + (size_t)t0 * TC_ROWS;
+    const int* dst = h->tree_info + (which == 0 ? rw : 3 * rw) + (size_t)t0 * TC_ROWS;
+    const int4* tiles = h->tree_tiles + (which == 0 ? 0 : h->n_tree_tiles) + t0;
+    const int grid = std::min(nt, h->n_sm);
+    const size_t sm = m2l_tc_smem(p);
+    if (h->ncomp == 1)
+        k_m2l_tc<1><<<grid, TC_THREADS, sm, h->stream>>>(p, 3, tiles, nt, src, dst, h->tree_tab_tc, h->tc_stride,
+                                                        h->tc_rows_max, X, X, h->tc_err);
+    else
+        k_m2l_tc<4><<<grid, TC_THREADS, sm, h->stream>>>(p, 3, tiles, nt, src, dst, h->tree_tab_tc, h->tc_stride,
+                                                        h->tc_rows_max, X, X, h->tc_err);
+    FMM_LAUNCHED();
     return 0;
 }
 

@@ -619,25 +619,29 @@ __global__ void __launch_bounds__(128) k_p2p_lap_bulk(const int* leaves, const i
     }
 }
 
-// Source-lane variant: one warp per target leaf, the lanes over the leaf's source
-// stream. The stream is the leaf's own Gauss points (the own panel skipped) followed by
-// those of every other leaf of its P2P list. Each round a lane takes two stream positions
-// (32 apart), so the lanes stay full whatever the leaf sizes. It loops over the leaf's
-// targets, read from shared memory as broadcasts, with one FP32 accumulator per target
-// in registers. Every PS_FOLD rounds the accumulators are folded into per-lane
-// compensated (hi, lo) sums in shared memory. At the end, lane i adds target i's 32
-// (hi, lo) pairs, again compensated, applies the FP64 correction row and writes the
-// result. Warps never wait on one another.
+// Source-lane variant: one block of PS_WARPS warps per target leaf (leaves in order of
+// decreasing work).
+// - The leaf's source stream is its own Gauss points (own panel skipped), then those of
+//   every other leaf of its P2P list.
+// - The stream is cut into rounds of 128 positions; round r goes to warp r mod
+//   PS_WARPS, and each lane takes four positions of the round, so lanes stay full
+//   whatever the leaf sizes.
+// - Each lane loops over the leaf's targets (shared memory, broadcast reads) with one
+//   FP32 accumulator per target in registers.
+// - Every PS_FOLD rounds the accumulators are folded into per-lane compensated (hi, lo)
+//   sums in shared memory.
+// - At the end thread i adds target i's partials of all lanes, compensated, applies the
+//   FP64 correction row and writes the result.
 constexpr int PS_WARPS = 4;
-constexpr int PS_TMAX = 40;   // targets per pass (a leaf of ncrit <= 160 Gauss points, K >= 4, is one pass)
+constexpr int PS_TMAX = 40;   // targets per pass (leaves of ncrit <= 160 Gauss points and K >= 4 are one pass)
 constexpr int PS_EMAX = 64;   // pair records per shared-memory chunk
-constexpr int PS_FOLD = 8;    // rounds between folds (16 terms per lane and target)
+constexpr int PS_FOLD = 8;    // rounds between folds (32 terms per lane and target)
 
 struct PsShared {
-    float4 t[PS_WARPS][PS_TMAX];
+    float4 t[PS_TMAX];
     float2 hl[PS_WARPS][PS_TMAX][32];
-    float4 rec[PS_WARPS][PS_EMAX];
-    int off[PS_WARPS][PS_EMAX + 1];
+    float4 rec[PS_EMAX];
+    int off[PS_EMAX + 1];
 };
 
 __device__ __forceinline__ void ps_fold(float* acc, float2* hl, int ntb, int lane) {
@@ -649,127 +653,151 @@ __device__ __forceinline__ void ps_fold(float* acc, float2* hl, int ntb, int lan
             hl[i * 32 + lane] = v;
         }
         acc[i] = 0.f;
+        asm volatile("" ::: "memory");
     }
 }
 
-// One round: two sources per lane against every target of the pass.
-__device__ __forceinline__ void ps_round(const float4* t, int ntb, float4 a, float4 b, float* acc) {
+// The target loop runs over groups of four targets, fully unrolled (so the accumulators
+// stay in registers) with one uniform branch per group; the target count of a pass is
+// padded to a multiple of four with far-away dummy targets whose sums are never read.
+// Each lane holds PS_SRC sources per round; every source costs 3 subtractions, the
+// squared distance (mul + 2 fma), one rsqrt and one fma into the accumulator.
+constexpr int PS_SRC = 4;
+
+__device__ __forceinline__ void ps_round(const float4* sT, int ntb, const float4 (&u)[PS_SRC], float* acc) {
 #pragma unroll
-    for (int i = 0; i < PS_TMAX; ++i) {
-        if (i < ntb) {
-            const float4 x = t[i];
-            acc[i] += lap_pair(x.x, x.y, x.z, a) + lap_pair(x.x, x.y, x.z, b);
+    for (int g = 0; g < PS_TMAX; g += 4) {
+        if (g < ntb) {
+#pragma unroll
+            for (int i = g; i < g + 4; ++i) {
+                const float4 x = sT[i];
+                float a = acc[i];
+#pragma unroll
+                for (int h = 0; h < PS_SRC; ++h) {
+                    const float dx = x.x - u[h].x, dy = x.y - u[h].y, dz = x.z - u[h].z;
+                    a = fmaf(u[h].w, rsqrt_approx(fmaf(dx, dx, fmaf(dy, dy, dz * dz))), a);
+                }
+                acc[i] = a;
+            }
         }
+        asm volatile("" ::: "memory");  // keeps the next group's target loads from being hoisted (register pressure)
     }
 }
 
-__global__ void __launch_bounds__(32 * PS_WARPS) k_p2p_lap_src(const int* order, int nleaves, const int2* range,
-                                                              const int* pptr, const float4* prec, const int* poff,
-                                                              const int* plen, const float4* srcw, const float4* tgt,
-                                                              int K, const int* cptr, const int* ccol,
-                                                              const double* cval, const double* xs, double* ynear) {
+__device__ __forceinline__ void ps_round_self(const float4* sT, int ntb, int tb, const float4 (&u)[PS_SRC],
+                                              const int (&gp)[PS_SRC], float* acc) {
+#pragma unroll
+    for (int g = 0; g < PS_TMAX; g += 4) {
+        if (g < ntb) {
+#pragma unroll
+            for (int i = g; i < g + 4; ++i) {
+                const float4 x = sT[i];
+                const int own = tb + i;
+                float a = acc[i];
+#pragma unroll
+                for (int h = 0; h < PS_SRC; ++h) {
+                    const float dx = x.x - u[h].x, dy = x.y - u[h].y, dz = x.z - u[h].z;
+                    const bool sk = gp[h] == own;  // the target's own panel
+                    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                    a = fmaf(sk ? 0.f : u[h].w, rsqrt_approx(sk ? 1.f : r2), a);
+                }
+                acc[i] = a;
+            }
+        }
+        asm volatile("" ::: "memory");
+    }
+}
+
+__global__ void __launch_bounds__(32 * PS_WARPS, 5) k_p2p_lap_src(const int* order, const int2* range, const int* pptr,
+                                                                 const float4* prec, const int* poff, const int* plen,
+                                                                 const float4* srcw, const float4* tgt, int K,
+                                                                 const int* cptr, const int* ccol, const double* cval,
+                                                                 const double* xs, double* ynear) {
     __shared__ PsShared sh;
+    constexpr int RND = 32 * PS_SRC;  // stream positions per warp round
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int li = blockIdx.x * PS_WARPS + warp;
-    if (li >= nleaves) return;
-    const int cell = order[li];
+    const int cell = order[blockIdx.x];
     const int2 r = range[cell];
     const int e0 = pptr[cell], e1 = pptr[cell + 1];
     const int total = plen[cell];
-    float4* sT = sh.t[warp];
+    float4* sT = sh.t;
     float2* sHL = &sh.hl[warp][0][0];
-    float4* sRec = sh.rec[warp];
-    int* sOff = sh.off[warp];
     const float4 far_src = make_float4(1e18f, 0.f, 0.f, 0.f);  // padding: contributes 0 * rsqrt(1e36)
     for (int tb = r.x; tb < r.y; tb += PS_TMAX) {
         const int ntb = min(PS_TMAX, r.y - tb);
-        for (int i = lane; i < ntb; i += 32) sT[i] = tgt[tb + i];
+        __syncthreads();
+        for (int i = threadIdx.x; i < ((ntb + 3) & ~3); i += blockDim.x)
+            sT[i] = i < ntb ? tgt[tb + i] : make_float4(1e18f, 1e18f, 1e18f, 0.f);
         for (int i = 0; i < ntb; ++i) sHL[i * 32 + lane] = make_float2(0.f, 0.f);
-        __syncwarp();
         float acc[PS_TMAX];
 #pragma unroll
         for (int i = 0; i < PS_TMAX; ++i) acc[i] = 0.f;
+        int rounds = 0;
+        __syncthreads();
         // own leaf: positions relative to the same centre; the target's own panel is skipped
         {
             const int g0 = r.x * K, n = (r.y - r.x) * K;
-            int rounds = 0;
-            for (int base = 0; base < n; base += 64) {
-                float4 u[2];
-                int gp[2];
+            for (int base = RND * warp; base < n; base += RND * PS_WARPS) {
+                float4 u[PS_SRC];
+                int gp[PS_SRC];
 #pragma unroll
-                for (int h = 0; h < 2; ++h) {
+                for (int h = 0; h < PS_SRC; ++h) {
                     const int q = base + 32 * h + lane;
                     u[h] = q < n ? srcw[g0 + q] : far_src;
                     gp[h] = q < n ? (g0 + q) / K : -1;
                 }
-#pragma unroll
-                for (int i = 0; i < PS_TMAX; ++i) {
-                    if (i < ntb) {
-                        const float4 x = sT[i];
-                        const int own = tb + i;
-                        float s = 0.f;
-#pragma unroll
-                        for (int h = 0; h < 2; ++h) {
-                            const float dx = x.x - u[h].x, dy = x.y - u[h].y, dz = x.z - u[h].z;
-                            const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                            const bool skip = gp[h] == own;
-                            s = fmaf(skip ? 0.f : u[h].w, rsqrt_approx(skip ? 1.f : r2), s);
-                        }
-                        acc[i] += s;
-                    }
-                }
+                ps_round_self(sT, ntb, tb, u, gp, acc);
                 if (++rounds == PS_FOLD) { ps_fold(acc, sHL, ntb, lane); rounds = 0; }
             }
         }
         // the other leaves, as one stream of Gauss points in chunks of PS_EMAX pair records
         for (int eb = e0; eb < e1; eb += PS_EMAX) {
             const int ne = min(PS_EMAX, e1 - eb);
-            __syncwarp();
-            for (int j = lane; j < ne; j += 32) {
-                sRec[j] = prec[eb + j];
-                sOff[j] = poff[eb + j];
+            __syncthreads();
+            for (int j = threadIdx.x; j < ne; j += blockDim.x) {
+                sh.rec[j] = prec[eb + j];
+                sh.off[j] = poff[eb + j];
             }
-            if (lane == 0) sOff[ne] = (eb + PS_EMAX < e1) ? poff[eb + PS_EMAX] : total;
-            __syncwarp();
-            const int s_beg = sOff[0], s_end = sOff[ne];
-            int cur[2] = {0, 0};  // per-lane cursor: pair record holding the lane's position
-            int rounds = 0;
-            for (int base = s_beg; base < s_end; base += 64) {
-                float4 u[2];
+            if (threadIdx.x == 0) sh.off[ne] = (eb + PS_EMAX < e1) ? poff[eb + PS_EMAX] : total;
+            __syncthreads();
+            const int s_beg = sh.off[0], s_end = sh.off[ne];
+            int cur = 0;  // per-lane cursor: the pair record holding the lane's next position
+            auto fetch = [&](int base, float4 (&u)[PS_SRC]) {
 #pragma unroll
-                for (int h = 0; h < 2; ++h) {
+                for (int h = 0; h < PS_SRC; ++h) {
                     const int pos = base + 32 * h + lane;
+                    u[h] = far_src;
                     if (pos < s_end) {
-                        int j = cur[h];
-                        while (sOff[j + 1] <= pos) ++j;
-                        cur[h] = j;
-                        const float4 rc = sRec[j];
-                        float4 v = srcw[__float_as_int(rc.w) + (pos - sOff[j])];
+                        while (sh.off[cur + 1] <= pos) ++cur;
+                        const float4 rc = sh.rec[cur];
+                        float4 v = srcw[__float_as_int(rc.w) + (pos - sh.off[cur])];
                         v.x += rc.x; v.y += rc.y; v.z += rc.z;
                         u[h] = v;
-                    } else {
-                        u[h] = far_src;
                     }
                 }
-                ps_round(sT, ntb, u[0], u[1], acc);
+            };
+            for (int base = s_beg + RND * warp; base < s_end; base += RND * PS_WARPS) {
+                float4 u[PS_SRC];
+                fetch(base, u);
+                ps_round(sT, ntb, u, acc);
                 if (++rounds == PS_FOLD) { ps_fold(acc, sHL, ntb, lane); rounds = 0; }
             }
         }
         ps_fold(acc, sHL, ntb, lane);
-        __syncwarp();
-        // lane i: target i of the pass sums the 32 lanes' compensated partials
-        for (int i = lane; i < ntb; i += 32) {
+        __syncthreads();
+        // thread i: target i of the pass adds the compensated partials of every lane of every warp
+        for (int i = threadIdx.x; i < ntb; i += blockDim.x) {
             float hi = 0.f, lo = 0.f;
-            for (int k = 0; k < 32; ++k) {
-                const float2 v = sHL[i * 32 + ((k + i) & 31)];
-                kahan_add(hi, lo, v.x);
-                kahan_add(hi, lo, -v.y);
-            }
+            for (int w = 0; w < PS_WARPS; ++w)
+                for (int k = 0; k < 32; ++k) {
+                    const float2 v = sh.hl[w][i][(k + i) & 31];
+                    kahan_add(hi, lo, v.x);
+                    kahan_add(hi, lo, -v.y);
+                }
             double out = (double)hi - (double)lo;
             add_correction<1>(tb + i, cptr, ccol, cval, xs, &out);
             ynear[tb + i] = out;
         }
-        __syncwarp();
     }
 }
 
@@ -859,9 +887,9 @@ int near_field_on(fmmbem_handle* h, bool fp64) {
         k_pack_sources<<<(unsigned)((h->NS + 255) / 256), 256, 0, h->stream>>>(h->src_rel, h->xin, h->K, h->NS, h->src_w);
         FMM_LAUNCHED();
         if (h->p2p_variant == 3 && h->p2p_order) {
-            k_p2p_lap_src<<<(h->n_leaves + PS_WARPS - 1) / PS_WARPS, 32 * PS_WARPS, 0, h->stream>>>(
-                h->p2p_order, h->n_leaves, h->cell_range, h->p2p_ptr, h->p2p_rec, h->p2p_off, h->p2p_len, h->src_w,
-                h->tgt_rel, h->K, h->corr_ptr, h->corr_col, h->corr_sl, h->xin, h->ynear);
+            k_p2p_lap_src<<<h->n_leaves, 32 * PS_WARPS, 0, h->stream>>>(
+                h->p2p_order, h->cell_range, h->p2p_ptr, h->p2p_rec, h->p2p_off, h->p2p_len, h->src_w, h->tgt_rel,
+                h->K, h->corr_ptr, h->corr_col, h->corr_sl, h->xin, h->ynear);
             FMM_LAUNCHED();
             h->launches += 1;
             prof_end(h, FMMBEM_PASS_P2P, 2);

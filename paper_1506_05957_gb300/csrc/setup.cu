@@ -266,18 +266,51 @@ __global__ void k_split_emit(int lb, int le, int next_start, int level, const in
     }
 }
 
+// Cluster radii of every cell about its box centre: .x = the farthest collocation point
+// (targets), .y = the farthest Gauss point (sources). The MAC uses them as the cluster
+// sizes, the a of eq. multipole_error.
+__global__ void k_cell_radii(int ncells, const double4* cs, const int2* range, const double4* tgt, const double4* src,
+                             int K, double2* rad) {
+    __shared__ double st[128], ss[128];
+    const int c = blockIdx.x;
+    if (c >= ncells) return;
+    const double4 cc = cs[c];
+    const int2 r = range[c];
+    double mt = 0.0, ms = 0.0;
+    for (int i = r.x + threadIdx.x; i < r.y; i += blockDim.x) {
+        const double4 t = tgt[i];
+        mt = fmax(mt, (t.x - cc.x) * (t.x - cc.x) + (t.y - cc.y) * (t.y - cc.y) + (t.z - cc.z) * (t.z - cc.z));
+    }
+    for (int g = r.x * K + threadIdx.x; g < r.y * K; g += blockDim.x) {
+        const double4 y = src[g];
+        ms = fmax(ms, (y.x - cc.x) * (y.x - cc.x) + (y.y - cc.y) * (y.y - cc.y) + (y.z - cc.z) * (y.z - cc.z));
+    }
+    st[threadIdx.x] = mt;
+    ss[threadIdx.x] = ms;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) {
+            st[threadIdx.x] = fmax(st[threadIdx.x], st[threadIdx.x + o]);
+            ss[threadIdx.x] = fmax(ss[threadIdx.x], ss[threadIdx.x + o]);
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) rad[c] = make_double2(sqrt(st[0]), sqrt(ss[0]));
+}
+
 // ---------------------------------------------------------------- dual-tree traversal
 // One round over a frontier of (target cell, source cell) pairs: accepted pairs go
 // to M2L, leaf-leaf pairs to P2P, the rest are split (both cells when they have the
-// same size, else the larger / the non-leaf one).
+// same size, else the larger / the non-leaf one). Acceptance: R_a + R_b < theta |c_a - c_b|
+// with R_a the target radius of a and R_b the source radius of b.
 __global__ void k_dtt_round(const int2* in, int n_in, const double4* cs, const int2* child, const int* clevel,
-                            double theta, double spill, int2* m2l, long long cap_m2l, int2* p2p, long long cap_p2p,
+                            double theta, const double2* rad, int2* m2l, long long cap_m2l, int2* p2p, long long cap_p2p,
                             int2* next, long long cap_next, unsigned long long* cnt, int* overflow) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n_in) return;
     const int a = in[i].x, b = in[i].y;
     const double4 ca = cs[a], cb = cs[b];
-    const double Ra = 0.8660254037844386 * ca.w + spill, Rb = 0.8660254037844386 * cb.w + spill;
+    const double Ra = rad[a].x, Rb = rad[b].y;
     const double dx = ca.x - cb.x, dy = ca.y - cb.y, dz = ca.z - cb.z;
     const double d = sqrt(dx * dx + dy * dy + dz * dz);
     if (Ra + Rb < theta * d) {
@@ -846,6 +879,9 @@ int build_geometry_tree_lists(fmmbem_handle* h, const fmmbem_mesh* mesh) {
 
     // ---- dual-tree traversal
     {
+        FMM_TRY(dalloc(&h->cell_rad, nc));
+        k_cell_radii<<<nc, 128, 0, st>>>(nc, h->cell_cs, h->cell_range, h->tgt_d, h->src_d, K, h->cell_rad);
+        FMM_LAUNCHED();
         long long cap_m2l = std::max<long long>(1024, 256LL * nc), cap_p2p = std::max<long long>(1024, 64LL * nc);
         long long cap_f = std::max<long long>(4096, 64LL * nc);
         int2 *m2l = nullptr, *p2p = nullptr, *fa = nullptr, *fb = nullptr;
@@ -869,7 +905,7 @@ int build_geometry_tree_lists(fmmbem_handle* h, const fmmbem_mesh* mesh) {
                 FMM_CU(cudaMemcpyAsync(cnt, c0, sizeof(c0), cudaMemcpyHostToDevice, st));
                 FMM_CU(cudaMemsetAsync(ovf, 0, sizeof(int), st));
                 k_dtt_round<<<(unsigned)((nf + T - 1) / T), T, 0, st>>>(fa, (int)nf, h->cell_cs, h->cell_child,
-                                                                       h->cell_level, h->theta, h->spill, m2l, cap_m2l,
+                                                                       h->cell_level, h->theta, h->cell_rad, m2l, cap_m2l,
                                                                        p2p, cap_p2p, fb, cap_f, cnt, ovf);
                 FMM_LAUNCHED();
                 unsigned long long c1[3];
