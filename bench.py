@@ -212,7 +212,7 @@ def run_ours(args, world, rank, local):
         solve()
     torch.cuda.synchronize(dev)
     barrier(world, dev)
-    h.profile_enable(True)
+    h.profile_enable(False)  # resets the launch counter; no per-pass events in the timed region
     sampler = ClockSampler(local)
     sampler.start()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
@@ -227,9 +227,20 @@ def run_ours(args, world, rank, local):
     torch.cuda.synchronize(dev)
     barrier(world, dev)
     clocks = sampler.stop()
+    launches = int(h.profile()["kernel_launches"])
+    step_ms = [a.elapsed_time(b_) for a, b_ in ev]
+    # per-pass timing (roofline and time shares): a second timed region of the same solves with
+    # the library's pass events on (they add a few percent, so the headline is taken without them)
+    n_prof = max(3, min(10, args.steps))
+    h.profile_enable(True)
+    torch.cuda.synchronize(dev)
+    for k in range(n_prof):
+        flush.fill_(float(k))
+        solve()
+    torch.cuda.synchronize(dev)
     prof = h.profile()
     h.profile_enable(False)
-    step_ms = [a.elapsed_time(b_) for a, b_ in ev]
+    prof_total_ms = prof["ms"]["matvec"] + prof["ms"]["krylov"]
     t_local = float(np.sum(step_ms)) / 1e3
     t_max = max_over_ranks(world, t_local, dev)
     sec_per_solve = t_max / args.steps / world  # whole job: world solves finish per step time
@@ -259,11 +270,10 @@ def run_ours(args, world, rank, local):
     # the stream that launches each pass, over the timed region
     ms = prof["ms"]
     smax = clocks.get("sm_max_mhz") or measured_peaks().get("sm_max_mhz", 2070.0)
-    total_ms = sum(step_ms)
-    share = {k_: round(v_ / total_ms, 4) for k_, v_ in ms.items() if k_ != "matvec"}
+    share = {k_: round(v_ / prof_total_ms, 4) for k_, v_ in ms.items() if k_ != "matvec"}
     p2p_ach = prof["p2p_interactions"] * P2P_FLOPS / (ms["p2p"] * 1e-3) / 1e12 if ms["p2p"] > 0 else 0.0
     p2p_peak = SM_COUNT * MUFU_PER_SM_CLK * smax * 1e6 * P2P_FLOPS / 1e12
-    rl_p2p = {"bound": "alu", "kernel": "k_p2p_lap (near field, FP32 + MUFU rsqrt)", "achieved": round(p2p_ach, 3),
+    rl_p2p = {"bound": "alu", "kernel": "k_p2p_lap_src (near field, FP32 + MUFU rsqrt)", "achieved": round(p2p_ach, 3),
               "peak": round(p2p_peak, 2), "unit": "TFLOP/s", "frac": round(p2p_ach / p2p_peak, 4), "traffic": None,
               "peak_source": "152 SMs x 16 rsqrt/clk x max SM clock x 11 flop per pair (derived, not measured)",
               "interactions_per_s": prof["p2p_interactions"] / (ms["p2p"] * 1e-3) if ms["p2p"] else None}
@@ -278,6 +288,9 @@ def run_ours(args, world, rank, local):
               "flops_convention": "2 (p+1)^4 per pair and expansion; hardware does 3x (3xTF32)"}
     roofline = dict(rl_p2p if ms["p2p"] >= ms["m2l"] else rl_m2l)
     roofline["time_share"] = share
+    roofline["time_share_note"] = ("per-pass CUDA-event time / solve time in a profiled region of %d solves; the "
+                                   "near field runs on a second stream concurrently with the far field, so shares "
+                                   "overlap" % n_prof)
     roofline["other"] = rl_m2l if ms["p2p"] >= ms["m2l"] else rl_p2p
 
     out = {"metric": METRIC, "value": sec_per_solve, "unit": "s", "n_gpus": world, "steps": args.steps,
@@ -286,7 +299,7 @@ def run_ours(args, world, rank, local):
            "config": dict(W, ncrit=args.ncrit, panels=n, parallelism="replicas" if world > 1 else "single",
                           l2="flushed between steps (512 MB write)", precision="mixed"),
            "matvec_per_s": mv_per_s, "iters": iters, "p_hist": r["p_hist"], "true_residual": r["true_res"],
-           "gpu_launches": int(prof["kernel_launches"]),
+           "gpu_launches": launches,
            "e2e": {"value": e2e, "unit": "s", "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 8 * n},
            "roofline": roofline, "clocks": clocks,
            "tree": {k_: stats[k_] for k_ in ("n_cells", "n_leaves", "n_levels", "n_m2l_pairs", "n_m2l_tables",

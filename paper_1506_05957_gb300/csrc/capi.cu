@@ -254,7 +254,7 @@ void fmmbem_destroy(fmmbem_handle* h) {
     if (!h) return;
     void* bufs[] = {h->perm, h->tgt_d, h->tgt_f, h->nrm_d, h->verts, h->src_d, h->src_f, h->src_rel, h->tgt_rel, h->src_w, h->cell_cs, h->cell_range, h->cell_rad,
                     h->cell_child, h->cell_level, h->cell_parent, h->leaves, h->parents, h->leaf_class, h->m2l_ptr, h->m2l_src, h->p2p_ptr,
-                    h->p2p_src, h->p2p_rec, h->p2p_off, h->p2p_len, h->p2p_order, h->p2p_cnt, h->p2p_toff, h->stage_ptr, h->stage_first, h->stage_bytes, h->corr_ptr, h->corr_col, h->corr_sl, h->corr_dl, h->oct_d, h->oct_f, h->M, h->L,
+                    h->p2p_src, h->p2p_rec, h->p2p_off, h->p2p_len, h->p2p_items, h->p2p_cnt, h->p2p_toff, h->stage_ptr, h->stage_first, h->stage_bytes, h->corr_ptr, h->corr_col, h->corr_sl, h->corr_dl, h->oct_d, h->oct_f, h->M, h->L,
                     h->xs, h->ys, h->ynear, h->m2l_pt, h->m2l_ps, h->m2l_refl, h->sign_f, h->sign_d, h->m2l_tiles, h->tab_d, h->tab_f, h->tab_tc, h->m2l_tiles_tc, h->tc_src_info, h->tc_dst_info, h->tree_tab_tc, h->tree_tiles, h->tree_info, h->tc_err, h->kerr, h->V, h->kw, h->xfix, h->kb, h->kx, h->kr, h->kpart, h->kh, h->kyv, h->arn_bar};
     for (void* b : bufs)
         if (b) cudaFree(b);
@@ -309,8 +309,13 @@ int fmmbem_create(const fmmbem_mesh* mesh, int kernel, int gauss_k, int ncrit, d
     h->precision = o.precision;
     h->stream = (cudaStream_t)o.stream;
     auto fail = [&](int rc) { fmmbem_destroy(h); return rc; };
-    if (cudaStreamCreateWithFlags(&h->stream2, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaStreamCreateWithFlags(&h->istream, cudaStreamNonBlocking) != cudaSuccess ||
+    // the near field (stream2) runs at the lowest priority and the solver's far-field chain
+    // (istream) at the highest, so that blocks of the short, dependent far-field kernels are
+    // dispatched ahead of queued near-field blocks as SMs free up
+    int prio_lo = 0, prio_hi = 0;
+    cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
+    if (cudaStreamCreateWithPriority(&h->stream2, cudaStreamNonBlocking, prio_lo) != cudaSuccess ||
+        cudaStreamCreateWithPriority(&h->istream, cudaStreamNonBlocking, prio_hi) != cudaSuccess ||
         cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&h->ev_out, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) != cudaSuccess ||

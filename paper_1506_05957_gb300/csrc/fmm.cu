@@ -490,12 +490,16 @@ int far_field_t(fmmbem_handle* h, int p) {
     prof_begin(h, FMMBEM_PASS_M2M);
     int nl = 0;
     const size_t sm_m2m = (size_t)(16 * NC + 8) * nco * 2 * sizeof(T);
+    if (tree_tc_on) {
+        FMM_TRY(tree_tc_zero(h, p));
+        ++nl;
+    }
     for (int l = h->n_levels - 2; l >= 0; --l) {
         const int pb = h->parent_start[l], pe = h->parent_start[l + 1];
         if (pe == pb) continue;
         if (tree_tc_on) {
             FMM_TRY(tree_tc(h, p, l, 0));
-            nl += 2;
+            ++nl;
         } else {
             k_m2m<T, NC><<<pe - pb, TREE_THREADS, sm_m2m, st>>>(p, h->parents + pb, h->cell_cs, h->cell_child, oct, M);
             FMM_LAUNCHED();

@@ -110,7 +110,8 @@ struct fmmbem_handle {
     int* stage_bytes = nullptr; // bytes of each stage
     int64_t n_stages = 0;
     int max_leaf_panels = 0;
-    int* p2p_order = nullptr;   // [n_leaves] leaves by decreasing near-field work (source-lane kernel order)
+    int4* p2p_items = nullptr;  // source-lane P2P work: (leaf, first target, target count), largest first
+    int n_p2p_items = 0;
     int p2p_variant = 3;        // 0: shared stream tiles, 1: sliced L1 broadcast, 2: bulk-copied stages, 3: source lanes
 
     // near-singular / self corrections (CSR by sorted target panel), FP64
@@ -170,6 +171,7 @@ int m2l_gemm(fmmbem_handle* h, int p, bool fp64);
 int build_m2l_tc(fmmbem_handle* h);
 int m2l_tc(fmmbem_handle* h, int p);
 int tree_tc(fmmbem_handle* h, int p, int level, int which);
+int tree_tc_zero(fmmbem_handle* h, int p);
 // fmm.cu
 int far_field(fmmbem_handle* h, int p, bool fp64);
 int far_eval_add(fmmbem_handle* h, int p, bool fp64, double* y_sorted, double scale);

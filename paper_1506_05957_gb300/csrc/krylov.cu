@@ -118,18 +118,39 @@ __device__ __forceinline__ bool grid_barrier(unsigned* count, volatile unsigned*
     return s_ok != 0;
 }
 
-// partial[j * gridDim.x + block] = sum over the block's rows of V_j w. Warp q takes the
-// vectors j = q, q + 8, ...; its lanes stride the rows; no block barrier between dots.
+// partial[j * gridDim.x + block] = sum over the block's rows of V_j w. Each thread takes its
+// rows (stride ARN_THREADS) and eight vectors at a time, so every row visit issues eight
+// independent loads; the eight sums are reduced across the block by warp shuffles and one
+// shared-memory pass in a fixed order (deterministic).
 __device__ void arn_partials(const double* V, int64_t ldv, int nv, const double* w, int64_t i0, int64_t i1,
                              double* partial) {
+    __shared__ double red[8][ARN_THREADS / 32];
     const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
-    for (int j = wp; j < nv; j += ARN_THREADS / 32) {
-        const double* v = V + (int64_t)j * ldv;
-        double s = 0.0;
-        for (int64_t i = i0 + lane; i < i1; i += 32) s += v[i] * w[i];
+    for (int j0 = 0; j0 < nv; j0 += 8) {
+        double s[8];
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if (lane == 0) partial[(int64_t)j * gridDim.x + blockIdx.x] = s;
+        for (int q = 0; q < 8; ++q) s[q] = 0.0;
+        for (int64_t i = i0 + threadIdx.x; i < i1; i += ARN_THREADS) {
+            const double wi = w[i];
+#pragma unroll
+            for (int q = 0; q < 8; ++q)
+                if (j0 + q < nv) s[q] += V[(int64_t)(j0 + q) * ldv + i] * wi;
+        }
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) s[q] += __shfl_xor_sync(0xffffffffu, s[q], o);
+        }
+        if (lane == 0)
+#pragma unroll
+            for (int q = 0; q < 8; ++q) red[q][wp] = s[q];
+        __syncthreads();
+        if (threadIdx.x < 8 && j0 + (int)threadIdx.x < nv) {
+            double t = 0.0;
+            for (int w2 = 0; w2 < ARN_THREADS / 32; ++w2) t += red[threadIdx.x][w2];
+            partial[(int64_t)(j0 + threadIdx.x) * gridDim.x + blockIdx.x] = t;
+        }
+        __syncthreads();
     }
 }
 
@@ -165,8 +186,15 @@ __global__ void __launch_bounds__(ARN_THREADS) k_arnoldi(double* V, int64_t n, i
         if (blockIdx.x == 0)
             for (int j = threadIdx.x; j < nv; j += ARN_THREADS) out[pass * (ARN_MAXV + 1) + j] = hs[j];
         for (int64_t i = i0 + threadIdx.x; i < i1; i += ARN_THREADS) {
+            // eight independent loads per group, so the group costs one memory latency
             double t = 0.0;
-            for (int j = 0; j < nv; ++j) t += hs[j] * V[(int64_t)j * n + i];
+            for (int j0 = 0; j0 < nv; j0 += 8) {
+                double v[8];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) v[q] = j0 + q < nv ? V[(int64_t)(j0 + q) * n + i] : 0.0;
+#pragma unroll
+                for (int q = 0; q < 8; ++q) t += (j0 + q < nv ? hs[j0 + q] : 0.0) * v[q];
+            }
             w[i] -= t;
         }
         __syncthreads();  // hs is rewritten by the next phase's reduction

@@ -711,19 +711,23 @@ int build_m2l_tc(fmmbem_handle* h) {
     return 0;
 }
 
-// One level of M2M (which = 0: children of level l into their parents) or L2L (which = 1:
-// parents of level l into their children) on the tensor cores. M2M first zeroes the
-// parents it accumulates into.
+// Zero the multipole expansions of every non-leaf cell (the M2M products accumulate into them).
+int tree_tc_zero(fmmbem_handle* h, int p) {
+    const int np = h->parent_start.back();
+    if (np <= 0) return 0;
+    k_zero_cells<<<np, 128, 0, h->stream>>>(h->parents, np, h->ncomp, 2 * ncoef(p), reinterpret_cast<float*>(h->M));
+    FMM_LAUNCHED();
+    return 0;
+}
+
+// One level of M2M (which = 0: children of level l into their parents, zeroed beforehand
+// by tree_tc_zero) or L2L (which = 1: parents of level l into their children) on the
+// tensor cores.
 int tree_tc(fmmbem_handle* h, int p, int level, int which) {
     const int t0 = h->tree_tile_start[level], t1 = h->tree_tile_start[level + 1];
     const int nt = t1 - t0;
     if (nt <= 0) return 0;
     float* X = reinterpret_cast<float*>(which == 0 ? h->M : h->L);
-    if (which == 0) {
-        const int pb = h->parent_start[level], pe = h->parent_start[level + 1];
-        k_zero_cells<<<pe - pb, 128, 0, h->stream>>>(h->parents + pb, pe - pb, h->ncomp, 2 * ncoef(p), X);
-        FMM_LAUNCHED();
-    }
     const size_t rw = (size_t)h->n_tree_tiles * TC_ROWS;
     const int* src = h->tree_info + (which == 0 ? 0 : 2 * rw) + (size_t)t0 * TC_ROWS;
     const int* dst = h->tree_info + (which == 0 ? rw : 3 * rw) + (size_t)t0 * TC_ROWS;

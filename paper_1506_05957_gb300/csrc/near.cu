@@ -619,8 +619,8 @@ __global__ void __launch_bounds__(128) k_p2p_lap_bulk(const int* leaves, const i
     }
 }
 
-// Source-lane variant: one block of PS_WARPS warps per target leaf (leaves in order of
-// decreasing work).
+// Source-lane variant: one block of PS_WARPS warps per work item, a chunk of at most
+// PS_TMAX targets of one leaf (items in order of decreasing work).
 // - The leaf's source stream is its own Gauss points (own panel skipped), then those of
 //   every other leaf of its P2P list.
 // - The stream is cut into rounds of 128 positions; round r goes to warp r mod
@@ -633,7 +633,7 @@ __global__ void __launch_bounds__(128) k_p2p_lap_bulk(const int* leaves, const i
 // - At the end thread i adds target i's partials of all lanes, compensated, applies the
 //   FP64 correction row and writes the result.
 constexpr int PS_WARPS = 4;
-constexpr int PS_TMAX = 40;   // targets per pass (leaves of ncrit <= 160 Gauss points and K >= 4 are one pass)
+constexpr int PS_TMAX = P2P_SRC_TMAX;  // targets per block (a leaf's targets are split into chunks of at most this)
 constexpr int PS_EMAX = 64;   // pair records per shared-memory chunk
 constexpr int PS_FOLD = 8;    // rounds between folds (32 terms per lane and target)
 
@@ -708,7 +708,7 @@ __device__ __forceinline__ void ps_round_self(const float4* sT, int ntb, int tb,
     }
 }
 
-__global__ void __launch_bounds__(32 * PS_WARPS, 5) k_p2p_lap_src(const int* order, const int2* range, const int* pptr,
+__global__ void __launch_bounds__(32 * PS_WARPS, 6) k_p2p_lap_src(const int4* items, const int2* range, const int* pptr,
                                                                  const float4* prec, const int* poff, const int* plen,
                                                                  const float4* srcw, const float4* tgt, int K,
                                                                  const int* cptr, const int* ccol, const double* cval,
@@ -716,15 +716,17 @@ __global__ void __launch_bounds__(32 * PS_WARPS, 5) k_p2p_lap_src(const int* ord
     __shared__ PsShared sh;
     constexpr int RND = 32 * PS_SRC;  // stream positions per warp round
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int cell = order[blockIdx.x];
+    const int4 item = items[blockIdx.x];
+    const int cell = item.x;
     const int2 r = range[cell];
     const int e0 = pptr[cell], e1 = pptr[cell + 1];
     const int total = plen[cell];
     float4* sT = sh.t;
     float2* sHL = &sh.hl[warp][0][0];
     const float4 far_src = make_float4(1e18f, 0.f, 0.f, 0.f);  // padding: contributes 0 * rsqrt(1e36)
-    for (int tb = r.x; tb < r.y; tb += PS_TMAX) {
-        const int ntb = min(PS_TMAX, r.y - tb);
+    {
+        const int tb = item.y;
+        const int ntb = item.z;
         __syncthreads();
         for (int i = threadIdx.x; i < ((ntb + 3) & ~3); i += blockDim.x)
             sT[i] = i < ntb ? tgt[tb + i] : make_float4(1e18f, 1e18f, 1e18f, 0.f);
@@ -886,9 +888,9 @@ int near_field_on(fmmbem_handle* h, bool fp64) {
     if (h->kernel == FMMBEM_LAPLACE && !fp64) {
         k_pack_sources<<<(unsigned)((h->NS + 255) / 256), 256, 0, h->stream>>>(h->src_rel, h->xin, h->K, h->NS, h->src_w);
         FMM_LAUNCHED();
-        if (h->p2p_variant == 3 && h->p2p_order) {
-            k_p2p_lap_src<<<h->n_leaves, 32 * PS_WARPS, 0, h->stream>>>(
-                h->p2p_order, h->cell_range, h->p2p_ptr, h->p2p_rec, h->p2p_off, h->p2p_len, h->src_w, h->tgt_rel,
+        if (h->p2p_variant == 3 && h->p2p_items) {
+            k_p2p_lap_src<<<h->n_p2p_items, 32 * PS_WARPS, 0, h->stream>>>(
+                h->p2p_items, h->cell_range, h->p2p_ptr, h->p2p_rec, h->p2p_off, h->p2p_len, h->src_w, h->tgt_rel,
                 h->K, h->corr_ptr, h->corr_col, h->corr_sl, h->xin, h->ynear);
             FMM_LAUNCHED();
             h->launches += 1;

@@ -964,8 +964,8 @@ int build_geometry_tree_lists(fmmbem_handle* h, const fmmbem_mesh* mesh) {
                                                      h->p2p_rec, h->p2p_off, h->p2p_len);
         FMM_LAUNCHED();
         {
-            // leaves by decreasing near-field work (targets x stream length), so that the
-            // source-lane kernel's blocks, issued in order, finish together
+            // source-lane kernel work in decreasing order (targets x stream length), so that its
+            // blocks, issued in order, finish together
             const int nl = h->n_leaves;
             std::vector<int> lv(nl), len(nc);
             std::vector<int2> rg(nc);
@@ -973,14 +973,27 @@ int build_geometry_tree_lists(fmmbem_handle* h, const fmmbem_mesh* mesh) {
             FMM_CU(cudaMemcpyAsync(len.data(), h->p2p_len, sizeof(int) * nc, cudaMemcpyDeviceToHost, st));
             FMM_CU(cudaMemcpyAsync(rg.data(), h->cell_range, sizeof(int2) * nc, cudaMemcpyDeviceToHost, st));
             FMM_CU(cudaStreamSynchronize(st));
-            std::vector<long long> cost(nc, 0);
+            // work items of the source-lane kernel: (leaf, first target, target count), a leaf's
+            // targets split evenly into chunks of at most P2P_SRC_TMAX, largest work first
+            std::vector<int4> items;
+            std::vector<long long> cost;
             for (int c : lv) {
-                const long long t = rg[c].y - rg[c].x;
-                cost[c] = t * ((long long)len[c] + t * K);
+                const int t = rg[c].y - rg[c].x;
+                const int nchk = (t + P2P_SRC_TMAX - 1) / P2P_SRC_TMAX;
+                for (int q = 0; q < nchk; ++q) {
+                    const int b = rg[c].x + (int)((long long)t * q / nchk), e = rg[c].x + (int)((long long)t * (q + 1) / nchk);
+                    items.push_back(make_int4(c, b, e - b, 0));
+                    cost.push_back((long long)(e - b) * ((long long)len[c] + (long long)t * K));
+                }
             }
-            std::stable_sort(lv.begin(), lv.end(), [&](int a, int b) { return cost[a] > cost[b]; });
-            FMM_TRY(dalloc(&h->p2p_order, nl));
-            FMM_CU(cudaMemcpyAsync(h->p2p_order, lv.data(), sizeof(int) * nl, cudaMemcpyHostToDevice, st));
+            std::vector<int> idx(items.size());
+            for (size_t q = 0; q < idx.size(); ++q) idx[q] = (int)q;
+            std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+            std::vector<int4> sorted(items.size());
+            for (size_t q = 0; q < idx.size(); ++q) sorted[q] = items[idx[q]];
+            h->n_p2p_items = (int)sorted.size();
+            FMM_TRY(dalloc(&h->p2p_items, sorted.size()));
+            FMM_CU(cudaMemcpyAsync(h->p2p_items, sorted.data(), sizeof(int4) * sorted.size(), cudaMemcpyHostToDevice, st));
             FMM_CU(cudaStreamSynchronize(st));
         }
         // stage plans of the bulk-copy near field (leaves of at most 1024 Gauss points)
