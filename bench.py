@@ -144,6 +144,27 @@ def measured_peaks():
         return {}
 
 
+def profiled_traffic(summary):
+    """DRAM bytes per launch (dram__bytes_read + dram__bytes_write) recorded by an ncu capture in
+    profiles/<summary>, or None when the kernel's source has changed since the capture (the
+    summary records the sha256 of the source file it was taken with)."""
+    import hashlib
+    import re
+    try:
+        text = open(os.path.join(ROOT, "profiles", summary)).read()
+    except OSError:
+        return None
+    m_b = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    m_s = re.search(r"source:\s*(\S+)\s+sha256\s+([0-9a-f]{64})", text)
+    if not m_b or not m_s:
+        return None
+    try:
+        digest = hashlib.sha256(open(os.path.join(ROOT, m_s.group(1)), "rb").read()).hexdigest()
+    except OSError:
+        return None
+    return float(m_b.group(1)) if digest == m_s.group(2) else None
+
+
 def oracle_sample(v, t, phi, n_rows, seed=0, reps=1):
     """Time the oracle's dense FP64 rows (the CPU baseline) on a sample of rows."""
     from oracle import dense
@@ -274,7 +295,8 @@ def run_ours(args, world, rank, local):
     p2p_ach = prof["p2p_interactions"] * P2P_FLOPS / (ms["p2p"] * 1e-3) / 1e12 if ms["p2p"] > 0 else 0.0
     p2p_peak = SM_COUNT * MUFU_PER_SM_CLK * smax * 1e6 * P2P_FLOPS / 1e12
     rl_p2p = {"bound": "alu", "kernel": "k_p2p_lap_src (near field, FP32 + MUFU rsqrt)", "achieved": round(p2p_ach, 3),
-              "peak": round(p2p_peak, 2), "unit": "TFLOP/s", "frac": round(p2p_ach / p2p_peak, 4), "traffic": None,
+              "peak": round(p2p_peak, 2), "unit": "TFLOP/s", "frac": round(p2p_ach / p2p_peak, 4),
+              "traffic": profiled_traffic("k_p2p_lap_src_traffic_laplace_ico6_81920.md"),
               "peak_source": "152 SMs x 16 rsqrt/clk x max SM clock x 11 flop per pair (derived, not measured)",
               "interactions_per_s": prof["p2p_interactions"] / (ms["p2p"] * 1e-3) if ms["p2p"] else None}
     bf16 = measured_peaks().get("bf16_tflops_sustained", 1729.8)
