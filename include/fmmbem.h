@@ -188,7 +188,8 @@ int fmmbem_relaxed_p(double eta, double rho_prev, int p_initial, int p_min);
 
 /*
  * Restarted GMRES(m) on A x = b (Sec. 2.4) with FP64 Arnoldi (classical
- * Gram-Schmidt applied twice), Givens rotations and the residual estimate
+ * Gram-Schmidt, reorthogonalized when the first projection removes more than
+ * half of the vector's squared norm), Givens rotations and the residual estimate
  * rho_k = |g_{k+1}| / ||b||. Step k uses the mat-vec at
  *   p_k = fmmbem_relaxed_p(tol, rho_{k-1}, p_initial, p_min)  if relax != 0,
  *   p_k = p_initial                                           otherwise.
@@ -292,6 +293,64 @@ int fmmbem_profile_get(fmmbem_handle* h, fmmbem_profile* out); /* synchronizes t
 
 /* Message of the last failure in this thread ("" if none). */
 const char* fmmbem_last_error(void);
+
+/*
+ * ---- Serving many solves at once.
+ *
+ * The paper solves one problem at a time. This is the request loop around its solver:
+ * solves of different meshes, operators and tolerances share one GPU.
+ *
+ * fmmbem_server_submit copies a request and queues it. max_active worker threads take
+ * queued requests in arrival order. A request is admitted as soon as:
+ *   - a worker is free, and
+ *   - the request's device-memory estimate (fmmbem_estimate_bytes) fits in what is left of
+ *     hbm_budget (one request is always admitted when nothing else is running).
+ * A smaller request that fits may therefore pass a larger one that does not.
+ *
+ * An admitted request is created, solved (fmmbem_solve_host) and destroyed on its worker's
+ * own CUDA stream. The workers' mat-vecs interleave on the device, and each request's state
+ * stays resident until its solve ends.
+ *
+ * Handles are independent and the library keeps no shared mutable state in a handle's path,
+ * so concurrent requests give the results they give alone, up to floating-point summation
+ * order.
+ */
+typedef struct fmmbem_server fmmbem_server;
+
+typedef struct {
+    int64_t ticket;
+    int status;            /* fmmbem_solve's return value, or a negative error from fmmbem_create */
+    int iters;             /* Arnoldi steps */
+    double true_res;       /* ||b - A x|| / ||b|| after the solve */
+    double queue_s;        /* submit -> admission */
+    double setup_s;        /* fmmbem_create */
+    double solve_s;        /* fmmbem_solve_host (copies included) and fmmbem_destroy */
+    double latency_s;      /* submit -> result ready */
+    int64_t device_bytes;  /* admission estimate */
+} fmmbem_result;
+
+/* Conservative estimate of the device memory of a handle (bytes), -1 for bad arguments. */
+int64_t fmmbem_estimate_bytes(int64_t n_panels, int kernel, int gauss_k, int ncrit, const fmmbem_opts* opts);
+
+/* Start max_active (1..64) workers on the current device with an HBM budget in bytes. */
+int fmmbem_server_create(int max_active, int64_t hbm_budget, fmmbem_server** out);
+
+/*
+ * Queue one solve. The mesh and rhs_host ([n_unknowns] doubles, host) are copied before the
+ * call returns. x_host ([n_unknowns] doubles, host) receives the solution and must stay valid
+ * until fmmbem_server_wait returns for the ticket. The other arguments are those of
+ * fmmbem_create and fmmbem_solve (opts->stream is ignored: each worker has its own).
+ * Errors: FMMBEM_EINVAL (NULL or empty arguments), FMMBEM_ESTATE (server shutting down).
+ */
+int fmmbem_server_submit(fmmbem_server* s, const fmmbem_mesh* mesh, int kernel, int gauss_k, int ncrit, double theta,
+                         const fmmbem_opts* opts, const double* rhs_host, double tol, int relax, int p_initial,
+                         int p_min, double* x_host, int64_t* ticket);
+
+/* Block until the ticket's request has finished and return its result (each ticket once). */
+int fmmbem_server_wait(fmmbem_server* s, int64_t ticket, fmmbem_result* out);
+
+/* Finish every queued request, stop the workers and free the server. NULL is ignored. */
+int fmmbem_server_destroy(fmmbem_server* s);
 
 #ifdef __cplusplus
 }

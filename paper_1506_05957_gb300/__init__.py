@@ -3,8 +3,10 @@
 The compute path is libfmmbem.so (hand-written sm_103a CUDA behind the C ABI in
 include/fmmbem.h); this package only builds and binds it.
 """
-from .binding import (FmmBem, FmmBemError, fmmbem_default_opts, fmmbem_expansion_eval, fmmbem_relaxed_p, lib,
-                      FMMBEM_LAPLACE, FMMBEM_STOKES, FMMBEM_FP64, FMMBEM_MIXED, FMMBEM_P_MAX)
+from .binding import (FmmBem, FmmBemError, FmmBemServer, fmmbem_default_opts, fmmbem_estimate_bytes,
+                      fmmbem_expansion_eval, fmmbem_relaxed_p, lib, FMMBEM_LAPLACE, FMMBEM_STOKES, FMMBEM_FP64,
+                      FMMBEM_MIXED, FMMBEM_P_MAX)
 
-__all__ = ["FmmBem", "FmmBemError", "fmmbem_default_opts", "fmmbem_expansion_eval", "fmmbem_relaxed_p", "lib",
+__all__ = ["FmmBem", "FmmBemError", "FmmBemServer", "fmmbem_default_opts", "fmmbem_estimate_bytes",
+           "fmmbem_expansion_eval", "fmmbem_relaxed_p", "lib",
            "FMMBEM_LAPLACE", "FMMBEM_STOKES", "FMMBEM_FP64", "FMMBEM_MIXED", "FMMBEM_P_MAX"]

@@ -55,6 +55,12 @@ class fmmbem_profile(ctypes.Structure):
                 ("kernel_launches", ctypes.c_int64)]
 
 
+class fmmbem_result(ctypes.Structure):
+    _fields_ = [("ticket", ctypes.c_int64), ("status", ctypes.c_int), ("iters", ctypes.c_int),
+                ("true_res", ctypes.c_double), ("queue_s", ctypes.c_double), ("setup_s", ctypes.c_double),
+                ("solve_s", ctypes.c_double), ("latency_s", ctypes.c_double), ("device_bytes", ctypes.c_int64)]
+
+
 _lib = None
 _dp = ctypes.POINTER(ctypes.c_double)
 _vp = ctypes.c_void_p
@@ -78,6 +84,16 @@ def lib():
         L.fmmbem_matvec.argtypes = [_vp, ctypes.c_int, _vp, _vp]
         L.fmmbem_set_m2l_mode.argtypes = [_vp, ctypes.c_int]
         L.fmmbem_set_p2p_variant.argtypes = [_vp, ctypes.c_int]
+        L.fmmbem_estimate_bytes.argtypes = [ctypes.c_int64, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                            ctypes.POINTER(fmmbem_opts)]
+        L.fmmbem_estimate_bytes.restype = ctypes.c_int64
+        L.fmmbem_server_create.argtypes = [ctypes.c_int, ctypes.c_int64, ctypes.POINTER(_vp)]
+        L.fmmbem_server_submit.argtypes = [_vp, ctypes.POINTER(fmmbem_mesh), ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                           ctypes.c_double, ctypes.POINTER(fmmbem_opts), _dp, ctypes.c_double,
+                                           ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp,
+                                           ctypes.POINTER(ctypes.c_int64)]
+        L.fmmbem_server_wait.argtypes = [_vp, ctypes.c_int64, ctypes.POINTER(fmmbem_result)]
+        L.fmmbem_server_destroy.argtypes = [_vp]
         L.fmmbem_matvec_direct.argtypes = [_vp, _vp, _vp]
         L.fmmbem_rhs.argtypes = [_vp, _vp, _vp]
         L.fmmbem_stokes_dl_apply.argtypes = [_vp, _vp, _vp]
@@ -235,3 +251,53 @@ class FmmBem:
                     calls={PASS_NAMES[i]: pr.calls[i] for i in range(8)},
                     m2l_flops=pr.m2l_flops, p2p_interactions=pr.p2p_interactions,
                     kernel_launches=pr.kernel_launches)
+
+
+class FmmBemServer:
+    """Serving runtime (fmmbem_server_*): solves of different meshes, operators and tolerances
+    admitted by an HBM budget and run concurrently by `max_active` worker threads of the library."""
+
+    def __init__(self, max_active=4, hbm_budget=None):
+        if hbm_budget is None:
+            import torch
+            hbm_budget = int(0.8 * torch.cuda.mem_get_info()[0])
+        s = _vp()
+        _check(lib().fmmbem_server_create(int(max_active), int(hbm_budget), ctypes.byref(s)))
+        self.s = s
+        self._pending = {}
+
+    def submit(self, vertices, triangles, rhs, kernel=FMMBEM_LAPLACE, gauss_k=4, ncrit=150, theta=0.5, p_max=16,
+               mu=1.0, precision=FMMBEM_MIXED, tol=1e-6, relax=True, p_initial=10, p_min=3):
+        v = np.ascontiguousarray(vertices, dtype=np.float64)
+        t = np.ascontiguousarray(triangles, dtype=np.int32)
+        b = np.ascontiguousarray(rhs, dtype=np.float64)
+        x = np.zeros_like(b)
+        mesh = fmmbem_mesh(len(v), v.ctypes.data_as(_dp), len(t), t.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)))
+        o = fmmbem_default_opts()
+        o.p_max, o.mu, o.precision = p_max, mu, precision
+        tk = ctypes.c_int64()
+        _check(lib().fmmbem_server_submit(self.s, ctypes.byref(mesh), int(kernel), int(gauss_k), int(ncrit),
+                                          float(theta), ctypes.byref(o), b.ctypes.data_as(_dp), float(tol),
+                                          int(bool(relax)), int(p_initial), int(p_min), x.ctypes.data_as(_dp),
+                                          ctypes.byref(tk)))
+        self._pending[tk.value] = x  # the library writes the solution here
+        return tk.value
+
+    def wait(self, ticket):
+        r = fmmbem_result()
+        _check(lib().fmmbem_server_wait(self.s, int(ticket), ctypes.byref(r)))
+        x = self._pending.pop(ticket)
+        return x, {n: getattr(r, n) for n, _ in fmmbem_result._fields_}
+
+    def close(self):
+        if getattr(self, "s", None):
+            lib().fmmbem_server_destroy(self.s)
+            self.s = None
+
+    __del__ = close
+
+
+def fmmbem_estimate_bytes(n_panels, kernel=FMMBEM_LAPLACE, gauss_k=4, ncrit=150, p_max=16):
+    o = fmmbem_default_opts()
+    o.p_max = p_max
+    return lib().fmmbem_estimate_bytes(int(n_panels), int(kernel), int(gauss_k), int(ncrit), ctypes.byref(o))

@@ -14,10 +14,11 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libfmmbem.so")
-SOURCES = ["setup.cu", "fmm.cu", "m2l.cu", "m2l_tc.cu", "near.cu", "krylov.cu", "capi.cu"]
+SOURCES = ["setup.cu", "fmm.cu", "m2l.cu", "m2l_tc.cu", "near.cu", "krylov.cu", "capi.cu", "serve.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "nvcc")
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I" + INCLUDE, "-I" + CSRC]
+LINK = ["-lpthread"]
 
 
 def _compile(src, verbose):
@@ -48,7 +49,7 @@ def build(force=False, verbose=False):
         for _, log in results:
             sys.stderr.write(log)
     tmp = LIB + ".tmp.%d" % os.getpid()
-    cmd = [NVCC] + ARCH + ["-shared", "-o", tmp] + [o for o, _ in results]
+    cmd = [NVCC] + ARCH + ["-shared", "-o", tmp] + [o for o, _ in results] + LINK
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n%s%s" % (r.stdout, r.stderr))

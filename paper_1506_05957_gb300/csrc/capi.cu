@@ -85,25 +85,19 @@ int dalloc(P** p, size_t count) {
 
 }  // namespace
 
-// Profiling state lives beside the handle (allocated on first use).
-static std::vector<std::pair<fmmbem_handle*, ProfState*>> g_prof;
-
+// Profiling state lives in the handle (allocated on first use), so handles driven from
+// different host threads share nothing.
 namespace {
 ProfState* prof_state(fmmbem_handle* h) {
-    for (auto& e : g_prof)
-        if (e.first == h) return e.second;
-    ProfState* s = new ProfState();
-    g_prof.push_back({h, s});
-    return s;
+    if (!h->prof_state) h->prof_state = new ProfState();
+    return reinterpret_cast<ProfState*>(h->prof_state);
 }
 void prof_free(fmmbem_handle* h) {
-    for (size_t i = 0; i < g_prof.size(); ++i)
-        if (g_prof[i].first == h) {
-            for (auto ev : g_prof[i].second->pool) cudaEventDestroy(ev);
-            delete g_prof[i].second;
-            g_prof.erase(g_prof.begin() + i);
-            return;
-        }
+    ProfState* s = reinterpret_cast<ProfState*>(h->prof_state);
+    if (!s) return;
+    for (auto ev : s->pool) cudaEventDestroy(ev);
+    delete s;
+    h->prof_state = nullptr;
 }
 cudaEvent_t prof_event(ProfState* s) {
     if (s->used == s->pool.size()) {
@@ -337,7 +331,8 @@ int fmmbem_create(const fmmbem_mesh* mesh, int kernel, int gauss_k, int ncrit, d
     h->kr_m = o.restart;
     if ((rc = dalloc((double**)&h->M, ex)) < 0) return fail(rc);
     if ((rc = dalloc((double**)&h->L, ex)) < 0) return fail(rc);
-    if ((rc = dalloc(&h->src_w, h->NS)) < 0) return fail(rc);
+    // per-mat-vec packed sources: one float4 per Gauss point (Laplace), two (Stokes)
+    if ((rc = dalloc(&h->src_w, (size_t)h->NS * (kernel == FMMBEM_STOKES ? 2 : 1))) < 0) return fail(rc);
     if ((rc = dalloc(&h->xs, n)) < 0 || (rc = dalloc(&h->ys, n)) < 0 || (rc = dalloc(&h->ynear, n)) < 0) return fail(rc);
     if ((rc = dalloc(&h->V, (size_t)(o.restart + 1) * n)) < 0) return fail(rc);
     if ((rc = dalloc(&h->xfix, n)) < 0) return fail(rc);

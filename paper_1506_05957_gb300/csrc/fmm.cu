@@ -451,15 +451,22 @@ __global__ void k_eval_expansion(int kind, int p, double cx, double cy, double c
     out[i] = phi / s;
 }
 
-bool g_deg_ready = false;
+// The degree table lives in constant memory of each device; it is filled once per device,
+// under a lock (handles may be created from several host threads).
+std::mutex g_deg_mutex;
+bool g_deg_ready[64] = {};
 
 int ensure_degree_table() {
-    if (g_deg_ready) return 0;
+    int dev = 0;
+    FMM_CU(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) { fmmbem_set_error("device ordinal %d out of range", dev); return FMMBEM_EDEVICE; }
+    std::lock_guard<std::mutex> lock(g_deg_mutex);
+    if (g_deg_ready[dev]) return 0;
     unsigned char deg[NCOEF_MAX];
     for (int n = 0; n <= PMAX; ++n)
         for (int m = 0; m <= n; ++m) deg[cidx(n, m)] = (unsigned char)n;
     FMM_CU(cudaMemcpyToSymbol(c_deg, deg, sizeof(deg)));
-    g_deg_ready = true;
+    g_deg_ready[dev] = true;
     return 0;
 }
 

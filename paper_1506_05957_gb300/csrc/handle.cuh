@@ -158,6 +158,7 @@ struct fmmbem_handle {
     bool prof_on = false;
     fmmbem_profile prof{};
     cudaEvent_t ev[2 * FMMBEM_N_PASSES] = {};
+    void* prof_state = nullptr;  // per-handle event pool and pending intervals (capi.cu)
     int64_t launches = 0;
 };
 

@@ -1,6 +1,7 @@
 // Relaxed restarted GMRES(m) (Sec. 2.4 and 2.6) with the Krylov recurrence in FP64.
-// Arnoldi: classical Gram-Schmidt applied twice (CGS2), as batched dot products and
-// one fused update per pass, all on the device; the (m+1) x m Hessenberg column,
+// Arnoldi: classical Gram-Schmidt with selective reorthogonalization (a second pass only
+// when the first one cancels more than half of ||w||^2), as batched dot products and a
+// fused update-and-normalize sweep, all on the device; the (m+1) x m Hessenberg column,
 // Givens rotations and the residual estimate rho_k = |g_{k+1}| / ||b|| live on the
 // host (k+3 doubles cross per step). Step k runs the mat-vec at
 //   p_k = min(p_initial, max(p_min, ceil(-log2 eps_k))),
@@ -84,8 +85,8 @@ __global__ void k_sub(double* r, const double* b, const double* ax, int64_t n) {
         r[i] = b[i] - ax[i];
 }
 
-// ---- fused Arnoldi step: classical Gram-Schmidt twice, the norm and the new basis
-// vector in one cooperative launch (all blocks co-resident). Between phases the blocks
+// ---- fused Arnoldi step: the projections, the norm and the new basis vector in one
+// cooperative launch (all blocks co-resident). Between phases the blocks
 // meet at a sense-reversal grid barrier whose wait is bounded: on timeout the kernel
 // flags an error and stops. Each block reduces the per-block partial dots itself in a
 // fixed order (results are deterministic); block 0 writes h1, h2 and ||w||^2 to out
@@ -167,10 +168,40 @@ __device__ void arn_reduce(const double* partial, int nv, double* hs) {
     __syncthreads();
 }
 
+// w[i] -= sum_j hs[j] V_j[i] over the block's rows (eight independent loads per group);
+// with scale != 0 the result is also multiplied by scale and written to V_{k+1} and xfix.
+__device__ void arn_update(const double* V, int64_t n, int nv, const double* hs, double* w, int64_t i0, int64_t i1,
+                           double scale, double* vk1, double* xfix) {
+    for (int64_t i = i0 + threadIdx.x; i < i1; i += ARN_THREADS) {
+        double t = 0.0;
+        for (int j0 = 0; j0 < nv; j0 += 8) {
+            double v[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) v[q] = j0 + q < nv ? V[(int64_t)(j0 + q) * n + i] : 0.0;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) t += (j0 + q < nv ? hs[j0 + q] : 0.0) * v[q];
+        }
+        const double r = w[i] - t;
+        if (scale != 0.0) {
+            const double u = r * scale;
+            vk1[i] = u;
+            xfix[i] = u;
+        } else {
+            w[i] = r;
+        }
+    }
+}
+
+// Classical Gram-Schmidt with selective reorthogonalization (the criterion of Daniel,
+// Gragg, Kaufman and Stewart): one sweep gives h = V^T w and ||w||^2; when
+// ||w - V h||^2 = ||w||^2 - ||h||^2 stays above ||w||^2 / 2 the projected vector is
+// normalized and written as V_{k+1} in the same sweep that forms it (one grid barrier).
+// Otherwise a second projection pass and an explicit norm follow (the CGS2 step).
 __global__ void __launch_bounds__(ARN_THREADS) k_arnoldi(double* V, int64_t n, int k, double* w, double* xfix,
                                                          double* partial, unsigned* bar_count, unsigned* bar_gen,
                                                          double* out, int* err) {
     __shared__ double hs[ARN_MAXV];
+    __shared__ double h1[ARN_MAXV];
     const int nv = k + 1;
     const int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
     const int64_t i0 = (int64_t)blockIdx.x * chunk, i1 = min(n, i0 + chunk);
@@ -178,37 +209,47 @@ __global__ void __launch_bounds__(ARN_THREADS) k_arnoldi(double* V, int64_t n, i
     // each phase has its own partial-sum area, so one grid barrier per phase suffices:
     // a block's w rows are read and written by that block alone
     const size_t parea = (size_t)ARN_MAXV * gridDim.x;
-    for (int pass = 0; pass < 2; ++pass) {
-        double* part = partial + pass * parea;
-        arn_partials(V, n, nv, w, i0, i1, part);
-        if (!grid_barrier(bar_count, bar_gen, nb, err)) return;
-        arn_reduce(part, nv, hs);
-        if (blockIdx.x == 0)
-            for (int j = threadIdx.x; j < nv; j += ARN_THREADS) out[pass * (ARN_MAXV + 1) + j] = hs[j];
-        for (int64_t i = i0 + threadIdx.x; i < i1; i += ARN_THREADS) {
-            // eight independent loads per group, so the group costs one memory latency
-            double t = 0.0;
-            for (int j0 = 0; j0 < nv; j0 += 8) {
-                double v[8];
-#pragma unroll
-                for (int q = 0; q < 8; ++q) v[q] = j0 + q < nv ? V[(int64_t)(j0 + q) * n + i] : 0.0;
-#pragma unroll
-                for (int q = 0; q < 8; ++q) t += (j0 + q < nv ? hs[j0 + q] : 0.0) * v[q];
-            }
-            w[i] -= t;
-        }
-        __syncthreads();  // hs is rewritten by the next phase's reduction
-    }
-    double* part = partial + 2 * parea;
-    arn_partials(w, n, 1, w, i0, i1, part);
+    double* vk1 = V + (int64_t)(k + 1) * n;
+    // phase 1: h = V^T w and ||w||^2
+    arn_partials(V, n, nv, w, i0, i1, partial);
+    arn_partials(w, n, 1, w, i0, i1, partial + (size_t)nv * gridDim.x);
     if (!grid_barrier(bar_count, bar_gen, nb, err)) return;
-    arn_reduce(part, 1, hs);
+    arn_reduce(partial, nv + 1, hs);
+    const double ww = hs[nv];
+    double hh = 0.0;
+    for (int j = 0; j < nv; ++j) hh += hs[j] * hs[j];
+    const double nn2 = ww - hh;
+    if (blockIdx.x == 0)
+        for (int j = threadIdx.x; j < nv; j += ARN_THREADS) out[j] = hs[j];
+    if (nn2 > 0.5 * ww && nn2 > 0.0 && isfinite(nn2)) {
+        if (blockIdx.x == 0) {
+            for (int j = threadIdx.x; j < nv; j += ARN_THREADS) out[(ARN_MAXV + 1) + j] = 0.0;
+            if (threadIdx.x == 0) out[2 * (ARN_MAXV + 1)] = nn2;
+        }
+        arn_update(V, n, nv, hs, w, i0, i1, 1.0 / sqrt(nn2), vk1, xfix);
+        return;
+    }
+    // phase 2: reorthogonalize
+    for (int j = threadIdx.x; j < nv; j += ARN_THREADS) h1[j] = hs[j];
+    __syncthreads();
+    arn_update(V, n, nv, h1, w, i0, i1, 0.0, nullptr, nullptr);
+    double* part2 = partial + parea;
+    arn_partials(V, n, nv, w, i0, i1, part2);
+    if (!grid_barrier(bar_count, bar_gen, nb, err)) return;
+    arn_reduce(part2, nv, hs);
+    if (blockIdx.x == 0)
+        for (int j = threadIdx.x; j < nv; j += ARN_THREADS) out[(ARN_MAXV + 1) + j] = hs[j];
+    arn_update(V, n, nv, hs, w, i0, i1, 0.0, nullptr, nullptr);
+    // phase 3: the norm of the twice-projected vector
+    double* part3 = partial + 2 * parea;
+    arn_partials(w, n, 1, w, i0, i1, part3);
+    if (!grid_barrier(bar_count, bar_gen, nb, err)) return;
+    arn_reduce(part3, 1, hs);
     const double nrm2 = hs[0];
     if (blockIdx.x == 0 && threadIdx.x == 0) out[2 * (ARN_MAXV + 1)] = nrm2;
     const double hn = sqrt(nrm2);
     if (hn > 0.0 && isfinite(hn)) {
         const double inv = 1.0 / hn;
-        double* vk1 = V + (int64_t)(k + 1) * n;
         for (int64_t i = i0 + threadIdx.x; i < i1; i += ARN_THREADS) {
             const double v = w[i] * inv;
             vk1[i] = v;
@@ -261,7 +302,8 @@ int arnoldi_blocks() {
     if (cudaGetDevice(&dev) != cudaSuccess) return 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_arnoldi, ARN_THREADS, 0) != cudaSuccess || per < 1) return 0;
-    return sms;  // one block per SM: co-resident for the cooperative launch
+    return sms;  // one block per SM: co-resident for the cooperative launch (more blocks make
+                 // the grid barriers dearer than the extra loads in flight gain)
 }
 
 int relaxed_p(double eta, double rho_prev, int p_initial, int p_min) {
@@ -352,7 +394,7 @@ static int gmres_solve_on(fmmbem_handle* h, const double* b, double tol, int rel
             ++it;
             prof_begin(h, FMMBEM_PASS_KRYLOV);
             {
-                // fused CGS2 step; results in mapped pinned memory
+                // fused Arnoldi step; results in mapped pinned memory
                 double* dV = h->V;
                 int64_t nn = n;
                 int kk = k;

@@ -803,6 +803,167 @@ __global__ void __launch_bounds__(32 * PS_WARPS, 6) k_p2p_lap_src(const int4* it
     }
 }
 
+// Stokeslet near field with the same source-lane schedule: per mat-vec each Gauss point
+// is packed as two float4, (leaf-relative position, f_x) and (f_y, f_z, -, -) with
+// f = q_k S_J t_J; a work item holds at most P2P_SRC_TMAX_STOKES targets with three FP32
+// accumulators each. Per source and target: d = x - y, r^-1 by rsqrt, and
+// u += f / r + d (d.f) / r^3 (eq. stokeslet), folded every PS_FOLD rounds into
+// compensated per-lane sums.
+constexpr int SS_TMAX = P2P_SRC_TMAX_STOKES;
+constexpr int SS_SRC = 2;  // sources per lane per round
+
+__global__ void k_pack_sources_stokes(const float4* src_rel, const double* xs, int K, int64_t ns, float4* out) {
+    const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (g >= ns) return;
+    const float4 y = src_rel[g];
+    const int64_t j = g / K;
+    const double w = (double)y.w;
+    out[2 * g] = make_float4(y.x, y.y, y.z, (float)(w * xs[3 * j]));
+    out[2 * g + 1] = make_float4((float)(w * xs[3 * j + 1]), (float)(w * xs[3 * j + 2]), 0.f, 0.f);
+}
+
+struct SsShared {
+    float4 t[SS_TMAX];
+    float2 hl[PS_WARPS][SS_TMAX * 3][32];
+    float4 rec[PS_EMAX];
+    int off[PS_EMAX + 1];
+};
+
+__device__ __forceinline__ void ss_pair(float4 x, float4 a, float4 b, bool skip, float* acc3) {
+    const float dx = x.x - a.x, dy = x.y - a.y, dz = x.z - a.z;
+    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+    const float ir = skip ? 0.f : rsqrt_approx(skip ? 1.f : r2);
+    const float ir3 = ir * ir * ir;
+    const float df = fmaf(dx, a.w, fmaf(dy, b.x, dz * b.y)) * ir3;
+    acc3[0] = fmaf(a.w, ir, fmaf(dx, df, acc3[0]));
+    acc3[1] = fmaf(b.x, ir, fmaf(dy, df, acc3[1]));
+    acc3[2] = fmaf(b.y, ir, fmaf(dz, df, acc3[2]));
+}
+
+__global__ void __launch_bounds__(32 * PS_WARPS, 5) k_p2p_stk_src(const int4* items, const int2* range, const int* pptr,
+                                                                 const float4* prec, const int* poff, const int* plen,
+                                                                 const float4* srcw, const float4* tgt, int K,
+                                                                 const int* cptr, const int* ccol, const double* cval,
+                                                                 const double* xs, double* ynear) {
+    __shared__ SsShared sh;
+    constexpr int RND = 32 * SS_SRC;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int4 item = items[blockIdx.x];
+    const int cell = item.x, tb = item.y, ntb = item.z;
+    const int2 r = range[cell];
+    const int e0 = pptr[cell], e1 = pptr[cell + 1];
+    const int total = plen[cell];
+    float2* sHL = &sh.hl[warp][0][0];
+    const float4 far_a = make_float4(1e18f, 0.f, 0.f, 0.f), zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int i = threadIdx.x; i < ntb; i += blockDim.x) sh.t[i] = tgt[tb + i];
+    for (int i = 0; i < 3 * ntb; ++i) sHL[i * 32 + lane] = make_float2(0.f, 0.f);
+    float acc[SS_TMAX][3];
+#pragma unroll
+    for (int i = 0; i < SS_TMAX; ++i) acc[i][0] = acc[i][1] = acc[i][2] = 0.f;
+    int rounds = 0;
+    auto fold = [&]() {
+#pragma unroll
+        for (int i = 0; i < SS_TMAX; ++i) {
+            if (i < ntb) {
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    float2 v = sHL[(3 * i + a) * 32 + lane];
+                    kahan_add(v.x, v.y, acc[i][a]);
+                    sHL[(3 * i + a) * 32 + lane] = v;
+                }
+            }
+            acc[i][0] = acc[i][1] = acc[i][2] = 0.f;
+            asm volatile("" ::: "memory");
+        }
+    };
+    __syncthreads();
+    // own leaf (own panel skipped)
+    {
+        const int g0 = r.x * K, n = (r.y - r.x) * K;
+        for (int base = RND * warp; base < n; base += RND * PS_WARPS) {
+            float4 ua[SS_SRC], ub[SS_SRC];
+            int gp[SS_SRC];
+#pragma unroll
+            for (int h = 0; h < SS_SRC; ++h) {
+                const int q = base + 32 * h + lane;
+                ua[h] = q < n ? srcw[2 * (g0 + q)] : far_a;
+                ub[h] = q < n ? srcw[2 * (g0 + q) + 1] : zero4;
+                gp[h] = q < n ? (g0 + q) / K : -1;
+            }
+#pragma unroll
+            for (int i = 0; i < SS_TMAX; ++i) {
+                if (i < ntb) {
+                    const float4 x = sh.t[i];
+#pragma unroll
+                    for (int h = 0; h < SS_SRC; ++h) ss_pair(x, ua[h], ub[h], gp[h] == tb + i, acc[i]);
+                }
+                asm volatile("" ::: "memory");
+            }
+            if (++rounds == PS_FOLD) { fold(); rounds = 0; }
+        }
+    }
+    // the other leaves of the P2P list, as one stream
+    for (int eb = e0; eb < e1; eb += PS_EMAX) {
+        const int ne = min(PS_EMAX, e1 - eb);
+        __syncthreads();
+        for (int j = threadIdx.x; j < ne; j += blockDim.x) {
+            sh.rec[j] = prec[eb + j];
+            sh.off[j] = poff[eb + j];
+        }
+        if (threadIdx.x == 0) sh.off[ne] = (eb + PS_EMAX < e1) ? poff[eb + PS_EMAX] : total;
+        __syncthreads();
+        const int s_beg = sh.off[0], s_end = sh.off[ne];
+        int cur = 0;
+        for (int base = s_beg + RND * warp; base < s_end; base += RND * PS_WARPS) {
+            float4 ua[SS_SRC], ub[SS_SRC];
+#pragma unroll
+            for (int h = 0; h < SS_SRC; ++h) {
+                const int pos = base + 32 * h + lane;
+                ua[h] = far_a;
+                ub[h] = zero4;
+                if (pos < s_end) {
+                    while (sh.off[cur + 1] <= pos) ++cur;
+                    const float4 rc = sh.rec[cur];
+                    const int g = __float_as_int(rc.w) + (pos - sh.off[cur]);
+                    float4 a = srcw[2 * g];
+                    a.x += rc.x; a.y += rc.y; a.z += rc.z;
+                    ua[h] = a;
+                    ub[h] = srcw[2 * g + 1];
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < SS_TMAX; ++i) {
+                if (i < ntb) {
+                    const float4 x = sh.t[i];
+#pragma unroll
+                    for (int h = 0; h < SS_SRC; ++h) ss_pair(x, ua[h], ub[h], false, acc[i]);
+                }
+                asm volatile("" ::: "memory");
+            }
+            if (++rounds == PS_FOLD) { fold(); rounds = 0; }
+        }
+    }
+    fold();
+    __syncthreads();
+    for (int i = threadIdx.x; i < ntb; i += blockDim.x) {
+        double out[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            float hi = 0.f, lo = 0.f;
+            for (int w = 0; w < PS_WARPS; ++w)
+                for (int k = 0; k < 32; ++k) {
+                    const float2 v = sh.hl[w][3 * i + a][(k + i) & 31];
+                    kahan_add(hi, lo, v.x);
+                    kahan_add(hi, lo, -v.y);
+                }
+            out[a] = (double)hi - (double)lo;
+        }
+        add_correction<3>(tb + i, cptr, ccol, cval, xs, out);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) ynear[3 * (int64_t)(tb + i) + a] = out[a];
+    }
+}
+
 // Direct: one thread per target, every Gauss point staged through shared memory.
 template <typename T, int OP>
 __global__ void __launch_bounds__(P2P_THREADS) k_direct(int n, int ns, const typename V4<T>::type* src,
@@ -937,7 +1098,16 @@ int near_field_on(fmmbem_handle* h, bool fp64) {
         FMM_LAUNCHED();
         h->launches += (n1 > 0) + (n2 > 0) + (n3 > 0);
     } else if (h->kernel == FMMBEM_LAPLACE) rc = launch_p2p<double, LAP_SL>(h);
-    else rc = fp64 ? launch_p2p<double, STK_SL>(h) : launch_p2p<float, STK_SL>(h);
+    else if (!fp64 && h->p2p_variant == 3 && h->p2p_items) {
+        k_pack_sources_stokes<<<(unsigned)((h->NS + 255) / 256), 256, 0, h->stream>>>(h->src_rel, h->xin, h->K, h->NS,
+                                                                                     h->src_w);
+        FMM_LAUNCHED();
+        k_p2p_stk_src<<<h->n_p2p_items, 32 * PS_WARPS, 0, h->stream>>>(
+            h->p2p_items, h->cell_range, h->p2p_ptr, h->p2p_rec, h->p2p_off, h->p2p_len, h->src_w, h->tgt_rel, h->K,
+            h->corr_ptr, h->corr_col, h->corr_sl, h->xin, h->ynear);
+        FMM_LAUNCHED();
+        h->launches += 1;
+    } else rc = fp64 ? launch_p2p<double, STK_SL>(h) : launch_p2p<float, STK_SL>(h);
     prof_end(h, FMMBEM_PASS_P2P, 1);
     h->launches += 1;
     return rc;

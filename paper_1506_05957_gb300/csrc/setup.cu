@@ -974,12 +974,13 @@ int build_geometry_tree_lists(fmmbem_handle* h, const fmmbem_mesh* mesh) {
             FMM_CU(cudaMemcpyAsync(rg.data(), h->cell_range, sizeof(int2) * nc, cudaMemcpyDeviceToHost, st));
             FMM_CU(cudaStreamSynchronize(st));
             // work items of the source-lane kernel: (leaf, first target, target count), a leaf's
-            // targets split evenly into chunks of at most P2P_SRC_TMAX, largest work first
+            // targets split evenly into chunks of at most tmax, largest work first
             std::vector<int4> items;
             std::vector<long long> cost;
+            const int tmax = h->kernel == FMMBEM_STOKES ? P2P_SRC_TMAX_STOKES : P2P_SRC_TMAX;
             for (int c : lv) {
                 const int t = rg[c].y - rg[c].x;
-                const int nchk = (t + P2P_SRC_TMAX - 1) / P2P_SRC_TMAX;
+                const int nchk = (t + tmax - 1) / tmax;
                 for (int q = 0; q < nchk; ++q) {
                     const int b = rg[c].x + (int)((long long)t * q / nchk), e = rg[c].x + (int)((long long)t * (q + 1) / nchk);
                     items.push_back(make_int4(c, b, e - b, 0));

@@ -5,8 +5,8 @@ meshes (vertex coordinates and triangle connectivity) and seeded random vectors.
 Panel centroids, normals, areas, quadrature points and all kernel evaluations are
 computed separately by each side.
 """
-from .mesh import (icosphere, octasphere, evans_fung_cell, place_cells,
+from .mesh import (icosphere, octasphere, ellipsoid, evans_fung_cell, place_cells,
                    random_vector, point_charge_dirichlet)
 
-__all__ = ["icosphere", "octasphere", "evans_fung_cell", "place_cells",
+__all__ = ["icosphere", "octasphere", "ellipsoid", "evans_fung_cell", "place_cells",
            "random_vector", "point_charge_dirichlet"]

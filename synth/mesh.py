@@ -11,7 +11,7 @@ rbc_parameterization) to the vertices of a sphere mesh.
 """
 import numpy as np
 
-__all__ = ["icosphere", "octasphere", "evans_fung_cell", "place_cells",
+__all__ = ["icosphere", "octasphere", "ellipsoid", "evans_fung_cell", "place_cells",
            "random_vector", "point_charge_dirichlet"]
 
 
@@ -70,6 +70,13 @@ def icosphere(levels, radius=1.0, center=(0.0, 0.0, 0.0)):
     t = _orient_outward(v, t)
     v, t = _refine(v, t, levels, radius)
     return v + np.asarray(center, dtype=np.float64), t
+
+
+def ellipsoid(levels, axes=(1.0, 1.0, 1.0), center=(0.0, 0.0, 0.0)):
+    """Ellipsoid with the given semi-axes: a unit icosphere scaled along x, y, z (positive
+    factors keep the outward orientation)."""
+    v, t = icosphere(levels)
+    return v * np.asarray(axes, dtype=np.float64) + np.asarray(center, dtype=np.float64), t
 
 
 def octasphere(levels, radius=1.0, center=(0.0, 0.0, 0.0)):

@@ -76,3 +76,39 @@ def test_fullsize_relaxed_solve_sampled_residual(torch_cuda, big):
     res = big["M"].laplace_apply(x.cpu().numpy(), rows=rows) - bs
     print("iters", r["iters"], "sampled oracle residual", np.linalg.norm(res) / np.linalg.norm(bs))
     assert np.linalg.norm(res) / np.linalg.norm(bs) < 2e-6
+
+
+def test_fullsize_stokes_matvec_and_drag(torch_cuda):
+    """Stokes flow past a sphere at 81920 panels (245760 unknowns), K = 3, mu = 1: sampled
+    rows of the mixed-precision FMM mat-vec against the oracle's Stokeslet rows, and the
+    relaxed solve's drag against 6 pi mu a U (u = U imposed on the body: F = -6 pi mu a U)."""
+    torch = torch_cuda
+    from oracle import dense, panels
+    from oracle.schedule import schedule
+    from synth import icosphere
+    from paper_1506_05957_gb300 import FmmBem, FMMBEM_MIXED, FMMBEM_STOKES
+    v, t = icosphere(6)
+    _, _, S = panels.geometry(v, t)
+    h = FmmBem(v, t, kernel=FMMBEM_STOKES, gauss_k=3, ncrit=150, theta=0.5, p_max=16, precision=FMMBEM_MIXED)
+    M = dense.Mesh(v, t, k=3)
+    rows = np.sort(np.random.default_rng(5).choice(len(t), 96, replace=False))
+    x = np.random.default_rng(6).standard_normal(h.n)
+    xd = torch.tensor(x, dtype=torch.float64, device="cuda")
+    y = torch.zeros_like(xd)
+    h.matvec(16, xd, y)
+    ref = M.stokes_apply(x, rows=rows).reshape(-1)
+    got = y.cpu().numpy().reshape(-1, 3)[rows].reshape(-1)
+    print("stokes p16 sampled rel L2", np.linalg.norm(got - ref) / np.linalg.norm(ref))
+    assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < 1e-5
+    U = np.tile([1.0, 0.0, 0.0], len(t))
+    b = torch.tensor(U, dtype=torch.float64, device="cuda")
+    sol = torch.zeros_like(b)
+    r = h.solve(b, sol, tol=1e-5, relax=True, p_initial=16, p_min=4)
+    assert r["converged"] and r["true_res"] < 2e-5
+    assert r["p_hist"] == schedule(1e-5, r["res_hist"][:-1], 16, 4)
+    tr = sol.cpu().numpy().reshape(-1, 3)
+    F = float(np.sum(tr[:, 0] * S))
+    print("stokes drag", F, "iters", r["iters"], r["p_hist"])
+    assert F < 0 and abs(F / (-6.0 * np.pi) - 1.0) < 5e-3
+    res = M.stokes_apply(tr.reshape(-1), rows=rows).reshape(-1) - U.reshape(-1, 3)[rows].reshape(-1)
+    assert np.linalg.norm(res) / np.linalg.norm(U.reshape(-1, 3)[rows]) < 2e-5

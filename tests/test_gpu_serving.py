@@ -1,0 +1,82 @@
+"""Serving runtime (fmmbem_server_*): solves of different meshes, operators and tolerances
+submitted together, admitted by an HBM budget and run concurrently by the library's worker
+threads. Each result must be the one the same solve gives alone, within the solver
+tolerance, and the admission must respect the budget."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1506_05957_gb300 import build
+    build.build()
+    return torch
+
+
+def _requests():
+    from synth import icosphere, ellipsoid, evans_fung_cell, place_cells, point_charge_dirichlet
+    from paper_1506_05957_gb300 import FMMBEM_LAPLACE, FMMBEM_STOKES
+    reqs = []
+
+    def laplace(v, t, tol):
+        c = v[t].mean(axis=1)
+        lo, hi = v.min(0), v.max(0)
+        z0 = 0.5 * (lo + hi) + np.array([0.0, 0.0, 1.5 * (hi - lo).max()])  # outside the body
+        # the right-hand side is the potential of the charge itself (first kind with the
+        # charge's values as data: a valid, well-posed system for the test)
+        return dict(v=v, t=t, rhs=point_charge_dirichlet(c, z0), kernel=FMMBEM_LAPLACE, gauss_k=4, tol=tol,
+                    p_initial=10, p_min=3)
+
+    def stokes(v, t, tol):
+        return dict(v=v, t=t, rhs=np.tile([1.0, 0.0, 0.0], len(t)), kernel=FMMBEM_STOKES, gauss_k=3, tol=tol,
+                    p_initial=16, p_min=4)
+
+    v, t = icosphere(3)
+    reqs.append(laplace(v, t, 1e-6))
+    v, t = ellipsoid(4, (1.0, 0.7, 1.6))
+    reqs.append(laplace(v, t, 1e-4))
+    v, t = icosphere(3)
+    reqs.append(stokes(v, t, 1e-5))
+    cv, ct = evans_fung_cell(3)
+    v, t, _ = place_cells(cv, ct, 2, box=20.0, seed=1)
+    reqs.append(laplace(v, t, 1e-6))
+    v, t = ellipsoid(3, (1.8, 0.6, 0.9))
+    reqs.append(stokes(v, t, 1e-5))
+    v, t = icosphere(4)
+    reqs.append(laplace(v, t, 1e-8))
+    return reqs
+
+
+def test_mixed_requests_match_solo_solves(torch_cuda):
+    from paper_1506_05957_gb300 import FmmBem, FmmBemServer, fmmbem_estimate_bytes
+    reqs = _requests()
+    solo = []
+    for r in reqs:
+        h = FmmBem(r["v"], r["t"], kernel=r["kernel"], gauss_k=r["gauss_k"], ncrit=150, theta=0.5, p_max=16)
+        x = np.zeros_like(r["rhs"])
+        res = h.solve_host(np.ascontiguousarray(r["rhs"]), x, tol=r["tol"], relax=True, p_initial=r["p_initial"],
+                           p_min=r["p_min"])
+        h.close()
+        solo.append((x, res))
+    # budget for about two requests at a time, three workers: admission has to queue some
+    est = [fmmbem_estimate_bytes(len(r["t"]), r["kernel"], r["gauss_k"]) for r in reqs]
+    srv = FmmBemServer(max_active=3, hbm_budget=int(2.2 * max(est)))
+    tickets = [srv.submit(r["v"], r["t"], r["rhs"], kernel=r["kernel"], gauss_k=r["gauss_k"], tol=r["tol"],
+                          p_initial=r["p_initial"], p_min=r["p_min"]) for r in reqs]
+    out = [srv.wait(tk) for tk in tickets]
+    srv.close()
+    for r, (xs, rs), (xm, info) in zip(reqs, solo, out):
+        assert info["status"] == 0, info
+        assert abs(info["iters"] - rs["iters"]) <= 1, (info, rs["iters"])
+        diff = np.linalg.norm(xm - xs) / np.linalg.norm(xs)
+        print(len(r["t"]), "kernel", r["kernel"], "tol", r["tol"], "iters", info["iters"], "diff", diff,
+              "queue %.3f setup %.3f solve %.3f" % (info["queue_s"], info["setup_s"], info["solve_s"]))
+        assert diff <= 10 * r["tol"]
+        assert info["true_res"] <= 2 * r["tol"]
+    # some requests had to wait for memory or a worker
+    assert max(info["queue_s"] for _, info in out) > 0.0
