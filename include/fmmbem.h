@@ -80,7 +80,9 @@ typedef struct {
     int precision;        /* FMMBEM_MIXED */
     int restart;          /* 50: GMRES restart length m */
     int max_iter;         /* 100: cap on Arnoldi steps (the paper's cap, Table stokes_min_p) */
-    void* stream;         /* NULL: the legacy default stream; else a cudaStream_t for all work */
+    void* stream;         /* NULL: the legacy default stream; else a cudaStream_t for all work;
+                             it must stay valid until fmmbem_destroy returns (the handle's
+                             device memory is stream-ordered and is released on it) */
 } fmmbem_opts;
 
 typedef struct fmmbem_handle fmmbem_handle;
@@ -140,6 +142,23 @@ int fmmbem_set_m2l_mode(fmmbem_handle* h, int mode);
  *     targets looped in registers (default).
  * Returns FMMBEM_EINVAL for any other value. */
 int fmmbem_set_p2p_variant(fmmbem_handle* h, int variant);
+
+/* Which boundary-integral operator A the mat-vecs and solves of a Laplace handle apply
+ * (eq. laplace_matrix):
+ *   SINGLE : A = V, V_ij = (1/4pi) int_j 1/r dS; the first-kind system for the unknown
+ *            normal derivative when phi is given (default).
+ *   DOUBLE : A = 1/2 I + K, K_ij = (1/4pi) int_j n_j.(x_i - y)/r^3 dS; the second-kind
+ *            system of eq. laplace_bem_final for the unknown phi when the normal
+ *            derivative q is given, with right-hand side V q. n is the panel normal of
+ *            the mesh's triangle order, which must point out of the solution domain: for
+ *            an exterior problem the triangles are ordered so that n points into the body.
+ *            The FMM far field then carries dipoles (P2M of n.grad of the regular solid
+ *            harmonics); the near field sums n_j.(x_i - y)/r^3 over the K Gauss points and
+ *            adds the double-layer correction rows.
+ * FMMBEM_ESTATE for DOUBLE on a Stokes handle, FMMBEM_EINVAL for another value. */
+#define FMMBEM_LAYER_SINGLE 0
+#define FMMBEM_LAYER_DOUBLE 1
+int fmmbem_set_layer(fmmbem_handle* h, int layer);
 
 /*
  * y = A x through the FMM at expansion order p (eq. matvec-onerow with the

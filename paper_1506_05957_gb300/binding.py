@@ -28,6 +28,8 @@ FMMBEM_P_MAX = 16
 FMMBEM_M2L_TABLES = 0
 FMMBEM_M2L_GATHER = 1
 FMMBEM_M2L_TENSOR = 2
+FMMBEM_LAYER_SINGLE = 0
+FMMBEM_LAYER_DOUBLE = 1
 PASS_NAMES = ["p2m", "m2m", "m2l", "l2l", "l2p", "p2p", "krylov", "matvec"]
 
 
@@ -84,6 +86,7 @@ def lib():
         L.fmmbem_matvec.argtypes = [_vp, ctypes.c_int, _vp, _vp]
         L.fmmbem_set_m2l_mode.argtypes = [_vp, ctypes.c_int]
         L.fmmbem_set_p2p_variant.argtypes = [_vp, ctypes.c_int]
+        L.fmmbem_set_layer.argtypes = [_vp, ctypes.c_int]
         L.fmmbem_estimate_bytes.argtypes = [ctypes.c_int64, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                             ctypes.POINTER(fmmbem_opts)]
         L.fmmbem_estimate_bytes.restype = ctypes.c_int64
@@ -199,6 +202,10 @@ class FmmBem:
 
     def set_precision(self, precision):
         _check(lib().fmmbem_set_precision(self.h, int(precision)))
+
+    def set_layer(self, layer):
+        """FMMBEM_LAYER_SINGLE (A = V) or FMMBEM_LAYER_DOUBLE (A = 1/2 I + K) for later mat-vecs and solves."""
+        _check(lib().fmmbem_set_layer(self.h, int(layer)))
 
     def set_p2p_variant(self, variant):
         _check(lib().fmmbem_set_p2p_variant(self.h, int(variant)))

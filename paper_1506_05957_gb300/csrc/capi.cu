@@ -2,6 +2,7 @@
 // mat-vec pipeline (near field, far field, evaluation) in Morton-sorted order,
 // permutations to and from the caller's panel order, solves and profiling.
 #include <stdarg.h>
+#include <mutex>
 #include <string.h>
 #include <algorithm>
 #include <chrono>
@@ -10,6 +11,11 @@
 
 namespace {
 thread_local char g_err[1024] = "";
+}
+
+cudaStream_t& fmm_alloc_stream() {
+    thread_local cudaStream_t s = nullptr;
+    return s;
 }
 
 void fmmbem_set_error(const char* fmt, ...) {
@@ -79,8 +85,35 @@ int perm_out(fmmbem_handle* h, const double* ys, double* y) {
 template <typename P>
 int dalloc(P** p, size_t count) {
     *p = nullptr;
-    FMM_CU(cudaMalloc((void**)p, (count ? count : 1) * sizeof(P)));
+    FMM_CU(fmm_malloc(p, (count ? count : 1) * sizeof(P)));
     return 0;
+}
+
+// Pinned host buffers (the solver's small result areas) are recycled through a free list
+// instead of being released, because freeing pinned memory synchronizes the device.
+std::mutex g_pinned_mu;
+std::vector<std::pair<size_t, void*>> g_pinned_free;
+
+void* pinned_get(size_t bytes, unsigned flags) {
+    {
+        std::lock_guard<std::mutex> lock(g_pinned_mu);
+        for (size_t i = 0; i < g_pinned_free.size(); ++i)
+            if (g_pinned_free[i].first >= bytes) {
+                void* p = g_pinned_free[i].second;
+                g_pinned_free.erase(g_pinned_free.begin() + i);
+                return p;
+            }
+    }
+    void* p = nullptr;
+    // every recycled buffer is mapped, so any request can take any of them
+    if (cudaHostAlloc(&p, bytes < 4096 ? 4096 : bytes, flags | cudaHostAllocMapped) != cudaSuccess) return nullptr;
+    return p;
+}
+
+void pinned_put(void* p, size_t bytes) {
+    if (!p) return;
+    std::lock_guard<std::mutex> lock(g_pinned_mu);
+    g_pinned_free.push_back({bytes < 4096 ? 4096 : bytes, p});
 }
 
 }  // namespace
@@ -163,7 +196,7 @@ static int matvec_launch(fmmbem_handle* h, int p, const double* xs, double* ys);
 // Mat-vecs of the solver (fixed buffers xfix -> kw, not profiling) replay one CUDA graph
 // per order p; the graph is recaptured when the arithmetic or kernel selection changed.
 int matvec_sorted(fmmbem_handle* h, int p, const double* xs, double* ys) {
-    const int mode = h->precision * 16 + h->m2l_mode + 4 * h->p2p_variant + 64 * (h->prof_on ? 1 : 0);
+    const int mode = h->precision * 16 + h->m2l_mode + 4 * h->p2p_variant + 64 * (h->prof_on ? 1 : 0) + 128 * h->layer;
     if (!h->use_graphs || xs != h->xfix || ys != h->kw || h->stream == nullptr)
         return matvec_launch(h, p, xs, ys);
     prof_harvest(h);
@@ -246,14 +279,19 @@ int fmmbem_relaxed_p(double eta, double rho_prev, int p_initial, int p_min) {
 
 void fmmbem_destroy(fmmbem_handle* h) {
     if (!h) return;
+    // the handle's own streams finish first; then its memory goes back to the pool in
+    // stream order (no device-wide synchronization)
+    if (h->stream2) cudaStreamSynchronize(h->stream2);
+    if (h->istream) cudaStreamSynchronize(h->istream);
+    fmm_alloc_stream() = h->stream;
     void* bufs[] = {h->perm, h->tgt_d, h->tgt_f, h->nrm_d, h->verts, h->src_d, h->src_f, h->src_rel, h->tgt_rel, h->src_w, h->cell_cs, h->cell_range, h->cell_rad,
                     h->cell_child, h->cell_level, h->cell_parent, h->leaves, h->parents, h->leaf_class, h->m2l_ptr, h->m2l_src, h->p2p_ptr,
                     h->p2p_src, h->p2p_rec, h->p2p_off, h->p2p_len, h->p2p_items, h->p2p_cnt, h->p2p_toff, h->stage_ptr, h->stage_first, h->stage_bytes, h->corr_ptr, h->corr_col, h->corr_sl, h->corr_dl, h->oct_d, h->oct_f, h->M, h->L,
                     h->xs, h->ys, h->ynear, h->m2l_pt, h->m2l_ps, h->m2l_refl, h->sign_f, h->sign_d, h->m2l_tiles, h->tab_d, h->tab_f, h->tab_tc, h->m2l_tiles_tc, h->tc_src_info, h->tc_dst_info, h->tree_tab_tc, h->tree_tiles, h->tree_info, h->tc_err, h->kerr, h->V, h->kw, h->xfix, h->kb, h->kx, h->kr, h->kpart, h->kh, h->kyv, h->arn_bar};
     for (void* b : bufs)
-        if (b) cudaFree(b);
-    if (h->kh_host) cudaFreeHost(h->kh_host);
-    if (h->arn_out_host) cudaFreeHost(h->arn_out_host);
+        if (b) fmm_free(b);
+    pinned_put(h->kh_host, sizeof(double) * 3 * (h->kr_m + 2));
+    pinned_put(h->arn_out_host, sizeof(double) * (2 * 65 + 1));
     for (int q = 0; q <= FMMBEM_P_MAX; ++q) {
         if (h->mv_graph[q]) cudaGraphExecDestroy(h->mv_graph[q]);
         for (int e = 0; e < 2 * FMMBEM_N_PASSES; ++e)
@@ -293,6 +331,19 @@ int fmmbem_create(const fmmbem_mesh* mesh, int kernel, int gauss_k, int ncrit, d
     if (o.precision != FMMBEM_FP64 && o.precision != FMMBEM_MIXED) { fmmbem_set_error("bad precision"); return FMMBEM_EINVAL; }
 
     fmmbem_handle* h = new fmmbem_handle();
+    fmm_alloc_stream() = (cudaStream_t)o.stream;
+    {
+        // freed device blocks stay in the default pool for the next handle
+        static std::once_flag pool_once;
+        std::call_once(pool_once, []() {
+            int dev = 0;
+            cudaMemPool_t pool;
+            if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+                uint64_t keep = UINT64_MAX;
+                cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+            }
+        });
+    }
     h->kernel = kernel;
     h->dof = kernel == FMMBEM_STOKES ? 3 : 1;
     h->ncomp = kernel == FMMBEM_STOKES ? 4 : 1;
@@ -331,8 +382,9 @@ int fmmbem_create(const fmmbem_mesh* mesh, int kernel, int gauss_k, int ncrit, d
     h->kr_m = o.restart;
     if ((rc = dalloc((double**)&h->M, ex)) < 0) return fail(rc);
     if ((rc = dalloc((double**)&h->L, ex)) < 0) return fail(rc);
-    // per-mat-vec packed sources: one float4 per Gauss point (Laplace), two (Stokes)
-    if ((rc = dalloc(&h->src_w, (size_t)h->NS * (kernel == FMMBEM_STOKES ? 2 : 1))) < 0) return fail(rc);
+    // per-mat-vec packed sources: one float4 per Gauss point (Laplace single layer), two
+    // (Stokeslet strengths, or the Laplace double layer's moment w n)
+    if ((rc = dalloc(&h->src_w, (size_t)h->NS * 2)) < 0) return fail(rc);
     if ((rc = dalloc(&h->xs, n)) < 0 || (rc = dalloc(&h->ys, n)) < 0 || (rc = dalloc(&h->ynear, n)) < 0) return fail(rc);
     if ((rc = dalloc(&h->V, (size_t)(o.restart + 1) * n)) < 0) return fail(rc);
     if ((rc = dalloc(&h->xfix, n)) < 0) return fail(rc);
@@ -347,14 +399,15 @@ int fmmbem_create(const fmmbem_mesh* mesh, int kernel, int gauss_k, int ncrit, d
     if ((rc = dalloc(&h->kpart, std::max((size_t)96 * (o.restart + 2), (size_t)3 * 64 * h->arn_blocks))) < 0) return fail(rc);
     if ((rc = dalloc(&h->arn_bar, 2)) < 0) return fail(rc);
     if (cudaMemsetAsync(h->arn_bar, 0, 2 * sizeof(unsigned), h->stream) != cudaSuccess) return fail(FMMBEM_EDEVICE);
-    if (cudaHostAlloc((void**)&h->arn_out_host, sizeof(double) * (2 * 65 + 1), cudaHostAllocMapped) != cudaSuccess ||
-        cudaHostGetDevicePointer((void**)&h->arn_out_dev, h->arn_out_host, 0) != cudaSuccess) {
+    h->arn_out_host = reinterpret_cast<double*>(pinned_get(sizeof(double) * (2 * 65 + 1), cudaHostAllocMapped));
+    if (!h->arn_out_host || cudaHostGetDevicePointer((void**)&h->arn_out_dev, h->arn_out_host, 0) != cudaSuccess) {
         fmmbem_set_error("mapped pinned allocation failed");
         return fail(FMMBEM_ENOMEM);
     }
     if ((rc = dalloc(&h->kh, (size_t)3 * (o.restart + 2))) < 0) return fail(rc);
     if ((rc = dalloc(&h->kyv, (size_t)(o.restart + 2))) < 0) return fail(rc);
-    if (cudaMallocHost((void**)&h->kh_host, sizeof(double) * 3 * (o.restart + 2)) != cudaSuccess) {
+    h->kh_host = reinterpret_cast<double*>(pinned_get(sizeof(double) * 3 * (o.restart + 2), cudaHostAllocDefault));
+    if (!h->kh_host) {
         fmmbem_set_error("pinned allocation failed");
         return fail(FMMBEM_ENOMEM);
     }
@@ -372,6 +425,16 @@ int64_t fmmbem_n_unknowns(const fmmbem_handle* h) { return h ? h->N * h->dof : -
 int fmmbem_set_precision(fmmbem_handle* h, int precision) {
     if (!h || (precision != FMMBEM_FP64 && precision != FMMBEM_MIXED)) { fmmbem_set_error("bad precision"); return FMMBEM_EINVAL; }
     h->precision = precision;
+    return 0;
+}
+
+int fmmbem_set_layer(fmmbem_handle* h, int layer) {
+    if (!h || (layer != FMMBEM_LAYER_SINGLE && layer != FMMBEM_LAYER_DOUBLE)) { fmmbem_set_error("bad layer"); return FMMBEM_EINVAL; }
+    if (layer == FMMBEM_LAYER_DOUBLE && h->kernel != FMMBEM_LAPLACE) {
+        fmmbem_set_error("the double-layer operator is built for Laplace handles");
+        return FMMBEM_ESTATE;
+    }
+    h->layer = layer;
     return 0;
 }
 
@@ -405,7 +468,13 @@ int fmmbem_matvec(fmmbem_handle* h, int p, const double* x_dev, double* y_dev) {
 int fmmbem_matvec_direct(fmmbem_handle* h, const double* x_dev, double* y_dev) {
     if (!h || !x_dev || !y_dev || x_dev == y_dev) { fmmbem_set_error("bad argument"); return FMMBEM_EINVAL; }
     FMM_TRY(perm_in(h, x_dev, h->xs));
-    FMM_TRY(direct_field(h, h->precision == FMMBEM_FP64, 0, h->xs, h->ys));
+    if (h->layer == FMMBEM_LAYER_DOUBLE) {  // 1/2 x + K x, in FP64
+        FMM_TRY(direct_field(h, true, 1, h->xs, h->ys));
+        k_axpy_half<<<(unsigned)((h->N + 255) / 256), 256, 0, h->stream>>>(h->ys, h->xs, h->N);
+        FMM_LAUNCHED();
+    } else {
+        FMM_TRY(direct_field(h, h->precision == FMMBEM_FP64, 0, h->xs, h->ys));
+    }
     FMM_TRY(perm_out(h, h->ys, y_dev));
     return 0;
 }

@@ -69,6 +69,17 @@ template <> FMM_HD double rsqrt_t<double>(double x) {
 
 }  // namespace fmmbem
 
+// Device memory of a handle is stream-ordered (cudaMallocAsync / cudaFreeAsync on the
+// handle's stream, from the device's default memory pool, which keeps freed blocks for
+// reuse), so creating or destroying a handle never waits for other handles' work.
+// fmm_alloc_stream() is the stream of the handle being built or torn down on this thread.
+cudaStream_t& fmm_alloc_stream();
+inline cudaError_t fmm_malloc_bytes(void** p, size_t bytes) { return cudaMallocAsync(p, bytes ? bytes : 16, fmm_alloc_stream()); }
+template <typename P> inline cudaError_t fmm_malloc(P** p, size_t bytes) {
+    return fmm_malloc_bytes(reinterpret_cast<void**>(p), bytes);
+}
+inline cudaError_t fmm_free(void* p) { return p ? cudaFreeAsync(p, fmm_alloc_stream()) : cudaSuccess; }
+
 // Thread-local message of the last failure (fmmbem_last_error).
 void fmmbem_set_error(const char* fmt, ...);
 

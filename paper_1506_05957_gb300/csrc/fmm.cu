@@ -129,6 +129,93 @@ __global__ void __launch_bounds__(32 * P2M_WARPS) k_p2m(int p, const int* leaves
     }
 }
 
+// P2M of the double layer (eq. laplace_bem_dGdn): Gauss point y carries a dipole of
+// moment w n_j (w = q_k S_j x_j, n_j its panel's normal), whose potential is
+// w n_j . grad_y (1/|x - y|). Its multipole coefficients are the conjugated directional
+// derivatives of the regular solid harmonics,
+//   M_n^m += w conj(n_z R_{n-1}^m + (n_x - i n_y)/2 R_{n-1}^{m+1} - (n_x + i n_y)/2 R_{n-1}^{m-1}),
+// which follow from dR_n^m/dz = R_{n-1}^m and (d/dx + i d/dy) R_n^m = R_{n-1}^{m+1},
+// (d/dx - i d/dy) R_n^m = -R_{n-1}^{m-1} for R_n^m = r^n P_n^m(cos theta) e^{i m phi} / (n+m)!,
+// with R_{n-1}^{-1} = -conj(R_{n-1}^1). In the scaled storage (M~_n = M_n / s^n, argument
+// (y - c)/s) the derivative brings one factor 1/s. M_0^0 is zero. Each R_k^j (k < p) a lane
+// generates is scattered into the coefficients of degree k + 1 it feeds, each reduced
+// across the warp as in k_p2m.
+template <typename T>
+__global__ void __launch_bounds__(32 * P2M_WARPS) k_p2m_dl(int p, const int* leaves, const double4* cs, const int2* range,
+                                                          const typename V4<T>::type* src, const double4* nrm,
+                                                          const double* xs, int K, T* M) {
+    extern __shared__ unsigned char smem_raw[];
+    T* acc = reinterpret_cast<T*>(smem_raw);  // [warps][ncoef][2]
+    const int nco = ncoef(p);
+    const int cell = leaves[blockIdx.x];
+    const double4 cc = cs[cell];
+    const int2 r = range[cell];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int q = threadIdx.x; q < P2M_WARPS * nco * 2; q += blockDim.x) acc[q] = T(0);
+    __syncthreads();
+    T* wacc = acc + warp * nco * 2;
+    const double inv_s = 1.0 / cc.w;
+    const int s0 = r.x * K, s1 = r.y * K;
+    for (int base = s0 + warp * 32; base < s1; base += P2M_WARPS * 32) {
+        const int s = base + lane;
+        T vx = 0, vy = 0, vz = 0, c = 0;
+        cpx<T> a = mk(T(0), T(0)), b = mk(T(0), T(0));  // w (n_x -+ i n_y) / 2
+        if (s < s1) {
+            const auto y = src[s];
+            const int pj = s / K;
+            const double4 n = nrm[pj];
+            vx = T(((double)y.x - cc.x) * inv_s);
+            vy = T(((double)y.y - cc.y) * inv_s);
+            vz = T(((double)y.z - cc.z) * inv_s);
+            const double w = (double)y.w * xs[pj] * inv_s;
+            c = T(w * n.z);
+            a = mk(T(0.5 * w * n.x), T(-0.5 * w * n.y));
+            b = mk(T(0.5 * w * n.x), T(0.5 * w * n.y));
+        }
+        auto add = [&](int n, int m, cpx<T> d) {  // M~(n, m) += conj(d), summed over the warp
+            const int qi = cidx(n, m);
+            const T re = warp_sum(d.re), im = warp_sum(-d.im);
+            if (lane == 0) {
+                wacc[2 * qi] += re;
+                wacc[2 * qi + 1] += im;
+            }
+        };
+        auto emit = [&](int k, int j, cpx<T> R) {  // R = R_k^j(v), k < p
+            add(k + 1, j, c * R);
+            if (j >= 1) add(k + 1, j - 1, a * R);
+            const cpx<T> bR = b * R;
+            add(k + 1, j + 1, mk(-bR.re, -bR.im));
+            if (j == 1) add(k + 1, 0, b * conj(R));  // the R_k^{-1} term of M_{k+1}^0
+        };
+        const T r2 = vx * vx + vy * vy + vz * vz;
+        const cpx<T> xy = mk(vx, vy);
+        cpx<T> diag = mk(T(1), T(0));
+        for (int m = 0; m < p; ++m) {
+            if (m > 0) diag = (T(-0.5) / T(m)) * (xy * diag);
+            emit(m, m, diag);
+            if (m + 1 >= p) break;
+            cpx<T> prev2 = diag, prev1 = vz * diag;
+            emit(m + 1, m, prev1);
+            for (int n = m + 2; n < p; ++n) {
+                const T inv = T(1) / T((n - m) * (n + m));
+                cpx<T> cur = mk((T(2 * n - 1) * vz * prev1.re - r2 * prev2.re) * inv,
+                                (T(2 * n - 1) * vz * prev1.im - r2 * prev2.im) * inv);
+                emit(n, m, cur);
+                prev2 = prev1;
+                prev1 = cur;
+            }
+        }
+    }
+    __syncthreads();
+    T* out = M + (size_t)cell * ESTRIDE;
+    for (int idx = threadIdx.x; idx < nco * 2; idx += blockDim.x) {
+        T v = 0;
+#pragma unroll
+        for (int w = 0; w < P2M_WARPS; ++w) v += acc[w * nco * 2 + idx];
+        out[idx] = v;
+    }
+}
+
 // M2M for the non-leaf cells of one level: M~_n^m(P) = sum_children sum_{j,k}
 // M~_j^k(c) 2^{-j} conj(R_{n-j}^{m-k}(d)), d = (c_child - c_parent)/s_parent.
 // One block per parent. The children's expansions and octant tables are staged in
@@ -324,7 +411,8 @@ __global__ void __launch_bounds__(TREE_THREADS) k_l2l(int p, const int* parents,
 //   (d_x + i d_y) R_n^m = R_{n-1}^{m+1}.
 template <typename T, int NC>
 __global__ void k_l2p(int p, const int* leaves, const double4* cs, const int2* range, const double4* tgt, const T* L,
-                      const double* ynear, double scale, double ox, double oy, double oz, double* yout) {
+                      const double* ynear, double scale, double ox, double oy, double oz, const double* xs_half,
+                      double* yout) {
     __shared__ T sL[NC * NCOEF_MAX * 2];
     const int cell = leaves[blockIdx.x];
     const double4 cc = cs[cell];
@@ -382,7 +470,7 @@ __global__ void k_l2p(int p, const int* leaves, const double4* cs, const int2* r
         }
         if (NC == 1) {
             const double far = (double)phi[0] * inv_s;
-            yout[i] = scale * (far + ynear[i]);
+            yout[i] = scale * (far + ynear[i]) + (xs_half ? 0.5 * xs_half[i] : 0.0);  // 1/2 I of the second kind
         } else {
             const double is2 = inv_s * inv_s;
             const double px = x.x - ox, py = x.y - oy, pz = x.z - oz;
@@ -486,8 +574,13 @@ int far_field_t(fmmbem_handle* h, int p) {
     // P2M
     prof_begin(h, FMMBEM_PASS_P2M);
     const size_t sm = (size_t)P2M_WARPS * NC * nco * 2 * sizeof(T);
-    k_p2m<T, NC><<<h->n_leaves, 32 * P2M_WARPS, sm, st>>>(p, h->leaves, h->cell_cs, h->cell_range, src, h->xin, h->K,
-                                                         h->origin[0], h->origin[1], h->origin[2], M);
+    if (NC == 1 && h->layer == FMMBEM_LAYER_DOUBLE) {
+        k_p2m_dl<T><<<h->n_leaves, 32 * P2M_WARPS, sm, st>>>(p, h->leaves, h->cell_cs, h->cell_range, src, h->nrm_d,
+                                                            h->xin, h->K, M);
+    } else {
+        k_p2m<T, NC><<<h->n_leaves, 32 * P2M_WARPS, sm, st>>>(p, h->leaves, h->cell_cs, h->cell_range, src, h->xin,
+                                                             h->K, h->origin[0], h->origin[1], h->origin[2], M);
+    }
     FMM_LAUNCHED();
     prof_end(h, FMMBEM_PASS_P2M, 1);
     // tensor-core tree translations in the mixed-precision M2L-TENSOR mode
@@ -550,7 +643,9 @@ int far_eval_t(fmmbem_handle* h, int p, double* y_sorted, double scale) {
     prof_begin(h, FMMBEM_PASS_L2P);
     k_l2p<T, NC><<<h->n_leaves, 128, 0, h->stream>>>(p, h->leaves, h->cell_cs, h->cell_range, h->tgt_d,
                                                     reinterpret_cast<const T*>(h->L), h->ynear, scale, h->origin[0],
-                                                    h->origin[1], h->origin[2], y_sorted);
+                                                    h->origin[1], h->origin[2],
+                                                    NC == 1 && h->layer == FMMBEM_LAYER_DOUBLE ? h->xin : nullptr,
+                                                    y_sorted);
     FMM_LAUNCHED();
     prof_end(h, FMMBEM_PASS_L2P, 1);
     h->launches += 1;
@@ -568,8 +663,8 @@ int init_octant_tables(fmmbem_handle* h) {
     FMM_CU(cudaFuncSetAttribute(k_m2m<double, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 24 * nmax * (int)sizeof(double)));
     FMM_CU(cudaFuncSetAttribute(k_m2m<double, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 72 * nmax * (int)sizeof(double)));
     FMM_CU(cudaFuncSetAttribute(k_l2l<double, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 12 * nmax * (int)sizeof(double)));
-    FMM_CU(cudaMalloc((void**)&h->oct_d, sizeof(double) * 8 * NCOEF_MAX * 2));
-    FMM_CU(cudaMalloc((void**)&h->oct_f, sizeof(float) * 8 * NCOEF_MAX * 2));
+    FMM_CU(fmm_malloc(&h->oct_d, sizeof(double) * 8 * NCOEF_MAX * 2));
+    FMM_CU(fmm_malloc(&h->oct_f, sizeof(float) * 8 * NCOEF_MAX * 2));
     k_octant_tables<<<1, 8, 0, h->stream>>>(h->oct_d, h->oct_f);
     FMM_LAUNCHED();
     return 0;

@@ -14,6 +14,7 @@ struct fmmbem_handle {
     double theta = 0.5;
     fmmbem_opts opts{};
     int precision = FMMBEM_MIXED;
+    int layer = FMMBEM_LAYER_SINGLE;  // operator of mat-vecs and solves (Laplace): V or 1/2 I + K
     cudaStream_t stream = nullptr;
     cudaStream_t stream2 = nullptr;  // near field runs here, concurrently with the far field
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;

@@ -34,7 +34,7 @@ constexpr int GEMM_KC = 16;           // inputs per shared-memory stage
 template <typename P>
 int dalloc(P** p, size_t count) {
     *p = nullptr;
-    FMM_CU(cudaMalloc((void**)p, (count ? count : 1) * sizeof(P)));
+    FMM_CU(fmm_malloc((void**)p, (count ? count : 1) * sizeof(P)));
     return 0;
 }
 
@@ -281,16 +281,16 @@ int build_m2l_tables(fmmbem_handle* h) {
     size_t tb = 0;
     FMM_CU(cub::DeviceRadixSort::SortPairs(nullptr, tb, key, key_s, idx, idx_s, (int)n, 0, 3 * KEY_BITS + 4, st));
     void* tmp = nullptr;
-    FMM_CU(cudaMalloc(&tmp, tb ? tb : 1));
+    FMM_CU(fmm_malloc(&tmp, tb ? tb : 1));
     FMM_CU(cub::DeviceRadixSort::SortPairs(tmp, tb, key, key_s, idx, idx_s, (int)n, 0, 3 * KEY_BITS + 4, st));
-    cudaFree(tmp);
+    fmm_free(tmp);
     k_mark_heads<<<gp, T, 0, st>>>(key_s, n, head);
     FMM_LAUNCHED();
     tb = 0;
     FMM_CU(cub::DeviceScan::InclusiveSum(nullptr, tb, head, scan, (int)n, st));
-    FMM_CU(cudaMalloc(&tmp, tb ? tb : 1));
+    FMM_CU(fmm_malloc(&tmp, tb ? tb : 1));
     FMM_CU(cub::DeviceScan::InclusiveSum(tmp, tb, head, scan, (int)n, st));
-    cudaFree(tmp);
+    fmm_free(tmp);
     int ntab = 0, bad_h = 0;
     FMM_CU(cudaMemcpyAsync(&ntab, scan + n - 1, sizeof(int), cudaMemcpyDeviceToHost, st));
     FMM_CU(cudaMemcpyAsync(&bad_h, bad, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -301,8 +301,8 @@ int build_m2l_tables(fmmbem_handle* h) {
     const size_t bytes = (size_t)ntab * per * (sizeof(double) + sizeof(float));
     if (bad_h || bytes > ((size_t)16 << 30)) {
         // keys out of range or tables too large: the gather kernel (k_m2l) handles M2L
-        cudaFree(pt); cudaFree(ps); cudaFree(idx); cudaFree(idx_s); cudaFree(head); cudaFree(scan); cudaFree(bad);
-        cudaFree(key); cudaFree(key_s); cudaFree(refl);
+        fmm_free(pt); fmm_free(ps); fmm_free(idx); fmm_free(idx_s); fmm_free(head); fmm_free(scan); fmm_free(bad);
+        fmm_free(key); fmm_free(key_s); fmm_free(refl);
         return 0;
     }
     int* tab_first = nullptr;
@@ -329,12 +329,12 @@ int build_m2l_tables(fmmbem_handle* h) {
     FMM_LAUNCHED();
     tb = 0;
     FMM_CU(cub::DeviceScan::ExclusiveSum(nullptr, tb, cnt, off, ntab + 1, st));
-    FMM_CU(cudaMalloc(&tmp, tb ? tb : 1));
+    FMM_CU(fmm_malloc(&tmp, tb ? tb : 1));
     FMM_CU(cub::DeviceScan::ExclusiveSum(tmp, tb, cnt, off, ntab + 1, st));
     int ntiles = 0;
     FMM_CU(cudaMemcpyAsync(&ntiles, off + ntab, sizeof(int), cudaMemcpyDeviceToHost, st));
     FMM_CU(cudaStreamSynchronize(st));
-    cudaFree(tmp);
+    fmm_free(tmp);
     FMM_TRY(dalloc(&h->m2l_tiles, ntiles));
     k_tile_emit<<<(ntab + T - 1) / T, T, 0, st>>>(tab_first, off, ntab, per_tile, h->m2l_tiles);
     FMM_LAUNCHED();
@@ -344,12 +344,12 @@ int build_m2l_tables(fmmbem_handle* h) {
         FMM_CU(cudaMemsetAsync(cnt, 0, sizeof(int) * (ntab + 1), st));
         k_tile_counts<<<(ntab + T - 1) / T, T, 0, st>>>(tab_first, ntab, per_tc, cnt);
         FMM_LAUNCHED();
-        FMM_CU(cudaMalloc(&tmp, tb ? tb : 1));
+        FMM_CU(fmm_malloc(&tmp, tb ? tb : 1));
         FMM_CU(cub::DeviceScan::ExclusiveSum(tmp, tb, cnt, off, ntab + 1, st));
         int ntc = 0;
         FMM_CU(cudaMemcpyAsync(&ntc, off + ntab, sizeof(int), cudaMemcpyDeviceToHost, st));
         FMM_CU(cudaStreamSynchronize(st));
-        cudaFree(tmp);
+        fmm_free(tmp);
         FMM_TRY(dalloc(&h->m2l_tiles_tc, ntc));
         k_tile_emit<<<(ntab + T - 1) / T, T, 0, st>>>(tab_first, off, ntab, per_tc, h->m2l_tiles_tc);
         FMM_LAUNCHED();
@@ -365,8 +365,8 @@ int build_m2l_tables(fmmbem_handle* h) {
     h->tab_ld = ld;
     h->tab_stride = per;
     h->m2l_tables = true;
-    cudaFree(pt); cudaFree(ps); cudaFree(idx); cudaFree(idx_s); cudaFree(head); cudaFree(scan); cudaFree(bad);
-    cudaFree(key); cudaFree(key_s); cudaFree(refl); cudaFree(tab_first); cudaFree(tab_key); cudaFree(cnt); cudaFree(off);
+    fmm_free(pt); fmm_free(ps); fmm_free(idx); fmm_free(idx_s); fmm_free(head); fmm_free(scan); fmm_free(bad);
+    fmm_free(key); fmm_free(key_s); fmm_free(refl); fmm_free(tab_first); fmm_free(tab_key); fmm_free(cnt); fmm_free(off);
     return 0;
 }
 

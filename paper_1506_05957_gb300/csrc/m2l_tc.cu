@@ -605,11 +605,11 @@ static int build_tree_tc(fmmbem_handle* h, int nr, int rows_max, int nch) {
     cudaStream_t st = h->stream;
     const int nc = h->n_cells, NC = h->ncomp;
     double* Td = nullptr;
-    FMM_CU(cudaMalloc((void**)&Td, sizeof(double) * 2 * (size_t)nr * nr));
+    FMM_CU(fmm_malloc((void**)&Td, sizeof(double) * 2 * (size_t)nr * nr));
     k_tree_ops<<<dim3(nr, 2), 128, 0, st>>>(h->opts.p_max, Td);
     FMM_LAUNCHED();
     const size_t per_tab = (size_t)nch * 2 * rows_max * TC_KC;
-    FMM_CU(cudaMalloc((void**)&h->tree_tab_tc, sizeof(float) * 2 * per_tab));
+    FMM_CU(fmm_malloc((void**)&h->tree_tab_tc, sizeof(float) * 2 * per_tab));
     k_tc_tables<<<256, 256, 0, st>>>(Td, 2, nr, nr, nch, rows_max, h->tree_tab_tc);
     FMM_LAUNCHED();
     std::vector<double4> cs(nc);
@@ -620,7 +620,7 @@ static int build_tree_tc(fmmbem_handle* h, int nr, int rows_max, int nch) {
     if (!par.empty())
         FMM_CU(cudaMemcpyAsync(par.data(), h->parents, sizeof(int) * par.size(), cudaMemcpyDeviceToHost, st));
     FMM_CU(cudaStreamSynchronize(st));
-    cudaFree(Td);
+    fmm_free(Td);
     std::vector<int4> tiles;
     std::vector<int> m_src, m_dst, l_src, l_dst;
     h->tree_tile_start.assign(1, 0);
@@ -655,8 +655,8 @@ static int build_tree_tc(fmmbem_handle* h, int nr, int rows_max, int nch) {
         h->tree_tile_start.push_back((int)tiles.size());
     }
     const size_t ntl = tiles.size();
-    FMM_CU(cudaMalloc((void**)&h->tree_tiles, sizeof(int4) * (ntl ? 2 * ntl : 1)));
-    FMM_CU(cudaMalloc((void**)&h->tree_info, sizeof(int) * (ntl ? 4 * ntl * TC_ROWS : 1)));
+    FMM_CU(fmm_malloc((void**)&h->tree_tiles, sizeof(int4) * (ntl ? 2 * ntl : 1)));
+    FMM_CU(fmm_malloc((void**)&h->tree_info, sizeof(int) * (ntl ? 4 * ntl * TC_ROWS : 1)));
     if (ntl) {
         std::vector<int4> both(tiles);
         for (auto& t : tiles) both.push_back(make_int4(1, 0, 0, 0));  // L2L tiles use op 1
@@ -681,13 +681,13 @@ int build_m2l_tc(fmmbem_handle* h) {
     const int rows_max = (nr + 15) & ~15;
     const int nch = (nr + TC_KC - 1) / TC_KC;
     const size_t per_tab = (size_t)nch * 2 * rows_max * TC_KC;
-    FMM_CU(cudaMalloc((void**)&h->tab_tc, sizeof(float) * per_tab * (size_t)h->n_tables));
+    FMM_CU(fmm_malloc((void**)&h->tab_tc, sizeof(float) * per_tab * (size_t)h->n_tables));
     k_tc_tables<<<2048, 256, 0, h->stream>>>(h->tab_d, h->n_tables, nr, h->tab_ld, nch, rows_max, h->tab_tc);
     FMM_LAUNCHED();
     h->tc_stride = per_tab;
     h->tc_rows_max = rows_max;
-    FMM_CU(cudaMalloc((void**)&h->tc_src_info, sizeof(int) * (size_t)h->n_tiles_tc * TC_ROWS));
-    FMM_CU(cudaMalloc((void**)&h->tc_dst_info, sizeof(int) * (size_t)h->n_tiles_tc * TC_ROWS));
+    FMM_CU(fmm_malloc((void**)&h->tc_src_info, sizeof(int) * (size_t)h->n_tiles_tc * TC_ROWS));
+    FMM_CU(fmm_malloc((void**)&h->tc_dst_info, sizeof(int) * (size_t)h->n_tiles_tc * TC_ROWS));
     if (h->n_tiles_tc > 0) {
         if (h->ncomp == 1)
             k_tc_rowinfo<1><<<h->n_tiles_tc, TC_ROWS, 0, h->stream>>>(h->m2l_tiles_tc, h->n_tiles_tc, h->m2l_pt, h->m2l_ps,
@@ -697,7 +697,7 @@ int build_m2l_tc(fmmbem_handle* h) {
                                                                      h->m2l_refl, h->tc_src_info, h->tc_dst_info);
         FMM_LAUNCHED();
     }
-    FMM_CU(cudaMalloc((void**)&h->tc_err, sizeof(int)));
+    FMM_CU(fmm_malloc((void**)&h->tc_err, sizeof(int)));
     FMM_CU(cudaMemsetAsync(h->tc_err, 0, sizeof(int), h->stream));
     FMM_TRY(build_tree_tc(h, nr, rows_max, nch));
     size_t smax = 0;

@@ -803,14 +803,20 @@ __global__ void __launch_bounds__(32 * PS_WARPS, 6) k_p2p_lap_src(const int4* it
     }
 }
 
-// Stokeslet near field with the same source-lane schedule: per mat-vec each Gauss point
-// is packed as two float4, (leaf-relative position, f_x) and (f_y, f_z, -, -) with
-// f = q_k S_J t_J; a work item holds at most P2P_SRC_TMAX_STOKES targets with three FP32
-// accumulators each. Per source and target: d = x - y, r^-1 by rsqrt, and
-// u += f / r + d (d.f) / r^3 (eq. stokeslet), folded every PS_FOLD rounds into
-// compensated per-lane sums.
-constexpr int SS_TMAX = P2P_SRC_TMAX_STOKES;
+// Two-float4 source lanes, the same schedule as k_p2p_lap_src for kernels whose sources
+// carry a vector: per mat-vec each Gauss point is packed as (leaf-relative position, v_x)
+// and (v_y, v_z, -, -).
+// - Stokeslet (eq. stokeslet): v = f = q_k S_J t_J; three FP32 accumulators per target,
+//   at most P2P_SRC_TMAX_STOKES targets per work item; per pair d = x - y, r^-1 by rsqrt,
+//   u += f / r + d (d.f) / r^3.
+// - Laplace double layer (eq. gauss:2nd-kind): v = q_k S_j x_j n_j; one accumulator per
+//   target, at most P2P_SRC_TMAX targets per item; per pair phi += (d.v) / r^3.
+// Accumulators are folded every PS_FOLD rounds into compensated per-lane sums.
 constexpr int SS_SRC = 2;  // sources per lane per round
+
+template <int OP> struct VecLane;
+template <> struct VecLane<STK_SL> { static constexpr int DOF = 3, TM = P2P_SRC_TMAX_STOKES; };
+template <> struct VecLane<LAP_DL> { static constexpr int DOF = 1, TM = P2P_SRC_TMAX; };
 
 __global__ void k_pack_sources_stokes(const float4* src_rel, const double* xs, int K, int64_t ns, float4* out) {
     const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -822,30 +828,50 @@ __global__ void k_pack_sources_stokes(const float4* src_rel, const double* xs, i
     out[2 * g + 1] = make_float4((float)(w * xs[3 * j + 1]), (float)(w * xs[3 * j + 2]), 0.f, 0.f);
 }
 
-struct SsShared {
-    float4 t[SS_TMAX];
-    float2 hl[PS_WARPS][SS_TMAX * 3][32];
+__global__ void k_pack_sources_dipole(const float4* src_rel, const double4* nrm, const double* xs, int K, int64_t ns,
+                                      float4* out) {
+    const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (g >= ns) return;
+    const float4 y = src_rel[g];
+    const int64_t j = g / K;
+    const double w = (double)y.w * xs[j];
+    const double4 n = nrm[j];
+    out[2 * g] = make_float4(y.x, y.y, y.z, (float)(w * n.x));
+    out[2 * g + 1] = make_float4((float)(w * n.y), (float)(w * n.z), 0.f, 0.f);
+}
+
+template <int OP> struct VlShared {
+    float4 t[VecLane<OP>::TM];
+    float2 hl[PS_WARPS][VecLane<OP>::TM * VecLane<OP>::DOF][32];
     float4 rec[PS_EMAX];
     int off[PS_EMAX + 1];
 };
 
-__device__ __forceinline__ void ss_pair(float4 x, float4 a, float4 b, bool skip, float* acc3) {
+template <int OP>
+__device__ __forceinline__ void vl_pair(float4 x, float4 a, float4 b, bool skip, float* acc) {
     const float dx = x.x - a.x, dy = x.y - a.y, dz = x.z - a.z;
     const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
     const float ir = skip ? 0.f : rsqrt_approx(skip ? 1.f : r2);
     const float ir3 = ir * ir * ir;
-    const float df = fmaf(dx, a.w, fmaf(dy, b.x, dz * b.y)) * ir3;
-    acc3[0] = fmaf(a.w, ir, fmaf(dx, df, acc3[0]));
-    acc3[1] = fmaf(b.x, ir, fmaf(dy, df, acc3[1]));
-    acc3[2] = fmaf(b.y, ir, fmaf(dz, df, acc3[2]));
+    const float dv = fmaf(dx, a.w, fmaf(dy, b.x, dz * b.y));
+    if (OP == STK_SL) {
+        const float df = dv * ir3;
+        acc[0] = fmaf(a.w, ir, fmaf(dx, df, acc[0]));
+        acc[1] = fmaf(b.x, ir, fmaf(dy, df, acc[1]));
+        acc[2] = fmaf(b.y, ir, fmaf(dz, df, acc[2]));
+    } else {
+        acc[0] = fmaf(dv, ir3, acc[0]);
+    }
 }
 
-__global__ void __launch_bounds__(32 * PS_WARPS, 5) k_p2p_stk_src(const int4* items, const int2* range, const int* pptr,
+template <int OP>
+__global__ void __launch_bounds__(32 * PS_WARPS, 5) k_p2p_vec_src(const int4* items, const int2* range, const int* pptr,
                                                                  const float4* prec, const int* poff, const int* plen,
                                                                  const float4* srcw, const float4* tgt, int K,
                                                                  const int* cptr, const int* ccol, const double* cval,
                                                                  const double* xs, double* ynear) {
-    __shared__ SsShared sh;
+    constexpr int DOF = VecLane<OP>::DOF, TM = VecLane<OP>::TM;
+    __shared__ VlShared<OP> sh;
     constexpr int RND = 32 * SS_SRC;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int4 item = items[blockIdx.x];
@@ -856,23 +882,26 @@ __global__ void __launch_bounds__(32 * PS_WARPS, 5) k_p2p_stk_src(const int4* it
     float2* sHL = &sh.hl[warp][0][0];
     const float4 far_a = make_float4(1e18f, 0.f, 0.f, 0.f), zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
     for (int i = threadIdx.x; i < ntb; i += blockDim.x) sh.t[i] = tgt[tb + i];
-    for (int i = 0; i < 3 * ntb; ++i) sHL[i * 32 + lane] = make_float2(0.f, 0.f);
-    float acc[SS_TMAX][3];
+    for (int i = 0; i < DOF * ntb; ++i) sHL[i * 32 + lane] = make_float2(0.f, 0.f);
+    float acc[TM][DOF];
 #pragma unroll
-    for (int i = 0; i < SS_TMAX; ++i) acc[i][0] = acc[i][1] = acc[i][2] = 0.f;
+    for (int i = 0; i < TM; ++i)
+#pragma unroll
+        for (int a = 0; a < DOF; ++a) acc[i][a] = 0.f;
     int rounds = 0;
     auto fold = [&]() {
 #pragma unroll
-        for (int i = 0; i < SS_TMAX; ++i) {
+        for (int i = 0; i < TM; ++i) {
             if (i < ntb) {
 #pragma unroll
-                for (int a = 0; a < 3; ++a) {
-                    float2 v = sHL[(3 * i + a) * 32 + lane];
+                for (int a = 0; a < DOF; ++a) {
+                    float2 v = sHL[(DOF * i + a) * 32 + lane];
                     kahan_add(v.x, v.y, acc[i][a]);
-                    sHL[(3 * i + a) * 32 + lane] = v;
+                    sHL[(DOF * i + a) * 32 + lane] = v;
                 }
             }
-            acc[i][0] = acc[i][1] = acc[i][2] = 0.f;
+#pragma unroll
+            for (int a = 0; a < DOF; ++a) acc[i][a] = 0.f;
             asm volatile("" ::: "memory");
         }
     };
@@ -891,11 +920,11 @@ __global__ void __launch_bounds__(32 * PS_WARPS, 5) k_p2p_stk_src(const int4* it
                 gp[h] = q < n ? (g0 + q) / K : -1;
             }
 #pragma unroll
-            for (int i = 0; i < SS_TMAX; ++i) {
+            for (int i = 0; i < TM; ++i) {
                 if (i < ntb) {
                     const float4 x = sh.t[i];
 #pragma unroll
-                    for (int h = 0; h < SS_SRC; ++h) ss_pair(x, ua[h], ub[h], gp[h] == tb + i, acc[i]);
+                    for (int h = 0; h < SS_SRC; ++h) vl_pair<OP>(x, ua[h], ub[h], gp[h] == tb + i, acc[i]);
                 }
                 asm volatile("" ::: "memory");
             }
@@ -932,11 +961,11 @@ __global__ void __launch_bounds__(32 * PS_WARPS, 5) k_p2p_stk_src(const int4* it
                 }
             }
 #pragma unroll
-            for (int i = 0; i < SS_TMAX; ++i) {
+            for (int i = 0; i < TM; ++i) {
                 if (i < ntb) {
                     const float4 x = sh.t[i];
 #pragma unroll
-                    for (int h = 0; h < SS_SRC; ++h) ss_pair(x, ua[h], ub[h], false, acc[i]);
+                    for (int h = 0; h < SS_SRC; ++h) vl_pair<OP>(x, ua[h], ub[h], false, acc[i]);
                 }
                 asm volatile("" ::: "memory");
             }
@@ -946,21 +975,21 @@ __global__ void __launch_bounds__(32 * PS_WARPS, 5) k_p2p_stk_src(const int4* it
     fold();
     __syncthreads();
     for (int i = threadIdx.x; i < ntb; i += blockDim.x) {
-        double out[3];
+        double out[DOF];
 #pragma unroll
-        for (int a = 0; a < 3; ++a) {
+        for (int a = 0; a < DOF; ++a) {
             float hi = 0.f, lo = 0.f;
             for (int w = 0; w < PS_WARPS; ++w)
                 for (int k = 0; k < 32; ++k) {
-                    const float2 v = sh.hl[w][3 * i + a][(k + i) & 31];
+                    const float2 v = sh.hl[w][DOF * i + a][(k + i) & 31];
                     kahan_add(hi, lo, v.x);
                     kahan_add(hi, lo, -v.y);
                 }
             out[a] = (double)hi - (double)lo;
         }
-        add_correction<3>(tb + i, cptr, ccol, cval, xs, out);
+        add_correction<DOF>(tb + i, cptr, ccol, cval, xs, out);
 #pragma unroll
-        for (int a = 0; a < 3; ++a) ynear[3 * (int64_t)(tb + i) + a] = out[a];
+        for (int a = 0; a < DOF; ++a) ynear[DOF * (int64_t)(tb + i) + a] = out[a];
     }
 }
 
@@ -1006,7 +1035,7 @@ __global__ void __launch_bounds__(P2P_THREADS) k_direct(int n, int ns, const typ
 }
 
 template <typename T, int OP>
-int launch_p2p(fmmbem_handle* h) {
+int launch_p2p(fmmbem_handle* h, const double* cval) {
     const bool rel = std::is_same<T, float>::value;
     const typename V4<T>::type* src = rel ? reinterpret_cast<const typename V4<T>::type*>(h->src_rel)
                                           : reinterpret_cast<const typename V4<T>::type*>(h->src_d);
@@ -1014,7 +1043,7 @@ int launch_p2p(fmmbem_handle* h) {
                                           : reinterpret_cast<const typename V4<T>::type*>(h->tgt_d);
     k_p2p<T, OP><<<h->n_leaves, P2P_THREADS, 0, h->stream>>>(h->leaves, h->cell_cs, h->cell_range, h->p2p_ptr,
                                                              h->p2p_src, src, tgt, rel, h->xin, h->nrm_d, h->K,
-                                                             h->corr_ptr, h->corr_col, h->corr_sl, h->ynear);
+                                                             h->corr_ptr, h->corr_col, cval, h->ynear);
     FMM_LAUNCHED();
     return 0;
 }
@@ -1046,6 +1075,23 @@ int near_field(fmmbem_handle* h, bool fp64, cudaStream_t st) {
 int near_field_on(fmmbem_handle* h, bool fp64) {
     prof_begin(h, FMMBEM_PASS_P2P);
     int rc = 0;
+    if (h->kernel == FMMBEM_LAPLACE && h->layer == FMMBEM_LAYER_DOUBLE) {
+        if (!fp64 && h->p2p_variant == 3 && h->p2p_items) {
+            k_pack_sources_dipole<<<(unsigned)((h->NS + 255) / 256), 256, 0, h->stream>>>(h->src_rel, h->nrm_d, h->xin,
+                                                                                         h->K, h->NS, h->src_w);
+            FMM_LAUNCHED();
+            k_p2p_vec_src<LAP_DL><<<h->n_p2p_items, 32 * PS_WARPS, 0, h->stream>>>(
+                h->p2p_items, h->cell_range, h->p2p_ptr, h->p2p_rec, h->p2p_off, h->p2p_len, h->src_w, h->tgt_rel,
+                h->K, h->corr_ptr, h->corr_col, h->corr_dl, h->xin, h->ynear);
+            FMM_LAUNCHED();
+            h->launches += 1;
+        } else {
+            rc = fp64 ? launch_p2p<double, LAP_DL>(h, h->corr_dl) : launch_p2p<float, LAP_DL>(h, h->corr_dl);
+        }
+        prof_end(h, FMMBEM_PASS_P2P, 1);
+        h->launches += 1;
+        return rc;
+    }
     if (h->kernel == FMMBEM_LAPLACE && !fp64) {
         k_pack_sources<<<(unsigned)((h->NS + 255) / 256), 256, 0, h->stream>>>(h->src_rel, h->xin, h->K, h->NS, h->src_w);
         FMM_LAUNCHED();
@@ -1097,17 +1143,17 @@ int near_field_on(fmmbem_handle* h, bool fp64) {
                                                     h->corr_col, h->corr_sl, h->xin, h->ynear);
         FMM_LAUNCHED();
         h->launches += (n1 > 0) + (n2 > 0) + (n3 > 0);
-    } else if (h->kernel == FMMBEM_LAPLACE) rc = launch_p2p<double, LAP_SL>(h);
+    } else if (h->kernel == FMMBEM_LAPLACE) rc = launch_p2p<double, LAP_SL>(h, h->corr_sl);
     else if (!fp64 && h->p2p_variant == 3 && h->p2p_items) {
         k_pack_sources_stokes<<<(unsigned)((h->NS + 255) / 256), 256, 0, h->stream>>>(h->src_rel, h->xin, h->K, h->NS,
                                                                                      h->src_w);
         FMM_LAUNCHED();
-        k_p2p_stk_src<<<h->n_p2p_items, 32 * PS_WARPS, 0, h->stream>>>(
+        k_p2p_vec_src<STK_SL><<<h->n_p2p_items, 32 * PS_WARPS, 0, h->stream>>>(
             h->p2p_items, h->cell_range, h->p2p_ptr, h->p2p_rec, h->p2p_off, h->p2p_len, h->src_w, h->tgt_rel, h->K,
             h->corr_ptr, h->corr_col, h->corr_sl, h->xin, h->ynear);
         FMM_LAUNCHED();
         h->launches += 1;
-    } else rc = fp64 ? launch_p2p<double, STK_SL>(h) : launch_p2p<float, STK_SL>(h);
+    } else rc = fp64 ? launch_p2p<double, STK_SL>(h, h->corr_sl) : launch_p2p<float, STK_SL>(h, h->corr_sl);
     prof_end(h, FMMBEM_PASS_P2P, 1);
     h->launches += 1;
     return rc;

@@ -22,7 +22,7 @@ template <typename P>
 int dalloc(P** p, size_t count) {
     *p = nullptr;
     if (count == 0) count = 1;
-    FMM_CU(cudaMalloc((void**)p, count * sizeof(P)));
+    FMM_CU(fmm_malloc((void**)p, count * sizeof(P)));
     return 0;
 }
 
@@ -615,7 +615,7 @@ int sort_pairs_to_csr(fmmbem_handle* h, int2* pairs, long long n, int** ptr_out,
     size_t tb = 0;
     FMM_CU(cub::DeviceRadixSort::SortKeys(nullptr, tb, k1, k2, (int)n, 0, end_bit, st));
     void* tmp = nullptr;
-    FMM_CU(cudaMalloc(&tmp, tb ? tb : 1));
+    FMM_CU(fmm_malloc(&tmp, tb ? tb : 1));
     FMM_CU(cub::DeviceRadixSort::SortKeys(tmp, tb, k1, k2, (int)n, 0, end_bit, st));
     FMM_TRY(dalloc(ptr_out, nc + 1));
     FMM_TRY(dalloc(src_out, n));
@@ -623,9 +623,9 @@ int sort_pairs_to_csr(fmmbem_handle* h, int2* pairs, long long n, int** ptr_out,
     FMM_LAUNCHED();
     if (n > 0) { k_unpack_src<<<(unsigned)((n + T - 1) / T), T, 0, st>>>(k2, n, nc, *src_out); FMM_LAUNCHED(); }
     FMM_CU(cudaStreamSynchronize(st));
-    cudaFree(tmp);
-    cudaFree(k1);
-    cudaFree(k2);
+    fmm_free(tmp);
+    fmm_free(k1);
+    fmm_free(k2);
     return 0;
 }
 
@@ -707,10 +707,10 @@ int build_geometry_tree_lists(fmmbem_handle* h, const fmmbem_mesh* mesh) {
         size_t tb = 0;
         FMM_CU(cub::DeviceRadixSort::SortPairs(nullptr, tb, key, key_s, idx, h->perm, (int)n, 0, 63, st));
         void* tmp = nullptr;
-        FMM_CU(cudaMalloc(&tmp, tb ? tb : 1));
+        FMM_CU(fmm_malloc(&tmp, tb ? tb : 1));
         FMM_CU(cub::DeviceRadixSort::SortPairs(tmp, tb, key, key_s, idx, h->perm, (int)n, 0, 63, st));
         FMM_CU(cudaStreamSynchronize(st));
-        cudaFree(tmp);
+        fmm_free(tmp);
     }
 
     FMM_TRY(dalloc(&h->tgt_d, n));
@@ -756,14 +756,14 @@ int build_geometry_tree_lists(fmmbem_handle* h, const fmmbem_mesh* mesh) {
             h->level_start.push_back(le);
             const int nl = le - lb;
             if (nl > scan_cap) {
-                if (nch) { cudaFree(nch); cudaFree(off); cudaFree(bounds); cudaFree(scan_tmp); }
+                if (nch) { fmm_free(nch); fmm_free(off); fmm_free(bounds); fmm_free(scan_tmp); }
                 scan_cap = std::max<long long>(2 * nl, 1024);
                 FMM_TRY(dalloc(&nch, scan_cap));
                 FMM_TRY(dalloc(&off, scan_cap));
                 FMM_TRY(dalloc(&bounds, 9 * scan_cap));
                 scan_tb = 0;
                 FMM_CU(cub::DeviceScan::ExclusiveSum(nullptr, scan_tb, nch, off, (int)scan_cap, st));
-                FMM_CU(cudaMalloc(&scan_tmp, scan_tb ? scan_tb : 1));
+                FMM_CU(fmm_malloc(&scan_tmp, scan_tb ? scan_tb : 1));
             }
             k_split_count<<<(nl + T - 1) / T, T, 0, st>>>(lb, le, level, range, key_s, K, h->ncrit, nch, bounds);
             FMM_LAUNCHED();
@@ -784,7 +784,7 @@ int build_geometry_tree_lists(fmmbem_handle* h, const fmmbem_mesh* mesh) {
                 FMM_CU(cudaMemcpyAsync(l2, clevel, sizeof(int) * le, cudaMemcpyDeviceToDevice, st));
                 FMM_CU(cudaMemcpyAsync(p2, parent, sizeof(int) * le, cudaMemcpyDeviceToDevice, st));
                 FMM_CU(cudaStreamSynchronize(st));
-                cudaFree(cs); cudaFree(range); cudaFree(child); cudaFree(clevel); cudaFree(parent);
+                fmm_free(cs); fmm_free(range); fmm_free(child); fmm_free(clevel); fmm_free(parent);
                 cs = cs2; range = r2; child = c2; clevel = l2; parent = p2;
                 cap = ncap;
             }
@@ -796,7 +796,7 @@ int build_geometry_tree_lists(fmmbem_handle* h, const fmmbem_mesh* mesh) {
             ++level;
         }
         FMM_CU(cudaStreamSynchronize(st));
-        cudaFree(nch); cudaFree(off); cudaFree(bounds); cudaFree(scan_tmp);
+        fmm_free(nch); fmm_free(off); fmm_free(bounds); fmm_free(scan_tmp);
         h->n_cells = le;
         h->n_levels = level;  // level_start has n_levels + 1 entries
         h->cell_cs = cs; h->cell_range = range; h->cell_child = child; h->cell_level = clevel; h->cell_parent = parent;
@@ -831,18 +831,18 @@ int build_geometry_tree_lists(fmmbem_handle* h, const fmmbem_mesh* mesh) {
         FMM_CU(cudaStreamSynchronize(st));
         h->n_leaves = cnt_h[0];
         h->max_leaf_panels = cnt_h[1];
-        cudaFree(cnt);
+        fmm_free(cnt);
         // deterministic leaf order (ascending cell id)
         int* ls = nullptr;
         FMM_TRY(dalloc(&ls, h->n_leaves));
         size_t tb = 0;
         FMM_CU(cub::DeviceRadixSort::SortKeys(nullptr, tb, h->leaves, ls, h->n_leaves, 0, 32, st));
         void* tmp = nullptr;
-        FMM_CU(cudaMalloc(&tmp, tb ? tb : 1));
+        FMM_CU(fmm_malloc(&tmp, tb ? tb : 1));
         FMM_CU(cub::DeviceRadixSort::SortKeys(tmp, tb, h->leaves, ls, h->n_leaves, 0, 32, st));
         FMM_CU(cudaStreamSynchronize(st));
-        cudaFree(tmp);
-        cudaFree(h->leaves);
+        fmm_free(tmp);
+        fmm_free(h->leaves);
         h->leaves = ls;
         // leaves ordered by target-count class for the near-field kernels
         {
@@ -857,12 +857,12 @@ int build_geometry_tree_lists(fmmbem_handle* h, const fmmbem_mesh* mesh) {
             size_t tb2 = 0;
             FMM_CU(cub::DeviceRadixSort::SortPairs(nullptr, tb2, ckey, ckey_s, h->leaves, h->leaf_class, h->n_leaves, 0, 2, st));
             void* tmp2 = nullptr;
-            FMM_CU(cudaMalloc(&tmp2, tb2 ? tb2 : 1));
+            FMM_CU(fmm_malloc(&tmp2, tb2 ? tb2 : 1));
             FMM_CU(cub::DeviceRadixSort::SortPairs(tmp2, tb2, ckey, ckey_s, h->leaves, h->leaf_class, h->n_leaves, 0, 2, st));
             int c_h[3];
             FMM_CU(cudaMemcpyAsync(c_h, counts, sizeof(c_h), cudaMemcpyDeviceToHost, st));
             FMM_CU(cudaStreamSynchronize(st));
-            cudaFree(tmp2); cudaFree(ckey); cudaFree(ckey_s); cudaFree(counts);
+            fmm_free(tmp2); fmm_free(ckey); fmm_free(ckey_s); fmm_free(counts);
             h->leaf_class_start[0] = 0;
             h->leaf_class_start[1] = c_h[0];
             h->leaf_class_start[2] = c_h[0] + c_h[1];
@@ -922,7 +922,7 @@ int build_geometry_tree_lists(fmmbem_handle* h, const fmmbem_mesh* mesh) {
                     FMM_TRY(dalloc(&nb, ncap));
                     if (keep) FMM_CU(cudaMemcpyAsync(nb, *buf, keep * sizeof(int2), cudaMemcpyDeviceToDevice, st));
                     FMM_CU(cudaStreamSynchronize(st));
-                    cudaFree(*buf);
+                    fmm_free(*buf);
                     *buf = nb;
                     cap = ncap;
                     return 0;
@@ -936,7 +936,7 @@ int build_geometry_tree_lists(fmmbem_handle* h, const fmmbem_mesh* mesh) {
                     FMM_TRY(dalloc(&nb, ncap));
                     FMM_CU(cudaMemcpyAsync(na, fa, nf * sizeof(int2), cudaMemcpyDeviceToDevice, st));
                     FMM_CU(cudaStreamSynchronize(st));
-                    cudaFree(fa); cudaFree(fb);
+                    fmm_free(fa); fmm_free(fb);
                     fa = na; fb = nb; cap_f = ncap;
                 }
             }
@@ -946,7 +946,7 @@ int build_geometry_tree_lists(fmmbem_handle* h, const fmmbem_mesh* mesh) {
         h->n_p2p = (int64_t)done[1];
         FMM_TRY(sort_pairs_to_csr(h, m2l, (long long)done[0], &h->m2l_ptr, &h->m2l_src));
         FMM_TRY(sort_pairs_to_csr(h, p2p, (long long)done[1], &h->p2p_ptr, &h->p2p_src));
-        cudaFree(m2l); cudaFree(p2p); cudaFree(fa); cudaFree(fb); cudaFree(ovf);
+        fmm_free(m2l); fmm_free(p2p); fmm_free(fa); fmm_free(fb); fmm_free(ovf);
         FMM_CU(cudaMemsetAsync(cnt, 0, 2 * sizeof(unsigned long long), st));
         k_list_stats<<<(nc + T - 1) / T, T, 0, st>>>(h->m2l_ptr, h->m2l_src, h->p2p_ptr, h->p2p_src, h->cell_level,
                                                     h->cell_range, nc, K, cnt, cnt + 1);
@@ -956,7 +956,7 @@ int build_geometry_tree_lists(fmmbem_handle* h, const fmmbem_mesh* mesh) {
         FMM_CU(cudaStreamSynchronize(st));
         h->n_m2l_same = (int64_t)s_h[0];
         h->n_p2p_inter = (int64_t)s_h[1];
-        cudaFree(cnt);
+        fmm_free(cnt);
         FMM_TRY(dalloc(&h->p2p_rec, h->n_p2p));
         FMM_TRY(dalloc(&h->p2p_off, h->n_p2p));
         FMM_TRY(dalloc(&h->p2p_len, nc));
@@ -1009,13 +1009,13 @@ int build_geometry_tree_lists(fmmbem_handle* h, const fmmbem_mesh* mesh) {
             size_t tb3 = 0;
             FMM_CU(cub::DeviceScan::ExclusiveSum(nullptr, tb3, nst, h->stage_ptr, nc + 1, st));
             void* tmp3 = nullptr;
-            FMM_CU(cudaMalloc(&tmp3, tb3 ? tb3 : 1));
+            FMM_CU(fmm_malloc(&tmp3, tb3 ? tb3 : 1));
             FMM_CU(cub::DeviceScan::ExclusiveSum(tmp3, tb3, nst, h->stage_ptr, nc + 1, st));
             int nstages = 0;
             FMM_CU(cudaMemcpyAsync(&nstages, h->stage_ptr + nc, sizeof(int), cudaMemcpyDeviceToHost, st));
             FMM_CU(cudaStreamSynchronize(st));
-            cudaFree(tmp3);
-            cudaFree(nst);
+            fmm_free(tmp3);
+            fmm_free(nst);
             h->n_stages = nstages;
             FMM_TRY(dalloc(&h->stage_first, nstages));
             FMM_TRY(dalloc(&h->stage_bytes, nstages));
@@ -1042,12 +1042,12 @@ int build_geometry_tree_lists(fmmbem_handle* h, const fmmbem_mesh* mesh) {
         size_t tb = 0;
         FMM_CU(cub::DeviceScan::ExclusiveSum(nullptr, tb, count, h->corr_ptr, (int)(n + 1), st));
         void* tmp = nullptr;
-        FMM_CU(cudaMalloc(&tmp, tb ? tb : 1));
+        FMM_CU(fmm_malloc(&tmp, tb ? tb : 1));
         FMM_CU(cub::DeviceScan::ExclusiveSum(tmp, tb, count, h->corr_ptr, (int)(n + 1), st));
         int nnz = 0;
         FMM_CU(cudaMemcpyAsync(&nnz, h->corr_ptr + n, sizeof(int), cudaMemcpyDeviceToHost, st));
         FMM_CU(cudaStreamSynchronize(st));
-        cudaFree(tmp);
+        fmm_free(tmp);
         h->n_corr = nnz;
         int* row = nullptr;
         FMM_TRY(dalloc(&row, nnz));
@@ -1066,12 +1066,12 @@ int build_geometry_tree_lists(fmmbem_handle* h, const fmmbem_mesh* mesh) {
             FMM_LAUNCHED();
         }
         FMM_CU(cudaStreamSynchronize(st));
-        cudaFree(row);
-        cudaFree(count);
+        fmm_free(row);
+        fmm_free(count);
     }
 
-    cudaFree(quad); cudaFree(dv); cudaFree(dt); cudaFree(cen); cudaFree(nrm); cudaFree(scal); cudaFree(bbox);
-    cudaFree(key); cudaFree(key_s); cudaFree(idx);
+    fmm_free(quad); fmm_free(dv); fmm_free(dt); fmm_free(cen); fmm_free(nrm); fmm_free(scal); fmm_free(bbox);
+    fmm_free(key); fmm_free(key_s); fmm_free(idx);
     return 0;
 }
 

@@ -1,0 +1,177 @@
+"""GPU parity of the Laplace second-kind operator A = 1/2 I + K (eq. laplace_bem_final with
+phi unknown) against the oracle, through the C ABI.
+
+The FMM carries dipoles in its far field (P2M of n.grad R) and the double-layer kernel in
+its near field. Tolerances (written per test) follow from the arithmetic:
+  - direct FP64 operator vs oracle: same quadrature, summation order only -> 1e-12;
+  - FMM in FP64: truncation error falling with p; a dipole expansion truncated at p
+    behaves like a charge expansion one order lower, so below 2^-p at theta = 0.5 and
+    below 1e-7 at p = 16;
+  - mixed precision: below 1e-5 at p >= 12;
+  - relaxed solve at tol 1e-6: oracle residual of the GPU solution <= 2 tol and the
+    solution within 1e-5 of the oracle's LU solution.
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1506_05957_gb300 import build
+    build.build()
+    return torch
+
+
+@pytest.fixture(scope="module")
+def exterior1280(torch_cuda):
+    """Exterior problem on the unit sphere (triangles reversed: normals into the body),
+    unit charge at x0 inside: phi = 1/(4 pi r), q = d phi/dn."""
+    from oracle import dense, panels
+    from synth import icosphere
+    v, t = icosphere(3)
+    t = np.ascontiguousarray(t[:, [0, 2, 1]])
+    M = dense.Mesh(v, t, k=4)
+    c, n_in, _ = panels.geometry(v, t)
+    x0 = np.array([0.1, -0.2, 0.3])
+    d = c - x0
+    r = np.linalg.norm(d, axis=1)
+    q = -(d * n_in).sum(1) / (4.0 * np.pi * r ** 3)
+    b = M.laplace_apply(q, kind="sl")
+    A = 0.5 * np.eye(M.n) + M.laplace_matrix(kind="dl")
+    return dict(v=v, t=t, M=M, q=q, b=b, A=A, phi=1.0 / (4.0 * np.pi * r), x_lu=np.linalg.solve(A, b))
+
+
+def _h(v, t, **kw):
+    from paper_1506_05957_gb300 import FmmBem, FMMBEM_LAYER_DOUBLE
+    kw.setdefault("gauss_k", 4)
+    kw.setdefault("ncrit", 150)
+    kw.setdefault("theta", 0.5)
+    h = FmmBem(v, t, **kw)
+    h.set_layer(FMMBEM_LAYER_DOUBLE)
+    return h
+
+
+def _dev(torch, a):
+    return torch.tensor(np.asarray(a), dtype=torch.float64, device="cuda")
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b)))
+
+
+def test_direct_second_kind_matches_oracle(torch_cuda, exterior1280):
+    torch = torch_cuda
+    from paper_1506_05957_gb300 import FMMBEM_FP64
+    s = exterior1280
+    x = np.random.default_rng(0).standard_normal(len(s["t"]))
+    h = _h(s["v"], s["t"], precision=FMMBEM_FP64)
+    y = torch.zeros(h.n, dtype=torch.float64, device="cuda")
+    h.matvec_direct(_dev(torch, x), y)
+    assert rel(y.cpu().numpy(), s["A"] @ x) < 1e-12
+
+
+@pytest.mark.parametrize("ncrit", [40, 150])
+def test_fmm_double_layer_fp64_error_falls_with_p(torch_cuda, exterior1280, ncrit):
+    torch = torch_cuda
+    from paper_1506_05957_gb300 import FMMBEM_FP64
+    s = exterior1280
+    x = np.random.default_rng(1).standard_normal(len(s["t"]))
+    ref = s["A"] @ x
+    h = _h(s["v"], s["t"], ncrit=ncrit, precision=FMMBEM_FP64)
+    xd = _dev(torch, x)
+    y = torch.zeros(h.n, dtype=torch.float64, device="cuda")
+    ps = (1, 2, 4, 6, 8, 10, 12, 16)
+    errs = []
+    for p in ps:
+        h.matvec(p, xd, y)
+        errs.append(rel(y.cpu().numpy(), ref))
+    print("ncrit", ncrit, "double-layer errors by p", ["%.2e" % e for e in errs])
+    for a, b in zip(errs, errs[1:]):
+        assert b < a * 1.05 or b < 1e-13
+    for p, e in zip(ps, errs):
+        assert e < 2.0 ** -p
+    assert errs[-1] < 1e-7
+
+
+def test_fmm_double_layer_mixed_and_variants(torch_cuda, exterior1280):
+    """Source-lane near field (default) and the shared-tile schedule compute the same FP32
+    double-layer sums; both within the mixed-precision bound of the oracle."""
+    torch = torch_cuda
+    from paper_1506_05957_gb300 import FMMBEM_MIXED
+    s = exterior1280
+    x = np.random.default_rng(2).standard_normal(len(s["t"]))
+    ref = s["A"] @ x
+    for ncrit in (40, 150, 600):
+        h = _h(s["v"], s["t"], ncrit=ncrit, precision=FMMBEM_MIXED)
+        xd = _dev(torch, x)
+        ys = {}
+        for variant in (3, 0):
+            h.set_p2p_variant(variant)
+            for p in (12, 16):
+                y = torch.zeros_like(xd)
+                h.matvec(p, xd, y)
+                ys[(variant, p)] = y.cpu().numpy()
+        for key, y in ys.items():
+            assert rel(y, ref) < 1e-5, (ncrit, key, rel(y, ref))
+        assert rel(ys[(3, 16)], ys[(0, 16)]) < 2e-6, ncrit
+
+
+def test_layer_switch_keeps_single_layer(torch_cuda, exterior1280):
+    """Switching a handle between V and 1/2 I + K re-selects the captured mat-vec graph."""
+    torch = torch_cuda
+    from paper_1506_05957_gb300 import FMMBEM_LAYER_SINGLE, FMMBEM_LAYER_DOUBLE
+    s = exterior1280
+    V = s["M"].laplace_matrix(kind="sl")
+    h = _h(s["v"], s["t"], p_max=12)
+    b = _dev(torch, s["b"])
+    sols = []
+    for layer in (FMMBEM_LAYER_SINGLE, FMMBEM_LAYER_DOUBLE, FMMBEM_LAYER_SINGLE):
+        h.set_layer(layer)
+        x = torch.zeros_like(b)
+        r = h.solve(b, x, tol=1e-6, relax=True, p_initial=10, p_min=3)
+        assert r["converged"]
+        sols.append(x.cpu().numpy())
+    assert rel(V @ sols[0], s["b"]) < 2e-6
+    assert rel(s["A"] @ sols[1], s["b"]) < 2e-6
+    assert rel(sols[2], sols[0]) < 1e-5
+
+
+def test_second_kind_relaxed_solve_matches_oracle(torch_cuda, exterior1280):
+    torch = torch_cuda
+    from oracle.gmres import gmres
+    from oracle.schedule import schedule
+    s = exterior1280
+    tol = 1e-6
+    h = _h(s["v"], s["t"], p_max=12)
+    b = _dev(torch, s["b"])
+    x = torch.zeros_like(b)
+    r = h.solve(b, x, tol=tol, relax=True, p_initial=10, p_min=3)
+    assert r["converged"]
+    assert r["p_hist"] == schedule(tol, r["res_hist"][:-1], 10, 3)
+    xs = x.cpu().numpy()
+    assert rel(s["A"] @ xs, s["b"]) < 2 * tol
+    assert rel(xs, s["x_lu"]) < 1e-5
+    # the discrete solution approximates the exterior potential (discretization error)
+    assert rel(xs, s["phi"]) < 2e-2
+    # few iterations: the second-kind operator is well conditioned (the paper needs <= 3 at
+    # tol 1e-6 on its spheres); the GPU count matches exact GMRES on the oracle's matrix
+    _, it_oracle, _ = gmres(lambda u, k: s["A"] @ u, s["b"], tol=tol, restart=50, max_iter=100)
+    print("second-kind iterations", r["iters"], "oracle", it_oracle, r["p_hist"])
+    assert abs(r["iters"] - it_oracle) <= 1
+    assert r["iters"] <= 12
+
+
+def test_double_layer_rejected_on_stokes(torch_cuda):
+    from paper_1506_05957_gb300 import FmmBem, FmmBemError, FMMBEM_STOKES, FMMBEM_LAYER_DOUBLE
+    from synth import icosphere
+    v, t = icosphere(2)
+    h = FmmBem(v, t, kernel=FMMBEM_STOKES, gauss_k=3, ncrit=60, theta=0.5)
+    with pytest.raises(FmmBemError):
+        h.set_layer(FMMBEM_LAYER_DOUBLE)
+    with pytest.raises(FmmBemError):
+        h.set_layer(7)
