@@ -43,9 +43,10 @@ def parse():
     ap.add_argument("--levels", type=int, default=6)
     ap.add_argument("--ncrit", type=int, default=WORKLOAD["ncrit"])
     ap.add_argument("--no-compare", action="store_true", help="skip the FP64 comparison solves")
-    ap.add_argument("--problem", default="laplace", choices=["laplace", "stokes", "serve"],
+    ap.add_argument("--problem", default="laplace", choices=["laplace", "stokes", "serve", "laplace2"],
                     help="laplace: the headline workload; stokes: Stokes flow past a sphere of 81920 panels; "
-                         "serve: a Poisson stream of mixed solves through the serving runtime")
+                         "serve: a Poisson stream of mixed solves through the serving runtime; "
+                         "laplace2: second-kind Laplace solves on octahedron spheres of 8192-131072 panels")
     ap.add_argument("--requests", type=int, default=48, help="serve: number of requests")
     ap.add_argument("--rate", type=float, default=20.0, help="serve: mean arrival rate (requests/s)")
     ap.add_argument("--max-active", type=int, default=6, help="serve: concurrent solves")
@@ -403,6 +404,9 @@ def run_ours(args, world, rank, local):
     h.close()
 
 
+LAPLACE2 = dict(workload="laplace2-exterior-sphere-octa7-131072", panels=131072, gauss_k=4, theta=0.5, p_initial=10,
+                p_min=3, tol=1e-6, restart=50, data="phi = dphi/dn = 1 on the unit sphere (exterior, normals into the body)")
+
 STOKES = dict(workload="stokes-sphere-ico6-81920", panels=81920, unknowns=245760, gauss_k=3, theta=0.5,
               p_initial=16, p_min=4, tol=1e-5, restart=50, ncrit=150, mu=1.0, data="u = (1,0,0) on the sphere")
 
@@ -468,6 +472,95 @@ def run_stokes(args, world, rank, local):
     if rank == 0:
         print(json.dumps(out), flush=True)
     h.close()
+
+
+def run_laplace2(args, world, rank, local):
+    """Laplace second kind (A = 1/2 I + K, eq. laplace_bem_final with phi unknown) on the
+    paper's grid-convergence case: the exterior of the unit sphere with phi = d phi/dn = 1
+    (normals into the body), spheres refined from the octahedron (8 4^L panels: 8192, 32768,
+    131072 for L = 5, 6, 7), initial p 10, tol 1e-6. The headline is the 131072-panel relaxed
+    mixed-precision solve; the table repeats the paper's relaxed vs non-relaxed comparison on
+    all three meshes (its Table laplace_2nd_relaxation) in both precisions."""
+    import torch
+    from synth import octasphere
+    from paper_1506_05957_gb300 import FmmBem, FMMBEM_FP64, FMMBEM_MIXED, FMMBEM_LAYER_DOUBLE, build
+    build.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    W = LAPLACE2
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def setup(level):
+        v, t = octasphere(level)
+        t = np.ascontiguousarray(t[:, [0, 2, 1]])  # normals into the body: out of the exterior domain
+        h = FmmBem(v, t, gauss_k=W["gauss_k"], ncrit=args.ncrit, theta=W["theta"], p_max=16, restart=W["restart"],
+                   max_iter=100, precision=FMMBEM_FP64, stream=stream.cuda_stream)
+        ones = torch.ones(len(t), dtype=torch.float64, device=dev)
+        b = torch.zeros_like(ones)
+        h.matvec(16, ones, b)  # b = V q with q = 1 (FP64 FMM at p = 16)
+        h.set_layer(FMMBEM_LAYER_DOUBLE)
+        h.set_precision(FMMBEM_MIXED)
+        return h, b, len(t)
+
+    def timed(h, b, x, relax, steps):
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        res = []
+        for k in range(steps):
+            flush.fill_(float(k))
+            x.zero_()
+            ev[k][0].record(stream)
+            res.append(h.solve(b, x, tol=W["tol"], relax=relax, p_initial=W["p_initial"], p_min=W["p_min"]))
+            ev[k][1].record(stream)
+        torch.cuda.synchronize(dev)
+        return float(np.sum([e0.elapsed_time(e1) for e0, e1 in ev])) / 1e3 / steps, res[-1]
+
+    h, b, n = setup(args.levels if args.levels != 6 else 7)
+    x = torch.zeros_like(b)
+    for _ in range(args.warmup):
+        x.zero_()
+        h.solve(b, x, tol=W["tol"], relax=True, p_initial=W["p_initial"], p_min=W["p_min"])
+    torch.cuda.synchronize(dev)
+    barrier(world, dev)
+    h.profile_enable(False)
+    sampler = ClockSampler(local)
+    sampler.start()
+    t_solve, r = timed(h, b, x, True, args.steps)
+    clocks = sampler.stop()
+    barrier(world, dev)
+    launches = int(h.profile()["kernel_launches"])
+    t_max = max_over_ranks(world, t_solve * args.steps, dev)
+    err = float(torch.linalg.vector_norm(x - 1.0) / np.sqrt(n))
+    out = {"metric": "relaxed GMRES solve s, Laplace second kind, exterior unit sphere (octahedron x7, 131072 panels)"
+                     " @1e-6", "value": t_max / args.steps / world, "unit": "s", "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": t_max / args.steps * 1e3, "higher_is_better": False,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+           "config": dict(W, ncrit=args.ncrit, panels=n, l2="flushed between steps (512 MB write)"),
+           "iters": r["iters"], "p_hist": r["p_hist"], "true_residual": r["true_res"], "gpu_launches": launches,
+           "rms_error_vs_exact_phi_1": err, "clocks": clocks}
+    h.close()
+    if not args.no_compare:
+        table = []
+        for level in (5, 6, 7):
+            h, b, n = setup(level)
+            x = torch.zeros_like(b)
+            row = {"panels": n}
+            for prec, name in ((FMMBEM_MIXED, "mixed"), (FMMBEM_FP64, "fp64")):
+                h.set_precision(prec)
+                h.solve(b, x, tol=W["tol"], relax=True, p_initial=W["p_initial"], p_min=W["p_min"])  # warm graphs
+                h.solve(b, x, tol=W["tol"], relax=False, p_initial=W["p_initial"], p_min=W["p_min"])
+                steps = 5 if prec == FMMBEM_MIXED else 1
+                t_fix, r_fix = timed(h, b, x, False, steps)
+                t_rel, r_rel = timed(h, b, x, True, steps)
+                row[name] = {"fixed_p_s": t_fix, "relaxed_s": t_rel, "speedup": t_fix / t_rel,
+                             "iters_fixed": r_fix["iters"], "iters_relaxed": r_rel["iters"],
+                             "p_hist_relaxed": r_rel["p_hist"]}
+            table.append(row)
+            h.close()
+        out["compare"] = {"relaxed_vs_fixed_p10": table,
+                          "paper_speedups_cpu": {"8192": 1.35, "32768": 1.29, "131072": 1.11}}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
 
 
 def serve_requests(n, seed=0):
@@ -560,6 +653,8 @@ def main():
         run_stokes(args, world, rank, local)
     elif args.problem == "serve":
         run_serve(args, world, rank, local)
+    elif args.problem == "laplace2":
+        run_laplace2(args, world, rank, local)
     else:
         run_ours(args, world, rank, local)
     if world > 1:

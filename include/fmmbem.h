@@ -133,6 +133,13 @@ int fmmbem_set_precision(fmmbem_handle* h, int precision);
 /* Select the M2L formulation; FMMBEM_ESTATE if the operator tables were not built. */
 int fmmbem_set_m2l_mode(fmmbem_handle* h, int mode);
 
+/* Lowest expansion order at which FMMBEM_MIXED mat-vecs in M2L mode TENSOR run M2L
+ * (m2l_min_p) and M2M/L2L (tree_min_p) on the tensor cores; below it they use the SIMT
+ * kernels (operator-table GEMM for M2L, per-parent translations for M2M/L2L), which are
+ * lighter per launch and share SMs with the concurrent near field. Both default to 1.
+ * FMMBEM_EINVAL for values below 1. */
+int fmmbem_set_tc_thresholds(fmmbem_handle* h, int m2l_min_p, int tree_min_p);
+
 /* Near-field kernel of FMMBEM_MIXED Laplace mat-vecs (same sums, different schedules):
  * 0 = source tiles staged in shared memory, targets held per lane;
  * 1 = (target, source slice) per thread, sources read through L1;

@@ -87,6 +87,7 @@ def lib():
         L.fmmbem_set_m2l_mode.argtypes = [_vp, ctypes.c_int]
         L.fmmbem_set_p2p_variant.argtypes = [_vp, ctypes.c_int]
         L.fmmbem_set_layer.argtypes = [_vp, ctypes.c_int]
+        L.fmmbem_set_tc_thresholds.argtypes = [_vp, ctypes.c_int, ctypes.c_int]
         L.fmmbem_estimate_bytes.argtypes = [ctypes.c_int64, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                             ctypes.POINTER(fmmbem_opts)]
         L.fmmbem_estimate_bytes.restype = ctypes.c_int64
@@ -206,6 +207,10 @@ class FmmBem:
     def set_layer(self, layer):
         """FMMBEM_LAYER_SINGLE (A = V) or FMMBEM_LAYER_DOUBLE (A = 1/2 I + K) for later mat-vecs and solves."""
         _check(lib().fmmbem_set_layer(self.h, int(layer)))
+
+    def set_tc_thresholds(self, m2l_min_p, tree_min_p):
+        """Lowest p at which M2L and M2M/L2L run on the tensor cores (mixed precision)."""
+        _check(lib().fmmbem_set_tc_thresholds(self.h, int(m2l_min_p), int(tree_min_p)))
 
     def set_p2p_variant(self, variant):
         _check(lib().fmmbem_set_p2p_variant(self.h, int(variant)))

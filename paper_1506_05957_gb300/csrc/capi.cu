@@ -196,7 +196,8 @@ static int matvec_launch(fmmbem_handle* h, int p, const double* xs, double* ys);
 // Mat-vecs of the solver (fixed buffers xfix -> kw, not profiling) replay one CUDA graph
 // per order p; the graph is recaptured when the arithmetic or kernel selection changed.
 int matvec_sorted(fmmbem_handle* h, int p, const double* xs, double* ys) {
-    const int mode = h->precision * 16 + h->m2l_mode + 4 * h->p2p_variant + 64 * (h->prof_on ? 1 : 0) + 128 * h->layer;
+    const int mode = h->precision * 16 + h->m2l_mode + 4 * h->p2p_variant + 64 * (h->prof_on ? 1 : 0) + 128 * h->layer +
+                     256 * (p >= h->tc_min_p) + 512 * (p >= h->tree_tc_min_p);
     if (!h->use_graphs || xs != h->xfix || ys != h->kw || h->stream == nullptr)
         return matvec_launch(h, p, xs, ys);
     prof_harvest(h);
@@ -435,6 +436,13 @@ int fmmbem_set_layer(fmmbem_handle* h, int layer) {
         return FMMBEM_ESTATE;
     }
     h->layer = layer;
+    return 0;
+}
+
+int fmmbem_set_tc_thresholds(fmmbem_handle* h, int m2l_min_p, int tree_min_p) {
+    if (!h || m2l_min_p < 1 || tree_min_p < 1) { fmmbem_set_error("bad tensor-core threshold"); return FMMBEM_EINVAL; }
+    h->tc_min_p = m2l_min_p;
+    h->tree_tc_min_p = tree_min_p;
     return 0;
 }
 

@@ -585,7 +585,7 @@ int far_field_t(fmmbem_handle* h, int p) {
     prof_end(h, FMMBEM_PASS_P2M, 1);
     // tensor-core tree translations in the mixed-precision M2L-TENSOR mode
     const bool tree_tc_on = std::is_same<T, float>::value && h->m2l_mode == FMMBEM_M2L_TENSOR && h->m2l_tc_ready &&
-                            h->tree_tiles != nullptr;
+                            h->tree_tiles != nullptr && p >= h->tree_tc_min_p;
     // M2M, deepest non-leaf level first
     prof_begin(h, FMMBEM_PASS_M2M);
     int nl = 0;

@@ -81,7 +81,8 @@ struct fmmbem_handle {
     // tensor-core (tcgen05) path: operators split into TF32 hi/lo, K-chunked core-matrix layout
     bool m2l_tc_ready = false;
     int m2l_mode = FMMBEM_M2L_TABLES;
-    int tc_min_p = 1;             // mixed-precision mat-vecs at p >= tc_min_p use the tensor cores
+    int tc_min_p = 1;             // mixed-precision M2L at p >= tc_min_p runs on the tensor cores
+    int tree_tc_min_p = 1;        // mixed-precision M2M/L2L at p >= tree_tc_min_p run on the tensor cores
     float* tab_tc = nullptr;
     size_t tc_stride = 0;
     int tc_rows_max = 0;

@@ -91,7 +91,7 @@ __global__ void k_sub(double* r, const double* b, const double* ax, int64_t n) {
 // flags an error and stops. Each block reduces the per-block partial dots itself in a
 // fixed order (results are deterministic); block 0 writes h1, h2 and ||w||^2 to out
 // (mapped pinned host memory).
-constexpr int ARN_THREADS = 256;
+constexpr int ARN_THREADS = 1024;  // largest block; the launch uses arnoldi_threads(n)
 constexpr int ARN_MAXV = 64;
 
 __device__ __forceinline__ bool grid_barrier(unsigned* count, volatile unsigned* gen, unsigned nb, int* err) {
@@ -120,7 +120,7 @@ __device__ __forceinline__ bool grid_barrier(unsigned* count, volatile unsigned*
 }
 
 // partial[j * gridDim.x + block] = sum over the block's rows of V_j w. Each thread takes its
-// rows (stride ARN_THREADS) and eight vectors at a time, so every row visit issues eight
+// rows (stride blockDim.x) and eight vectors at a time, so every row visit issues eight
 // independent loads; the eight sums are reduced across the block by warp shuffles and one
 // shared-memory pass in a fixed order (deterministic).
 __device__ void arn_partials(const double* V, int64_t ldv, int nv, const double* w, int64_t i0, int64_t i1,
@@ -131,7 +131,7 @@ __device__ void arn_partials(const double* V, int64_t ldv, int nv, const double*
         double s[8];
 #pragma unroll
         for (int q = 0; q < 8; ++q) s[q] = 0.0;
-        for (int64_t i = i0 + threadIdx.x; i < i1; i += ARN_THREADS) {
+        for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
             const double wi = w[i];
 #pragma unroll
             for (int q = 0; q < 8; ++q)
@@ -148,7 +148,7 @@ __device__ void arn_partials(const double* V, int64_t ldv, int nv, const double*
         __syncthreads();
         if (threadIdx.x < 8 && j0 + (int)threadIdx.x < nv) {
             double t = 0.0;
-            for (int w2 = 0; w2 < ARN_THREADS / 32; ++w2) t += red[threadIdx.x][w2];
+            for (int w2 = 0; w2 < (int)(blockDim.x >> 5); ++w2) t += red[threadIdx.x][w2];
             partial[(int64_t)(j0 + threadIdx.x) * gridDim.x + blockIdx.x] = t;
         }
         __syncthreads();
@@ -158,7 +158,7 @@ __device__ void arn_partials(const double* V, int64_t ldv, int nv, const double*
 // hs[j] = sum over blocks of partial[j][.], one warp per j, fixed order per lane and tree
 __device__ void arn_reduce(const double* partial, int nv, double* hs) {
     const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
-    for (int j = wp; j < nv; j += ARN_THREADS / 32) {
+    for (int j = wp; j < nv; j += (int)(blockDim.x >> 5)) {
         double t = 0.0;
         for (int b = lane; b < (int)gridDim.x; b += 32) t += partial[(int64_t)j * gridDim.x + b];
 #pragma unroll
@@ -172,7 +172,7 @@ __device__ void arn_reduce(const double* partial, int nv, double* hs) {
 // with scale != 0 the result is also multiplied by scale and written to V_{k+1} and xfix.
 __device__ void arn_update(const double* V, int64_t n, int nv, const double* hs, double* w, int64_t i0, int64_t i1,
                            double scale, double* vk1, double* xfix) {
-    for (int64_t i = i0 + threadIdx.x; i < i1; i += ARN_THREADS) {
+    for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
         double t = 0.0;
         for (int j0 = 0; j0 < nv; j0 += 8) {
             double v[8];
@@ -197,7 +197,7 @@ __device__ void arn_update(const double* V, int64_t n, int nv, const double* hs,
 // ||w - V h||^2 = ||w||^2 - ||h||^2 stays above ||w||^2 / 2 the projected vector is
 // normalized and written as V_{k+1} in the same sweep that forms it (one grid barrier).
 // Otherwise a second projection pass and an explicit norm follow (the CGS2 step).
-__global__ void __launch_bounds__(ARN_THREADS) k_arnoldi(double* V, int64_t n, int k, double* w, double* xfix,
+__global__ void __launch_bounds__(ARN_THREADS, 1) k_arnoldi(double* V, int64_t n, int k, double* w, double* xfix,
                                                          double* partial, unsigned* bar_count, unsigned* bar_gen,
                                                          double* out, int* err) {
     __shared__ double hs[ARN_MAXV];
@@ -220,17 +220,17 @@ __global__ void __launch_bounds__(ARN_THREADS) k_arnoldi(double* V, int64_t n, i
     for (int j = 0; j < nv; ++j) hh += hs[j] * hs[j];
     const double nn2 = ww - hh;
     if (blockIdx.x == 0)
-        for (int j = threadIdx.x; j < nv; j += ARN_THREADS) out[j] = hs[j];
+        for (int j = threadIdx.x; j < nv; j += blockDim.x) out[j] = hs[j];
     if (nn2 > 0.5 * ww && nn2 > 0.0 && isfinite(nn2)) {
         if (blockIdx.x == 0) {
-            for (int j = threadIdx.x; j < nv; j += ARN_THREADS) out[(ARN_MAXV + 1) + j] = 0.0;
+            for (int j = threadIdx.x; j < nv; j += blockDim.x) out[(ARN_MAXV + 1) + j] = 0.0;
             if (threadIdx.x == 0) out[2 * (ARN_MAXV + 1)] = nn2;
         }
         arn_update(V, n, nv, hs, w, i0, i1, 1.0 / sqrt(nn2), vk1, xfix);
         return;
     }
     // phase 2: reorthogonalize
-    for (int j = threadIdx.x; j < nv; j += ARN_THREADS) h1[j] = hs[j];
+    for (int j = threadIdx.x; j < nv; j += blockDim.x) h1[j] = hs[j];
     __syncthreads();
     arn_update(V, n, nv, h1, w, i0, i1, 0.0, nullptr, nullptr);
     double* part2 = partial + parea;
@@ -238,7 +238,7 @@ __global__ void __launch_bounds__(ARN_THREADS) k_arnoldi(double* V, int64_t n, i
     if (!grid_barrier(bar_count, bar_gen, nb, err)) return;
     arn_reduce(part2, nv, hs);
     if (blockIdx.x == 0)
-        for (int j = threadIdx.x; j < nv; j += ARN_THREADS) out[(ARN_MAXV + 1) + j] = hs[j];
+        for (int j = threadIdx.x; j < nv; j += blockDim.x) out[(ARN_MAXV + 1) + j] = hs[j];
     arn_update(V, n, nv, hs, w, i0, i1, 0.0, nullptr, nullptr);
     // phase 3: the norm of the twice-projected vector
     double* part3 = partial + 2 * parea;
@@ -250,7 +250,7 @@ __global__ void __launch_bounds__(ARN_THREADS) k_arnoldi(double* V, int64_t n, i
     const double hn = sqrt(nrm2);
     if (hn > 0.0 && isfinite(hn)) {
         const double inv = 1.0 / hn;
-        for (int64_t i = i0 + threadIdx.x; i < i1; i += ARN_THREADS) {
+        for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
             const double v = w[i] * inv;
             vk1[i] = v;
             xfix[i] = v;
@@ -304,6 +304,14 @@ int arnoldi_blocks() {
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_arnoldi, ARN_THREADS, 0) != cudaSuccess || per < 1) return 0;
     return sms;  // one block per SM: co-resident for the cooperative launch (more blocks make
                  // the grid barriers dearer than the extra loads in flight gain)
+}
+
+// Threads per Arnoldi block: enough that each thread holds about one row of its block's
+// slice, so every vector load of a phase is in flight at once (a multiple of 128, 256-1024).
+int arnoldi_threads(int64_t n, int blocks) {
+    const int64_t rows = (n + blocks - 1) / std::max(blocks, 1);
+    const int64_t t = (rows + 127) / 128 * 128;
+    return (int)std::min<int64_t>(ARN_THREADS, std::max<int64_t>(256, t));
 }
 
 int relaxed_p(double eta, double rho_prev, int p_initial, int p_min) {
@@ -406,7 +414,7 @@ static int gmres_solve_on(fmmbem_handle* h, const double* b, double tol, int rel
                 double* dout = h->arn_out_dev;
                 int* de = h->kerr;
                 void* args[] = {&dV, &nn, &kk, &dw, &dx, &dp, &bc, &bg, &dout, &de};
-                FMM_CU(cudaLaunchCooperativeKernel((const void*)k_arnoldi, dim3(h->arn_blocks), dim3(ARN_THREADS), args, 0,
+                FMM_CU(cudaLaunchCooperativeKernel((const void*)k_arnoldi, dim3(h->arn_blocks), dim3(arnoldi_threads(n, h->arn_blocks)), args, 0,
                                                    st));
                 h->launches += 1;
             }
