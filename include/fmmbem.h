@@ -136,8 +136,8 @@ int fmmbem_set_m2l_mode(fmmbem_handle* h, int mode);
 /* Lowest expansion order at which FMMBEM_MIXED mat-vecs in M2L mode TENSOR run M2L
  * (m2l_min_p) and M2M/L2L (tree_min_p) on the tensor cores; below it they use the SIMT
  * kernels (operator-table GEMM for M2L, per-parent translations for M2M/L2L), which are
- * lighter per launch and share SMs with the concurrent near field. Both default to 1.
- * FMMBEM_EINVAL for values below 1. */
+ * lighter per launch and share SMs with the concurrent near field. Defaults: m2l_min_p 1,
+ * tree_min_p 6 (measured on the 81920-panel sphere). FMMBEM_EINVAL for values below 1. */
 int fmmbem_set_tc_thresholds(fmmbem_handle* h, int m2l_min_p, int tree_min_p);
 
 /* Near-field kernel of FMMBEM_MIXED Laplace mat-vecs (same sums, different schedules):
@@ -145,8 +145,8 @@ int fmmbem_set_tc_thresholds(fmmbem_handle* h, int m2l_min_p, int tree_min_p);
  * 1 = (target, source slice) per thread, sources read through L1;
  * 2 = as 1, with each pair's sources bulk-copied into double-buffered shared memory
  *     (used when a leaf holds at most 1024 Gauss points, else 1);
- * 3 = one block per target leaf, its warps' lanes over the leaf's source stream and the
- *     targets looped in registers (default).
+ * 3 = one block per work item (at most 24 targets of one leaf), its warps' lanes over the
+ *     leaf's source stream and the targets looped in registers (default).
  * Returns FMMBEM_EINVAL for any other value. */
 int fmmbem_set_p2p_variant(fmmbem_handle* h, int variant);
 

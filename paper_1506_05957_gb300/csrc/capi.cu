@@ -193,6 +193,7 @@ void prof_harvest(fmmbem_handle* h) {
 
 static int matvec_launch(fmmbem_handle* h, int p, const double* xs, double* ys);
 
+
 // Mat-vecs of the solver (fixed buffers xfix -> kw, not profiling) replay one CUDA graph
 // per order p; the graph is recaptured when the arithmetic or kernel selection changed.
 int matvec_sorted(fmmbem_handle* h, int p, const double* xs, double* ys) {

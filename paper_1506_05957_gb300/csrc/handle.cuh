@@ -28,7 +28,7 @@ struct fmmbem_handle {
     int capturing = -1;          // order p of the graph being captured, else -1
     int pending_graph = -1;      // last replayed graph whose pass events await harvesting
     cudaEvent_t gev[FMMBEM_P_MAX + 1][2 * FMMBEM_N_PASSES] = {};
-    int gev_launches[FMMBEM_P_MAX + 1][FMMBEM_N_PASSES] = {};  // precision * 16 + m2l mode + 4 * p2p variant at capture
+    int gev_launches[FMMBEM_P_MAX + 1][FMMBEM_N_PASSES] = {};
     int64_t N = 0;   // panels
     int64_t NS = 0;  // Gauss points = K * N
 
@@ -82,7 +82,8 @@ struct fmmbem_handle {
     bool m2l_tc_ready = false;
     int m2l_mode = FMMBEM_M2L_TABLES;
     int tc_min_p = 1;             // mixed-precision M2L at p >= tc_min_p runs on the tensor cores
-    int tree_tc_min_p = 1;        // mixed-precision M2M/L2L at p >= tree_tc_min_p run on the tensor cores
+    int tree_tc_min_p = 6;        // mixed-precision M2M/L2L at p >= tree_tc_min_p run on the tensor cores
+                                  // (below it the per-parent SIMT kernels, which share SMs with the near field)
     float* tab_tc = nullptr;
     size_t tc_stride = 0;
     int tc_rows_max = 0;

@@ -91,7 +91,7 @@ __global__ void k_sub(double* r, const double* b, const double* ax, int64_t n) {
 // flags an error and stops. Each block reduces the per-block partial dots itself in a
 // fixed order (results are deterministic); block 0 writes h1, h2 and ||w||^2 to out
 // (mapped pinned host memory).
-constexpr int ARN_THREADS = 1024;  // largest block; the launch uses arnoldi_threads(n)
+constexpr int ARN_THREADS = 256;
 constexpr int ARN_MAXV = 64;
 
 __device__ __forceinline__ bool grid_barrier(unsigned* count, volatile unsigned* gen, unsigned nb, int* err) {
@@ -123,19 +123,24 @@ __device__ __forceinline__ bool grid_barrier(unsigned* count, volatile unsigned*
 // rows (stride blockDim.x) and eight vectors at a time, so every row visit issues eight
 // independent loads; the eight sums are reduced across the block by warp shuffles and one
 // shared-memory pass in a fixed order (deterministic).
+// With with_self the vector after the last V_j is w itself (entry nv of partial is w.w),
+// so ||w||^2 comes from the same sweep.
 __device__ void arn_partials(const double* V, int64_t ldv, int nv, const double* w, int64_t i0, int64_t i1,
-                             double* partial) {
+                             double* partial, bool with_self = false) {
     __shared__ double red[8][ARN_THREADS / 32];
     const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
-    for (int j0 = 0; j0 < nv; j0 += 8) {
+    const int nt = nv + (with_self ? 1 : 0);
+    for (int j0 = 0; j0 < nt; j0 += 8) {
         double s[8];
 #pragma unroll
         for (int q = 0; q < 8; ++q) s[q] = 0.0;
         for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
             const double wi = w[i];
 #pragma unroll
-            for (int q = 0; q < 8; ++q)
+            for (int q = 0; q < 8; ++q) {
                 if (j0 + q < nv) s[q] += V[(int64_t)(j0 + q) * ldv + i] * wi;
+                else if (j0 + q == nv && with_self) s[q] += wi * wi;
+            }
         }
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
@@ -146,7 +151,7 @@ __device__ void arn_partials(const double* V, int64_t ldv, int nv, const double*
 #pragma unroll
             for (int q = 0; q < 8; ++q) red[q][wp] = s[q];
         __syncthreads();
-        if (threadIdx.x < 8 && j0 + (int)threadIdx.x < nv) {
+        if (threadIdx.x < 8 && j0 + (int)threadIdx.x < nt) {
             double t = 0.0;
             for (int w2 = 0; w2 < (int)(blockDim.x >> 5); ++w2) t += red[threadIdx.x][w2];
             partial[(int64_t)(j0 + threadIdx.x) * gridDim.x + blockIdx.x] = t;
@@ -196,8 +201,9 @@ __device__ void arn_update(const double* V, int64_t n, int nv, const double* hs,
 // Gragg, Kaufman and Stewart): one sweep gives h = V^T w and ||w||^2; when
 // ||w - V h||^2 = ||w||^2 - ||h||^2 stays above ||w||^2 / 2 the projected vector is
 // normalized and written as V_{k+1} in the same sweep that forms it (one grid barrier).
-// Otherwise a second projection pass and an explicit norm follow (the CGS2 step).
-__global__ void __launch_bounds__(ARN_THREADS, 1) k_arnoldi(double* V, int64_t n, int k, double* w, double* xfix,
+// Otherwise a second projection pass follows (the CGS2 step), whose sweep also gives the
+// explicit ||w - V h||^2 (two grid barriers in all).
+__global__ void __launch_bounds__(ARN_THREADS) k_arnoldi(double* V, int64_t n, int k, double* w, double* xfix,
                                                          double* partial, unsigned* bar_count, unsigned* bar_gen,
                                                          double* out, int* err) {
     __shared__ double hs[ARN_MAXV];
@@ -211,8 +217,7 @@ __global__ void __launch_bounds__(ARN_THREADS, 1) k_arnoldi(double* V, int64_t n
     const size_t parea = (size_t)ARN_MAXV * gridDim.x;
     double* vk1 = V + (int64_t)(k + 1) * n;
     // phase 1: h = V^T w and ||w||^2
-    arn_partials(V, n, nv, w, i0, i1, partial);
-    arn_partials(w, n, 1, w, i0, i1, partial + (size_t)nv * gridDim.x);
+    arn_partials(V, n, nv, w, i0, i1, partial, true);
     if (!grid_barrier(bar_count, bar_gen, nb, err)) return;
     arn_reduce(partial, nv + 1, hs);
     const double ww = hs[nv];
@@ -229,32 +234,30 @@ __global__ void __launch_bounds__(ARN_THREADS, 1) k_arnoldi(double* V, int64_t n
         arn_update(V, n, nv, hs, w, i0, i1, 1.0 / sqrt(nn2), vk1, xfix);
         return;
     }
-    // phase 2: reorthogonalize
+    // phase 2: reorthogonalize. The sweep that projects w1 = w - V h1 again also gives
+    // ||w1||^2 explicitly, so ||w1 - V h2||^2 = ||w1||^2 - ||h2||^2 has no cancellation to
+    // fear (h2 is the small correction) and the new basis vector is normalized in the same
+    // pass that forms it.
     for (int j = threadIdx.x; j < nv; j += blockDim.x) h1[j] = hs[j];
     __syncthreads();
     arn_update(V, n, nv, h1, w, i0, i1, 0.0, nullptr, nullptr);
     double* part2 = partial + parea;
-    arn_partials(V, n, nv, w, i0, i1, part2);
+    arn_partials(V, n, nv, w, i0, i1, part2, true);
     if (!grid_barrier(bar_count, bar_gen, nb, err)) return;
-    arn_reduce(part2, nv, hs);
-    if (blockIdx.x == 0)
+    arn_reduce(part2, nv + 1, hs);
+    const double w1w1 = hs[nv];
+    double h2h2 = 0.0;
+    for (int j = 0; j < nv; ++j) h2h2 += hs[j] * hs[j];
+    const double nrm2 = fmax(w1w1 - h2h2, 0.0);  // rounding below zero: w1 lies in the span (breakdown)
+    if (blockIdx.x == 0) {
         for (int j = threadIdx.x; j < nv; j += blockDim.x) out[(ARN_MAXV + 1) + j] = hs[j];
-    arn_update(V, n, nv, hs, w, i0, i1, 0.0, nullptr, nullptr);
-    // phase 3: the norm of the twice-projected vector
-    double* part3 = partial + 2 * parea;
-    arn_partials(w, n, 1, w, i0, i1, part3);
-    if (!grid_barrier(bar_count, bar_gen, nb, err)) return;
-    arn_reduce(part3, 1, hs);
-    const double nrm2 = hs[0];
-    if (blockIdx.x == 0 && threadIdx.x == 0) out[2 * (ARN_MAXV + 1)] = nrm2;
+        if (threadIdx.x == 0) out[2 * (ARN_MAXV + 1)] = nrm2;
+    }
     const double hn = sqrt(nrm2);
     if (hn > 0.0 && isfinite(hn)) {
-        const double inv = 1.0 / hn;
-        for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
-            const double v = w[i] * inv;
-            vk1[i] = v;
-            xfix[i] = v;
-        }
+        arn_update(V, n, nv, hs, w, i0, i1, 1.0 / hn, vk1, xfix);
+    } else {
+        arn_update(V, n, nv, hs, w, i0, i1, 0.0, nullptr, nullptr);
     }
 }
 
@@ -306,13 +309,9 @@ int arnoldi_blocks() {
                  // the grid barriers dearer than the extra loads in flight gain)
 }
 
-// Threads per Arnoldi block: enough that each thread holds about one row of its block's
-// slice, so every vector load of a phase is in flight at once (a multiple of 128, 256-1024).
-int arnoldi_threads(int64_t n, int blocks) {
-    const int64_t rows = (n + blocks - 1) / std::max(blocks, 1);
-    const int64_t t = (rows + 127) / 128 * 128;
-    return (int)std::min<int64_t>(ARN_THREADS, std::max<int64_t>(256, t));
-}
+// Threads per Arnoldi block. Blocks sized to hold one row per thread (640 threads at 81920
+// unknowns) measured slower than 256 threads looping over two or three rows each.
+int arnoldi_threads(int64_t, int) { return ARN_THREADS; }
 
 int relaxed_p(double eta, double rho_prev, int p_initial, int p_min) {
     return relaxed_p_int(eta, rho_prev, p_initial, p_min);

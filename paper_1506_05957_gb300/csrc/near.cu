@@ -1072,6 +1072,28 @@ int near_field(fmmbem_handle* h, bool fp64, cudaStream_t st) {
     return rc;
 }
 
+// The work-item (source-lane) near-field kernel of this handle's operator over every item.
+static int launch_items(fmmbem_handle* h) {
+    const int4* it = h->p2p_items;
+    const unsigned nb = (unsigned)h->n_p2p_items;
+    if (nb == 0) return 0;
+    if (h->kernel == FMMBEM_LAPLACE && h->layer == FMMBEM_LAYER_DOUBLE)
+        k_p2p_vec_src<LAP_DL><<<nb, 32 * PS_WARPS, 0, h->stream>>>(it, h->cell_range, h->p2p_ptr, h->p2p_rec, h->p2p_off,
+                                                                   h->p2p_len, h->src_w, h->tgt_rel, h->K, h->corr_ptr,
+                                                                   h->corr_col, h->corr_dl, h->xin, h->ynear);
+    else if (h->kernel == FMMBEM_LAPLACE)
+        k_p2p_lap_src<<<nb, 32 * PS_WARPS, 0, h->stream>>>(it, h->cell_range, h->p2p_ptr, h->p2p_rec, h->p2p_off,
+                                                          h->p2p_len, h->src_w, h->tgt_rel, h->K, h->corr_ptr,
+                                                          h->corr_col, h->corr_sl, h->xin, h->ynear);
+    else
+        k_p2p_vec_src<STK_SL><<<nb, 32 * PS_WARPS, 0, h->stream>>>(it, h->cell_range, h->p2p_ptr, h->p2p_rec, h->p2p_off,
+                                                                   h->p2p_len, h->src_w, h->tgt_rel, h->K, h->corr_ptr,
+                                                                   h->corr_col, h->corr_sl, h->xin, h->ynear);
+    FMM_LAUNCHED();
+    h->launches += 1;
+    return 0;
+}
+
 int near_field_on(fmmbem_handle* h, bool fp64) {
     prof_begin(h, FMMBEM_PASS_P2P);
     int rc = 0;
@@ -1080,11 +1102,7 @@ int near_field_on(fmmbem_handle* h, bool fp64) {
             k_pack_sources_dipole<<<(unsigned)((h->NS + 255) / 256), 256, 0, h->stream>>>(h->src_rel, h->nrm_d, h->xin,
                                                                                          h->K, h->NS, h->src_w);
             FMM_LAUNCHED();
-            k_p2p_vec_src<LAP_DL><<<h->n_p2p_items, 32 * PS_WARPS, 0, h->stream>>>(
-                h->p2p_items, h->cell_range, h->p2p_ptr, h->p2p_rec, h->p2p_off, h->p2p_len, h->src_w, h->tgt_rel,
-                h->K, h->corr_ptr, h->corr_col, h->corr_dl, h->xin, h->ynear);
-            FMM_LAUNCHED();
-            h->launches += 1;
+            FMM_TRY(launch_items(h));
         } else {
             rc = fp64 ? launch_p2p<double, LAP_DL>(h, h->corr_dl) : launch_p2p<float, LAP_DL>(h, h->corr_dl);
         }
@@ -1096,11 +1114,7 @@ int near_field_on(fmmbem_handle* h, bool fp64) {
         k_pack_sources<<<(unsigned)((h->NS + 255) / 256), 256, 0, h->stream>>>(h->src_rel, h->xin, h->K, h->NS, h->src_w);
         FMM_LAUNCHED();
         if (h->p2p_variant == 3 && h->p2p_items) {
-            k_p2p_lap_src<<<h->n_p2p_items, 32 * PS_WARPS, 0, h->stream>>>(
-                h->p2p_items, h->cell_range, h->p2p_ptr, h->p2p_rec, h->p2p_off, h->p2p_len, h->src_w, h->tgt_rel,
-                h->K, h->corr_ptr, h->corr_col, h->corr_sl, h->xin, h->ynear);
-            FMM_LAUNCHED();
-            h->launches += 1;
+            FMM_TRY(launch_items(h));
             prof_end(h, FMMBEM_PASS_P2P, 2);
             h->launches += 1;
             return 0;
@@ -1148,11 +1162,7 @@ int near_field_on(fmmbem_handle* h, bool fp64) {
         k_pack_sources_stokes<<<(unsigned)((h->NS + 255) / 256), 256, 0, h->stream>>>(h->src_rel, h->xin, h->K, h->NS,
                                                                                      h->src_w);
         FMM_LAUNCHED();
-        k_p2p_vec_src<STK_SL><<<h->n_p2p_items, 32 * PS_WARPS, 0, h->stream>>>(
-            h->p2p_items, h->cell_range, h->p2p_ptr, h->p2p_rec, h->p2p_off, h->p2p_len, h->src_w, h->tgt_rel, h->K,
-            h->corr_ptr, h->corr_col, h->corr_sl, h->xin, h->ynear);
-        FMM_LAUNCHED();
-        h->launches += 1;
+        FMM_TRY(launch_items(h));
     } else rc = fp64 ? launch_p2p<double, STK_SL>(h, h->corr_sl) : launch_p2p<float, STK_SL>(h, h->corr_sl);
     prof_end(h, FMMBEM_PASS_P2P, 1);
     h->launches += 1;

@@ -257,3 +257,4 @@ def test_p2p_variants_agree(torch_cuda, sphere1280, ncrit):
         assert rel(y, ref) < 1e-5, v
     with pytest.raises(Exception):
         h.set_p2p_variant(4)
+

@@ -88,14 +88,34 @@ def test_mixed_requests_match_solo_solves(torch_cuda):
         c = np.sum(np.einsum("ij,ij->i", tr, nrm) * area) / np.sum(area)
         return (tr - c * nrm).reshape(-1)
 
+    import torch
     for r, (xs, rs), (xm, info) in zip(reqs, solo, out):
         assert info["status"] == 0, info
         assert abs(info["iters"] - rs["iters"]) <= 1, (info, rs["iters"])
-        xs, xm = comparable(r, xs), comparable(r, xm)
-        diff = np.linalg.norm(xm - xs) / np.linalg.norm(xs)
-        print(len(r["t"]), "kernel", r["kernel"], "tol", r["tol"], "iters", info["iters"], "diff", diff,
-              "queue %.3f setup %.3f solve %.3f" % (info["queue_s"], info["setup_s"], info["solve_s"]))
-        assert diff <= 10 * r["tol"]
         assert info["true_res"] <= 2 * r["tol"]
+        # Both solutions meet the tolerance on their residuals, so their difference d
+        # satisfies ||A d|| <= 4 tol ||b||: checked with the exact (direct FP64) operator.
+        h = FmmBem(r["v"], r["t"], kernel=r["kernel"], gauss_k=r["gauss_k"], ncrit=150, theta=0.5, p_max=16,
+                   precision=FMMBEM_FP64)
+        d = torch.tensor(xm - xs, dtype=torch.float64, device="cuda")
+        ad = torch.zeros_like(d)
+        h.matvec_direct(d, ad)
+        h.close()
+        op_diff = float(torch.linalg.vector_norm(ad)) / np.linalg.norm(r["rhs"])
+        xs_c, xm_c = comparable(r, xs), comparable(r, xm)
+        diff = np.linalg.norm(xm_c - xs_c) / np.linalg.norm(xs_c)
+        print(len(r["t"]), "kernel", r["kernel"], "tol", r["tol"], "iters", info["iters"], "diff", diff,
+              "op_diff", op_diff, "queue %.3f setup %.3f solve %.3f" % (info["queue_s"], info["setup_s"],
+                                                                         info["solve_s"]))
+        assert op_diff <= 4 * r["tol"]
+        if r["kernel"] == FMMBEM_STOKES:
+            # Stokes first kind is ill-conditioned beyond its null space on elongated bodies:
+            # the traction may differ by more than tol, the drag (its integral) may not
+            p = r["v"][r["t"]]
+            area = 0.5 * np.linalg.norm(np.cross(p[:, 1] - p[:, 0], p[:, 2] - p[:, 0]), axis=1)
+            fs, fm = (np.sum(z.reshape(-1, 3)[:, 0] * area) for z in (xs, xm))
+            assert abs(fm - fs) <= 10 * r["tol"] * abs(fs)
+        else:
+            assert diff <= 10 * r["tol"]
     # some requests had to wait for memory or a worker
     assert max(info["queue_s"] for _, info in out) > 0.0
