@@ -129,6 +129,93 @@ __global__ void __launch_bounds__(32 * P2M_WARPS) k_p2m(int p, const int* leaves
     }
 }
 
+// Mixed-precision P2M from the packed sources (pack_sources): each Gauss point is a float4
+// (position relative to its leaf centre, strength), so the pass does no FP64 arithmetic
+// (FP64 throughput is scarce on this GPU). Otherwise as k_p2m: a lane per Gauss point,
+// harmonics column by column, coefficients reduced across the warp into shared memory.
+// DL = true: the double layer's dipoles (two float4 per Gauss point, the moment w n in
+// .w of the first and .x, .y of the second), scattered as in k_p2m_dl.
+template <bool DL>
+__global__ void __launch_bounds__(32 * P2M_WARPS) k_p2m_packed(int p, const int* leaves, const double4* cs,
+                                                              const int2* range, const float4* srcw, int K, float* M) {
+    extern __shared__ unsigned char smem_raw[];
+    float* acc = reinterpret_cast<float*>(smem_raw);  // [warps][ncoef][2]
+    const int nco = ncoef(p);
+    const int cell = leaves[blockIdx.x];
+    const int2 r = range[cell];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int q = threadIdx.x; q < P2M_WARPS * nco * 2; q += blockDim.x) acc[q] = 0.f;
+    __syncthreads();
+    float* wacc = acc + warp * nco * 2;
+    const float inv_s = (float)(1.0 / cs[cell].w);
+    const int s0 = r.x * K, s1 = r.y * K;
+    auto add = [&](int n, int m, cpx<float> d) {  // M~(n, m) += conj(d), summed over the warp
+        const int qi = cidx(n, m);
+        const float re = warp_sum(d.re), im = warp_sum(-d.im);
+        if (lane == 0) {
+            wacc[2 * qi] += re;
+            wacc[2 * qi + 1] += im;
+        }
+    };
+    for (int base = s0 + warp * 32; base < s1; base += P2M_WARPS * 32) {
+        const int s = base + lane;
+        float vx = 0.f, vy = 0.f, vz = 0.f, q = 0.f, c = 0.f;
+        cpx<float> a = mk(0.f, 0.f), b = mk(0.f, 0.f);
+        if (s < s1) {
+            if (DL) {
+                const float4 u = srcw[2 * s], u2 = srcw[2 * s + 1];
+                vx = u.x * inv_s; vy = u.y * inv_s; vz = u.z * inv_s;
+                const float mx = u.w * inv_s, my = u2.x * inv_s, mz = u2.y * inv_s;
+                c = mz;
+                a = mk(0.5f * mx, -0.5f * my);
+                b = mk(0.5f * mx, 0.5f * my);
+            } else {
+                const float4 u = srcw[s];
+                vx = u.x * inv_s; vy = u.y * inv_s; vz = u.z * inv_s;
+                q = u.w;
+            }
+        }
+        auto emit = [&](int n, int m, cpx<float> R) {
+            if (DL) {  // R = R_n^m, n < p: feeds degree n + 1
+                add(n + 1, m, c * R);
+                if (m >= 1) add(n + 1, m - 1, a * R);
+                const cpx<float> bR = b * R;
+                add(n + 1, m + 1, mk(-bR.re, -bR.im));
+                if (m == 1) add(n + 1, 0, b * conj(R));
+            } else {
+                add(n, m, q * R);
+            }
+        };
+        const int nmax = DL ? p - 1 : p;  // highest degree generated
+        const float r2 = vx * vx + vy * vy + vz * vz;
+        const cpx<float> xy = mk(vx, vy);
+        cpx<float> diag = mk(1.f, 0.f);
+        for (int m = 0; m <= nmax; ++m) {
+            if (m > 0) diag = (-0.5f / (float)m) * (xy * diag);
+            emit(m, m, diag);
+            if (m + 1 > nmax) break;
+            cpx<float> prev2 = diag, prev1 = vz * diag;
+            emit(m + 1, m, prev1);
+            for (int n = m + 2; n <= nmax; ++n) {
+                const float inv = 1.f / (float)((n - m) * (n + m));
+                cpx<float> cur = mk(((float)(2 * n - 1) * vz * prev1.re - r2 * prev2.re) * inv,
+                                    ((float)(2 * n - 1) * vz * prev1.im - r2 * prev2.im) * inv);
+                emit(n, m, cur);
+                prev2 = prev1;
+                prev1 = cur;
+            }
+        }
+    }
+    __syncthreads();
+    float* out = M + (size_t)cell * ESTRIDE;
+    for (int idx = threadIdx.x; idx < nco * 2; idx += blockDim.x) {
+        float v = 0.f;
+#pragma unroll
+        for (int w = 0; w < P2M_WARPS; ++w) v += acc[w * nco * 2 + idx];
+        out[idx] = v;
+    }
+}
+
 // P2M of the double layer (eq. laplace_bem_dGdn): Gauss point y carries a dipole of
 // moment w n_j (w = q_k S_j x_j, n_j its panel's normal), whose potential is
 // w n_j . grad_y (1/|x - y|). Its multipole coefficients are the conjugated directional
@@ -412,7 +499,7 @@ __global__ void __launch_bounds__(TREE_THREADS) k_l2l(int p, const int* parents,
 template <typename T, int NC>
 __global__ void k_l2p(int p, const int* leaves, const double4* cs, const int2* range, const double4* tgt, const T* L,
                       const double* ynear, double scale, double ox, double oy, double oz, const double* xs_half,
-                      double* yout) {
+                      const float4* tgt_rel, double* yout) {
     __shared__ T sL[NC * NCOEF_MAX * 2];
     const int cell = leaves[blockIdx.x];
     const double4 cc = cs[cell];
@@ -426,9 +513,19 @@ __global__ void k_l2p(int p, const int* leaves, const double4* cs, const int2* r
     }
     __syncthreads();
     const double inv_s = 1.0 / cc.w;
+    // FP32 with one expansion: the FP32 offsets from the leaf centre (no FP64 arithmetic)
+    constexpr bool rel = std::is_same<T, float>::value && NC == 1;
+    const float inv_sf = (float)inv_s;
     for (int i = r.x + threadIdx.x; i < r.y; i += blockDim.x) {
-        const double4 x = tgt[i];
-        const T vx = T((x.x - cc.x) * inv_s), vy = T((x.y - cc.y) * inv_s), vz = T((x.z - cc.z) * inv_s);
+        T vx, vy, vz;
+        double4 x = make_double4(0.0, 0.0, 0.0, 0.0);
+        if (rel) {
+            const float4 t = tgt_rel[i];
+            vx = T(t.x * inv_sf); vy = T(t.y * inv_sf); vz = T(t.z * inv_sf);
+        } else {
+            x = tgt[i];
+            vx = T((x.x - cc.x) * inv_s); vy = T((x.y - cc.y) * inv_s); vz = T((x.z - cc.z) * inv_s);
+        }
         const T r2 = vx * vx + vy * vy + vz * vz;
         const cpx<T> xy = mk(vx, vy);
         T phi[NC], gz[NC];
@@ -469,7 +566,7 @@ __global__ void k_l2p(int p, const int* leaves, const double4* cs, const int2* r
             }
         }
         if (NC == 1) {
-            const double far = (double)phi[0] * inv_s;
+            const double far = rel ? (double)(phi[0] * inv_sf) : (double)phi[0] * inv_s;
             yout[i] = scale * (far + ynear[i]) + (xs_half ? 0.5 * xs_half[i] : 0.0);  // 1/2 I of the second kind
         } else {
             const double is2 = inv_s * inv_s;
@@ -574,7 +671,16 @@ int far_field_t(fmmbem_handle* h, int p) {
     // P2M
     prof_begin(h, FMMBEM_PASS_P2M);
     const size_t sm = (size_t)P2M_WARPS * NC * nco * 2 * sizeof(T);
-    if (NC == 1 && h->layer == FMMBEM_LAYER_DOUBLE) {
+    if (std::is_same<T, float>::value && NC == 1) {
+        // mixed precision: the packed FP32 sources
+        float* Mf = reinterpret_cast<float*>(h->M);
+        if (h->layer == FMMBEM_LAYER_DOUBLE)
+            k_p2m_packed<true><<<h->n_leaves, 32 * P2M_WARPS, sm, st>>>(p, h->leaves, h->cell_cs, h->cell_range,
+                                                                       h->src_w, h->K, Mf);
+        else
+            k_p2m_packed<false><<<h->n_leaves, 32 * P2M_WARPS, sm, st>>>(p, h->leaves, h->cell_cs, h->cell_range,
+                                                                        h->src_w, h->K, Mf);
+    } else if (NC == 1 && h->layer == FMMBEM_LAYER_DOUBLE) {
         k_p2m_dl<T><<<h->n_leaves, 32 * P2M_WARPS, sm, st>>>(p, h->leaves, h->cell_cs, h->cell_range, src, h->nrm_d,
                                                             h->xin, h->K, M);
     } else {
@@ -645,7 +751,7 @@ int far_eval_t(fmmbem_handle* h, int p, double* y_sorted, double scale) {
                                                     reinterpret_cast<const T*>(h->L), h->ynear, scale, h->origin[0],
                                                     h->origin[1], h->origin[2],
                                                     NC == 1 && h->layer == FMMBEM_LAYER_DOUBLE ? h->xin : nullptr,
-                                                    y_sorted);
+                                                    h->tgt_rel, y_sorted);
     FMM_LAUNCHED();
     prof_end(h, FMMBEM_PASS_L2P, 1);
     h->launches += 1;

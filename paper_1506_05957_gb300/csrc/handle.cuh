@@ -37,6 +37,7 @@ struct fmmbem_handle {
     double4* tgt_d = nullptr;     // [N] centroid (x,y,z, area)
     float4* tgt_f = nullptr;
     double4* nrm_d = nullptr;     // [N] unit normal (x,y,z, area)
+    float4* nrm_f = nullptr;      // [N] the same in FP32 (mixed-precision double layer)
     double* verts = nullptr;      // [N][9] panel vertices
     double4* src_d = nullptr;     // [NS] Gauss point (x,y,z, q_k S_j), panel-major
     float4* src_f = nullptr;
@@ -183,6 +184,7 @@ int expansion_eval(int kind, int p, const double* center, double scale, int n_sr
                    int n_tgt, const double* tgt, double* out, cudaStream_t st);
 int init_octant_tables(fmmbem_handle* h);
 // near.cu
+int pack_sources(fmmbem_handle* h);
 int near_field(fmmbem_handle* h, bool fp64, cudaStream_t st);
 int direct_field(fmmbem_handle* h, bool fp64, int which, const double* x_sorted, double* y_sorted);
 // krylov.cu

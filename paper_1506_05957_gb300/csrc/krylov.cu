@@ -119,49 +119,39 @@ __device__ __forceinline__ bool grid_barrier(unsigned* count, volatile unsigned*
     return s_ok != 0;
 }
 
-// partial[j * gridDim.x + block] = sum over the block's rows of V_j w. Each thread takes its
-// rows (stride blockDim.x) and eight vectors at a time, so every row visit issues eight
-// independent loads; the eight sums are reduced across the block by warp shuffles and one
-// shared-memory pass in a fixed order (deterministic).
-// With with_self the vector after the last V_j is w itself (entry nv of partial is w.w),
-// so ||w||^2 comes from the same sweep.
+// FP64 throughput is scarce on this GPU (a few FP64 operations per clock per SM), so the
+// helpers below spend about one FP64 operation per vector element and little on reductions.
+
+// partial[j * gridDim.x + block] = sum over the block's rows of V_j w. One warp per vector:
+// its lanes stride over the block's rows with four independent accumulators (eight loads in
+// flight per lane), then one five-level shuffle reduction per vector. With with_self the
+// vector after the last V_j is w itself (entry nv is w.w), so ||w||^2 comes from the same
+// sweep. Fixed summation order: deterministic.
 __device__ void arn_partials(const double* V, int64_t ldv, int nv, const double* w, int64_t i0, int64_t i1,
                              double* partial, bool with_self = false) {
-    __shared__ double red[8][ARN_THREADS / 32];
-    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5, nw = (int)(blockDim.x >> 5);
     const int nt = nv + (with_self ? 1 : 0);
-    for (int j0 = 0; j0 < nt; j0 += 8) {
-        double s[8];
-#pragma unroll
-        for (int q = 0; q < 8; ++q) s[q] = 0.0;
-        for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
-            const double wi = w[i];
-#pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                if (j0 + q < nv) s[q] += V[(int64_t)(j0 + q) * ldv + i] * wi;
-                else if (j0 + q == nv && with_self) s[q] += wi * wi;
-            }
+    for (int j = wp; j < nt; j += nw) {
+        const double* vj = j < nv ? V + (int64_t)j * ldv : w;
+        double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+        int64_t i = i0 + lane;
+        for (; i + 96 < i1; i += 128) {
+            s0 = fma(vj[i], w[i], s0);
+            s1 = fma(vj[i + 32], w[i + 32], s1);
+            s2 = fma(vj[i + 64], w[i + 64], s2);
+            s3 = fma(vj[i + 96], w[i + 96], s3);
         }
+        for (; i < i1; i += 32) s0 = fma(vj[i], w[i], s0);
+        double t = (s0 + s1) + (s2 + s3);
 #pragma unroll
-        for (int q = 0; q < 8; ++q) {
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) s[q] += __shfl_xor_sync(0xffffffffu, s[q], o);
-        }
-        if (lane == 0)
-#pragma unroll
-            for (int q = 0; q < 8; ++q) red[q][wp] = s[q];
-        __syncthreads();
-        if (threadIdx.x < 8 && j0 + (int)threadIdx.x < nt) {
-            double t = 0.0;
-            for (int w2 = 0; w2 < (int)(blockDim.x >> 5); ++w2) t += red[threadIdx.x][w2];
-            partial[(int64_t)(j0 + threadIdx.x) * gridDim.x + blockIdx.x] = t;
-        }
-        __syncthreads();
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        if (lane == 0) partial[(int64_t)j * gridDim.x + blockIdx.x] = t;
     }
 }
 
-// hs[j] = sum over blocks of partial[j][.], one warp per j, fixed order per lane and tree
-__device__ void arn_reduce(const double* partial, int nv, double* hs) {
+// hs[j] = sum over blocks of partial[j][.] (one warp per j, fixed order); every block forms
+// the same hs. With sq != nullptr, *sq = sum_{j < nsq} hs[j]^2, by one warp.
+__device__ void arn_reduce(const double* partial, int nv, double* hs, int nsq = 0, double* sq = nullptr) {
     const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
     for (int j = wp; j < nv; j += (int)(blockDim.x >> 5)) {
         double t = 0.0;
@@ -171,21 +161,32 @@ __device__ void arn_reduce(const double* partial, int nv, double* hs) {
         if (lane == 0) hs[j] = t;
     }
     __syncthreads();
+    if (sq && wp == 0) {
+        double t = 0.0;
+        for (int j = lane; j < nsq; j += 32) t = fma(hs[j], hs[j], t);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        if (lane == 0) *sq = t;
+    }
+    if (sq) __syncthreads();
 }
 
-// w[i] -= sum_j hs[j] V_j[i] over the block's rows (eight independent loads per group);
-// with scale != 0 the result is also multiplied by scale and written to V_{k+1} and xfix.
+// w[i] -= sum_j hs[j] V_j[i] over the block's rows (eight independent loads per full group,
+// then the remaining vectors one by one: exactly nv FP64 multiply-adds per row); with
+// scale != 0 the result is also multiplied by scale and written to V_{k+1} and xfix.
 __device__ void arn_update(const double* V, int64_t n, int nv, const double* hs, double* w, int64_t i0, int64_t i1,
                            double scale, double* vk1, double* xfix) {
+    const int full = nv & ~7;
     for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
         double t = 0.0;
-        for (int j0 = 0; j0 < nv; j0 += 8) {
+        for (int j0 = 0; j0 < full; j0 += 8) {
             double v[8];
 #pragma unroll
-            for (int q = 0; q < 8; ++q) v[q] = j0 + q < nv ? V[(int64_t)(j0 + q) * n + i] : 0.0;
+            for (int q = 0; q < 8; ++q) v[q] = V[(int64_t)(j0 + q) * n + i];
 #pragma unroll
-            for (int q = 0; q < 8; ++q) t += (j0 + q < nv ? hs[j0 + q] : 0.0) * v[q];
+            for (int q = 0; q < 8; ++q) t = fma(hs[j0 + q], v[q], t);
         }
+        for (int j = full; j < nv; ++j) t = fma(hs[j], V[(int64_t)j * n + i], t);
         const double r = w[i] - t;
         if (scale != 0.0) {
             const double u = r * scale;
@@ -217,13 +218,12 @@ __global__ void __launch_bounds__(ARN_THREADS) k_arnoldi(double* V, int64_t n, i
     const size_t parea = (size_t)ARN_MAXV * gridDim.x;
     double* vk1 = V + (int64_t)(k + 1) * n;
     // phase 1: h = V^T w and ||w||^2
+    __shared__ double s_sq;
     arn_partials(V, n, nv, w, i0, i1, partial, true);
     if (!grid_barrier(bar_count, bar_gen, nb, err)) return;
-    arn_reduce(partial, nv + 1, hs);
+    arn_reduce(partial, nv + 1, hs, nv, &s_sq);
     const double ww = hs[nv];
-    double hh = 0.0;
-    for (int j = 0; j < nv; ++j) hh += hs[j] * hs[j];
-    const double nn2 = ww - hh;
+    const double nn2 = ww - s_sq;
     if (blockIdx.x == 0)
         for (int j = threadIdx.x; j < nv; j += blockDim.x) out[j] = hs[j];
     if (nn2 > 0.5 * ww && nn2 > 0.0 && isfinite(nn2)) {
@@ -241,14 +241,13 @@ __global__ void __launch_bounds__(ARN_THREADS) k_arnoldi(double* V, int64_t n, i
     for (int j = threadIdx.x; j < nv; j += blockDim.x) h1[j] = hs[j];
     __syncthreads();
     arn_update(V, n, nv, h1, w, i0, i1, 0.0, nullptr, nullptr);
+    __syncthreads();  // arn_partials reads rows of w that other threads of the block updated
     double* part2 = partial + parea;
     arn_partials(V, n, nv, w, i0, i1, part2, true);
     if (!grid_barrier(bar_count, bar_gen, nb, err)) return;
-    arn_reduce(part2, nv + 1, hs);
+    arn_reduce(part2, nv + 1, hs, nv, &s_sq);
     const double w1w1 = hs[nv];
-    double h2h2 = 0.0;
-    for (int j = 0; j < nv; ++j) h2h2 += hs[j] * hs[j];
-    const double nrm2 = fmax(w1w1 - h2h2, 0.0);  // rounding below zero: w1 lies in the span (breakdown)
+    const double nrm2 = fmax(w1w1 - s_sq, 0.0);  // rounding below zero: w1 lies in the span (breakdown)
     if (blockIdx.x == 0) {
         for (int j = threadIdx.x; j < nv; j += blockDim.x) out[(ARN_MAXV + 1) + j] = hs[j];
         if (threadIdx.x == 0) out[2 * (ARN_MAXV + 1)] = nrm2;

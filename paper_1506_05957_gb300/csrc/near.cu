@@ -207,11 +207,17 @@ __global__ void __launch_bounds__(P2P_THREADS) k_p2p(const int* leaves, const do
 // interactions. FP32 partial sums over 32 sources are added to FP64 accumulators.
 constexpr int LAP_TILE = 1024;
 
-__global__ void k_pack_sources(const float4* src_rel, const double* xs, int K, int64_t ns, float4* out) {
-    const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (g >= ns) return;
-    const float4 y = src_rel[g];
-    out[g] = make_float4(y.x, y.y, y.z, (float)((double)y.w * xs[g / K]));
+// One thread per panel converts x_j to FP32 once and writes its K Gauss points as
+// (leaf-relative position, q_k S_j x_j): FP64 throughput is scarce on this GPU, so the
+// conversion is done once per panel, not per Gauss point or per pass.
+__global__ void k_pack_sources(const float4* src_rel, const double* xs, int K, int64_t n, float4* out) {
+    const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    const float x = (float)xs[j];
+    for (int k = 0; k < K; ++k) {
+        const float4 y = src_rel[j * K + k];
+        out[j * K + k] = make_float4(y.x, y.y, y.z, y.w * x);
+    }
 }
 
 __device__ __forceinline__ float rsqrt_approx(float x) {
@@ -818,26 +824,32 @@ template <int OP> struct VecLane;
 template <> struct VecLane<STK_SL> { static constexpr int DOF = 3, TM = P2P_SRC_TMAX_STOKES; };
 template <> struct VecLane<LAP_DL> { static constexpr int DOF = 1, TM = P2P_SRC_TMAX; };
 
-__global__ void k_pack_sources_stokes(const float4* src_rel, const double* xs, int K, int64_t ns, float4* out) {
-    const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (g >= ns) return;
-    const float4 y = src_rel[g];
-    const int64_t j = g / K;
-    const double w = (double)y.w;
-    out[2 * g] = make_float4(y.x, y.y, y.z, (float)(w * xs[3 * j]));
-    out[2 * g + 1] = make_float4((float)(w * xs[3 * j + 1]), (float)(w * xs[3 * j + 2]), 0.f, 0.f);
+// Both pack per panel (one FP64-to-FP32 conversion per unknown, as k_pack_sources).
+__global__ void k_pack_sources_stokes(const float4* src_rel, const double* xs, int K, int64_t n, float4* out) {
+    const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    const float t0 = (float)xs[3 * j], t1 = (float)xs[3 * j + 1], t2 = (float)xs[3 * j + 2];
+    for (int k = 0; k < K; ++k) {
+        const int64_t g = j * K + k;
+        const float4 y = src_rel[g];
+        out[2 * g] = make_float4(y.x, y.y, y.z, y.w * t0);
+        out[2 * g + 1] = make_float4(y.w * t1, y.w * t2, 0.f, 0.f);
+    }
 }
 
-__global__ void k_pack_sources_dipole(const float4* src_rel, const double4* nrm, const double* xs, int K, int64_t ns,
+__global__ void k_pack_sources_dipole(const float4* src_rel, const float4* nrm_f, const double* xs, int K, int64_t n,
                                       float4* out) {
-    const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (g >= ns) return;
-    const float4 y = src_rel[g];
-    const int64_t j = g / K;
-    const double w = (double)y.w * xs[j];
-    const double4 n = nrm[j];
-    out[2 * g] = make_float4(y.x, y.y, y.z, (float)(w * n.x));
-    out[2 * g + 1] = make_float4((float)(w * n.y), (float)(w * n.z), 0.f, 0.f);
+    const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    const float x = (float)xs[j];
+    const float4 nv = nrm_f[j];
+    for (int k = 0; k < K; ++k) {
+        const int64_t g = j * K + k;
+        const float4 y = src_rel[g];
+        const float w = y.w * x;
+        out[2 * g] = make_float4(y.x, y.y, y.z, w * nv.x);
+        out[2 * g + 1] = make_float4(w * nv.y, w * nv.z, 0.f, 0.f);
+    }
 }
 
 template <int OP> struct VlShared {
@@ -1064,6 +1076,21 @@ int launch_direct(fmmbem_handle* h, const double* xs, double* y, const double* c
 
 int near_field_on(fmmbem_handle* h, bool fp64);
 
+// Per-mat-vec FP32 source data of the mixed-precision passes (P2M and the near field read
+// it), on the handle's stream before the near and far fields fork.
+int pack_sources(fmmbem_handle* h) {
+    const unsigned g = (unsigned)((h->N + 255) / 256);
+    if (h->kernel == FMMBEM_STOKES)
+        k_pack_sources_stokes<<<g, 256, 0, h->stream>>>(h->src_rel, h->xin, h->K, h->N, h->src_w);
+    else if (h->layer == FMMBEM_LAYER_DOUBLE)
+        k_pack_sources_dipole<<<g, 256, 0, h->stream>>>(h->src_rel, h->nrm_f, h->xin, h->K, h->N, h->src_w);
+    else
+        k_pack_sources<<<g, 256, 0, h->stream>>>(h->src_rel, h->xin, h->K, h->N, h->src_w);
+    FMM_LAUNCHED();
+    h->launches += 1;
+    return 0;
+}
+
 int near_field(fmmbem_handle* h, bool fp64, cudaStream_t st) {
     cudaStream_t keep = h->stream;
     h->stream = st;
@@ -1094,79 +1121,64 @@ static int launch_items(fmmbem_handle* h) {
     return 0;
 }
 
+// The near field of one mat-vec (P2P plus the correction rows) on h->stream. The
+// mixed-precision kernels read the sources packed by pack_sources.
 int near_field_on(fmmbem_handle* h, bool fp64) {
     prof_begin(h, FMMBEM_PASS_P2P);
-    int rc = 0;
+    const int64_t l0 = h->launches;
+    const bool items = !fp64 && h->p2p_variant == 3 && h->p2p_items;
     if (h->kernel == FMMBEM_LAPLACE && h->layer == FMMBEM_LAYER_DOUBLE) {
-        if (!fp64 && h->p2p_variant == 3 && h->p2p_items) {
-            k_pack_sources_dipole<<<(unsigned)((h->NS + 255) / 256), 256, 0, h->stream>>>(h->src_rel, h->nrm_d, h->xin,
-                                                                                         h->K, h->NS, h->src_w);
-            FMM_LAUNCHED();
-            FMM_TRY(launch_items(h));
-        } else {
-            rc = fp64 ? launch_p2p<double, LAP_DL>(h, h->corr_dl) : launch_p2p<float, LAP_DL>(h, h->corr_dl);
-        }
-        prof_end(h, FMMBEM_PASS_P2P, 1);
-        h->launches += 1;
-        return rc;
-    }
-    if (h->kernel == FMMBEM_LAPLACE && !fp64) {
-        k_pack_sources<<<(unsigned)((h->NS + 255) / 256), 256, 0, h->stream>>>(h->src_rel, h->xin, h->K, h->NS, h->src_w);
-        FMM_LAUNCHED();
-        if (h->p2p_variant == 3 && h->p2p_items) {
-            FMM_TRY(launch_items(h));
-            prof_end(h, FMMBEM_PASS_P2P, 2);
+        if (items) FMM_TRY(launch_items(h));
+        else {
+            FMM_TRY((fp64 ? launch_p2p<double, LAP_DL>(h, h->corr_dl) : launch_p2p<float, LAP_DL>(h, h->corr_dl)));
             h->launches += 1;
-            return 0;
         }
-        if (h->p2p_variant == 2 && h->stage_ptr) {
+    } else if (h->kernel == FMMBEM_LAPLACE && !fp64) {
+        if (items) {
+            FMM_TRY(launch_items(h));
+        } else if (h->p2p_variant == 2 && h->stage_ptr) {
             k_p2p_lap_bulk<<<h->n_leaves, 128, 0, h->stream>>>(
                 h->leaves, h->cell_range, h->p2p_ptr, h->p2p_src, h->p2p_rec, h->p2p_cnt, h->p2p_toff, h->stage_ptr,
                 h->stage_first, h->stage_bytes, h->src_w, h->tgt_rel, h->K, h->corr_ptr, h->corr_col, h->corr_sl,
                 h->xin, h->ynear, h->kerr);
             FMM_LAUNCHED();
             h->launches += 1;
-            prof_end(h, FMMBEM_PASS_P2P, 2);
-            h->launches += 1;
-            return 0;
-        }
-        if (h->p2p_variant == 1) {
+        } else if (h->p2p_variant == 1) {
             k_p2p_lap_sliced<<<h->n_leaves, 128, 0, h->stream>>>(h->leaves, h->cell_range, h->p2p_ptr, h->p2p_src,
                                                                 h->p2p_rec, h->src_w, h->tgt_rel, h->K, h->corr_ptr,
                                                                 h->corr_col, h->corr_sl, h->xin, h->ynear);
             FMM_LAUNCHED();
             h->launches += 1;
-            prof_end(h, FMMBEM_PASS_P2P, 2);
-            h->launches += 1;
-            return 0;
+        } else {
+            // leaves grouped by target count: <= 32, <= 64, more (targets per lane 1, 2, 4)
+            const int* cls = h->leaf_class;
+            const int n1 = h->leaf_class_start[1], n2 = h->leaf_class_start[2] - n1, n3 = h->n_leaves - n1 - n2;
+            if (n1 > 0)
+                k_p2p_lap<1><<<n1, 128, 0, h->stream>>>(cls, h->cell_range, h->p2p_ptr, h->p2p_rec, h->p2p_off,
+                                                        h->p2p_len, h->src_w, h->tgt_rel, h->K, h->corr_ptr,
+                                                        h->corr_col, h->corr_sl, h->xin, h->ynear);
+            if (n2 > 0)
+                k_p2p_lap<2><<<n2, 128, 0, h->stream>>>(cls + n1, h->cell_range, h->p2p_ptr, h->p2p_rec, h->p2p_off,
+                                                        h->p2p_len, h->src_w, h->tgt_rel, h->K, h->corr_ptr,
+                                                        h->corr_col, h->corr_sl, h->xin, h->ynear);
+            if (n3 > 0)
+                k_p2p_lap<4><<<n3, 128, 0, h->stream>>>(cls + n1 + n2, h->cell_range, h->p2p_ptr, h->p2p_rec,
+                                                        h->p2p_off, h->p2p_len, h->src_w, h->tgt_rel, h->K,
+                                                        h->corr_ptr, h->corr_col, h->corr_sl, h->xin, h->ynear);
+            FMM_LAUNCHED();
+            h->launches += (n1 > 0) + (n2 > 0) + (n3 > 0);
         }
-        // leaves grouped by target count: <= 32, <= 64, more (targets per lane 1, 2, 4)
-        const int* cls = h->leaf_class;
-        const int n1 = h->leaf_class_start[1], n2 = h->leaf_class_start[2] - n1, n3 = h->n_leaves - n1 - n2;
-        if (n1 > 0)
-            k_p2p_lap<1><<<n1, 128, 0, h->stream>>>(cls, h->cell_range, h->p2p_ptr, h->p2p_rec, h->p2p_off, h->p2p_len,
-                                                    h->src_w, h->tgt_rel, h->K, h->corr_ptr, h->corr_col, h->corr_sl,
-                                                    h->xin, h->ynear);
-        if (n2 > 0)
-            k_p2p_lap<2><<<n2, 128, 0, h->stream>>>(cls + n1, h->cell_range, h->p2p_ptr, h->p2p_rec, h->p2p_off,
-                                                    h->p2p_len, h->src_w, h->tgt_rel, h->K, h->corr_ptr, h->corr_col,
-                                                    h->corr_sl, h->xin, h->ynear);
-        if (n3 > 0)
-            k_p2p_lap<4><<<n3, 128, 0, h->stream>>>(cls + n1 + n2, h->cell_range, h->p2p_ptr, h->p2p_rec,
-                                                    h->p2p_off, h->p2p_len, h->src_w, h->tgt_rel, h->K, h->corr_ptr,
-                                                    h->corr_col, h->corr_sl, h->xin, h->ynear);
-        FMM_LAUNCHED();
-        h->launches += (n1 > 0) + (n2 > 0) + (n3 > 0);
-    } else if (h->kernel == FMMBEM_LAPLACE) rc = launch_p2p<double, LAP_SL>(h, h->corr_sl);
-    else if (!fp64 && h->p2p_variant == 3 && h->p2p_items) {
-        k_pack_sources_stokes<<<(unsigned)((h->NS + 255) / 256), 256, 0, h->stream>>>(h->src_rel, h->xin, h->K, h->NS,
-                                                                                     h->src_w);
-        FMM_LAUNCHED();
+    } else if (h->kernel == FMMBEM_LAPLACE) {
+        FMM_TRY((launch_p2p<double, LAP_SL>(h, h->corr_sl)));
+        h->launches += 1;
+    } else if (items) {
         FMM_TRY(launch_items(h));
-    } else rc = fp64 ? launch_p2p<double, STK_SL>(h, h->corr_sl) : launch_p2p<float, STK_SL>(h, h->corr_sl);
-    prof_end(h, FMMBEM_PASS_P2P, 1);
-    h->launches += 1;
-    return rc;
+    } else {
+        FMM_TRY((fp64 ? launch_p2p<double, STK_SL>(h, h->corr_sl) : launch_p2p<float, STK_SL>(h, h->corr_sl)));
+        h->launches += 1;
+    }
+    prof_end(h, FMMBEM_PASS_P2P, (int)(h->launches - l0));
+    return 0;
 }
 
 // which: 0 single layer (scale of the operator), 1 double layer / stresslet.

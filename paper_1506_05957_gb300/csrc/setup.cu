@@ -190,14 +190,16 @@ __global__ void k_morton(const double4* cen, int64_t n, double lox, double loy, 
 // Sorted-order copies: centroids, normals, vertices and the K Gauss points of each panel.
 __global__ void k_gather_sorted(const int* perm, int64_t n, const double* v, const int* tri, const double4* cen,
                                 const double4* nrm, const double* quad, int K, double4* tgt_d, float4* tgt_f,
-                                double4* nrm_d, double* verts, double4* src_d, float4* src_f) {
+                                double4* nrm_d, float4* nrm_f, double* verts, double4* src_d, float4* src_f) {
     int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (s >= n) return;
     int i = perm[s];
     double4 c = cen[i];
     tgt_d[s] = c;
     tgt_f[s] = make_float4((float)c.x, (float)c.y, (float)c.z, (float)c.w);
-    nrm_d[s] = nrm[i];
+    const double4 nv = nrm[i];
+    nrm_d[s] = nv;
+    nrm_f[s] = make_float4((float)nv.x, (float)nv.y, (float)nv.z, (float)nv.w);
     double P[3][3];
     for (int a = 0; a < 3; ++a)
         for (int d = 0; d < 3; ++d) {
@@ -716,11 +718,12 @@ int build_geometry_tree_lists(fmmbem_handle* h, const fmmbem_mesh* mesh) {
     FMM_TRY(dalloc(&h->tgt_d, n));
     FMM_TRY(dalloc(&h->tgt_f, n));
     FMM_TRY(dalloc(&h->nrm_d, n));
+    FMM_TRY(dalloc(&h->nrm_f, n));
     FMM_TRY(dalloc(&h->verts, 9 * n));
     FMM_TRY(dalloc(&h->src_d, h->NS));
     FMM_TRY(dalloc(&h->src_f, h->NS));
-    k_gather_sorted<<<gn, T, 0, st>>>(h->perm, n, dv, dt, cen, nrm, quad, K, h->tgt_d, h->tgt_f, h->nrm_d, h->verts,
-                                      h->src_d, h->src_f);
+    k_gather_sorted<<<gn, T, 0, st>>>(h->perm, n, dv, dt, cen, nrm, quad, K, h->tgt_d, h->tgt_f, h->nrm_d, h->nrm_f,
+                                      h->verts, h->src_d, h->src_f);
     FMM_LAUNCHED();
 
     // ---- octree, level by level
