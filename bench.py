@@ -43,10 +43,11 @@ def parse():
     ap.add_argument("--levels", type=int, default=6)
     ap.add_argument("--ncrit", type=int, default=WORKLOAD["ncrit"])
     ap.add_argument("--no-compare", action="store_true", help="skip the FP64 comparison solves")
-    ap.add_argument("--problem", default="laplace", choices=["laplace", "stokes", "serve", "laplace2"],
+    ap.add_argument("--problem", default="laplace", choices=["laplace", "stokes", "serve", "laplace2", "sweeps"],
                     help="laplace: the headline workload; stokes: Stokes flow past a sphere of 81920 panels; "
                          "serve: a Poisson stream of mixed solves through the serving runtime; "
-                         "laplace2: second-kind Laplace solves on octahedron spheres of 8192-131072 panels")
+                         "laplace2: second-kind Laplace solves on octahedron spheres of 8192-131072 panels; "
+                         "sweeps: the paper's parameter studies (initial p, tolerance, p_min, red blood cell)")
     ap.add_argument("--requests", type=int, default=48, help="serve: number of requests")
     ap.add_argument("--rate", type=float, default=20.0, help="serve: mean arrival rate (requests/s)")
     ap.add_argument("--max-active", type=int, default=6, help="serve: concurrent solves")
@@ -563,6 +564,129 @@ def run_laplace2(args, world, rank, local):
         print(json.dumps(out), flush=True)
 
 
+def run_sweeps(args, world, rank, local):
+    """The paper's parameter studies on the GPU (its Tables laplace_1st_p_relaxation,
+    laplace_1st_tolerance_relaxation, stokes_min_p, rbc_richardson_values and
+    single_cell_relaxation_results), relaxed against non-relaxed GMRES on the same handle:
+      - initial p 5-15, Laplace first kind, 32768-panel sphere, 10 GMRES iterations;
+      - tolerance 1e-5 .. 1e-11, Laplace first kind, 8192-panel sphere, initial p 10;
+      - p_min 5 .. 1, Stokes sphere of 2048, 8192, 32768 panels, initial p 16, tol 1e-5:
+        drag error against 6 pi mu R and iterations;
+      - Richardson study of the drag on one red blood cell of 512, 2048, 8192 panels;
+      - one red blood cell of 2048-131072 panels, relaxed against fixed p = 16.
+    Spheres are refined octahedra (8 4^L panels), as in the paper. Times are per solve."""
+    import math
+    import torch
+    from synth import octasphere, evans_fung_cell
+    from paper_1506_05957_gb300 import FmmBem, FMMBEM_FP64, FMMBEM_MIXED, FMMBEM_STOKES, build
+    build.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def timed(h, b, x, reps, **kw):
+        h.solve(b, x, **kw)  # graphs captured outside the timing
+        ts, r = [], None
+        for k in range(reps):
+            flush.fill_(float(k))
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            x.zero_()
+            e0.record(stream)
+            r = h.solve(b, x, **kw)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            ts.append(e0.elapsed_time(e1))
+        return float(np.median(ts)), r
+
+    def laplace(level, precision, max_iter=100):
+        v, t = octasphere(level)
+        c = v[t].mean(axis=1)
+        d = c - np.array([0.0, 0.0, 3.0])
+        phi = 1.0 / (4.0 * np.pi * np.sqrt((d * d).sum(1)))
+        h = FmmBem(v, t, gauss_k=4, ncrit=args.ncrit, theta=0.5, p_max=16, restart=50, max_iter=max_iter,
+                   precision=precision, stream=stream.cuda_stream)
+        b = torch.empty(len(t), dtype=torch.float64, device=dev)
+        h.rhs(torch.tensor(phi, dtype=torch.float64, device=dev), b)
+        return h, b
+
+    out = {"metric": "paper parameter studies, relaxed vs non-relaxed GMRES solve ms", "n_gpus": world,
+           "data": "synthetic", "unit": "ms"}
+    # initial p, 10 iterations
+    h, b = laplace(6, FMMBEM_MIXED, max_iter=10)
+    x = torch.zeros_like(b)
+    rows = []
+    for p in (5, 8, 10, 12, 15):
+        t_rel, r_rel = timed(h, b, x, 5, tol=1e-6, relax=True, p_initial=p, p_min=3)
+        t_fix, r_fix = timed(h, b, x, 5, tol=1e-6, relax=False, p_initial=p, p_min=3)
+        rows.append({"p_initial": p, "relaxed_ms": round(t_rel, 3), "fixed_ms": round(t_fix, 3),
+                     "speedup": round(t_fix / t_rel, 3), "iters": r_rel["iters"], "p_hist": r_rel["p_hist"]})
+    h.close()
+    out["initial_p_32768_10_iterations"] = {"rows": rows, "paper_speedups_cpu": [1.91, 2.00, 2.20, 2.00, 1.71]}
+    # tolerance
+    rows = []
+    for prec, name in ((FMMBEM_MIXED, "mixed"), (FMMBEM_FP64, "fp64")):
+        h, b = laplace(5, prec)
+        x = torch.zeros_like(b)
+        for tol in (1e-5, 1e-6, 1e-7, 1e-8, 1e-9, 1e-10, 1e-11):
+            if prec == FMMBEM_MIXED and tol < 1e-6:
+                continue  # the mixed mat-vec resolves about 1e-6
+            reps = 5 if prec == FMMBEM_MIXED else 2
+            t_rel, r_rel = timed(h, b, x, reps, tol=tol, relax=True, p_initial=10, p_min=3)
+            t_fix, r_fix = timed(h, b, x, reps, tol=tol, relax=False, p_initial=10, p_min=3)
+            rows.append({"precision": name, "tol": tol, "relaxed_ms": round(t_rel, 3), "fixed_ms": round(t_fix, 3),
+                         "speedup": round(t_fix / t_rel, 3), "iters_relaxed": r_rel["iters"],
+                         "iters_fixed": r_fix["iters"], "true_res": r_rel["true_res"]})
+        h.close()
+    out["tolerance_8192_p10"] = {"rows": rows,
+                                 "paper_speedups_cpu": [1.90, 2.01, 1.95, 1.71, 1.54, 1.61, 1.46]}
+    # p_min, Stokes sphere, mu = 1e-3: drag 6 pi mu R = 0.01885
+    mu = 1e-3
+    exact = 6.0 * np.pi * mu
+    rows = []
+    for level in (4, 5, 6):
+        v, t = octasphere(level)
+        p3 = v[t]
+        area = 0.5 * np.linalg.norm(np.cross(p3[:, 1] - p3[:, 0], p3[:, 2] - p3[:, 0]), axis=1)
+        h = FmmBem(v, t, kernel=FMMBEM_STOKES, gauss_k=3, ncrit=args.ncrit, theta=0.5, p_max=16, mu=mu,
+                   restart=50, max_iter=100, precision=FMMBEM_MIXED, stream=stream.cuda_stream)
+        b = torch.tensor(np.tile([1.0, 0.0, 0.0], len(t)), dtype=torch.float64, device=dev)
+        x = torch.zeros_like(b)
+        for pmin in (5, 4, 3, 2, 1):
+            tm, r = timed(h, b, x, 2, tol=1e-5, relax=True, p_initial=16, p_min=pmin)
+            drag = float(np.sum(x.cpu().numpy().reshape(-1, 3)[:, 0] * area))
+            rows.append({"panels": len(t), "p_min": pmin, "drag_error": abs(abs(drag) - exact) / exact,
+                         "iters": r["iters"], "converged": r["converged"], "ms": round(tm, 3)})
+        h.close()
+    out["stokes_pmin"] = {"rows": rows, "exact_drag": exact}
+    # red blood cell: Richardson study (512, 2048, 8192 panels) and relaxation speed-ups
+    drags, rows = [], []
+    for level in (3, 4, 5, 6, 7):
+        v, t = evans_fung_cell(level)
+        p3 = v[t]
+        area = 0.5 * np.linalg.norm(np.cross(p3[:, 1] - p3[:, 0], p3[:, 2] - p3[:, 0]), axis=1)
+        h = FmmBem(v, t, kernel=FMMBEM_STOKES, gauss_k=3, ncrit=args.ncrit, theta=0.5, p_max=16, mu=mu,
+                   restart=50, max_iter=100, precision=FMMBEM_MIXED, stream=stream.cuda_stream)
+        b = torch.tensor(np.tile([1.0, 0.0, 0.0], len(t)), dtype=torch.float64, device=dev)
+        x = torch.zeros_like(b)
+        t_rel, r_rel = timed(h, b, x, 2, tol=1e-5, relax=True, p_initial=16, p_min=5)
+        drags.append(float(np.sum(x.cpu().numpy().reshape(-1, 3)[:, 0] * area)))
+        if level >= 4:
+            t_fix, r_fix = timed(h, b, x, 2, tol=1e-5, relax=False, p_initial=16, p_min=5)
+            rows.append({"panels": len(t), "relaxed_ms": round(t_rel, 3), "fixed_ms": round(t_fix, 3),
+                         "speedup": round(t_fix / t_rel, 3), "iters_relaxed": r_rel["iters"],
+                         "iters_fixed": r_fix["iters"]})
+        h.close()
+    f1, f2, f3 = drags[:3]
+    out["rbc_richardson"] = {"panels": [512, 2048, 8192], "drag": [f1, f2, f3],
+                             "extrapolated": (f1 * f3 - f2 * f2) / (f1 - 2.0 * f2 + f3),
+                             "observed_order": math.log((f2 - f1) / (f3 - f2)) / math.log(4.0),
+                             "paper_observed_order": 0.52}
+    out["rbc_single_cell"] = {"rows": rows, "paper_speedups_cpu": [3.30, 3.40, 3.54, 4.90]}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
 def serve_requests(n, seed=0):
     """Mixed solve requests: Laplace or Stokes on spheres (1280-81920 panels), ellipsoids
     (semi-axes U[0.5, 2]) or clusters of 1-16 red-blood-cell surfaces (2048 panels each),
@@ -655,6 +779,8 @@ def main():
         run_serve(args, world, rank, local)
     elif args.problem == "laplace2":
         run_laplace2(args, world, rank, local)
+    elif args.problem == "sweeps":
+        run_sweeps(args, world, rank, local)
     else:
         run_ours(args, world, rank, local)
     if world > 1:

@@ -91,7 +91,7 @@ __global__ void k_sub(double* r, const double* b, const double* ax, int64_t n) {
 // flags an error and stops. Each block reduces the per-block partial dots itself in a
 // fixed order (results are deterministic); block 0 writes h1, h2 and ||w||^2 to out
 // (mapped pinned host memory).
-constexpr int ARN_THREADS = 256;
+constexpr int ARN_THREADS = 512;
 constexpr int ARN_MAXV = 64;
 
 __device__ __forceinline__ bool grid_barrier(unsigned* count, volatile unsigned* gen, unsigned nb, int* err) {
@@ -127,25 +127,37 @@ __device__ __forceinline__ bool grid_barrier(unsigned* count, volatile unsigned*
 // flight per lane), then one five-level shuffle reduction per vector. With with_self the
 // vector after the last V_j is w itself (entry nv is w.w), so ||w||^2 comes from the same
 // sweep. Fixed summation order: deterministic.
+// When the block has more warps than vectors, each vector's rows are cut into ns slices
+// (one warp each) and partial holds one entry per slice: partial[(j * ns + slice) * gridDim.x
+// + block]; arn_reduce sums over slices and blocks.
+__device__ __forceinline__ int arn_slices(int nt) {
+    const int nw = (int)(blockDim.x >> 5);
+    return nw > nt ? nw / nt : 1;
+}
+
 __device__ void arn_partials(const double* V, int64_t ldv, int nv, const double* w, int64_t i0, int64_t i1,
                              double* partial, bool with_self = false) {
     const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5, nw = (int)(blockDim.x >> 5);
     const int nt = nv + (with_self ? 1 : 0);
-    for (int j = wp; j < nt; j += nw) {
+    const int ns = arn_slices(nt);
+    const int64_t len = (i1 - i0 + ns - 1) / ns;
+    for (int item = wp; item < nt * ns; item += nw) {
+        const int j = item / ns, sl = item - j * ns;
         const double* vj = j < nv ? V + (int64_t)j * ldv : w;
+        const int64_t a = i0 + sl * len, e = min(i1, a + len);
         double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
-        int64_t i = i0 + lane;
-        for (; i + 96 < i1; i += 128) {
+        int64_t i = a + lane;
+        for (; i + 96 < e; i += 128) {
             s0 = fma(vj[i], w[i], s0);
             s1 = fma(vj[i + 32], w[i + 32], s1);
             s2 = fma(vj[i + 64], w[i + 64], s2);
             s3 = fma(vj[i + 96], w[i + 96], s3);
         }
-        for (; i < i1; i += 32) s0 = fma(vj[i], w[i], s0);
+        for (; i < e; i += 32) s0 = fma(vj[i], w[i], s0);
         double t = (s0 + s1) + (s2 + s3);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-        if (lane == 0) partial[(int64_t)j * gridDim.x + blockIdx.x] = t;
+        if (lane == 0) partial[(int64_t)item * gridDim.x + blockIdx.x] = t;
     }
 }
 
@@ -153,9 +165,11 @@ __device__ void arn_partials(const double* V, int64_t ldv, int nv, const double*
 // the same hs. With sq != nullptr, *sq = sum_{j < nsq} hs[j]^2, by one warp.
 __device__ void arn_reduce(const double* partial, int nv, double* hs, int nsq = 0, double* sq = nullptr) {
     const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+    const int ns = arn_slices(nv);
+    const int nb = (int)gridDim.x * ns;  // a vector's entries are contiguous: slices x blocks
     for (int j = wp; j < nv; j += (int)(blockDim.x >> 5)) {
         double t = 0.0;
-        for (int b = lane; b < (int)gridDim.x; b += 32) t += partial[(int64_t)j * gridDim.x + b];
+        for (int b = lane; b < nb; b += 32) t += partial[(int64_t)j * nb + b];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
         if (lane == 0) hs[j] = t;
@@ -308,8 +322,7 @@ int arnoldi_blocks() {
                  // the grid barriers dearer than the extra loads in flight gain)
 }
 
-// Threads per Arnoldi block. Blocks sized to hold one row per thread (640 threads at 81920
-// unknowns) measured slower than 256 threads looping over two or three rows each.
+// Threads per Arnoldi block (one block per SM).
 int arnoldi_threads(int64_t, int) { return ARN_THREADS; }
 
 int relaxed_p(double eta, double rho_prev, int p_initial, int p_min) {
