@@ -43,11 +43,13 @@ def parse():
     ap.add_argument("--levels", type=int, default=6)
     ap.add_argument("--ncrit", type=int, default=WORKLOAD["ncrit"])
     ap.add_argument("--no-compare", action="store_true", help="skip the FP64 comparison solves")
-    ap.add_argument("--problem", default="laplace", choices=["laplace", "stokes", "serve", "laplace2", "sweeps"],
+    ap.add_argument("--problem", default="laplace",
+                    choices=["laplace", "stokes", "serve", "laplace2", "sweeps", "batch"],
                     help="laplace: the headline workload; stokes: Stokes flow past a sphere of 81920 panels; "
                          "serve: a Poisson stream of mixed solves through the serving runtime; "
                          "laplace2: second-kind Laplace solves on octahedron spheres of 8192-131072 panels; "
-                         "sweeps: the paper's parameter studies (initial p, tolerance, p_min, red blood cell)")
+                         "sweeps: the paper's parameter studies (initial p, tolerance, p_min, red blood cell); "
+                         "batch: four right-hand sides in one batched solve against four single solves")
     ap.add_argument("--requests", type=int, default=48, help="serve: number of requests")
     ap.add_argument("--rate", type=float, default=20.0, help="serve: mean arrival rate (requests/s)")
     ap.add_argument("--max-active", type=int, default=6, help="serve: concurrent solves")
@@ -687,6 +689,81 @@ def run_sweeps(args, world, rank, local):
         print(json.dumps(out), flush=True)
 
 
+def run_batch(args, world, rank, local):
+    """Four right-hand sides on the headline sphere (81920 panels): one batched handle
+    (fmmbem_solve_batch, four vectors per mat-vec) against four solves on a single-vector
+    handle. The right-hand sides are the first-kind data of unit charges at four positions
+    outside the sphere. value = seconds per right-hand side of the batched solve."""
+    import torch
+    from synth import icosphere
+    from paper_1506_05957_gb300 import FmmBem, FMMBEM_MIXED, build
+    build.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    W = WORKLOAD
+    v, t = icosphere(args.levels)
+    n = len(t)
+    c = v[t].mean(axis=1)
+    single = FmmBem(v, t, gauss_k=W["gauss_k"], ncrit=args.ncrit, theta=W["theta"], p_max=16, restart=W["restart"],
+                    max_iter=100, precision=FMMBEM_MIXED, stream=stream.cuda_stream)
+    batch = FmmBem(v, t, gauss_k=W["gauss_k"], ncrit=args.ncrit, theta=W["theta"], p_max=16, restart=W["restart"],
+                   max_iter=100, precision=FMMBEM_MIXED, stream=stream.cuda_stream, nrhs=4)
+    B = torch.empty(4 * n, dtype=torch.float64, device=dev)
+    for q, z0 in enumerate(((0.0, 0.0, 3.0), (2.5, 0.5, 0.0), (-0.3, -2.2, 1.1), (1.2, 1.2, -2.0))):
+        d = c - np.asarray(z0)
+        phi = torch.tensor(1.0 / (4.0 * np.pi * np.sqrt((d * d).sum(1))), dtype=torch.float64, device=dev)
+        single.rhs(phi, B[q * n:(q + 1) * n])
+    X = torch.zeros_like(B)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    kw = dict(tol=W["tol"], relax=True, p_initial=W["p_initial"], p_min=W["p_min"])
+
+    def run_batch_solve():
+        return batch.solve_batch(B, X, **kw)
+
+    def run_singles():
+        rs = []
+        for q in range(4):
+            rs.append(single.solve(B[q * n:(q + 1) * n], X[q * n:(q + 1) * n], **kw))
+        return rs
+
+    for _ in range(args.warmup):
+        run_batch_solve()
+        run_singles()
+    torch.cuda.synchronize(dev)
+    sampler = ClockSampler(local)
+    sampler.start()
+    tb, ts = [], []
+    for k in range(args.steps):
+        for fn, acc in ((run_batch_solve, tb), (run_singles, ts)):
+            flush.fill_(float(k))
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            r = fn()
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            acc.append(e0.elapsed_time(e1))
+            if fn is run_batch_solve:
+                rb = r
+            else:
+                rsg = r
+    clocks = sampler.stop()
+    t_b = float(np.median(tb)) / 1e3
+    t_s = float(np.median(ts)) / 1e3
+    out = {"metric": "relaxed GMRES solve s per right-hand side, 4 right-hand sides batched (81920-panel sphere)",
+           "value": t_b / 4.0, "unit": "s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+           "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+           "data": "synthetic", "config": dict(W, workload="laplace-sphere-ico6-81920-batch4", ncrit=args.ncrit,
+                                               rhs="unit charges at four outside points"),
+           "batched_s": t_b, "four_single_solves_s": t_s, "throughput_gain": t_s / t_b,
+           "iters_batched": rb["iters"], "iters_single": [r_["iters"] for r_ in rsg],
+           "p_hist_batched": rb["p_hist"], "true_res_batched": rb["true_res"], "clocks": clocks}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    single.close()
+    batch.close()
+
+
 def serve_requests(n, seed=0):
     """Mixed solve requests: Laplace or Stokes on spheres (1280-81920 panels), ellipsoids
     (semi-axes U[0.5, 2]) or clusters of 1-16 red-blood-cell surfaces (2048 panels each),
@@ -781,6 +858,8 @@ def main():
         run_laplace2(args, world, rank, local)
     elif args.problem == "sweeps":
         run_sweeps(args, world, rank, local)
+    elif args.problem == "batch":
+        run_batch(args, world, rank, local)
     else:
         run_ours(args, world, rank, local)
     if world > 1:

@@ -83,7 +83,12 @@ typedef struct {
     void* stream;         /* NULL: the legacy default stream; else a cudaStream_t for all work;
                              it must stay valid until fmmbem_destroy returns (the handle's
                              device memory is stream-ordered and is released on it) */
+    int nrhs;             /* 1: one vector per mat-vec. FMMBEM_BATCH (Laplace single layer only):
+                             every mat-vec and solve of the handle takes FMMBEM_BATCH vectors
+                             at once, laid out [FMMBEM_BATCH][n_panels] (see fmmbem_solve_batch) */
 } fmmbem_opts;
+
+#define FMMBEM_BATCH 4
 
 typedef struct fmmbem_handle fmmbem_handle;
 
@@ -172,8 +177,8 @@ int fmmbem_set_layer(fmmbem_handle* h, int layer);
  * far field by P2M, M2M, M2L, L2L, L2P and the near field by P2P plus the
  * precomputed corrections).
  *   p      : 1 <= p <= opts.p_max
- *   x_dev  : [n_unknowns] doubles, device
- *   y_dev  : [n_unknowns] doubles, device (must not alias x_dev)
+ *   x_dev  : [n_unknowns] doubles, device ([FMMBEM_BATCH][n_unknowns] on a batched handle)
+ *   y_dev  : as x_dev (must not alias x_dev)
  * Asynchronous on the handle's stream. Errors: FMMBEM_EINVAL, FMMBEM_EDEVICE.
  */
 int fmmbem_matvec(fmmbem_handle* h, int p, const double* x_dev, double* y_dev);
@@ -241,6 +246,25 @@ int fmmbem_solve(fmmbem_handle* h, const double* rhs_dev, double tol, int relax,
 int fmmbem_solve_host(fmmbem_handle* h, const double* rhs_host, double tol, int relax,
                       int p_initial, int p_min, double* x_host, int* iters, int* p_hist,
                       double* res_hist, double* true_res);
+
+/*
+ * Relaxed GMRES for the FMMBEM_BATCH systems A x_q = b_q of a batched handle (opts.nrhs =
+ * FMMBEM_BATCH, Laplace single layer), in lockstep: every mat-vec evaluates all systems'
+ * basis vectors together (one P2M, M2M, M2L, L2L, L2P and P2P pass over four expansions
+ * and four strengths per Gauss point) at the largest order p_k any active system's
+ * relaxation rule (Sec. 2.6) asks for; each system keeps its own residual, Hessenberg
+ * matrix and restarts and leaves the lockstep when it converges.
+ *   rhs_dev, x_dev : [FMMBEM_BATCH][n_panels] doubles, device
+ *   iters          : [FMMBEM_BATCH] host, mat-vecs while each system was active (or NULL)
+ *   p_hist         : [max_iter] host, the order of each batched mat-vec (or NULL)
+ *   res_hist       : [FMMBEM_BATCH][max_iter + 1] host (or NULL)
+ *   true_res       : [FMMBEM_BATCH] host, ||b - A x|| / ||b|| at p_initial (or NULL)
+ * Returns 0 when every system converged, FMMBEM_NOT_CONVERGED otherwise, FMMBEM_ESTATE on a
+ * handle that is not batched (and fmmbem_solve returns FMMBEM_ESTATE on a batched one).
+ */
+int fmmbem_solve_batch(fmmbem_handle* h, const double* rhs_dev, double tol, int relax, int p_initial,
+                       int p_min, double* x_dev, int* iters, int* p_hist, double* res_hist,
+                       double* true_res);
 
 /*
  * Single expansions (Sec. 2.5, spherical-harmonic forms of M_n^m and L_n^m):

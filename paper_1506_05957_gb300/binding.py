@@ -41,7 +41,7 @@ class fmmbem_mesh(ctypes.Structure):
 class fmmbem_opts(ctypes.Structure):
     _fields_ = [("p_max", ctypes.c_int), ("near_factor", ctypes.c_double), ("mu", ctypes.c_double),
                 ("precision", ctypes.c_int), ("restart", ctypes.c_int), ("max_iter", ctypes.c_int),
-                ("stream", ctypes.c_void_p)]
+                ("stream", ctypes.c_void_p), ("nrhs", ctypes.c_int)]
 
 
 class fmmbem_stats(ctypes.Structure):
@@ -87,6 +87,8 @@ def lib():
         L.fmmbem_set_m2l_mode.argtypes = [_vp, ctypes.c_int]
         L.fmmbem_set_p2p_variant.argtypes = [_vp, ctypes.c_int]
         L.fmmbem_set_layer.argtypes = [_vp, ctypes.c_int]
+        L.fmmbem_solve_batch.argtypes = [_vp, _vp, ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, _vp,
+                                         _vp, _vp, _vp]
         L.fmmbem_set_tc_thresholds.argtypes = [_vp, ctypes.c_int, ctypes.c_int]
         L.fmmbem_estimate_bytes.argtypes = [ctypes.c_int64, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                             ctypes.POINTER(fmmbem_opts)]
@@ -174,13 +176,14 @@ class FmmBem:
     """One resident BEM problem: fmmbem_create ... fmmbem_destroy."""
 
     def __init__(self, vertices, triangles, kernel=FMMBEM_LAPLACE, gauss_k=4, ncrit=150, theta=0.5, p_max=16,
-                 near_factor=2.0, mu=1.0, precision=FMMBEM_MIXED, restart=50, max_iter=100, stream=None):
+                 near_factor=2.0, mu=1.0, precision=FMMBEM_MIXED, restart=50, max_iter=100, stream=None, nrhs=1):
         v = np.ascontiguousarray(vertices, dtype=np.float64)
         t = np.ascontiguousarray(triangles, dtype=np.int32)
         mesh = fmmbem_mesh(len(v), v.ctypes.data_as(_dp), len(t), t.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)))
         o = fmmbem_default_opts()
         o.p_max, o.near_factor, o.mu, o.precision = p_max, near_factor, mu, precision
         o.restart, o.max_iter = restart, max_iter
+        o.nrhs = nrhs
         if stream is None:
             import torch
             stream = torch.cuda.current_stream().cuda_stream
@@ -191,7 +194,8 @@ class FmmBem:
         self.h = h
         self.kernel = kernel
         self.max_iter = max_iter
-        self.n = int(lib().fmmbem_n_unknowns(h))
+        self.nrhs = int(nrhs)
+        self.n = int(lib().fmmbem_n_unknowns(h)) * self.nrhs  # doubles per mat-vec vector (all of a batch)
         self.n_panels = len(t)
 
     def close(self):
@@ -225,7 +229,8 @@ class FmmBem:
         _check(lib().fmmbem_matvec_direct(self.h, _dev(x, self.n), _dev(y, self.n)))
 
     def rhs(self, known, b):
-        _check(lib().fmmbem_rhs(self.h, _dev(known, self.n_panels), _dev(b, self.n_panels)))
+        m = self.n_panels * self.nrhs
+        _check(lib().fmmbem_rhs(self.h, _dev(known, m), _dev(b, m)))
 
     def stokes_dl_apply(self, u, y):
         _check(lib().fmmbem_stokes_dl_apply(self.h, _dev(u, self.n), _dev(y, self.n)))
@@ -240,6 +245,20 @@ class FmmBem:
         k = it.value
         return dict(converged=(rc == 0), iters=k, p_hist=ph[:k].tolist(), res_hist=rh[:k + 1].tolist(),
                     true_res=tr.value)
+
+    def solve_batch(self, b, x, tol=1e-6, relax=True, p_initial=10, p_min=3):
+        """fmmbem_solve_batch: b, x are [nrhs * n_panels] device tensors (vector q at q * n_panels)."""
+        nb = self.nrhs
+        it = np.zeros(nb, dtype=np.int32)
+        ph = np.zeros(self.max_iter + 1, dtype=np.int32)
+        rh = np.zeros(nb * (self.max_iter + 1), dtype=np.float64)
+        tr = np.zeros(nb, dtype=np.float64)
+        rc = _check(lib().fmmbem_solve_batch(self.h, _dev(b, self.n), float(tol), int(bool(relax)), int(p_initial),
+                                             int(p_min), _dev(x, self.n), _vp(it.ctypes.data), _vp(ph.ctypes.data),
+                                             _vp(rh.ctypes.data), _vp(tr.ctypes.data)))
+        return dict(converged=(rc == 0), iters=it.tolist(), p_hist=ph[:int(it.max())].tolist(),
+                    res_hist=[rh[q * (self.max_iter + 1):q * (self.max_iter + 1) + it[q] + 1].tolist()
+                              for q in range(nb)], true_res=tr.tolist())
 
     def solve(self, b, x, tol=1e-6, relax=True, p_initial=10, p_min=3):
         return self._solve(lib().fmmbem_solve, _dev(b, self.n), _dev(x, self.n), tol, relax, p_initial, p_min)

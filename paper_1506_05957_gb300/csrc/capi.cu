@@ -29,18 +29,21 @@ namespace fmmbem {
 
 namespace {
 
+// Caller order <-> Morton-sorted order; blockIdx.y selects the vector of a batch ([nrhs][n][dof]).
 __global__ void k_perm_in(const double* x, const int* perm, int64_t n, int dof, double* xs) {
     int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (s >= n) return;
+    const int64_t off = (int64_t)blockIdx.y * n * dof;
     const int64_t i = perm[s];
-    for (int a = 0; a < dof; ++a) xs[dof * s + a] = x[dof * i + a];
+    for (int a = 0; a < dof; ++a) xs[off + dof * s + a] = x[off + dof * i + a];
 }
 
 __global__ void k_perm_out(const double* ys, const int* perm, int64_t n, int dof, double* y) {
     int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (s >= n) return;
+    const int64_t off = (int64_t)blockIdx.y * n * dof;
     const int64_t i = perm[s];
-    for (int a = 0; a < dof; ++a) y[dof * i + a] = ys[dof * s + a];
+    for (int a = 0; a < dof; ++a) y[off + dof * i + a] = ys[off + dof * s + a];
 }
 
 __global__ void k_axpy_half(double* y, const double* x, int64_t n) {
@@ -68,7 +71,7 @@ double operator_scale(const fmmbem_handle* h) {
 
 int perm_in(fmmbem_handle* h, const double* x, double* xs) {
     const int64_t n = h->N;
-    k_perm_in<<<(unsigned)((n + 255) / 256), 256, 0, h->stream>>>(x, h->perm, n, h->dof, xs);
+    k_perm_in<<<dim3((unsigned)((n + 255) / 256), h->nrhs), 256, 0, h->stream>>>(x, h->perm, n, h->dof, xs);
     FMM_LAUNCHED();
     h->launches += 1;
     return 0;
@@ -76,7 +79,7 @@ int perm_in(fmmbem_handle* h, const double* x, double* xs) {
 
 int perm_out(fmmbem_handle* h, const double* ys, double* y) {
     const int64_t n = h->N;
-    k_perm_out<<<(unsigned)((n + 255) / 256), 256, 0, h->stream>>>(ys, h->perm, n, h->dof, y);
+    k_perm_out<<<dim3((unsigned)((n + 255) / 256), h->nrhs), 256, 0, h->stream>>>(ys, h->perm, n, h->dof, y);
     FMM_LAUNCHED();
     h->launches += 1;
     return 0;
@@ -273,6 +276,7 @@ int fmmbem_default_opts(fmmbem_opts* o) {
     o->restart = 50;
     o->max_iter = 100;
     o->stream = nullptr;
+    o->nrhs = 1;
     return 0;
 }
 
@@ -293,8 +297,8 @@ void fmmbem_destroy(fmmbem_handle* h) {
                     h->xs, h->ys, h->ynear, h->m2l_pt, h->m2l_ps, h->m2l_refl, h->sign_f, h->sign_d, h->m2l_tiles, h->tab_d, h->tab_f, h->tab_tc, h->m2l_tiles_tc, h->tc_src_info, h->tc_dst_info, h->tree_tab_tc, h->tree_tiles, h->tree_info, h->tc_err, h->kerr, h->V, h->kw, h->xfix, h->kb, h->kx, h->kr, h->kpart, h->kh, h->kyv, h->arn_bar};
     for (void* b : bufs)
         if (b) fmm_free(b);
-    pinned_put(h->kh_host, sizeof(double) * 3 * (h->kr_m + 2));
-    pinned_put(h->arn_out_host, sizeof(double) * (2 * 65 + 1));
+    pinned_put(h->kh_host, sizeof(double) * 3 * (h->kr_m + 2) * h->nrhs);
+    pinned_put(h->arn_out_host, sizeof(double) * (2 * 65 + 1) * h->nrhs);
     for (int q = 0; q <= FMMBEM_P_MAX; ++q) {
         if (h->mv_graph[q]) cudaGraphExecDestroy(h->mv_graph[q]);
         for (int e = 0; e < 2 * FMMBEM_N_PASSES; ++e)
@@ -332,6 +336,8 @@ int fmmbem_create(const fmmbem_mesh* mesh, int kernel, int gauss_k, int ncrit, d
     if (!(o.near_factor >= 0.0)) { fmmbem_set_error("near_factor < 0"); return FMMBEM_EINVAL; }
     if (!(o.mu > 0.0)) { fmmbem_set_error("mu must be > 0"); return FMMBEM_EINVAL; }
     if (o.precision != FMMBEM_FP64 && o.precision != FMMBEM_MIXED) { fmmbem_set_error("bad precision"); return FMMBEM_EINVAL; }
+    if (o.nrhs != 1 && o.nrhs != FMMBEM_BATCH) { fmmbem_set_error("nrhs must be 1 or %d", FMMBEM_BATCH); return FMMBEM_EINVAL; }
+    if (o.nrhs != 1 && kernel != FMMBEM_LAPLACE) { fmmbem_set_error("batched handles are Laplace only"); return FMMBEM_EINVAL; }
 
     fmmbem_handle* h = new fmmbem_handle();
     fmm_alloc_stream() = (cudaStream_t)o.stream;
@@ -349,7 +355,8 @@ int fmmbem_create(const fmmbem_mesh* mesh, int kernel, int gauss_k, int ncrit, d
     }
     h->kernel = kernel;
     h->dof = kernel == FMMBEM_STOKES ? 3 : 1;
-    h->ncomp = kernel == FMMBEM_STOKES ? 4 : 1;
+    h->nrhs = o.nrhs;
+    h->ncomp = kernel == FMMBEM_STOKES ? 4 : o.nrhs;
     h->K = gauss_k;
     h->ncrit = ncrit;
     h->theta = theta;
@@ -381,7 +388,8 @@ int fmmbem_create(const fmmbem_mesh* mesh, int kernel, int gauss_k, int ncrit, d
     if (rc < 0) return fail(rc);
     h->m2l_mode = h->m2l_tc_ready ? FMMBEM_M2L_TENSOR : (h->m2l_tables ? FMMBEM_M2L_TABLES : FMMBEM_M2L_GATHER);
     const size_t ex = (size_t)h->n_cells * h->ncomp * ESTRIDE;
-    const int64_t n = h->N * h->dof;
+    const int64_t n = h->N * h->dof * h->nrhs;  // every work vector holds the nrhs vectors of a batch
+    const int nb = h->nrhs;
     h->kr_m = o.restart;
     if ((rc = dalloc((double**)&h->M, ex)) < 0) return fail(rc);
     if ((rc = dalloc((double**)&h->L, ex)) < 0) return fail(rc);
@@ -399,17 +407,17 @@ int fmmbem_create(const fmmbem_mesh* mesh, int kernel, int gauss_k, int ncrit, d
     h->arn_blocks = arnoldi_blocks();
     if (h->arn_blocks < 1) { fmmbem_set_error("cooperative Arnoldi kernel cannot be resident"); return fail(FMMBEM_EDEVICE); }
     // partial dots: the fused Arnoldi step uses three areas of [64][blocks]; the restart dots [m+2][96]
-    if ((rc = dalloc(&h->kpart, std::max((size_t)96 * (o.restart + 2), (size_t)3 * 64 * h->arn_blocks))) < 0) return fail(rc);
-    if ((rc = dalloc(&h->arn_bar, 2)) < 0) return fail(rc);
-    if (cudaMemsetAsync(h->arn_bar, 0, 2 * sizeof(unsigned), h->stream) != cudaSuccess) return fail(FMMBEM_EDEVICE);
-    h->arn_out_host = reinterpret_cast<double*>(pinned_get(sizeof(double) * (2 * 65 + 1), cudaHostAllocMapped));
+    if ((rc = dalloc(&h->kpart, std::max((size_t)96 * (o.restart + 2), (size_t)3 * 64 * h->arn_blocks * nb))) < 0) return fail(rc);
+    if ((rc = dalloc(&h->arn_bar, 2 * nb)) < 0) return fail(rc);  // one barrier pair per system of a batch
+    if (cudaMemsetAsync(h->arn_bar, 0, 2 * nb * sizeof(unsigned), h->stream) != cudaSuccess) return fail(FMMBEM_EDEVICE);
+    h->arn_out_host = reinterpret_cast<double*>(pinned_get(sizeof(double) * (2 * 65 + 1) * nb, cudaHostAllocMapped));
     if (!h->arn_out_host || cudaHostGetDevicePointer((void**)&h->arn_out_dev, h->arn_out_host, 0) != cudaSuccess) {
         fmmbem_set_error("mapped pinned allocation failed");
         return fail(FMMBEM_ENOMEM);
     }
-    if ((rc = dalloc(&h->kh, (size_t)3 * (o.restart + 2))) < 0) return fail(rc);
-    if ((rc = dalloc(&h->kyv, (size_t)(o.restart + 2))) < 0) return fail(rc);
-    h->kh_host = reinterpret_cast<double*>(pinned_get(sizeof(double) * 3 * (o.restart + 2), cudaHostAllocDefault));
+    if ((rc = dalloc(&h->kh, (size_t)3 * (o.restart + 2) * nb)) < 0) return fail(rc);
+    if ((rc = dalloc(&h->kyv, (size_t)(o.restart + 2) * nb)) < 0) return fail(rc);
+    h->kh_host = reinterpret_cast<double*>(pinned_get(sizeof(double) * 3 * (o.restart + 2) * nb, cudaHostAllocDefault));
     if (!h->kh_host) {
         fmmbem_set_error("pinned allocation failed");
         return fail(FMMBEM_ENOMEM);
@@ -433,7 +441,7 @@ int fmmbem_set_precision(fmmbem_handle* h, int precision) {
 
 int fmmbem_set_layer(fmmbem_handle* h, int layer) {
     if (!h || (layer != FMMBEM_LAYER_SINGLE && layer != FMMBEM_LAYER_DOUBLE)) { fmmbem_set_error("bad layer"); return FMMBEM_EINVAL; }
-    if (layer == FMMBEM_LAYER_DOUBLE && h->kernel != FMMBEM_LAPLACE) {
+    if (layer == FMMBEM_LAYER_DOUBLE && (h->kernel != FMMBEM_LAPLACE || h->nrhs > 1)) {
         fmmbem_set_error("the double-layer operator is built for Laplace handles");
         return FMMBEM_ESTATE;
     }
@@ -483,7 +491,8 @@ int fmmbem_matvec_direct(fmmbem_handle* h, const double* x_dev, double* y_dev) {
         k_axpy_half<<<(unsigned)((h->N + 255) / 256), 256, 0, h->stream>>>(h->ys, h->xs, h->N);
         FMM_LAUNCHED();
     } else {
-        FMM_TRY(direct_field(h, h->precision == FMMBEM_FP64, 0, h->xs, h->ys));
+        for (int q = 0; q < h->nrhs; ++q)  // a batch: each vector in turn
+            FMM_TRY(direct_field(h, h->precision == FMMBEM_FP64, 0, h->xs + q * h->N * h->dof, h->ys + q * h->N * h->dof));
     }
     FMM_TRY(perm_out(h, h->ys, y_dev));
     return 0;
@@ -493,9 +502,11 @@ int fmmbem_rhs(fmmbem_handle* h, const double* known_dev, double* b_dev) {
     if (!h || !known_dev || !b_dev || known_dev == b_dev) { fmmbem_set_error("bad argument"); return FMMBEM_EINVAL; }
     if (h->kernel != FMMBEM_LAPLACE) { fmmbem_set_error("fmmbem_rhs needs a Laplace handle"); return FMMBEM_ESTATE; }
     FMM_TRY(perm_in(h, known_dev, h->xs));
-    FMM_TRY(direct_field(h, true, 1, h->xs, h->ys));
-    k_axpy_half<<<(unsigned)((h->N + 255) / 256), 256, 0, h->stream>>>(h->ys, h->xs, h->N);
-    FMM_LAUNCHED();
+    for (int q = 0; q < h->nrhs; ++q) {  // a batch: each vector in turn
+        FMM_TRY(direct_field(h, true, 1, h->xs + q * h->N, h->ys + q * h->N));
+        k_axpy_half<<<(unsigned)((h->N + 255) / 256), 256, 0, h->stream>>>(h->ys + q * h->N, h->xs + q * h->N, h->N);
+        FMM_LAUNCHED();
+    }
     FMM_TRY(perm_out(h, h->ys, b_dev));
     return 0;
 }
@@ -509,8 +520,23 @@ int fmmbem_stokes_dl_apply(fmmbem_handle* h, const double* u_dev, double* y_dev)
     return 0;
 }
 
+static int solve_checked(fmmbem_handle* h, const double* rhs_dev, double tol, int relax, int p_initial, int p_min,
+                         double* x_dev, int* iters, int* p_hist, double* res_hist, double* true_res);
+
 int fmmbem_solve(fmmbem_handle* h, const double* rhs_dev, double tol, int relax, int p_initial, int p_min,
                  double* x_dev, int* iters, int* p_hist, double* res_hist, double* true_res) {
+    if (h && h->nrhs > 1) { fmmbem_set_error("batched handle: use fmmbem_solve_batch"); return FMMBEM_ESTATE; }
+    return solve_checked(h, rhs_dev, tol, relax, p_initial, p_min, x_dev, iters, p_hist, res_hist, true_res);
+}
+
+int fmmbem_solve_batch(fmmbem_handle* h, const double* rhs_dev, double tol, int relax, int p_initial, int p_min,
+                       double* x_dev, int* iters, int* p_hist, double* res_hist, double* true_res) {
+    if (h && h->nrhs == 1) { fmmbem_set_error("fmmbem_solve_batch needs a batched handle (opts.nrhs)"); return FMMBEM_ESTATE; }
+    return solve_checked(h, rhs_dev, tol, relax, p_initial, p_min, x_dev, iters, p_hist, res_hist, true_res);
+}
+
+static int solve_checked(fmmbem_handle* h, const double* rhs_dev, double tol, int relax, int p_initial, int p_min,
+                         double* x_dev, int* iters, int* p_hist, double* res_hist, double* true_res) {
     if (!h || !rhs_dev || !x_dev) { fmmbem_set_error("NULL argument"); return FMMBEM_EINVAL; }
     if (p_initial < 1 || p_initial > h->opts.p_max || p_min < 1 || p_min > p_initial) {
         fmmbem_set_error("need 1 <= p_min <= p_initial <= p_max");
@@ -527,6 +553,7 @@ int fmmbem_solve(fmmbem_handle* h, const double* rhs_dev, double tol, int relax,
 int fmmbem_solve_host(fmmbem_handle* h, const double* rhs_host, double tol, int relax, int p_initial, int p_min,
                       double* x_host, int* iters, int* p_hist, double* res_hist, double* true_res) {
     if (!h || !rhs_host || !x_host) { fmmbem_set_error("NULL argument"); return FMMBEM_EINVAL; }
+    if (h->nrhs > 1) { fmmbem_set_error("batched handle: use fmmbem_solve_batch"); return FMMBEM_ESTATE; }
     const int64_t n = h->N * h->dof;
     FMM_CU(cudaMemcpyAsync(h->ys, rhs_host, sizeof(double) * n, cudaMemcpyHostToDevice, h->stream));
     int rc = fmmbem_solve(h, h->ys, tol, relax, p_initial, p_min, h->xs, iters, p_hist, res_hist, true_res);

@@ -53,7 +53,7 @@ constexpr int P2M_WARPS = 4;
 template <typename T, int NC>
 __global__ void __launch_bounds__(32 * P2M_WARPS) k_p2m(int p, const int* leaves, const double4* cs, const int2* range,
                                                        const typename V4<T>::type* src, const double* xs, int K,
-                                                       double ox, double oy, double oz, T* M) {
+                                                       double ox, double oy, double oz, T* M, int64_t bstride) {
     extern __shared__ unsigned char smem_raw[];
     T* acc = reinterpret_cast<T*>(smem_raw);  // [warps][NC][ncoef][2]
     const int nco = ncoef(p);
@@ -79,6 +79,9 @@ __global__ void __launch_bounds__(32 * P2M_WARPS) k_p2m(int p, const int* leaves
             vz = T(((double)y.z - cc.z) * inv_s);
             if (NC == 1) {
                 q[0] = T((double)y.w * xs[pj]);
+            } else if (bstride) {  // a batch of vectors: plain strengths, vector c at xs + c * bstride
+#pragma unroll
+                for (int c = 0; c < NC; ++c) q[c] = T((double)y.w * xs[c * bstride + pj]);
             } else {
                 const double t0 = xs[3 * pj], t1 = xs[3 * pj + 1], t2 = xs[3 * pj + 2];
                 const double w = (double)y.w;
@@ -135,22 +138,26 @@ __global__ void __launch_bounds__(32 * P2M_WARPS) k_p2m(int p, const int* leaves
 // harmonics column by column, coefficients reduced across the warp into shared memory.
 // DL = true: the double layer's dipoles (two float4 per Gauss point, the moment w n in
 // .w of the first and .x, .y of the second), scattered as in k_p2m_dl.
-template <bool DL>
+// MODE 2: a batch of four vectors (strengths in .w of the first float4 and .x, .y, .z of the
+// second), four expansions per cell.
+template <int MODE>
 __global__ void __launch_bounds__(32 * P2M_WARPS) k_p2m_packed(int p, const int* leaves, const double4* cs,
                                                               const int2* range, const float4* srcw, int K, float* M) {
+    constexpr bool DL = MODE == 1;
+    constexpr int NC = MODE == 2 ? 4 : 1;
     extern __shared__ unsigned char smem_raw[];
-    float* acc = reinterpret_cast<float*>(smem_raw);  // [warps][ncoef][2]
+    float* acc = reinterpret_cast<float*>(smem_raw);  // [warps][NC][ncoef][2]
     const int nco = ncoef(p);
     const int cell = leaves[blockIdx.x];
     const int2 r = range[cell];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int q = threadIdx.x; q < P2M_WARPS * nco * 2; q += blockDim.x) acc[q] = 0.f;
+    for (int q = threadIdx.x; q < P2M_WARPS * NC * nco * 2; q += blockDim.x) acc[q] = 0.f;
     __syncthreads();
-    float* wacc = acc + warp * nco * 2;
+    float* wacc = acc + warp * NC * nco * 2;
     const float inv_s = (float)(1.0 / cs[cell].w);
     const int s0 = r.x * K, s1 = r.y * K;
-    auto add = [&](int n, int m, cpx<float> d) {  // M~(n, m) += conj(d), summed over the warp
-        const int qi = cidx(n, m);
+    auto add = [&](int comp, int n, int m, cpx<float> d) {  // M~_comp(n, m) += conj(d), summed over the warp
+        const int qi = comp * nco + cidx(n, m);
         const float re = warp_sum(d.re), im = warp_sum(-d.im);
         if (lane == 0) {
             wacc[2 * qi] += re;
@@ -160,9 +167,14 @@ __global__ void __launch_bounds__(32 * P2M_WARPS) k_p2m_packed(int p, const int*
     for (int base = s0 + warp * 32; base < s1; base += P2M_WARPS * 32) {
         const int s = base + lane;
         float vx = 0.f, vy = 0.f, vz = 0.f, q = 0.f, c = 0.f;
+        float qb[4] = {0.f, 0.f, 0.f, 0.f};
         cpx<float> a = mk(0.f, 0.f), b = mk(0.f, 0.f);
         if (s < s1) {
-            if (DL) {
+            if (MODE == 2) {
+                const float4 u = srcw[2 * s], u2 = srcw[2 * s + 1];
+                vx = u.x * inv_s; vy = u.y * inv_s; vz = u.z * inv_s;
+                qb[0] = u.w; qb[1] = u2.x; qb[2] = u2.y; qb[3] = u2.z;
+            } else if (DL) {
                 const float4 u = srcw[2 * s], u2 = srcw[2 * s + 1];
                 vx = u.x * inv_s; vy = u.y * inv_s; vz = u.z * inv_s;
                 const float mx = u.w * inv_s, my = u2.x * inv_s, mz = u2.y * inv_s;
@@ -177,13 +189,16 @@ __global__ void __launch_bounds__(32 * P2M_WARPS) k_p2m_packed(int p, const int*
         }
         auto emit = [&](int n, int m, cpx<float> R) {
             if (DL) {  // R = R_n^m, n < p: feeds degree n + 1
-                add(n + 1, m, c * R);
-                if (m >= 1) add(n + 1, m - 1, a * R);
+                add(0, n + 1, m, c * R);
+                if (m >= 1) add(0, n + 1, m - 1, a * R);
                 const cpx<float> bR = b * R;
-                add(n + 1, m + 1, mk(-bR.re, -bR.im));
-                if (m == 1) add(n + 1, 0, b * conj(R));
+                add(0, n + 1, m + 1, mk(-bR.re, -bR.im));
+                if (m == 1) add(0, n + 1, 0, b * conj(R));
+            } else if (MODE == 2) {
+#pragma unroll
+                for (int cc = 0; cc < 4; ++cc) add(cc, n, m, qb[cc] * R);
             } else {
-                add(n, m, q * R);
+                add(0, n, m, q * R);
             }
         };
         const int nmax = DL ? p - 1 : p;  // highest degree generated
@@ -207,12 +222,13 @@ __global__ void __launch_bounds__(32 * P2M_WARPS) k_p2m_packed(int p, const int*
         }
     }
     __syncthreads();
-    float* out = M + (size_t)cell * ESTRIDE;
-    for (int idx = threadIdx.x; idx < nco * 2; idx += blockDim.x) {
+    float* out = M + (size_t)cell * NC * ESTRIDE;
+    for (int idx = threadIdx.x; idx < NC * nco * 2; idx += blockDim.x) {
+        const int cc = idx / (nco * 2), rest = idx % (nco * 2);
         float v = 0.f;
 #pragma unroll
-        for (int w = 0; w < P2M_WARPS; ++w) v += acc[w * nco * 2 + idx];
-        out[idx] = v;
+        for (int w = 0; w < P2M_WARPS; ++w) v += acc[w * NC * nco * 2 + idx];
+        out[cc * ESTRIDE + rest] = v;
     }
 }
 
@@ -499,7 +515,7 @@ __global__ void __launch_bounds__(TREE_THREADS) k_l2l(int p, const int* parents,
 template <typename T, int NC>
 __global__ void k_l2p(int p, const int* leaves, const double4* cs, const int2* range, const double4* tgt, const T* L,
                       const double* ynear, double scale, double ox, double oy, double oz, const double* xs_half,
-                      const float4* tgt_rel, double* yout) {
+                      const float4* tgt_rel, double* yout, int64_t bstride) {
     __shared__ T sL[NC * NCOEF_MAX * 2];
     const int cell = leaves[blockIdx.x];
     const double4 cc = cs[cell];
@@ -513,8 +529,8 @@ __global__ void k_l2p(int p, const int* leaves, const double4* cs, const int2* r
     }
     __syncthreads();
     const double inv_s = 1.0 / cc.w;
-    // FP32 with one expansion: the FP32 offsets from the leaf centre (no FP64 arithmetic)
-    constexpr bool rel = std::is_same<T, float>::value && NC == 1;
+    // FP32 with one expansion, or a batch: the FP32 offsets from the leaf centre (no FP64 arithmetic)
+    const bool rel = std::is_same<T, float>::value && (NC == 1 || bstride != 0);
     const float inv_sf = (float)inv_s;
     for (int i = r.x + threadIdx.x; i < r.y; i += blockDim.x) {
         T vx, vy, vz;
@@ -540,7 +556,7 @@ __global__ void k_l2p(int p, const int* leaves, const double4* cs, const int2* r
                 const T* Lb = sL + c * NCOEF_MAX * 2;
                 const cpx<T> a = ld(Lb, cidx(n, m));
                 phi[c] += wgt * (a.re * R.re - a.im * R.im);
-                if (NC > 1 && n + 1 <= p) {
+                if (NC > 1 && bstride == 0 && n + 1 <= p) {  // Stokes: the gradients too
                     const cpx<T> b = ld(Lb, cidx(n + 1, m));
                     gz[c] += wgt * (b.re * R.re - b.im * R.im);
                     if (m >= 1) cfma(F[c], ld(Lb, cidx(n + 1, m - 1)), R);
@@ -568,6 +584,12 @@ __global__ void k_l2p(int p, const int* leaves, const double4* cs, const int2* r
         if (NC == 1) {
             const double far = rel ? (double)(phi[0] * inv_sf) : (double)phi[0] * inv_s;
             yout[i] = scale * (far + ynear[i]) + (xs_half ? 0.5 * xs_half[i] : 0.0);  // 1/2 I of the second kind
+        } else if (bstride) {  // a batch: potential of each vector, near field interleaved [N][NC]
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+                const double far = rel ? (double)(phi[c] * inv_sf) : (double)phi[c] * inv_s;
+                yout[c * bstride + i] = scale * (far + ynear[(int64_t)NC * i + c]);
+            }
         } else {
             const double is2 = inv_s * inv_s;
             const double px = x.x - ox, py = x.y - oy, pz = x.z - oz;
@@ -671,21 +693,25 @@ int far_field_t(fmmbem_handle* h, int p) {
     // P2M
     prof_begin(h, FMMBEM_PASS_P2M);
     const size_t sm = (size_t)P2M_WARPS * NC * nco * 2 * sizeof(T);
-    if (std::is_same<T, float>::value && NC == 1) {
+    if (std::is_same<T, float>::value && (NC == 1 || h->nrhs > 1)) {
         // mixed precision: the packed FP32 sources
         float* Mf = reinterpret_cast<float*>(h->M);
-        if (h->layer == FMMBEM_LAYER_DOUBLE)
-            k_p2m_packed<true><<<h->n_leaves, 32 * P2M_WARPS, sm, st>>>(p, h->leaves, h->cell_cs, h->cell_range,
-                                                                       h->src_w, h->K, Mf);
+        if (h->nrhs > 1)
+            k_p2m_packed<2><<<h->n_leaves, 32 * P2M_WARPS, sm, st>>>(p, h->leaves, h->cell_cs, h->cell_range,
+                                                                    h->src_w, h->K, Mf);
+        else if (h->layer == FMMBEM_LAYER_DOUBLE)
+            k_p2m_packed<1><<<h->n_leaves, 32 * P2M_WARPS, sm, st>>>(p, h->leaves, h->cell_cs, h->cell_range,
+                                                                    h->src_w, h->K, Mf);
         else
-            k_p2m_packed<false><<<h->n_leaves, 32 * P2M_WARPS, sm, st>>>(p, h->leaves, h->cell_cs, h->cell_range,
-                                                                        h->src_w, h->K, Mf);
+            k_p2m_packed<0><<<h->n_leaves, 32 * P2M_WARPS, sm, st>>>(p, h->leaves, h->cell_cs, h->cell_range,
+                                                                    h->src_w, h->K, Mf);
     } else if (NC == 1 && h->layer == FMMBEM_LAYER_DOUBLE) {
         k_p2m_dl<T><<<h->n_leaves, 32 * P2M_WARPS, sm, st>>>(p, h->leaves, h->cell_cs, h->cell_range, src, h->nrm_d,
                                                             h->xin, h->K, M);
     } else {
         k_p2m<T, NC><<<h->n_leaves, 32 * P2M_WARPS, sm, st>>>(p, h->leaves, h->cell_cs, h->cell_range, src, h->xin,
-                                                             h->K, h->origin[0], h->origin[1], h->origin[2], M);
+                                                             h->K, h->origin[0], h->origin[1], h->origin[2], M,
+                                                             h->nrhs > 1 ? h->N : 0);
     }
     FMM_LAUNCHED();
     prof_end(h, FMMBEM_PASS_P2M, 1);
@@ -751,7 +777,7 @@ int far_eval_t(fmmbem_handle* h, int p, double* y_sorted, double scale) {
                                                     reinterpret_cast<const T*>(h->L), h->ynear, scale, h->origin[0],
                                                     h->origin[1], h->origin[2],
                                                     NC == 1 && h->layer == FMMBEM_LAYER_DOUBLE ? h->xin : nullptr,
-                                                    h->tgt_rel, y_sorted);
+                                                    h->tgt_rel, y_sorted, h->nrhs > 1 ? h->N : 0);
     FMM_LAUNCHED();
     prof_end(h, FMMBEM_PASS_L2P, 1);
     h->launches += 1;

@@ -8,7 +8,8 @@ struct fmmbem_handle {
     // problem
     int kernel = FMMBEM_LAPLACE;  // FMMBEM_LAPLACE or FMMBEM_STOKES
     int dof = 1;                  // unknowns per panel
-    int ncomp = 1;                // harmonic expansions per cell (1 Laplace, 4 Stokes)
+    int ncomp = 1;                // harmonic expansions per cell (1 Laplace, 4 Stokes, nrhs batched Laplace)
+    int nrhs = 1;                 // vectors per mat-vec ([nrhs][N] layout; FMMBEM_BATCH for batched handles)
     int K = 4;                    // far-field Gauss points per panel
     int ncrit = 150;
     double theta = 0.5;

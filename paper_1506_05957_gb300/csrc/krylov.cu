@@ -135,8 +135,9 @@ __device__ __forceinline__ int arn_slices(int nt) {
     return nw > nt ? nw / nt : 1;
 }
 
+// nbk, bk: the blocks that share this system and this block's index among them.
 __device__ void arn_partials(const double* V, int64_t ldv, int nv, const double* w, int64_t i0, int64_t i1,
-                             double* partial, bool with_self = false) {
+                             double* partial, int nbk, int bk, bool with_self = false) {
     const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5, nw = (int)(blockDim.x >> 5);
     const int nt = nv + (with_self ? 1 : 0);
     const int ns = arn_slices(nt);
@@ -157,16 +158,16 @@ __device__ void arn_partials(const double* V, int64_t ldv, int nv, const double*
         double t = (s0 + s1) + (s2 + s3);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-        if (lane == 0) partial[(int64_t)item * gridDim.x + blockIdx.x] = t;
+        if (lane == 0) partial[(int64_t)item * nbk + bk] = t;
     }
 }
 
-// hs[j] = sum over blocks of partial[j][.] (one warp per j, fixed order); every block forms
+// hs[j] = sum over the system's blocks of partial[j][.] (one warp per j, fixed order); every block forms
 // the same hs. With sq != nullptr, *sq = sum_{j < nsq} hs[j]^2, by one warp.
-__device__ void arn_reduce(const double* partial, int nv, double* hs, int nsq = 0, double* sq = nullptr) {
+__device__ void arn_reduce(const double* partial, int nv, int nbk, double* hs, int nsq = 0, double* sq = nullptr) {
     const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
     const int ns = arn_slices(nv);
-    const int nb = (int)gridDim.x * ns;  // a vector's entries are contiguous: slices x blocks
+    const int nb = nbk * ns;  // a vector's entries are contiguous: slices x blocks
     for (int j = wp; j < nv; j += (int)(blockDim.x >> 5)) {
         double t = 0.0;
         for (int b = lane; b < nb; b += 32) t += partial[(int64_t)j * nb + b];
@@ -218,30 +219,45 @@ __device__ void arn_update(const double* V, int64_t n, int nv, const double* hs,
 // normalized and written as V_{k+1} in the same sweep that forms it (one grid barrier).
 // Otherwise a second projection pass follows (the CGS2 step), whose sweep also gives the
 // explicit ||w - V h||^2 (two grid barriers in all).
+// A launch may carry several systems of a batch: the grid is cut into nsys equal groups of
+// blocks, group q working on system q (its basis at V + q * vstride, its vectors at
+// w + q * wstride and xfix + q * wstride, its partial sums, barrier pair and output areas
+// offset likewise). A system whose bit in active is clear does nothing (its whole group
+// returns at once, so barrier counts stay consistent).
 __global__ void __launch_bounds__(ARN_THREADS) k_arnoldi(double* V, int64_t n, int k, double* w, double* xfix,
-                                                         double* partial, unsigned* bar_count, unsigned* bar_gen,
-                                                         double* out, int* err) {
+                                                         double* partial, unsigned* bar, double* out, int* err,
+                                                         int nsys, int64_t vstride, int64_t wstride,
+                                                         unsigned active) {
     __shared__ double hs[ARN_MAXV];
     __shared__ double h1[ARN_MAXV];
+    const int nbk = (int)gridDim.x / nsys;
+    const int sys = (int)blockIdx.x / nbk, bk = (int)blockIdx.x - sys * nbk;
+    if (sys >= nsys || !((active >> sys) & 1u)) return;
+    V += sys * vstride;
+    w += sys * wstride;
+    xfix += sys * wstride;
+    const size_t parea = (size_t)ARN_MAXV * nbk;
+    partial += (size_t)sys * 2 * parea;
+    unsigned* bar_count = bar + 2 * sys;
+    unsigned* bar_gen = bar + 2 * sys + 1;
+    out += (size_t)sys * (2 * (ARN_MAXV + 1) + 1);
     const int nv = k + 1;
-    const int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
-    const int64_t i0 = (int64_t)blockIdx.x * chunk, i1 = min(n, i0 + chunk);
-    const unsigned nb = gridDim.x;
+    const int64_t chunk = (n + nbk - 1) / nbk;
+    const int64_t i0 = (int64_t)bk * chunk, i1 = min(n, i0 + chunk);
     // each phase has its own partial-sum area, so one grid barrier per phase suffices:
     // a block's w rows are read and written by that block alone
-    const size_t parea = (size_t)ARN_MAXV * gridDim.x;
     double* vk1 = V + (int64_t)(k + 1) * n;
     // phase 1: h = V^T w and ||w||^2
     __shared__ double s_sq;
-    arn_partials(V, n, nv, w, i0, i1, partial, true);
-    if (!grid_barrier(bar_count, bar_gen, nb, err)) return;
-    arn_reduce(partial, nv + 1, hs, nv, &s_sq);
+    arn_partials(V, n, nv, w, i0, i1, partial, nbk, bk, true);
+    if (!grid_barrier(bar_count, bar_gen, (unsigned)nbk, err)) return;
+    arn_reduce(partial, nv + 1, nbk, hs, nv, &s_sq);
     const double ww = hs[nv];
     const double nn2 = ww - s_sq;
-    if (blockIdx.x == 0)
+    if (bk == 0)
         for (int j = threadIdx.x; j < nv; j += blockDim.x) out[j] = hs[j];
     if (nn2 > 0.5 * ww && nn2 > 0.0 && isfinite(nn2)) {
-        if (blockIdx.x == 0) {
+        if (bk == 0) {
             for (int j = threadIdx.x; j < nv; j += blockDim.x) out[(ARN_MAXV + 1) + j] = 0.0;
             if (threadIdx.x == 0) out[2 * (ARN_MAXV + 1)] = nn2;
         }
@@ -257,12 +273,12 @@ __global__ void __launch_bounds__(ARN_THREADS) k_arnoldi(double* V, int64_t n, i
     arn_update(V, n, nv, h1, w, i0, i1, 0.0, nullptr, nullptr);
     __syncthreads();  // arn_partials reads rows of w that other threads of the block updated
     double* part2 = partial + parea;
-    arn_partials(V, n, nv, w, i0, i1, part2, true);
-    if (!grid_barrier(bar_count, bar_gen, nb, err)) return;
-    arn_reduce(part2, nv + 1, hs, nv, &s_sq);
+    arn_partials(V, n, nv, w, i0, i1, part2, nbk, bk, true);
+    if (!grid_barrier(bar_count, bar_gen, (unsigned)nbk, err)) return;
+    arn_reduce(part2, nv + 1, nbk, hs, nv, &s_sq);
     const double w1w1 = hs[nv];
     const double nrm2 = fmax(w1w1 - s_sq, 0.0);  // rounding below zero: w1 lies in the span (breakdown)
-    if (blockIdx.x == 0) {
+    if (bk == 0) {
         for (int j = threadIdx.x; j < nv; j += blockDim.x) out[(ARN_MAXV + 1) + j] = hs[j];
         if (threadIdx.x == 0) out[2 * (ARN_MAXV + 1)] = nrm2;
     }
@@ -334,13 +350,19 @@ static int gmres_solve_on(fmmbem_handle* h, const double* b, double tol, int rel
 
 // The solve runs on the handle's internal stream (capturable, so the mat-vec graphs can
 // be recorded), ordered after the caller's stream on entry and before it on exit.
+static int gmres_batch_on(fmmbem_handle* h, const double* b, double tol, int relax, int p_initial, int p_min,
+                          double* x, int* iters, int* p_hist, double* res_hist, double* true_res);
+
+// Batched handles (nrhs > 1): b, x are [nrhs][n]; iters, true_res hold nrhs entries,
+// res_hist [nrhs][max_iter + 1]; p_hist (one order per mat-vec) is shared.
 int gmres_solve(fmmbem_handle* h, const double* b, double tol, int relax, int p_initial, int p_min, double* x,
                 int* iters, int* p_hist, double* res_hist, double* true_res) {
     cudaStream_t user = h->stream;
     FMM_CU(cudaEventRecord(h->ev_in, user));
     FMM_CU(cudaStreamWaitEvent(h->istream, h->ev_in, 0));
     h->stream = h->istream;
-    const int rc = gmres_solve_on(h, b, tol, relax, p_initial, p_min, x, iters, p_hist, res_hist, true_res);
+    const int rc = h->nrhs > 1 ? gmres_batch_on(h, b, tol, relax, p_initial, p_min, x, iters, p_hist, res_hist, true_res)
+                               : gmres_solve_on(h, b, tol, relax, p_initial, p_min, x, iters, p_hist, res_hist, true_res);
     h->stream = user;
     if (rc < 0) return rc;
     // bounded device waits (grid barrier, bulk-copy and tensor-core barriers) report here
@@ -352,7 +374,7 @@ int gmres_solve(fmmbem_handle* h, const double* b, double tol, int relax, int p_
         fmmbem_set_error("a bounded device wait gave up (code %d/%d); results are invalid", flags[0], flags[1]);
         cudaMemsetAsync(h->kerr, 0, sizeof(int), h->istream);
         if (h->tc_err) cudaMemsetAsync(h->tc_err, 0, sizeof(int), h->istream);
-        cudaMemsetAsync(h->arn_bar, 0, 2 * sizeof(unsigned), h->istream);
+        cudaMemsetAsync(h->arn_bar, 0, 2 * h->nrhs * sizeof(unsigned), h->istream);
         cudaStreamSynchronize(h->istream);
         return FMMBEM_EDEVICE;
     }
@@ -420,11 +442,13 @@ static int gmres_solve_on(fmmbem_handle* h, const double* b, double tol, int rel
                 double* dw = h->kw;
                 double* dx = h->xfix;
                 double* dp = h->kpart;
-                unsigned* bc = h->arn_bar;
-                unsigned* bg = h->arn_bar + 1;
+                unsigned* bar = h->arn_bar;
                 double* dout = h->arn_out_dev;
                 int* de = h->kerr;
-                void* args[] = {&dV, &nn, &kk, &dw, &dx, &dp, &bc, &bg, &dout, &de};
+                int nsys = 1;
+                int64_t vstride = 0, wstride = 0;
+                unsigned active = 1u;
+                void* args[] = {&dV, &nn, &kk, &dw, &dx, &dp, &bar, &dout, &de, &nsys, &vstride, &wstride, &active};
                 FMM_CU(cudaLaunchCooperativeKernel((const void*)k_arnoldi, dim3(h->arn_blocks), dim3(arnoldi_threads(n, h->arn_blocks)), args, 0,
                                                    st));
                 h->launches += 1;
@@ -502,6 +526,210 @@ static int gmres_solve_on(fmmbem_handle* h, const double* b, double tol, int rel
         *true_res = sqrt(hb[0]) / bnorm;
     }
     return converged ? 0 : FMMBEM_NOT_CONVERGED;
+}
+
+// Restarted GMRES for the nrhs systems of a batched handle, in lockstep: each mat-vec
+// evaluates every system's current basis vector at once, at the largest order any active
+// system's relaxation rule asks for (a higher order than a system needs only makes its
+// product more accurate, so each system still meets its own bound). Each system keeps its
+// own Hessenberg matrix, Givens rotations, residual and restart state, and leaves the
+// lockstep once converged (its input vector is then zero). One cooperative launch runs the
+// Arnoldi steps of all active systems, one group of blocks per system.
+static int gmres_batch_on(fmmbem_handle* h, const double* b, double tol, int relax, int p_initial, int p_min,
+                          double* x, int* iters, int* p_hist, double* res_hist, double* true_res) {
+    const int nb = h->nrhs;
+    const int64_t n = h->N;  // per system
+    const int m_max = h->kr_m;
+    const int max_iter = h->opts.max_iter;
+    cudaStream_t st = h->stream;
+    Kr kr{h, n, (unsigned)std::min<int64_t>((n + 255) / 256, 2048)};
+    double* hb = h->kh_host;
+    double* knr = h->kh + 2 * (m_max + 2) * nb;
+    const int64_t vstride = (int64_t)(m_max + 1) * n;
+    FMM_CU(cudaMemsetAsync(x, 0, sizeof(double) * n * nb, st));
+    for (int q = 0; q < nb; ++q) FMM_TRY(kr.dots(b + q * n, 1, b + q * n, knr + q));
+    FMM_CU(cudaMemcpyAsync(hb, knr, sizeof(double) * nb, cudaMemcpyDeviceToHost, st));
+    FMM_CU(cudaStreamSynchronize(st));
+    prof_harvest(h);
+    struct Sys {
+        double bnorm = 0, beta = 0, rho = 1;
+        bool active = false, converged = false;
+        int it = 0, k_done = 0;
+        std::vector<double> H, cs, sn, g, y;
+    };
+    std::vector<Sys> sy(nb);
+    for (int q = 0; q < nb; ++q) {
+        Sys& S = sy[q];
+        S.bnorm = S.beta = sqrt(hb[q]);
+        S.H.assign((size_t)(m_max + 1) * m_max, 0.0);
+        S.cs.assign(m_max, 0.0);
+        S.sn.assign(m_max, 0.0);
+        S.g.assign(m_max + 1, 0.0);
+        S.y.assign(m_max, 0.0);
+        if (iters) iters[q] = 0;
+        if (res_hist) res_hist[(size_t)q * (max_iter + 1)] = 1.0;
+        if (!std::isfinite(S.bnorm)) return FMMBEM_ENAN;
+        S.converged = S.bnorm == 0.0;
+        S.active = !S.converged;
+    }
+    // r0 = b (x0 = 0)
+    FMM_CU(cudaMemcpyAsync(h->kr, b, sizeof(double) * n * nb, cudaMemcpyDeviceToDevice, st));
+    int it = 0, status = 0;
+    auto any_active = [&]() {
+        for (const Sys& S : sy) if (S.active) return true;
+        return false;
+    };
+    while (any_active() && it < max_iter) {
+        const int m = std::min(m_max, max_iter - it);
+        // v_0 = r / beta for the active systems; inactive inputs are zero
+        for (int q = 0; q < nb; ++q) {
+            Sys& S = sy[q];
+            if (S.active) {
+                k_scale<<<kr.gs, 256, 0, st>>>(h->V + q * vstride, h->xfix + q * n, h->kr + q * n, 1.0 / S.beta, n);
+                FMM_LAUNCHED();
+                h->launches += 1;
+                std::fill(S.H.begin(), S.H.end(), 0.0);
+                std::fill(S.g.begin(), S.g.end(), 0.0);
+                S.g[0] = S.beta;
+                S.k_done = 0;
+            } else {
+                FMM_CU(cudaMemsetAsync(h->xfix + q * n, 0, sizeof(double) * n, st));
+            }
+        }
+        unsigned cycle = 0;  // systems taking part in this cycle
+        for (int q = 0; q < nb; ++q) cycle |= (sy[q].active ? 1u : 0u) << q;
+        for (int k = 0; k < m; ++k) {
+            int p = p_min;
+            for (const Sys& S : sy)
+                if (S.active) p = std::max(p, relax ? relaxed_p_int(tol, S.rho, p_initial, p_min) : p_initial);
+            FMM_TRY(matvec_sorted(h, p, h->xfix, h->kw));
+            if (p_hist) p_hist[it] = p;
+            ++it;
+            unsigned active = 0;
+            for (int q = 0; q < nb; ++q) active |= (sy[q].active ? 1u : 0u) << q;
+            prof_begin(h, FMMBEM_PASS_KRYLOV);
+            {
+                double* dV = h->V;
+                int64_t nn = n;
+                int kk = k;
+                double* dw = h->kw;
+                double* dx = h->xfix;
+                double* dp = h->kpart;
+                unsigned* bar = h->arn_bar;
+                double* dout = h->arn_out_dev;
+                int* de = h->kerr;
+                int nsys = nb;
+                int64_t vs = vstride, ws = n;
+                void* args[] = {&dV, &nn, &kk, &dw, &dx, &dp, &bar, &dout, &de, &nsys, &vs, &ws, &active};
+                const int grid = (h->arn_blocks / nb) * nb;
+                FMM_CU(cudaLaunchCooperativeKernel((const void*)k_arnoldi, dim3(grid),
+                                                   dim3(arnoldi_threads(n, grid)), args, 0, st));
+                h->launches += 1;
+            }
+            FMM_CU(cudaStreamSynchronize(st));
+            prof_harvest(h);
+            for (int q = 0; q < nb; ++q) {
+                Sys& S = sy[q];
+                if (!S.active) continue;
+                auto Hc = [&](int i, int c) -> double& { return S.H[(size_t)i * m_max + c]; };
+                const volatile double* ao = h->arn_out_host + (size_t)q * (2 * (ARN_MAXV + 1) + 1);
+                for (int i = 0; i <= k; ++i) Hc(i, k) = ao[i] + ao[(ARN_MAXV + 1) + i];
+                const double hn = sqrt(ao[2 * (ARN_MAXV + 1)]);
+                Hc(k + 1, k) = hn;
+                if (!std::isfinite(hn)) { status = FMMBEM_ENAN; break; }
+                for (int i = 0; i < k; ++i) {
+                    const double t = S.cs[i] * Hc(i, k) + S.sn[i] * Hc(i + 1, k);
+                    Hc(i + 1, k) = -S.sn[i] * Hc(i, k) + S.cs[i] * Hc(i + 1, k);
+                    Hc(i, k) = t;
+                }
+                const double den = hypot(Hc(k, k), Hc(k + 1, k));
+                S.cs[k] = Hc(k, k) / den;
+                S.sn[k] = Hc(k + 1, k) / den;
+                Hc(k, k) = den;
+                Hc(k + 1, k) = 0.0;
+                S.g[k + 1] = -S.sn[k] * S.g[k];
+                S.g[k] = S.cs[k] * S.g[k];
+                S.rho = fabs(S.g[k + 1]) / S.bnorm;
+                S.it = it;
+                S.k_done = k + 1;
+                if (res_hist) res_hist[(size_t)q * (max_iter + 1) + it] = S.rho;
+                if (!std::isfinite(S.rho)) { status = FMMBEM_ENAN; break; }
+                if (S.rho <= tol || hn == 0.0) {
+                    S.converged = true;
+                    S.active = false;  // its basis stays as is; x is updated at the end of the cycle
+                    FMM_CU(cudaMemsetAsync(h->xfix + q * n, 0, sizeof(double) * n, st));
+                }
+            }
+            prof_end(h, FMMBEM_PASS_KRYLOV, 1);
+            if (status < 0) break;
+            if (!any_active() || it >= max_iter) break;
+        }
+        if (status < 0) break;
+        // y = H^{-1} g, x += V y for every system of this cycle
+        for (int q = 0; q < nb; ++q) {
+            Sys& S = sy[q];
+            if (!((cycle >> q) & 1u) || S.k_done == 0) continue;
+            auto Hc = [&](int i, int c) -> double& { return S.H[(size_t)i * m_max + c]; };
+            for (int i = S.k_done - 1; i >= 0; --i) {
+                double t = S.g[i];
+                for (int j = i + 1; j < S.k_done; ++j) t -= Hc(i, j) * S.y[j];
+                S.y[i] = t / Hc(i, i);
+            }
+            FMM_CU(cudaMemcpyAsync(h->kyv + q * (m_max + 2), S.y.data(), sizeof(double) * S.k_done,
+                                   cudaMemcpyHostToDevice, st));
+            k_add_combo<<<kr.gs, 256, 0, st>>>(x + q * n, h->V + q * vstride, n, S.k_done, h->kyv + q * (m_max + 2), n);
+            FMM_LAUNCHED();
+            h->launches += 1;
+        }
+        if (!any_active() || it >= max_iter) break;
+        // restart the active systems: r = b - A x at p_initial (the batch mat-vec, inactive inputs zero)
+        for (int q = 0; q < nb; ++q) {
+            if (sy[q].active) FMM_CU(cudaMemcpyAsync(h->xfix + q * n, x + q * n, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+            else FMM_CU(cudaMemsetAsync(h->xfix + q * n, 0, sizeof(double) * n, st));
+        }
+        FMM_TRY(matvec_sorted(h, p_initial, h->xfix, h->kw));
+        for (int q = 0; q < nb; ++q) {
+            if (!sy[q].active) continue;
+            k_sub<<<kr.gs, 256, 0, st>>>(h->kr + q * n, b + q * n, h->kw + q * n, n);
+            FMM_LAUNCHED();
+            h->launches += 1;
+            FMM_TRY(kr.dots(h->kr + q * n, 1, h->kr + q * n, knr + q));
+        }
+        FMM_CU(cudaMemcpyAsync(hb, knr, sizeof(double) * nb, cudaMemcpyDeviceToHost, st));
+        FMM_CU(cudaStreamSynchronize(st));
+        prof_harvest(h);
+        for (int q = 0; q < nb; ++q) {
+            Sys& S = sy[q];
+            if (!S.active) continue;
+            S.beta = sqrt(hb[q]);
+            S.rho = S.beta / S.bnorm;
+            if (res_hist) res_hist[(size_t)q * (max_iter + 1) + it] = S.rho;
+            if (S.rho <= tol || !(S.beta > 0.0)) {
+                S.converged = S.rho <= tol || S.beta == 0.0;
+                S.active = false;
+            }
+        }
+    }
+    for (int q = 0; q < nb; ++q)
+        if (iters) iters[q] = sy[q].it;
+    if (status < 0) return status;
+    if (true_res) {
+        FMM_CU(cudaMemcpyAsync(h->xfix, x, sizeof(double) * n * nb, cudaMemcpyDeviceToDevice, st));
+        FMM_TRY(matvec_sorted(h, p_initial, h->xfix, h->kw));
+        for (int q = 0; q < nb; ++q) {
+            k_sub<<<kr.gs, 256, 0, st>>>(h->kr + q * n, b + q * n, h->kw + q * n, n);
+            FMM_LAUNCHED();
+            h->launches += 1;
+            FMM_TRY(kr.dots(h->kr + q * n, 1, h->kr + q * n, knr + q));
+        }
+        FMM_CU(cudaMemcpyAsync(hb, knr, sizeof(double) * nb, cudaMemcpyDeviceToHost, st));
+        FMM_CU(cudaStreamSynchronize(st));
+        prof_harvest(h);
+        for (int q = 0; q < nb; ++q) true_res[q] = sy[q].bnorm > 0.0 ? sqrt(hb[q]) / sy[q].bnorm : 0.0;
+    }
+    bool all = true;
+    for (const Sys& S : sy) all = all && S.converged;
+    return all ? 0 : FMMBEM_NOT_CONVERGED;
 }
 
 }  // namespace fmmbem

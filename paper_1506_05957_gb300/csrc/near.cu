@@ -21,9 +21,11 @@ namespace {
 constexpr int P2P_THREADS = 128;
 constexpr int P2P_TILE = 512;
 
-enum Op { LAP_SL = 0, LAP_DL = 1, STK_SL = 2, STK_DL = 3 };
+// LAP_B4: the Laplace single layer for a batch of FMMBEM_BATCH vectors ([4][N] input,
+// [N][4] near-field output).
+enum Op { LAP_SL = 0, LAP_DL = 1, STK_SL = 2, STK_DL = 3, LAP_B4 = 4 };
 
-template <int OP> struct OpDof { static constexpr int v = (OP == STK_SL || OP == STK_DL) ? 3 : 1; };
+template <int OP> struct OpDof { static constexpr int v = (OP == STK_SL || OP == STK_DL) ? 3 : (OP == LAP_B4 ? 4 : 1); };
 
 // Accumulate one source into acc (unscaled kernel sums).
 //   LAP_SL : w / r
@@ -36,6 +38,9 @@ __device__ __forceinline__ void interact(T dx, T dy, T dz, const T* s, T* acc) {
     const T ir = rsqrt_t<T>(r2);
     if (OP == LAP_SL) {
         acc[0] += s[0] * ir;
+    } else if (OP == LAP_B4) {
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[c] += s[c] * ir;
     } else if (OP == LAP_DL) {
         const T ir3 = ir * ir * ir;
         acc[0] += s[0] * (dx * s[1] + dy * s[2] + dz * s[3]) * ir3;
@@ -57,12 +62,15 @@ __device__ __forceinline__ void interact(T dx, T dy, T dz, const T* s, T* acc) {
     }
 }
 
-template <int OP> struct SrcWidth { static constexpr int v = (OP == LAP_SL) ? 1 : (OP == LAP_DL ? 4 : (OP == STK_SL ? 3 : 6)); };
+template <int OP> struct SrcWidth {
+    static constexpr int v = (OP == LAP_SL) ? 1 : (OP == LAP_DL || OP == LAP_B4 ? 4 : (OP == STK_SL ? 3 : 6));
+};
 
 // Stage source q (global Gauss-point index) into shared memory: position + strength terms.
+// bstride: LAP_B4's distance between the batch's vectors in xs (N).
 template <typename T, int OP>
 __device__ __forceinline__ void stage(int g, const typename V4<T>::type* src, const double* xs, const double4* nrm, int K,
-                                      T* spos, T* sval, int slot) {
+                                      T* spos, T* sval, int slot, int64_t bstride = 0) {
     const auto y = src[g];
     const int pj = g / K;
     spos[3 * slot] = y.x;
@@ -73,6 +81,9 @@ __device__ __forceinline__ void stage(int g, const typename V4<T>::type* src, co
     const double w = (double)y.w;
     if (OP == LAP_SL) {
         v[0] = T(w * xs[pj]);
+    } else if (OP == LAP_B4) {
+#pragma unroll
+        for (int c = 0; c < 4; ++c) v[c] = T(w * xs[c * bstride + pj]);
     } else if (OP == LAP_DL) {
         const double4 n = nrm[pj];
         v[0] = T(w * xs[pj]);
@@ -86,14 +97,19 @@ __device__ __forceinline__ void stage(int g, const typename V4<T>::type* src, co
     }
 }
 
-// Add the correction row of target i: sum_e C_e x_{col_e} (1x1 or 3x3 blocks), FP64.
+// Add the correction row of target i: sum_e C_e x_{col_e} (1x1 or 3x3 blocks), FP64. DOF 4:
+// one scalar entry applied to each vector of a batch (vector c at xs + c * bstride).
 template <int DOF>
 __device__ __forceinline__ void add_correction(int i, const int* cptr, const int* ccol, const double* cval,
-                                               const double* xs, double* out) {
+                                               const double* xs, double* out, int64_t bstride = 0) {
     for (int e = cptr[i]; e < cptr[i + 1]; ++e) {
         const int j = ccol[e];
         if (DOF == 1) {
             out[0] += cval[e] * xs[j];
+        } else if (DOF == 4) {
+            const double c0 = cval[e];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) out[c] += c0 * xs[c * bstride + j];
         } else {
             const double* B = cval + 9 * (int64_t)e;
             const double x0 = xs[3 * j], x1 = xs[3 * j + 1], x2 = xs[3 * j + 2];
@@ -116,7 +132,7 @@ __global__ void __launch_bounds__(P2P_THREADS) k_p2p(const int* leaves, const do
                                                      const int* pptr, const int* psrc, const typename V4<T>::type* src,
                                                      const typename V4<T>::type* tgt, bool relative, const double* xs,
                                                      const double4* nrm, int K, const int* cptr, const int* ccol,
-                                                     const double* cval, double* ynear) {
+                                                     const double* cval, double* ynear, int64_t bstride) {
     constexpr int DOF = OpDof<OP>::v;
     constexpr int W = SrcWidth<OP>::v;
     __shared__ T spos[3 * P2P_TILE];
@@ -153,7 +169,7 @@ __global__ void __launch_bounds__(P2P_THREADS) k_p2p(const int* leaves, const do
                 const int nt = min(P2P_TILE, g1 - gb);
                 __syncthreads();
                 for (int q = tid; q < nt; q += P2P_THREADS) {
-                    stage<T, OP>(gb + q, src, xs, nrm, K, spos, sval, q);
+                    stage<T, OP>(gb + q, src, xs, nrm, K, spos, sval, q, bstride);
                     spos[3 * q] += shx;
                     spos[3 * q + 1] += shy;
                     spos[3 * q + 2] += shz;
@@ -192,7 +208,7 @@ __global__ void __launch_bounds__(P2P_THREADS) k_p2p(const int* leaves, const do
             for (int s = 0; s < nsl; ++s)
 #pragma unroll
                 for (int a = 0; a < DOF; ++a) out[a] += sred[(s * chunk + ti) * DOF + a];
-            add_correction<DOF>(i, cptr, ccol, cval, xs, out);
+            add_correction<DOF>(i, cptr, ccol, cval, xs, out, bstride);
 #pragma unroll
             for (int a = 0; a < DOF; ++a) ynear[(int64_t)DOF * i + a] = out[a];
         }
@@ -823,6 +839,7 @@ constexpr int SS_SRC = 2;  // sources per lane per round
 template <int OP> struct VecLane;
 template <> struct VecLane<STK_SL> { static constexpr int DOF = 3, TM = P2P_SRC_TMAX_STOKES; };
 template <> struct VecLane<LAP_DL> { static constexpr int DOF = 1, TM = P2P_SRC_TMAX; };
+template <> struct VecLane<LAP_B4> { static constexpr int DOF = 4, TM = P2P_SRC_TMAX_BATCH; };
 
 // Both pack per panel (one FP64-to-FP32 conversion per unknown, as k_pack_sources).
 __global__ void k_pack_sources_stokes(const float4* src_rel, const double* xs, int K, int64_t n, float4* out) {
@@ -834,6 +851,19 @@ __global__ void k_pack_sources_stokes(const float4* src_rel, const double* xs, i
         const float4 y = src_rel[g];
         out[2 * g] = make_float4(y.x, y.y, y.z, y.w * t0);
         out[2 * g + 1] = make_float4(y.w * t1, y.w * t2, 0.f, 0.f);
+    }
+}
+
+// A batch of four vectors ([4][n] in xs): (position, w x_0) and (w x_1, w x_2, w x_3, 0).
+__global__ void k_pack_sources_b4(const float4* src_rel, const double* xs, int K, int64_t n, float4* out) {
+    const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    const float x0 = (float)xs[j], x1 = (float)xs[n + j], x2 = (float)xs[2 * n + j], x3 = (float)xs[3 * n + j];
+    for (int k = 0; k < K; ++k) {
+        const int64_t g = j * K + k;
+        const float4 y = src_rel[g];
+        out[2 * g] = make_float4(y.x, y.y, y.z, y.w * x0);
+        out[2 * g + 1] = make_float4(y.w * x1, y.w * x2, y.w * x3, 0.f);
     }
 }
 
@@ -865,6 +895,13 @@ __device__ __forceinline__ void vl_pair(float4 x, float4 a, float4 b, bool skip,
     const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
     const float ir = skip ? 0.f : rsqrt_approx(skip ? 1.f : r2);
     const float ir3 = ir * ir * ir;
+    if (OP == LAP_B4) {
+        acc[0] = fmaf(a.w, ir, acc[0]);
+        acc[1] = fmaf(b.x, ir, acc[1]);
+        acc[2] = fmaf(b.y, ir, acc[2]);
+        acc[3] = fmaf(b.z, ir, acc[3]);
+        return;
+    }
     const float dv = fmaf(dx, a.w, fmaf(dy, b.x, dz * b.y));
     if (OP == STK_SL) {
         const float df = dv * ir3;
@@ -881,7 +918,7 @@ __global__ void __launch_bounds__(32 * PS_WARPS, 5) k_p2p_vec_src(const int4* it
                                                                  const float4* prec, const int* poff, const int* plen,
                                                                  const float4* srcw, const float4* tgt, int K,
                                                                  const int* cptr, const int* ccol, const double* cval,
-                                                                 const double* xs, double* ynear) {
+                                                                 const double* xs, double* ynear, int64_t bstride) {
     constexpr int DOF = VecLane<OP>::DOF, TM = VecLane<OP>::TM;
     __shared__ VlShared<OP> sh;
     constexpr int RND = 32 * SS_SRC;
@@ -999,7 +1036,7 @@ __global__ void __launch_bounds__(32 * PS_WARPS, 5) k_p2p_vec_src(const int4* it
                 }
             out[a] = (double)hi - (double)lo;
         }
-        add_correction<DOF>(tb + i, cptr, ccol, cval, xs, out);
+        add_correction<DOF>(tb + i, cptr, ccol, cval, xs, out, bstride);
 #pragma unroll
         for (int a = 0; a < DOF; ++a) ynear[DOF * (int64_t)(tb + i) + a] = out[a];
     }
@@ -1055,7 +1092,7 @@ int launch_p2p(fmmbem_handle* h, const double* cval) {
                                           : reinterpret_cast<const typename V4<T>::type*>(h->tgt_d);
     k_p2p<T, OP><<<h->n_leaves, P2P_THREADS, 0, h->stream>>>(h->leaves, h->cell_cs, h->cell_range, h->p2p_ptr,
                                                              h->p2p_src, src, tgt, rel, h->xin, h->nrm_d, h->K,
-                                                             h->corr_ptr, h->corr_col, cval, h->ynear);
+                                                             h->corr_ptr, h->corr_col, cval, h->ynear, h->N);
     FMM_LAUNCHED();
     return 0;
 }
@@ -1080,7 +1117,9 @@ int near_field_on(fmmbem_handle* h, bool fp64);
 // it), on the handle's stream before the near and far fields fork.
 int pack_sources(fmmbem_handle* h) {
     const unsigned g = (unsigned)((h->N + 255) / 256);
-    if (h->kernel == FMMBEM_STOKES)
+    if (h->nrhs > 1)
+        k_pack_sources_b4<<<g, 256, 0, h->stream>>>(h->src_rel, h->xin, h->K, h->N, h->src_w);
+    else if (h->kernel == FMMBEM_STOKES)
         k_pack_sources_stokes<<<g, 256, 0, h->stream>>>(h->src_rel, h->xin, h->K, h->N, h->src_w);
     else if (h->layer == FMMBEM_LAYER_DOUBLE)
         k_pack_sources_dipole<<<g, 256, 0, h->stream>>>(h->src_rel, h->nrm_f, h->xin, h->K, h->N, h->src_w);
@@ -1104,10 +1143,14 @@ static int launch_items(fmmbem_handle* h) {
     const int4* it = h->p2p_items;
     const unsigned nb = (unsigned)h->n_p2p_items;
     if (nb == 0) return 0;
-    if (h->kernel == FMMBEM_LAPLACE && h->layer == FMMBEM_LAYER_DOUBLE)
+    if (h->nrhs > 1)
+        k_p2p_vec_src<LAP_B4><<<nb, 32 * PS_WARPS, 0, h->stream>>>(it, h->cell_range, h->p2p_ptr, h->p2p_rec, h->p2p_off,
+                                                                   h->p2p_len, h->src_w, h->tgt_rel, h->K, h->corr_ptr,
+                                                                   h->corr_col, h->corr_sl, h->xin, h->ynear, h->N);
+    else if (h->kernel == FMMBEM_LAPLACE && h->layer == FMMBEM_LAYER_DOUBLE)
         k_p2p_vec_src<LAP_DL><<<nb, 32 * PS_WARPS, 0, h->stream>>>(it, h->cell_range, h->p2p_ptr, h->p2p_rec, h->p2p_off,
                                                                    h->p2p_len, h->src_w, h->tgt_rel, h->K, h->corr_ptr,
-                                                                   h->corr_col, h->corr_dl, h->xin, h->ynear);
+                                                                   h->corr_col, h->corr_dl, h->xin, h->ynear, 0);
     else if (h->kernel == FMMBEM_LAPLACE)
         k_p2p_lap_src<<<nb, 32 * PS_WARPS, 0, h->stream>>>(it, h->cell_range, h->p2p_ptr, h->p2p_rec, h->p2p_off,
                                                           h->p2p_len, h->src_w, h->tgt_rel, h->K, h->corr_ptr,
@@ -1115,7 +1158,7 @@ static int launch_items(fmmbem_handle* h) {
     else
         k_p2p_vec_src<STK_SL><<<nb, 32 * PS_WARPS, 0, h->stream>>>(it, h->cell_range, h->p2p_ptr, h->p2p_rec, h->p2p_off,
                                                                    h->p2p_len, h->src_w, h->tgt_rel, h->K, h->corr_ptr,
-                                                                   h->corr_col, h->corr_sl, h->xin, h->ynear);
+                                                                   h->corr_col, h->corr_sl, h->xin, h->ynear, 0);
     FMM_LAUNCHED();
     h->launches += 1;
     return 0;
@@ -1127,7 +1170,13 @@ int near_field_on(fmmbem_handle* h, bool fp64) {
     prof_begin(h, FMMBEM_PASS_P2P);
     const int64_t l0 = h->launches;
     const bool items = !fp64 && h->p2p_variant == 3 && h->p2p_items;
-    if (h->kernel == FMMBEM_LAPLACE && h->layer == FMMBEM_LAYER_DOUBLE) {
+    if (h->nrhs > 1) {
+        if (items) FMM_TRY(launch_items(h));
+        else {
+            FMM_TRY((fp64 ? launch_p2p<double, LAP_B4>(h, h->corr_sl) : launch_p2p<float, LAP_B4>(h, h->corr_sl)));
+            h->launches += 1;
+        }
+    } else if (h->kernel == FMMBEM_LAPLACE && h->layer == FMMBEM_LAYER_DOUBLE) {
         if (items) FMM_TRY(launch_items(h));
         else {
             FMM_TRY((fp64 ? launch_p2p<double, LAP_DL>(h, h->corr_dl) : launch_p2p<float, LAP_DL>(h, h->corr_dl)));

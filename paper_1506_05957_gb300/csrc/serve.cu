@@ -172,6 +172,10 @@ int fmmbem_server_submit(fmmbem_server* s, const fmmbem_mesh* mesh, int kernel, 
         fmmbem_set_error("bad request");
         return FMMBEM_EINVAL;
     }
+    if (opts && opts->nrhs != 1) {
+        fmmbem_set_error("served requests carry one right-hand side (opts.nrhs = 1)");
+        return FMMBEM_EINVAL;
+    }
     Request* r = new Request();
     r->vertices.assign(mesh->vertices, mesh->vertices + 3 * mesh->n_vertices);
     r->triangles.assign(mesh->triangles, mesh->triangles + 3 * mesh->n_panels);
