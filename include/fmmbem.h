@@ -155,8 +155,8 @@ int fmmbem_set_tc_thresholds(fmmbem_handle* h, int m2l_min_p, int tree_min_p);
  * Returns FMMBEM_EINVAL for any other value. */
 int fmmbem_set_p2p_variant(fmmbem_handle* h, int variant);
 
-/* Which boundary-integral operator A the mat-vecs and solves of a Laplace handle apply
- * (eq. laplace_matrix):
+/* Which boundary-integral operator A the mat-vecs and solves of a handle apply
+ * (eq. laplace_matrix; for Stokes eqs. stokes_bem_discretized and stresslet):
  *   SINGLE : A = V, V_ij = (1/4pi) int_j 1/r dS; the first-kind system for the unknown
  *            normal derivative when phi is given (default).
  *   DOUBLE : A = 1/2 I + K, K_ij = (1/4pi) int_j n_j.(x_i - y)/r^3 dS; the second-kind
@@ -167,7 +167,14 @@ int fmmbem_set_p2p_variant(fmmbem_handle* h, int variant);
  *            The FMM far field then carries dipoles (P2M of n.grad of the regular solid
  *            harmonics); the near field sums n_j.(x_i - y)/r^3 over the K Gauss points and
  *            adds the double-layer correction rows.
- * FMMBEM_ESTATE for DOUBLE on a Stokes handle, FMMBEM_EINVAL for another value. */
+ *            Stokes: A = 1/2 I + B, B the stresslet double layer (1/8pi) int T.n dS, the
+ *            second-kind system for the velocity u when the traction t is given (right-hand
+ *            side A_single t). Its far field is four Laplace dipole expansions evaluated like
+ *            the Stokeslet's: sum (a.r)(n.r) r / r^5 = (S_i - x_b d_i S_b + d_i S_0) / 6 with
+ *            dipole moments a_b n + n_b a and (a.y) n + (n.y) a. On a closed surface the
+ *            normal field n is a (near-)null vector of 1/2 I + B: solutions are determined up
+ *            to c n, as the single layer's tractions are.
+ * FMMBEM_ESTATE for DOUBLE on a batched handle, FMMBEM_EINVAL for another value. */
 #define FMMBEM_LAYER_SINGLE 0
 #define FMMBEM_LAYER_DOUBLE 1
 int fmmbem_set_layer(fmmbem_handle* h, int layer);

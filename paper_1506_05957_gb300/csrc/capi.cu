@@ -66,7 +66,8 @@ ProfState* prof_state(fmmbem_handle* h);
 
 double operator_scale(const fmmbem_handle* h) {
     const double pi = 3.14159265358979323846;
-    return h->kernel == FMMBEM_LAPLACE ? 1.0 / (4.0 * pi) : -1.0 / (8.0 * pi * h->opts.mu);
+    if (h->kernel == FMMBEM_LAPLACE) return 1.0 / (4.0 * pi);
+    return h->layer == FMMBEM_LAYER_DOUBLE ? 1.0 / (8.0 * pi) : -1.0 / (8.0 * pi * h->opts.mu);
 }
 
 int perm_in(fmmbem_handle* h, const double* x, double* xs) {
@@ -441,8 +442,8 @@ int fmmbem_set_precision(fmmbem_handle* h, int precision) {
 
 int fmmbem_set_layer(fmmbem_handle* h, int layer) {
     if (!h || (layer != FMMBEM_LAYER_SINGLE && layer != FMMBEM_LAYER_DOUBLE)) { fmmbem_set_error("bad layer"); return FMMBEM_EINVAL; }
-    if (layer == FMMBEM_LAYER_DOUBLE && (h->kernel != FMMBEM_LAPLACE || h->nrhs > 1)) {
-        fmmbem_set_error("the double-layer operator is built for Laplace handles");
+    if (layer == FMMBEM_LAYER_DOUBLE && h->nrhs > 1) {
+        fmmbem_set_error("the double-layer operator is not built for batched handles");
         return FMMBEM_ESTATE;
     }
     h->layer = layer;
@@ -487,8 +488,9 @@ int fmmbem_matvec_direct(fmmbem_handle* h, const double* x_dev, double* y_dev) {
     if (!h || !x_dev || !y_dev || x_dev == y_dev) { fmmbem_set_error("bad argument"); return FMMBEM_EINVAL; }
     FMM_TRY(perm_in(h, x_dev, h->xs));
     if (h->layer == FMMBEM_LAYER_DOUBLE) {  // 1/2 x + K x, in FP64
+        const int64_t nd = h->N * h->dof;
         FMM_TRY(direct_field(h, true, 1, h->xs, h->ys));
-        k_axpy_half<<<(unsigned)((h->N + 255) / 256), 256, 0, h->stream>>>(h->ys, h->xs, h->N);
+        k_axpy_half<<<(unsigned)((nd + 255) / 256), 256, 0, h->stream>>>(h->ys, h->xs, nd);
         FMM_LAUNCHED();
     } else {
         for (int q = 0; q < h->nrhs; ++q)  // a batch: each vector in turn

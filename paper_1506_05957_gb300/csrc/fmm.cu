@@ -319,6 +319,128 @@ __global__ void __launch_bounds__(32 * P2M_WARPS) k_p2m_dl(int p, const int* lea
     }
 }
 
+// P2M of the stresslet double layer (eq. stresslet) as four Laplace dipole expansions.
+// With r = x - y, a = q_k S_j u_j (the density times the quadrature weight) and n_j the
+// panel normal,
+//   sum (a.r)(n.r) r_i / |r|^5 = (1/6) [ S_i - x_b d_i S_b + d_i S_0 ],
+// where S_b (b = 1..3) is the potential of dipoles of moment a_b n + n_b a and S_0 that of
+// moments (a.y') n + (n.y') a (y' = y - origin, x likewise in the evaluation): the sum is
+// the Stokeslet's four-potential evaluation of L2P applied to these dipole expansions.
+// The moments are stored negated so that the far field carries the near-field kernel's
+// sign (-6 (r.a)(r.n) r / |r|^5). Component c of a cell: c < 3 -> S_{c+1}, c = 3 -> S_0.
+// Each harmonic R_k^j (k < p) a lane generates feeds degree k + 1 of every component, as in
+// k_p2m_dl. FP32 path: packed sources (position relative to the leaf centre, a) and the
+// FP32 normals; FP64 path: absolute Gauss points, x and the FP64 normals.
+template <typename T, bool PACKED>
+__global__ void __launch_bounds__(32 * P2M_WARPS) k_p2m_sdl(int p, const int* leaves, const double4* cs,
+                                                           const int2* range, const typename V4<T>::type* src,
+                                                           const float4* srcw, const double4* nrm_d,
+                                                           const float4* nrm_f, const double* xs, int K, double ox,
+                                                           double oy, double oz, T* M) {
+    extern __shared__ unsigned char smem_raw[];
+    T* acc = reinterpret_cast<T*>(smem_raw);  // [warps][4][ncoef][2]
+    const int nco = ncoef(p);
+    const int cell = leaves[blockIdx.x];
+    const double4 cc = cs[cell];
+    const int2 r = range[cell];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int q = threadIdx.x; q < P2M_WARPS * 4 * nco * 2; q += blockDim.x) acc[q] = T(0);
+    __syncthreads();
+    T* wacc = acc + warp * 4 * nco * 2;
+    const double inv_s = 1.0 / cc.w;
+    const T co_x = T(cc.x - ox), co_y = T(cc.y - oy), co_z = T(cc.z - oz);  // leaf centre from the origin
+    const int s0 = r.x * K, s1 = r.y * K;
+    auto add = [&](int comp, int n, int m, cpx<T> d) {  // M~_comp(n, m) += conj(d), summed over the warp
+        const int qi = comp * nco + cidx(n, m);
+        const T re = warp_sum(d.re), im = warp_sum(-d.im);
+        if (lane == 0) {
+            wacc[2 * qi] += re;
+            wacc[2 * qi + 1] += im;
+        }
+    };
+    for (int base = s0 + warp * 32; base < s1; base += P2M_WARPS * 32) {
+        const int s = base + lane;
+        T vx = 0, vy = 0, vz = 0;
+        T mom[4][3];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) mom[c][0] = mom[c][1] = mom[c][2] = T(0);
+        if (s < s1) {
+            T rx, ry, rz, a[3], nn[3];
+            const int pj = s / K;
+            if (PACKED) {
+                const float4 u = srcw[2 * s], u2 = srcw[2 * s + 1];
+                const float4 nv = nrm_f[pj];
+                rx = u.x; ry = u.y; rz = u.z;
+                a[0] = u.w; a[1] = u2.x; a[2] = u2.y;
+                nn[0] = nv.x; nn[1] = nv.y; nn[2] = nv.z;
+            } else {
+                const auto y = src[s];
+                const double4 nv = nrm_d[pj];
+                rx = T((double)y.x - cc.x); ry = T((double)y.y - cc.y); rz = T((double)y.z - cc.z);
+                const double w = (double)y.w;
+                a[0] = T(w * xs[3 * pj]); a[1] = T(w * xs[3 * pj + 1]); a[2] = T(w * xs[3 * pj + 2]);
+                nn[0] = T(nv.x); nn[1] = T(nv.y); nn[2] = T(nv.z);
+            }
+            vx = rx * T(inv_s); vy = ry * T(inv_s); vz = rz * T(inv_s);
+            const T yx = co_x + rx, yy = co_y + ry, yz = co_z + rz;  // y - origin
+            const T ay = a[0] * yx + a[1] * yy + a[2] * yz, ny = nn[0] * yx + nn[1] * yy + nn[2] * yz;
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+#pragma unroll
+                for (int b = 0; b < 3; ++b) mom[b][d] = -(a[b] * nn[d] + nn[b] * a[d]);
+                mom[3][d] = -(ay * nn[d] + ny * a[d]);
+            }
+        }
+        // per component: c = m_z / s, a = (m_x - i m_y) / 2s, b = (m_x + i m_y) / 2s
+        T cz[4];
+        cpx<T> ca[4], cb[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const T mx = mom[c][0] * T(inv_s), my = mom[c][1] * T(inv_s), mz = mom[c][2] * T(inv_s);
+            cz[c] = mz;
+            ca[c] = mk(T(0.5) * mx, T(-0.5) * my);
+            cb[c] = mk(T(0.5) * mx, T(0.5) * my);
+        }
+        auto emit = [&](int k, int j, cpx<T> R) {  // R = R_k^j(v), k < p
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                add(c, k + 1, j, cz[c] * R);
+                if (j >= 1) add(c, k + 1, j - 1, ca[c] * R);
+                const cpx<T> bR = cb[c] * R;
+                add(c, k + 1, j + 1, mk(-bR.re, -bR.im));
+                if (j == 1) add(c, k + 1, 0, cb[c] * conj(R));
+            }
+        };
+        const T r2 = vx * vx + vy * vy + vz * vz;
+        const cpx<T> xy = mk(vx, vy);
+        cpx<T> diag = mk(T(1), T(0));
+        for (int m = 0; m < p; ++m) {
+            if (m > 0) diag = (T(-0.5) / T(m)) * (xy * diag);
+            emit(m, m, diag);
+            if (m + 1 >= p) break;
+            cpx<T> prev2 = diag, prev1 = vz * diag;
+            emit(m + 1, m, prev1);
+            for (int n = m + 2; n < p; ++n) {
+                const T inv = T(1) / T((n - m) * (n + m));
+                cpx<T> cur = mk((T(2 * n - 1) * vz * prev1.re - r2 * prev2.re) * inv,
+                                (T(2 * n - 1) * vz * prev1.im - r2 * prev2.im) * inv);
+                emit(n, m, cur);
+                prev2 = prev1;
+                prev1 = cur;
+            }
+        }
+    }
+    __syncthreads();
+    T* out = M + (size_t)cell * 4 * ESTRIDE;
+    for (int idx = threadIdx.x; idx < 4 * nco * 2; idx += blockDim.x) {
+        const int c = idx / (nco * 2), rest = idx % (nco * 2);
+        T v = 0;
+#pragma unroll
+        for (int w = 0; w < P2M_WARPS; ++w) v += acc[w * 4 * nco * 2 + idx];
+        out[c * ESTRIDE + rest] = v;
+    }
+}
+
 // M2M for the non-leaf cells of one level: M~_n^m(P) = sum_children sum_{j,k}
 // M~_j^k(c) 2^{-j} conj(R_{n-j}^{m-k}(d)), d = (c_child - c_parent)/s_parent.
 // One block per parent. The children's expansions and octant tables are staged in
@@ -599,7 +721,8 @@ __global__ void k_l2p(int p, const int* leaves, const double4* cs, const int2* r
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
                 const double u = (double)phi[a] * inv_s - (px * g[0][a] + py * g[1][a] + pz * g[2][a]) + g[NC - 1][a];
-                yout[3 * (int64_t)i + a] = scale * (u + ynear[3 * (int64_t)i + a]);
+                yout[3 * (int64_t)i + a] = scale * (u + ynear[3 * (int64_t)i + a]) +
+                                           (xs_half ? 0.5 * xs_half[3 * (int64_t)i + a] : 0.0);  // 1/2 I (double layer)
             }
         }
     }
@@ -708,6 +831,15 @@ int far_field_t(fmmbem_handle* h, int p) {
     } else if (NC == 1 && h->layer == FMMBEM_LAYER_DOUBLE) {
         k_p2m_dl<T><<<h->n_leaves, 32 * P2M_WARPS, sm, st>>>(p, h->leaves, h->cell_cs, h->cell_range, src, h->nrm_d,
                                                             h->xin, h->K, M);
+    } else if (NC == 4 && h->kernel == FMMBEM_STOKES && h->layer == FMMBEM_LAYER_DOUBLE) {
+        if (std::is_same<T, float>::value)
+            k_p2m_sdl<T, true><<<h->n_leaves, 32 * P2M_WARPS, sm, st>>>(
+                p, h->leaves, h->cell_cs, h->cell_range, src, h->src_w, h->nrm_d, h->nrm_f, h->xin, h->K, h->origin[0],
+                h->origin[1], h->origin[2], M);
+        else
+            k_p2m_sdl<T, false><<<h->n_leaves, 32 * P2M_WARPS, sm, st>>>(
+                p, h->leaves, h->cell_cs, h->cell_range, src, h->src_w, h->nrm_d, h->nrm_f, h->xin, h->K, h->origin[0],
+                h->origin[1], h->origin[2], M);
     } else {
         k_p2m<T, NC><<<h->n_leaves, 32 * P2M_WARPS, sm, st>>>(p, h->leaves, h->cell_cs, h->cell_range, src, h->xin,
                                                              h->K, h->origin[0], h->origin[1], h->origin[2], M,
@@ -776,7 +908,7 @@ int far_eval_t(fmmbem_handle* h, int p, double* y_sorted, double scale) {
     k_l2p<T, NC><<<h->n_leaves, 128, 0, h->stream>>>(p, h->leaves, h->cell_cs, h->cell_range, h->tgt_d,
                                                     reinterpret_cast<const T*>(h->L), h->ynear, scale, h->origin[0],
                                                     h->origin[1], h->origin[2],
-                                                    NC == 1 && h->layer == FMMBEM_LAYER_DOUBLE ? h->xin : nullptr,
+                                                    h->layer == FMMBEM_LAYER_DOUBLE ? h->xin : nullptr,
                                                     h->tgt_rel, y_sorted, h->nrhs > 1 ? h->N : 0);
     FMM_LAUNCHED();
     prof_end(h, FMMBEM_PASS_L2P, 1);

@@ -1176,6 +1176,10 @@ int near_field_on(fmmbem_handle* h, bool fp64) {
             FMM_TRY((fp64 ? launch_p2p<double, LAP_B4>(h, h->corr_sl) : launch_p2p<float, LAP_B4>(h, h->corr_sl)));
             h->launches += 1;
         }
+    } else if (h->kernel == FMMBEM_STOKES && h->layer == FMMBEM_LAYER_DOUBLE) {
+        // the stresslet double layer: the shared-tile schedule with the FP64 3x3 correction rows
+        FMM_TRY((fp64 ? launch_p2p<double, STK_DL>(h, h->corr_dl) : launch_p2p<float, STK_DL>(h, h->corr_dl)));
+        h->launches += 1;
     } else if (h->kernel == FMMBEM_LAPLACE && h->layer == FMMBEM_LAYER_DOUBLE) {
         if (items) FMM_TRY(launch_items(h));
         else {

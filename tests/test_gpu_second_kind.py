@@ -166,11 +166,84 @@ def test_second_kind_relaxed_solve_matches_oracle(torch_cuda, exterior1280):
     assert r["iters"] <= 12
 
 
-def test_double_layer_rejected_on_stokes(torch_cuda):
-    from paper_1506_05957_gb300 import FmmBem, FmmBemError, FMMBEM_STOKES, FMMBEM_LAYER_DOUBLE
+@pytest.fixture(scope="module")
+def stokes1280(torch_cuda):
+    """Stokes second kind on the unit sphere: A = 1/2 I + B (stresslet double layer)."""
+    from oracle import dense, panels
+    from synth import icosphere
+    v, t = icosphere(3)
+    M = dense.Mesh(v, t, k=3)
+    A = 0.5 * np.eye(3 * M.n) + M.stokes_matrix(kind="dl")
+    c, n_out, S = panels.geometry(v, t)
+    return dict(v=v, t=t, M=M, A=A, c=c, n=n_out, S=S)
+
+
+def _stokes_dl(v, t, **kw):
+    from paper_1506_05957_gb300 import FmmBem, FMMBEM_STOKES, FMMBEM_LAYER_DOUBLE
+    kw.setdefault("ncrit", 60)
+    h = FmmBem(v, t, kernel=FMMBEM_STOKES, gauss_k=3, theta=0.5, **kw)
+    h.set_layer(FMMBEM_LAYER_DOUBLE)
+    return h
+
+
+def test_stokes_double_layer_direct_and_fmm(torch_cuda, stokes1280):
+    torch = torch_cuda
+    from paper_1506_05957_gb300 import FMMBEM_FP64, FMMBEM_MIXED
+    s = stokes1280
+    x = np.random.default_rng(4).standard_normal(3 * len(s["t"]))
+    ref = s["A"] @ x
+    h = _stokes_dl(s["v"], s["t"], precision=FMMBEM_FP64)
+    xd = _dev(torch, x)
+    y = torch.zeros_like(xd)
+    h.matvec_direct(xd, y)
+    assert rel(y.cpu().numpy(), ref) < 1e-12
+    errs = []
+    for p in (2, 4, 8, 12, 16):
+        h.matvec(p, xd, y)
+        errs.append(rel(y.cpu().numpy(), ref))
+    print("stresslet FMM errors by p", ["%.2e" % e for e in errs])
+    for a, b in zip(errs, errs[1:]):
+        assert b < a * 1.05 or b < 1e-12
+    assert errs[-1] < 1e-7
+    h.set_precision(FMMBEM_MIXED)
+    for p in (12, 16):
+        h.matvec(p, xd, y)
+        assert rel(y.cpu().numpy(), ref) < 1e-5, p
+
+
+def test_stokes_second_kind_relaxed_solve(torch_cuda, stokes1280):
+    """Velocity from the second-kind system for data of a rigid motion plus a smooth field:
+    the GPU solution meets the oracle residual and equals the oracle's solution up to the
+    operator's near-null normal field."""
+    torch = torch_cuda
+    s = stokes1280
+    c, nrm, S = s["c"], s["n"], s["S"]
+    u = np.tile([1.0, -0.5, 0.25], (len(c), 1)) + np.cross([0.3, 0.0, -0.7], c)
+    u += 0.2 * np.stack([c[:, 1] * c[:, 2], c[:, 0] ** 2, -c[:, 0] * c[:, 1]], axis=1)
+    u_true = u.reshape(-1)
+    b = s["A"] @ u_true
+    tol = 1e-6
+    h = _stokes_dl(s["v"], s["t"], p_max=16)
+    bd = _dev(torch, b)
+    x = torch.zeros_like(bd)
+    r = h.solve(bd, x, tol=tol, relax=True, p_initial=12, p_min=4)
+    assert r["converged"], r
+    xs = x.cpu().numpy()
+    assert rel(s["A"] @ xs, b) < 2 * tol
+
+    def modn(z):
+        z = z.reshape(-1, 3)
+        cc = np.sum(np.einsum("ij,ij->i", z, nrm) * S) / np.sum(S)
+        return (z - cc * nrm).reshape(-1)
+    assert rel(modn(xs), modn(u_true)) < 1e-3
+    print("stokes second kind iterations", r["iters"], r["p_hist"])
+
+
+def test_double_layer_rejected_on_batch(torch_cuda):
+    from paper_1506_05957_gb300 import FmmBem, FmmBemError, FMMBEM_LAYER_DOUBLE
     from synth import icosphere
     v, t = icosphere(2)
-    h = FmmBem(v, t, kernel=FMMBEM_STOKES, gauss_k=3, ncrit=60, theta=0.5)
+    h = FmmBem(v, t, gauss_k=4, ncrit=60, theta=0.5, nrhs=4)
     with pytest.raises(FmmBemError):
         h.set_layer(FMMBEM_LAYER_DOUBLE)
     with pytest.raises(FmmBemError):
