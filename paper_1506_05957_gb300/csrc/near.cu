@@ -730,7 +730,7 @@ __device__ __forceinline__ void ps_round_self(const float4* sT, int ntb, int tb,
     }
 }
 
-__global__ void __launch_bounds__(32 * PS_WARPS, 6) k_p2p_lap_src(const int4* items, const int2* range, const int* pptr,
+__global__ void __launch_bounds__(32 * PS_WARPS, 8) k_p2p_lap_src(const int4* items, const int2* range, const int* pptr,
                                                                  const float4* prec, const int* poff, const int* plen,
                                                                  const float4* srcw, const float4* tgt, int K,
                                                                  const int* cptr, const int* ccol, const double* cval,
