@@ -120,7 +120,8 @@ int fmmbem_create(const fmmbem_mesh* mesh, int kernel, int gauss_k, int ncrit, d
 /* Release all device memory of the handle. NULL is ignored. */
 void fmmbem_destroy(fmmbem_handle* h);
 
-/* Number of unknowns: n_panels (Laplace) or 3 n_panels (Stokes). -1 for NULL. */
+/* Number of unknowns of one vector: n_panels (Laplace) or 3 n_panels (Stokes); a batched
+ * handle's mat-vecs and solves take FMMBEM_BATCH such vectors. -1 for NULL. */
 int64_t fmmbem_n_unknowns(const fmmbem_handle* h);
 
 /* Switch the arithmetic of later mat-vecs and solves (FMMBEM_FP64 or FMMBEM_MIXED). */

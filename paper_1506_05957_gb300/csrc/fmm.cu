@@ -134,24 +134,31 @@ __global__ void __launch_bounds__(32 * P2M_WARPS) k_p2m(int p, const int* leaves
 
 // Mixed-precision P2M from the packed sources (pack_sources): each Gauss point is a float4
 // (position relative to its leaf centre, strength), so the pass does no FP64 arithmetic
-// (FP64 throughput is scarce on this GPU). Otherwise as k_p2m: a lane per Gauss point,
-// harmonics column by column, coefficients reduced across the warp into shared memory.
-// DL = true: the double layer's dipoles (two float4 per Gauss point, the moment w n in
-// .w of the first and .x, .y of the second), scattered as in k_p2m_dl.
-// MODE 2: a batch of four vectors (strengths in .w of the first float4 and .x, .y, .z of the
-// second), four expansions per cell.
+// (FP64 throughput is scarce on this GPU). Each lane carries SPL Gauss points and runs
+// their harmonic recurrences side by side; every coefficient is summed over the lane's
+// points in registers and then across the warp by one shuffle reduction, so a reduction
+// serves 32 SPL points (the reductions are dependent shuffle chains, and they bounded the
+// one-point-per-lane form). Two warps per block take the leaf's points in chunks of 32 SPL.
+// MODE 1: the double layer's dipoles (two float4 per Gauss point, the moment w n in .w of
+// the first and .x, .y of the second), scattered as in k_p2m_dl. MODE 2: a batch of four
+// vectors (strengths in .w of the first float4 and .x, .y, .z of the second), four
+// expansions per cell.
+constexpr int P2MP_WARPS = 2;
+template <int MODE> struct P2mSpl { static constexpr int v = MODE == 2 ? 2 : 4; };
+
 template <int MODE>
-__global__ void __launch_bounds__(32 * P2M_WARPS) k_p2m_packed(int p, const int* leaves, const double4* cs,
-                                                              const int2* range, const float4* srcw, int K, float* M) {
+__global__ void __launch_bounds__(32 * P2MP_WARPS) k_p2m_packed(int p, const int* leaves, const double4* cs,
+                                                               const int2* range, const float4* srcw, int K, float* M) {
     constexpr bool DL = MODE == 1;
     constexpr int NC = MODE == 2 ? 4 : 1;
+    constexpr int SPL = P2mSpl<MODE>::v;
     extern __shared__ unsigned char smem_raw[];
     float* acc = reinterpret_cast<float*>(smem_raw);  // [warps][NC][ncoef][2]
     const int nco = ncoef(p);
     const int cell = leaves[blockIdx.x];
     const int2 r = range[cell];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int q = threadIdx.x; q < P2M_WARPS * NC * nco * 2; q += blockDim.x) acc[q] = 0.f;
+    for (int q = threadIdx.x; q < P2MP_WARPS * NC * nco * 2; q += blockDim.x) acc[q] = 0.f;
     __syncthreads();
     float* wacc = acc + warp * NC * nco * 2;
     const float inv_s = (float)(1.0 / cs[cell].w);
@@ -164,60 +171,96 @@ __global__ void __launch_bounds__(32 * P2M_WARPS) k_p2m_packed(int p, const int*
             wacc[2 * qi + 1] += im;
         }
     };
-    for (int base = s0 + warp * 32; base < s1; base += P2M_WARPS * 32) {
-        const int s = base + lane;
-        float vx = 0.f, vy = 0.f, vz = 0.f, q = 0.f, c = 0.f;
-        float qb[4] = {0.f, 0.f, 0.f, 0.f};
-        cpx<float> a = mk(0.f, 0.f), b = mk(0.f, 0.f);
-        if (s < s1) {
-            if (MODE == 2) {
-                const float4 u = srcw[2 * s], u2 = srcw[2 * s + 1];
-                vx = u.x * inv_s; vy = u.y * inv_s; vz = u.z * inv_s;
-                qb[0] = u.w; qb[1] = u2.x; qb[2] = u2.y; qb[3] = u2.z;
-            } else if (DL) {
-                const float4 u = srcw[2 * s], u2 = srcw[2 * s + 1];
-                vx = u.x * inv_s; vy = u.y * inv_s; vz = u.z * inv_s;
-                const float mx = u.w * inv_s, my = u2.x * inv_s, mz = u2.y * inv_s;
-                c = mz;
-                a = mk(0.5f * mx, -0.5f * my);
-                b = mk(0.5f * mx, 0.5f * my);
-            } else {
-                const float4 u = srcw[s];
-                vx = u.x * inv_s; vy = u.y * inv_s; vz = u.z * inv_s;
-                q = u.w;
+    for (int base = s0 + warp * 32 * SPL; base < s1; base += P2MP_WARPS * 32 * SPL) {
+        float vx[SPL], vy[SPL], vz[SPL], q[SPL], c[SPL], qb[SPL][4];
+        cpx<float> a[SPL], b[SPL];
+#pragma unroll
+        for (int h = 0; h < SPL; ++h) {
+            const int s = base + 32 * h + lane;
+            vx[h] = vy[h] = vz[h] = q[h] = c[h] = 0.f;
+            qb[h][0] = qb[h][1] = qb[h][2] = qb[h][3] = 0.f;
+            a[h] = b[h] = mk(0.f, 0.f);
+            if (s < s1) {
+                if (MODE == 2) {
+                    const float4 u = srcw[2 * s], u2 = srcw[2 * s + 1];
+                    vx[h] = u.x * inv_s; vy[h] = u.y * inv_s; vz[h] = u.z * inv_s;
+                    qb[h][0] = u.w; qb[h][1] = u2.x; qb[h][2] = u2.y; qb[h][3] = u2.z;
+                } else if (DL) {
+                    const float4 u = srcw[2 * s], u2 = srcw[2 * s + 1];
+                    vx[h] = u.x * inv_s; vy[h] = u.y * inv_s; vz[h] = u.z * inv_s;
+                    const float mx = u.w * inv_s, my = u2.x * inv_s, mz = u2.y * inv_s;
+                    c[h] = mz;
+                    a[h] = mk(0.5f * mx, -0.5f * my);
+                    b[h] = mk(0.5f * mx, 0.5f * my);
+                } else {
+                    const float4 u = srcw[s];
+                    vx[h] = u.x * inv_s; vy[h] = u.y * inv_s; vz[h] = u.z * inv_s;
+                    q[h] = u.w;
+                }
             }
         }
-        auto emit = [&](int n, int m, cpx<float> R) {
+        auto emit = [&](int n, int m, const cpx<float> (&R)[SPL]) {
             if (DL) {  // R = R_n^m, n < p: feeds degree n + 1
-                add(0, n + 1, m, c * R);
-                if (m >= 1) add(0, n + 1, m - 1, a * R);
-                const cpx<float> bR = b * R;
-                add(0, n + 1, m + 1, mk(-bR.re, -bR.im));
-                if (m == 1) add(0, n + 1, 0, b * conj(R));
+                cpx<float> t0 = mk(0.f, 0.f), t1 = t0, t2 = t0, t3 = t0;
+#pragma unroll
+                for (int h = 0; h < SPL; ++h) {
+                    cfma(t0, mk(c[h], 0.f), R[h]);
+                    cfma(t1, a[h], R[h]);
+                    cfma(t2, b[h], R[h]);
+                    cfma(t3, b[h], conj(R[h]));
+                }
+                add(0, n + 1, m, t0);
+                if (m >= 1) add(0, n + 1, m - 1, t1);
+                add(0, n + 1, m + 1, mk(-t2.re, -t2.im));
+                if (m == 1) add(0, n + 1, 0, t3);
             } else if (MODE == 2) {
 #pragma unroll
-                for (int cc = 0; cc < 4; ++cc) add(cc, n, m, qb[cc] * R);
+                for (int cc = 0; cc < 4; ++cc) {
+                    cpx<float> t = mk(0.f, 0.f);
+#pragma unroll
+                    for (int h = 0; h < SPL; ++h) t = t + qb[h][cc] * R[h];
+                    add(cc, n, m, t);
+                }
             } else {
-                add(0, n, m, q * R);
+                cpx<float> t = mk(0.f, 0.f);
+#pragma unroll
+                for (int h = 0; h < SPL; ++h) t = t + q[h] * R[h];
+                add(0, n, m, t);
             }
         };
         const int nmax = DL ? p - 1 : p;  // highest degree generated
-        const float r2 = vx * vx + vy * vy + vz * vz;
-        const cpx<float> xy = mk(vx, vy);
-        cpx<float> diag = mk(1.f, 0.f);
+        float r2[SPL];
+        cpx<float> xy[SPL], diag[SPL], prev1[SPL], prev2[SPL], cur[SPL];
+#pragma unroll
+        for (int h = 0; h < SPL; ++h) {
+            r2[h] = vx[h] * vx[h] + vy[h] * vy[h] + vz[h] * vz[h];
+            xy[h] = mk(vx[h], vy[h]);
+            diag[h] = mk(1.f, 0.f);
+        }
         for (int m = 0; m <= nmax; ++m) {
-            if (m > 0) diag = (-0.5f / (float)m) * (xy * diag);
+            if (m > 0) {
+                const float f = -0.5f / (float)m;
+#pragma unroll
+                for (int h = 0; h < SPL; ++h) diag[h] = f * (xy[h] * diag[h]);
+            }
             emit(m, m, diag);
             if (m + 1 > nmax) break;
-            cpx<float> prev2 = diag, prev1 = vz * diag;
+#pragma unroll
+            for (int h = 0; h < SPL; ++h) {
+                prev2[h] = diag[h];
+                prev1[h] = vz[h] * diag[h];
+            }
             emit(m + 1, m, prev1);
             for (int n = m + 2; n <= nmax; ++n) {
-                const float inv = 1.f / (float)((n - m) * (n + m));
-                cpx<float> cur = mk(((float)(2 * n - 1) * vz * prev1.re - r2 * prev2.re) * inv,
-                                    ((float)(2 * n - 1) * vz * prev1.im - r2 * prev2.im) * inv);
+                const float inv = 1.f / (float)((n - m) * (n + m)), tn = (float)(2 * n - 1);
+#pragma unroll
+                for (int h = 0; h < SPL; ++h) {
+                    cur[h] = mk((tn * vz[h] * prev1[h].re - r2[h] * prev2[h].re) * inv,
+                                (tn * vz[h] * prev1[h].im - r2[h] * prev2[h].im) * inv);
+                    prev2[h] = prev1[h];
+                    prev1[h] = cur[h];
+                }
                 emit(n, m, cur);
-                prev2 = prev1;
-                prev1 = cur;
             }
         }
     }
@@ -227,7 +270,7 @@ __global__ void __launch_bounds__(32 * P2M_WARPS) k_p2m_packed(int p, const int*
         const int cc = idx / (nco * 2), rest = idx % (nco * 2);
         float v = 0.f;
 #pragma unroll
-        for (int w = 0; w < P2M_WARPS; ++w) v += acc[w * NC * nco * 2 + idx];
+        for (int w = 0; w < P2MP_WARPS; ++w) v += acc[w * NC * nco * 2 + idx];
         out[cc * ESTRIDE + rest] = v;
     }
 }
@@ -819,15 +862,16 @@ int far_field_t(fmmbem_handle* h, int p) {
     if (std::is_same<T, float>::value && (NC == 1 || h->nrhs > 1)) {
         // mixed precision: the packed FP32 sources
         float* Mf = reinterpret_cast<float*>(h->M);
+        const size_t smp = (size_t)P2MP_WARPS * NC * nco * 2 * sizeof(float);
         if (h->nrhs > 1)
-            k_p2m_packed<2><<<h->n_leaves, 32 * P2M_WARPS, sm, st>>>(p, h->leaves, h->cell_cs, h->cell_range,
-                                                                    h->src_w, h->K, Mf);
+            k_p2m_packed<2><<<h->n_leaves, 32 * P2MP_WARPS, smp, st>>>(p, h->leaves, h->cell_cs, h->cell_range,
+                                                                      h->src_w, h->K, Mf);
         else if (h->layer == FMMBEM_LAYER_DOUBLE)
-            k_p2m_packed<1><<<h->n_leaves, 32 * P2M_WARPS, sm, st>>>(p, h->leaves, h->cell_cs, h->cell_range,
-                                                                    h->src_w, h->K, Mf);
+            k_p2m_packed<1><<<h->n_leaves, 32 * P2MP_WARPS, smp, st>>>(p, h->leaves, h->cell_cs, h->cell_range,
+                                                                      h->src_w, h->K, Mf);
         else
-            k_p2m_packed<0><<<h->n_leaves, 32 * P2M_WARPS, sm, st>>>(p, h->leaves, h->cell_cs, h->cell_range,
-                                                                    h->src_w, h->K, Mf);
+            k_p2m_packed<0><<<h->n_leaves, 32 * P2MP_WARPS, smp, st>>>(p, h->leaves, h->cell_cs, h->cell_range,
+                                                                      h->src_w, h->K, Mf);
     } else if (NC == 1 && h->layer == FMMBEM_LAYER_DOUBLE) {
         k_p2m_dl<T><<<h->n_leaves, 32 * P2M_WARPS, sm, st>>>(p, h->leaves, h->cell_cs, h->cell_range, src, h->nrm_d,
                                                             h->xin, h->K, M);
@@ -861,7 +905,9 @@ int far_field_t(fmmbem_handle* h, int p) {
     for (int l = h->n_levels - 2; l >= 0; --l) {
         const int pb = h->parent_start[l], pe = h->parent_start[l + 1];
         if (pe == pb) continue;
-        if (tree_tc_on) {
+        // levels with fewer parents than SMs: the SIMT kernel (a persistent tensor-core launch
+        // of one or two CTAs costs more than the translations it performs)
+        if (tree_tc_on && pe - pb >= h->n_sm) {
             FMM_TRY(tree_tc(h, p, l, 0));
             ++nl;
         } else {
@@ -889,7 +935,7 @@ int far_field_t(fmmbem_handle* h, int p) {
     for (int l = 0; l + 1 < h->n_levels; ++l) {
         const int pb = h->parent_start[l], pe = h->parent_start[l + 1];
         if (pe == pb) continue;
-        if (tree_tc_on) {
+        if (tree_tc_on && pe - pb >= h->n_sm) {
             FMM_TRY(tree_tc(h, p, l, 1));
         } else {
             k_l2l<T, NC><<<pe - pb, TREE_THREADS, sm_l2l, st>>>(p, h->parents + pb, h->cell_cs, h->cell_child, oct, L);
@@ -905,7 +951,8 @@ int far_field_t(fmmbem_handle* h, int p) {
 template <typename T, int NC>
 int far_eval_t(fmmbem_handle* h, int p, double* y_sorted, double scale) {
     prof_begin(h, FMMBEM_PASS_L2P);
-    k_l2p<T, NC><<<h->n_leaves, 128, 0, h->stream>>>(p, h->leaves, h->cell_cs, h->cell_range, h->tgt_d,
+    // one warp per leaf: a leaf holds about 20 targets (a 128-thread block left most threads idle)
+    k_l2p<T, NC><<<h->n_leaves, 32, 0, h->stream>>>(p, h->leaves, h->cell_cs, h->cell_range, h->tgt_d,
                                                     reinterpret_cast<const T*>(h->L), h->ynear, scale, h->origin[0],
                                                     h->origin[1], h->origin[2],
                                                     h->layer == FMMBEM_LAYER_DOUBLE ? h->xin : nullptr,
