@@ -905,9 +905,7 @@ int far_field_t(fmmbem_handle* h, int p) {
     for (int l = h->n_levels - 2; l >= 0; --l) {
         const int pb = h->parent_start[l], pe = h->parent_start[l + 1];
         if (pe == pb) continue;
-        // levels with fewer parents than SMs: the SIMT kernel (a persistent tensor-core launch
-        // of one or two CTAs costs more than the translations it performs)
-        if (tree_tc_on && pe - pb >= h->n_sm) {
+        if (tree_tc_on) {
             FMM_TRY(tree_tc(h, p, l, 0));
             ++nl;
         } else {
@@ -935,7 +933,7 @@ int far_field_t(fmmbem_handle* h, int p) {
     for (int l = 0; l + 1 < h->n_levels; ++l) {
         const int pb = h->parent_start[l], pe = h->parent_start[l + 1];
         if (pe == pb) continue;
-        if (tree_tc_on && pe - pb >= h->n_sm) {
+        if (tree_tc_on) {
             FMM_TRY(tree_tc(h, p, l, 1));
         } else {
             k_l2l<T, NC><<<pe - pb, TREE_THREADS, sm_l2l, st>>>(p, h->parents + pb, h->cell_cs, h->cell_child, oct, L);
