@@ -137,13 +137,16 @@ __global__ void __launch_bounds__(32 * P2M_WARPS) k_p2m(int p, const int* leaves
 // (FP64 throughput is scarce on this GPU). Each lane carries SPL Gauss points and runs
 // their harmonic recurrences side by side; every coefficient is summed over the lane's
 // points in registers and then across the warp by one shuffle reduction, so a reduction
-// serves 32 SPL points (the reductions are dependent shuffle chains, and they bounded the
-// one-point-per-lane form). Two warps per block take the leaf's points in chunks of 32 SPL.
+// serves 32 SPL points. The block's warps split the harmonic columns m (every warp walks
+// all of the leaf's points and runs the cheap diagonal recurrence, but only the owner of
+// column m runs and reduces its n-recurrence): a leaf holds one or two chunks of points, so
+// splitting the points left one warp doing all the work while the others waited (ncu:
+// barrier stalls, 14 of 64 warps active).
 // MODE 1: the double layer's dipoles (two float4 per Gauss point, the moment w n in .w of
 // the first and .x, .y of the second), scattered as in k_p2m_dl. MODE 2: a batch of four
 // vectors (strengths in .w of the first float4 and .x, .y, .z of the second), four
 // expansions per cell.
-constexpr int P2MP_WARPS = 2;
+constexpr int P2MP_WARPS = 4;
 template <int MODE> struct P2mSpl { static constexpr int v = MODE == 2 ? 2 : 4; };
 
 template <int MODE>
@@ -171,7 +174,13 @@ __global__ void __launch_bounds__(32 * P2MP_WARPS) k_p2m_packed(int p, const int
             wacc[2 * qi + 1] += im;
         }
     };
-    for (int base = s0 + warp * 32 * SPL; base < s1; base += P2MP_WARPS * 32 * SPL) {
+    // column m belongs to warp w in a snake order (0 1 2 3 3 2 1 0 0 ...), which balances the
+    // column lengths p - m + 1 between the warps
+    auto owns = [&](int m) {
+        const int qd = m / P2MP_WARPS, rm = m - qd * P2MP_WARPS;
+        return ((qd & 1) ? P2MP_WARPS - 1 - rm : rm) == warp;
+    };
+    for (int base = s0; base < s1; base += 32 * SPL) {
         float vx[SPL], vy[SPL], vz[SPL], q[SPL], c[SPL], qb[SPL][4];
         cpx<float> a[SPL], b[SPL];
 #pragma unroll
@@ -243,8 +252,9 @@ __global__ void __launch_bounds__(32 * P2MP_WARPS) k_p2m_packed(int p, const int
 #pragma unroll
                 for (int h = 0; h < SPL; ++h) diag[h] = f * (xy[h] * diag[h]);
             }
+            if (!owns(m)) continue;
             emit(m, m, diag);
-            if (m + 1 > nmax) break;
+            if (m + 1 > nmax) continue;
 #pragma unroll
             for (int h = 0; h < SPL; ++h) {
                 prev2[h] = diag[h];
