@@ -112,3 +112,46 @@ def test_fullsize_stokes_matvec_and_drag(torch_cuda):
     assert F < 0 and abs(F / (-6.0 * np.pi) - 1.0) < 5e-3
     res = M.stokes_apply(tr.reshape(-1), rows=rows).reshape(-1) - U.reshape(-1, 3)[rows].reshape(-1)
     assert np.linalg.norm(res) / np.linalg.norm(U.reshape(-1, 3)[rows]) < 2e-5
+
+
+def test_64_red_blood_cells_stokes(torch_cuda):
+    """Stokes flow around 64 red blood cells: Evans-Fung surfaces of 2048 panels each
+    (131072 panels, 393216 unknowns), random non-overlapping placement (gap >= 0.5) in a cube
+    of side 40, U = (1, 0, 0), K = 3, relaxed p 16 -> 4, tol 1e-5, mixed precision. Sampled
+    rows of the p = 16 mat-vec against the oracle's Stokeslet rows; the solve's true residual
+    and sampled oracle residual; every cell's drag opposes the flow."""
+    torch = torch_cuda
+    from oracle import dense, panels
+    from oracle.schedule import schedule
+    from synth import evans_fung_cell, place_cells
+    from paper_1506_05957_gb300 import FmmBem, FMMBEM_MIXED, FMMBEM_STOKES
+    cv, ct = evans_fung_cell(4)
+    v, t, body = place_cells(cv, ct, 64, box=40.0, min_gap=0.5, seed=0)
+    assert len(t) == 131072
+    _, _, S = panels.geometry(v, t)
+    mu = 1e-3
+    h = FmmBem(v, t, kernel=FMMBEM_STOKES, gauss_k=3, ncrit=150, theta=0.5, p_max=16, mu=mu,
+               precision=FMMBEM_MIXED)
+    M = dense.Mesh(v, t, k=3)
+    rows = np.sort(np.random.default_rng(7).choice(len(t), 64, replace=False))
+    x = np.random.default_rng(8).standard_normal(h.n)
+    xd = torch.tensor(x, dtype=torch.float64, device="cuda")
+    y = torch.zeros_like(xd)
+    h.matvec(16, xd, y)
+    ref = M.stokes_apply(x, mu=mu, rows=rows).reshape(-1)
+    got = y.cpu().numpy().reshape(-1, 3)[rows].reshape(-1)
+    print("64 cells p16 sampled rel L2", np.linalg.norm(got - ref) / np.linalg.norm(ref))
+    assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < 1e-5
+    U = np.tile([1.0, 0.0, 0.0], len(t))
+    b = torch.tensor(U, dtype=torch.float64, device="cuda")
+    sol = torch.zeros_like(b)
+    r = h.solve(b, sol, tol=1e-5, relax=True, p_initial=16, p_min=4)
+    print("64 cells iters", r["iters"], r["p_hist"], "true residual", r["true_res"])
+    assert r["converged"] and r["true_res"] < 2e-5
+    assert r["p_hist"] == schedule(1e-5, r["res_hist"][:-1], 16, 4)
+    tr = sol.cpu().numpy().reshape(-1, 3)
+    res = M.stokes_apply(tr.reshape(-1), mu=mu, rows=rows).reshape(-1) - U.reshape(-1, 3)[rows].reshape(-1)
+    assert np.linalg.norm(res) / np.linalg.norm(U.reshape(-1, 3)[rows]) < 2e-5
+    drag = np.bincount(np.asarray(body), weights=tr[:, 0] * S, minlength=64)
+    print("per-cell drag range", drag.min(), drag.max())
+    assert np.all(drag < 0)
