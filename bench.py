@@ -44,15 +44,18 @@ def parse():
     ap.add_argument("--ncrit", type=int, default=WORKLOAD["ncrit"])
     ap.add_argument("--no-compare", action="store_true", help="skip the FP64 comparison solves")
     ap.add_argument("--problem", default="laplace",
-                    choices=["laplace", "stokes", "serve", "laplace2", "sweeps", "batch"],
+                    choices=["laplace", "stokes", "serve", "laplace2", "sweeps", "batch", "rbc64"],
                     help="laplace: the headline workload; stokes: Stokes flow past a sphere of 81920 panels; "
                          "serve: a Poisson stream of mixed solves through the serving runtime; "
                          "laplace2: second-kind Laplace solves on octahedron spheres of 8192-131072 panels; "
                          "sweeps: the paper's parameter studies (initial p, tolerance, p_min, red blood cell); "
-                         "batch: four right-hand sides in one batched solve against four single solves")
+                         "batch: four right-hand sides in one batched solve against four single solves; "
+                         "rbc64: Stokes flow around 64 red blood cells (131072 panels)")
     ap.add_argument("--requests", type=int, default=48, help="serve: number of requests")
     ap.add_argument("--rate", type=float, default=20.0, help="serve: mean arrival rate (requests/s)")
     ap.add_argument("--max-active", type=int, default=6, help="serve: concurrent solves")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="laplace: keep the default per-order tensor-core choices instead of fmmbem_autotune's")
     return ap.parse_args()
 
 
@@ -255,6 +258,8 @@ def run_ours(args, world, rank, local):
     b = torch.empty_like(phi_d)
     h.rhs(phi_d, b)
     x = torch.zeros_like(b)
+    # per-order choice of tensor-core or SIMT translations (part of setup, untimed)
+    tuned = None if args.no_autotune else h.autotune(W["p_min"], W["p_initial"])
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     solve = lambda: h.solve(b, x, tol=W["tol"], relax=True, p_initial=W["p_initial"], p_min=W["p_min"])
 
@@ -364,6 +369,7 @@ def run_ours(args, world, rank, local):
            "config": dict(W, ncrit=args.ncrit, panels=n, parallelism="replicas" if world > 1 else "single",
                           l2="flushed between steps (512 MB write)", precision="mixed"),
            "matvec_per_s": mv_per_s, "iters": iters, "p_hist": r["p_hist"], "true_residual": r["true_res"],
+           "autotune": tuned,
            "gpu_launches": launches,
            "e2e": {"value": e2e, "unit": "s", "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 8 * n},
            "roofline": roofline, "clocks": clocks,
@@ -770,6 +776,67 @@ def run_batch(args, world, rank, local):
     batch.close()
 
 
+def run_rbc64(args, world, rank, local):
+    """Stokes flow around 64 red blood cells (Evans-Fung surfaces of 2048 panels, 131072
+    panels, 393216 unknowns, random non-overlapping placement with gap >= 0.5 in a cube of
+    side 40, seed 0), U = (1, 0, 0), mu = 1e-3, relaxed p 16 -> 4 against fixed p = 16, tol
+    1e-5, mixed precision (the paper's Table multiple_cell_relaxation_results_2048, last row:
+    1481 s relaxed, 7078 s fixed on its CPU). value = seconds per relaxed solve."""
+    import torch
+    from synth import evans_fung_cell, place_cells
+    from paper_1506_05957_gb300 import FmmBem, FMMBEM_MIXED, FMMBEM_STOKES, build
+    build.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    cv, ct = evans_fung_cell(4)
+    v, t, body = place_cells(cv, ct, 64, box=40.0, min_gap=0.5, seed=0)
+    p3 = v[t]
+    area = 0.5 * np.linalg.norm(np.cross(p3[:, 1] - p3[:, 0], p3[:, 2] - p3[:, 0]), axis=1)
+    h = FmmBem(v, t, kernel=FMMBEM_STOKES, gauss_k=3, ncrit=args.ncrit, theta=0.5, p_max=16, mu=1e-3, restart=50,
+               max_iter=100, precision=FMMBEM_MIXED, stream=stream.cuda_stream)
+    b = torch.tensor(np.tile([1.0, 0.0, 0.0], len(t)), dtype=torch.float64, device=dev)
+    x = torch.zeros_like(b)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def timed(relax, steps):
+        ts, r = [], None
+        for k in range(steps):
+            flush.fill_(float(k))
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            r = h.solve(b, x, tol=1e-5, relax=relax, p_initial=16, p_min=4)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            ts.append(e0.elapsed_time(e1))
+        return float(np.median(ts)) / 1e3, r
+
+    for _ in range(max(1, args.warmup)):
+        h.solve(b, x, tol=1e-5, relax=True, p_initial=16, p_min=4)
+    h.solve(b, x, tol=1e-5, relax=False, p_initial=16, p_min=4)
+    torch.cuda.synchronize(dev)
+    sampler = ClockSampler(local)
+    sampler.start()
+    t_rel, r_rel = timed(True, args.steps)
+    clocks = sampler.stop()
+    drag = np.bincount(np.asarray(body), weights=x.cpu().numpy().reshape(-1, 3)[:, 0] * area, minlength=64)
+    t_fix, r_fix = timed(False, max(1, min(3, args.steps)))
+    out = {"metric": "relaxed GMRES solve s, Stokes flow around 64 red blood cells (131072 panels, 393216 unknowns)"
+                     " @1e-5", "value": t_rel, "unit": "s", "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f32+f64", "data": "synthetic",
+           "config": {"workload": "stokes-64-rbc-131072", "panels": len(t), "unknowns": 3 * len(t), "gauss_k": 3,
+                      "theta": 0.5, "ncrit": args.ncrit, "p_initial": 16, "p_min": 4, "tol": 1e-5, "mu": 1e-3,
+                      "placement": "seed 0, cube 40, gap 0.5"},
+           "iters": r_rel["iters"], "p_hist": r_rel["p_hist"], "true_residual": r_rel["true_res"],
+           "fixed_p16_s": t_fix, "fixed_p16_iters": r_fix["iters"], "relaxation_speedup": t_fix / t_rel,
+           "drag_total": float(drag.sum()), "drag_per_cell_range": [float(drag.min()), float(drag.max())],
+           "paper_cpu_s": {"relaxed": 1481.47, "fixed": 7077.77, "speedup": 4.78}, "clocks": clocks}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    h.close()
+
+
 def serve_requests(n, seed=0):
     """Mixed solve requests: Laplace or Stokes on spheres (1280-81920 panels), ellipsoids
     (semi-axes U[0.5, 2]) or clusters of 1-16 red-blood-cell surfaces (2048 panels each),
@@ -866,6 +933,8 @@ def main():
         run_sweeps(args, world, rank, local)
     elif args.problem == "batch":
         run_batch(args, world, rank, local)
+    elif args.problem == "rbc64":
+        run_rbc64(args, world, rank, local)
     else:
         run_ours(args, world, rank, local)
     if world > 1:

@@ -146,6 +146,16 @@ int fmmbem_set_m2l_mode(fmmbem_handle* h, int mode);
  * tree_min_p 6 (measured on the 81920-panel sphere). FMMBEM_EINVAL for values below 1. */
 int fmmbem_set_tc_thresholds(fmmbem_handle* h, int m2l_min_p, int tree_min_p);
 
+/* Autotuner: for every order p in [p_lo, p_hi], time the handle's mat-vec (its captured
+ * graph, on the handle's stream) with M2L and with M2M/L2L on the tensor cores or on the SIMT
+ * kernels (four configurations, three timed runs each after a capture run) and keep the
+ * fastest per p. choice (optional, [p_max + 1] ints, host): 2 * (M2L on tensor cores) +
+ * (M2M/L2L on tensor cores) for each tuned p. The sums are the same in every configuration
+ * (FP32 passes, 3xTF32 products). Synchronizes the handle's stream; does nothing but report
+ * the current choices for FMMBEM_FP64 handles or without tensor-core tables. Errors:
+ * FMMBEM_EINVAL, FMMBEM_EDEVICE. */
+int fmmbem_autotune(fmmbem_handle* h, int p_lo, int p_hi, int* choice);
+
 /* Near-field kernel of FMMBEM_MIXED Laplace mat-vecs (same sums, different schedules):
  * 0 = source tiles staged in shared memory, targets held per lane;
  * 1 = (target, source slice) per thread, sources read through L1;

@@ -90,6 +90,7 @@ def lib():
         L.fmmbem_solve_batch.argtypes = [_vp, _vp, ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, _vp,
                                          _vp, _vp, _vp]
         L.fmmbem_set_tc_thresholds.argtypes = [_vp, ctypes.c_int, ctypes.c_int]
+        L.fmmbem_autotune.argtypes = [_vp, ctypes.c_int, ctypes.c_int, _vp]
         L.fmmbem_estimate_bytes.argtypes = [ctypes.c_int64, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                             ctypes.POINTER(fmmbem_opts)]
         L.fmmbem_estimate_bytes.restype = ctypes.c_int64
@@ -195,6 +196,7 @@ class FmmBem:
         self.kernel = kernel
         self.max_iter = max_iter
         self.nrhs = int(nrhs)
+        self.p_max = int(p_max)
         self.n = int(lib().fmmbem_n_unknowns(h)) * self.nrhs  # doubles per mat-vec vector (all of a batch)
         self.n_panels = len(t)
 
@@ -215,6 +217,13 @@ class FmmBem:
     def set_tc_thresholds(self, m2l_min_p, tree_min_p):
         """Lowest p at which M2L and M2M/L2L run on the tensor cores (mixed precision)."""
         _check(lib().fmmbem_set_tc_thresholds(self.h, int(m2l_min_p), int(tree_min_p)))
+
+    def autotune(self, p_lo=1, p_hi=None):
+        """fmmbem_autotune: per-order choice of tensor-core or SIMT M2L and M2M/L2L; returns {p: choice}."""
+        p_hi = self.p_max if p_hi is None else p_hi
+        ch = np.full(FMMBEM_P_MAX + 1, -1, dtype=np.int32)
+        _check(lib().fmmbem_autotune(self.h, int(p_lo), int(p_hi), _vp(ch.ctypes.data)))
+        return {p: int(ch[p]) for p in range(p_lo, p_hi + 1)}
 
     def set_p2p_variant(self, variant):
         _check(lib().fmmbem_set_p2p_variant(self.h, int(variant)))

@@ -202,7 +202,7 @@ static int matvec_launch(fmmbem_handle* h, int p, const double* xs, double* ys);
 // per order p; the graph is recaptured when the arithmetic or kernel selection changed.
 int matvec_sorted(fmmbem_handle* h, int p, const double* xs, double* ys) {
     const int mode = h->precision * 16 + h->m2l_mode + 4 * h->p2p_variant + 64 * (h->prof_on ? 1 : 0) + 128 * h->layer +
-                     256 * (p >= h->tc_min_p) + 512 * (p >= h->tree_tc_min_p);
+                     256 * h->m2l_tc_at[p] + 512 * h->tree_tc_at[p];
     if (!h->use_graphs || xs != h->xfix || ys != h->kw || h->stream == nullptr)
         return matvec_launch(h, p, xs, ys);
     prof_harvest(h);
@@ -355,6 +355,10 @@ int fmmbem_create(const fmmbem_mesh* mesh, int kernel, int gauss_k, int ncrit, d
         });
     }
     h->kernel = kernel;
+    for (int q = 0; q <= FMMBEM_P_MAX; ++q) {  // defaults measured on the 81920-panel sphere
+        h->m2l_tc_at[q] = 1;
+        h->tree_tc_at[q] = q >= 6;
+    }
     h->dof = kernel == FMMBEM_STOKES ? 3 : 1;
     h->nrhs = o.nrhs;
     h->ncomp = kernel == FMMBEM_STOKES ? 4 : o.nrhs;
@@ -452,9 +456,58 @@ int fmmbem_set_layer(fmmbem_handle* h, int layer) {
 
 int fmmbem_set_tc_thresholds(fmmbem_handle* h, int m2l_min_p, int tree_min_p) {
     if (!h || m2l_min_p < 1 || tree_min_p < 1) { fmmbem_set_error("bad tensor-core threshold"); return FMMBEM_EINVAL; }
-    h->tc_min_p = m2l_min_p;
-    h->tree_tc_min_p = tree_min_p;
+    for (int q = 0; q <= FMMBEM_P_MAX; ++q) {
+        h->m2l_tc_at[q] = q >= m2l_min_p;
+        h->tree_tc_at[q] = q >= tree_min_p;
+    }
     return 0;
+}
+
+int fmmbem_autotune(fmmbem_handle* h, int p_lo, int p_hi, int* choice) {
+    if (!h || p_lo < 1 || p_hi > h->opts.p_max || p_lo > p_hi) { fmmbem_set_error("need 1 <= p_lo <= p_hi <= p_max"); return FMMBEM_EINVAL; }
+    if (h->precision != FMMBEM_MIXED || !h->m2l_tc_ready || h->m2l_mode != FMMBEM_M2L_TENSOR) {
+        for (int p = p_lo; p <= p_hi; ++p)
+            if (choice) choice[p] = 2 * h->m2l_tc_at[p] + h->tree_tc_at[p];
+        return 0;  // nothing to choose: the tensor-core paths are not in use
+    }
+    // the solver's fixed mat-vec buffers carry the timed products (zero input: no kernel has a
+    // data-dependent path, so the timing is that of any input)
+    FMM_CU(cudaMemsetAsync(h->xfix, 0, sizeof(double) * h->N * h->dof * h->nrhs, h->stream));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    FMM_CU(cudaEventCreate(&e0));
+    FMM_CU(cudaEventCreate(&e1));
+    int rc = 0;
+    for (int p = p_lo; p <= p_hi && rc == 0; ++p) {
+        float best = 0.f;
+        int best_cfg = 3;
+        for (int cfg = 3; cfg >= 0 && rc == 0; --cfg) {  // bit 1: M2L, bit 0: M2M/L2L on the tensor cores
+            h->m2l_tc_at[p] = (cfg >> 1) & 1;
+            h->tree_tc_at[p] = cfg & 1;
+            float ms = 0.f;
+            for (int rep = 0; rep < 4 && rc == 0; ++rep) {  // the first run captures the graph
+                if (cudaEventRecord(e0, h->stream) != cudaSuccess) { rc = FMMBEM_EDEVICE; break; }
+                rc = matvec_sorted(h, p, h->xfix, h->kw);
+                if (rc < 0) break;
+                if (cudaEventRecord(e1, h->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) {
+                    rc = FMMBEM_EDEVICE;
+                    break;
+                }
+                float t = 0.f;
+                cudaEventElapsedTime(&t, e0, e1);
+                if (rep > 0) ms += t;
+            }
+            if (rc == 0 && (cfg == 3 || ms < best)) {
+                best = ms;
+                best_cfg = cfg;
+            }
+        }
+        h->m2l_tc_at[p] = (best_cfg >> 1) & 1;
+        h->tree_tc_at[p] = best_cfg & 1;
+        if (choice) choice[p] = best_cfg;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return rc < 0 ? rc : 0;
 }
 
 int fmmbem_set_p2p_variant(fmmbem_handle* h, int variant) {

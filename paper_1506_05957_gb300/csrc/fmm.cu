@@ -903,7 +903,7 @@ int far_field_t(fmmbem_handle* h, int p) {
     prof_end(h, FMMBEM_PASS_P2M, 1);
     // tensor-core tree translations in the mixed-precision M2L-TENSOR mode
     const bool tree_tc_on = std::is_same<T, float>::value && h->m2l_mode == FMMBEM_M2L_TENSOR && h->m2l_tc_ready &&
-                            h->tree_tiles != nullptr && p >= h->tree_tc_min_p;
+                            h->tree_tiles != nullptr && h->tree_tc_at[p];
     // M2M, deepest non-leaf level first
     prof_begin(h, FMMBEM_PASS_M2M);
     int nl = 0;
@@ -927,7 +927,7 @@ int far_field_t(fmmbem_handle* h, int p) {
     prof_end(h, FMMBEM_PASS_M2M, nl);
     // M2L
     prof_begin(h, FMMBEM_PASS_M2L);
-    if (std::is_same<T, float>::value && h->m2l_mode == FMMBEM_M2L_TENSOR && h->m2l_tc_ready && p >= h->tc_min_p) {
+    if (std::is_same<T, float>::value && h->m2l_mode == FMMBEM_M2L_TENSOR && h->m2l_tc_ready && h->m2l_tc_at[p]) {
         FMM_TRY(m2l_tc(h, p));
     } else if (h->m2l_mode != FMMBEM_M2L_GATHER && h->m2l_tables) {
         FMM_TRY(m2l_gemm(h, p, !std::is_same<T, float>::value));

@@ -83,9 +83,10 @@ struct fmmbem_handle {
     // tensor-core (tcgen05) path: operators split into TF32 hi/lo, K-chunked core-matrix layout
     bool m2l_tc_ready = false;
     int m2l_mode = FMMBEM_M2L_TABLES;
-    int tc_min_p = 1;             // mixed-precision M2L at p >= tc_min_p runs on the tensor cores
-    int tree_tc_min_p = 6;        // mixed-precision M2M/L2L at p >= tree_tc_min_p run on the tensor cores
-                                  // (below it the per-parent SIMT kernels, which share SMs with the near field)
+    // per order p, mixed precision: M2L (m2l_tc_at) and M2M/L2L (tree_tc_at) on the tensor cores
+    // (1) or on the SIMT kernels (0); set by fmmbem_set_tc_thresholds or fmmbem_autotune
+    unsigned char m2l_tc_at[FMMBEM_P_MAX + 1] = {};
+    unsigned char tree_tc_at[FMMBEM_P_MAX + 1] = {};
     float* tab_tc = nullptr;
     size_t tc_stride = 0;
     int tc_rows_max = 0;

@@ -258,3 +258,21 @@ def test_p2p_variants_agree(torch_cuda, sphere1280, ncrit):
     with pytest.raises(Exception):
         h.set_p2p_variant(4)
 
+
+
+def test_autotune_keeps_results(torch_cuda, sphere1280):
+    """The autotuner only chooses between tensor-core and SIMT translations per order p: the
+    solve after tuning matches the oracle as before, and every choice is one of the four."""
+    torch = torch_cuda
+    s = sphere1280
+    h = _h(torch, s["v"], s["t"], p_max=12)
+    ch = h.autotune(3, 12)
+    print("autotune choices", ch)
+    assert set(ch) == set(range(3, 13)) and all(c in (0, 1, 2, 3) for c in ch.values())
+    b = _dev(torch, s["b"])
+    x = torch.zeros_like(b)
+    r = h.solve(b, x, tol=1e-6, relax=True, p_initial=10, p_min=3)
+    assert r["converged"]
+    assert rel(x.cpu().numpy(), s["x_lu"]) < 1e-5
+    with pytest.raises(Exception):
+        h.autotune(0, 5)
