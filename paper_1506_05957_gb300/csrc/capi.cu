@@ -387,6 +387,8 @@ int fmmbem_create(const fmmbem_mesh* mesh, int kernel, int gauss_k, int ncrit, d
     if (rc < 0) return fail(rc);
     rc = init_octant_tables(h);
     if (rc < 0) return fail(rc);
+    rc = init_near_attrs();
+    if (rc < 0) return fail(rc);
     rc = build_m2l_tables(h);
     if (rc < 0) return fail(rc);
     rc = build_m2l_tc(h);

@@ -186,6 +186,7 @@ int expansion_eval(int kind, int p, const double* center, double scale, int n_sr
                    int n_tgt, const double* tgt, double* out, cudaStream_t st);
 int init_octant_tables(fmmbem_handle* h);
 // near.cu
+int init_near_attrs();
 int pack_sources(fmmbem_handle* h);
 int near_field(fmmbem_handle* h, bool fp64, cudaStream_t st);
 int direct_field(fmmbem_handle* h, bool fp64, int which, const double* x_sorted, double* y_sorted);

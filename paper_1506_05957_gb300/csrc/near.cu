@@ -652,78 +652,141 @@ __global__ void __launch_bounds__(128) k_p2p_lap_bulk(const int* leaves, const i
 //   FP32 accumulator per target in registers.
 // - Every PS_FOLD rounds the accumulators are folded into per-lane compensated (hi, lo)
 //   sums in shared memory.
-// - At the end thread i adds target i's partials of all lanes, compensated, applies the
-//   FP64 correction row and writes the result.
+// - At the end lane i of every warp adds target i's partials of the warp's lanes, then
+//   thread i adds the warp sums (both compensated), applies the FP64 correction row and
+//   writes the result.
 constexpr int PS_WARPS = 4;
 constexpr int PS_TMAX = P2P_SRC_TMAX;  // targets per block (a leaf's targets are split into chunks of at most this)
 constexpr int PS_EMAX = 64;   // pair records per shared-memory chunk
 constexpr int PS_FOLD = 8;    // rounds between folds (32 terms per lane and target)
+static_assert(PS_TMAX <= 32, "the epilogue gives each target of a block one lane per warp");
 
+// Pair records are staged per warp, so the warps of a block never wait for one another
+// between the target load and the epilogue. Targets are stored in pairs: (x_a, x_b, y_a, y_b)
+// and (z_a, z_b).
 struct PsShared {
-    float4 t[PS_TMAX];
+    float4 txy[PS_TMAX / 2];
+    float2 tz[PS_TMAX / 2];
     float2 hl[PS_WARPS][PS_TMAX][32];
-    float4 rec[PS_EMAX];
-    int off[PS_EMAX + 1];
+    float4 rec[PS_WARPS][PS_EMAX];
+    int off[PS_WARPS][PS_EMAX + 1];
+    float2 wsum[PS_WARPS][PS_TMAX];
 };
+static_assert(PS_TMAX % 4 == 0, "targets are processed in groups of four");
 
-__device__ __forceinline__ void ps_fold(float* acc, float2* hl, int ntb, int lane) {
+// Two FP32 values in one 64-bit register, operated on by the paired FP32 instructions of
+// sm_100-family GPUs (PTX .f32x2): one instruction applies the same operation to both halves,
+// each rounded as the scalar FP32 operation, which halves the issue slots of the arithmetic.
+typedef unsigned long long f32x2;
+__device__ __forceinline__ f32x2 f2_pack(float a, float b) {
+    f32x2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void f2_unpack(f32x2 v, float& a, float& b) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+}
+__device__ __forceinline__ f32x2 f2_sub(f32x2 a, f32x2 b) {
+    f32x2 d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f32x2 f2_mul(f32x2 a, f32x2 b) {
+    f32x2 d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f32x2 f2_fma(f32x2 a, f32x2 b, f32x2 c) {
+    f32x2 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+
+// A source of the round, each component repeated in both halves.
+struct PsSrc {
+    f32x2 x, y, z, w;
+};
+__device__ __forceinline__ PsSrc ps_src(float4 u) {
+    return {f2_pack(u.x, u.x), f2_pack(u.y, u.y), f2_pack(u.z, u.z), f2_pack(u.w, u.w)};
+}
+
+// acc[j] holds the running sums of targets 2j and 2j + 1.
+__device__ __forceinline__ void ps_fold(f32x2* acc, float2* hl, int ntb, int lane) {
 #pragma unroll
-    for (int i = 0; i < PS_TMAX; ++i) {
-        if (i < ntb) {
-            float2 v = hl[i * 32 + lane];
-            kahan_add(v.x, v.y, acc[i]);
-            hl[i * 32 + lane] = v;
+    for (int j = 0; j < PS_TMAX / 2; ++j) {
+        float a0, a1;
+        f2_unpack(acc[j], a0, a1);
+        if (2 * j < ntb) {
+            float2 v = hl[2 * j * 32 + lane];
+            kahan_add(v.x, v.y, a0);
+            hl[2 * j * 32 + lane] = v;
         }
-        acc[i] = 0.f;
+        if (2 * j + 1 < ntb) {
+            float2 v = hl[(2 * j + 1) * 32 + lane];
+            kahan_add(v.x, v.y, a1);
+            hl[(2 * j + 1) * 32 + lane] = v;
+        }
+        acc[j] = 0ull;
         asm volatile("" ::: "memory");
     }
 }
 
-// The target loop runs over groups of four targets, fully unrolled (so the accumulators
-// stay in registers) with one uniform branch per group; the target count of a pass is
-// padded to a multiple of four with far-away dummy targets whose sums are never read.
-// Each lane holds PS_SRC sources per round; every source costs 3 subtractions, the
-// squared distance (mul + 2 fma), one rsqrt and one fma into the accumulator.
+// The target loop runs over groups of four targets (two pairs), fully unrolled (so the
+// accumulators stay in registers) with one uniform branch per group; the target count of a
+// pass is padded to a multiple of four with far-away dummy targets whose sums are never read.
+// Each lane holds PS_SRC sources per round; per source and target pair: 3 paired
+// subtractions, the squared distances (paired mul + 2 paired fma), two rsqrt and one paired
+// fma into the accumulators.
 constexpr int PS_SRC = 4;
 
-__device__ __forceinline__ void ps_round(const float4* sT, int ntb, const float4 (&u)[PS_SRC], float* acc) {
+__device__ __forceinline__ void ps_round(const float4* sXY, const float2* sZ, int ntb, const PsSrc (&u)[PS_SRC],
+                                         f32x2* acc) {
 #pragma unroll
     for (int g = 0; g < PS_TMAX; g += 4) {
         if (g < ntb) {
 #pragma unroll
-            for (int i = g; i < g + 4; ++i) {
-                const float4 x = sT[i];
-                float a = acc[i];
+            for (int j = g / 2; j < g / 2 + 2; ++j) {
+                const float4 A = sXY[j];
+                const float2 B = sZ[j];
+                const f32x2 tx = f2_pack(A.x, A.y), ty = f2_pack(A.z, A.w), tz = f2_pack(B.x, B.y);
+                f32x2 a = acc[j];
 #pragma unroll
                 for (int h = 0; h < PS_SRC; ++h) {
-                    const float dx = x.x - u[h].x, dy = x.y - u[h].y, dz = x.z - u[h].z;
-                    a = fmaf(u[h].w, rsqrt_approx(fmaf(dx, dx, fmaf(dy, dy, dz * dz))), a);
+                    const f32x2 dx = f2_sub(tx, u[h].x), dy = f2_sub(ty, u[h].y), dz = f2_sub(tz, u[h].z);
+                    float r0, r1;
+                    f2_unpack(f2_fma(dx, dx, f2_fma(dy, dy, f2_mul(dz, dz))), r0, r1);
+                    a = f2_fma(u[h].w, f2_pack(rsqrt_approx(r0), rsqrt_approx(r1)), a);
                 }
-                acc[i] = a;
+                acc[j] = a;
             }
         }
         asm volatile("" ::: "memory");  // keeps the next group's target loads from being hoisted (register pressure)
     }
 }
 
-__device__ __forceinline__ void ps_round_self(const float4* sT, int ntb, int tb, const float4 (&u)[PS_SRC],
-                                              const int (&gp)[PS_SRC], float* acc) {
+// The own leaf: a source on the target's own panel contributes nothing.
+__device__ __forceinline__ void ps_round_self(const float4* sXY, const float2* sZ, int ntb, int tb,
+                                              const PsSrc (&u)[PS_SRC], const int (&gp)[PS_SRC], f32x2* acc) {
 #pragma unroll
     for (int g = 0; g < PS_TMAX; g += 4) {
         if (g < ntb) {
 #pragma unroll
-            for (int i = g; i < g + 4; ++i) {
-                const float4 x = sT[i];
-                const int own = tb + i;
-                float a = acc[i];
+            for (int j = g / 2; j < g / 2 + 2; ++j) {
+                const float4 A = sXY[j];
+                const float2 B = sZ[j];
+                const f32x2 tx = f2_pack(A.x, A.y), ty = f2_pack(A.z, A.w), tz = f2_pack(B.x, B.y);
+                const int own = tb + 2 * j;
+                f32x2 a = acc[j];
 #pragma unroll
                 for (int h = 0; h < PS_SRC; ++h) {
-                    const float dx = x.x - u[h].x, dy = x.y - u[h].y, dz = x.z - u[h].z;
-                    const bool sk = gp[h] == own;  // the target's own panel
-                    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                    a = fmaf(sk ? 0.f : u[h].w, rsqrt_approx(sk ? 1.f : r2), a);
+                    const f32x2 dx = f2_sub(tx, u[h].x), dy = f2_sub(ty, u[h].y), dz = f2_sub(tz, u[h].z);
+                    float r0, r1;
+                    f2_unpack(f2_fma(dx, dx, f2_fma(dy, dy, f2_mul(dz, dz))), r0, r1);
+                    const bool s0 = gp[h] == own, s1 = gp[h] == own + 1;
+                    const float i0 = rsqrt_approx(s0 ? 1.f : r0), i1 = rsqrt_approx(s1 ? 1.f : r1);
+                    a = f2_fma(u[h].w, f2_pack(s0 ? 0.f : i0, s1 ? 0.f : i1), a);
                 }
-                acc[i] = a;
+                acc[j] = a;
             }
         }
         asm volatile("" ::: "memory");
@@ -743,81 +806,101 @@ __global__ void __launch_bounds__(32 * PS_WARPS, 8) k_p2p_lap_src(const int4* it
     const int2 r = range[cell];
     const int e0 = pptr[cell], e1 = pptr[cell + 1];
     const int total = plen[cell];
-    float4* sT = sh.t;
     float2* sHL = &sh.hl[warp][0][0];
     const float4 far_src = make_float4(1e18f, 0.f, 0.f, 0.f);  // padding: contributes 0 * rsqrt(1e36)
     {
         const int tb = item.y;
         const int ntb = item.z;
         __syncthreads();
-        for (int i = threadIdx.x; i < ((ntb + 3) & ~3); i += blockDim.x)
-            sT[i] = i < ntb ? tgt[tb + i] : make_float4(1e18f, 1e18f, 1e18f, 0.f);
+        for (int i = threadIdx.x; i < ((ntb + 3) & ~3); i += blockDim.x) {
+            const float4 x = i < ntb ? tgt[tb + i] : make_float4(1e18f, 1e18f, 1e18f, 0.f);
+            float* xy = reinterpret_cast<float*>(&sh.txy[i >> 1]);
+            float* z = reinterpret_cast<float*>(&sh.tz[i >> 1]);
+            xy[i & 1] = x.x;
+            xy[2 + (i & 1)] = x.y;
+            z[i & 1] = x.z;
+        }
         for (int i = 0; i < ntb; ++i) sHL[i * 32 + lane] = make_float2(0.f, 0.f);
-        float acc[PS_TMAX];
+        f32x2 acc[PS_TMAX / 2];
 #pragma unroll
-        for (int i = 0; i < PS_TMAX; ++i) acc[i] = 0.f;
+        for (int j = 0; j < PS_TMAX / 2; ++j) acc[j] = 0ull;
         int rounds = 0;
         __syncthreads();
         // own leaf: positions relative to the same centre; the target's own panel is skipped
         {
             const int g0 = r.x * K, n = (r.y - r.x) * K;
             for (int base = RND * warp; base < n; base += RND * PS_WARPS) {
-                float4 u[PS_SRC];
+                PsSrc u[PS_SRC];
                 int gp[PS_SRC];
 #pragma unroll
                 for (int h = 0; h < PS_SRC; ++h) {
                     const int q = base + 32 * h + lane;
-                    u[h] = q < n ? srcw[g0 + q] : far_src;
+                    u[h] = ps_src(q < n ? srcw[g0 + q] : far_src);
                     gp[h] = q < n ? (g0 + q) / K : -1;
                 }
-                ps_round_self(sT, ntb, tb, u, gp, acc);
+                ps_round_self(sh.txy, sh.tz, ntb, tb, u, gp, acc);
                 if (++rounds == PS_FOLD) { ps_fold(acc, sHL, ntb, lane); rounds = 0; }
             }
         }
-        // the other leaves, as one stream of Gauss points in chunks of PS_EMAX pair records
+        // the other leaves, as one stream of Gauss points in chunks of PS_EMAX pair records,
+        // each warp staging its own copy of a chunk's records
+        float4* wrec = sh.rec[warp];
+        int* woff = sh.off[warp];
         for (int eb = e0; eb < e1; eb += PS_EMAX) {
             const int ne = min(PS_EMAX, e1 - eb);
-            __syncthreads();
-            for (int j = threadIdx.x; j < ne; j += blockDim.x) {
-                sh.rec[j] = prec[eb + j];
-                sh.off[j] = poff[eb + j];
+            __syncwarp();
+            for (int j = lane; j < ne; j += 32) {
+                wrec[j] = prec[eb + j];
+                woff[j] = poff[eb + j];
             }
-            if (threadIdx.x == 0) sh.off[ne] = (eb + PS_EMAX < e1) ? poff[eb + PS_EMAX] : total;
-            __syncthreads();
-            const int s_beg = sh.off[0], s_end = sh.off[ne];
+            if (lane == 0) woff[ne] = (eb + PS_EMAX < e1) ? poff[eb + PS_EMAX] : total;
+            __syncwarp();
+            const int s_beg = woff[0], s_end = woff[ne];
             int cur = 0;  // per-lane cursor: the pair record holding the lane's next position
-            auto fetch = [&](int base, float4 (&u)[PS_SRC]) {
+            auto fetch = [&](int base, PsSrc (&u)[PS_SRC]) {
 #pragma unroll
                 for (int h = 0; h < PS_SRC; ++h) {
                     const int pos = base + 32 * h + lane;
-                    u[h] = far_src;
+                    float4 v = far_src;
                     if (pos < s_end) {
-                        while (sh.off[cur + 1] <= pos) ++cur;
-                        const float4 rc = sh.rec[cur];
-                        float4 v = srcw[__float_as_int(rc.w) + (pos - sh.off[cur])];
+                        while (woff[cur + 1] <= pos) ++cur;
+                        const float4 rc = wrec[cur];
+                        v = srcw[__float_as_int(rc.w) + (pos - woff[cur])];
                         v.x += rc.x; v.y += rc.y; v.z += rc.z;
-                        u[h] = v;
                     }
+                    u[h] = ps_src(v);
                 }
             };
             for (int base = s_beg + RND * warp; base < s_end; base += RND * PS_WARPS) {
-                float4 u[PS_SRC];
+                PsSrc u[PS_SRC];
                 fetch(base, u);
-                ps_round(sT, ntb, u, acc);
+                ps_round(sh.txy, sh.tz, ntb, u, acc);
                 if (++rounds == PS_FOLD) { ps_fold(acc, sHL, ntb, lane); rounds = 0; }
             }
         }
         ps_fold(acc, sHL, ntb, lane);
-        __syncthreads();
-        // thread i: target i of the pass adds the compensated partials of every lane of every warp
-        for (int i = threadIdx.x; i < ntb; i += blockDim.x) {
+        __syncwarp();
+        // lane i of each warp adds target i's compensated partials of the warp's 32 lanes,
+        // then thread i adds the PS_WARPS warp sums
+        if (lane < ntb) {
             float hi = 0.f, lo = 0.f;
-            for (int w = 0; w < PS_WARPS; ++w)
-                for (int k = 0; k < 32; ++k) {
-                    const float2 v = sh.hl[w][i][(k + i) & 31];
-                    kahan_add(hi, lo, v.x);
-                    kahan_add(hi, lo, -v.y);
-                }
+            for (int k = 0; k < 32; ++k) {
+                const float2 v = sHL[lane * 32 + ((k + lane) & 31)];
+                kahan_add(hi, lo, v.x);
+                kahan_add(hi, lo, -v.y);
+            }
+            sh.wsum[warp][lane] = make_float2(hi, lo);
+        }
+        __syncthreads();
+        if (threadIdx.x < ntb) {
+            const int i = threadIdx.x;
+            float hi = 0.f, lo = 0.f;
+#pragma unroll
+            for (int w = 0; w < PS_WARPS; ++w) {
+                const float2 v = sh.wsum[w][i];
+                kahan_add(hi, lo, v.x);
+                kahan_add(hi, lo, -v.y);
+            }
             double out = (double)hi - (double)lo;
             add_correction<1>(tb + i, cptr, ccol, cval, xs, &out);
             ynear[tb + i] = out;
@@ -882,11 +965,19 @@ __global__ void k_pack_sources_dipole(const float4* src_rel, const float4* nrm_f
     }
 }
 
+// Pair records are staged per warp (VS_EMAX per chunk), so warps do not wait for one another
+// in the main loop; the epilogue's warp sums reuse the record area.
+constexpr int VS_EMAX = 32;
 template <int OP> struct VlShared {
     float4 t[VecLane<OP>::TM];
     float2 hl[PS_WARPS][VecLane<OP>::TM * VecLane<OP>::DOF][32];
-    float4 rec[PS_EMAX];
-    int off[PS_EMAX + 1];
+    union {
+        struct {
+            float4 rec[PS_WARPS][VS_EMAX];
+            int off[PS_WARPS][VS_EMAX + 1];
+        } s;
+        float2 wsum[PS_WARPS][VecLane<OP>::TM * VecLane<OP>::DOF];
+    } u;
 };
 
 template <int OP>
@@ -981,16 +1072,18 @@ __global__ void __launch_bounds__(32 * PS_WARPS, 5) k_p2p_vec_src(const int4* it
         }
     }
     // the other leaves of the P2P list, as one stream
-    for (int eb = e0; eb < e1; eb += PS_EMAX) {
-        const int ne = min(PS_EMAX, e1 - eb);
-        __syncthreads();
-        for (int j = threadIdx.x; j < ne; j += blockDim.x) {
-            sh.rec[j] = prec[eb + j];
-            sh.off[j] = poff[eb + j];
+    float4* wrec = sh.u.s.rec[warp];
+    int* woff = sh.u.s.off[warp];
+    for (int eb = e0; eb < e1; eb += VS_EMAX) {
+        const int ne = min(VS_EMAX, e1 - eb);
+        __syncwarp();
+        if (lane < ne) {
+            wrec[lane] = prec[eb + lane];
+            woff[lane] = poff[eb + lane];
         }
-        if (threadIdx.x == 0) sh.off[ne] = (eb + PS_EMAX < e1) ? poff[eb + PS_EMAX] : total;
-        __syncthreads();
-        const int s_beg = sh.off[0], s_end = sh.off[ne];
+        if (lane == 0) woff[ne] = (eb + VS_EMAX < e1) ? poff[eb + VS_EMAX] : total;
+        __syncwarp();
+        const int s_beg = woff[0], s_end = woff[ne];
         int cur = 0;
         for (int base = s_beg + RND * warp; base < s_end; base += RND * PS_WARPS) {
             float4 ua[SS_SRC], ub[SS_SRC];
@@ -1000,9 +1093,9 @@ __global__ void __launch_bounds__(32 * PS_WARPS, 5) k_p2p_vec_src(const int4* it
                 ua[h] = far_a;
                 ub[h] = zero4;
                 if (pos < s_end) {
-                    while (sh.off[cur + 1] <= pos) ++cur;
-                    const float4 rc = sh.rec[cur];
-                    const int g = __float_as_int(rc.w) + (pos - sh.off[cur]);
+                    while (woff[cur + 1] <= pos) ++cur;
+                    const float4 rc = wrec[cur];
+                    const int g = __float_as_int(rc.w) + (pos - woff[cur]);
                     float4 a = srcw[2 * g];
                     a.x += rc.x; a.y += rc.y; a.z += rc.z;
                     ua[h] = a;
@@ -1022,18 +1115,29 @@ __global__ void __launch_bounds__(32 * PS_WARPS, 5) k_p2p_vec_src(const int4* it
         }
     }
     fold();
+    __syncthreads();  // every warp is done with its records before the warp sums overwrite them
+    // each warp adds, per (target, component) row, the compensated partials of its 32 lanes
+    for (int row = lane; row < DOF * ntb; row += 32) {
+        float hi = 0.f, lo = 0.f;
+        for (int k = 0; k < 32; ++k) {
+            const float2 v = sHL[row * 32 + ((k + row) & 31)];
+            kahan_add(hi, lo, v.x);
+            kahan_add(hi, lo, -v.y);
+        }
+        sh.u.wsum[warp][row] = make_float2(hi, lo);
+    }
     __syncthreads();
     for (int i = threadIdx.x; i < ntb; i += blockDim.x) {
         double out[DOF];
 #pragma unroll
         for (int a = 0; a < DOF; ++a) {
             float hi = 0.f, lo = 0.f;
-            for (int w = 0; w < PS_WARPS; ++w)
-                for (int k = 0; k < 32; ++k) {
-                    const float2 v = sh.hl[w][DOF * i + a][(k + i) & 31];
-                    kahan_add(hi, lo, v.x);
-                    kahan_add(hi, lo, -v.y);
-                }
+#pragma unroll
+            for (int w = 0; w < PS_WARPS; ++w) {
+                const float2 v = sh.u.wsum[w][DOF * i + a];
+                kahan_add(hi, lo, v.x);
+                kahan_add(hi, lo, -v.y);
+            }
             out[a] = (double)hi - (double)lo;
         }
         add_correction<DOF>(tb + i, cptr, ccol, cval, xs, out, bstride);
@@ -1136,6 +1240,18 @@ int near_field(fmmbem_handle* h, bool fp64, cudaStream_t st) {
     const int rc = near_field_on(h, fp64);
     h->stream = keep;
     return rc;
+}
+
+// The source-lane kernels' resident blocks (eight of 26.6 KB for the Laplace single layer,
+// five of up to 43.7 KB for the others) fit on an SM only with the largest shared-memory
+// carveout.
+int init_near_attrs() {
+    const int c = (int)cudaSharedmemCarveoutMaxShared;
+    FMM_CU(cudaFuncSetAttribute(k_p2p_lap_src, cudaFuncAttributePreferredSharedMemoryCarveout, c));
+    FMM_CU(cudaFuncSetAttribute(k_p2p_vec_src<STK_SL>, cudaFuncAttributePreferredSharedMemoryCarveout, c));
+    FMM_CU(cudaFuncSetAttribute(k_p2p_vec_src<LAP_DL>, cudaFuncAttributePreferredSharedMemoryCarveout, c));
+    FMM_CU(cudaFuncSetAttribute(k_p2p_vec_src<LAP_B4>, cudaFuncAttributePreferredSharedMemoryCarveout, c));
+    return 0;
 }
 
 // The work-item (source-lane) near-field kernel of this handle's operator over every item.
