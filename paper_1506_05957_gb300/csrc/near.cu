@@ -968,8 +968,11 @@ __global__ void k_pack_sources_dipole(const float4* src_rel, const float4* nrm_f
 // Pair records are staged per warp (VS_EMAX per chunk), so warps do not wait for one another
 // in the main loop; the epilogue's warp sums reuse the record area.
 constexpr int VS_EMAX = 32;
+static_assert(P2P_SRC_TMAX % 2 == 0 && P2P_SRC_TMAX_STOKES % 2 == 0 && P2P_SRC_TMAX_BATCH % 2 == 0,
+              "targets are processed in pairs");
 template <int OP> struct VlShared {
-    float4 t[VecLane<OP>::TM];
+    float4 txy[VecLane<OP>::TM / 2];  // target pairs (x_a, x_b, y_a, y_b) and (z_a, z_b)
+    float2 tz[VecLane<OP>::TM / 2];
     float2 hl[PS_WARPS][VecLane<OP>::TM * VecLane<OP>::DOF][32];
     union {
         struct {
@@ -980,27 +983,41 @@ template <int OP> struct VlShared {
     } u;
 };
 
+// One source against a target pair (paired FP32, as in the Laplace kernel). The source's
+// position and strength components are repeated in both halves; sk0/sk1 drop the pair's
+// first/second target (the source lies on that target's own panel).
+struct VlSrc {
+    f32x2 x, y, z, v0, v1, v2, v3;
+};
+__device__ __forceinline__ VlSrc vl_src(float4 a, float4 b) {
+    return {f2_pack(a.x, a.x), f2_pack(a.y, a.y), f2_pack(a.z, a.z), f2_pack(a.w, a.w),
+            f2_pack(b.x, b.x), f2_pack(b.y, b.y), f2_pack(b.z, b.z)};
+}
+
 template <int OP>
-__device__ __forceinline__ void vl_pair(float4 x, float4 a, float4 b, bool skip, float* acc) {
-    const float dx = x.x - a.x, dy = x.y - a.y, dz = x.z - a.z;
-    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-    const float ir = skip ? 0.f : rsqrt_approx(skip ? 1.f : r2);
-    const float ir3 = ir * ir * ir;
+__device__ __forceinline__ void vl_pair(f32x2 tx, f32x2 ty, f32x2 tz, const VlSrc& u, bool sk0, bool sk1,
+                                        f32x2* acc) {
+    const f32x2 dx = f2_sub(tx, u.x), dy = f2_sub(ty, u.y), dz = f2_sub(tz, u.z);
+    float r0, r1;
+    f2_unpack(f2_fma(dx, dx, f2_fma(dy, dy, f2_mul(dz, dz))), r0, r1);
+    const float i0 = rsqrt_approx(sk0 ? 1.f : r0), i1 = rsqrt_approx(sk1 ? 1.f : r1);
+    const f32x2 ir = f2_pack(sk0 ? 0.f : i0, sk1 ? 0.f : i1);
     if (OP == LAP_B4) {
-        acc[0] = fmaf(a.w, ir, acc[0]);
-        acc[1] = fmaf(b.x, ir, acc[1]);
-        acc[2] = fmaf(b.y, ir, acc[2]);
-        acc[3] = fmaf(b.z, ir, acc[3]);
+        acc[0] = f2_fma(u.v0, ir, acc[0]);
+        acc[1] = f2_fma(u.v1, ir, acc[1]);
+        acc[2] = f2_fma(u.v2, ir, acc[2]);
+        acc[3] = f2_fma(u.v3, ir, acc[3]);
         return;
     }
-    const float dv = fmaf(dx, a.w, fmaf(dy, b.x, dz * b.y));
+    const f32x2 ir3 = f2_mul(ir, f2_mul(ir, ir));
+    const f32x2 dv = f2_fma(dx, u.v0, f2_fma(dy, u.v1, f2_mul(dz, u.v2)));
     if (OP == STK_SL) {
-        const float df = dv * ir3;
-        acc[0] = fmaf(a.w, ir, fmaf(dx, df, acc[0]));
-        acc[1] = fmaf(b.x, ir, fmaf(dy, df, acc[1]));
-        acc[2] = fmaf(b.y, ir, fmaf(dz, df, acc[2]));
+        const f32x2 df = f2_mul(dv, ir3);
+        acc[0] = f2_fma(u.v0, ir, f2_fma(dx, df, acc[0]));
+        acc[1] = f2_fma(u.v1, ir, f2_fma(dy, df, acc[1]));
+        acc[2] = f2_fma(u.v2, ir, f2_fma(dz, df, acc[2]));
     } else {
-        acc[0] = fmaf(dv, ir3, acc[0]);
+        acc[0] = f2_fma(dv, ir3, acc[0]);
     }
 }
 
@@ -1021,27 +1038,56 @@ __global__ void __launch_bounds__(32 * PS_WARPS, 5) k_p2p_vec_src(const int4* it
     const int total = plen[cell];
     float2* sHL = &sh.hl[warp][0][0];
     const float4 far_a = make_float4(1e18f, 0.f, 0.f, 0.f), zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
-    for (int i = threadIdx.x; i < ntb; i += blockDim.x) sh.t[i] = tgt[tb + i];
+    // targets in pairs; an odd count is padded with a far-away target whose sums are never read
+    for (int i = threadIdx.x; i < ((ntb + 1) & ~1); i += blockDim.x) {
+        const float4 x = i < ntb ? tgt[tb + i] : make_float4(1e18f, 1e18f, 1e18f, 0.f);
+        float* xy = reinterpret_cast<float*>(&sh.txy[i >> 1]);
+        float* z = reinterpret_cast<float*>(&sh.tz[i >> 1]);
+        xy[i & 1] = x.x;
+        xy[2 + (i & 1)] = x.y;
+        z[i & 1] = x.z;
+    }
     for (int i = 0; i < DOF * ntb; ++i) sHL[i * 32 + lane] = make_float2(0.f, 0.f);
-    float acc[TM][DOF];
+    f32x2 acc[TM / 2][DOF];  // acc[j][a]: component a of targets 2j and 2j + 1
 #pragma unroll
-    for (int i = 0; i < TM; ++i)
+    for (int j = 0; j < TM / 2; ++j)
 #pragma unroll
-        for (int a = 0; a < DOF; ++a) acc[i][a] = 0.f;
+        for (int a = 0; a < DOF; ++a) acc[j][a] = 0ull;
     int rounds = 0;
     auto fold = [&]() {
 #pragma unroll
-        for (int i = 0; i < TM; ++i) {
-            if (i < ntb) {
+        for (int j = 0; j < TM / 2; ++j) {
 #pragma unroll
-                for (int a = 0; a < DOF; ++a) {
-                    float2 v = sHL[(DOF * i + a) * 32 + lane];
-                    kahan_add(v.x, v.y, acc[i][a]);
-                    sHL[(DOF * i + a) * 32 + lane] = v;
+            for (int a = 0; a < DOF; ++a) {
+                float a0, a1;
+                f2_unpack(acc[j][a], a0, a1);
+                if (2 * j < ntb) {
+                    float2 v = sHL[(DOF * 2 * j + a) * 32 + lane];
+                    kahan_add(v.x, v.y, a0);
+                    sHL[(DOF * 2 * j + a) * 32 + lane] = v;
                 }
+                if (2 * j + 1 < ntb) {
+                    float2 v = sHL[(DOF * (2 * j + 1) + a) * 32 + lane];
+                    kahan_add(v.x, v.y, a1);
+                    sHL[(DOF * (2 * j + 1) + a) * 32 + lane] = v;
+                }
+                acc[j][a] = 0ull;
             }
+            asm volatile("" ::: "memory");
+        }
+    };
+    auto round = [&](const VlSrc (&u)[SS_SRC], const int (&gp)[SS_SRC], bool self) {
 #pragma unroll
-            for (int a = 0; a < DOF; ++a) acc[i][a] = 0.f;
+        for (int j = 0; j < TM / 2; ++j) {
+            if (2 * j < ntb) {
+                const float4 A = sh.txy[j];
+                const float2 B = sh.tz[j];
+                const f32x2 tx = f2_pack(A.x, A.y), ty = f2_pack(A.z, A.w), tz = f2_pack(B.x, B.y);
+#pragma unroll
+                for (int h = 0; h < SS_SRC; ++h)
+                    vl_pair<OP>(tx, ty, tz, u[h], self && gp[h] == tb + 2 * j, self && gp[h] == tb + 2 * j + 1,
+                                acc[j]);
+            }
             asm volatile("" ::: "memory");
         }
     };
@@ -1050,24 +1096,15 @@ __global__ void __launch_bounds__(32 * PS_WARPS, 5) k_p2p_vec_src(const int4* it
     {
         const int g0 = r.x * K, n = (r.y - r.x) * K;
         for (int base = RND * warp; base < n; base += RND * PS_WARPS) {
-            float4 ua[SS_SRC], ub[SS_SRC];
+            VlSrc u[SS_SRC];
             int gp[SS_SRC];
 #pragma unroll
             for (int h = 0; h < SS_SRC; ++h) {
                 const int q = base + 32 * h + lane;
-                ua[h] = q < n ? srcw[2 * (g0 + q)] : far_a;
-                ub[h] = q < n ? srcw[2 * (g0 + q) + 1] : zero4;
+                u[h] = vl_src(q < n ? srcw[2 * (g0 + q)] : far_a, q < n ? srcw[2 * (g0 + q) + 1] : zero4);
                 gp[h] = q < n ? (g0 + q) / K : -1;
             }
-#pragma unroll
-            for (int i = 0; i < TM; ++i) {
-                if (i < ntb) {
-                    const float4 x = sh.t[i];
-#pragma unroll
-                    for (int h = 0; h < SS_SRC; ++h) vl_pair<OP>(x, ua[h], ub[h], gp[h] == tb + i, acc[i]);
-                }
-                asm volatile("" ::: "memory");
-            }
+            round(u, gp, true);
             if (++rounds == PS_FOLD) { fold(); rounds = 0; }
         }
     }
@@ -1086,31 +1123,24 @@ __global__ void __launch_bounds__(32 * PS_WARPS, 5) k_p2p_vec_src(const int4* it
         const int s_beg = woff[0], s_end = woff[ne];
         int cur = 0;
         for (int base = s_beg + RND * warp; base < s_end; base += RND * PS_WARPS) {
-            float4 ua[SS_SRC], ub[SS_SRC];
+            VlSrc u[SS_SRC];
+            int gp[SS_SRC];
 #pragma unroll
             for (int h = 0; h < SS_SRC; ++h) {
                 const int pos = base + 32 * h + lane;
-                ua[h] = far_a;
-                ub[h] = zero4;
+                float4 a = far_a, b = zero4;
                 if (pos < s_end) {
                     while (woff[cur + 1] <= pos) ++cur;
                     const float4 rc = wrec[cur];
                     const int g = __float_as_int(rc.w) + (pos - woff[cur]);
-                    float4 a = srcw[2 * g];
+                    a = srcw[2 * g];
                     a.x += rc.x; a.y += rc.y; a.z += rc.z;
-                    ua[h] = a;
-                    ub[h] = srcw[2 * g + 1];
+                    b = srcw[2 * g + 1];
                 }
+                u[h] = vl_src(a, b);
+                gp[h] = -1;
             }
-#pragma unroll
-            for (int i = 0; i < TM; ++i) {
-                if (i < ntb) {
-                    const float4 x = sh.t[i];
-#pragma unroll
-                    for (int h = 0; h < SS_SRC; ++h) vl_pair<OP>(x, ua[h], ub[h], false, acc[i]);
-                }
-                asm volatile("" ::: "memory");
-            }
+            round(u, gp, false);
             if (++rounds == PS_FOLD) { fold(); rounds = 0; }
         }
     }
