@@ -48,6 +48,34 @@ template <typename T> FMM_HD void cfma_conja(cpx<T>& acc, cpx<T> a, cpx<T> b) {
     acc.im += a.re * b.im - a.im * b.re;
 }
 
+// Two FP32 values in one 64-bit register, operated on by the paired FP32 instructions of
+// sm_100-family GPUs (PTX .f32x2): one instruction applies the same operation to both halves,
+// each rounded as the scalar FP32 operation, which halves the issue slots of the arithmetic.
+typedef unsigned long long f32x2;
+__device__ __forceinline__ f32x2 f2_pack(float a, float b) {
+    f32x2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void f2_unpack(f32x2 v, float& a, float& b) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+}
+__device__ __forceinline__ f32x2 f2_sub(f32x2 a, f32x2 b) {
+    f32x2 d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f32x2 f2_mul(f32x2 a, f32x2 b) {
+    f32x2 d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f32x2 f2_fma(f32x2 a, f32x2 b, f32x2 c) {
+    f32x2 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+
 // 4-wide vector of the arithmetic type (positions + weight).
 template <typename T> struct V4;
 template <> struct V4<float> { typedef float4 type; };

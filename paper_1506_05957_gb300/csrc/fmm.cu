@@ -180,6 +180,8 @@ __global__ void __launch_bounds__(32 * P2MP_WARPS) k_p2m_packed(int p, const int
         const int qd = m / P2MP_WARPS, rm = m - qd * P2MP_WARPS;
         return ((qd & 1) ? P2MP_WARPS - 1 - rm : rm) == warp;
     };
+    constexpr int NP = SPL / 2;  // pairs of points per lane
+    static_assert(SPL % 2 == 0, "points are processed in pairs");
     for (int base = s0; base < s1; base += 32 * SPL) {
         float vx[SPL], vy[SPL], vz[SPL], q[SPL], c[SPL], qb[SPL][4];
         cpx<float> a[SPL], b[SPL];
@@ -208,7 +210,30 @@ __global__ void __launch_bounds__(32 * P2MP_WARPS) k_p2m_packed(int p, const int
                 }
             }
         }
-        auto emit = [&](int n, int m, const cpx<float> (&R)[SPL]) {
+        f32x2 q2[NP];
+#pragma unroll
+        for (int k = 0; k < NP; ++k) q2[k] = f2_pack(q[2 * k], q[2 * k + 1]);
+        // R_n^m of the lane's points, held as pairs of points (re and im of points 2k, 2k + 1)
+        auto emit = [&](int n, int m, const f32x2 (&Rre)[NP], const f32x2 (&Rim)[NP]) {
+            if (!DL && MODE != 2) {  // single layer: sum_h q_h R_h with paired multiply-adds
+                f32x2 sre = f2_mul(q2[0], Rre[0]), sim = f2_mul(q2[0], Rim[0]);
+#pragma unroll
+                for (int k = 1; k < NP; ++k) {
+                    sre = f2_fma(q2[k], Rre[k], sre);
+                    sim = f2_fma(q2[k], Rim[k], sim);
+                }
+                float a0, a1, b0, b1;
+                f2_unpack(sre, a0, a1);
+                f2_unpack(sim, b0, b1);
+                add(0, n, m, mk(a0 + a1, b0 + b1));
+                return;
+            }
+            cpx<float> R[SPL];
+#pragma unroll
+            for (int k = 0; k < NP; ++k) {
+                f2_unpack(Rre[k], R[2 * k].re, R[2 * k + 1].re);
+                f2_unpack(Rim[k], R[2 * k].im, R[2 * k + 1].im);
+            }
             if (DL) {  // R = R_n^m, n < p: feeds degree n + 1
                 cpx<float> t0 = mk(0.f, 0.f), t1 = t0, t2 = t0, t3 = t0;
 #pragma unroll
@@ -230,47 +255,62 @@ __global__ void __launch_bounds__(32 * P2MP_WARPS) k_p2m_packed(int p, const int
                     for (int h = 0; h < SPL; ++h) t = t + qb[h][cc] * R[h];
                     add(cc, n, m, t);
                 }
-            } else {
-                cpx<float> t = mk(0.f, 0.f);
-#pragma unroll
-                for (int h = 0; h < SPL; ++h) t = t + q[h] * R[h];
-                add(0, n, m, t);
             }
         };
         const int nmax = DL ? p - 1 : p;  // highest degree generated
-        float r2[SPL];
-        cpx<float> xy[SPL], diag[SPL], prev1[SPL], prev2[SPL], cur[SPL];
+        // The recurrences run on pairs of points with paired FP32 instructions:
+        //   R_m^m = (-(x + iy) / (2m)) R_{m-1}^{m-1},  R_{m+1}^m = z R_m^m,
+        //   R_n^m = ((2n - 1) z R_{n-1}^m - r^2 R_{n-2}^m) / ((n - m)(n + m)).
+        f32x2 vz2[NP], nr2[NP], xre[NP], xim[NP], nxim[NP], dre[NP], dim[NP], p1re[NP], p1im[NP], p2re[NP], p2im[NP];
 #pragma unroll
-        for (int h = 0; h < SPL; ++h) {
-            r2[h] = vx[h] * vx[h] + vy[h] * vy[h] + vz[h] * vz[h];
-            xy[h] = mk(vx[h], vy[h]);
-            diag[h] = mk(1.f, 0.f);
+        for (int k = 0; k < NP; ++k) {
+            const int h0 = 2 * k, h1 = 2 * k + 1;
+            vz2[k] = f2_pack(vz[h0], vz[h1]);
+            nr2[k] = f2_pack(-(vx[h0] * vx[h0] + vy[h0] * vy[h0] + vz[h0] * vz[h0]),
+                             -(vx[h1] * vx[h1] + vy[h1] * vy[h1] + vz[h1] * vz[h1]));
+            xre[k] = f2_pack(vx[h0], vx[h1]);
+            xim[k] = f2_pack(vy[h0], vy[h1]);
+            nxim[k] = f2_pack(-vy[h0], -vy[h1]);
+            dre[k] = f2_pack(1.f, 1.f);
+            dim[k] = 0ull;
         }
         for (int m = 0; m <= nmax; ++m) {
             if (m > 0) {
                 const float f = -0.5f / (float)m;
+                const f32x2 f2 = f2_pack(f, f);
 #pragma unroll
-                for (int h = 0; h < SPL; ++h) diag[h] = f * (xy[h] * diag[h]);
+                for (int k = 0; k < NP; ++k) {
+                    const f32x2 re = f2_fma(xre[k], dre[k], f2_mul(nxim[k], dim[k]));
+                    const f32x2 im = f2_fma(xre[k], dim[k], f2_mul(xim[k], dre[k]));
+                    dre[k] = f2_mul(f2, re);
+                    dim[k] = f2_mul(f2, im);
+                }
             }
             if (!owns(m)) continue;
-            emit(m, m, diag);
+            emit(m, m, dre, dim);
             if (m + 1 > nmax) continue;
 #pragma unroll
-            for (int h = 0; h < SPL; ++h) {
-                prev2[h] = diag[h];
-                prev1[h] = vz[h] * diag[h];
+            for (int k = 0; k < NP; ++k) {
+                p2re[k] = dre[k];
+                p2im[k] = dim[k];
+                p1re[k] = f2_mul(vz2[k], dre[k]);
+                p1im[k] = f2_mul(vz2[k], dim[k]);
             }
-            emit(m + 1, m, prev1);
+            emit(m + 1, m, p1re, p1im);
             for (int n = m + 2; n <= nmax; ++n) {
                 const float inv = 1.f / (float)((n - m) * (n + m)), tn = (float)(2 * n - 1);
+                const f32x2 inv2 = f2_pack(inv, inv), tn2 = f2_pack(tn, tn);
 #pragma unroll
-                for (int h = 0; h < SPL; ++h) {
-                    cur[h] = mk((tn * vz[h] * prev1[h].re - r2[h] * prev2[h].re) * inv,
-                                (tn * vz[h] * prev1[h].im - r2[h] * prev2[h].im) * inv);
-                    prev2[h] = prev1[h];
-                    prev1[h] = cur[h];
+                for (int k = 0; k < NP; ++k) {
+                    const f32x2 tz = f2_mul(tn2, vz2[k]);
+                    const f32x2 cre = f2_mul(f2_fma(tz, p1re[k], f2_mul(nr2[k], p2re[k])), inv2);
+                    const f32x2 cim = f2_mul(f2_fma(tz, p1im[k], f2_mul(nr2[k], p2im[k])), inv2);
+                    p2re[k] = p1re[k];
+                    p2im[k] = p1im[k];
+                    p1re[k] = cre;
+                    p1im[k] = cim;
                 }
-                emit(n, m, cur);
+                emit(n, m, p1re, p1im);
             }
         }
     }
@@ -781,6 +821,73 @@ __global__ void k_l2p(int p, const int* leaves, const double4* cs, const int2* r
     }
 }
 
+// L2P of one FP32 expansion (the Laplace mat-vec) with paired FP32 instructions: each lane
+// takes two targets of the leaf (positions base + lane and base + 32 + lane) and runs their
+// recurrences as one pair; the coefficients are staged with their weight (2 for m > 0) and
+// repeated in both halves, (w re, w re, -w im, -w im). Same sums as k_l2p<float, 1>.
+__global__ void k_l2p_pair(int p, const int* leaves, const double4* cs, const int2* range, const float* L,
+                           const double* ynear, double scale, const double* xs_half, const float4* tgt_rel,
+                           double* yout) {
+    __shared__ float4 sA[NCOEF_MAX];
+    const int cell = leaves[blockIdx.x];
+    const int2 r = range[cell];
+    const int nco = ncoef(p);
+    const float* Lc = L + (size_t)cell * ESTRIDE;
+    for (int q = threadIdx.x; q < nco; q += blockDim.x) {
+        int n, m;
+        decode(q, n, m);
+        const float w = m ? 2.f : 1.f, are = w * Lc[2 * q], aim = w * Lc[2 * q + 1];
+        sA[q] = make_float4(are, are, -aim, -aim);
+    }
+    __syncthreads();
+    const float inv_sf = (float)(1.0 / cs[cell].w);
+    for (int base = r.x; base < r.y; base += 64) {
+        const int i0 = base + threadIdx.x, i1 = i0 + 32;
+        const float4 t0 = i0 < r.y ? tgt_rel[i0] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float4 t1 = i1 < r.y ? tgt_rel[i1] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float x0 = t0.x * inv_sf, y0 = t0.y * inv_sf, z0 = t0.z * inv_sf;
+        const float x1 = t1.x * inv_sf, y1 = t1.y * inv_sf, z1 = t1.z * inv_sf;
+        const f32x2 vz = f2_pack(z0, z1), xre = f2_pack(x0, x1), xim = f2_pack(y0, y1), nxim = f2_pack(-y0, -y1);
+        const f32x2 nr2 = f2_pack(-(x0 * x0 + y0 * y0 + z0 * z0), -(x1 * x1 + y1 * y1 + z1 * z1));
+        f32x2 phi = 0ull, dre = f2_pack(1.f, 1.f), dim = 0ull;
+        auto use = [&](int q, f32x2 Rre, f32x2 Rim) {
+            const float4 a = sA[q];
+            phi = f2_fma(f2_pack(a.x, a.y), Rre, f2_fma(f2_pack(a.z, a.w), Rim, phi));
+        };
+        for (int m = 0; m <= p; ++m) {
+            if (m > 0) {
+                const float f = -0.5f / (float)m;
+                const f32x2 f2 = f2_pack(f, f);
+                const f32x2 re = f2_fma(xre, dre, f2_mul(nxim, dim));
+                const f32x2 im = f2_fma(xre, dim, f2_mul(xim, dre));
+                dre = f2_mul(f2, re);
+                dim = f2_mul(f2, im);
+            }
+            use(cidx(m, m), dre, dim);
+            if (m + 1 > p) break;
+            f32x2 p2re = dre, p2im = dim, p1re = f2_mul(vz, dre), p1im = f2_mul(vz, dim);
+            use(cidx(m + 1, m), p1re, p1im);
+            for (int n = m + 2; n <= p; ++n) {
+                const float inv = 1.f / (float)((n - m) * (n + m)), tn = (float)(2 * n - 1);
+                const f32x2 inv2 = f2_pack(inv, inv), tz = f2_mul(f2_pack(tn, tn), vz);
+                const f32x2 cre = f2_mul(f2_fma(tz, p1re, f2_mul(nr2, p2re)), inv2);
+                const f32x2 cim = f2_mul(f2_fma(tz, p1im, f2_mul(nr2, p2im)), inv2);
+                p2re = p1re;
+                p2im = p1im;
+                p1re = cre;
+                p1im = cim;
+                use(cidx(n, m), p1re, p1im);
+            }
+        }
+        float ph0, ph1;
+        f2_unpack(phi, ph0, ph1);
+        if (i0 < r.y)
+            yout[i0] = scale * ((double)(ph0 * inv_sf) + ynear[i0]) + (xs_half ? 0.5 * xs_half[i0] : 0.0);
+        if (i1 < r.y)
+            yout[i1] = scale * ((double)(ph1 * inv_sf) + ynear[i1]) + (xs_half ? 0.5 * xs_half[i1] : 0.0);
+    }
+}
+
 __global__ void k_octant_tables(double* od, float* of) {
     const int o = threadIdx.x;
     if (o >= 8) return;
@@ -960,11 +1067,17 @@ template <typename T, int NC>
 int far_eval_t(fmmbem_handle* h, int p, double* y_sorted, double scale) {
     prof_begin(h, FMMBEM_PASS_L2P);
     // one warp per leaf: a leaf holds about 20 targets (a 128-thread block left most threads idle)
-    k_l2p<T, NC><<<h->n_leaves, 32, 0, h->stream>>>(p, h->leaves, h->cell_cs, h->cell_range, h->tgt_d,
-                                                    reinterpret_cast<const T*>(h->L), h->ynear, scale, h->origin[0],
-                                                    h->origin[1], h->origin[2],
-                                                    h->layer == FMMBEM_LAYER_DOUBLE ? h->xin : nullptr,
-                                                    h->tgt_rel, y_sorted, h->nrhs > 1 ? h->N : 0);
+    if (std::is_same<T, float>::value && NC == 1)
+        k_l2p_pair<<<h->n_leaves, 32, 0, h->stream>>>(p, h->leaves, h->cell_cs, h->cell_range,
+                                                      reinterpret_cast<const float*>(h->L), h->ynear, scale,
+                                                      h->layer == FMMBEM_LAYER_DOUBLE ? h->xin : nullptr,
+                                                      h->tgt_rel, y_sorted);
+    else
+        k_l2p<T, NC><<<h->n_leaves, 32, 0, h->stream>>>(p, h->leaves, h->cell_cs, h->cell_range, h->tgt_d,
+                                                        reinterpret_cast<const T*>(h->L), h->ynear, scale,
+                                                        h->origin[0], h->origin[1], h->origin[2],
+                                                        h->layer == FMMBEM_LAYER_DOUBLE ? h->xin : nullptr,
+                                                        h->tgt_rel, y_sorted, h->nrhs > 1 ? h->N : 0);
     FMM_LAUNCHED();
     prof_end(h, FMMBEM_PASS_L2P, 1);
     h->launches += 1;
