@@ -161,7 +161,7 @@ int fmmbem_autotune(fmmbem_handle* h, int p_lo, int p_hi, int* choice);
  * 1 = (target, source slice) per thread, sources read through L1;
  * 2 = as 1, with each pair's sources bulk-copied into double-buffered shared memory
  *     (used when a leaf holds at most 1024 Gauss points, else 1);
- * 3 = one block per work item (at most 20 targets of one leaf), its warps' lanes over the
+ * 3 = one block per work item (at most 24 targets of one leaf), its warps' lanes over the
  *     leaf's source stream and the targets looped in registers (default).
  * Returns FMMBEM_EINVAL for any other value. */
 int fmmbem_set_p2p_variant(fmmbem_handle* h, int variant);

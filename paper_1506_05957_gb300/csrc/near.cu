@@ -672,7 +672,8 @@ struct PsShared {
     int off[PS_WARPS][PS_EMAX + 1];
     float2 wsum[PS_WARPS][PS_TMAX];
 };
-static_assert(PS_TMAX % 4 == 0, "targets are processed in groups of four");
+constexpr int PS_GRP = 4;  // targets per group of the unrolled target loop (a multiple of the pair)
+static_assert(PS_TMAX % PS_GRP == 0 && PS_GRP % 2 == 0, "targets are processed in groups of whole pairs");
 
 // A source of the round, each component repeated in both halves.
 struct PsSrc {
@@ -703,9 +704,9 @@ __device__ __forceinline__ void ps_fold(f32x2* acc, float2* hl, int ntb, int lan
     }
 }
 
-// The target loop runs over groups of four targets (two pairs), fully unrolled (so the
+// The target loop runs over groups of PS_GRP targets (whole pairs), fully unrolled (so the
 // accumulators stay in registers) with one uniform branch per group; the target count of a
-// pass is padded to a multiple of four with far-away dummy targets whose sums are never read.
+// pass is padded to a multiple of PS_GRP with far-away dummy targets whose sums are never read.
 // Each lane holds PS_SRC sources per round; per source and target pair: 3 paired
 // subtractions, the squared distances (paired mul + 2 paired fma), two rsqrt and one paired
 // fma into the accumulators.
@@ -714,10 +715,10 @@ constexpr int PS_SRC = 4;
 __device__ __forceinline__ void ps_round(const float4* sXY, const float2* sZ, int ntb, const PsSrc (&u)[PS_SRC],
                                          f32x2* acc) {
 #pragma unroll
-    for (int g = 0; g < PS_TMAX; g += 4) {
+    for (int g = 0; g < PS_TMAX; g += PS_GRP) {
         if (g < ntb) {
 #pragma unroll
-            for (int j = g / 2; j < g / 2 + 2; ++j) {
+            for (int j = g / 2; j < (g + PS_GRP) / 2; ++j) {
                 const float4 A = sXY[j];
                 const float2 B = sZ[j];
                 const f32x2 tx = f2_pack(A.x, A.y), ty = f2_pack(A.z, A.w), tz = f2_pack(B.x, B.y);
@@ -740,10 +741,10 @@ __device__ __forceinline__ void ps_round(const float4* sXY, const float2* sZ, in
 __device__ __forceinline__ void ps_round_self(const float4* sXY, const float2* sZ, int ntb, int tb,
                                               const PsSrc (&u)[PS_SRC], const int (&gp)[PS_SRC], f32x2* acc) {
 #pragma unroll
-    for (int g = 0; g < PS_TMAX; g += 4) {
+    for (int g = 0; g < PS_TMAX; g += PS_GRP) {
         if (g < ntb) {
 #pragma unroll
-            for (int j = g / 2; j < g / 2 + 2; ++j) {
+            for (int j = g / 2; j < (g + PS_GRP) / 2; ++j) {
                 const float4 A = sXY[j];
                 const float2 B = sZ[j];
                 const f32x2 tx = f2_pack(A.x, A.y), ty = f2_pack(A.z, A.w), tz = f2_pack(B.x, B.y);
@@ -765,7 +766,7 @@ __device__ __forceinline__ void ps_round_self(const float4* sXY, const float2* s
     }
 }
 
-__global__ void __launch_bounds__(32 * PS_WARPS, 8) k_p2p_lap_src(const int4* items, const int2* range, const int* pptr,
+__global__ void __launch_bounds__(32 * PS_WARPS, 7) k_p2p_lap_src(const int4* items, const int2* range, const int* pptr,
                                                                  const float4* prec, const int* poff, const int* plen,
                                                                  const float4* srcw, const float4* tgt, int K,
                                                                  const int* cptr, const int* ccol, const double* cval,
@@ -784,7 +785,7 @@ __global__ void __launch_bounds__(32 * PS_WARPS, 8) k_p2p_lap_src(const int4* it
         const int tb = item.y;
         const int ntb = item.z;
         __syncthreads();
-        for (int i = threadIdx.x; i < ((ntb + 3) & ~3); i += blockDim.x) {
+        for (int i = threadIdx.x; i < (ntb + PS_GRP - 1) / PS_GRP * PS_GRP; i += blockDim.x) {
             const float4 x = i < ntb ? tgt[tb + i] : make_float4(1e18f, 1e18f, 1e18f, 0.f);
             float* xy = reinterpret_cast<float*>(&sh.txy[i >> 1]);
             float* z = reinterpret_cast<float*>(&sh.tz[i >> 1]);
@@ -1244,7 +1245,7 @@ int near_field(fmmbem_handle* h, bool fp64, cudaStream_t st) {
     return rc;
 }
 
-// The source-lane kernels' resident blocks (eight of 26.6 KB for the Laplace single layer,
+// The source-lane kernels' resident blocks (seven of 30.8 KB for the Laplace single layer,
 // five of up to 43.7 KB for the others) fit on an SM only with the largest shared-memory
 // carveout.
 int init_near_attrs() {
