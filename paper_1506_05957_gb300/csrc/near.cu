@@ -893,9 +893,11 @@ __global__ void __launch_bounds__(32 * PS_WARPS, 7) k_p2p_lap_src(const int4* it
 constexpr int SS_SRC = 2;  // sources per lane per round
 
 template <int OP> struct VecLane;
-template <> struct VecLane<STK_SL> { static constexpr int DOF = 3, TM = P2P_SRC_TMAX_STOKES; };
-template <> struct VecLane<LAP_DL> { static constexpr int DOF = 1, TM = P2P_SRC_TMAX; };
-template <> struct VecLane<LAP_B4> { static constexpr int DOF = 4, TM = P2P_SRC_TMAX_BATCH; };
+// DOF accumulators per target, at most TM targets per item, MINB resident blocks per SM the
+// register budget is set for.
+template <> struct VecLane<STK_SL> { static constexpr int DOF = 3, TM = P2P_SRC_TMAX_STOKES, MINB = 7; };
+template <> struct VecLane<LAP_DL> { static constexpr int DOF = 1, TM = P2P_SRC_TMAX, MINB = 5; };
+template <> struct VecLane<LAP_B4> { static constexpr int DOF = 4, TM = P2P_SRC_TMAX_BATCH, MINB = 5; };
 
 // Both pack per panel (one FP64-to-FP32 conversion per unknown, as k_pack_sources).
 __global__ void k_pack_sources_stokes(const float4* src_rel, const double* xs, int K, int64_t n, float4* out) {
@@ -995,7 +997,7 @@ __device__ __forceinline__ void vl_pair(f32x2 tx, f32x2 ty, f32x2 tz, const VlSr
 }
 
 template <int OP>
-__global__ void __launch_bounds__(32 * PS_WARPS, 5) k_p2p_vec_src(const int4* items, const int2* range, const int* pptr,
+__global__ void __launch_bounds__(32 * PS_WARPS, VecLane<OP>::MINB) k_p2p_vec_src(const int4* items, const int2* range, const int* pptr,
                                                                  const float4* prec, const int* poff, const int* plen,
                                                                  const float4* srcw, const float4* tgt, int K,
                                                                  const int* cptr, const int* ccol, const double* cval,
