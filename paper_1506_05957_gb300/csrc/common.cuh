@@ -22,7 +22,7 @@ constexpr int ESTRIDE = 320;
 constexpr int MAX_LEVELS = 21;  // 63-bit Morton keys, 21 bits per axis
 constexpr int P2P_SRC_TMAX = 24;  // targets per block of the source-lane near-field kernel
 constexpr int P2P_SRC_TMAX_STOKES = 8;   // the same for the Stokeslet (three accumulators per target)
-constexpr int P2P_SRC_TMAX_BATCH = 10;   // the same for a batch of four vectors (four accumulators per target;
+constexpr int P2P_SRC_TMAX_BATCH = 8;    // the same for a batch of four vectors (four accumulators per target;
                                          // the per-lane partial sums stay within 48 KB of shared memory)
 
 FMM_HD int cidx(int n, int m) { return (n * (n + 1)) / 2 + m; }

@@ -897,7 +897,7 @@ template <int OP> struct VecLane;
 // register budget is set for.
 template <> struct VecLane<STK_SL> { static constexpr int DOF = 3, TM = P2P_SRC_TMAX_STOKES, MINB = 7; };
 template <> struct VecLane<LAP_DL> { static constexpr int DOF = 1, TM = P2P_SRC_TMAX, MINB = 5; };
-template <> struct VecLane<LAP_B4> { static constexpr int DOF = 4, TM = P2P_SRC_TMAX_BATCH, MINB = 5; };
+template <> struct VecLane<LAP_B4> { static constexpr int DOF = 4, TM = P2P_SRC_TMAX_BATCH, MINB = 6; };
 
 // Both pack per panel (one FP64-to-FP32 conversion per unknown, as k_pack_sources).
 __global__ void k_pack_sources_stokes(const float4* src_rel, const double* xs, int K, int64_t n, float4* out) {
@@ -1248,7 +1248,7 @@ int near_field(fmmbem_handle* h, bool fp64, cudaStream_t st) {
 }
 
 // The source-lane kernels' resident blocks (seven of 30.8 KB for the Laplace single layer,
-// five of up to 43.7 KB for the others) fit on an SM only with the largest shared-memory
+// five to seven of 27-36 KB for the others) fit on an SM only with the largest shared-memory
 // carveout.
 int init_near_attrs() {
     const int c = (int)cudaSharedmemCarveoutMaxShared;
