@@ -896,7 +896,7 @@ template <int OP> struct VecLane;
 // DOF accumulators per target, at most TM targets per item, MINB resident blocks per SM the
 // register budget is set for.
 template <> struct VecLane<STK_SL> { static constexpr int DOF = 3, TM = P2P_SRC_TMAX_STOKES, MINB = 7; };
-template <> struct VecLane<LAP_DL> { static constexpr int DOF = 1, TM = P2P_SRC_TMAX, MINB = 5; };
+template <> struct VecLane<LAP_DL> { static constexpr int DOF = 1, TM = P2P_SRC_TMAX, MINB = 7; };
 template <> struct VecLane<LAP_B4> { static constexpr int DOF = 4, TM = P2P_SRC_TMAX_BATCH, MINB = 6; };
 
 // Both pack per panel (one FP64-to-FP32 conversion per unknown, as k_pack_sources).
