@@ -340,7 +340,8 @@ def run_ours(args, world, rank, local):
     p2p_peak = SM_COUNT * MUFU_PER_SM_CLK * smax * 1e6 * P2P_FLOPS / 1e12
     rl_p2p = {"bound": "alu", "kernel": "k_p2p_lap_src (near field, FP32 + MUFU rsqrt)", "achieved": round(p2p_ach, 3),
               "peak": round(p2p_peak, 2), "unit": "TFLOP/s", "frac": round(p2p_ach / p2p_peak, 4),
-              "traffic": profiled_traffic("k_p2p_lap_src_traffic_laplace_ico6_81920.md"),
+              # the ncu capture is of the 81920-panel workload; other sizes have no traffic figure
+              "traffic": profiled_traffic("k_p2p_lap_src_traffic_laplace_ico6_81920.md") if n == 81920 else None,
               "peak_source": "152 SMs x 16 rsqrt/clk x max SM clock x 11 flop per pair (derived, not measured)",
               "interactions_per_s": prof["p2p_interactions"] / (ms["p2p"] * 1e-3) if ms["p2p"] else None}
     bf16 = measured_peaks().get("bf16_tflops_sustained", 1729.8)
@@ -366,7 +367,8 @@ def run_ours(args, world, rank, local):
            "warmup": args.warmup, "warmup_solves": k_w, "ms_per_step": t_max / args.steps * 1e3,
            "higher_is_better": False,
            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-           "config": dict(W, ncrit=args.ncrit, panels=n, parallelism="replicas" if world > 1 else "single",
+           "config": dict(W, workload="laplace-sphere-ico%d-%d" % (args.levels, n), ncrit=args.ncrit, panels=n,
+                          parallelism="replicas" if world > 1 else "single",
                           l2="flushed between steps (512 MB write)", precision="mixed"),
            "matvec_per_s": mv_per_s, "iters": iters, "p_hist": r["p_hist"], "true_residual": r["true_res"],
            "autotune": tuned,

@@ -62,9 +62,11 @@ __global__ void __launch_bounds__(32 * P2M_WARPS) k_p2m(int p, const int* leaves
     const int2 r = range[cell];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int q = threadIdx.x; q < P2M_WARPS * NC * nco * 2; q += blockDim.x) acc[q] = T(0);
+    __shared__ double s_inv;  // 1 / side: one FP64 division per block (FP64 is scarce on this GPU)
+    if (threadIdx.x == 0) s_inv = 1.0 / cc.w;
     __syncthreads();
     T* wacc = acc + warp * NC * nco * 2;
-    const double inv_s = 1.0 / cc.w;
+    const double inv_s = s_inv;
     const int s0 = r.x * K, s1 = r.y * K;
     for (int base = s0 + warp * 32; base < s1; base += P2M_WARPS * 32) {
         const int s = base + lane;
@@ -162,9 +164,11 @@ __global__ void __launch_bounds__(32 * P2MP_WARPS) k_p2m_packed(int p, const int
     const int2 r = range[cell];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int q = threadIdx.x; q < P2MP_WARPS * NC * nco * 2; q += blockDim.x) acc[q] = 0.f;
+    __shared__ float s_inv;  // 1 / side: one FP64 division per block (FP64 is scarce on this GPU)
+    if (threadIdx.x == 0) s_inv = (float)(1.0 / cs[cell].w);
     __syncthreads();
     float* wacc = acc + warp * NC * nco * 2;
-    const float inv_s = (float)(1.0 / cs[cell].w);
+    const float inv_s = s_inv;
     const int s0 = r.x * K, s1 = r.y * K;
     auto add = [&](int comp, int n, int m, cpx<float> d) {  // M~_comp(n, m) += conj(d), summed over the warp
         const int qi = comp * nco + cidx(n, m);
@@ -742,8 +746,10 @@ __global__ void k_l2p(int p, const int* leaves, const double4* cs, const int2* r
         sL[(c * NCOEF_MAX + q) * 2] = Lc[c * ESTRIDE + 2 * q];
         sL[(c * NCOEF_MAX + q) * 2 + 1] = Lc[c * ESTRIDE + 2 * q + 1];
     }
+    __shared__ double s_inv;  // 1 / side: one FP64 division per block
+    if (threadIdx.x == 0) s_inv = 1.0 / cc.w;
     __syncthreads();
-    const double inv_s = 1.0 / cc.w;
+    const double inv_s = s_inv;
     // FP32 with one expansion, or a batch: the FP32 offsets from the leaf centre (no FP64 arithmetic)
     const bool rel = std::is_same<T, float>::value && (NC == 1 || bstride != 0);
     const float inv_sf = (float)inv_s;
@@ -839,8 +845,10 @@ __global__ void k_l2p_pair(int p, const int* leaves, const double4* cs, const in
         const float w = m ? 2.f : 1.f, are = w * Lc[2 * q], aim = w * Lc[2 * q + 1];
         sA[q] = make_float4(are, are, -aim, -aim);
     }
+    __shared__ float s_inv;  // 1 / side: one FP64 division per block
+    if (threadIdx.x == 0) s_inv = (float)(1.0 / cs[cell].w);
     __syncthreads();
-    const float inv_sf = (float)(1.0 / cs[cell].w);
+    const float inv_sf = s_inv;
     for (int base = r.x; base < r.y; base += 64) {
         const int i0 = base + threadIdx.x, i1 = i0 + 32;
         const float4 t0 = i0 < r.y ? tgt_rel[i0] : make_float4(0.f, 0.f, 0.f, 0.f);
