@@ -15,7 +15,9 @@ Pins (tests/test_oracle_bem.py): V 1 -> 1 on the unit sphere; V z ~ z/3
 closed-form self-integral of an equilateral triangle; trace identity of the
 Stokes self block; brute-force Duffy quadrature of the self-integrals;
 Laplace solve error vs the analytic flux falling with N; Stokes drag vs
-6 pi mu a U.
+6 pi mu a U. The near-singular regime (the 2 sqrt(2 S_j) switch and the
+20-point rule) is pinned against an independent quadrature of each entry in
+tests/test_oracle_near_regime.py.
 """
 import ctypes
 import numpy as np

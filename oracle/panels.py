@@ -25,10 +25,3 @@ def geometry(vertices, triangles):
     ln = np.linalg.norm(cr, axis=1)
     return (a + b + c) / 3.0, cr / ln[:, None], 0.5 * ln
 
-
-def quad_points(vertices, triangles, bary):
-    """Quadrature points [n, k, 3] of every panel for barycentric points [k, 3]."""
-    v = np.asarray(vertices, dtype=np.float64)
-    t = np.asarray(triangles)
-    P = v[t]  # n, 3, 3
-    return np.einsum("kv,nvd->nkd", np.asarray(bary), P)
