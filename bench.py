@@ -27,11 +27,10 @@ METRIC = "relaxed GMRES solve s (and matvec/s, % roofline) vs fixed-p FP64 on 1 
 WORKLOAD = dict(workload="laplace-sphere-ico6-81920", panels=81920, gauss_k=4, theta=0.5, p_initial=12, p_min=3,
                 tol=1e-6, restart=50, ncrit=150, data="unit point charge at (0,0,3)")
 L2_FLUSH_BYTES = 512 << 20
-SM_COUNT = 152
-FP32_LANES_PER_SM = 128
-MUFU_PER_SM_CLK = 16          # rsqrt results per SM per clock (special-function units)
 P2P_FLOPS = 11                # per Laplace pair: 3 sub, r^2 (mul + 2 fma), rsqrt, fma (rsqrt counted as 1)
-TF32_PER_BF16 = 1.1 / 2.25    # nominal dense tensor-core ratio
+TF32_PER_BF16 = 1.1 / 2.25    # nominal dense tensor-core ratio (only for the derived cross-check)
+# iterations of each peak-rate launch (about 20 ms each on a GB300 at full clock)
+PEAK_ITERS = {"ffma": 500000, "ffma2": 250000, "rsqrt": 80000, "dfma": 10000, "tf32": 60000}
 
 
 def parse():
@@ -44,13 +43,14 @@ def parse():
     ap.add_argument("--ncrit", type=int, default=WORKLOAD["ncrit"])
     ap.add_argument("--no-compare", action="store_true", help="skip the FP64 comparison solves")
     ap.add_argument("--problem", default="laplace",
-                    choices=["laplace", "stokes", "serve", "laplace2", "sweeps", "batch", "rbc64"],
+                    choices=["laplace", "stokes", "serve", "laplace2", "sweeps", "batch", "rbc64", "peaks"],
                     help="laplace: the headline workload; stokes: Stokes flow past a sphere of 81920 panels; "
                          "serve: a Poisson stream of mixed solves through the serving runtime; "
                          "laplace2: second-kind Laplace solves on octahedron spheres of 8192-131072 panels; "
                          "sweeps: the paper's parameter studies (initial p, tolerance, p_min, red blood cell); "
                          "batch: four right-hand sides in one batched solve against four single solves; "
-                         "rbc64: Stokes flow around 64 red blood cells (131072 panels)")
+                         "rbc64: Stokes flow around 64 red blood cells (131072 panels); "
+                         "peaks: the peak rates the rooflines divide by (FP32, paired FP32, rsqrt, FP64, TF32 tensor)")
     ap.add_argument("--requests", type=int, default=48, help="serve: number of requests")
     ap.add_argument("--rate", type=float, default=20.0, help="serve: mean arrival rate (requests/s)")
     ap.add_argument("--max-active", type=int, default=6, help="serve: concurrent solves")
@@ -157,6 +157,28 @@ def measured_peaks():
         return {}
 
 
+def measure_peaks(dev, reps=3, scale=1.0):
+    """Peak rates of this GPU at its current clocks (fmmbem_peak): FP32 fma, paired FP32 fma,
+    rsqrt, FP64 fma and tcgen05 TF32 products, the best of `reps` launches each. Returns rates
+    in operations per second ("tflops" keys: flop/s / 1e12; "rsqrt_per_s": results/s)."""
+    import torch
+    from paper_1506_05957_gb300.binding import (fmmbem_peak, FMMBEM_PEAK_FFMA, FMMBEM_PEAK_FFMA2, FMMBEM_PEAK_RSQRT,
+                                                FMMBEM_PEAK_DFMA, FMMBEM_PEAK_TF32)
+    st = torch.cuda.current_stream(dev).cuda_stream
+    kinds = [("ffma", FMMBEM_PEAK_FFMA), ("ffma2", FMMBEM_PEAK_FFMA2), ("rsqrt", FMMBEM_PEAK_RSQRT),
+             ("dfma", FMMBEM_PEAK_DFMA), ("tf32", FMMBEM_PEAK_TF32)]
+    out = {}
+    for name, kind in kinds:
+        it = max(1, int(PEAK_ITERS[name] * scale))
+        fmmbem_peak(kind, max(1, it // 20), stream=st)  # warm-up launch
+        best = 0.0
+        for _ in range(reps):
+            ops, ms = fmmbem_peak(kind, it, stream=st)
+            best = max(best, ops / (ms * 1e-3))
+        out["rsqrt_per_s" if name == "rsqrt" else name + "_tflops"] = best if name == "rsqrt" else best / 1e12
+    return out
+
+
 def kernel_region(text, begin, kernel):
     """Source text from the line `begin` to the closing brace of the function `kernel`: the
     kernel and the device helpers written above it."""
@@ -251,6 +273,11 @@ def run_ours(args, world, rank, local):
     v, t, phi = problem(args.levels)
     n = len(t)
     W = WORKLOAD
+    # the roofline denominators, measured on this GPU before the solves (clocks sampled meanwhile)
+    psampler = ClockSampler(local)
+    psampler.start()
+    peaks = measure_peaks(dev)
+    peaks["clocks"] = psampler.stop()
     h = FmmBem(v, t, gauss_k=W["gauss_k"], ncrit=args.ncrit, theta=W["theta"], p_max=16, restart=W["restart"],
                max_iter=100, precision=FMMBEM_MIXED, stream=stream.cuda_stream)
     stats = h.stats()
@@ -331,37 +358,45 @@ def run_ours(args, world, rank, local):
         e2e_t.append(time.perf_counter() - t0)
     e2e = max_over_ranks(world, float(np.sum(e2e_t)), dev) / args.steps / world
 
-    # roofline of the dominant kernel class, from the library's CUDA events recorded on
-    # the stream that launches each pass, over the timed region
+    # roofline of the kernel with the largest device time, from the library's CUDA events
+    # recorded on the stream that launches each pass, over the profiled region, against peak
+    # rates measured on this GPU just before (measure_peaks)
     ms = prof["ms"]
-    smax = clocks.get("sm_max_mhz") or measured_peaks().get("sm_max_mhz", 2070.0)
     share = {k_: round(v_ / prof_wall_ms, 4) for k_, v_ in ms.items() if k_ != "matvec"}
-    p2p_ach = prof["p2p_interactions"] * P2P_FLOPS / (ms["p2p"] * 1e-3) / 1e12 if ms["p2p"] > 0 else 0.0
-    p2p_peak = SM_COUNT * MUFU_PER_SM_CLK * smax * 1e6 * P2P_FLOPS / 1e12
-    rl_p2p = {"bound": "alu", "kernel": "k_p2p_lap_src (near field, FP32 + MUFU rsqrt)", "achieved": round(p2p_ach, 3),
-              "peak": round(p2p_peak, 2), "unit": "TFLOP/s", "frac": round(p2p_ach / p2p_peak, 4),
+    share["k_m2l_tc"] = round(prof["tc_ms"] / prof_wall_ms, 4)
+    rs = peaks["rsqrt_per_s"]
+    p2p_rate = prof["p2p_interactions"] / (ms["p2p"] * 1e-3) if ms["p2p"] > 0 else 0.0
+    rl_p2p = {"bound": "alu", "kernel": "k_p2p_lap_src (near field, FP32 + MUFU rsqrt, one rsqrt per pair)",
+              "achieved": round(p2p_rate * P2P_FLOPS / 1e12, 3), "peak": round(rs * P2P_FLOPS / 1e12, 2),
+              "unit": "TFLOP/s", "frac": round(p2p_rate / rs, 4),
               # the ncu capture is of the 81920-panel workload; other sizes have no traffic figure
               "traffic": profiled_traffic("k_p2p_lap_src_traffic_laplace_ico6_81920.md") if n == 81920 else None,
-              "peak_source": "152 SMs x 16 rsqrt/clk x max SM clock x 11 flop per pair (derived, not measured)",
-              "interactions_per_s": prof["p2p_interactions"] / (ms["p2p"] * 1e-3) if ms["p2p"] else None}
-    bf16 = measured_peaks().get("bf16_tflops_sustained", 1729.8)
-    tf32_peak = bf16 * TF32_PER_BF16
-    m2l_alg = prof["m2l_flops"] / (ms["m2l"] * 1e-3) / 1e12 if ms["m2l"] > 0 else 0.0
-    rl_m2l = {"bound": "tensor", "kernel": "k_m2l_tc (M2L, tcgen05 kind::tf32, 3 products per term)",
-              "achieved": round(3 * m2l_alg, 3), "peak": round(tf32_peak, 1), "unit": "TFLOP/s",
-              "frac": round(3 * m2l_alg / tf32_peak, 4), "traffic": None,
-              "peak_source": "measured sustained BF16 x nominal TF32/BF16 ratio 1.1/2.25",
-              "algorithmic_tflops": round(m2l_alg, 3),
-              "flops_convention": "2 (p+1)^4 per pair and expansion; hardware does 3x (3xTF32)"}
-    roofline = dict(rl_p2p if ms["p2p"] >= ms["m2l"] else rl_m2l)
+              "peak_source": "measured on this GPU: rsqrt.approx.ftz.f32 results/s (fmmbem_peak RSQRT) x 11 flop per pair",
+              "interactions_per_s": p2p_rate, "ms_per_solve": round(ms["p2p"] / n_prof, 4)}
+    tf32 = peaks["tf32_tflops"]
+    tc_ach = prof["tc_flops"] / (prof["tc_ms"] * 1e-3) / 1e12 if prof["tc_ms"] > 0 else 0.0
+    rl_tc = {"bound": "tensor", "kernel": "k_m2l_tc (M2L, M2M and L2L on tcgen05 kind::tf32, 3xTF32)",
+             "achieved": round(tc_ach, 3), "peak": round(tf32 / 3.0, 2), "unit": "TFLOP/s",
+             "frac": round(tc_ach / (tf32 / 3.0), 4),
+             "traffic": profiled_traffic("k_m2l_tc_traffic_laplace_ico6_81920.md") if n == 81920 else None,
+             "peak_source": "measured on this GPU: tcgen05.mma kind::tf32 flop/s (fmmbem_peak TF32) / 3, the rate "
+                            "of FP32-accurate 3xTF32 products",
+             "peak_tf32_tflops": round(tf32, 1),
+             "peak_tf32_derived_tflops": round(measured_peaks().get("bf16_tflops_sustained", 1678.1) * TF32_PER_BF16, 1),
+             "flops_convention": "2 (p+1)^4 per M2L pair and expansion and per M2M/L2L translation; the tensor "
+                                 "pipe does 3x that (3xTF32)",
+             "ms_per_solve": round(prof["tc_ms"] / n_prof, 4)}
+    tc_dominant = prof["tc_ms"] >= ms["p2p"]
+    roofline = dict(rl_tc if tc_dominant else rl_p2p)
     roofline["time_share"] = share
     # device time not inside a mat-vec or an Arnoldi step: host round trips between steps,
     # the restart and final residuals, copies
     roofline["outside_passes_share"] = round(max(0.0, 1.0 - prof_total_ms / prof_wall_ms), 4)
     roofline["time_share_note"] = ("per-pass CUDA-event time / solve time in a profiled region of %d solves; the "
                                    "near field runs on a second stream concurrently with the far field, so shares "
-                                   "overlap" % n_prof)
-    roofline["other"] = rl_m2l if ms["p2p"] >= ms["m2l"] else rl_p2p
+                                   "overlap; k_m2l_tc = the M2M, M2L and L2L passes that ran on it" % n_prof)
+    roofline["other"] = rl_p2p if tc_dominant else rl_tc
+    roofline["peaks_measured"] = {k_: (round(v_, 4) if isinstance(v_, float) else v_) for k_, v_ in peaks.items()}
 
     out = {"metric": METRIC, "value": sec_per_solve, "unit": "s", "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "warmup_solves": k_w, "ms_per_step": t_max / args.steps * 1e3,
@@ -425,14 +460,19 @@ LAPLACE2 = dict(workload="laplace2-exterior-sphere-octa7-131072", panels=131072,
                 p_min=3, tol=1e-6, restart=50, data="phi = dphi/dn = 1 on the unit sphere (exterior, normals into the body)")
 
 STOKES = dict(workload="stokes-sphere-ico6-81920", panels=81920, unknowns=245760, gauss_k=3, theta=0.5,
-              p_initial=16, p_min=4, tol=1e-5, restart=50, ncrit=150, mu=1.0, data="u = (1,0,0) on the sphere")
+              p_initial=16, p_min=4, tol=1e-5, restart=50, ncrit=150, mu=1.0,
+              data="timed: seeded smooth random velocity field on the sphere (8 plane-wave modes, seed 0, "
+                   "area-weighted normal flux removed); "
+                   "drag check: u = (1,0,0), an eigenvector of the single layer on a sphere (one iteration)")
 
 
 def run_stokes(args, world, rank, local):
     """Stokes flow past a unit sphere (Stokeslet single layer, 3 unknowns per panel), relaxed
-    p 16 -> 4, tol 1e-5, mixed precision; drag checked against 6 pi mu a U."""
+    p 16 -> 4, tol 1e-5, mixed precision. The timed solves take a smooth random velocity field
+    (uniform motion is an eigenvector of the sphere's single layer, so GMRES would stop after one
+    step and the relaxation would never act); the drag is checked against 6 pi mu a U with u = U."""
     import torch
-    from synth import icosphere
+    from synth import icosphere, smooth_random_field
     from paper_1506_05957_gb300 import FmmBem, FMMBEM_FP64, FMMBEM_MIXED, FMMBEM_STOKES, build
     build.build()
     torch.cuda.set_device(local)
@@ -444,7 +484,14 @@ def run_stokes(args, world, rank, local):
     area = 0.5 * np.linalg.norm(np.cross(b_ - a_, c_ - a_), axis=1)
     h = FmmBem(v, t, kernel=FMMBEM_STOKES, gauss_k=W["gauss_k"], ncrit=args.ncrit, theta=W["theta"], p_max=16,
                restart=W["restart"], max_iter=100, precision=FMMBEM_MIXED, stream=stream.cuda_stream)
-    b = torch.tensor(np.tile([1.0, 0.0, 0.0], len(t)), dtype=torch.float64, device=dev)
+    bU = torch.tensor(np.tile([1.0, 0.0, 0.0], len(t)), dtype=torch.float64, device=dev)
+    # a smooth random field with its area-weighted normal flux removed: the single layer's range is
+    # orthogonal to the normal field, so only flux-free data gives a solvable first-kind system
+    nrm = np.cross(b_ - a_, c_ - a_)
+    nrm /= np.linalg.norm(nrm, axis=1)[:, None]
+    u = smooth_random_field((a_ + b_ + c_) / 3.0, seed=0)
+    u -= (np.sum(area * np.einsum("ij,ij->i", u, nrm)) / np.sum(area)) * nrm
+    b = torch.tensor(u.reshape(-1), dtype=torch.float64, device=dev)
     x = torch.zeros_like(b)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     solve = lambda: h.solve(b, x, tol=W["tol"], relax=True, p_initial=W["p_initial"], p_min=W["p_min"])
@@ -468,24 +515,35 @@ def run_stokes(args, world, rank, local):
     launches = int(h.profile()["kernel_launches"])
     t_max = max_over_ranks(world, float(np.sum([e0.elapsed_time(e1) for e0, e1 in ev])) / 1e3, dev)
     r = res[-1]
-    drag = float(np.sum(x.cpu().numpy().reshape(-1, 3)[:, 0] * area))
+    xU = torch.zeros_like(bU)
+    rU = h.solve(bU, xU, tol=W["tol"], relax=True, p_initial=W["p_initial"], p_min=W["p_min"])
+    drag = float(h.body_integrals(xU)[0, 0])
     out = {"metric": "relaxed GMRES solve s, Stokes sphere (81920 panels, 245760 unknowns) @1e-5", "value":
            t_max / args.steps / world, "unit": "s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": t_max / args.steps * 1e3, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
            "dtype": "f32+f64", "data": "synthetic", "config": dict(W, ncrit=args.ncrit, panels=len(t),
                                                                     l2="flushed between steps (512 MB write)"),
            "iters": r["iters"], "p_hist": r["p_hist"], "true_residual": r["true_res"], "gpu_launches": launches,
-           "drag": drag, "drag_rel_err_vs_6pi": abs(drag / (-6.0 * np.pi) - 1.0), "clocks": clocks}
+           "drag": drag, "drag_rel_err_vs_6pi": abs(drag / (-6.0 * np.pi) - 1.0), "drag_iters": rU["iters"],
+           "clocks": clocks}
     if not args.no_compare:
-        h.set_precision(FMMBEM_FP64)
-        x.zero_()
-        torch.cuda.synchronize(dev)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        r64 = h.solve(b, x, tol=W["tol"], relax=False, p_initial=W["p_initial"], p_min=W["p_min"])
-        e1.record(stream)
-        torch.cuda.synchronize(dev)
-        out["compare"] = {"fixed_p_fp64_s": e0.elapsed_time(e1) / 1e3, "fixed_p_fp64_iters": r64["iters"]}
+        def timed(prec, relax):
+            h.set_precision(prec)
+            x.zero_()
+            torch.cuda.synchronize(dev)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            rr = h.solve(b, x, tol=W["tol"], relax=relax, p_initial=W["p_initial"], p_min=W["p_min"])
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            return e0.elapsed_time(e1) / 1e3, rr
+        t_fixed32, r32 = timed(FMMBEM_MIXED, False)
+        t_fixed64, r64 = timed(FMMBEM_FP64, False)
+        h.set_precision(FMMBEM_MIXED)
+        out["compare"] = {"fixed_p_mixed_s": t_fixed32, "fixed_p_mixed_iters": r32["iters"],
+                          "relaxation_speedup_mixed": t_fixed32 / (t_max / args.steps),
+                          "fixed_p_fp64_s": t_fixed64, "fixed_p_fp64_iters": r64["iters"],
+                          "speedup_vs_fixed_p_fp64": t_fixed64 / (t_max / args.steps)}
     if rank == 0:
         print(json.dumps(out), flush=True)
     h.close()
@@ -943,6 +1001,28 @@ def run_serve(args, world, rank, local):
         print(json.dumps(out), flush=True)
 
 
+def run_peaks(args, world, rank, local):
+    """The roofline denominators on this GPU: each rate is the best of `steps` launches of
+    about 0.2 s, with the SM clock sampled during them (one line per rate, then a summary)."""
+    import torch
+    from paper_1506_05957_gb300 import build
+    build.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    sampler = ClockSampler(local)
+    sampler.start()
+    t0 = time.perf_counter()
+    peaks = measure_peaks(dev, reps=max(1, args.steps), scale=10.0)
+    wall = time.perf_counter() - t0
+    clocks = sampler.stop()
+    nominal = {"ffma_tflops": 152 * 128 * 2 * 2.07e9 / 1e12, "tf32_tflops": 1100.0}
+    line = {"metric": "peak rates (roofline denominators)", "peaks": peaks, "clocks": clocks, "wall_s": wall,
+            "nominal_at_2070_mhz": nominal, "hbm_gbs_measured_copy": measured_peaks().get("hbm_gbs"),
+            "bf16_tflops_measured": measured_peaks().get("bf16_tflops")}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     world, rank, local = dist_init(args)
@@ -960,6 +1040,8 @@ def main():
         run_batch(args, world, rank, local)
     elif args.problem == "rbc64":
         run_rbc64(args, world, rank, local)
+    elif args.problem == "peaks":
+        run_peaks(args, world, rank, local)
     else:
         run_ours(args, world, rank, local)
     if world > 1:

@@ -48,6 +48,8 @@ extern "C" {
 #define FMMBEM_EDEVICE (-3)  /* CUDA error reported by a launch or a copy */
 #define FMMBEM_ENAN (-4)     /* NaN/Inf met in the Krylov recurrence */
 #define FMMBEM_ESTATE (-5)   /* call not valid for this handle (e.g. Stokes-only call on a Laplace handle) */
+#define FMMBEM_ETIMEOUT (-6) /* a bounded device wait gave up (grid barrier, bulk-copy or tensor-core
+                                barrier); the results of that call are invalid, the handle stays usable */
 
 /* Operators (Sec. 2.1-2.2). */
 #define FMMBEM_LAPLACE 0     /* Laplace single layer, 1 unknown per panel */
@@ -64,12 +66,16 @@ extern "C" {
 
 /* A surface triangulation in host memory. Triangles are counter-clockwise
  * when seen from the side the normal should point to (outward for a closed
- * body). Copied to the device by fmmbem_create; not referenced afterwards. */
+ * body). Copied to the device by fmmbem_create; not referenced afterwards.
+ * A mesh may hold several bodies (the cells of the red-blood-cell configurations);
+ * body_of_panel names each panel's body for fmmbem_body_integrals. */
 typedef struct {
     int64_t n_vertices;
     const double* vertices;   /* [n_vertices][3], host */
     int64_t n_panels;
     const int32_t* triangles; /* [n_panels][3] vertex indices, host */
+    int32_t n_bodies;         /* 0 or 1: the whole mesh is one body (body_of_panel ignored) */
+    const int32_t* body_of_panel; /* [n_panels] body index in [0, n_bodies), host; required when n_bodies > 1 */
 } fmmbem_mesh;
 
 /* Options; fmmbem_default_opts fills the defaults shown. */
@@ -86,6 +92,9 @@ typedef struct {
     int nrhs;             /* 1: one vector per mat-vec. FMMBEM_BATCH (Laplace single layer only):
                              every mat-vec and solve of the handle takes FMMBEM_BATCH vectors
                              at once, laid out [FMMBEM_BATCH][n_panels] (see fmmbem_solve_batch) */
+    int near_k;           /* 20: points of the near-singular rule (Sec. 2.3 gives K ~ 20): a collapsed
+                             Gauss product of nu x (nu - 1) points, exact to total degree 2 nu - 3;
+                             one of 6, 12, 20, 30, 42 (nu = 3..7); 0 selects 20 */
 } fmmbem_opts;
 
 #define FMMBEM_BATCH 4
@@ -220,6 +229,21 @@ int fmmbem_matvec_direct(fmmbem_handle* h, const double* x_dev, double* y_dev);
 int fmmbem_rhs(fmmbem_handle* h, const double* known_dev, double* b_dev);
 
 /*
+ * Integral of a panel field over each body: out[b][a] = sum over the panels j of body b of
+ * S_j x_j[a] (a < 1 Laplace, a < 3 Stokes), in FP64. For the traction t of a Stokes solve
+ * this is the force on body b (the drag of Sec. 3.2 and Table rbc_richardson_values); for
+ * the Laplace unknown q = dphi/dn it is the flux through the body's surface.
+ *   x_dev   : [n_unknowns] doubles, device, the caller's panel order
+ *   out_host: [fmmbem_n_bodies(h)][dof] doubles, host (written before the call returns)
+ * Synchronizes the handle's stream. Errors: FMMBEM_EINVAL, FMMBEM_ESTATE on a batched handle,
+ * FMMBEM_EDEVICE.
+ */
+int fmmbem_body_integrals(fmmbem_handle* h, const double* x_dev, double* out_host);
+
+/* Number of bodies of the handle's mesh (1 when the mesh named none); -1 for NULL. */
+int fmmbem_n_bodies(const fmmbem_handle* h);
+
+/*
  * Stokes double layer (eq. stresslet, T_ijk contracted once with the panel
  * normal): y = B u with B_iJ = 1/(8 pi) int_J 6 e e^T (e.n_J)/|e|^5 dS_y,
  * e = y - c_i, by direct summation in FP64 (the self term of a flat panel is
@@ -350,17 +374,61 @@ typedef struct {
     double ms[FMMBEM_N_PASSES];       /* accumulated milliseconds */
     int64_t launches[FMMBEM_N_PASSES]; /* kernel launches counted in each pass */
     int64_t calls[FMMBEM_N_PASSES];    /* timed intervals */
-    double m2l_flops;                  /* accumulated algorithmic M2L flops (8 per complex MAC) */
+    double m2l_flops;                  /* accumulated algorithmic M2L flops: 2 (p+1)^4 per pair and expansion */
     double p2p_interactions;           /* accumulated P2P pair interactions */
     int64_t kernel_launches;           /* every kernel launched by the handle since the reset */
+    double tc_ms;                      /* milliseconds of the M2M, M2L and L2L passes that ran on the
+                                          tensor-core kernel (k_m2l_tc), a subset of ms[] */
+    double tc_flops;                   /* algorithmic flops of those passes: 2 (p+1)^4 per M2L pair and
+                                          expansion, and per M2M and per L2L translation of a cell */
 } fmmbem_profile;
 
 /* enable != 0 starts recording (and resets the counters); 0 stops. */
 int fmmbem_profile_enable(fmmbem_handle* h, int enable);
 int fmmbem_profile_get(fmmbem_handle* h, fmmbem_profile* out); /* synchronizes the stream */
 
-/* Message of the last failure in this thread ("" if none). */
+/* Message of the last failure in this thread ("" if none). The message is kept per host
+ * thread, not per handle, because fmmbem_create can fail before any handle exists. */
 const char* fmmbem_last_error(void);
+
+/*
+ * Bounded device waits. Every wait inside the library's kernels (the grid barrier of the
+ * cooperative Arnoldi step, the near field's bulk-copy stages, the tensor-core pipeline's
+ * mbarriers) gives up after a fixed number of polls and raises a flag on the handle rather
+ * than hold the GPU. fmmbem_solve and fmmbem_solve_batch clear the flags on entry and return
+ * FMMBEM_ETIMEOUT when one was raised during the solve. fmmbem_matvec and
+ * fmmbem_matvec_direct are asynchronous and do not read them: fmmbem_check_waits does.
+ */
+/* Synchronize the handle's streams, read and clear its wait flags: 0, or FMMBEM_ETIMEOUT when a
+ * wait of the work queued since the last check gave up (the results of that work are invalid). */
+int fmmbem_check_waits(fmmbem_handle* h);
+/* Test hook: polls (about 64 ns each) after which a grid-barrier wait of the Arnoldi step gives
+ * up; 0 restores the default 2^26. A tiny limit makes the waits run out on purpose, so that the
+ * error path can be exercised without a fault: the solve returns FMMBEM_ETIMEOUT, the barrier
+ * counters are reset and the handle stays usable. */
+int fmmbem_set_wait_limit(fmmbem_handle* h, unsigned limit);
+
+/*
+ * Peak rates of this GPU at its current clocks: the denominators of the rooflines (the paper
+ * has no counterpart; it is a measurement interface). One launch of `blocks` blocks
+ * (0: 4 blocks of 256 threads per SM, one CTA per SM for TF32; at most one per SM for TF32)
+ * runs `iters` iterations of eight independent chains per thread of one operation:
+ *   FFMA  : fma.rn.f32                    2 flop each
+ *   FFMA2 : fma.rn.f32x2 (paired FP32)    4 flop each
+ *   RSQRT : rsqrt.approx.ftz.f32 (special-function unit), 1 result each
+ *   DFMA  : FP64 fma                      2 flop each
+ *   TF32  : tcgen05.mma.kind::tf32, M 128, N 256, K 8, from shared memory into TMEM,
+ *           2 M N K flop each, 4 per iteration
+ * ops receives the operations done, ms the CUDA-event time of the launch on `stream`
+ * (synchronizes it). Errors: FMMBEM_EINVAL, FMMBEM_EDEVICE, FMMBEM_ETIMEOUT (the tensor-core
+ * completion wait gave up).
+ */
+#define FMMBEM_PEAK_FFMA 0
+#define FMMBEM_PEAK_FFMA2 1
+#define FMMBEM_PEAK_RSQRT 2
+#define FMMBEM_PEAK_DFMA 3
+#define FMMBEM_PEAK_TF32 4
+int fmmbem_peak(int kind, int blocks, int64_t iters, double* ops, double* ms, void* stream);
 
 /*
  * ---- Serving many solves at once.

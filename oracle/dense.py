@@ -55,7 +55,13 @@ class Mesh:
         self.n = len(self.pv)
         self.k = k
         fb, fw = triangle_rule(k)
-        nb, nw = near_rule() if near_k == 20 else triangle_rule(near_k)
+        # near rule: a collapsed Gauss product of nu x (nu - 1) points (5 x 4 = 20 by default,
+        # the K ~ 20 of Sec. 2.3); other point counts name a plain triangle rule
+        nu = int(round((1.0 + np.sqrt(1.0 + 4.0 * near_k)) / 2.0))
+        if nu * (nu - 1) == near_k and 3 <= nu <= 7:
+            nb, nw = near_rule(nu, nu - 1)
+        else:
+            nb, nw = triangle_rule(near_k)
         self.fb, self.fw = np.ascontiguousarray(fb), np.ascontiguousarray(fw)
         self.nb, self.nw = np.ascontiguousarray(nb), np.ascontiguousarray(nw)
         self.near_factor = float(near_factor)

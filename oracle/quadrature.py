@@ -76,4 +76,6 @@ def near_rule(nu=5, nv=4):
 
 
 def rule_degree(k):
-    return {1: 1, 3: 2, 4: 3, 7: 5, 20: 7}[k]
+    """Total degree integrated exactly: the triangle rules, and the collapsed near rules of
+    nu x (nu - 1) points (degree 2 (nu - 1) - 1 from the nu - 1 nodes in v)."""
+    return {1: 1, 3: 2, 4: 3, 7: 5, 6: 3, 12: 5, 20: 7, 30: 9, 42: 11}[k]

@@ -20,6 +20,7 @@ FMMBEM_ENOMEM = -2
 FMMBEM_EDEVICE = -3
 FMMBEM_ENAN = -4
 FMMBEM_ESTATE = -5
+FMMBEM_ETIMEOUT = -6
 FMMBEM_LAPLACE = 0
 FMMBEM_STOKES = 1
 FMMBEM_FP64 = 0
@@ -31,17 +32,23 @@ FMMBEM_M2L_TENSOR = 2
 FMMBEM_LAYER_SINGLE = 0
 FMMBEM_LAYER_DOUBLE = 1
 PASS_NAMES = ["p2m", "m2m", "m2l", "l2l", "l2p", "p2p", "krylov", "matvec"]
+FMMBEM_PEAK_FFMA = 0
+FMMBEM_PEAK_FFMA2 = 1
+FMMBEM_PEAK_RSQRT = 2
+FMMBEM_PEAK_DFMA = 3
+FMMBEM_PEAK_TF32 = 4
 
 
 class fmmbem_mesh(ctypes.Structure):
     _fields_ = [("n_vertices", ctypes.c_int64), ("vertices", ctypes.POINTER(ctypes.c_double)),
-                ("n_panels", ctypes.c_int64), ("triangles", ctypes.POINTER(ctypes.c_int32))]
+                ("n_panels", ctypes.c_int64), ("triangles", ctypes.POINTER(ctypes.c_int32)),
+                ("n_bodies", ctypes.c_int32), ("body_of_panel", ctypes.POINTER(ctypes.c_int32))]
 
 
 class fmmbem_opts(ctypes.Structure):
     _fields_ = [("p_max", ctypes.c_int), ("near_factor", ctypes.c_double), ("mu", ctypes.c_double),
                 ("precision", ctypes.c_int), ("restart", ctypes.c_int), ("max_iter", ctypes.c_int),
-                ("stream", ctypes.c_void_p), ("nrhs", ctypes.c_int)]
+                ("stream", ctypes.c_void_p), ("nrhs", ctypes.c_int), ("near_k", ctypes.c_int)]
 
 
 class fmmbem_stats(ctypes.Structure):
@@ -54,7 +61,7 @@ class fmmbem_stats(ctypes.Structure):
 class fmmbem_profile(ctypes.Structure):
     _fields_ = [("ms", ctypes.c_double * 8), ("launches", ctypes.c_int64 * 8), ("calls", ctypes.c_int64 * 8),
                 ("m2l_flops", ctypes.c_double), ("p2p_interactions", ctypes.c_double),
-                ("kernel_launches", ctypes.c_int64)]
+                ("kernel_launches", ctypes.c_int64), ("tc_ms", ctypes.c_double), ("tc_flops", ctypes.c_double)]
 
 
 class fmmbem_result(ctypes.Structure):
@@ -117,6 +124,11 @@ def lib():
         L.fmmbem_profile_enable.argtypes = [_vp, ctypes.c_int]
         L.fmmbem_profile_get.argtypes = [_vp, ctypes.POINTER(fmmbem_profile)]
         L.fmmbem_last_error.restype = ctypes.c_char_p
+        L.fmmbem_body_integrals.argtypes = [_vp, _vp, _vp]
+        L.fmmbem_n_bodies.argtypes = [_vp]
+        L.fmmbem_check_waits.argtypes = [_vp]
+        L.fmmbem_set_wait_limit.argtypes = [_vp, ctypes.c_uint]
+        L.fmmbem_peak.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int64, _dp, _dp, _vp]
         _lib = L
     return _lib
 
@@ -173,18 +185,33 @@ def fmmbem_expansion_eval_static(kind, p, center, scale, src, tgt, out, stream=N
                                               int(tgt.shape[0]), _dev(tgt), _dev(out), _vp(stream)))
 
 
+def fmmbem_peak(kind, iters, blocks=0, stream=None):
+    """fmmbem_peak: (operations, milliseconds) of one peak-rate launch (synchronizes the stream)."""
+    ops, ms = ctypes.c_double(0.0), ctypes.c_double(0.0)
+    _check(lib().fmmbem_peak(int(kind), int(blocks), int(iters), ctypes.byref(ops), ctypes.byref(ms), _vp(stream)))
+    return ops.value, ms.value
+
+
 class FmmBem:
     """One resident BEM problem: fmmbem_create ... fmmbem_destroy."""
 
     def __init__(self, vertices, triangles, kernel=FMMBEM_LAPLACE, gauss_k=4, ncrit=150, theta=0.5, p_max=16,
-                 near_factor=2.0, mu=1.0, precision=FMMBEM_MIXED, restart=50, max_iter=100, stream=None, nrhs=1):
+                 near_factor=2.0, mu=1.0, precision=FMMBEM_MIXED, restart=50, max_iter=100, stream=None, nrhs=1,
+                 near_k=20, body_of_panel=None):
         v = np.ascontiguousarray(vertices, dtype=np.float64)
         t = np.ascontiguousarray(triangles, dtype=np.int32)
         mesh = fmmbem_mesh(len(v), v.ctypes.data_as(_dp), len(t), t.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)))
+        if body_of_panel is not None:
+            bop = np.ascontiguousarray(body_of_panel, dtype=np.int32)
+            if bop.shape != (len(t),):
+                raise ValueError("body_of_panel needs one entry per panel")
+            mesh.n_bodies = int(bop.max()) + 1 if len(bop) else 0
+            mesh.body_of_panel = bop.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
         o = fmmbem_default_opts()
         o.p_max, o.near_factor, o.mu, o.precision = p_max, near_factor, mu, precision
         o.restart, o.max_iter = restart, max_iter
         o.nrhs = nrhs
+        o.near_k = near_k
         if stream is None:
             import torch
             stream = torch.cuda.current_stream().cuda_stream
@@ -199,6 +226,7 @@ class FmmBem:
         self.p_max = int(p_max)
         self.n = int(lib().fmmbem_n_unknowns(h)) * self.nrhs  # doubles per mat-vec vector (all of a batch)
         self.n_panels = len(t)
+        self.n_bodies = int(lib().fmmbem_n_bodies(h))
 
     def close(self):
         if getattr(self, "h", None):
@@ -224,6 +252,23 @@ class FmmBem:
         ch = np.full(FMMBEM_P_MAX + 1, -1, dtype=np.int32)
         _check(lib().fmmbem_autotune(self.h, int(p_lo), int(p_hi), _vp(ch.ctypes.data)))
         return {p: int(ch[p]) for p in range(p_lo, p_hi + 1)}
+
+    def body_integrals(self, x):
+        """fmmbem_body_integrals: [n_bodies, dof] sums of S_j x_j over each body's panels (Stokes traction
+        -> force on each body)."""
+        dof = 3 if self.kernel == FMMBEM_STOKES else 1
+        out = np.zeros((self.n_bodies, dof), dtype=np.float64)
+        _check(lib().fmmbem_body_integrals(self.h, _dev(x, self.n), _vp(out.ctypes.data)))
+        return out
+
+    def check_waits(self):
+        """fmmbem_check_waits: raises FmmBemError(FMMBEM_ETIMEOUT) if a bounded device wait of the work
+        queued since the last check gave up (mat-vecs do not report it themselves)."""
+        _check(lib().fmmbem_check_waits(self.h))
+
+    def set_wait_limit(self, limit):
+        """Test hook: polls before a grid-barrier wait of the Arnoldi step gives up (0 = default)."""
+        _check(lib().fmmbem_set_wait_limit(self.h, int(limit)))
 
     def set_p2p_variant(self, variant):
         _check(lib().fmmbem_set_p2p_variant(self.h, int(variant)))
@@ -290,7 +335,7 @@ class FmmBem:
                     launches={PASS_NAMES[i]: pr.launches[i] for i in range(8)},
                     calls={PASS_NAMES[i]: pr.calls[i] for i in range(8)},
                     m2l_flops=pr.m2l_flops, p2p_interactions=pr.p2p_interactions,
-                    kernel_launches=pr.kernel_launches)
+                    kernel_launches=pr.kernel_launches, tc_ms=pr.tc_ms, tc_flops=pr.tc_flops)
 
 
 class FmmBemServer:

@@ -46,6 +46,18 @@ __global__ void k_perm_out(const double* ys, const int* perm, int64_t n, int dof
     for (int a = 0; a < dof; ++a) y[off + dof * i + a] = ys[off + dof * s + a];
 }
 
+// out[body][a] += S_s x[perm[s]][a] over the sorted panels s (FP64 atomics; the order of the
+// additions is not fixed, so the sums agree with a serial sum to rounding)
+__global__ void k_body_sums(const double* x, const int* perm, const double4* tgt, const int* body, int64_t n, int dof,
+                            double* out) {
+    int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    const int64_t i = perm[s];
+    const int b = body ? body[s] : 0;
+    const double S = tgt[s].w;
+    for (int a = 0; a < dof; ++a) atomicAdd(out + (int64_t)b * dof + a, S * x[dof * i + a]);
+}
+
 __global__ void k_axpy_half(double* y, const double* x, int64_t n) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i < n) y[i] += 0.5 * x[i];
@@ -55,6 +67,7 @@ struct ProfRec {
     int pass;
     int launches;
     cudaEvent_t a, b;
+    bool tc;  // the pass ran on the tensor-core kernel
 };
 struct ProfState {
     std::vector<cudaEvent_t> pool;
@@ -170,13 +183,14 @@ void prof_end(fmmbem_handle* h, int pass, int launches) {
         if (!e) cudaEventCreate(&e);
         cudaEventRecordWithFlags(e, h->stream, cudaEventRecordExternal);
         h->gev_launches[h->capturing][pass] = launches;
+        h->gev_tc[h->capturing] = h->tc_pass_bits;
         return;
     }
     ProfState* s = prof_state(h);
     if (!s->open[pass]) return;
     cudaEvent_t e = prof_event(s);
     cudaEventRecord(e, h->stream);
-    s->recs.push_back({pass, launches, s->open[pass], e});
+    s->recs.push_back({pass, launches, s->open[pass], e, ((h->tc_pass_bits >> pass) & 1) != 0});
     s->open[pass] = nullptr;
 }
 
@@ -192,7 +206,20 @@ void prof_harvest(fmmbem_handle* h) {
         h->prof.ms[pass] += ms;
         h->prof.launches[pass] += h->gev_launches[p][pass];
         h->prof.calls[pass] += 1;
+        if ((h->gev_tc[p] >> pass) & 1) h->prof.tc_ms += ms;
     }
+}
+
+// Algorithmic flops of the passes of one mat-vec at order p that run on the tensor-core
+// kernel: 2 (p+1)^4 per M2L pair and expansion, the same per M2M and per L2L translation
+// (one per non-root cell).
+static double tc_flops(const fmmbem_handle* h, int p) {
+    if (h->precision != FMMBEM_MIXED || h->m2l_mode != FMMBEM_M2L_TENSOR || !h->m2l_tc_ready) return 0.0;
+    const double q = (double)(p + 1) * (p + 1), per = 2.0 * q * q * h->ncomp;
+    double f = 0.0;
+    if (h->m2l_tc_at[p]) f += per * (double)h->n_m2l;
+    if (h->tree_tc_at[p] && h->tree_tiles) f += 2.0 * per * (double)(h->n_cells - 1);
+    return f;
 }
 
 static int matvec_launch(fmmbem_handle* h, int p, const double* xs, double* ys);
@@ -234,6 +261,7 @@ int matvec_sorted(fmmbem_handle* h, int p, const double* xs, double* ys) {
         const double q = (double)(p + 1) * (p + 1);
         h->prof.m2l_flops += 2.0 * q * q * h->ncomp * (double)h->n_m2l;
         h->prof.p2p_interactions += (double)h->n_p2p_inter;
+        h->prof.tc_flops += tc_flops(h, p);
     }
     return 0;
 }
@@ -252,10 +280,11 @@ static int matvec_launch(fmmbem_handle* h, int p, const double* xs, double* ys) 
     FMM_CU(cudaStreamWaitEvent(h->stream, h->ev_join, 0));
     FMM_TRY(far_eval_add(h, p, fp64, ys, operator_scale(h)));
     prof_end(h, FMMBEM_PASS_MATVEC, 0);
-    if (h->prof_on) {
+    if (h->prof_on && h->capturing < 0) {  // a captured graph counts its work at each replay
         const double q = (double)(p + 1) * (p + 1);
         h->prof.m2l_flops += 2.0 * q * q * h->ncomp * (double)h->n_m2l;
         h->prof.p2p_interactions += (double)h->n_p2p_inter;
+        h->prof.tc_flops += tc_flops(h, p);
     }
     return 0;
 }
@@ -278,6 +307,7 @@ int fmmbem_default_opts(fmmbem_opts* o) {
     o->max_iter = 100;
     o->stream = nullptr;
     o->nrhs = 1;
+    o->near_k = 20;
     return 0;
 }
 
@@ -292,7 +322,7 @@ void fmmbem_destroy(fmmbem_handle* h) {
     if (h->stream2) cudaStreamSynchronize(h->stream2);
     if (h->istream) cudaStreamSynchronize(h->istream);
     fmm_alloc_stream() = h->stream;
-    void* bufs[] = {h->perm, h->tgt_d, h->tgt_f, h->nrm_d, h->nrm_f, h->verts, h->src_d, h->src_f, h->src_rel, h->tgt_rel, h->src_w, h->cell_cs, h->cell_range, h->cell_rad,
+    void* bufs[] = {h->perm, h->body, h->body_acc, h->tgt_d, h->tgt_f, h->nrm_d, h->nrm_f, h->verts, h->src_d, h->src_f, h->src_rel, h->tgt_rel, h->src_w, h->cell_cs, h->cell_range, h->cell_rad,
                     h->cell_child, h->cell_level, h->cell_parent, h->leaves, h->parents, h->leaf_class, h->m2l_ptr, h->m2l_src, h->p2p_ptr,
                     h->p2p_src, h->p2p_rec, h->p2p_off, h->p2p_len, h->p2p_items, h->p2p_cnt, h->p2p_toff, h->stage_ptr, h->stage_first, h->stage_bytes, h->corr_ptr, h->corr_col, h->corr_sl, h->corr_dl, h->oct_d, h->oct_f, h->M, h->L,
                     h->xs, h->ys, h->ynear, h->m2l_pt, h->m2l_ps, h->m2l_refl, h->sign_f, h->sign_d, h->m2l_tiles, h->tab_d, h->tab_f, h->tab_tc, h->m2l_tiles_tc, h->tc_src_info, h->tc_dst_info, h->tree_tab_tc, h->tree_tiles, h->tree_info, h->tc_err, h->kerr, h->V, h->kw, h->xfix, h->kb, h->kx, h->kr, h->kpart, h->kh, h->kyv, h->arn_bar};
@@ -339,6 +369,20 @@ int fmmbem_create(const fmmbem_mesh* mesh, int kernel, int gauss_k, int ncrit, d
     if (o.precision != FMMBEM_FP64 && o.precision != FMMBEM_MIXED) { fmmbem_set_error("bad precision"); return FMMBEM_EINVAL; }
     if (o.nrhs != 1 && o.nrhs != FMMBEM_BATCH) { fmmbem_set_error("nrhs must be 1 or %d", FMMBEM_BATCH); return FMMBEM_EINVAL; }
     if (o.nrhs != 1 && kernel != FMMBEM_LAPLACE) { fmmbem_set_error("batched handles are Laplace only"); return FMMBEM_EINVAL; }
+    if (o.near_k == 0) o.near_k = 20;  // callers that fill the options themselves get the default rule
+    if (o.near_k != 6 && o.near_k != 12 && o.near_k != 20 && o.near_k != 30 && o.near_k != 42) {
+        fmmbem_set_error("near_k must be 6, 12, 20, 30 or 42 (collapsed products of nu x (nu - 1) points)");
+        return FMMBEM_EINVAL;
+    }
+    if (mesh->n_bodies > 1) {
+        if (!mesh->body_of_panel) { fmmbem_set_error("n_bodies > 1 needs body_of_panel"); return FMMBEM_EINVAL; }
+        for (int64_t j = 0; j < mesh->n_panels; ++j)
+            if (mesh->body_of_panel[j] < 0 || mesh->body_of_panel[j] >= mesh->n_bodies) {
+                fmmbem_set_error("body_of_panel[%lld] = %d outside [0, %d)", (long long)j, mesh->body_of_panel[j],
+                                 mesh->n_bodies);
+                return FMMBEM_EINVAL;
+            }
+    }
 
     fmmbem_handle* h = new fmmbem_handle();
     fmm_alloc_stream() = (cudaStream_t)o.stream;
@@ -385,6 +429,23 @@ int fmmbem_create(const fmmbem_mesh* mesh, int kernel, int gauss_k, int ncrit, d
     }
     int rc = build_geometry_tree_lists(h, mesh);
     if (rc < 0) return fail(rc);
+    h->n_bodies = mesh->n_bodies > 1 ? mesh->n_bodies : 1;
+    if ((rc = dalloc(&h->body_acc, (size_t)h->n_bodies * h->dof)) < 0) return fail(rc);
+    if (mesh->n_bodies > 1) {  // each sorted panel's body: body[s] = body_of_panel[perm[s]]
+        std::vector<int> perm_h(h->N), body_h(h->N);
+        if (cudaMemcpyAsync(perm_h.data(), h->perm, sizeof(int) * h->N, cudaMemcpyDeviceToHost, h->stream) != cudaSuccess ||
+            cudaStreamSynchronize(h->stream) != cudaSuccess) {
+            fmmbem_set_error("create: %s", cudaGetErrorString(cudaGetLastError()));
+            return fail(FMMBEM_EDEVICE);
+        }
+        for (int64_t s_ = 0; s_ < h->N; ++s_) body_h[s_] = mesh->body_of_panel[perm_h[s_]];
+        if ((rc = dalloc(&h->body, h->N)) < 0) return fail(rc);
+        if (cudaMemcpyAsync(h->body, body_h.data(), sizeof(int) * h->N, cudaMemcpyHostToDevice, h->stream) != cudaSuccess ||
+            cudaStreamSynchronize(h->stream) != cudaSuccess) {
+            fmmbem_set_error("create: %s", cudaGetErrorString(cudaGetLastError()));
+            return fail(FMMBEM_EDEVICE);
+        }
+    }
     rc = init_octant_tables(h);
     if (rc < 0) return fail(rc);
     rc = init_near_attrs();
@@ -439,6 +500,22 @@ int fmmbem_create(const fmmbem_mesh* mesh, int kernel, int gauss_k, int ncrit, d
 }
 
 int64_t fmmbem_n_unknowns(const fmmbem_handle* h) { return h ? h->N * h->dof : -1; }
+
+int fmmbem_n_bodies(const fmmbem_handle* h) { return h ? h->n_bodies : -1; }
+
+int fmmbem_body_integrals(fmmbem_handle* h, const double* x_dev, double* out_host) {
+    if (!h || !x_dev || !out_host) { fmmbem_set_error("NULL argument"); return FMMBEM_EINVAL; }
+    if (h->nrhs > 1) { fmmbem_set_error("body integrals take one vector (not a batched handle)"); return FMMBEM_ESTATE; }
+    const size_t bytes = sizeof(double) * h->n_bodies * h->dof;
+    FMM_CU(cudaMemsetAsync(h->body_acc, 0, bytes, h->stream));
+    k_body_sums<<<(unsigned)((h->N + 255) / 256), 256, 0, h->stream>>>(x_dev, h->perm, h->tgt_d, h->body, h->N, h->dof,
+                                                                       h->body_acc);
+    FMM_LAUNCHED();
+    h->launches += 1;
+    FMM_CU(cudaMemcpyAsync(out_host, h->body_acc, bytes, cudaMemcpyDeviceToHost, h->stream));
+    FMM_CU(cudaStreamSynchronize(h->stream));
+    return 0;
+}
 
 int fmmbem_set_precision(fmmbem_handle* h, int precision) {
     if (!h || (precision != FMMBEM_FP64 && precision != FMMBEM_MIXED)) { fmmbem_set_error("bad precision"); return FMMBEM_EINVAL; }
@@ -630,6 +707,20 @@ int fmmbem_expansion_eval(int kind, int p, const double* center, double scale, i
     return fmmbem::expansion_eval(kind, p, center, scale, n_src, src_dev, n_tgt, tgt_dev, out_dev, (cudaStream_t)stream);
 }
 
+int fmmbem_check_waits(fmmbem_handle* h) {
+    if (!h) { fmmbem_set_error("NULL handle"); return FMMBEM_EINVAL; }
+    FMM_CU(cudaStreamSynchronize(h->stream2));
+    FMM_CU(cudaStreamSynchronize(h->istream));
+    return read_wait_flags(h, h->stream);
+}
+
+int fmmbem_set_wait_limit(fmmbem_handle* h, unsigned limit) {
+    if (!h) { fmmbem_set_error("NULL handle"); return FMMBEM_EINVAL; }
+    h->wait_limit = limit ? limit : (1u << 26);
+    return 0;
+}
+
+
 int fmmbem_get_stats(const fmmbem_handle* h, fmmbem_stats* s) {
     if (!h || !s) { fmmbem_set_error("NULL argument"); return FMMBEM_EINVAL; }
     s->n_panels = h->N;
@@ -674,6 +765,7 @@ int fmmbem_profile_get(fmmbem_handle* h, fmmbem_profile* out) {
         h->prof.ms[r.pass] += ms;
         h->prof.launches[r.pass] += r.launches;
         h->prof.calls[r.pass] += 1;
+        if (r.tc) h->prof.tc_ms += ms;
     }
     s->recs.clear();
     s->used = 0;

@@ -1019,6 +1019,11 @@ int far_field_t(fmmbem_handle* h, int p) {
     // tensor-core tree translations in the mixed-precision M2L-TENSOR mode
     const bool tree_tc_on = std::is_same<T, float>::value && h->m2l_mode == FMMBEM_M2L_TENSOR && h->m2l_tc_ready &&
                             h->tree_tiles != nullptr && h->tree_tc_at[p];
+    const bool m2l_tc_on = std::is_same<T, float>::value && h->m2l_mode == FMMBEM_M2L_TENSOR && h->m2l_tc_ready &&
+                           h->m2l_tc_at[p];
+    // passes of this mat-vec that run on the tensor-core kernel (profiling attributes their time to it)
+    h->tc_pass_bits = (tree_tc_on ? (1 << FMMBEM_PASS_M2M) | (1 << FMMBEM_PASS_L2L) : 0) |
+                      (m2l_tc_on ? 1 << FMMBEM_PASS_M2L : 0);
     // M2M, deepest non-leaf level first
     prof_begin(h, FMMBEM_PASS_M2M);
     int nl = 0;
@@ -1027,7 +1032,7 @@ int far_field_t(fmmbem_handle* h, int p) {
         FMM_TRY(tree_tc_zero(h, p));
         ++nl;
     }
-    for (int l = h->n_levels - 2; l >= 0; --l) {
+    for (int l = h->n_levels - 2; l >= h->m2m_lmin; --l) {
         const int pb = h->parent_start[l], pe = h->parent_start[l + 1];
         if (pe == pb) continue;
         if (tree_tc_on) {
@@ -1042,7 +1047,7 @@ int far_field_t(fmmbem_handle* h, int p) {
     prof_end(h, FMMBEM_PASS_M2M, nl);
     // M2L
     prof_begin(h, FMMBEM_PASS_M2L);
-    if (std::is_same<T, float>::value && h->m2l_mode == FMMBEM_M2L_TENSOR && h->m2l_tc_ready && h->m2l_tc_at[p]) {
+    if (m2l_tc_on) {
         FMM_TRY(m2l_tc(h, p));
     } else if (h->m2l_mode != FMMBEM_M2L_GATHER && h->m2l_tables) {
         FMM_TRY(m2l_gemm(h, p, !std::is_same<T, float>::value));
@@ -1055,7 +1060,7 @@ int far_field_t(fmmbem_handle* h, int p) {
     prof_begin(h, FMMBEM_PASS_L2L);
     int nl2 = 0;
     const size_t sm_l2l = (size_t)(NC + 8) * nco * 2 * sizeof(T);
-    for (int l = 0; l + 1 < h->n_levels; ++l) {
+    for (int l = h->l2l_lmin; l + 1 < h->n_levels; ++l) {
         const int pb = h->parent_start[l], pe = h->parent_start[l + 1];
         if (pe == pb) continue;
         if (tree_tc_on) {
@@ -1125,17 +1130,26 @@ int expansion_eval(int kind, int p, const double* center, double scale, int n_sr
     FMM_TRY(ensure_degree_table());
     double* E = nullptr;
     FMM_CU(cudaMalloc((void**)&E, sizeof(double) * NCOEF_MAX * 2));
+    // every exit below releases E
+    auto finish = [&](int rc) {
+        cudaStreamSynchronize(st);
+        cudaFree(E);
+        return rc;
+    };
     k_form_expansion<<<1, coef_block(p), 0, st>>>(kind, p, center[0], center[1], center[2], scale, n_src,
                                                   reinterpret_cast<const double4*>(src), E);
-    FMM_LAUNCHED();
-    if (n_tgt > 0) {
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess && n_tgt > 0) {
         k_eval_expansion<<<(n_tgt + 127) / 128, 128, 0, st>>>(kind, p, center[0], center[1], center[2], scale, E, n_tgt,
                                                              tgt, out);
-        FMM_LAUNCHED();
+        e = cudaGetLastError();
     }
-    FMM_CU(cudaStreamSynchronize(st));
-    cudaFree(E);
-    return 0;
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        fmmbem_set_error("expansion_eval: %s", cudaGetErrorString(e));
+        return finish(FMMBEM_EDEVICE);
+    }
+    return finish(0);
 }
 
 }  // namespace fmmbem
@@ -1154,17 +1168,16 @@ namespace {
 // coefficients = 2448 bytes. Every GPU that loads the library holds it until exit.
 static __device__ __align__(256) double g_expansion_scratch[fmmbem::NCOEF_MAX * 2];
 
-struct ScratchSlot {
-    std::once_flag once;
-    double* ptr = nullptr;
-    cudaError_t err = cudaSuccess;
-};
+// Per device: the scratch array's device address once its set-up has succeeded. A failed
+// set-up (say, a first call made inside a stream capture) is not cached: the next call on
+// that device tries again.
 constexpr int kMaxDevices = 64;
-ScratchSlot g_scratch_slots[kMaxDevices];
+std::mutex g_scratch_mutex;
+double* g_scratch_ptr[kMaxDevices] = {};
 
-// Per-device set-up, done once with that device current: the device address of the
-// scratch array (host code only sees a host-side stand-in for the symbol) and the
-// degree table the kernels read from constant memory.
+// Per-device set-up, with that device current: the device address of the scratch array
+// (host code only sees a host-side stand-in for the symbol) and the degree table the
+// kernels read from constant memory (shared with the allocating path).
 int scratch_address(double** out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -1176,20 +1189,19 @@ int scratch_address(double** out) {
         fmmbem_set_error("device ordinal %d beyond the %d supported", dev, kMaxDevices);
         return FMMBEM_EDEVICE;
     }
-    ScratchSlot& s = g_scratch_slots[dev];
-    std::call_once(s.once, [&s]() {
-        s.err = cudaGetSymbolAddress((void**)&s.ptr, g_expansion_scratch);
-        if (s.err != cudaSuccess) return;
-        unsigned char deg[fmmbem::NCOEF_MAX];
-        for (int n = 0; n <= fmmbem::PMAX; ++n)
-            for (int m = 0; m <= n; ++m) deg[fmmbem::cidx(n, m)] = (unsigned char)n;
-        s.err = cudaMemcpyToSymbol(fmmbem::c_deg, deg, sizeof(deg));
-    });
-    if (s.err != cudaSuccess || !s.ptr) {
-        fmmbem_set_error("static scratch set-up on device %d: %s", dev, cudaGetErrorString(s.err));
-        return FMMBEM_EDEVICE;
+    std::lock_guard<std::mutex> lock(g_scratch_mutex);
+    if (!g_scratch_ptr[dev]) {
+        const int rc = fmmbem::ensure_degree_table();
+        if (rc < 0) return rc;
+        double* p = nullptr;
+        e = cudaGetSymbolAddress((void**)&p, g_expansion_scratch);
+        if (e != cudaSuccess || !p) {
+            fmmbem_set_error("static scratch set-up on device %d: %s", dev, cudaGetErrorString(e));
+            return FMMBEM_EDEVICE;
+        }
+        g_scratch_ptr[dev] = p;
     }
-    *out = s.ptr;
+    *out = g_scratch_ptr[dev];
     return 0;
 }
 

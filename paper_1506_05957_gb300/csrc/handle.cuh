@@ -30,11 +30,16 @@ struct fmmbem_handle {
     int pending_graph = -1;      // last replayed graph whose pass events await harvesting
     cudaEvent_t gev[FMMBEM_P_MAX + 1][2 * FMMBEM_N_PASSES] = {};
     int gev_launches[FMMBEM_P_MAX + 1][FMMBEM_N_PASSES] = {};
+    int gev_tc[FMMBEM_P_MAX + 1] = {};  // tc_pass_bits of each captured graph
+    int tc_pass_bits = 0;               // passes of the mat-vec being issued that run on k_m2l_tc
     int64_t N = 0;   // panels
     int64_t NS = 0;  // Gauss points = K * N
 
     // geometry, in Morton-sorted panel order
     int* perm = nullptr;          // [N] sorted index -> caller's index
+    int n_bodies = 1;
+    int* body = nullptr;          // [N] body of each panel, sorted order (NULL: one body)
+    double* body_acc = nullptr;   // [n_bodies][dof] sums of fmmbem_body_integrals
     double4* tgt_d = nullptr;     // [N] centroid (x,y,z, area)
     float4* tgt_f = nullptr;
     double4* nrm_d = nullptr;     // [N] unit normal (x,y,z, area)
@@ -51,6 +56,10 @@ struct fmmbem_handle {
 
     // octree (cells in breadth-first order, levels contiguous)
     int n_cells = 0, n_leaves = 0, n_levels = 0;
+    // shallowest level holding an M2L source / target: the multipoles of shallower cells are
+    // never read and their local expansions stay zero, so M2M into and L2L out of the levels
+    // above are skipped
+    int m2m_lmin = 0, l2l_lmin = 0;
     std::vector<int> level_start;  // host, [n_levels + 1]
     double4* cell_cs = nullptr;    // [n_cells] centre (x,y,z) and side
     int2* cell_range = nullptr;    // [n_cells] sorted panel range [begin, end)
@@ -156,6 +165,7 @@ struct fmmbem_handle {
     // fused Arnoldi step (cooperative launch)
     int arn_blocks = 0;
     unsigned* arn_bar = nullptr;       // grid barrier counter and generation
+    unsigned wait_limit = 1u << 26;    // polls before a grid-barrier wait gives up (fmmbem_set_wait_limit)
     double* arn_out_host = nullptr;    // mapped pinned: h1[65], h2[65], ||w||^2
     double* arn_out_dev = nullptr;
 
@@ -195,6 +205,9 @@ int relaxed_p(double eta, double rho_prev, int p_initial, int p_min);
 int arnoldi_blocks();
 int gmres_solve(fmmbem_handle* h, const double* b_sorted, double tol, int relax, int p_initial, int p_min,
                 double* x_sorted, int* iters, int* p_hist, double* res_hist, double* true_res);
+int read_wait_flags(fmmbem_handle* h, cudaStream_t st);
+// peaks.cu
+int peak_rate(int kind, int blocks, int64_t iters, double* ops, double* ms, cudaStream_t st);
 // capi.cu
 int matvec_sorted(fmmbem_handle* h, int p, const double* xs, double* ys);
 void prof_begin(fmmbem_handle* h, int pass);

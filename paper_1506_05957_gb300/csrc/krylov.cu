@@ -94,7 +94,8 @@ __global__ void k_sub(double* r, const double* b, const double* ax, int64_t n) {
 constexpr int ARN_THREADS = 512;
 constexpr int ARN_MAXV = 64;
 
-__device__ __forceinline__ bool grid_barrier(unsigned* count, volatile unsigned* gen, unsigned nb, int* err) {
+__device__ __forceinline__ bool grid_barrier(unsigned* count, volatile unsigned* gen, unsigned nb, int* err,
+                                             unsigned limit) {
     __syncthreads();
     bool ok = true;
     if (threadIdx.x == 0) {
@@ -107,7 +108,7 @@ __device__ __forceinline__ bool grid_barrier(unsigned* count, volatile unsigned*
         } else {
             unsigned it = 0;
             while (*gen == g) {
-                if (++it > (1u << 26)) { atomicExch(err, 5); ok = false; break; }
+                if (++it > limit) { atomicExch(err, 5); ok = false; break; }
                 __nanosleep(64);
             }
         }
@@ -227,7 +228,7 @@ __device__ void arn_update(const double* V, int64_t n, int nv, const double* hs,
 __global__ void __launch_bounds__(ARN_THREADS) k_arnoldi(double* V, int64_t n, int k, double* w, double* xfix,
                                                          double* partial, unsigned* bar, double* out, int* err,
                                                          int nsys, int64_t vstride, int64_t wstride,
-                                                         unsigned active) {
+                                                         unsigned active, unsigned wait_limit) {
     __shared__ double hs[ARN_MAXV];
     __shared__ double h1[ARN_MAXV];
     const int nbk = (int)gridDim.x / nsys;
@@ -250,7 +251,12 @@ __global__ void __launch_bounds__(ARN_THREADS) k_arnoldi(double* V, int64_t n, i
     // phase 1: h = V^T w and ||w||^2
     __shared__ double s_sq;
     arn_partials(V, n, nv, w, i0, i1, partial, nbk, bk, true);
-    if (!grid_barrier(bar_count, bar_gen, (unsigned)nbk, err)) return;
+    // a barrier that gives up marks the step's norm NaN in the output: the host stops there
+    // and reports the flag set in err
+    if (!grid_barrier(bar_count, bar_gen, (unsigned)nbk, err, wait_limit)) {
+        if (threadIdx.x == 0) out[2 * (ARN_MAXV + 1)] = __longlong_as_double(0x7ff8000000000000ll);
+        return;
+    }
     arn_reduce(partial, nv + 1, nbk, hs, nv, &s_sq);
     const double ww = hs[nv];
     const double nn2 = ww - s_sq;
@@ -274,7 +280,10 @@ __global__ void __launch_bounds__(ARN_THREADS) k_arnoldi(double* V, int64_t n, i
     __syncthreads();  // arn_partials reads rows of w that other threads of the block updated
     double* part2 = partial + parea;
     arn_partials(V, n, nv, w, i0, i1, part2, nbk, bk, true);
-    if (!grid_barrier(bar_count, bar_gen, (unsigned)nbk, err)) return;
+    if (!grid_barrier(bar_count, bar_gen, (unsigned)nbk, err, wait_limit)) {
+        if (threadIdx.x == 0) out[2 * (ARN_MAXV + 1)] = __longlong_as_double(0x7ff8000000000000ll);
+        return;
+    }
     arn_reduce(part2, nv + 1, nbk, hs, nv, &s_sq);
     const double w1w1 = hs[nv];
     const double nrm2 = fmax(w1w1 - s_sq, 0.0);  // rounding below zero: w1 lies in the span (breakdown)
@@ -353,6 +362,23 @@ static int gmres_solve_on(fmmbem_handle* h, const double* b, double tol, int rel
 static int gmres_batch_on(fmmbem_handle* h, const double* b, double tol, int relax, int p_initial, int p_min,
                           double* x, int* iters, int* p_hist, double* res_hist, double* true_res);
 
+// Read and clear the handle's bounded-wait flags after the work queued on st: 0 when no
+// wait gave up, FMMBEM_ETIMEOUT otherwise (the grid-barrier counters are then reset too,
+// so the handle stays usable).
+int read_wait_flags(fmmbem_handle* h, cudaStream_t st) {
+    int flags[2] = {0, 0};
+    FMM_CU(cudaMemcpyAsync(&flags[0], h->kerr, sizeof(int), cudaMemcpyDeviceToHost, st));
+    if (h->tc_err) FMM_CU(cudaMemcpyAsync(&flags[1], h->tc_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    FMM_CU(cudaStreamSynchronize(st));
+    if (!flags[0] && !flags[1]) return 0;
+    fmmbem_set_error("a bounded device wait gave up (code %d/%d); results are invalid", flags[0], flags[1]);
+    FMM_CU(cudaMemsetAsync(h->kerr, 0, sizeof(int), st));
+    if (h->tc_err) FMM_CU(cudaMemsetAsync(h->tc_err, 0, sizeof(int), st));
+    FMM_CU(cudaMemsetAsync(h->arn_bar, 0, 2 * h->nrhs * sizeof(unsigned), st));
+    FMM_CU(cudaStreamSynchronize(st));
+    return FMMBEM_ETIMEOUT;
+}
+
 // Batched handles (nrhs > 1): b, x are [nrhs][n]; iters, true_res hold nrhs entries,
 // res_hist [nrhs][max_iter + 1]; p_hist (one order per mat-vec) is shared.
 int gmres_solve(fmmbem_handle* h, const double* b, double tol, int relax, int p_initial, int p_min, double* x,
@@ -360,24 +386,20 @@ int gmres_solve(fmmbem_handle* h, const double* b, double tol, int relax, int p_
     cudaStream_t user = h->stream;
     FMM_CU(cudaEventRecord(h->ev_in, user));
     FMM_CU(cudaStreamWaitEvent(h->istream, h->ev_in, 0));
+    // a flag left by an earlier mat-vec of this handle must not fail this solve: its waits
+    // are cleared here (earlier mat-vecs report through fmmbem_check_waits)
+    FMM_CU(cudaMemsetAsync(h->kerr, 0, sizeof(int), h->istream));
+    if (h->tc_err) FMM_CU(cudaMemsetAsync(h->tc_err, 0, sizeof(int), h->istream));
     h->stream = h->istream;
     const int rc = h->nrhs > 1 ? gmres_batch_on(h, b, tol, relax, p_initial, p_min, x, iters, p_hist, res_hist, true_res)
                                : gmres_solve_on(h, b, tol, relax, p_initial, p_min, x, iters, p_hist, res_hist, true_res);
     h->stream = user;
+    if (rc == FMMBEM_EDEVICE || rc == FMMBEM_ENOMEM) return rc;
+    // bounded device waits (grid barrier, bulk-copy and tensor-core barriers) report here,
+    // ahead of a NaN status that a wait giving up may have caused
+    const int wr = read_wait_flags(h, h->istream);
+    if (wr < 0) return wr;
     if (rc < 0) return rc;
-    // bounded device waits (grid barrier, bulk-copy and tensor-core barriers) report here
-    int flags[2] = {0, 0};
-    FMM_CU(cudaMemcpyAsync(&flags[0], h->kerr, sizeof(int), cudaMemcpyDeviceToHost, h->istream));
-    if (h->tc_err) FMM_CU(cudaMemcpyAsync(&flags[1], h->tc_err, sizeof(int), cudaMemcpyDeviceToHost, h->istream));
-    FMM_CU(cudaStreamSynchronize(h->istream));
-    if (flags[0] || flags[1]) {
-        fmmbem_set_error("a bounded device wait gave up (code %d/%d); results are invalid", flags[0], flags[1]);
-        cudaMemsetAsync(h->kerr, 0, sizeof(int), h->istream);
-        if (h->tc_err) cudaMemsetAsync(h->tc_err, 0, sizeof(int), h->istream);
-        cudaMemsetAsync(h->arn_bar, 0, 2 * h->nrhs * sizeof(unsigned), h->istream);
-        cudaStreamSynchronize(h->istream);
-        return FMMBEM_EDEVICE;
-    }
     FMM_CU(cudaEventRecord(h->ev_out, h->istream));
     FMM_CU(cudaStreamWaitEvent(user, h->ev_out, 0));
     return rc;
@@ -448,7 +470,8 @@ static int gmres_solve_on(fmmbem_handle* h, const double* b, double tol, int rel
                 int nsys = 1;
                 int64_t vstride = 0, wstride = 0;
                 unsigned active = 1u;
-                void* args[] = {&dV, &nn, &kk, &dw, &dx, &dp, &bar, &dout, &de, &nsys, &vstride, &wstride, &active};
+                unsigned wl = h->wait_limit;
+                void* args[] = {&dV, &nn, &kk, &dw, &dx, &dp, &bar, &dout, &de, &nsys, &vstride, &wstride, &active, &wl};
                 FMM_CU(cudaLaunchCooperativeKernel((const void*)k_arnoldi, dim3(h->arn_blocks), dim3(arnoldi_threads(n, h->arn_blocks)), args, 0,
                                                    st));
                 h->launches += 1;
@@ -620,7 +643,8 @@ static int gmres_batch_on(fmmbem_handle* h, const double* b, double tol, int rel
                 int* de = h->kerr;
                 int nsys = nb;
                 int64_t vs = vstride, ws = n;
-                void* args[] = {&dV, &nn, &kk, &dw, &dx, &dp, &bar, &dout, &de, &nsys, &vs, &ws, &active};
+                unsigned wl = h->wait_limit;
+                void* args[] = {&dV, &nn, &kk, &dw, &dx, &dp, &bar, &dout, &de, &nsys, &vs, &ws, &active, &wl};
                 const int grid = (h->arn_blocks / nb) * nb;
                 FMM_CU(cudaLaunchCooperativeKernel((const void*)k_arnoldi, dim3(grid),
                                                    dim3(arnoldi_threads(n, grid)), args, 0, st));

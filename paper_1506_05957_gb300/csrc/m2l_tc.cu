@@ -18,6 +18,7 @@
 #include <vector>
 #include "handle.cuh"
 #include "harmonics.cuh"
+#include "tc_ptx.cuh"
 
 namespace fmmbem {
 
@@ -27,20 +28,7 @@ constexpr int TC_ROWS = 128;  // rows per tile (MMA M)
 constexpr int TC_KC = 32;     // K per staged chunk
 constexpr uint32_t WAIT_LIMIT = 1u << 24;
 
-__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-// Shared-memory matrix descriptor: start, leading-dimension byte offset (between
-// core matrices along K), stride byte offset (between 8-row groups), version 1,
-// no swizzle.
-__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
-    return (uint64_t)((saddr & 0x3FFFF) >> 4) | ((uint64_t)((lbo & 0x3FFFF) >> 4) << 16) |
-           ((uint64_t)((sbo & 0x3FFFF) >> 4) << 32) | ((uint64_t)1 << 46);
-}
-
-// Instruction descriptor of kind::tf32: D F32, A/B TF32, both K-major.
-__device__ __forceinline__ uint32_t idesc_tf32(int m, int n) {
-    return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
-}
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) { return mbar_wait_bounded(mbar, parity, WAIT_LIMIT); }
 
 // element (r, k) of a K-major operand chunk with TC_KC columns, in floats
 __device__ __forceinline__ int cm_index(int r, int k) {
@@ -49,26 +37,6 @@ __device__ __forceinline__ int cm_index(int r, int k) {
 
 __device__ __forceinline__ float tf32_hi(float x) {
     return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
-}
-
-__device__ __forceinline__ void mma_tf32(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d),
-        "l"(a), "l"(b), "r"(idesc), "r"(acc));
-}
-
-__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
-    for (uint32_t it = 0; it < WAIT_LIMIT; ++it) {
-        uint32_t done;
-        asm volatile(
-            "{\n\t.reg .pred q;\n\tmbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2;\n\tselp.u32 %0, 1, 0, q;\n\t}\n"
-            : "=r"(done)
-            : "r"(mbar), "r"(parity)
-            : "memory");
-        if (done) return true;
-    }
-    return false;
 }
 
 // Operator tables for this path: per operator, per 32-wide input chunk c, the hi and

@@ -64,8 +64,9 @@ int far_rule_host(int K, double* q /* K x 4: l1,l2,l3,w */) {
 }
 
 // Near-singular rule: collapsed coordinates l1 = 1-u, l2 = u(1-v), l3 = uv with
-// 5 Gauss-Legendre nodes in u (weight multiplied by the Jacobian u) and 4 in v,
-// scaled so the weights sum to one. Legendre roots by Newton's method on P_n.
+// nu Gauss-Legendre nodes in u (weight multiplied by the Jacobian u) and nv = nu - 1 in v
+// (5 x 4 = 20 points by default, the K ~ 20 of Sec. 2.3), scaled so the weights sum to
+// one; exact to total degree 2 nv - 1. Legendre roots by Newton's method on P_n.
 __device__ void legendre_rule01(int n, double* x, double* w) {
     for (int i = 0; i < n; ++i) {
         double t = cos(3.14159265358979323846 * (i + 0.75) / (n + 0.5));
@@ -88,13 +89,13 @@ __device__ void legendre_rule01(int n, double* x, double* w) {
     }
 }
 
-__global__ void k_near_rule(double* q /* 20 x 4 */) {
-    double xu[5], wu[5], xv[4], wv[4];
-    legendre_rule01(5, xu, wu);
-    legendre_rule01(4, xv, wv);
-    for (int i = 0; i < 5; ++i)
-        for (int j = 0; j < 4; ++j) {
-            double* o = q + 4 * (4 * i + j);
+__global__ void k_near_rule(int nu, int nv, double* q /* nu nv x 4 */) {
+    double xu[8], wu[8], xv[8], wv[8];
+    legendre_rule01(nu, xu, wu);
+    legendre_rule01(nv, xv, wv);
+    for (int i = 0; i < nu; ++i)
+        for (int j = 0; j < nv; ++j) {
+            double* o = q + 4 * (nv * i + j);
             o[0] = 1.0 - xu[i];
             o[1] = xu[i] * (1.0 - xv[j]);
             o[2] = xu[i] * xv[j];
@@ -365,13 +366,23 @@ __global__ void k_csr_ptr(const unsigned long long* key, long long n, long long 
     ptr[c] = (int)lo;
 }
 
+// Pair counts of the lists, and the shallowest levels holding an M2L source (lmin[0]) and an
+// M2L target (lmin[1]): M2M above the first and L2L above the second carry nothing.
 __global__ void k_list_stats(const int* m2l_ptr, const int* m2l_src, const int* p2p_ptr, const int* p2p_src,
                              const int* clevel, const int2* range, int ncells, int K,
-                             unsigned long long* same_level, unsigned long long* p2p_inter) {
+                             unsigned long long* same_level, unsigned long long* p2p_inter, int* lmin) {
     int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= ncells) return;
     unsigned long long same = 0, inter = 0;
-    for (int e = m2l_ptr[c]; e < m2l_ptr[c + 1]; ++e) same += (clevel[m2l_src[e]] == clevel[c]);
+    int ls = 1 << 30;
+    for (int e = m2l_ptr[c]; e < m2l_ptr[c + 1]; ++e) {
+        same += (clevel[m2l_src[e]] == clevel[c]);
+        ls = min(ls, clevel[m2l_src[e]]);
+    }
+    if (m2l_ptr[c + 1] > m2l_ptr[c]) {
+        atomicMin(lmin, ls);
+        atomicMin(lmin + 1, clevel[c]);
+    }
     const int nt = range[c].y - range[c].x;
     for (int e = p2p_ptr[c]; e < p2p_ptr[c + 1]; ++e) {
         const int2 r = range[p2p_src[e]];
@@ -642,16 +653,23 @@ int build_geometry_tree_lists(fmmbem_handle* h, const fmmbem_mesh* mesh) {
     h->N = n;
     h->NS = (int64_t)K * n;
 
-    // quadrature tables: [far K x 4 | near 20 x 4]
+    // quadrature tables: [far K x 4 | near near_k x 4]
     double farq_h[7 * 4];
     if (far_rule_host(K, farq_h) != 0) {
         fmmbem_set_error("unsupported gauss_k=%d (use 1, 3, 4 or 7)", K);
         return FMMBEM_EINVAL;
     }
+    const int nq = h->opts.near_k;
+    int nu = 3;
+    while (nu * (nu - 1) < nq) ++nu;
+    if (nu * (nu - 1) != nq || nu > 7) {
+        fmmbem_set_error("near_k=%d is not nu (nu - 1) for nu in 3..7", nq);
+        return FMMBEM_EINVAL;
+    }
     double* quad = nullptr;
-    FMM_TRY(dalloc(&quad, 4 * (K + 20)));
+    FMM_TRY(dalloc(&quad, 4 * (K + nq)));
     FMM_CU(cudaMemcpyAsync(quad, farq_h, sizeof(double) * 4 * K, cudaMemcpyHostToDevice, st));
-    k_near_rule<<<1, 1, 0, st>>>(quad + 4 * K);
+    k_near_rule<<<1, 1, 0, st>>>(nu, nu - 1, quad + 4 * K);
     FMM_LAUNCHED();
 
     // upload mesh
@@ -951,14 +969,21 @@ int build_geometry_tree_lists(fmmbem_handle* h, const fmmbem_mesh* mesh) {
         FMM_TRY(sort_pairs_to_csr(h, p2p, (long long)done[1], &h->p2p_ptr, &h->p2p_src));
         fmm_free(m2l); fmm_free(p2p); fmm_free(fa); fmm_free(fb); fmm_free(ovf);
         FMM_CU(cudaMemsetAsync(cnt, 0, 2 * sizeof(unsigned long long), st));
+        int* lmin = reinterpret_cast<int*>(cnt + 2);
+        const int lmin_init[2] = {1 << 30, 1 << 30};
+        FMM_CU(cudaMemcpyAsync(lmin, lmin_init, sizeof(lmin_init), cudaMemcpyHostToDevice, st));
         k_list_stats<<<(nc + T - 1) / T, T, 0, st>>>(h->m2l_ptr, h->m2l_src, h->p2p_ptr, h->p2p_src, h->cell_level,
-                                                    h->cell_range, nc, K, cnt, cnt + 1);
+                                                    h->cell_range, nc, K, cnt, cnt + 1, lmin);
         FMM_LAUNCHED();
-        unsigned long long s_h[2];
+        unsigned long long s_h[3];
         FMM_CU(cudaMemcpyAsync(s_h, cnt, sizeof(s_h), cudaMemcpyDeviceToHost, st));
         FMM_CU(cudaStreamSynchronize(st));
         h->n_m2l_same = (int64_t)s_h[0];
         h->n_p2p_inter = (int64_t)s_h[1];
+        int lmin_h[2];
+        memcpy(lmin_h, &s_h[2], sizeof(lmin_h));
+        h->m2m_lmin = std::min(lmin_h[0], h->n_levels);
+        h->l2l_lmin = std::min(lmin_h[1], h->n_levels);
         fmm_free(cnt);
         FMM_TRY(dalloc(&h->p2p_rec, h->n_p2p));
         FMM_TRY(dalloc(&h->p2p_off, h->n_p2p));
@@ -1065,7 +1090,7 @@ int build_geometry_tree_lists(fmmbem_handle* h, const fmmbem_mesh* mesh) {
         FMM_TRY(dalloc(&h->corr_dl, (int64_t)per * nnz));
         if (nnz > 0) {
             k_corrections<<<(unsigned)((nnz + 127) / 128), 128, 0, st>>>(nnz, row, h->corr_col, h->tgt_d, h->nrm_d,
-                                                                       h->verts, quad, K, quad + 4 * K, 20, stokes,
+                                                                       h->verts, quad, K, quad + 4 * K, nq, stokes,
                                                                        h->corr_sl, h->corr_dl);
             FMM_LAUNCHED();
         }

@@ -6,7 +6,7 @@ Panel centroids, normals, areas, quadrature points and all kernel evaluations ar
 computed separately by each side.
 """
 from .mesh import (icosphere, octasphere, ellipsoid, evans_fung_cell, place_cells,
-                   random_vector, point_charge_dirichlet)
+                   random_vector, point_charge_dirichlet, smooth_random_field)
 
 __all__ = ["icosphere", "octasphere", "ellipsoid", "evans_fung_cell", "place_cells",
-           "random_vector", "point_charge_dirichlet"]
+           "random_vector", "point_charge_dirichlet", "smooth_random_field"]

@@ -159,3 +159,20 @@ def point_charge_dirichlet(points, z0=(0.0, 0.0, 3.0)):
     """Potential of a unit point charge at z0 at the given points: 1/(4 pi |x - z0|)."""
     d = np.asarray(points, dtype=np.float64) - np.asarray(z0, dtype=np.float64)
     return 1.0 / (4.0 * np.pi * np.sqrt((d * d).sum(-1)))
+
+
+def smooth_random_field(points, seed=0, modes=8, k_min=1.0, k_max=3.0):
+    """Seeded smooth vector field at the given points: a sum of `modes` plane waves
+    a_m sin(k_m . x + phase_m) with random unit amplitudes a_m (3-vectors), wave vectors of
+    length in [k_min, k_max] and phases. Boundary data that excites many spherical harmonics at
+    once (unlike a rigid motion of a sphere, which is an eigenfunction of its layer operators)."""
+    rng = np.random.default_rng(seed)
+    x = np.asarray(points, dtype=np.float64)
+    out = np.zeros((len(x), 3))
+    for _ in range(modes):
+        k = rng.standard_normal(3)
+        k *= rng.uniform(k_min, k_max) / np.linalg.norm(k)
+        a = rng.standard_normal(3)
+        a /= np.linalg.norm(a)
+        out += a[None, :] * np.sin(x @ k + rng.uniform(0.0, 2.0 * np.pi))[:, None]
+    return out

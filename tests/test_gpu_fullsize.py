@@ -155,3 +155,43 @@ def test_64_red_blood_cells_stokes(torch_cuda):
     drag = np.bincount(np.asarray(body), weights=tr[:, 0] * S, minlength=64)
     print("per-cell drag range", drag.min(), drag.max())
     assert np.all(drag < 0)
+
+
+def test_fullsize_stokes_relaxation_random_field(torch_cuda):
+    """The Stokes sphere of 81920 panels with data that is not an eigenvector of the single
+    layer (a seeded smooth random velocity field without net normal flux; uniform motion
+    converges in one step), so the
+    relaxed solve runs many iterations and p falls from 16 to the floor 4 (Sec. 2.6): the order
+    sequence is the oracle's schedule of the residuals seen, the relaxed and fixed-p solves take
+    the same number of iterations within one, and the sampled oracle residual is <= 2 tol."""
+    torch = torch_cuda
+    from oracle import dense, panels
+    from oracle.schedule import schedule
+    from synth import icosphere, smooth_random_field
+    from paper_1506_05957_gb300 import FmmBem, FMMBEM_MIXED, FMMBEM_STOKES
+    v, t = icosphere(6)
+    c, nrm, S = panels.geometry(v, t)
+    # the single layer's range is orthogonal to the normal field (int G n dS = 0), so the data of
+    # a solvable first-kind system carries no net normal flux (as the velocity of an
+    # incompressible flow on a closed surface): the area-weighted normal component is removed
+    u = smooth_random_field(c, seed=0)
+    u = (u - (np.sum(S * np.einsum("ij,ij->i", u, nrm)) / np.sum(S)) * nrm).reshape(-1)
+    h = FmmBem(v, t, kernel=FMMBEM_STOKES, gauss_k=3, ncrit=150, theta=0.5, p_max=16, precision=FMMBEM_MIXED)
+    b = torch.tensor(u, dtype=torch.float64, device="cuda")
+    sol = torch.zeros_like(b)
+    r = h.solve(b, sol, tol=1e-5, relax=True, p_initial=16, p_min=4)
+    print("random field relaxed: iters", r["iters"], r["p_hist"], "true residual", r["true_res"])
+    assert r["converged"] and r["true_res"] < 2e-5
+    assert r["iters"] > 10
+    assert r["p_hist"] == schedule(1e-5, r["res_hist"][:-1], 16, 4)
+    assert r["p_hist"][0] == 16 and r["p_hist"][-1] == 4
+    M = dense.Mesh(v, t, k=3)
+    rows = np.sort(np.random.default_rng(9).choice(len(t), 96, replace=False))
+    ub = u.reshape(-1, 3)[rows].reshape(-1)
+    res = M.stokes_apply(sol.cpu().numpy(), rows=rows).reshape(-1) - ub
+    print("sampled oracle residual", np.linalg.norm(res) / np.linalg.norm(ub))
+    assert np.linalg.norm(res) / np.linalg.norm(ub) < 2e-5
+    sol2 = torch.zeros_like(b)
+    r2 = h.solve(b, sol2, tol=1e-5, relax=False, p_initial=16, p_min=4)
+    print("fixed p = 16: iters", r2["iters"])
+    assert r2["converged"] and abs(r2["iters"] - r["iters"]) <= 1

@@ -133,13 +133,16 @@ def test_relaxed_solve_matches_oracle(torch_cuda, sphere1280):
     res = rel(s["A"] @ xs, s["b"])
     assert res < 2 * tol
     assert rel(xs, s["x_lu"]) < 1e-5
-    # iteration counts: relaxed ~ fixed ~ exact GMRES (the paper's observation)
+    # iteration counts: relaxed ~ fixed ~ exact GMRES (the paper's observation, Sec. 3.1). The GPU
+    # iterates on the mixed-precision FMM operator at p <= 10, which differs from the dense matrix by
+    # ~1e-6 relative, so the residual estimate may cross tol one step earlier or later than exact
+    # GMRES does (observed: 16 relaxed, 16 fixed, 15 exact); one step is the allowance.
     x2 = torch.zeros_like(b)
     r2 = h.solve(b, x2, tol=tol, relax=False, p_initial=10, p_min=3)
     _, it_oracle, _ = gmres(lambda u, k: s["A"] @ u, s["b"], tol=tol, restart=50, max_iter=100)
     print("iters relaxed/fixed/oracle", r["iters"], r2["iters"], it_oracle, r["p_hist"])
-    assert abs(r["iters"] - r2["iters"]) <= 2
-    assert abs(r2["iters"] - it_oracle) <= 2
+    assert abs(r["iters"] - r2["iters"]) <= 1
+    assert abs(r2["iters"] - it_oracle) <= 1
     assert all(p == 10 for p in r2["p_hist"])
 
 

@@ -73,3 +73,30 @@ def test_create_rejects_bad_arguments_without_touching_the_gpu(libfmm):
         rc = binding.lib().fmmbem_create(ctypes.byref(mesh), kernel, k, ncrit, theta, None, ctypes.byref(h))
         assert rc == binding.FMMBEM_EINVAL
         assert binding.lib().fmmbem_last_error().decode()
+
+
+def test_create_rejects_bad_near_rule_and_bodies(libfmm):
+    # near_k outside the collapsed products and body indices out of range are refused before any CUDA call
+    from paper_1506_05957_gb300 import binding
+    from synth import icosphere
+    v, t = icosphere(1)
+    v = np.ascontiguousarray(v)
+    t = np.ascontiguousarray(t, dtype=np.int32)
+    mesh = binding.fmmbem_mesh(len(v), v.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), len(t),
+                               t.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)))
+    h = ctypes.c_void_p()
+    for nk in (7, 20 + 1, 56, -2):
+        o = binding.fmmbem_default_opts()
+        o.near_k = nk
+        rc = binding.lib().fmmbem_create(ctypes.byref(mesh), 0, 4, 150, 0.5, ctypes.byref(o), ctypes.byref(h))
+        assert rc == binding.FMMBEM_EINVAL and not h.value
+        assert b"near_k" in binding.lib().fmmbem_last_error()
+    body = np.zeros(len(t), dtype=np.int32)
+    body[3] = 2
+    mesh.n_bodies = 2
+    mesh.body_of_panel = body.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+    rc = binding.lib().fmmbem_create(ctypes.byref(mesh), 0, 4, 150, 0.5, None, ctypes.byref(h))
+    assert rc == binding.FMMBEM_EINVAL and b"body_of_panel" in binding.lib().fmmbem_last_error()
+    mesh.body_of_panel = None
+    rc = binding.lib().fmmbem_create(ctypes.byref(mesh), 0, 4, 150, 0.5, None, ctypes.byref(h))
+    assert rc == binding.FMMBEM_EINVAL and not h.value

@@ -43,3 +43,19 @@ def test_gauss_legendre_matches_numpy(n):
     xr, wr = np.polynomial.legendre.leggauss(n)
     assert np.allclose(np.sort(x), 0.5 * (xr + 1.0), atol=1e-14)
     assert np.allclose(w[np.argsort(x)], 0.5 * wr, atol=1e-14)
+
+
+@pytest.mark.parametrize("nu", [3, 4, 5, 6, 7])
+def test_collapsed_near_rules(nu):
+    # the near rules of nu x (nu - 1) points (the near_k option; 5 x 4 = 20 by default) integrate
+    # every monomial to total degree 2 nu - 3 and miss one degree above
+    bary, w = near_rule(nu, nu - 1)
+    k = nu * (nu - 1)
+    assert len(w) == k and abs(w.sum() - 1.0) < 1e-14
+    deg = rule_degree(k)
+    assert deg == 2 * nu - 3
+    for tot in range(deg + 1):
+        for a in range(tot + 1):
+            assert abs(integrate(bary, w, a, tot - a) - exact_monomial(a, tot - a)) < 1e-14
+    errs = [abs(integrate(bary, w, a, deg + 1 - a) - exact_monomial(a, deg + 1 - a)) for a in range(deg + 2)]
+    assert max(errs) > 1e-9
