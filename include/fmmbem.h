@@ -89,15 +89,21 @@ typedef struct {
     void* stream;         /* NULL: the legacy default stream; else a cudaStream_t for all work;
                              it must stay valid until fmmbem_destroy returns (the handle's
                              device memory is stream-ordered and is released on it) */
-    int nrhs;             /* 1: one vector per mat-vec. FMMBEM_BATCH (Laplace single layer only):
-                             every mat-vec and solve of the handle takes FMMBEM_BATCH vectors
-                             at once, laid out [FMMBEM_BATCH][n_panels] (see fmmbem_solve_batch) */
+    int nrhs;             /* 1: one vector per mat-vec. A batched handle's mat-vecs and solves take
+                             nrhs vectors at once, laid out [nrhs][n_unknowns] (see
+                             fmmbem_solve_batch): FMMBEM_BATCH for a Laplace handle, 2 to
+                             FMMBEM_STOKES_BATCH_MAX for a Stokes handle (single layer only) */
     int near_k;           /* 20: points of the near-singular rule (Sec. 2.3 gives K ~ 20): a collapsed
                              Gauss product of nu x (nu - 1) points, exact to total degree 2 nu - 3;
                              one of 6, 12, 20, 30, 42 (nu = 3..7); 0 selects 20 */
 } fmmbem_opts;
 
 #define FMMBEM_BATCH 4
+/* Largest Stokes batch. Each pass of a Stokes batch's mat-vec is one launch for all vectors:
+ * the tensor-core M2M, M2L and L2L take every vector's expansion rows in their tiles (one
+ * operator chunk serves 4 nrhs rows per pair), the other kernels take the vector from the
+ * launch's second grid dimension. */
+#define FMMBEM_STOKES_BATCH_MAX 8
 
 typedef struct fmmbem_handle fmmbem_handle;
 
@@ -233,10 +239,10 @@ int fmmbem_rhs(fmmbem_handle* h, const double* known_dev, double* b_dev);
  * S_j x_j[a] (a < 1 Laplace, a < 3 Stokes), in FP64. For the traction t of a Stokes solve
  * this is the force on body b (the drag of Sec. 3.2 and Table rbc_richardson_values); for
  * the Laplace unknown q = dphi/dn it is the flux through the body's surface.
- *   x_dev   : [n_unknowns] doubles, device, the caller's panel order
+ *   x_dev   : [n_unknowns] doubles, device, the caller's panel order (one vector; vector q of a
+ *             batch starts at x_dev + q n_unknowns)
  *   out_host: [fmmbem_n_bodies(h)][dof] doubles, host (written before the call returns)
- * Synchronizes the handle's stream. Errors: FMMBEM_EINVAL, FMMBEM_ESTATE on a batched handle,
- * FMMBEM_EDEVICE.
+ * Synchronizes the handle's stream. Errors: FMMBEM_EINVAL, FMMBEM_EDEVICE.
  */
 int fmmbem_body_integrals(fmmbem_handle* h, const double* x_dev, double* out_host);
 
@@ -290,17 +296,17 @@ int fmmbem_solve_host(fmmbem_handle* h, const double* rhs_host, double tol, int 
                       double* res_hist, double* true_res);
 
 /*
- * Relaxed GMRES for the FMMBEM_BATCH systems A x_q = b_q of a batched handle (opts.nrhs =
- * FMMBEM_BATCH, Laplace single layer), in lockstep: every mat-vec evaluates all systems'
- * basis vectors together (one P2M, M2M, M2L, L2L, L2P and P2P pass over four expansions
- * and four strengths per Gauss point) at the largest order p_k any active system's
+ * Relaxed GMRES for the nrhs systems A x_q = b_q of a batched handle (opts.nrhs > 1:
+ * FMMBEM_BATCH Laplace or up to FMMBEM_STOKES_BATCH_MAX Stokes right-hand sides), in
+ * lockstep: every mat-vec evaluates all systems' basis vectors together (one P2M, M2M, M2L,
+ * L2L, L2P and P2P pass for the whole batch) at the largest order p_k any active system's
  * relaxation rule (Sec. 2.6) asks for; each system keeps its own residual, Hessenberg
  * matrix and restarts and leaves the lockstep when it converges.
- *   rhs_dev, x_dev : [FMMBEM_BATCH][n_panels] doubles, device
- *   iters          : [FMMBEM_BATCH] host, mat-vecs while each system was active (or NULL)
+ *   rhs_dev, x_dev : [nrhs][n_unknowns] doubles, device
+ *   iters          : [nrhs] host, mat-vecs while each system was active (or NULL)
  *   p_hist         : [max_iter] host, the order of each batched mat-vec (or NULL)
- *   res_hist       : [FMMBEM_BATCH][max_iter + 1] host (or NULL)
- *   true_res       : [FMMBEM_BATCH] host, ||b - A x|| / ||b|| at p_initial (or NULL)
+ *   res_hist       : [nrhs][max_iter + 1] host (or NULL)
+ *   true_res       : [nrhs] host, ||b - A x|| / ||b|| at p_initial (or NULL)
  * Returns 0 when every system converged, FMMBEM_NOT_CONVERGED otherwise, FMMBEM_ESTATE on a
  * handle that is not batched (and fmmbem_solve returns FMMBEM_ESTATE on a batched one).
  */
@@ -383,7 +389,10 @@ typedef struct {
                                           expansion, and per M2M and per L2L translation of a cell */
 } fmmbem_profile;
 
-/* enable != 0 starts recording (and resets the counters); 0 stops. */
+/* enable != 0 starts recording (and resets the counters); 0 stops. enable = 2 also runs each
+ * profiled mat-vec's near field before its far field on one stream (same sums), so that every
+ * pass's time is its kernels' own time rather than time spent waiting for SMs held by the
+ * other field; 1 keeps the concurrent schedule of unprofiled mat-vecs. */
 int fmmbem_profile_enable(fmmbem_handle* h, int enable);
 int fmmbem_profile_get(fmmbem_handle* h, fmmbem_profile* out); /* synchronizes the stream */
 

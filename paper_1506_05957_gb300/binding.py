@@ -258,7 +258,7 @@ class FmmBem:
         -> force on each body)."""
         dof = 3 if self.kernel == FMMBEM_STOKES else 1
         out = np.zeros((self.n_bodies, dof), dtype=np.float64)
-        _check(lib().fmmbem_body_integrals(self.h, _dev(x, self.n), _vp(out.ctypes.data)))
+        _check(lib().fmmbem_body_integrals(self.h, _dev(x, self.n // self.nrhs), _vp(out.ctypes.data)))
         return out
 
     def check_waits(self):
@@ -326,6 +326,7 @@ class FmmBem:
         return {n: getattr(s, n) for n, _ in fmmbem_stats._fields_}
 
     def profile_enable(self, on=True):
+        """fmmbem_profile_enable: 0 off, 1 (True) the solve's own schedule, 2 passes serialized."""
         _check(lib().fmmbem_profile_enable(self.h, int(on)))
 
     def profile(self):

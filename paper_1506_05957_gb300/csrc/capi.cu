@@ -215,7 +215,7 @@ void prof_harvest(fmmbem_handle* h) {
 // (one per non-root cell).
 static double tc_flops(const fmmbem_handle* h, int p) {
     if (h->precision != FMMBEM_MIXED || h->m2l_mode != FMMBEM_M2L_TENSOR || !h->m2l_tc_ready) return 0.0;
-    const double q = (double)(p + 1) * (p + 1), per = 2.0 * q * q * h->ncomp;
+    const double q = (double)(p + 1) * (p + 1), per = 2.0 * q * q * h->ncomp * h->nsys;
     double f = 0.0;
     if (h->m2l_tc_at[p]) f += per * (double)h->n_m2l;
     if (h->tree_tc_at[p] && h->tree_tiles) f += 2.0 * per * (double)(h->n_cells - 1);
@@ -229,7 +229,7 @@ static int matvec_launch(fmmbem_handle* h, int p, const double* xs, double* ys);
 // per order p; the graph is recaptured when the arithmetic or kernel selection changed.
 int matvec_sorted(fmmbem_handle* h, int p, const double* xs, double* ys) {
     const int mode = h->precision * 16 + h->m2l_mode + 4 * h->p2p_variant + 64 * (h->prof_on ? 1 : 0) + 128 * h->layer +
-                     256 * h->m2l_tc_at[p] + 512 * h->tree_tc_at[p];
+                     256 * h->m2l_tc_at[p] + 512 * h->tree_tc_at[p] + 1024 * (h->prof_serial ? 1 : 0);
     if (!h->use_graphs || xs != h->xfix || ys != h->kw || h->stream == nullptr)
         return matvec_launch(h, p, xs, ys);
     prof_harvest(h);
@@ -259,8 +259,8 @@ int matvec_sorted(fmmbem_handle* h, int p, const double* xs, double* ys) {
     if (h->prof_on) h->pending_graph = p;
     if (h->prof_on) {
         const double q = (double)(p + 1) * (p + 1);
-        h->prof.m2l_flops += 2.0 * q * q * h->ncomp * (double)h->n_m2l;
-        h->prof.p2p_interactions += (double)h->n_p2p_inter;
+        h->prof.m2l_flops += 2.0 * q * q * h->ncomp * h->nsys * (double)h->n_m2l;
+        h->prof.p2p_interactions += (double)h->n_p2p_inter * h->nsys;
         h->prof.tc_flops += tc_flops(h, p);
     }
     return 0;
@@ -270,20 +270,27 @@ static int matvec_launch(fmmbem_handle* h, int p, const double* xs, double* ys) 
     const bool fp64 = h->precision == FMMBEM_FP64;
     h->xin = xs;
     prof_begin(h, FMMBEM_PASS_MATVEC);
-    // near field on the second stream, far field on the handle's stream, joined before L2P
+    // near field on the second stream, far field on the handle's stream, joined before L2P;
+    // in serial profiling the near field runs first on the handle's stream, so that every
+    // pass's events time its kernels alone (no wait for SMs held by the other field)
     if (!fp64) FMM_TRY(pack_sources(h));
-    FMM_CU(cudaEventRecord(h->ev_fork, h->stream));
-    FMM_CU(cudaStreamWaitEvent(h->stream2, h->ev_fork, 0));
-    FMM_TRY(near_field(h, fp64, h->stream2));
-    FMM_TRY(far_field(h, p, fp64));
-    FMM_CU(cudaEventRecord(h->ev_join, h->stream2));
-    FMM_CU(cudaStreamWaitEvent(h->stream, h->ev_join, 0));
+    if (h->prof_on && h->prof_serial) {
+        FMM_TRY(near_field(h, fp64, h->stream));
+        FMM_TRY(far_field(h, p, fp64));
+    } else {
+        FMM_CU(cudaEventRecord(h->ev_fork, h->stream));
+        FMM_CU(cudaStreamWaitEvent(h->stream2, h->ev_fork, 0));
+        FMM_TRY(near_field(h, fp64, h->stream2));
+        FMM_TRY(far_field(h, p, fp64));
+        FMM_CU(cudaEventRecord(h->ev_join, h->stream2));
+        FMM_CU(cudaStreamWaitEvent(h->stream, h->ev_join, 0));
+    }
     FMM_TRY(far_eval_add(h, p, fp64, ys, operator_scale(h)));
     prof_end(h, FMMBEM_PASS_MATVEC, 0);
     if (h->prof_on && h->capturing < 0) {  // a captured graph counts its work at each replay
         const double q = (double)(p + 1) * (p + 1);
-        h->prof.m2l_flops += 2.0 * q * q * h->ncomp * (double)h->n_m2l;
-        h->prof.p2p_interactions += (double)h->n_p2p_inter;
+        h->prof.m2l_flops += 2.0 * q * q * h->ncomp * h->nsys * (double)h->n_m2l;
+        h->prof.p2p_interactions += (double)h->n_p2p_inter * h->nsys;
         h->prof.tc_flops += tc_flops(h, p);
     }
     return 0;
@@ -367,8 +374,14 @@ int fmmbem_create(const fmmbem_mesh* mesh, int kernel, int gauss_k, int ncrit, d
     if (!(o.near_factor >= 0.0)) { fmmbem_set_error("near_factor < 0"); return FMMBEM_EINVAL; }
     if (!(o.mu > 0.0)) { fmmbem_set_error("mu must be > 0"); return FMMBEM_EINVAL; }
     if (o.precision != FMMBEM_FP64 && o.precision != FMMBEM_MIXED) { fmmbem_set_error("bad precision"); return FMMBEM_EINVAL; }
-    if (o.nrhs != 1 && o.nrhs != FMMBEM_BATCH) { fmmbem_set_error("nrhs must be 1 or %d", FMMBEM_BATCH); return FMMBEM_EINVAL; }
-    if (o.nrhs != 1 && kernel != FMMBEM_LAPLACE) { fmmbem_set_error("batched handles are Laplace only"); return FMMBEM_EINVAL; }
+    if (kernel == FMMBEM_LAPLACE && o.nrhs != 1 && o.nrhs != FMMBEM_BATCH) {
+        fmmbem_set_error("a Laplace handle takes nrhs 1 or %d", FMMBEM_BATCH);
+        return FMMBEM_EINVAL;
+    }
+    if (kernel == FMMBEM_STOKES && (o.nrhs < 1 || o.nrhs > FMMBEM_STOKES_BATCH_MAX)) {
+        fmmbem_set_error("a Stokes handle takes nrhs in [1, %d]", FMMBEM_STOKES_BATCH_MAX);
+        return FMMBEM_EINVAL;
+    }
     if (o.near_k == 0) o.near_k = 20;  // callers that fill the options themselves get the default rule
     if (o.near_k != 6 && o.near_k != 12 && o.near_k != 20 && o.near_k != 30 && o.near_k != 42) {
         fmmbem_set_error("near_k must be 6, 12, 20, 30 or 42 (collapsed products of nu x (nu - 1) points)");
@@ -429,6 +442,9 @@ int fmmbem_create(const fmmbem_mesh* mesh, int kernel, int gauss_k, int ncrit, d
     }
     int rc = build_geometry_tree_lists(h, mesh);
     if (rc < 0) return fail(rc);
+    // a Stokes batch keeps one copy of the expansions per vector (see handle.cuh)
+    h->nsys = kernel == FMMBEM_STOKES ? o.nrhs : 1;
+    h->esys = (size_t)h->n_cells * h->ncomp * ESTRIDE;
     h->n_bodies = mesh->n_bodies > 1 ? mesh->n_bodies : 1;
     if ((rc = dalloc(&h->body_acc, (size_t)h->n_bodies * h->dof)) < 0) return fail(rc);
     if (mesh->n_bodies > 1) {  // each sorted panel's body: body[s] = body_of_panel[perm[s]]
@@ -455,7 +471,7 @@ int fmmbem_create(const fmmbem_mesh* mesh, int kernel, int gauss_k, int ncrit, d
     rc = build_m2l_tc(h);
     if (rc < 0) return fail(rc);
     h->m2l_mode = h->m2l_tc_ready ? FMMBEM_M2L_TENSOR : (h->m2l_tables ? FMMBEM_M2L_TABLES : FMMBEM_M2L_GATHER);
-    const size_t ex = (size_t)h->n_cells * h->ncomp * ESTRIDE;
+    const size_t ex = h->esys * h->nsys;
     const int64_t n = h->N * h->dof * h->nrhs;  // every work vector holds the nrhs vectors of a batch
     const int nb = h->nrhs;
     h->kr_m = o.restart;
@@ -463,7 +479,7 @@ int fmmbem_create(const fmmbem_mesh* mesh, int kernel, int gauss_k, int ncrit, d
     if ((rc = dalloc((double**)&h->L, ex)) < 0) return fail(rc);
     // per-mat-vec packed sources: one float4 per Gauss point (Laplace single layer), two
     // (Stokeslet strengths, or the Laplace double layer's moment w n)
-    if ((rc = dalloc(&h->src_w, (size_t)h->NS * 2)) < 0) return fail(rc);
+    if ((rc = dalloc(&h->src_w, (size_t)h->NS * 2 * h->nsys)) < 0) return fail(rc);
     if ((rc = dalloc(&h->xs, n)) < 0 || (rc = dalloc(&h->ys, n)) < 0 || (rc = dalloc(&h->ynear, n)) < 0) return fail(rc);
     if ((rc = dalloc(&h->V, (size_t)(o.restart + 1) * n)) < 0) return fail(rc);
     if ((rc = dalloc(&h->xfix, n)) < 0) return fail(rc);
@@ -505,7 +521,6 @@ int fmmbem_n_bodies(const fmmbem_handle* h) { return h ? h->n_bodies : -1; }
 
 int fmmbem_body_integrals(fmmbem_handle* h, const double* x_dev, double* out_host) {
     if (!h || !x_dev || !out_host) { fmmbem_set_error("NULL argument"); return FMMBEM_EINVAL; }
-    if (h->nrhs > 1) { fmmbem_set_error("body integrals take one vector (not a batched handle)"); return FMMBEM_ESTATE; }
     const size_t bytes = sizeof(double) * h->n_bodies * h->dof;
     FMM_CU(cudaMemsetAsync(h->body_acc, 0, bytes, h->stream));
     k_body_sums<<<(unsigned)((h->N + 255) / 256), 256, 0, h->stream>>>(x_dev, h->perm, h->tgt_d, h->body, h->N, h->dof,
@@ -750,6 +765,7 @@ int fmmbem_profile_enable(fmmbem_handle* h, int enable) {
     h->launches = 0;
     h->pending_graph = -1;
     h->prof_on = enable != 0;
+    h->prof_serial = enable == 2;
     return 0;
 }
 

@@ -53,9 +53,12 @@ constexpr int P2M_WARPS = 4;
 template <typename T, int NC>
 __global__ void __launch_bounds__(32 * P2M_WARPS) k_p2m(int p, const int* leaves, const double4* cs, const int2* range,
                                                        const typename V4<T>::type* src, const double* xs, int K,
-                                                       double ox, double oy, double oz, T* M, int64_t bstride) {
+                                                       double ox, double oy, double oz, T* M, int64_t bstride,
+                                                       int64_t xsys, size_t msys) {
     extern __shared__ unsigned char smem_raw[];
     T* acc = reinterpret_cast<T*>(smem_raw);  // [warps][NC][ncoef][2]
+    xs += blockIdx.y * xsys;  // copy blockIdx.y of a Stokes batch
+    M += blockIdx.y * msys;
     const int nco = ncoef(p);
     const int cell = leaves[blockIdx.x];
     const double4 cc = cs[cell];
@@ -547,7 +550,8 @@ constexpr int TREE_THREADS = 256;
 
 template <typename T, int NC>
 __global__ void __launch_bounds__(TREE_THREADS) k_m2m(int p, const int* parents, const double4* cs, const int2* child,
-                                                      const T* oct, T* M) {
+                                                      const T* oct, T* M, size_t msys) {
+    M += blockIdx.y * msys;  // copy blockIdx.y of a Stokes batch
     extern __shared__ unsigned char smem_raw[];
     const int nco = ncoef(p);
     const int cell = parents[blockIdx.x];
@@ -604,7 +608,9 @@ __global__ void __launch_bounds__(TREE_THREADS) k_m2m(int p, const int* parents,
 // One thread per output coefficient (j, k); the irregular table of each pair is
 // built in shared memory, one column per thread.
 template <typename T, int NC>
-__global__ void k_m2l(int p, const int* ptr, const int* srcl, const double4* cs, const T* M, T* L) {
+__global__ void k_m2l(int p, const int* ptr, const int* srcl, const double4* cs, const T* M, T* L, size_t msys) {
+    M += blockIdx.y * msys;  // copy blockIdx.y of a Stokes batch
+    L += blockIdx.y * msys;
     __shared__ T sI[NI_MAX * 2];
     __shared__ T sM[NC * NCOEF_MAX * 2];
     const int tc = blockIdx.x;
@@ -681,7 +687,8 @@ __global__ void k_m2l(int p, const int* ptr, const int* srcl, const double4* cs,
 // staged in shared memory; thread (child x, coefficient q) writes one output.
 template <typename T, int NC>
 __global__ void __launch_bounds__(TREE_THREADS) k_l2l(int p, const int* parents, const double4* cs, const int2* child,
-                                                      const T* oct, T* L) {
+                                                      const T* oct, T* L, size_t msys) {
+    L += blockIdx.y * msys;  // copy blockIdx.y of a Stokes batch
     extern __shared__ unsigned char smem_raw[];
     const int nco = ncoef(p);
     const int cell = parents[blockIdx.x];
@@ -734,8 +741,11 @@ __global__ void __launch_bounds__(TREE_THREADS) k_l2l(int p, const int* parents,
 template <typename T, int NC>
 __global__ void k_l2p(int p, const int* leaves, const double4* cs, const int2* range, const double4* tgt, const T* L,
                       const double* ynear, double scale, double ox, double oy, double oz, const double* xs_half,
-                      const float4* tgt_rel, double* yout, int64_t bstride) {
+                      const float4* tgt_rel, double* yout, int64_t bstride, size_t msys, int64_t ysys) {
     __shared__ T sL[NC * NCOEF_MAX * 2];
+    L += blockIdx.y * msys;  // copy blockIdx.y of a Stokes batch and its output vector
+    ynear += blockIdx.y * ysys;
+    yout += blockIdx.y * ysys;
     const int cell = leaves[blockIdx.x];
     const double4 cc = cs[cell];
     const int2 r = range[cell];
@@ -984,7 +994,7 @@ int far_field_t(fmmbem_handle* h, int p) {
     // P2M
     prof_begin(h, FMMBEM_PASS_P2M);
     const size_t sm = (size_t)P2M_WARPS * NC * nco * 2 * sizeof(T);
-    if (std::is_same<T, float>::value && (NC == 1 || h->nrhs > 1)) {
+    if (std::is_same<T, float>::value && (NC == 1 || (h->nrhs > 1 && h->kernel == FMMBEM_LAPLACE))) {
         // mixed precision: the packed FP32 sources
         float* Mf = reinterpret_cast<float*>(h->M);
         const size_t smp = (size_t)P2MP_WARPS * NC * nco * 2 * sizeof(float);
@@ -1010,9 +1020,10 @@ int far_field_t(fmmbem_handle* h, int p) {
                 p, h->leaves, h->cell_cs, h->cell_range, src, h->src_w, h->nrm_d, h->nrm_f, h->xin, h->K, h->origin[0],
                 h->origin[1], h->origin[2], M);
     } else {
-        k_p2m<T, NC><<<h->n_leaves, 32 * P2M_WARPS, sm, st>>>(p, h->leaves, h->cell_cs, h->cell_range, src, h->xin,
-                                                             h->K, h->origin[0], h->origin[1], h->origin[2], M,
-                                                             h->nrhs > 1 ? h->N : 0);
+        const bool copies = h->nsys > 1;
+        k_p2m<T, NC><<<dim3(h->n_leaves, h->nsys), 32 * P2M_WARPS, sm, st>>>(
+            p, h->leaves, h->cell_cs, h->cell_range, src, h->xin, h->K, h->origin[0], h->origin[1], h->origin[2], M,
+            (h->nrhs > 1 && !copies) ? h->N : 0, h->N * h->dof, h->esys);
     }
     FMM_LAUNCHED();
     prof_end(h, FMMBEM_PASS_P2M, 1);
@@ -1039,7 +1050,8 @@ int far_field_t(fmmbem_handle* h, int p) {
             FMM_TRY(tree_tc(h, p, l, 0));
             ++nl;
         } else {
-            k_m2m<T, NC><<<pe - pb, TREE_THREADS, sm_m2m, st>>>(p, h->parents + pb, h->cell_cs, h->cell_child, oct, M);
+            k_m2m<T, NC><<<dim3(pe - pb, h->nsys), TREE_THREADS, sm_m2m, st>>>(p, h->parents + pb, h->cell_cs,
+                                                                             h->cell_child, oct, M, h->esys);
             FMM_LAUNCHED();
             ++nl;
         }
@@ -1052,7 +1064,8 @@ int far_field_t(fmmbem_handle* h, int p) {
     } else if (h->m2l_mode != FMMBEM_M2L_GATHER && h->m2l_tables) {
         FMM_TRY(m2l_gemm(h, p, !std::is_same<T, float>::value));
     } else {
-        k_m2l<T, NC><<<h->n_cells, m2l_block(p), 0, st>>>(p, h->m2l_ptr, h->m2l_src, h->cell_cs, M, L);
+        k_m2l<T, NC><<<dim3(h->n_cells, h->nsys), m2l_block(p), 0, st>>>(p, h->m2l_ptr, h->m2l_src, h->cell_cs, M, L,
+                                                                         h->esys);
         FMM_LAUNCHED();
     }
     prof_end(h, FMMBEM_PASS_M2L, 1);
@@ -1066,7 +1079,8 @@ int far_field_t(fmmbem_handle* h, int p) {
         if (tree_tc_on) {
             FMM_TRY(tree_tc(h, p, l, 1));
         } else {
-            k_l2l<T, NC><<<pe - pb, TREE_THREADS, sm_l2l, st>>>(p, h->parents + pb, h->cell_cs, h->cell_child, oct, L);
+            k_l2l<T, NC><<<dim3(pe - pb, h->nsys), TREE_THREADS, sm_l2l, st>>>(p, h->parents + pb, h->cell_cs,
+                                                                             h->cell_child, oct, L, h->esys);
             FMM_LAUNCHED();
         }
         ++nl2;
@@ -1086,11 +1100,10 @@ int far_eval_t(fmmbem_handle* h, int p, double* y_sorted, double scale) {
                                                       h->layer == FMMBEM_LAYER_DOUBLE ? h->xin : nullptr,
                                                       h->tgt_rel, y_sorted);
     else
-        k_l2p<T, NC><<<h->n_leaves, 32, 0, h->stream>>>(p, h->leaves, h->cell_cs, h->cell_range, h->tgt_d,
-                                                        reinterpret_cast<const T*>(h->L), h->ynear, scale,
-                                                        h->origin[0], h->origin[1], h->origin[2],
-                                                        h->layer == FMMBEM_LAYER_DOUBLE ? h->xin : nullptr,
-                                                        h->tgt_rel, y_sorted, h->nrhs > 1 ? h->N : 0);
+        k_l2p<T, NC><<<dim3(h->n_leaves, h->nsys), 32, 0, h->stream>>>(
+            p, h->leaves, h->cell_cs, h->cell_range, h->tgt_d, reinterpret_cast<const T*>(h->L), h->ynear, scale,
+            h->origin[0], h->origin[1], h->origin[2], h->layer == FMMBEM_LAYER_DOUBLE ? h->xin : nullptr, h->tgt_rel,
+            y_sorted, (h->nrhs > 1 && h->nsys == 1) ? h->N : 0, h->esys, h->N * h->dof);
     FMM_LAUNCHED();
     prof_end(h, FMMBEM_PASS_L2P, 1);
     h->launches += 1;

@@ -8,8 +8,14 @@ struct fmmbem_handle {
     // problem
     int kernel = FMMBEM_LAPLACE;  // FMMBEM_LAPLACE or FMMBEM_STOKES
     int dof = 1;                  // unknowns per panel
-    int ncomp = 1;                // harmonic expansions per cell (1 Laplace, 4 Stokes, nrhs batched Laplace)
-    int nrhs = 1;                 // vectors per mat-vec ([nrhs][N] layout; FMMBEM_BATCH for batched handles)
+    int ncomp = 1;                // harmonic expansions per cell and copy (1 Laplace, 4 Stokes, nrhs batched Laplace)
+    int nrhs = 1;                 // vectors per mat-vec ([nrhs][N * dof] layout)
+    // A batch of Stokes vectors keeps one copy of the expansion arrays per vector, copy r at
+    // M + r esys (RHS-major): the tensor-core passes take every copy's rows in one launch, the
+    // other kernels take the copy from blockIdx.y. 1 copy otherwise (a Laplace batch
+    // interleaves its four vectors as components instead).
+    int nsys = 1;
+    size_t esys = 0;              // reals per copy: n_cells * ncomp * ESTRIDE
     int K = 4;                    // far-field Gauss points per panel
     int ncrit = 150;
     double theta = 0.5;
@@ -172,6 +178,7 @@ struct fmmbem_handle {
     // timing
     double setup_seconds = 0.0;
     bool prof_on = false;
+    bool prof_serial = false;  // profiled mat-vecs run the near field on the far field's stream
     fmmbem_profile prof{};
     cudaEvent_t ev[2 * FMMBEM_N_PASSES] = {};
     void* prof_state = nullptr;  // per-handle event pool and pending intervals (capi.cu)

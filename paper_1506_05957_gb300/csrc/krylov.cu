@@ -561,7 +561,7 @@ static int gmres_solve_on(fmmbem_handle* h, const double* b, double tol, int rel
 static int gmres_batch_on(fmmbem_handle* h, const double* b, double tol, int relax, int p_initial, int p_min,
                           double* x, int* iters, int* p_hist, double* res_hist, double* true_res) {
     const int nb = h->nrhs;
-    const int64_t n = h->N;  // per system
+    const int64_t n = h->N * h->dof;  // per system
     const int m_max = h->kr_m;
     const int max_iter = h->opts.max_iter;
     cudaStream_t st = h->stream;

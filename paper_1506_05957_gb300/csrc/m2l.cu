@@ -188,8 +188,10 @@ template <> struct Vec4<double> { typedef double4 type; };
 template <typename T, int RPT, int NC>
 __global__ void __launch_bounds__(GEMM_THREADS) k_m2l_gemm(int p, const int4* tiles, const int* pt, const int* ps,
                                                           const int* prefl, const T* sign, const T* tables,
-                                                          size_t tab_stride, int ld, const T* M, T* L) {
+                                                          size_t tab_stride, int ld, const T* M, T* L, size_t msys) {
     constexpr int RP = 16 * RPT;
+    M += blockIdx.y * msys;  // copy blockIdx.y of a Stokes batch
+    L += blockIdx.y * msys;
     __shared__ __align__(16) T sA[GEMM_KC][RP];
     __shared__ __align__(16) T sB[GEMM_KC][GEMM_COLS];
     const int4 tile = tiles[blockIdx.x];
@@ -340,7 +342,7 @@ int build_m2l_tables(fmmbem_handle* h) {
     FMM_LAUNCHED();
     // tiles of 128 rows for the tensor-core path (128 pairs Laplace, 32 pairs x 4 Stokes)
     {
-        const int per_tc = 128 / h->ncomp;
+        const int per_tc = 128 / (h->ncomp * h->nsys);  // rows of a pair: every component of every copy
         FMM_CU(cudaMemsetAsync(cnt, 0, sizeof(int) * (ntab + 1), st));
         k_tile_counts<<<(ntab + T - 1) / T, T, 0, st>>>(tab_first, ntab, per_tc, cnt);
         FMM_LAUNCHED();
@@ -376,11 +378,11 @@ int m2l_gemm_t(fmmbem_handle* h, int p) {
     const T* M = reinterpret_cast<const T*>(h->M);
     const T* tab = std::is_same<T, float>::value ? reinterpret_cast<const T*>(h->tab_f) : reinterpret_cast<const T*>(h->tab_d);
     const T* sign = std::is_same<T, float>::value ? reinterpret_cast<const T*>(h->sign_f) : reinterpret_cast<const T*>(h->sign_d);
-    FMM_CU(cudaMemsetAsync(L, 0, sizeof(T) * (size_t)h->n_cells * NC * ESTRIDE, h->stream));
+    FMM_CU(cudaMemsetAsync(L, 0, sizeof(T) * h->esys * h->nsys, h->stream));
     const int rpt = rpt_for(p);
-    const dim3 g(h->n_tiles), b(GEMM_THREADS);
+    const dim3 g(h->n_tiles, h->nsys), b(GEMM_THREADS);
 #define M2L_CASE(R) \
-    case R: k_m2l_gemm<T, R, NC><<<g, b, 0, h->stream>>>(p, h->m2l_tiles, h->m2l_pt, h->m2l_ps, h->m2l_refl, sign, tab, h->tab_stride, h->tab_ld, M, L); break;
+    case R: k_m2l_gemm<T, R, NC><<<g, b, 0, h->stream>>>(p, h->m2l_tiles, h->m2l_pt, h->m2l_ps, h->m2l_refl, sign, tab, h->tab_stride, h->tab_ld, M, L, h->esys); break;
     switch (rpt) {
         M2L_CASE(1) M2L_CASE(2) M2L_CASE(4) M2L_CASE(8) M2L_CASE(12) M2L_CASE(16) M2L_CASE(20)
         default: fmmbem_set_error("no M2L kernel for p=%d", p); return FMMBEM_EINVAL;

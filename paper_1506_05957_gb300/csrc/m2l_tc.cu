@@ -487,18 +487,19 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_m2l_tc(int p, int prods, cons
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(512));
 }
 
-// Row tables of the tensor-core tiles (see k_m2l_tc).
-template <int NC>
-__global__ void k_tc_rowinfo(const int4* tiles, int ntiles, const int* pt, const int* ps, const int* prefl, int* src_info,
-                             int* dst_info) {
+// Row tables of the tensor-core tiles (see k_m2l_tc). A pair has nc * nsys rows: component c
+// of copy q (a Stokes batch keeps one copy of the expansions per vector, esys reals apart).
+__global__ void k_tc_rowinfo(const int4* tiles, int ntiles, const int* pt, const int* ps, const int* prefl, int nc,
+                             int nsys, size_t esys, int* src_info, int* dst_info) {
     const int t = blockIdx.x, r = threadIdx.x;
     if (t >= ntiles || r >= TC_ROWS) return;
     const int4 tile = tiles[t];
+    const int rows = nc * nsys;
     int si = -1, di = -1;
-    if (r < tile.z * NC) {
-        const int pr = tile.y + r / NC, comp = r % NC;
-        si = (int)(((size_t)ps[pr] * NC + comp) * ESTRIDE) * 8 + prefl[pr];
-        di = (int)(((size_t)pt[pr] * NC + comp) * ESTRIDE) * 8 + prefl[pr];
+    if (r < tile.z * rows) {
+        const int pr = tile.y + r / rows, q = (r % rows) / nc, comp = r % nc;
+        si = (int)(q * esys + ((size_t)ps[pr] * nc + comp) * ESTRIDE) * 8 + prefl[pr];
+        di = (int)(q * esys + ((size_t)pt[pr] * nc + comp) * ESTRIDE) * 8 + prefl[pr];
     }
     src_info[(size_t)t * TC_ROWS + r] = si;
     dst_info[(size_t)t * TC_ROWS + r] = di;
@@ -554,10 +555,10 @@ __global__ void k_tree_ops(int pmax, double* Td) {
 }
 
 // Zero the first R reals of every expansion of the listed cells (M2M accumulates into them).
-__global__ void k_zero_cells(const int* cells, int n, int nc, int R, float* X) {
+__global__ void k_zero_cells(const int* cells, int n, int nc, int R, float* X, size_t esys) {
     const int c = blockIdx.x;
     if (c >= n) return;
-    float* row = X + (size_t)cells[c] * nc * ESTRIDE;
+    float* row = X + blockIdx.y * esys + (size_t)cells[c] * nc * ESTRIDE;  // copy blockIdx.y of a Stokes batch
     for (int e = threadIdx.x; e < nc * R; e += blockDim.x) row[(e / R) * ESTRIDE + e % R] = 0.f;
 }
 
@@ -599,13 +600,15 @@ static int build_tree_tc(fmmbem_handle* h, int nr, int rows_max, int nch) {
             for (int x = 0; x < ch[pc].y; ++x) {
                 const int cc = ch[pc].x + x;
                 const int o = (cs[cc].x > cs[pc].x ? 1 : 0) | (cs[cc].y > cs[pc].y ? 2 : 0) | (cs[cc].z > cs[pc].z ? 4 : 0);
-                for (int comp = 0; comp < NC; ++comp) {
-                    const int prow = (pc * NC + comp) * ESTRIDE, crow = (cc * NC + comp) * ESTRIDE;
-                    rows_ms.push_back(crow * 8 + o);
-                    rows_md.push_back(prow * 8 + o);
-                    rows_ls.push_back(prow * 8 + (7 - o));
-                    rows_ld.push_back(crow * 8 + (7 - o));
-                }
+                for (int q = 0; q < h->nsys; ++q)  // every copy of a Stokes batch
+                    for (int comp = 0; comp < NC; ++comp) {
+                        const int prow = (int)(q * h->esys) + (pc * NC + comp) * ESTRIDE;
+                        const int crow = (int)(q * h->esys) + (cc * NC + comp) * ESTRIDE;
+                        rows_ms.push_back(crow * 8 + o);
+                        rows_md.push_back(prow * 8 + o);
+                        rows_ls.push_back(prow * 8 + (7 - o));
+                        rows_ld.push_back(crow * 8 + (7 - o));
+                    }
             }
         }
         const int nt = ((int)rows_ms.size() + TC_ROWS - 1) / TC_ROWS;
@@ -643,7 +646,7 @@ static int build_tree_tc(fmmbem_handle* h, int nr, int rows_max, int nch) {
 int build_m2l_tc(fmmbem_handle* h) {
     if (!h->m2l_tables) return 0;
     // row tables pack (offset * 8 + reflection) into an int
-    if ((double)h->n_cells * h->ncomp * ESTRIDE * 8.0 >= 2147483647.0) return 0;
+    if ((double)h->esys * h->nsys * 8.0 >= 2147483647.0) return 0;
     const int pmax = h->opts.p_max;
     const int nr = 2 * ncoef(pmax);
     const int rows_max = (nr + 15) & ~15;
@@ -657,12 +660,9 @@ int build_m2l_tc(fmmbem_handle* h) {
     FMM_CU(fmm_malloc((void**)&h->tc_src_info, sizeof(int) * (size_t)h->n_tiles_tc * TC_ROWS));
     FMM_CU(fmm_malloc((void**)&h->tc_dst_info, sizeof(int) * (size_t)h->n_tiles_tc * TC_ROWS));
     if (h->n_tiles_tc > 0) {
-        if (h->ncomp == 1)
-            k_tc_rowinfo<1><<<h->n_tiles_tc, TC_ROWS, 0, h->stream>>>(h->m2l_tiles_tc, h->n_tiles_tc, h->m2l_pt, h->m2l_ps,
-                                                                     h->m2l_refl, h->tc_src_info, h->tc_dst_info);
-        else
-            k_tc_rowinfo<4><<<h->n_tiles_tc, TC_ROWS, 0, h->stream>>>(h->m2l_tiles_tc, h->n_tiles_tc, h->m2l_pt, h->m2l_ps,
-                                                                     h->m2l_refl, h->tc_src_info, h->tc_dst_info);
+        k_tc_rowinfo<<<h->n_tiles_tc, TC_ROWS, 0, h->stream>>>(h->m2l_tiles_tc, h->n_tiles_tc, h->m2l_pt, h->m2l_ps,
+                                                               h->m2l_refl, h->ncomp, h->nsys, h->esys, h->tc_src_info,
+                                                               h->tc_dst_info);
         FMM_LAUNCHED();
     }
     FMM_CU(fmm_malloc((void**)&h->tc_err, sizeof(int)));
@@ -683,7 +683,8 @@ int build_m2l_tc(fmmbem_handle* h) {
 int tree_tc_zero(fmmbem_handle* h, int p) {
     const int np = h->parent_start.back();
     if (np <= 0) return 0;
-    k_zero_cells<<<np, 128, 0, h->stream>>>(h->parents, np, h->ncomp, 2 * ncoef(p), reinterpret_cast<float*>(h->M));
+    k_zero_cells<<<dim3(np, h->nsys), 128, 0, h->stream>>>(h->parents, np, h->ncomp, 2 * ncoef(p),
+                                                            reinterpret_cast<float*>(h->M), h->esys);
     FMM_LAUNCHED();
     return 0;
 }
@@ -715,7 +716,7 @@ int tree_tc(fmmbem_handle* h, int p, int level, int which) {
 int m2l_tc(fmmbem_handle* h, int p) {
     float* L = reinterpret_cast<float*>(h->L);
     const float* M = reinterpret_cast<const float*>(h->M);
-    FMM_CU(cudaMemsetAsync(L, 0, sizeof(float) * (size_t)h->n_cells * h->ncomp * ESTRIDE, h->stream));
+    FMM_CU(cudaMemsetAsync(L, 0, sizeof(float) * h->esys * h->nsys, h->stream));
     const size_t sm = m2l_tc_smem(p);
     const int grid = std::min(h->n_tiles_tc, h->n_sm);  // persistent: one CTA per SM (512 TMEM columns each)
     const int prods = 3;

@@ -903,6 +903,8 @@ template <> struct VecLane<LAP_B4> { static constexpr int DOF = 4, TM = P2P_SRC_
 __global__ void k_pack_sources_stokes(const float4* src_rel, const double* xs, int K, int64_t n, float4* out) {
     const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (j >= n) return;
+    xs += blockIdx.y * 3 * n;  // vector blockIdx.y of a Stokes batch
+    out += blockIdx.y * 2 * (int64_t)K * n;
     const float t0 = (float)xs[3 * j], t1 = (float)xs[3 * j + 1], t2 = (float)xs[3 * j + 2];
     for (int k = 0; k < K; ++k) {
         const int64_t g = j * K + k;
@@ -1001,8 +1003,12 @@ __global__ void __launch_bounds__(32 * PS_WARPS, VecLane<OP>::MINB) k_p2p_vec_sr
                                                                  const float4* prec, const int* poff, const int* plen,
                                                                  const float4* srcw, const float4* tgt, int K,
                                                                  const int* cptr, const int* ccol, const double* cval,
-                                                                 const double* xs, double* ynear, int64_t bstride) {
+                                                                 const double* xs, double* ynear, int64_t bstride,
+                                                                 int64_t ssys, int64_t xsys) {
     constexpr int DOF = VecLane<OP>::DOF, TM = VecLane<OP>::TM;
+    srcw += blockIdx.y * ssys;  // vector blockIdx.y of a Stokes batch: its strengths, input and output
+    xs += blockIdx.y * xsys;
+    ynear += blockIdx.y * xsys;
     __shared__ VlShared<OP> sh;
     constexpr int RND = 32 * SS_SRC;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -1226,10 +1232,10 @@ int near_field_on(fmmbem_handle* h, bool fp64);
 // it), on the handle's stream before the near and far fields fork.
 int pack_sources(fmmbem_handle* h) {
     const unsigned g = (unsigned)((h->N + 255) / 256);
-    if (h->nrhs > 1)
+    if (h->nrhs > 1 && h->kernel == FMMBEM_LAPLACE)
         k_pack_sources_b4<<<g, 256, 0, h->stream>>>(h->src_rel, h->xin, h->K, h->N, h->src_w);
     else if (h->kernel == FMMBEM_STOKES)
-        k_pack_sources_stokes<<<g, 256, 0, h->stream>>>(h->src_rel, h->xin, h->K, h->N, h->src_w);
+        k_pack_sources_stokes<<<dim3(g, h->nsys), 256, 0, h->stream>>>(h->src_rel, h->xin, h->K, h->N, h->src_w);
     else if (h->layer == FMMBEM_LAYER_DOUBLE)
         k_pack_sources_dipole<<<g, 256, 0, h->stream>>>(h->src_rel, h->nrm_f, h->xin, h->K, h->N, h->src_w);
     else
@@ -1264,22 +1270,22 @@ static int launch_items(fmmbem_handle* h) {
     const int4* it = h->p2p_items;
     const unsigned nb = (unsigned)h->n_p2p_items;
     if (nb == 0) return 0;
-    if (h->nrhs > 1)
+    if (h->nrhs > 1 && h->kernel == FMMBEM_LAPLACE)
         k_p2p_vec_src<LAP_B4><<<nb, 32 * PS_WARPS, 0, h->stream>>>(it, h->cell_range, h->p2p_ptr, h->p2p_rec, h->p2p_off,
                                                                    h->p2p_len, h->src_w, h->tgt_rel, h->K, h->corr_ptr,
-                                                                   h->corr_col, h->corr_sl, h->xin, h->ynear, h->N);
+                                                                   h->corr_col, h->corr_sl, h->xin, h->ynear, h->N, 0, 0);
     else if (h->kernel == FMMBEM_LAPLACE && h->layer == FMMBEM_LAYER_DOUBLE)
         k_p2p_vec_src<LAP_DL><<<nb, 32 * PS_WARPS, 0, h->stream>>>(it, h->cell_range, h->p2p_ptr, h->p2p_rec, h->p2p_off,
                                                                    h->p2p_len, h->src_w, h->tgt_rel, h->K, h->corr_ptr,
-                                                                   h->corr_col, h->corr_dl, h->xin, h->ynear, 0);
+                                                                   h->corr_col, h->corr_dl, h->xin, h->ynear, 0, 0, 0);
     else if (h->kernel == FMMBEM_LAPLACE)
         k_p2p_lap_src<<<nb, 32 * PS_WARPS, 0, h->stream>>>(it, h->cell_range, h->p2p_ptr, h->p2p_rec, h->p2p_off,
                                                           h->p2p_len, h->src_w, h->tgt_rel, h->K, h->corr_ptr,
                                                           h->corr_col, h->corr_sl, h->xin, h->ynear);
-    else
-        k_p2p_vec_src<STK_SL><<<nb, 32 * PS_WARPS, 0, h->stream>>>(it, h->cell_range, h->p2p_ptr, h->p2p_rec, h->p2p_off,
-                                                                   h->p2p_len, h->src_w, h->tgt_rel, h->K, h->corr_ptr,
-                                                                   h->corr_col, h->corr_sl, h->xin, h->ynear, 0);
+    else  // the Stokeslet: one launch for every vector of a batch (blockIdx.y)
+        k_p2p_vec_src<STK_SL><<<dim3(nb, h->nsys), 32 * PS_WARPS, 0, h->stream>>>(
+            it, h->cell_range, h->p2p_ptr, h->p2p_rec, h->p2p_off, h->p2p_len, h->src_w, h->tgt_rel, h->K, h->corr_ptr,
+            h->corr_col, h->corr_sl, h->xin, h->ynear, 0, 2 * h->NS, 3 * h->N);
     FMM_LAUNCHED();
     h->launches += 1;
     return 0;
@@ -1291,7 +1297,7 @@ int near_field_on(fmmbem_handle* h, bool fp64) {
     prof_begin(h, FMMBEM_PASS_P2P);
     const int64_t l0 = h->launches;
     const bool items = !fp64 && h->p2p_variant == 3 && h->p2p_items;
-    if (h->nrhs > 1) {
+    if (h->nrhs > 1 && h->kernel == FMMBEM_LAPLACE) {
         if (items) FMM_TRY(launch_items(h));
         else {
             FMM_TRY((fp64 ? launch_p2p<double, LAP_B4>(h, h->corr_sl) : launch_p2p<float, LAP_B4>(h, h->corr_sl)));
@@ -1348,8 +1354,18 @@ int near_field_on(fmmbem_handle* h, bool fp64) {
     } else if (items) {
         FMM_TRY(launch_items(h));
     } else {
-        FMM_TRY((fp64 ? launch_p2p<double, STK_SL>(h, h->corr_sl) : launch_p2p<float, STK_SL>(h, h->corr_sl)));
-        h->launches += 1;
+        // the shared-tile schedule takes one vector per launch: each vector of a batch in turn
+        const double* x0 = h->xin;
+        double* y0 = h->ynear;
+        for (int q = 0; q < h->nsys; ++q) {
+            h->xin = x0 + q * 3 * h->N;
+            h->ynear = y0 + q * 3 * h->N;
+            const int rc = fp64 ? launch_p2p<double, STK_SL>(h, h->corr_sl) : launch_p2p<float, STK_SL>(h, h->corr_sl);
+            h->xin = x0;
+            h->ynear = y0;
+            FMM_TRY(rc);
+            h->launches += 1;
+        }
     }
     prof_end(h, FMMBEM_PASS_P2P, (int)(h->launches - l0));
     return 0;

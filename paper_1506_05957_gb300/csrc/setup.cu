@@ -1005,8 +1005,8 @@ int build_geometry_tree_lists(fmmbem_handle* h, const fmmbem_mesh* mesh) {
             // targets split evenly into chunks of at most tmax, largest work first
             std::vector<int4> items;
             std::vector<long long> cost;
-            const int tmax = h->nrhs > 1 ? P2P_SRC_TMAX_BATCH
-                                         : (h->kernel == FMMBEM_STOKES ? P2P_SRC_TMAX_STOKES : P2P_SRC_TMAX);
+            const int tmax = h->kernel == FMMBEM_STOKES ? P2P_SRC_TMAX_STOKES
+                                                        : (h->nrhs > 1 ? P2P_SRC_TMAX_BATCH : P2P_SRC_TMAX);
             for (int c : lv) {
                 const int t = rg[c].y - rg[c].x;
                 const int nchk = (t + tmax - 1) / tmax;

@@ -139,6 +139,6 @@ def test_batch_argument_errors(torch_cuda, sphere1280):
     with pytest.raises(FmmBemError):
         batch.set_layer(FMMBEM_LAYER_DOUBLE)
     with pytest.raises(FmmBemError):
-        FmmBem(s["v"], s["t"], kernel=FMMBEM_STOKES, gauss_k=3, nrhs=4)
+        FmmBem(s["v"], s["t"], kernel=FMMBEM_STOKES, gauss_k=3, nrhs=9)  # beyond FMMBEM_STOKES_BATCH_MAX
     with pytest.raises(FmmBemError):
-        FmmBem(s["v"], s["t"], nrhs=3)
+        FmmBem(s["v"], s["t"], nrhs=3)  # a Laplace batch holds FMMBEM_BATCH vectors
