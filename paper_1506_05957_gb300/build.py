@@ -14,7 +14,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libfmmbem.so")
-SOURCES = ["setup.cu", "fmm.cu", "m2l.cu", "m2l_tc.cu", "near.cu", "krylov.cu", "capi.cu", "serve.cu", "peaks.cu"]
+SOURCES = ["setup.cu", "fmm.cu", "m2l.cu", "m2l_tc.cu", "near.cu", "krylov.cu", "capi.cu", "serve.cu", "peaks.cu", "sort.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "nvcc")
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I" + INCLUDE, "-I" + CSRC]

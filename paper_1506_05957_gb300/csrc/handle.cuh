@@ -105,6 +105,7 @@ struct fmmbem_handle {
     float* tab_tc = nullptr;
     size_t tc_stride = 0;
     int tc_rows_max = 0;
+    int tc_kc = 32;               // K width of the tensor-core operand chunks (tables and kernel)
     int4* m2l_tiles_tc = nullptr;
     int n_tiles_tc = 0;
     int* tc_src_info = nullptr;   // [n_tiles_tc][128]: source row offset * 8 + reflection (-1: empty row)
@@ -215,6 +216,12 @@ int gmres_solve(fmmbem_handle* h, const double* b_sorted, double tol, int relax,
 int read_wait_flags(fmmbem_handle* h, cudaStream_t st);
 // peaks.cu
 int peak_rate(int kind, int blocks, int64_t iters, double* ops, double* ms, cudaStream_t st);
+// sort.cu: stable LSD radix sorts of keys [0, end_bit) (values optional: NULL), and prefix sums;
+// outputs must not alias inputs except for the scans; temporaries are stream-ordered on st
+int radix_sort(const uint64_t* kin, uint64_t* kout, const int* vin, int* vout, int64_t n, int end_bit, cudaStream_t st);
+int radix_sort(const uint32_t* kin, uint32_t* kout, const int* vin, int* vout, int64_t n, int end_bit, cudaStream_t st);
+int exclusive_scan(const int* in, int* out, int64_t n, cudaStream_t st);
+int inclusive_scan(const int* in, int* out, int64_t n, cudaStream_t st);
 // capi.cu
 int matvec_sorted(fmmbem_handle* h, int p, const double* xs, double* ys);
 void prof_begin(fmmbem_handle* h, int pass);

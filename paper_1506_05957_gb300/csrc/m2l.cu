@@ -15,7 +15,6 @@
 // form T_v = D_Q T_{Qv} D_Q with D_Q diagonal +-1. Operators are stored only for
 // v with non-negative components; each pair carries the reflection Q (3 bits) that maps
 // its v there, and the products apply D_Q to the gathered input and to the output.
-#include <cub/cub.cuh>
 #include <algorithm>
 #include <type_traits>
 #include "handle.cuh"
@@ -280,19 +279,11 @@ int build_m2l_tables(fmmbem_handle* h) {
     FMM_LAUNCHED();
     k_pair_keys<<<gp, T, 0, st>>>(pt, ps, n, h->cell_cs, h->cell_level, key, idx, refl, bad);
     FMM_LAUNCHED();
-    size_t tb = 0;
-    FMM_CU(cub::DeviceRadixSort::SortPairs(nullptr, tb, key, key_s, idx, idx_s, (int)n, 0, 3 * KEY_BITS + 4, st));
-    void* tmp = nullptr;
-    FMM_CU(fmm_malloc(&tmp, tb ? tb : 1));
-    FMM_CU(cub::DeviceRadixSort::SortPairs(tmp, tb, key, key_s, idx, idx_s, (int)n, 0, 3 * KEY_BITS + 4, st));
-    fmm_free(tmp);
+    FMM_TRY(radix_sort(reinterpret_cast<const uint64_t*>(key), reinterpret_cast<uint64_t*>(key_s), idx, idx_s, n,
+                       3 * KEY_BITS + 4, st));
     k_mark_heads<<<gp, T, 0, st>>>(key_s, n, head);
     FMM_LAUNCHED();
-    tb = 0;
-    FMM_CU(cub::DeviceScan::InclusiveSum(nullptr, tb, head, scan, (int)n, st));
-    FMM_CU(fmm_malloc(&tmp, tb ? tb : 1));
-    FMM_CU(cub::DeviceScan::InclusiveSum(tmp, tb, head, scan, (int)n, st));
-    fmm_free(tmp);
+    FMM_TRY(inclusive_scan(head, scan, n, st));
     int ntab = 0, bad_h = 0;
     FMM_CU(cudaMemcpyAsync(&ntab, scan + n - 1, sizeof(int), cudaMemcpyDeviceToHost, st));
     FMM_CU(cudaMemcpyAsync(&bad_h, bad, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -329,14 +320,10 @@ int build_m2l_tables(fmmbem_handle* h) {
     FMM_CU(cudaMemsetAsync(cnt, 0, sizeof(int) * (ntab + 1), st));
     k_tile_counts<<<(ntab + T - 1) / T, T, 0, st>>>(tab_first, ntab, per_tile, cnt);
     FMM_LAUNCHED();
-    tb = 0;
-    FMM_CU(cub::DeviceScan::ExclusiveSum(nullptr, tb, cnt, off, ntab + 1, st));
-    FMM_CU(fmm_malloc(&tmp, tb ? tb : 1));
-    FMM_CU(cub::DeviceScan::ExclusiveSum(tmp, tb, cnt, off, ntab + 1, st));
+    FMM_TRY(exclusive_scan(cnt, off, ntab + 1, st));
     int ntiles = 0;
     FMM_CU(cudaMemcpyAsync(&ntiles, off + ntab, sizeof(int), cudaMemcpyDeviceToHost, st));
     FMM_CU(cudaStreamSynchronize(st));
-    fmm_free(tmp);
     FMM_TRY(dalloc(&h->m2l_tiles, ntiles));
     k_tile_emit<<<(ntab + T - 1) / T, T, 0, st>>>(tab_first, off, ntab, per_tile, h->m2l_tiles);
     FMM_LAUNCHED();
@@ -346,12 +333,10 @@ int build_m2l_tables(fmmbem_handle* h) {
         FMM_CU(cudaMemsetAsync(cnt, 0, sizeof(int) * (ntab + 1), st));
         k_tile_counts<<<(ntab + T - 1) / T, T, 0, st>>>(tab_first, ntab, per_tc, cnt);
         FMM_LAUNCHED();
-        FMM_CU(fmm_malloc(&tmp, tb ? tb : 1));
-        FMM_CU(cub::DeviceScan::ExclusiveSum(tmp, tb, cnt, off, ntab + 1, st));
+        FMM_TRY(exclusive_scan(cnt, off, ntab + 1, st));
         int ntc = 0;
         FMM_CU(cudaMemcpyAsync(&ntc, off + ntab, sizeof(int), cudaMemcpyDeviceToHost, st));
         FMM_CU(cudaStreamSynchronize(st));
-        fmm_free(tmp);
         FMM_TRY(dalloc(&h->m2l_tiles_tc, ntc));
         k_tile_emit<<<(ntab + T - 1) / T, T, 0, st>>>(tab_first, off, ntab, per_tc, h->m2l_tiles_tc);
         FMM_LAUNCHED();

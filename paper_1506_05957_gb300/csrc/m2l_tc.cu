@@ -6,7 +6,7 @@
 // real coefficients, X holds the gathered source expansions and T the operator
 // (row r = output coefficient). Both operands are K-major in the no-swizzle
 // core-matrix layout (8 rows x 16 bytes per core matrix; 128 bytes between core
-// matrices along K, 1024 bytes between 8-row groups for 32-wide K chunks).
+// matrices along K, 32 KC bytes between 8-row groups of a KC-wide K chunk).
 // FP32 accuracy comes from the 3xTF32 split: x = x_hi + x_lo with x_hi rounded to
 // TF32, D = X_hi T_hi + X_hi T_lo + X_lo T_hi (the X_lo T_lo term is below FP32
 // rounding). T_hi/T_lo are precomputed; X is split while it is staged.
@@ -25,14 +25,22 @@ namespace fmmbem {
 namespace {
 
 constexpr int TC_ROWS = 128;  // rows per tile (MMA M)
-constexpr int TC_KC = 32;     // K per staged chunk
+// K per staged chunk, a kernel template parameter: 32 for handles of one expansion per row
+// group (fewer, larger pipeline items), 16 when four or more expansions per pair make a
+// stage large (p = 16 Stokes: three 56 KB stages in flight instead of one of 112 KB).
+template <int KC> struct Kc {
+    static_assert(KC % 16 == 0, "a gather lane covers whole k-quads of 16-wide steps");
+    static constexpr int KQ = KC / 4;           // k-quads (core matrices along K) per chunk
+    static constexpr int E = KC / 16;           // k-quads per gather lane and item
+    static constexpr uint32_t SBO = 32u * KC;   // bytes between 8-row groups of an operand chunk
+};
 constexpr uint32_t WAIT_LIMIT = 1u << 24;
 
 __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) { return mbar_wait_bounded(mbar, parity, WAIT_LIMIT); }
 
-// element (r, k) of a K-major operand chunk with TC_KC columns, in floats
-__device__ __forceinline__ int cm_index(int r, int k) {
-    return ((r >> 3) * (TC_KC / 4) + (k >> 2)) * 32 + (r & 7) * 4 + (k & 3);
+// element (r, k) of a K-major operand chunk with KC columns, in floats
+template <int KC> __device__ __forceinline__ int cm_index(int r, int k) {
+    return ((r >> 3) * (KC / 4) + (k >> 2)) * 32 + (r & 7) * 4 + (k & 3);
 }
 
 __device__ __forceinline__ float tf32_hi(float x) {
@@ -41,20 +49,21 @@ __device__ __forceinline__ float tf32_hi(float x) {
 
 // Operator tables for this path: per operator, per 32-wide input chunk c, the hi and
 // lo parts of rows [0, rows_max) in the core-matrix layout:
-//   tab[g][c][h][cm_index(r, k mod 32)], h = 0 (hi) or 1 (lo).
+//   tab[g][c][h][cm_index<KC>(r, k mod KC)], h = 0 (hi) or 1 (lo).
+template <int KC>
 __global__ void k_tc_tables(const double* Td, int ntab, int nr, int ld, int nch, int rows_max, float* out) {
-    const size_t per_tab = (size_t)nch * 2 * rows_max * TC_KC;
+    const size_t per_tab = (size_t)nch * 2 * rows_max * KC;
     const size_t total = (size_t)ntab * per_tab;
     for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
         const size_t g = e / per_tab;
         size_t rem = e % per_tab;
-        const int c = (int)(rem / (2 * (size_t)rows_max * TC_KC));
-        rem %= 2 * (size_t)rows_max * TC_KC;
-        const int h = (int)(rem / ((size_t)rows_max * TC_KC));
-        const int q = (int)(rem % ((size_t)rows_max * TC_KC));
+        const int c = (int)(rem / (2 * (size_t)rows_max * KC));
+        rem %= 2 * (size_t)rows_max * KC;
+        const int h = (int)(rem / ((size_t)rows_max * KC));
+        const int q = (int)(rem % ((size_t)rows_max * KC));
         // invert cm_index: q = ((r/8)*8 + kq)*32 + (r%8)*4 + k%4
         const int blk = q >> 5, w = q & 31;
-        const int r = (blk >> 3) * 8 + (w >> 2), k = c * TC_KC + (blk & 7) * 4 + (w & 3);
+        const int r = (blk / Kc<KC>::KQ) * 8 + (w >> 2), k = c * KC + (blk % Kc<KC>::KQ) * 4 + (w & 3);
         double v = 0.0;
         if (r < nr && k < nr) v = Td[g * (size_t)nr * ld + (size_t)k * ld + r];
         const float hi = (float)v;
@@ -89,16 +98,17 @@ constexpr int TC_SMEM_BUDGET = 222 * 1024;
 constexpr int TC_SIGN_TAB = 16 * 8;  // (K chunk, k-quad) entries: chunks of 32 reals up to 2 ncoef(P_MAX) <= 320
 
 struct TcLayout {
-    int nst, nb, np;
-    __host__ __device__ int stage_floats() const { return 2 * TC_ROWS * TC_KC + 2 * np * TC_KC; }
+    int nst, nb, np, kc;
+    __host__ __device__ int stage_floats() const { return 2 * TC_ROWS * kc + 2 * np * kc; }
     __host__ __device__ int epi_floats() const { return 8 * 32 * EPI_LD; }
     __host__ __device__ size_t bytes() const {
         return (size_t)(nst * stage_floats() + epi_floats()) * sizeof(float) + 16 * 8 + 64 + 2 * TC_SIGN_TAB * 4;
     }
 };
 
-__host__ __device__ inline TcLayout tc_layout(int p) {
+__host__ __device__ inline TcLayout tc_layout(int p, int kc) {
     TcLayout t;
+    t.kc = kc;
     const int R = 2 * ncoef(p);
     t.np = (R + 15) & ~15;
     t.nb = t.np <= 128 ? 4 : (t.np <= 256 ? 2 : 1);
@@ -164,24 +174,24 @@ __device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
 
 // rinfo[t * 128 + r] = (row offset of pair row r of tile t in the expansion array) * 8 + reflection,
 // -1 past the tile's rows; one table for the sources (gather) and one for the targets (epilogue).
-template <int NC>
+template <int KC>
 __global__ void __launch_bounds__(TC_THREADS, 1) k_m2l_tc(int p, int prods, const int4* tiles, int ntiles,
                                                          const int* src_info, const int* dst_info, const float* tab,
                                                          size_t tab_stride, int rows_max, const float* M, float* L,
                                                          int* err) {
     extern __shared__ __align__(1024) unsigned char smem[];
-    const TcLayout lay = tc_layout(p);
+    const TcLayout lay = tc_layout(p, KC);
     const int R = 2 * ncoef(p);
     const int Np = lay.np, NST = lay.nst, NB = lay.nb;
-    const int nch = (R + TC_KC - 1) / TC_KC;
-    const uint32_t chunk_bytes = (uint32_t)Np * TC_KC * 4;
+    const int nch = (R + KC - 1) / KC;
+    const uint32_t chunk_bytes = (uint32_t)Np * KC * 4;
     float* stage0 = reinterpret_cast<float*>(smem);
     const int sf = lay.stage_floats();
     float* epi = stage0 + NST * sf;
     uint64_t* bar = reinterpret_cast<uint64_t*>(epi + lay.epi_floats());  // full[4], empty[4], acc_full[4], acc_empty[4]
     uint32_t* taddr_slot = reinterpret_cast<uint32_t*>(bar + 16);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(taddr_slot + 1);
-    // sgn_tab[c * 8 + kq]: bits 4q..4q+3 = sign flips of the 4 reals at k = 32 c + 4 kq under
+    // sgn_tab[k / 4]: bits 4q..4q+3 = sign flips of the 4 reals at k = 4 (k / 4) .. under
     // reflection q; zm_tab: bit e set when k + e >= R (coefficient of degree > p, zeroed)
     uint32_t* sgn_tab = reinterpret_cast<uint32_t*>(smem) + (lay.bytes() - 2 * TC_SIGN_TAB * 4) / 4;
     uint32_t* zm_tab = sgn_tab + TC_SIGN_TAB;
@@ -190,13 +200,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_m2l_tc(int p, int prods, cons
     auto acc_full = [&](int b) { return smem_u32(&bar[8 + b]); };
     auto acc_empty = [&](int b) { return smem_u32(&bar[12 + b]); };
     auto xh = [&](int st) { return stage0 + st * sf; };
-    auto xl = [&](int st) { return stage0 + st * sf + TC_ROWS * TC_KC; };
-    auto th = [&](int st) { return stage0 + st * sf + 2 * TC_ROWS * TC_KC; };
-    auto tl = [&](int st) { return stage0 + st * sf + 2 * TC_ROWS * TC_KC + Np * TC_KC; };
+    auto xl = [&](int st) { return stage0 + st * sf + TC_ROWS * KC; };
+    auto th = [&](int st) { return stage0 + st * sf + 2 * TC_ROWS * KC; };
+    auto tl = [&](int st) { return stage0 + st * sf + 2 * TC_ROWS * KC + Np * KC; };
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     for (int e = tid; e < TC_SIGN_TAB; e += blockDim.x) {
-        const int k0 = 4 * e;  // e = c * 8 + kq  ->  k0 = 32 c + 4 kq
+        const int k0 = 4 * e;  // entry e holds the k-quad of reals k0 .. k0 + 3
         const uint32_t nm_a = coef_nm_bits(k0 >> 1), nm_b = coef_nm_bits((k0 >> 1) + 1);
         uint32_t sg = 0;
         for (int q = 0; q < 8; ++q) sg |= sign_bits(nm_a, nm_b, q) << (4 * q);
@@ -247,10 +257,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_m2l_tc(int p, int prods, cons
                 if (c == 0 && j + 1 < my_tiles) {
                     const float* nt = tab + (size_t)next_tile.x * tab_stride;
                     for (int cc = 0; cc < nch; ++cc) {
-                        const float* q = nt + (size_t)cc * 2 * rows_max * TC_KC;
+                        const float* q = nt + (size_t)cc * 2 * rows_max * KC;
                         asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(q), "r"(chunk_bytes) : "memory");
                         if (prods == 3)
-                            asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(q + (size_t)rows_max * TC_KC),
+                            asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(q + (size_t)rows_max * KC),
                                          "r"(chunk_bytes)
                                          : "memory");
                     }
@@ -258,7 +268,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_m2l_tc(int p, int prods, cons
                 if (k > 0 && !mbar_wait_ab(empty(st), (uint32_t)((k - 1) & 1), abort_flag)) { fail(1); break; }
                 if (*abort_flag) break;
                 asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(full(st)), "r"(bytes) : "memory");
-                const float* src = tab + (size_t)tile.x * tab_stride + (size_t)c * 2 * rows_max * TC_KC;
+                const float* src = tab + (size_t)tile.x * tab_stride + (size_t)c * 2 * rows_max * KC;
                 asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
                                  smem_u32(th(st))),
                              "l"(src), "r"(chunk_bytes), "r"(full(st))
@@ -266,7 +276,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_m2l_tc(int p, int prods, cons
                 if (prods == 3)
                     asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
                                      smem_u32(tl(st))),
-                                 "l"(src + (size_t)rows_max * TC_KC), "r"(chunk_bytes), "r"(full(st))
+                                 "l"(src + (size_t)rows_max * KC), "r"(chunk_bytes), "r"(full(st))
                                  : "memory");
                 issued_tma = i + 1;
                 if (++st == NST) { st = 0; ++k; }
@@ -292,22 +302,22 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_m2l_tc(int p, int prods, cons
                 asm volatile("tcgen05.fence::after_thread_sync;");
                 const uint32_t acc = taddr + (uint32_t)b * buf_cols;
                 const uint32_t ah = smem_u32(xh(st)), al = smem_u32(xl(st)), bh = smem_u32(th(st)), bl = smem_u32(tl(st));
-                for (int ks = 0; ks < TC_KC / 8; ++ks) {
+                for (int ks = 0; ks < KC / 8; ++ks) {
                     const uint32_t off = 256u * ks;
-                    const uint64_t a_hi = smem_desc(ah + off, 128, 1024), b_hi = smem_desc(bh + off, 128, 1024);
+                    const uint64_t a_hi = smem_desc(ah + off, 128, Kc<KC>::SBO), b_hi = smem_desc(bh + off, 128, Kc<KC>::SBO);
                     const uint32_t first = (c == 0 && ks == 0) ? 0u : 1u;
                     mma_tf32(acc, a_hi, b_hi, id1, first);
                     if (prods == 3) {
-                        mma_tf32(acc, a_hi, smem_desc(bl + off, 128, 1024), id1, 1u);
-                        mma_tf32(acc, smem_desc(al + off, 128, 1024), b_hi, id1, 1u);
+                        mma_tf32(acc, a_hi, smem_desc(bl + off, 128, Kc<KC>::SBO), id1, 1u);
+                        mma_tf32(acc, smem_desc(al + off, 128, Kc<KC>::SBO), b_hi, id1, 1u);
                     }
                     if (Np > 256) {
-                        const uint32_t boff = 32u * 1024u;  // operator rows 256.. start 32 row groups later
-                        const uint64_t b2_hi = smem_desc(bh + off + boff, 128, 1024);
+                        const uint32_t boff = 32u * Kc<KC>::SBO;  // operator rows 256.. start 32 row groups later
+                        const uint64_t b2_hi = smem_desc(bh + off + boff, 128, Kc<KC>::SBO);
                         mma_tf32(acc + 256, a_hi, b2_hi, id2, first);
                         if (prods == 3) {
-                            mma_tf32(acc + 256, a_hi, smem_desc(bl + off + boff, 128, 1024), id2, 1u);
-                            mma_tf32(acc + 256, smem_desc(al + off, 128, 1024), b2_hi, id2, 1u);
+                            mma_tf32(acc + 256, a_hi, smem_desc(bl + off + boff, 128, Kc<KC>::SBO), id2, 1u);
+                            mma_tf32(acc + 256, smem_desc(al + off, 128, Kc<KC>::SBO), b2_hi, id2, 1u);
                         }
                     }
                 }
@@ -335,7 +345,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_m2l_tc(int p, int prods, cons
         // phase) advance incrementally; signs and the order-p mask come from the CTA's tables.
         const int pw = warp - TC_PROD0, r7 = lane & 7, kq0 = lane >> 3;
         const int row0 = 16 * pw + r7;
-        float4 d[3][2][2];
+        float4 d[3][2][Kc<KC>::E];
         int f[3][2];
         struct Ctr {
             int j, c;
@@ -346,12 +356,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_m2l_tc(int p, int prods, cons
             for (int h = 0; h < 2; ++h)
                 info[h] = t.j < my_tiles ? src_info[(size_t)tile_of(t.j) * TC_ROWS + row0 + 8 * h] : -1;
         };
-        auto load_data = [&](const Ctr& t, const int (&info)[2], float4 (&v)[2][2]) {
+        auto load_data = [&](const Ctr& t, const int (&info)[2], float4 (&v)[2][Kc<KC>::E]) {
 #pragma unroll
             for (int h = 0; h < 2; ++h)
 #pragma unroll
-                for (int e = 0; e < 2; ++e) {
-                    const int k = t.c * TC_KC + 4 * (kq0 + 4 * e);
+                for (int e = 0; e < Kc<KC>::E; ++e) {
+                    const int k = t.c * KC + 4 * (kq0 + 4 * e);
                     v[h][e] = (t.j < my_tiles && info[h] >= 0)
                                   ? *reinterpret_cast<const float4*>(M + (size_t)(info[h] >> 3) + k)
                                   : make_float4(0.f, 0.f, 0.f, 0.f);
@@ -391,18 +401,18 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_m2l_tc(int p, int prods, cons
                 float* xh_s = xh(st);
                 float* xl_s = xl(st);
 #pragma unroll
-                for (int e = 0; e < 2; ++e) {
+                for (int e = 0; e < Kc<KC>::E; ++e) {
                     const int kq = 4 * (kq0 + 4 * e);
-                    const int te = ci.c * 8 + kq0 + 4 * e;
+                    const int te = ci.c * Kc<KC>::KQ + kq0 + 4 * e;
                     const uint32_t sg = sgn_tab[te], zm = zm_tab[te];
 #pragma unroll
                     for (int h = 0; h < 2; ++h) {
                         const int row = row0 + 8 * h;
                         const float4 x = apply_zero(apply_signs(d[sa][h][e], (sg >> (4 * (f[sa][h] & 7))) & 15u), zm);
                         const float4 hi = make_float4(tf32_hi(x.x), tf32_hi(x.y), tf32_hi(x.z), tf32_hi(x.w));
-                        *reinterpret_cast<float4*>(xh_s + cm_index(row, kq)) = hi;
+                        *reinterpret_cast<float4*>(xh_s + cm_index<KC>(row, kq)) = hi;
                         if (prods == 3)
-                            *reinterpret_cast<float4*>(xl_s + cm_index(row, kq)) =
+                            *reinterpret_cast<float4*>(xl_s + cm_index<KC>(row, kq)) =
                                 make_float4(x.x - hi.x, x.y - hi.y, x.z - hi.z, x.w - hi.w);
                     }
                 }
@@ -564,7 +574,14 @@ __global__ void k_zero_cells(const int* cells, int n, int nc, int R, float* X, s
 
 }  // namespace
 
-size_t m2l_tc_smem(int p) { return tc_layout(p).bytes(); }
+size_t m2l_tc_smem(const fmmbem_handle* h, int p) { return tc_layout(p, h->tc_kc).bytes(); }
+
+// The operator tables in the handle's chunk layout.
+static void launch_tc_tables(const fmmbem_handle* h, unsigned grid, const double* Td, int ntab, int nr, int ld, int nch,
+                             int rows_max, float* out, cudaStream_t st) {
+    if (h->tc_kc == 16) k_tc_tables<16><<<grid, 256, 0, st>>>(Td, ntab, nr, ld, nch, rows_max, out);
+    else k_tc_tables<32><<<grid, 256, 0, st>>>(Td, ntab, nr, ld, nch, rows_max, out);
+}
 
 // M2M and L2L of each level as tensor-core products: the pairs (parent at level l, child)
 // in tiles of 128 rows with the row tables of the M2L path; op 0 (M2M) reads the children
@@ -577,9 +594,9 @@ static int build_tree_tc(fmmbem_handle* h, int nr, int rows_max, int nch) {
     FMM_CU(fmm_malloc((void**)&Td, sizeof(double) * 2 * (size_t)nr * nr));
     k_tree_ops<<<dim3(nr, 2), 128, 0, st>>>(h->opts.p_max, Td);
     FMM_LAUNCHED();
-    const size_t per_tab = (size_t)nch * 2 * rows_max * TC_KC;
+    const size_t per_tab = (size_t)nch * 2 * rows_max * h->tc_kc;
     FMM_CU(fmm_malloc((void**)&h->tree_tab_tc, sizeof(float) * 2 * per_tab));
-    k_tc_tables<<<256, 256, 0, st>>>(Td, 2, nr, nr, nch, rows_max, h->tree_tab_tc);
+    launch_tc_tables(h, 256, Td, 2, nr, nr, nch, rows_max, h->tree_tab_tc, st);
     FMM_LAUNCHED();
     std::vector<double4> cs(nc);
     std::vector<int2> ch(nc);
@@ -650,10 +667,12 @@ int build_m2l_tc(fmmbem_handle* h) {
     const int pmax = h->opts.p_max;
     const int nr = 2 * ncoef(pmax);
     const int rows_max = (nr + 15) & ~15;
-    const int nch = (nr + TC_KC - 1) / TC_KC;
-    const size_t per_tab = (size_t)nch * 2 * rows_max * TC_KC;
+    // 16-wide chunks when a pair carries four or more expansions (their stages are large)
+    h->tc_kc = h->ncomp * h->nsys >= 4 ? 16 : 32;
+    const int nch = (nr + h->tc_kc - 1) / h->tc_kc;
+    const size_t per_tab = (size_t)nch * 2 * rows_max * h->tc_kc;
     FMM_CU(fmm_malloc((void**)&h->tab_tc, sizeof(float) * per_tab * (size_t)h->n_tables));
-    k_tc_tables<<<2048, 256, 0, h->stream>>>(h->tab_d, h->n_tables, nr, h->tab_ld, nch, rows_max, h->tab_tc);
+    launch_tc_tables(h, 2048, h->tab_d, h->n_tables, nr, h->tab_ld, nch, rows_max, h->tab_tc, h->stream);
     FMM_LAUNCHED();
     h->tc_stride = per_tab;
     h->tc_rows_max = rows_max;
@@ -669,9 +688,9 @@ int build_m2l_tc(fmmbem_handle* h) {
     FMM_CU(cudaMemsetAsync(h->tc_err, 0, sizeof(int), h->stream));
     FMM_TRY(build_tree_tc(h, nr, rows_max, nch));
     size_t smax = 0;
-    for (int q = 1; q <= pmax; ++q) smax = std::max(smax, m2l_tc_smem(q));
-    FMM_CU(cudaFuncSetAttribute(k_m2l_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smax));
-    FMM_CU(cudaFuncSetAttribute(k_m2l_tc<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smax));
+    for (int q = 1; q <= pmax; ++q) smax = std::max(smax, m2l_tc_smem(h, q));
+    if (h->tc_kc == 16) FMM_CU(cudaFuncSetAttribute(k_m2l_tc<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smax));
+    else FMM_CU(cudaFuncSetAttribute(k_m2l_tc<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smax));
     int dev = 0;
     FMM_CU(cudaGetDevice(&dev));
     FMM_CU(cudaDeviceGetAttribute(&h->n_sm, cudaDevAttrMultiProcessorCount, dev));
@@ -702,13 +721,13 @@ int tree_tc(fmmbem_handle* h, int p, int level, int which) {
     const int* dst = h->tree_info + (which == 0 ? rw : 3 * rw) + (size_t)t0 * TC_ROWS;
     const int4* tiles = h->tree_tiles + (which == 0 ? 0 : h->n_tree_tiles) + t0;
     const int grid = std::min(nt, h->n_sm);
-    const size_t sm = m2l_tc_smem(p);
-    if (h->ncomp == 1)
-        k_m2l_tc<1><<<grid, TC_THREADS, sm, h->stream>>>(p, 3, tiles, nt, src, dst, h->tree_tab_tc, h->tc_stride,
-                                                        h->tc_rows_max, X, X, h->tc_err);
+    const size_t sm = m2l_tc_smem(h, p);
+    if (h->tc_kc == 16)
+        k_m2l_tc<16><<<grid, TC_THREADS, sm, h->stream>>>(p, 3, tiles, nt, src, dst, h->tree_tab_tc, h->tc_stride,
+                                                         h->tc_rows_max, X, X, h->tc_err);
     else
-        k_m2l_tc<4><<<grid, TC_THREADS, sm, h->stream>>>(p, 3, tiles, nt, src, dst, h->tree_tab_tc, h->tc_stride,
-                                                        h->tc_rows_max, X, X, h->tc_err);
+        k_m2l_tc<32><<<grid, TC_THREADS, sm, h->stream>>>(p, 3, tiles, nt, src, dst, h->tree_tab_tc, h->tc_stride,
+                                                         h->tc_rows_max, X, X, h->tc_err);
     FMM_LAUNCHED();
     return 0;
 }
@@ -717,18 +736,18 @@ int m2l_tc(fmmbem_handle* h, int p) {
     float* L = reinterpret_cast<float*>(h->L);
     const float* M = reinterpret_cast<const float*>(h->M);
     FMM_CU(cudaMemsetAsync(L, 0, sizeof(float) * h->esys * h->nsys, h->stream));
-    const size_t sm = m2l_tc_smem(p);
+    const size_t sm = m2l_tc_smem(h, p);
     const int grid = std::min(h->n_tiles_tc, h->n_sm);  // persistent: one CTA per SM (512 TMEM columns each)
     const int prods = 3;
     if (grid <= 0) return 0;
-    if (h->ncomp == 1)
-        k_m2l_tc<1><<<grid, TC_THREADS, sm, h->stream>>>(p, prods, h->m2l_tiles_tc, h->n_tiles_tc, h->tc_src_info,
-                                                        h->tc_dst_info, h->tab_tc, h->tc_stride, h->tc_rows_max, M, L,
-                                                        h->tc_err);
+    if (h->tc_kc == 16)
+        k_m2l_tc<16><<<grid, TC_THREADS, sm, h->stream>>>(p, prods, h->m2l_tiles_tc, h->n_tiles_tc, h->tc_src_info,
+                                                         h->tc_dst_info, h->tab_tc, h->tc_stride, h->tc_rows_max, M, L,
+                                                         h->tc_err);
     else
-        k_m2l_tc<4><<<grid, TC_THREADS, sm, h->stream>>>(p, prods, h->m2l_tiles_tc, h->n_tiles_tc, h->tc_src_info,
-                                                        h->tc_dst_info, h->tab_tc, h->tc_stride, h->tc_rows_max, M, L,
-                                                        h->tc_err);
+        k_m2l_tc<32><<<grid, TC_THREADS, sm, h->stream>>>(p, prods, h->m2l_tiles_tc, h->n_tiles_tc, h->tc_src_info,
+                                                         h->tc_dst_info, h->tab_tc, h->tc_stride, h->tc_rows_max, M, L,
+                                                         h->tc_err);
     FMM_LAUNCHED();
     return 0;
 }

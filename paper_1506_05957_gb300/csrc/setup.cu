@@ -7,7 +7,6 @@
 //   the near-singular search (|c_i - c_j| < f sqrt(2 S_j)) and the FP64 correction
 //   table: 20-point rule minus K-point rule for near panels, the semi-analytic
 //   integral for the self panel (Sec. 2.3, Hess-Smith decomposition).
-#include <cub/cub.cuh>
 #include <algorithm>
 #include <cstring>
 #include <vector>
@@ -625,18 +624,14 @@ int sort_pairs_to_csr(fmmbem_handle* h, int2* pairs, long long n, int** ptr_out,
     if (n > 0) { k_pack_pairs<<<(unsigned)((n + T - 1) / T), T, 0, st>>>(pairs, n, nc, k1); FMM_LAUNCHED(); }
     int end_bit = 1;
     while (end_bit < 64 && ((unsigned long long)nc * (unsigned long long)nc >> end_bit) != 0) ++end_bit;
-    size_t tb = 0;
-    FMM_CU(cub::DeviceRadixSort::SortKeys(nullptr, tb, k1, k2, (int)n, 0, end_bit, st));
-    void* tmp = nullptr;
-    FMM_CU(fmm_malloc(&tmp, tb ? tb : 1));
-    FMM_CU(cub::DeviceRadixSort::SortKeys(tmp, tb, k1, k2, (int)n, 0, end_bit, st));
+    FMM_TRY(radix_sort(reinterpret_cast<const uint64_t*>(k1), reinterpret_cast<uint64_t*>(k2), nullptr, nullptr, n,
+                       end_bit, st));
     FMM_TRY(dalloc(ptr_out, nc + 1));
     FMM_TRY(dalloc(src_out, n));
     k_csr_ptr<<<(unsigned)((nc + 1 + T - 1) / T), T, 0, st>>>(k2, n, nc, *ptr_out);
     FMM_LAUNCHED();
     if (n > 0) { k_unpack_src<<<(unsigned)((n + T - 1) / T), T, 0, st>>>(k2, n, nc, *src_out); FMM_LAUNCHED(); }
     FMM_CU(cudaStreamSynchronize(st));
-    fmm_free(tmp);
     fmm_free(k1);
     fmm_free(k2);
     return 0;
@@ -723,15 +718,7 @@ int build_geometry_tree_lists(fmmbem_handle* h, const fmmbem_mesh* mesh) {
     k_morton<<<gn, T, 0, st>>>(cen, n, h->origin[0] - h->half, h->origin[1] - h->half, h->origin[2] - h->half,
                                2.0 * h->half, key, idx);
     FMM_LAUNCHED();
-    {
-        size_t tb = 0;
-        FMM_CU(cub::DeviceRadixSort::SortPairs(nullptr, tb, key, key_s, idx, h->perm, (int)n, 0, 63, st));
-        void* tmp = nullptr;
-        FMM_CU(fmm_malloc(&tmp, tb ? tb : 1));
-        FMM_CU(cub::DeviceRadixSort::SortPairs(tmp, tb, key, key_s, idx, h->perm, (int)n, 0, 63, st));
-        FMM_CU(cudaStreamSynchronize(st));
-        fmm_free(tmp);
-    }
+    FMM_TRY(radix_sort(key, key_s, idx, h->perm, n, 63, st));
 
     FMM_TRY(dalloc(&h->tgt_d, n));
     FMM_TRY(dalloc(&h->tgt_f, n));
@@ -770,25 +757,20 @@ int build_geometry_tree_lists(fmmbem_handle* h, const fmmbem_mesh* mesh) {
         FMM_CU(cudaMemcpyAsync(parent, &minus1, sizeof(int), cudaMemcpyHostToDevice, st));
         h->level_start.assign(1, 0);
         int lb = 0, le = 1, level = 0;
-        void* scan_tmp = nullptr;
-        size_t scan_tb = 0;
         long long scan_cap = 0;
         while (le > lb) {
             h->level_start.push_back(le);
             const int nl = le - lb;
             if (nl > scan_cap) {
-                if (nch) { fmm_free(nch); fmm_free(off); fmm_free(bounds); fmm_free(scan_tmp); }
+                if (nch) { fmm_free(nch); fmm_free(off); fmm_free(bounds); }
                 scan_cap = std::max<long long>(2 * nl, 1024);
                 FMM_TRY(dalloc(&nch, scan_cap));
                 FMM_TRY(dalloc(&off, scan_cap));
                 FMM_TRY(dalloc(&bounds, 9 * scan_cap));
-                scan_tb = 0;
-                FMM_CU(cub::DeviceScan::ExclusiveSum(nullptr, scan_tb, nch, off, (int)scan_cap, st));
-                FMM_CU(fmm_malloc(&scan_tmp, scan_tb ? scan_tb : 1));
             }
             k_split_count<<<(nl + T - 1) / T, T, 0, st>>>(lb, le, level, range, key_s, K, h->ncrit, nch, bounds);
             FMM_LAUNCHED();
-            FMM_CU(cub::DeviceScan::ExclusiveSum(scan_tmp, scan_tb, nch, off, nl, st));
+            FMM_TRY(exclusive_scan(nch, off, nl, st));
             int last[2];
             FMM_CU(cudaMemcpyAsync(&last[0], off + nl - 1, sizeof(int), cudaMemcpyDeviceToHost, st));
             FMM_CU(cudaMemcpyAsync(&last[1], nch + nl - 1, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -817,7 +799,7 @@ int build_geometry_tree_lists(fmmbem_handle* h, const fmmbem_mesh* mesh) {
             ++level;
         }
         FMM_CU(cudaStreamSynchronize(st));
-        fmm_free(nch); fmm_free(off); fmm_free(bounds); fmm_free(scan_tmp);
+        fmm_free(nch); fmm_free(off); fmm_free(bounds);
         h->n_cells = le;
         h->n_levels = level;  // level_start has n_levels + 1 entries
         h->cell_cs = cs; h->cell_range = range; h->cell_child = child; h->cell_level = clevel; h->cell_parent = parent;
@@ -856,13 +838,10 @@ int build_geometry_tree_lists(fmmbem_handle* h, const fmmbem_mesh* mesh) {
         // deterministic leaf order (ascending cell id)
         int* ls = nullptr;
         FMM_TRY(dalloc(&ls, h->n_leaves));
-        size_t tb = 0;
-        FMM_CU(cub::DeviceRadixSort::SortKeys(nullptr, tb, h->leaves, ls, h->n_leaves, 0, 32, st));
-        void* tmp = nullptr;
-        FMM_CU(fmm_malloc(&tmp, tb ? tb : 1));
-        FMM_CU(cub::DeviceRadixSort::SortKeys(tmp, tb, h->leaves, ls, h->n_leaves, 0, 32, st));
+        // cell ids are non-negative, so their unsigned order is their order
+        FMM_TRY(radix_sort(reinterpret_cast<const uint32_t*>(h->leaves), reinterpret_cast<uint32_t*>(ls), nullptr,
+                           nullptr, h->n_leaves, 32, st));
         FMM_CU(cudaStreamSynchronize(st));
-        fmm_free(tmp);
         fmm_free(h->leaves);
         h->leaves = ls;
         // leaves ordered by target-count class for the near-field kernels
@@ -875,15 +854,12 @@ int build_geometry_tree_lists(fmmbem_handle* h, const fmmbem_mesh* mesh) {
             FMM_CU(cudaMemsetAsync(counts, 0, 3 * sizeof(int), st));
             k_leaf_class_key<<<(h->n_leaves + T - 1) / T, T, 0, st>>>(h->leaves, h->cell_range, h->n_leaves, ckey, counts);
             FMM_LAUNCHED();
-            size_t tb2 = 0;
-            FMM_CU(cub::DeviceRadixSort::SortPairs(nullptr, tb2, ckey, ckey_s, h->leaves, h->leaf_class, h->n_leaves, 0, 2, st));
-            void* tmp2 = nullptr;
-            FMM_CU(fmm_malloc(&tmp2, tb2 ? tb2 : 1));
-            FMM_CU(cub::DeviceRadixSort::SortPairs(tmp2, tb2, ckey, ckey_s, h->leaves, h->leaf_class, h->n_leaves, 0, 2, st));
+            FMM_TRY(radix_sort(reinterpret_cast<const uint32_t*>(ckey), reinterpret_cast<uint32_t*>(ckey_s), h->leaves,
+                               h->leaf_class, h->n_leaves, 2, st));
             int c_h[3];
             FMM_CU(cudaMemcpyAsync(c_h, counts, sizeof(c_h), cudaMemcpyDeviceToHost, st));
             FMM_CU(cudaStreamSynchronize(st));
-            fmm_free(tmp2); fmm_free(ckey); fmm_free(ckey_s); fmm_free(counts);
+            fmm_free(ckey); fmm_free(ckey_s); fmm_free(counts);
             h->leaf_class_start[0] = 0;
             h->leaf_class_start[1] = c_h[0];
             h->leaf_class_start[2] = c_h[0] + c_h[1];
@@ -1035,15 +1011,10 @@ int build_geometry_tree_lists(fmmbem_handle* h, const fmmbem_mesh* mesh) {
                                                             nullptr, nullptr, nullptr, nullptr, nullptr);
             FMM_LAUNCHED();
             FMM_TRY(dalloc(&h->stage_ptr, nc + 1));
-            size_t tb3 = 0;
-            FMM_CU(cub::DeviceScan::ExclusiveSum(nullptr, tb3, nst, h->stage_ptr, nc + 1, st));
-            void* tmp3 = nullptr;
-            FMM_CU(fmm_malloc(&tmp3, tb3 ? tb3 : 1));
-            FMM_CU(cub::DeviceScan::ExclusiveSum(tmp3, tb3, nst, h->stage_ptr, nc + 1, st));
+            FMM_TRY(exclusive_scan(nst, h->stage_ptr, nc + 1, st));
             int nstages = 0;
             FMM_CU(cudaMemcpyAsync(&nstages, h->stage_ptr + nc, sizeof(int), cudaMemcpyDeviceToHost, st));
             FMM_CU(cudaStreamSynchronize(st));
-            fmm_free(tmp3);
             fmm_free(nst);
             h->n_stages = nstages;
             FMM_TRY(dalloc(&h->stage_first, nstages));
@@ -1068,15 +1039,10 @@ int build_geometry_tree_lists(fmmbem_handle* h, const fmmbem_mesh* mesh) {
                                                count, nullptr, nullptr, nullptr);
         FMM_LAUNCHED();
         FMM_TRY(dalloc(&h->corr_ptr, n + 1));
-        size_t tb = 0;
-        FMM_CU(cub::DeviceScan::ExclusiveSum(nullptr, tb, count, h->corr_ptr, (int)(n + 1), st));
-        void* tmp = nullptr;
-        FMM_CU(fmm_malloc(&tmp, tb ? tb : 1));
-        FMM_CU(cub::DeviceScan::ExclusiveSum(tmp, tb, count, h->corr_ptr, (int)(n + 1), st));
+        FMM_TRY(exclusive_scan(count, h->corr_ptr, n + 1, st));
         int nnz = 0;
         FMM_CU(cudaMemcpyAsync(&nnz, h->corr_ptr + n, sizeof(int), cudaMemcpyDeviceToHost, st));
         FMM_CU(cudaStreamSynchronize(st));
-        fmm_free(tmp);
         h->n_corr = nnz;
         int* row = nullptr;
         FMM_TRY(dalloc(&row, nnz));
