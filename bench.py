@@ -1036,7 +1036,11 @@ def run_serve(args, world, rank, local):
            "mean_queue_s": float(np.mean([i["queue_s"] for i, _ in res])),
            "mean_setup_s": float(np.mean([i["setup_s"] for i, _ in res])),
            "mean_solve_s": float(np.mean([i["solve_s"] for i, _ in res])),
-           "panels": {"min": int(min(len(r["t"]) for _, r in res)), "max": int(max(len(r["t"]) for _, r in res))}}
+           "panels": {"min": int(min(len(r["t"]) for _, r in res)), "max": int(max(len(r["t"]) for _, r in res))},
+           "requests_detail": [{"shape": r["shape"], "kernel": r["kernel"], "panels": int(len(r["t"])), "tol": r["tol"],
+                                "status": int(i["status"]), "iters": int(i["iters"]), "true_res": float(i["true_res"]),
+                                "setup_s": round(float(i["setup_s"]), 4), "solve_s": round(float(i["solve_s"]), 4),
+                                "latency_s": round(float(i["latency_s"]), 4)} for i, r in res]}
     if rank == 0:
         print(json.dumps(out), flush=True)
 

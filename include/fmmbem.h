@@ -117,7 +117,9 @@ int fmmbem_default_opts(fmmbem_opts* opts);
  * acceptance criterion (R_a + R_b) < theta |c_a - c_b| (c = box centre; R_a = the
  * largest distance from c_a to a collocation point of the target cell a, R_b = the
  * largest distance from c_b to a Gauss point of the source cell b: the cluster
- * sizes of eq. multipole_error), and the sparse table of near-singular and
+ * sizes of eq. multipole_error) together with |c_a - c_b| >= the larger cell's side
+ * (which keeps the FP32 translation operators in range at p <= 16; a closed surface mesh
+ * meets it whenever the first condition holds), and the sparse table of near-singular and
  * self-panel corrections (accurate integral minus the K-point sum), in FP64.
  *   mesh      : host mesh (see fmmbem_mesh)
  *   kernel    : FMMBEM_LAPLACE or FMMBEM_STOKES

@@ -607,36 +607,40 @@ __global__ void __launch_bounds__(TREE_THREADS) k_m2m(int p, const int* parents,
 // t = c_target - c_source, rho = s_source / s_target (a power of two).
 // One thread per output coefficient (j, k); the irregular table of each pair is
 // built in shared memory, one column per thread.
+// The gather form computes in FP64 whatever the storage type T: its irregular harmonics reach
+// degree 2p, and their magnitudes ((n - m)! P_n^m / r^(n+1), n up to 32) leave the FP32 range
+// for offsets of about one cell side and below. It is the fallback of trees whose operators
+// are not tabulated, so its speed matters less than its range.
 template <typename T, int NC>
 __global__ void k_m2l(int p, const int* ptr, const int* srcl, const double4* cs, const T* M, T* L, size_t msys) {
     M += blockIdx.y * msys;  // copy blockIdx.y of a Stokes batch
     L += blockIdx.y * msys;
-    __shared__ T sI[NI_MAX * 2];
-    __shared__ T sM[NC * NCOEF_MAX * 2];
+    __shared__ double sI[NI_MAX * 2];
+    __shared__ double sM[NC * NCOEF_MAX * 2];
     const int tc = blockIdx.x;
     const int nco = ncoef(p);
     const int t = threadIdx.x;
     int j = 0, k = 0;
     if (t < nco) decode(t, j, k);
     const double4 ct = cs[tc];
-    cpx<T> acc[NC];
+    cpx<double> acc[NC];
 #pragma unroll
-    for (int c = 0; c < NC; ++c) acc[c] = mk(T(0), T(0));
+    for (int c = 0; c < NC; ++c) acc[c] = mk(0.0, 0.0);
     const int e0 = ptr[tc], e1 = ptr[tc + 1];
     for (int e = e0; e < e1; ++e) {
         const int sc = srcl[e];
         const double4 cv = cs[sc];
         const double is = 1.0 / ct.w;
-        const T vx = T((ct.x - cv.x) * is), vy = T((ct.y - cv.y) * is), vz = T((ct.z - cv.z) * is);
+        const double vx = (ct.x - cv.x) * is, vy = (ct.y - cv.y) * is, vz = (ct.z - cv.z) * is;
         const int dl = ilogb(cv.w * is);  // log2(rho), exact for cells of the same tree
         __syncthreads();
-        if (t <= 2 * p) irregular_column<T>(vx, vy, vz, t, 2 * p, reinterpret_cast<cpx<T>*>(sI));
+        if (t <= 2 * p) irregular_column<double>(vx, vy, vz, t, 2 * p, reinterpret_cast<cpx<double>*>(sI));
         const T* Ms = M + (size_t)sc * NC * ESTRIDE;
         for (int idx = t; idx < NC * nco; idx += blockDim.x) {
             const int c = idx / nco, q = idx % nco;
-            const T f = (dl == 0) ? T(1) : T(ldexp(1.0, dl * (int)c_deg[q]));
-            sM[(c * NCOEF_MAX + q) * 2] = f * Ms[c * ESTRIDE + 2 * q];
-            sM[(c * NCOEF_MAX + q) * 2 + 1] = f * Ms[c * ESTRIDE + 2 * q + 1];
+            const double f = (dl == 0) ? 1.0 : ldexp(1.0, dl * (int)c_deg[q]);
+            sM[(c * NCOEF_MAX + q) * 2] = f * (double)Ms[c * ESTRIDE + 2 * q];
+            sM[(c * NCOEF_MAX + q) * 2 + 1] = f * (double)Ms[c * ESTRIDE + 2 * q + 1];
         }
         __syncthreads();
         if (t < nco) {
@@ -645,24 +649,24 @@ __global__ void k_m2l(int p, const int* ptr, const int* srcl, const double4* cs,
                 const int base = cidx(n, 0);
                 // m >= 0: M_n^m I_{n+j}^{m+k}
                 for (int m = 0; m <= n; ++m) {
-                    const cpx<T> I = ld(sI, cidx(nj, m + k));
+                    const cpx<double> I = ld(sI, cidx(nj, m + k));
 #pragma unroll
                     for (int c = 0; c < NC; ++c) cfma(acc[c], ld(sM + c * NCOEF_MAX * 2, base + m), I);
                 }
                 // m = -mu, 1 <= mu <= min(n, k): (-1)^mu conj(M_n^mu) I_{n+j}^{k-mu}
                 const int mk1 = min(n, k);
                 for (int mu = 1; mu <= mk1; ++mu) {
-                    cpx<T> I = ld(sI, cidx(nj, k - mu));
+                    cpx<double> I = ld(sI, cidx(nj, k - mu));
                     if (mu & 1) I = mk(-I.re, -I.im);
 #pragma unroll
                     for (int c = 0; c < NC; ++c) cfma_conja(acc[c], ld(sM + c * NCOEF_MAX * 2, base + mu), I);
                 }
                 // m = -mu, k < mu <= n: (-1)^k conj(M_n^mu I_{n+j}^{mu-k})
                 for (int mu = k + 1; mu <= n; ++mu) {
-                    const cpx<T> I = ld(sI, cidx(nj, mu - k));
+                    const cpx<double> I = ld(sI, cidx(nj, mu - k));
 #pragma unroll
                     for (int c = 0; c < NC; ++c) {
-                        const cpx<T> v = ld(sM + c * NCOEF_MAX * 2, base + mu) * I;
+                        const cpx<double> v = ld(sM + c * NCOEF_MAX * 2, base + mu) * I;
                         if (k & 1) { acc[c].re -= v.re; acc[c].im += v.im; }
                         else { acc[c].re += v.re; acc[c].im -= v.im; }
                     }
@@ -674,9 +678,9 @@ __global__ void k_m2l(int p, const int* ptr, const int* srcl, const double4* cs,
         T* out = L + (size_t)tc * NC * ESTRIDE;
 #pragma unroll
         for (int c = 0; c < NC; ++c) {
-            cpx<T> v = conj(acc[c]);
+            cpx<double> v = conj(acc[c]);
             if (j & 1) v = mk(-v.re, -v.im);
-            st(out + c * ESTRIDE, t, v);
+            st(out + c * ESTRIDE, t, mk(T(v.re), T(v.im)));
         }
     }
 }

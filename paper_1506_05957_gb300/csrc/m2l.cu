@@ -5,7 +5,7 @@
 // rho = s_s / s_t = 2^dl:
 //   L^_j^k = (-1)^j conj( sum_{n,m} rho^n M~_n^m I_{n+j}^{m+k}(v) )
 // (Sec. 2.5; the complex form is derived in harmonics.cuh). For cells of one octree v
-// is a multiple of 1/16 for |dl| <= 3, so every pair of the dual-tree traversal maps to
+// is a multiple of 1/256 for dl >= -7, so every pair of the dual-tree traversal maps to
 // one of a few thousand distinct operators. Each operator is stored once as a real
 // matrix acting on the interleaved (Re, Im) coefficients, ordered by degree so that the
 // leading 2 ncoef(p) x 2 ncoef(p) block is the order-p operator for every p <= p_max.
@@ -24,8 +24,13 @@ namespace fmmbem {
 
 namespace {
 
-constexpr int KEY_BITS = 11;          // per coordinate, 16 v + 1024 in [0, 2048)
+// Operator key: 4 bits of level difference dl + 8 (dl in [-8, 7]) above three coordinates of
+// KEY_BITS bits, each KEY_RES v + KEY_BIAS. A centre offset is a multiple of 2^(dl - 1) target
+// sides when the source is the smaller cell (dl < 0) and of 1/2 otherwise, so a resolution of
+// 1/256 represents every offset exactly for dl >= -7, up to |v| < 2048.
+constexpr int KEY_BITS = 20;
 constexpr int KEY_BIAS = 1 << (KEY_BITS - 1);
+constexpr double KEY_RES = 256.0;
 constexpr int GEMM_THREADS = 256;     // 16 x 16 threads
 constexpr int GEMM_COLS = 64;         // (pair, component) columns per tile
 constexpr int GEMM_KC = 16;           // inputs per shared-memory stage
@@ -59,13 +64,13 @@ __global__ void k_pair_keys(const int* pt, const int* ps, long long n, const dou
     const int t = pt[i], s = ps[i];
     const double4 ct = cs[t], cv = cs[s];
     const int dl = lev[t] - lev[s];
-    const double is = 16.0 / ct.w;
+    const double is = KEY_RES / ct.w;
     long long kx = llrint((ct.x - cv.x) * is), ky = llrint((ct.y - cv.y) * is), kz = llrint((ct.z - cv.z) * is);
     const int q = (kx < 0 ? 1 : 0) | (ky < 0 ? 2 : 0) | (kz < 0 ? 4 : 0);  // reflection to the canonical octant
     kx = llabs(kx);
     ky = llabs(ky);
     kz = llabs(kz);
-    if (dl < -3 || dl > 3 || kx >= KEY_BIAS || ky >= KEY_BIAS || kz >= KEY_BIAS) atomicExch(bad, 1);
+    if (dl < -7 || dl > 7 || kx >= KEY_BIAS || ky >= KEY_BIAS || kz >= KEY_BIAS) atomicExch(bad, 1);
     key[i] = ((unsigned long long)(dl + 8) << (3 * KEY_BITS)) | ((unsigned long long)(kx + KEY_BIAS) << (2 * KEY_BITS)) |
              ((unsigned long long)(ky + KEY_BIAS) << KEY_BITS) | (unsigned long long)(kz + KEY_BIAS);
     idx[i] = (int)i;
@@ -119,9 +124,9 @@ __global__ void k_gen_tables(const unsigned long long* tab_key, int pmax, int ld
     const unsigned long long key = tab_key[g];
     const int mask = (1 << KEY_BITS) - 1;
     const int dl = (int)(key >> (3 * KEY_BITS)) - 8;
-    const double vx = ((int)((key >> (2 * KEY_BITS)) & mask) - KEY_BIAS) / 16.0;
-    const double vy = ((int)((key >> KEY_BITS) & mask) - KEY_BIAS) / 16.0;
-    const double vz = ((int)(key & mask) - KEY_BIAS) / 16.0;
+    const double vx = ((int)((key >> (2 * KEY_BITS)) & mask) - KEY_BIAS) / KEY_RES;
+    const double vy = ((int)((key >> KEY_BITS) & mask) - KEY_BIAS) / KEY_RES;
+    const double vz = ((int)(key & mask) - KEY_BIAS) / KEY_RES;
     if (threadIdx.x <= 2 * pmax) irregular_column<double>(vx, vy, vz, threadIdx.x, 2 * pmax, sI);
     __syncthreads();
     const int nr = 2 * ncoef(pmax);

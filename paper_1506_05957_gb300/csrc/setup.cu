@@ -271,19 +271,26 @@ __global__ void k_split_emit(int lb, int le, int next_start, int level, const in
 // Cluster radii of every cell about its box centre: .x = the farthest collocation point
 // (targets), .y = the farthest Gauss point (sources). The MAC uses them as the cluster
 // sizes, the a of eq. multipole_error.
+// Each cell's range is cut into gridDim.y slices; each block reduces the squared distances of
+// its slice and raises the cell's maximum with an integer max on the bit patterns (squared
+// distances are non-negative, and non-negative doubles order like their bits). rad2 must
+// be zero on entry; k_cell_radii_sqrt then takes the square roots.
 __global__ void k_cell_radii(int ncells, const double4* cs, const int2* range, const double4* tgt, const double4* src,
-                             int K, double2* rad) {
+                             int K, unsigned long long* rad2) {
     __shared__ double st[128], ss[128];
     const int c = blockIdx.x;
     if (c >= ncells) return;
     const double4 cc = cs[c];
     const int2 r = range[c];
+    const int nsl = (int)gridDim.y, sl = (int)blockIdx.y;
     double mt = 0.0, ms = 0.0;
-    for (int i = r.x + threadIdx.x; i < r.y; i += blockDim.x) {
+    const int nt = r.y - r.x, t0 = r.x + (int)((long long)nt * sl / nsl), t1 = r.x + (int)((long long)nt * (sl + 1) / nsl);
+    for (int i = t0 + threadIdx.x; i < t1; i += blockDim.x) {
         const double4 t = tgt[i];
         mt = fmax(mt, (t.x - cc.x) * (t.x - cc.x) + (t.y - cc.y) * (t.y - cc.y) + (t.z - cc.z) * (t.z - cc.z));
     }
-    for (int g = r.x * K + threadIdx.x; g < r.y * K; g += blockDim.x) {
+    const int ns = nt * K, g0 = r.x * K + (int)((long long)ns * sl / nsl), g1 = r.x * K + (int)((long long)ns * (sl + 1) / nsl);
+    for (int g = g0 + threadIdx.x; g < g1; g += blockDim.x) {
         const double4 y = src[g];
         ms = fmax(ms, (y.x - cc.x) * (y.x - cc.x) + (y.y - cc.y) * (y.y - cc.y) + (y.z - cc.z) * (y.z - cc.z));
     }
@@ -297,7 +304,17 @@ __global__ void k_cell_radii(int ncells, const double4* cs, const int2* range, c
         }
         __syncthreads();
     }
-    if (threadIdx.x == 0) rad[c] = make_double2(sqrt(st[0]), sqrt(ss[0]));
+    if (threadIdx.x == 0) {
+        atomicMax(rad2 + 2 * c, (unsigned long long)__double_as_longlong(st[0]));
+        atomicMax(rad2 + 2 * c + 1, (unsigned long long)__double_as_longlong(ss[0]));
+    }
+}
+
+__global__ void k_cell_radii_sqrt(int ncells, const unsigned long long* rad2, double2* rad) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ncells) return;
+    rad[c] = make_double2(sqrt(__longlong_as_double((long long)rad2[2 * c])),
+                          sqrt(__longlong_as_double((long long)rad2[2 * c + 1])));
 }
 
 // ---------------------------------------------------------------- dual-tree traversal
@@ -315,7 +332,13 @@ __global__ void k_dtt_round(const int2* in, int n_in, const double4* cs, const i
     const double Ra = rad[a].x, Rb = rad[b].y;
     const double dx = ca.x - cb.x, dy = ca.y - cb.y, dz = ca.z - cb.z;
     const double d = sqrt(dx * dx + dy * dy + dz * dz);
-    if (Ra + Rb < theta * d) {
+    // the multipole acceptance criterion with the cluster radii, and centres at least the
+    // larger cell's side apart: the translation operator's entries grow like
+    // rho^n (n + j)! / |v|^(n + j + 1) with v the offset in units of the target's side, and
+    // a coarse cell holding a small piece of surface could otherwise pass with |v| << 1 and
+    // carry entries beyond the FP32 range at p = 16 (on a closed surface mesh the cluster
+    // radii already keep |v| above 2)
+    if (Ra + Rb < theta * d && d >= fmax(ca.w, cb.w)) {
         unsigned long long k = atomicAdd(&cnt[0], 1ULL);
         if ((long long)k < cap_m2l) m2l[k] = make_int2(a, b); else atomicExch(overflow, 1);
         return;
@@ -563,17 +586,19 @@ __device__ void rule_sums(const double* P, const double4 nj, const double* c, co
         double d[3];
         for (int x = 0; x < 3; ++x) d[x] = c[x] - (g[0] * P[x] + g[1] * P[3 + x] + g[2] * P[6 + x]);
         const double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
-        const double r = sqrt(r2);
+        // one FP64 reciprocal square root per point instead of a square root and divisions
+        // (FP64 throughput is scarce on this GPU); rsqrt is within 1 ulp
+        const double ir = rsqrt(r2), ir2 = ir * ir, ir3 = ir2 * ir;
         const double w = g[3] * nj.w;
         const double dn = d[0] * nj.x + d[1] * nj.y + d[2] * nj.z;
         if (!stokes) {
-            sl[0] += w / r;
-            dl[0] += w * dn / (r2 * r);
+            sl[0] += w * ir;
+            dl[0] += w * dn * ir3;
         } else {
-            const double ir3 = 1.0 / (r2 * r), ir5 = ir3 / r2;
+            const double ir5 = ir3 * ir2;
             for (int x = 0; x < 3; ++x)
                 for (int y = 0; y < 3; ++y) {
-                    sl[3 * x + y] += w * ((x == y ? 1.0 / r : 0.0) + d[x] * d[y] * ir3);
+                    sl[3 * x + y] += w * ((x == y ? ir : 0.0) + d[x] * d[y] * ir3);
                     dl[3 * x + y] += w * 6.0 * d[x] * d[y] * (-dn) * ir5;
                 }
         }
@@ -877,8 +902,16 @@ int build_geometry_tree_lists(fmmbem_handle* h, const fmmbem_mesh* mesh) {
     // ---- dual-tree traversal
     {
         FMM_TRY(dalloc(&h->cell_rad, nc));
-        k_cell_radii<<<nc, 128, 0, st>>>(nc, h->cell_cs, h->cell_range, h->tgt_d, h->src_d, K, h->cell_rad);
-        FMM_LAUNCHED();
+        {
+            unsigned long long* rad2 = nullptr;
+            FMM_TRY(dalloc(&rad2, 2 * (size_t)nc));
+            FMM_CU(cudaMemsetAsync(rad2, 0, sizeof(unsigned long long) * 2 * nc, st));
+            k_cell_radii<<<dim3(nc, 16), 128, 0, st>>>(nc, h->cell_cs, h->cell_range, h->tgt_d, h->src_d, K, rad2);
+            FMM_LAUNCHED();
+            k_cell_radii_sqrt<<<(nc + T - 1) / T, T, 0, st>>>(nc, rad2, h->cell_rad);
+            FMM_LAUNCHED();
+            fmm_free(rad2);
+        }
         long long cap_m2l = std::max<long long>(1024, 256LL * nc), cap_p2p = std::max<long long>(1024, 64LL * nc);
         long long cap_f = std::max<long long>(4096, 64LL * nc);
         int2 *m2l = nullptr, *p2p = nullptr, *fa = nullptr, *fb = nullptr;

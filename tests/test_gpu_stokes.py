@@ -106,3 +106,39 @@ def test_stokes_relaxed_solve_drag(torch_cuda, sphere):
     x2 = torch.zeros_like(b)
     r2 = h.solve(b, x2, tol=tol, relax=False, p_initial=16, p_min=4)
     assert abs(r["iters"] - r2["iters"]) <= 2
+
+
+def test_cell_cluster_high_order_stays_finite():
+    """Clusters of red-blood-cell surfaces in a large box leave coarse cells that hold a small
+    piece of surface: with the cluster radii alone such a cell could be accepted for M2L with a
+    centre offset much smaller than its side, and the FP32 translation operators of degree up
+    to 2p = 32 overflowed (NaN mat-vecs at p = 16 on these two placements). The acceptance
+    criterion also asks for centres at least the larger side apart: the p = 16 mat-vecs are
+    finite and match the oracle's Stokeslet rows, and the relaxed solves converge."""
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1506_05957_gb300 import build, FmmBem, FMMBEM_MIXED, FMMBEM_STOKES
+    build.build()
+    from oracle import dense
+    from synth import evans_fung_cell, place_cells
+    cv, ct = evans_fung_cell(4)
+    for n_cells, seed in ((4, 1016323256), (16, 995813860)):
+        v, t, _ = place_cells(cv, ct, n_cells, box=40.0, min_gap=0.5, seed=seed)
+        h = FmmBem(v, t, kernel=FMMBEM_STOKES, gauss_k=3, ncrit=150, theta=0.5, p_max=16, precision=FMMBEM_MIXED)
+        x = np.random.default_rng(seed % 1000).standard_normal(h.n)
+        xd = torch.tensor(x, dtype=torch.float64, device="cuda")
+        y = torch.zeros_like(xd)
+        h.matvec(16, xd, y)
+        h.check_waits()
+        got = y.cpu().numpy()
+        assert np.all(np.isfinite(got))
+        rows = np.sort(np.random.default_rng(3).choice(len(t), 48, replace=False))
+        ref = dense.Mesh(v, t, k=3).stokes_apply(x, rows=rows).reshape(-1)
+        g = got.reshape(-1, 3)[rows].reshape(-1)
+        assert np.linalg.norm(g - ref) / np.linalg.norm(ref) < 1e-5
+        b = torch.tensor(np.tile([1.0, 0.0, 0.0], len(t)), dtype=torch.float64, device="cuda")
+        sol = torch.zeros_like(b)
+        r = h.solve(b, sol, tol=1e-6, relax=True, p_initial=16, p_min=4)
+        assert r["converged"] and np.isfinite(r["true_res"]) and r["true_res"] < 2e-6
+        h.close()
