@@ -59,6 +59,13 @@ extern "C" {
 #define FMMBEM_FP64 0        /* every pass in FP64 */
 #define FMMBEM_MIXED 1       /* P2M/M2M/M2L/L2L/L2P and P2P in FP32 with FP64 tile sums;
                                 singular/near-singular corrections and the output in FP64 */
+#define FMMBEM_MIXED_REFINED 2 /* solves: iterative refinement with FP64 residuals around the
+                                relaxed FMMBEM_MIXED GMRES, for tolerances below what FP32 passes
+                                resolve (about 1e-6): each outer step solves A d = r with mixed
+                                mat-vecs to a relative 1e-5 (or the final tolerance if looser),
+                                adds d to x and recomputes r = b - A x with an FP64 mat-vec at
+                                p_initial, until ||r|| / ||b|| <= tol. Mat-vecs run as FMMBEM_MIXED.
+                                Single-vector handles only. */
 
 /* Largest supported expansion order (degrees n = 0..p, (p+1)(p+2)/2 complex
  * coefficients per expansion). */
@@ -282,6 +289,9 @@ int fmmbem_relaxed_p(double eta, double rho_prev, int p_initial, int p_min);
  *   p_hist    : out, [opts.max_iter] ints, host, p used at each step (may be NULL)
  *   res_hist  : out, [opts.max_iter + 1] doubles, host, rho_0 = 1, rho_1.. (may be NULL)
  *   true_res  : out, ||b - A_{p_initial} x|| / ||b|| after the solve (may be NULL)
+ * With FMMBEM_MIXED_REFINED, iters, p_hist and res_hist count the inner (mixed) Arnoldi steps
+ * of all outer steps in order; the entry of res_hist after an outer step's last inner step is
+ * that step's FP64 residual, and true_res the last one.
  * Returns 0 (converged), FMMBEM_NOT_CONVERGED, or a negative error.
  */
 int fmmbem_solve(fmmbem_handle* h, const double* rhs_dev, double tol, int relax, int p_initial,

@@ -5,9 +5,9 @@ include/fmmbem.h); this package only builds and binds it.
 """
 from .binding import (FmmBem, FmmBemError, FmmBemServer, fmmbem_default_opts, fmmbem_estimate_bytes,
                       fmmbem_expansion_eval, fmmbem_relaxed_p, lib, FMMBEM_LAPLACE, FMMBEM_STOKES, FMMBEM_FP64,
-                      FMMBEM_MIXED, FMMBEM_P_MAX, FMMBEM_LAYER_SINGLE, FMMBEM_LAYER_DOUBLE)
+                      FMMBEM_MIXED, FMMBEM_MIXED_REFINED, FMMBEM_P_MAX, FMMBEM_LAYER_SINGLE, FMMBEM_LAYER_DOUBLE)
 
 __all__ = ["FmmBem", "FmmBemError", "FmmBemServer", "fmmbem_default_opts", "fmmbem_estimate_bytes",
            "fmmbem_expansion_eval", "fmmbem_relaxed_p", "lib",
-           "FMMBEM_LAPLACE", "FMMBEM_STOKES", "FMMBEM_FP64", "FMMBEM_MIXED", "FMMBEM_P_MAX",
+           "FMMBEM_LAPLACE", "FMMBEM_STOKES", "FMMBEM_FP64", "FMMBEM_MIXED", "FMMBEM_MIXED_REFINED", "FMMBEM_P_MAX",
            "FMMBEM_LAYER_SINGLE", "FMMBEM_LAYER_DOUBLE"]

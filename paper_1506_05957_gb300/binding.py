@@ -25,6 +25,7 @@ FMMBEM_LAPLACE = 0
 FMMBEM_STOKES = 1
 FMMBEM_FP64 = 0
 FMMBEM_MIXED = 1
+FMMBEM_MIXED_REFINED = 2
 FMMBEM_P_MAX = 16
 FMMBEM_M2L_TABLES = 0
 FMMBEM_M2L_GATHER = 1

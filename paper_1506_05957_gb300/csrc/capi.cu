@@ -214,7 +214,7 @@ void prof_harvest(fmmbem_handle* h) {
 // kernel: 2 (p+1)^4 per M2L pair and expansion, the same per M2M and per L2L translation
 // (one per non-root cell).
 static double tc_flops(const fmmbem_handle* h, int p) {
-    if (h->precision != FMMBEM_MIXED || h->m2l_mode != FMMBEM_M2L_TENSOR || !h->m2l_tc_ready) return 0.0;
+    if (h->precision == FMMBEM_FP64 || h->m2l_mode != FMMBEM_M2L_TENSOR || !h->m2l_tc_ready) return 0.0;
     const double q = (double)(p + 1) * (p + 1), per = 2.0 * q * q * h->ncomp * h->nsys;
     double f = 0.0;
     if (h->m2l_tc_at[p]) f += per * (double)h->n_m2l;
@@ -233,30 +233,31 @@ int matvec_sorted(fmmbem_handle* h, int p, const double* xs, double* ys) {
     if (!h->use_graphs || xs != h->xfix || ys != h->kw || h->stream == nullptr)
         return matvec_launch(h, p, xs, ys);
     prof_harvest(h);
-    if (h->mv_graph[p] && h->mv_graph_mode[p] != mode) {
-        cudaGraphExecDestroy(h->mv_graph[p]);
-        h->mv_graph[p] = nullptr;
+    const int g_i = p + (h->precision == FMMBEM_FP64 ? FMMBEM_P_MAX + 1 : 0);  // graph slot
+    if (h->mv_graph[g_i] && h->mv_graph_mode[g_i] != mode) {
+        cudaGraphExecDestroy(h->mv_graph[g_i]);
+        h->mv_graph[g_i] = nullptr;
     }
-    if (!h->mv_graph[p]) {
+    if (!h->mv_graph[g_i]) {
         cudaGraph_t g = nullptr;
         const int64_t keep = h->launches;
         FMM_CU(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
-        h->capturing = p;
+        h->capturing = g_i;
         const int rc = matvec_launch(h, p, xs, ys);
         h->capturing = -1;
         cudaError_t e = cudaStreamEndCapture(h->stream, &g);
         if (rc < 0) { if (g) cudaGraphDestroy(g); return rc; }
         FMM_CU(e);
-        e = cudaGraphInstantiate(&h->mv_graph[p], g, 0);
+        e = cudaGraphInstantiate(&h->mv_graph[g_i], g, 0);
         cudaGraphDestroy(g);
         FMM_CU(e);
-        h->mv_graph_mode[p] = mode;
-        h->graph_launches[p] = h->launches - keep;
+        h->mv_graph_mode[g_i] = mode;
+        h->graph_launches[g_i] = h->launches - keep;
         h->launches = keep;
     }
-    FMM_CU(cudaGraphLaunch(h->mv_graph[p], h->stream));
-    h->launches += h->graph_launches[p];
-    if (h->prof_on) h->pending_graph = p;
+    FMM_CU(cudaGraphLaunch(h->mv_graph[g_i], h->stream));
+    h->launches += h->graph_launches[g_i];
+    if (h->prof_on) h->pending_graph = g_i;
     if (h->prof_on) {
         const double q = (double)(p + 1) * (p + 1);
         h->prof.m2l_flops += 2.0 * q * q * h->ncomp * h->nsys * (double)h->n_m2l;
@@ -329,7 +330,7 @@ void fmmbem_destroy(fmmbem_handle* h) {
     if (h->stream2) cudaStreamSynchronize(h->stream2);
     if (h->istream) cudaStreamSynchronize(h->istream);
     fmm_alloc_stream() = h->stream;
-    void* bufs[] = {h->perm, h->body, h->body_acc, h->tgt_d, h->tgt_f, h->nrm_d, h->nrm_f, h->verts, h->src_d, h->src_f, h->src_rel, h->tgt_rel, h->src_w, h->cell_cs, h->cell_range, h->cell_rad,
+    void* bufs[] = {h->perm, h->body, h->body_acc, h->rf_r, h->rf_d, h->tgt_d, h->tgt_f, h->nrm_d, h->nrm_f, h->verts, h->src_d, h->src_f, h->src_rel, h->tgt_rel, h->src_w, h->cell_cs, h->cell_range, h->cell_rad,
                     h->cell_child, h->cell_level, h->cell_parent, h->leaves, h->parents, h->leaf_class, h->m2l_ptr, h->m2l_src, h->p2p_ptr,
                     h->p2p_src, h->p2p_rec, h->p2p_off, h->p2p_len, h->p2p_items, h->p2p_cnt, h->p2p_toff, h->stage_ptr, h->stage_first, h->stage_bytes, h->corr_ptr, h->corr_col, h->corr_sl, h->corr_dl, h->oct_d, h->oct_f, h->M, h->L,
                     h->xs, h->ys, h->ynear, h->m2l_pt, h->m2l_ps, h->m2l_refl, h->sign_f, h->sign_d, h->m2l_tiles, h->tab_d, h->tab_f, h->tab_tc, h->m2l_tiles_tc, h->tc_src_info, h->tc_dst_info, h->tree_tab_tc, h->tree_tiles, h->tree_info, h->tc_err, h->kerr, h->V, h->kw, h->xfix, h->kb, h->kx, h->kr, h->kpart, h->kh, h->kyv, h->arn_bar};
@@ -337,7 +338,7 @@ void fmmbem_destroy(fmmbem_handle* h) {
         if (b) fmm_free(b);
     pinned_put(h->kh_host, sizeof(double) * 3 * (h->kr_m + 2) * h->nrhs);
     pinned_put(h->arn_out_host, sizeof(double) * (2 * 65 + 1) * h->nrhs);
-    for (int q = 0; q <= FMMBEM_P_MAX; ++q) {
+    for (int q = 0; q < fmmbem_handle::NGRAPH; ++q) {
         if (h->mv_graph[q]) cudaGraphExecDestroy(h->mv_graph[q]);
         for (int e = 0; e < 2 * FMMBEM_N_PASSES; ++e)
             if (h->gev[q][e]) cudaEventDestroy(h->gev[q][e]);
@@ -373,7 +374,14 @@ int fmmbem_create(const fmmbem_mesh* mesh, int kernel, int gauss_k, int ncrit, d
     if (o.max_iter < 1) { fmmbem_set_error("max_iter < 1"); return FMMBEM_EINVAL; }
     if (!(o.near_factor >= 0.0)) { fmmbem_set_error("near_factor < 0"); return FMMBEM_EINVAL; }
     if (!(o.mu > 0.0)) { fmmbem_set_error("mu must be > 0"); return FMMBEM_EINVAL; }
-    if (o.precision != FMMBEM_FP64 && o.precision != FMMBEM_MIXED) { fmmbem_set_error("bad precision"); return FMMBEM_EINVAL; }
+    if (o.precision != FMMBEM_FP64 && o.precision != FMMBEM_MIXED && o.precision != FMMBEM_MIXED_REFINED) {
+        fmmbem_set_error("bad precision");
+        return FMMBEM_EINVAL;
+    }
+    if (o.precision == FMMBEM_MIXED_REFINED && o.nrhs > 1) {
+        fmmbem_set_error("refined solves take one right-hand side");
+        return FMMBEM_EINVAL;
+    }
     if (kernel == FMMBEM_LAPLACE && o.nrhs != 1 && o.nrhs != FMMBEM_BATCH) {
         fmmbem_set_error("a Laplace handle takes nrhs 1 or %d", FMMBEM_BATCH);
         return FMMBEM_EINVAL;
@@ -501,6 +509,7 @@ int fmmbem_create(const fmmbem_mesh* mesh, int kernel, int gauss_k, int ncrit, d
     }
     if ((rc = dalloc(&h->kh, (size_t)3 * (o.restart + 2) * nb)) < 0) return fail(rc);
     if ((rc = dalloc(&h->kyv, (size_t)(o.restart + 2) * nb)) < 0) return fail(rc);
+    if (nb == 1 && ((rc = dalloc(&h->rf_r, n)) < 0 || (rc = dalloc(&h->rf_d, n)) < 0)) return fail(rc);
     h->kh_host = reinterpret_cast<double*>(pinned_get(sizeof(double) * 3 * (o.restart + 2) * nb, cudaHostAllocDefault));
     if (!h->kh_host) {
         fmmbem_set_error("pinned allocation failed");
@@ -533,7 +542,14 @@ int fmmbem_body_integrals(fmmbem_handle* h, const double* x_dev, double* out_hos
 }
 
 int fmmbem_set_precision(fmmbem_handle* h, int precision) {
-    if (!h || (precision != FMMBEM_FP64 && precision != FMMBEM_MIXED)) { fmmbem_set_error("bad precision"); return FMMBEM_EINVAL; }
+    if (!h || (precision != FMMBEM_FP64 && precision != FMMBEM_MIXED && precision != FMMBEM_MIXED_REFINED)) {
+        fmmbem_set_error("bad precision");
+        return FMMBEM_EINVAL;
+    }
+    if (precision == FMMBEM_MIXED_REFINED && h->nrhs > 1) {
+        fmmbem_set_error("refined solves take one right-hand side");
+        return FMMBEM_ESTATE;
+    }
     h->precision = precision;
     return 0;
 }
@@ -559,7 +575,7 @@ int fmmbem_set_tc_thresholds(fmmbem_handle* h, int m2l_min_p, int tree_min_p) {
 
 int fmmbem_autotune(fmmbem_handle* h, int p_lo, int p_hi, int* choice) {
     if (!h || p_lo < 1 || p_hi > h->opts.p_max || p_lo > p_hi) { fmmbem_set_error("need 1 <= p_lo <= p_hi <= p_max"); return FMMBEM_EINVAL; }
-    if (h->precision != FMMBEM_MIXED || !h->m2l_tc_ready || h->m2l_mode != FMMBEM_M2L_TENSOR) {
+    if (h->precision == FMMBEM_FP64 || !h->m2l_tc_ready || h->m2l_mode != FMMBEM_M2L_TENSOR) {
         for (int p = p_lo; p <= p_hi; ++p)
             if (choice) choice[p] = 2 * h->m2l_tc_at[p] + h->tree_tc_at[p];
         return 0;  // nothing to choose: the tensor-core paths are not in use

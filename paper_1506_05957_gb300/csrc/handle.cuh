@@ -27,16 +27,19 @@ struct fmmbem_handle {
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     cudaStream_t istream = nullptr;  // internal stream of fmmbem_solve
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;
-    // one captured mat-vec per order p (input xfix, output kw), instantiated on first use
+    // one captured mat-vec per arithmetic and order p (input xfix, output kw), instantiated on
+    // first use: slot p for the mixed arithmetic, FMMBEM_P_MAX + 1 + p for FP64 (the refined
+    // solve alternates between them)
+    static constexpr int NGRAPH = 2 * (FMMBEM_P_MAX + 1);
     bool use_graphs = true;
-    cudaGraphExec_t mv_graph[FMMBEM_P_MAX + 1] = {};
-    int mv_graph_mode[FMMBEM_P_MAX + 1] = {};
-    int64_t graph_launches[FMMBEM_P_MAX + 1] = {};
-    int capturing = -1;          // order p of the graph being captured, else -1
+    cudaGraphExec_t mv_graph[NGRAPH] = {};
+    int mv_graph_mode[NGRAPH] = {};
+    int64_t graph_launches[NGRAPH] = {};
+    int capturing = -1;          // slot of the graph being captured, else -1
     int pending_graph = -1;      // last replayed graph whose pass events await harvesting
-    cudaEvent_t gev[FMMBEM_P_MAX + 1][2 * FMMBEM_N_PASSES] = {};
-    int gev_launches[FMMBEM_P_MAX + 1][FMMBEM_N_PASSES] = {};
-    int gev_tc[FMMBEM_P_MAX + 1] = {};  // tc_pass_bits of each captured graph
+    cudaEvent_t gev[NGRAPH][2 * FMMBEM_N_PASSES] = {};
+    int gev_launches[NGRAPH][FMMBEM_N_PASSES] = {};
+    int gev_tc[NGRAPH] = {};     // tc_pass_bits of each captured graph
     int tc_pass_bits = 0;               // passes of the mat-vec being issued that run on k_m2l_tc
     int64_t N = 0;   // panels
     int64_t NS = 0;  // Gauss points = K * N
@@ -169,6 +172,8 @@ struct fmmbem_handle {
     double* kh = nullptr;       // [m+2] dot results
     double* kh_host = nullptr;  // pinned
     double* kyv = nullptr;      // [m] update coefficients
+    double* rf_r = nullptr;     // [n] outer residual of the refined solve (FMMBEM_MIXED_REFINED)
+    double* rf_d = nullptr;     // [n] its inner correction
     // fused Arnoldi step (cooperative launch)
     int arn_blocks = 0;
     unsigned* arn_bar = nullptr;       // grid barrier counter and generation

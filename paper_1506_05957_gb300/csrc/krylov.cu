@@ -80,6 +80,12 @@ __global__ void k_scale(double* dst, double* dst2, const double* src, double a, 
     }
 }
 
+// x += d
+__global__ void k_add(double* x, const double* d, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        x[i] += d[i];
+}
+
 __global__ void k_sub(double* r, const double* b, const double* ax, int64_t n) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         r[i] = b[i] - ax[i];
@@ -356,6 +362,8 @@ int relaxed_p(double eta, double rho_prev, int p_initial, int p_min) {
 
 static int gmres_solve_on(fmmbem_handle* h, const double* b, double tol, int relax, int p_initial, int p_min, double* x,
                           int* iters, int* p_hist, double* res_hist, double* true_res);
+static int gmres_refine_on(fmmbem_handle* h, const double* b, double tol, int relax, int p_initial, int p_min,
+                           double* x, int* iters, int* p_hist, double* res_hist, double* true_res);
 
 // The solve runs on the handle's internal stream (capturable, so the mat-vec graphs can
 // be recorded), ordered after the caller's stream on entry and before it on exit.
@@ -392,7 +400,9 @@ int gmres_solve(fmmbem_handle* h, const double* b, double tol, int relax, int p_
     if (h->tc_err) FMM_CU(cudaMemsetAsync(h->tc_err, 0, sizeof(int), h->istream));
     h->stream = h->istream;
     const int rc = h->nrhs > 1 ? gmres_batch_on(h, b, tol, relax, p_initial, p_min, x, iters, p_hist, res_hist, true_res)
-                               : gmres_solve_on(h, b, tol, relax, p_initial, p_min, x, iters, p_hist, res_hist, true_res);
+                   : h->precision == FMMBEM_MIXED_REFINED
+                       ? gmres_refine_on(h, b, tol, relax, p_initial, p_min, x, iters, p_hist, res_hist, true_res)
+                       : gmres_solve_on(h, b, tol, relax, p_initial, p_min, x, iters, p_hist, res_hist, true_res);
     h->stream = user;
     if (rc == FMMBEM_EDEVICE || rc == FMMBEM_ENOMEM) return rc;
     // bounded device waits (grid barrier, bulk-copy and tensor-core barriers) report here,
@@ -548,6 +558,89 @@ static int gmres_solve_on(fmmbem_handle* h, const double* b, double tol, int rel
         prof_harvest(h);
         *true_res = sqrt(hb[0]) / bnorm;
     }
+    return converged ? 0 : FMMBEM_NOT_CONVERGED;
+}
+
+// Iterative refinement around the mixed-precision relaxed GMRES: the FP32 passes resolve the
+// operator to about 1e-6, so each outer step solves A d = r with mixed mat-vecs only to a
+// relative RF_INNER_TOL (or to the final tolerance when that is looser), then x += d and
+// r = b - A x with an FP64 mat-vec at p_initial. The error of one step is about the inner
+// tolerance plus the mixed operator's relative error times the conditioning, so two or three
+// outer steps reach 1e-8 where an all-FP64 solve runs every mat-vec at a few times the cost.
+constexpr double RF_INNER_TOL = 1e-5;
+constexpr int RF_MAX_OUTER = 8;
+
+static int gmres_refine_on(fmmbem_handle* h, const double* b, double tol, int relax, int p_initial, int p_min,
+                           double* x, int* iters, int* p_hist, double* res_hist, double* true_res) {
+    const int64_t n = h->N * h->dof;
+    const int max_iter = h->opts.max_iter;
+    cudaStream_t st = h->stream;
+    Kr kr{h, n, (unsigned)std::min<int64_t>((n + 255) / 256, 2048)};
+    double* hb = h->kh_host;
+    double* knr = h->kh + 2 * (h->kr_m + 2);
+    double* r = h->rf_r;
+    double* d = h->rf_d;
+    auto norm_of = [&](const double* v, double* out) -> int {
+        FMM_TRY(kr.dots(v, 1, v, knr));
+        FMM_CU(cudaMemcpyAsync(hb, knr, sizeof(double), cudaMemcpyDeviceToHost, st));
+        FMM_CU(cudaStreamSynchronize(st));
+        prof_harvest(h);
+        *out = sqrt(hb[0]);
+        return 0;
+    };
+    FMM_CU(cudaMemsetAsync(x, 0, sizeof(double) * n, st));
+    double bnorm = 0.0;
+    FMM_TRY(norm_of(b, &bnorm));
+    if (iters) *iters = 0;
+    if (res_hist) res_hist[0] = 1.0;
+    if (!(bnorm > 0.0)) {
+        if (true_res) *true_res = 0.0;
+        return bnorm == 0.0 ? 0 : FMMBEM_ENAN;
+    }
+    FMM_CU(cudaMemcpyAsync(r, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+    std::vector<int> ph(max_iter + 1);
+    std::vector<double> rh(max_iter + 2);
+    double rho = 1.0;
+    int it = 0, rc = 0;
+    bool converged = false;
+    for (int outer = 0; outer < RF_MAX_OUTER && it < max_iter; ++outer) {
+        // inner: A d = r, mixed mat-vecs, relaxed by the inner tolerance
+        const double tin = std::min(0.5, std::max(RF_INNER_TOL, tol / rho));
+        int it_in = 0;
+        const int keep_max = h->opts.max_iter;
+        h->opts.max_iter = max_iter - it;
+        h->precision = FMMBEM_MIXED;
+        rc = gmres_solve_on(h, r, tin, relax, p_initial, p_min, d, &it_in, ph.data(), rh.data(), nullptr);
+        h->precision = FMMBEM_MIXED_REFINED;
+        h->opts.max_iter = keep_max;
+        if (rc < 0) return rc;
+        for (int k = 0; k < it_in; ++k) {
+            if (p_hist) p_hist[it + k] = ph[k];
+            if (res_hist) res_hist[it + k + 1] = rh[k + 1] * rho;  // the inner estimate, relative to ||b||
+        }
+        it += it_in;
+        k_add<<<kr.gs, 256, 0, st>>>(x, d, n);
+        FMM_LAUNCHED();
+        h->launches += 1;
+        // outer: r = b - A x with an FP64 mat-vec at p_initial
+        FMM_CU(cudaMemcpyAsync(h->xfix, x, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+        h->precision = FMMBEM_FP64;
+        rc = matvec_sorted(h, p_initial, h->xfix, h->kw);
+        h->precision = FMMBEM_MIXED_REFINED;
+        if (rc < 0) return rc;
+        k_sub<<<kr.gs, 256, 0, st>>>(r, b, h->kw, n);
+        FMM_LAUNCHED();
+        h->launches += 1;
+        double rn = 0.0;
+        FMM_TRY(norm_of(r, &rn));
+        rho = rn / bnorm;
+        if (res_hist && it > 0) res_hist[it] = rho;
+        if (!std::isfinite(rho)) return FMMBEM_ENAN;
+        if (rho <= tol) { converged = true; break; }
+        if (it_in == 0) break;  // no progress possible (the inner solve met its tolerance at once)
+    }
+    if (iters) *iters = it;
+    if (true_res) *true_res = rho;
     return converged ? 0 : FMMBEM_NOT_CONVERGED;
 }
 
