@@ -51,11 +51,16 @@ def parse():
                          "batch: four right-hand sides in one batched solve against four single solves; "
                          "rbc64: Stokes flow around 64 red blood cells (131072 panels); "
                          "peaks: the peak rates the rooflines divide by (FP32, paired FP32, rsqrt, FP64, TF32 tensor)")
+    ap.add_argument("--quick", action="store_true",
+                    help="sweeps: the same studies on small meshes with one timed run each (a check of the harness)")
     ap.add_argument("--requests", type=int, default=48, help="serve: number of requests")
     ap.add_argument("--rate", type=float, default=20.0, help="serve: mean arrival rate (requests/s)")
     ap.add_argument("--max-active", type=int, default=6, help="serve: concurrent solves")
     ap.add_argument("--no-autotune", action="store_true",
                     help="laplace: keep the default per-order tensor-core choices instead of fmmbem_autotune's")
+    ap.add_argument("--tune-ncrit", default="",
+                    help="laplace: comma-separated leaf capacities; the handle is created by fmmbem_create_tuned "
+                         "over them (the workload's ncrit stays the reported configuration's otherwise)")
     return ap.parse_args()
 
 
@@ -278,8 +283,15 @@ def run_ours(args, world, rank, local):
     psampler.start()
     peaks = measure_peaks(dev)
     peaks["clocks"] = psampler.stop()
-    h = FmmBem(v, t, gauss_k=W["gauss_k"], ncrit=args.ncrit, theta=W["theta"], p_max=16, restart=W["restart"],
-               max_iter=100, precision=FMMBEM_MIXED, stream=stream.cuda_stream)
+    if args.tune_ncrit:
+        cand = [int(c) for c in args.tune_ncrit.split(",")]
+        h = FmmBem.tuned(v, t, ncrit_candidates=cand, p_lo=W["p_min"], p_hi=W["p_initial"], gauss_k=W["gauss_k"],
+                         theta=W["theta"], p_max=16, restart=W["restart"], max_iter=100, precision=FMMBEM_MIXED,
+                         stream=stream.cuda_stream)
+        args.ncrit = h.tuned_ncrit
+    else:
+        h = FmmBem(v, t, gauss_k=W["gauss_k"], ncrit=args.ncrit, theta=W["theta"], p_max=16, restart=W["restart"],
+                   max_iter=100, precision=FMMBEM_MIXED, stream=stream.cuda_stream)
     stats = h.stats()
     phi_d = torch.tensor(phi, dtype=torch.float64, device=dev)
     b = torch.empty_like(phi_d)
@@ -667,7 +679,10 @@ def run_sweeps(args, world, rank, local):
     import math
     import torch
     from synth import octasphere, evans_fung_cell
-    from paper_1506_05957_gb300 import FmmBem, FMMBEM_FP64, FMMBEM_MIXED, FMMBEM_STOKES, build
+    from paper_1506_05957_gb300 import FmmBem, FMMBEM_FP64, FMMBEM_MIXED, FMMBEM_MIXED_REFINED, FMMBEM_STOKES, build
+    q = args.quick  # small meshes, one timed run: a check of the harness, not a measurement
+    lv = (lambda full, small: small if q else full)
+    nrep = (lambda full: 1 if q else full)
     build.build()
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
@@ -699,41 +714,53 @@ def run_sweeps(args, world, rank, local):
         h.rhs(torch.tensor(phi, dtype=torch.float64, device=dev), b)
         return h, b
 
-    out = {"metric": "paper parameter studies, relaxed vs non-relaxed GMRES solve ms", "n_gpus": world,
-           "data": "synthetic", "unit": "ms"}
+    lines = []
+
+    def emit(study, table, body):
+        line = {"metric": "paper parameter study: relaxed vs non-relaxed GMRES solve ms", "study": study,
+                "paper_table": table, "n_gpus": world, "data": "synthetic", "unit": "ms", "quick": bool(q)}
+        line.update(body)
+        lines.append(line)
+
     # initial p, 10 iterations
-    h, b = laplace(6, FMMBEM_MIXED, max_iter=10)
+    h, b = laplace(lv(6, 4), FMMBEM_MIXED, max_iter=10)
     x = torch.zeros_like(b)
     rows = []
     for p in (5, 8, 10, 12, 15):
-        t_rel, r_rel = timed(h, b, x, 5, tol=1e-6, relax=True, p_initial=p, p_min=3)
-        t_fix, r_fix = timed(h, b, x, 5, tol=1e-6, relax=False, p_initial=p, p_min=3)
+        t_rel, r_rel = timed(h, b, x, nrep(5), tol=1e-6, relax=True, p_initial=p, p_min=3)
+        t_fix, r_fix = timed(h, b, x, nrep(5), tol=1e-6, relax=False, p_initial=p, p_min=3)
         rows.append({"p_initial": p, "relaxed_ms": round(t_rel, 3), "fixed_ms": round(t_fix, 3),
-                     "speedup": round(t_fix / t_rel, 3), "iters": r_rel["iters"], "p_hist": r_rel["p_hist"]})
+                     "speedup": round(t_fix / t_rel, 3), "iters": r_rel["iters"], "iters_fixed": r_fix["iters"],
+                     "p_hist": r_rel["p_hist"]})
+    panels = h.n_panels
     h.close()
-    out["initial_p_32768_10_iterations"] = {"rows": rows, "paper_speedups_cpu": [1.91, 2.00, 2.20, 2.00, 1.71]}
-    # tolerance
+    emit("initial_p", "laplace_1st_p_relaxation", {"panels": panels, "iterations": 10, "rows": rows,
+                                                   "paper_speedups_cpu": [1.91, 2.00, 2.20, 2.00, 1.71]})
+    # tolerance; below 1e-6 the mixed-precision mat-vec is refined with FP64 residuals
     rows = []
-    for prec, name in ((FMMBEM_MIXED, "mixed"), (FMMBEM_FP64, "fp64")):
-        h, b = laplace(5, prec)
+    for prec, name in ((FMMBEM_MIXED, "mixed"), (FMMBEM_MIXED_REFINED, "refined"), (FMMBEM_FP64, "fp64")):
+        h, b = laplace(lv(5, 3), prec)
         x = torch.zeros_like(b)
         for tol in (1e-5, 1e-6, 1e-7, 1e-8, 1e-9, 1e-10, 1e-11):
-            if prec == FMMBEM_MIXED and tol < 1e-6:
-                continue  # the mixed mat-vec resolves about 1e-6
-            reps = 5 if prec == FMMBEM_MIXED else 2
+            if (prec == FMMBEM_MIXED and tol < 1e-6) or (prec == FMMBEM_MIXED_REFINED and tol >= 1e-6):
+                continue  # the mixed mat-vec resolves about 1e-6; refinement serves the tolerances below
+            reps = nrep(5 if prec != FMMBEM_FP64 else 2)
             t_rel, r_rel = timed(h, b, x, reps, tol=tol, relax=True, p_initial=10, p_min=3)
             t_fix, r_fix = timed(h, b, x, reps, tol=tol, relax=False, p_initial=10, p_min=3)
             rows.append({"precision": name, "tol": tol, "relaxed_ms": round(t_rel, 3), "fixed_ms": round(t_fix, 3),
                          "speedup": round(t_fix / t_rel, 3), "iters_relaxed": r_rel["iters"],
-                         "iters_fixed": r_fix["iters"], "true_res": r_rel["true_res"]})
+                         "iters_fixed": r_fix["iters"], "true_res": r_rel["true_res"],
+                         "converged": bool(r_rel["converged"] and r_fix["converged"])})
+        panels = h.n_panels
         h.close()
-    out["tolerance_8192_p10"] = {"rows": rows,
-                                 "paper_speedups_cpu": [1.90, 2.01, 1.95, 1.71, 1.54, 1.61, 1.46]}
+    emit("tolerance", "laplace_1st_tolerance_relaxation",
+         {"panels": panels, "p_initial": 10, "rows": rows,
+          "paper_speedups_cpu": [1.90, 2.01, 1.95, 1.71, 1.54, 1.61, 1.46]})
     # p_min, Stokes sphere, mu = 1e-3: drag 6 pi mu R = 0.01885
     mu = 1e-3
     exact = 6.0 * np.pi * mu
     rows = []
-    for level in (4, 5, 6):
+    for level in lv((4, 5, 6), (3, 4)):
         v, t = octasphere(level)
         p3 = v[t]
         area = 0.5 * np.linalg.norm(np.cross(p3[:, 1] - p3[:, 0], p3[:, 2] - p3[:, 0]), axis=1)
@@ -742,15 +769,15 @@ def run_sweeps(args, world, rank, local):
         b = torch.tensor(np.tile([1.0, 0.0, 0.0], len(t)), dtype=torch.float64, device=dev)
         x = torch.zeros_like(b)
         for pmin in (5, 4, 3, 2, 1):
-            tm, r = timed(h, b, x, 2, tol=1e-5, relax=True, p_initial=16, p_min=pmin)
+            tm, r = timed(h, b, x, nrep(2), tol=1e-5, relax=True, p_initial=16, p_min=pmin)
             drag = float(np.sum(x.cpu().numpy().reshape(-1, 3)[:, 0] * area))
             rows.append({"panels": len(t), "p_min": pmin, "drag_error": abs(abs(drag) - exact) / exact,
                          "iters": r["iters"], "converged": r["converged"], "ms": round(tm, 3)})
         h.close()
-    out["stokes_pmin"] = {"rows": rows, "exact_drag": exact}
+    emit("p_min", "stokes_min_p", {"rows": rows, "exact_drag": exact, "mu": mu, "tol": 1e-5})
     # red blood cell: Richardson study (512, 2048, 8192 panels) and relaxation speed-ups
     drags, rows = [], []
-    for level in (3, 4, 5, 6, 7):
+    for level in lv((3, 4, 5, 6, 7), (3, 4, 5)):
         v, t = evans_fung_cell(level)
         p3 = v[t]
         area = 0.5 * np.linalg.norm(np.cross(p3[:, 1] - p3[:, 0], p3[:, 2] - p3[:, 0]), axis=1)
@@ -758,22 +785,24 @@ def run_sweeps(args, world, rank, local):
                    restart=50, max_iter=100, precision=FMMBEM_MIXED, stream=stream.cuda_stream)
         b = torch.tensor(np.tile([1.0, 0.0, 0.0], len(t)), dtype=torch.float64, device=dev)
         x = torch.zeros_like(b)
-        t_rel, r_rel = timed(h, b, x, 2, tol=1e-5, relax=True, p_initial=16, p_min=5)
+        t_rel, r_rel = timed(h, b, x, nrep(2), tol=1e-5, relax=True, p_initial=16, p_min=5)
         drags.append(float(np.sum(x.cpu().numpy().reshape(-1, 3)[:, 0] * area)))
         if level >= 4:
-            t_fix, r_fix = timed(h, b, x, 2, tol=1e-5, relax=False, p_initial=16, p_min=5)
+            t_fix, r_fix = timed(h, b, x, nrep(2), tol=1e-5, relax=False, p_initial=16, p_min=5)
             rows.append({"panels": len(t), "relaxed_ms": round(t_rel, 3), "fixed_ms": round(t_fix, 3),
                          "speedup": round(t_fix / t_rel, 3), "iters_relaxed": r_rel["iters"],
                          "iters_fixed": r_fix["iters"]})
         h.close()
     f1, f2, f3 = drags[:3]
-    out["rbc_richardson"] = {"panels": [512, 2048, 8192], "drag": [f1, f2, f3],
-                             "extrapolated": (f1 * f3 - f2 * f2) / (f1 - 2.0 * f2 + f3),
-                             "observed_order": math.log((f2 - f1) / (f3 - f2)) / math.log(4.0),
-                             "paper_observed_order": 0.52}
-    out["rbc_single_cell"] = {"rows": rows, "paper_speedups_cpu": [3.30, 3.40, 3.54, 4.90]}
+    emit("rbc_richardson", "rbc_richardson_values",
+         {"panels": [512, 2048, 8192], "drag": [f1, f2, f3],
+          "extrapolated": (f1 * f3 - f2 * f2) / (f1 - 2.0 * f2 + f3),
+          "observed_order": math.log((f2 - f1) / (f3 - f2)) / math.log(4.0), "paper_observed_order": 0.52})
+    emit("rbc_single_cell", "single_cell_relaxation_results",
+         {"rows": rows, "paper_speedups_cpu": [3.30, 3.40, 3.54, 4.90]})
     if rank == 0:
-        print(json.dumps(out), flush=True)
+        for line in lines:
+            print(json.dumps(line), flush=True)
 
 
 def run_batch(args, world, rank, local):

@@ -170,15 +170,31 @@ int fmmbem_set_m2l_mode(fmmbem_handle* h, int mode);
  * tree_min_p 6 (measured on the 81920-panel sphere). FMMBEM_EINVAL for values below 1. */
 int fmmbem_set_tc_thresholds(fmmbem_handle* h, int m2l_min_p, int tree_min_p);
 
-/* Autotuner: for every order p in [p_lo, p_hi], time the handle's mat-vec (its captured
- * graph, on the handle's stream) with M2L and with M2M/L2L on the tensor cores or on the SIMT
- * kernels (four configurations, three timed runs each after a capture run) and keep the
- * fastest per p. choice (optional, [p_max + 1] ints, host): 2 * (M2L on tensor cores) +
- * (M2M/L2L on tensor cores) for each tuned p. The sums are the same in every configuration
- * (FP32 passes, 3xTF32 products). Synchronizes the handle's stream; does nothing but report
- * the current choices for FMMBEM_FP64 handles or without tensor-core tables. Errors:
- * FMMBEM_EINVAL, FMMBEM_EDEVICE. */
+/* Autotuner: first the near-field schedule (fmmbem_set_p2p_variant's four, timed at p_hi:
+ * the near field does not depend on p), then for every order p in [p_lo, p_hi] M2L and
+ * M2M/L2L on the tensor cores or on the SIMT kernels (four configurations): each candidate
+ * times the handle's mat-vec (its captured graph, on the handle's stream) over three runs
+ * after a capture run, and the fastest is kept. choice (optional, [p_max + 1] ints, host):
+ * 2 * (M2L on tensor cores) + (M2M/L2L on tensor cores) for each tuned p, and in choice[0]
+ * the near-field schedule. The sums are the same in every configuration (FP32 passes, 3xTF32
+ * products). Synchronizes the handle's stream; for FMMBEM_FP64 handles or without
+ * tensor-core tables it only reports the current choices. Errors: FMMBEM_EINVAL,
+ * FMMBEM_EDEVICE. */
 int fmmbem_autotune(fmmbem_handle* h, int p_lo, int p_hi, int* choice);
+
+/*
+ * Create with the leaf capacity chosen by measurement (Sec. 3 tunes N_CRIT separately for
+ * relaxed and fixed-p runs): for each of the n_cand leaf capacities ncrit_cand[i] (host), build
+ * the handle (fmmbem_create), run fmmbem_autotune(h, p_lo, p_hi), and time one mat-vec at
+ * every order of [p_lo, p_hi] (their sum weighs the low orders of a relaxed solve as much as
+ * the high ones); keep the fastest handle and destroy the others. Other arguments as
+ * fmmbem_create. ncrit_out (optional, host) receives the chosen capacity, ms_out (optional) the
+ * chosen handle's summed mat-vec milliseconds. Errors: those of fmmbem_create and
+ * fmmbem_autotune; FMMBEM_EINVAL for an empty candidate list or a bad order range.
+ */
+int fmmbem_create_tuned(const fmmbem_mesh* mesh, int kernel, int gauss_k, int n_cand, const int* ncrit_cand,
+                        double theta, const fmmbem_opts* opts, int p_lo, int p_hi, fmmbem_handle** out,
+                        int* ncrit_out, double* ms_out);
 
 /* Near-field kernel of FMMBEM_MIXED Laplace mat-vecs (same sums, different schedules):
  * 0 = source tiles staged in shared memory, targets held per lane;

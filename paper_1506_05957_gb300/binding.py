@@ -125,6 +125,10 @@ def lib():
         L.fmmbem_profile_enable.argtypes = [_vp, ctypes.c_int]
         L.fmmbem_profile_get.argtypes = [_vp, ctypes.POINTER(fmmbem_profile)]
         L.fmmbem_last_error.restype = ctypes.c_char_p
+        L.fmmbem_create_tuned.argtypes = [ctypes.POINTER(fmmbem_mesh), ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                          ctypes.POINTER(ctypes.c_int), ctypes.c_double, ctypes.POINTER(fmmbem_opts),
+                                          ctypes.c_int, ctypes.c_int, ctypes.POINTER(_vp), ctypes.POINTER(ctypes.c_int),
+                                          _dp]
         L.fmmbem_body_integrals.argtypes = [_vp, _vp, _vp]
         L.fmmbem_n_bodies.argtypes = [_vp]
         L.fmmbem_check_waits.argtypes = [_vp]
@@ -198,7 +202,8 @@ class FmmBem:
 
     def __init__(self, vertices, triangles, kernel=FMMBEM_LAPLACE, gauss_k=4, ncrit=150, theta=0.5, p_max=16,
                  near_factor=2.0, mu=1.0, precision=FMMBEM_MIXED, restart=50, max_iter=100, stream=None, nrhs=1,
-                 near_k=20, body_of_panel=None):
+                 near_k=20, body_of_panel=None, _tune=None):
+        """_tune = (ncrit candidates, p_lo, p_hi): create through fmmbem_create_tuned (see FmmBem.tuned)."""
         v = np.ascontiguousarray(vertices, dtype=np.float64)
         t = np.ascontiguousarray(triangles, dtype=np.int32)
         mesh = fmmbem_mesh(len(v), v.ctypes.data_as(_dp), len(t), t.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)))
@@ -218,8 +223,18 @@ class FmmBem:
             stream = torch.cuda.current_stream().cuda_stream
         o.stream = stream
         h = _vp()
-        _check(lib().fmmbem_create(ctypes.byref(mesh), int(kernel), int(gauss_k), int(ncrit), float(theta),
-                                   ctypes.byref(o), ctypes.byref(h)))
+        self.tuned_ncrit, self.tuned_ms = None, None
+        if _tune is None:
+            _check(lib().fmmbem_create(ctypes.byref(mesh), int(kernel), int(gauss_k), int(ncrit), float(theta),
+                                       ctypes.byref(o), ctypes.byref(h)))
+        else:
+            cand, p_lo, p_hi = _tune
+            arr = (ctypes.c_int * len(cand))(*[int(c) for c in cand])
+            nc, ms = ctypes.c_int(0), ctypes.c_double(0.0)
+            _check(lib().fmmbem_create_tuned(ctypes.byref(mesh), int(kernel), int(gauss_k), len(cand), arr,
+                                             float(theta), ctypes.byref(o), int(p_lo), int(p_hi), ctypes.byref(h),
+                                             ctypes.byref(nc), ctypes.byref(ms)))
+            self.tuned_ncrit, self.tuned_ms = nc.value, ms.value
         self.h = h
         self.kernel = kernel
         self.max_iter = max_iter
@@ -228,6 +243,12 @@ class FmmBem:
         self.n = int(lib().fmmbem_n_unknowns(h)) * self.nrhs  # doubles per mat-vec vector (all of a batch)
         self.n_panels = len(t)
         self.n_bodies = int(lib().fmmbem_n_bodies(h))
+
+    @classmethod
+    def tuned(cls, vertices, triangles, ncrit_candidates=(100, 125, 150, 175, 200), p_lo=3, p_hi=12, **kw):
+        """fmmbem_create_tuned: the leaf capacity (and per-order kernel choices) picked by timing mat-vecs
+        over [p_lo, p_hi]; .tuned_ncrit holds the choice."""
+        return cls(vertices, triangles, _tune=(tuple(ncrit_candidates), p_lo, p_hi), **kw)
 
     def close(self):
         if getattr(self, "h", None):
@@ -248,11 +269,14 @@ class FmmBem:
         _check(lib().fmmbem_set_tc_thresholds(self.h, int(m2l_min_p), int(tree_min_p)))
 
     def autotune(self, p_lo=1, p_hi=None):
-        """fmmbem_autotune: per-order choice of tensor-core or SIMT M2L and M2M/L2L; returns {p: choice}."""
+        """fmmbem_autotune: near-field schedule (key 0) and per-order choice of tensor-core or SIMT M2L and
+        M2M/L2L; returns {0: p2p variant, p: choice}."""
         p_hi = self.p_max if p_hi is None else p_hi
         ch = np.full(FMMBEM_P_MAX + 1, -1, dtype=np.int32)
         _check(lib().fmmbem_autotune(self.h, int(p_lo), int(p_hi), _vp(ch.ctypes.data)))
-        return {p: int(ch[p]) for p in range(p_lo, p_hi + 1)}
+        out = {0: int(ch[0])}
+        out.update({p: int(ch[p]) for p in range(p_lo, p_hi + 1)})
+        return out
 
     def body_integrals(self, x):
         """fmmbem_body_integrals: [n_bodies, dof] sums of S_j x_j over each body's panels (Stokes traction

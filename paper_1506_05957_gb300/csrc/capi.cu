@@ -573,8 +573,26 @@ int fmmbem_set_tc_thresholds(fmmbem_handle* h, int m2l_min_p, int tree_min_p) {
     return 0;
 }
 
+// Milliseconds of the handle's mat-vec at order p (its captured graph on the fixed buffers),
+// summed over three runs after a capture run.
+static int time_matvec(fmmbem_handle* h, int p, cudaEvent_t e0, cudaEvent_t e1, float* ms_out) {
+    float ms = 0.f;
+    for (int rep = 0; rep < 4; ++rep) {
+        FMM_CU(cudaEventRecord(e0, h->stream));
+        FMM_TRY(matvec_sorted(h, p, h->xfix, h->kw));
+        FMM_CU(cudaEventRecord(e1, h->stream));
+        FMM_CU(cudaEventSynchronize(e1));
+        float t = 0.f;
+        FMM_CU(cudaEventElapsedTime(&t, e0, e1));
+        if (rep > 0) ms += t;
+    }
+    *ms_out = ms;
+    return 0;
+}
+
 int fmmbem_autotune(fmmbem_handle* h, int p_lo, int p_hi, int* choice) {
     if (!h || p_lo < 1 || p_hi > h->opts.p_max || p_lo > p_hi) { fmmbem_set_error("need 1 <= p_lo <= p_hi <= p_max"); return FMMBEM_EINVAL; }
+    if (choice) choice[0] = h->p2p_variant;
     if (h->precision == FMMBEM_FP64 || !h->m2l_tc_ready || h->m2l_mode != FMMBEM_M2L_TENSOR) {
         for (int p = p_lo; p <= p_hi; ++p)
             if (choice) choice[p] = 2 * h->m2l_tc_at[p] + h->tree_tc_at[p];
@@ -587,6 +605,20 @@ int fmmbem_autotune(fmmbem_handle* h, int p_lo, int p_hi, int* choice) {
     FMM_CU(cudaEventCreate(&e0));
     FMM_CU(cudaEventCreate(&e1));
     int rc = 0;
+    {  // the near-field schedule, at the highest order (the near field does not depend on p)
+        const int keep = h->p2p_variant;
+        float best = 0.f;
+        int best_v = keep;
+        for (int v : {3, 1, 0, 2}) {
+            h->p2p_variant = v;
+            float ms = 0.f;
+            rc = time_matvec(h, p_hi, e0, e1, &ms);
+            if (rc < 0) break;
+            if (v == 3 || ms < best) { best = ms; best_v = v; }
+        }
+        h->p2p_variant = rc < 0 ? keep : best_v;
+        if (choice) choice[0] = h->p2p_variant;
+    }
     for (int p = p_lo; p <= p_hi && rc == 0; ++p) {
         float best = 0.f;
         int best_cfg = 3;
@@ -618,6 +650,57 @@ int fmmbem_autotune(fmmbem_handle* h, int p_lo, int p_hi, int* choice) {
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     return rc < 0 ? rc : 0;
+}
+
+int fmmbem_create_tuned(const fmmbem_mesh* mesh, int kernel, int gauss_k, int n_cand, const int* ncrit_cand,
+                        double theta, const fmmbem_opts* opts, int p_lo, int p_hi, fmmbem_handle** out, int* ncrit_out,
+                        double* ms_out) {
+    if (!out || !ncrit_cand || n_cand < 1 || p_lo < 1 || p_lo > p_hi) {
+        fmmbem_set_error("need candidates and 1 <= p_lo <= p_hi");
+        return FMMBEM_EINVAL;
+    }
+    *out = nullptr;
+    fmmbem_handle* best = nullptr;
+    double best_ms = 0.0;
+    int best_nc = 0;
+    for (int i = 0; i < n_cand; ++i) {
+        fmmbem_handle* h = nullptr;
+        int rc = fmmbem_create(mesh, kernel, gauss_k, ncrit_cand[i], theta, opts, &h);
+        if (rc == 0 && p_hi > h->opts.p_max) {
+            fmmbem_set_error("p_hi beyond p_max");
+            rc = FMMBEM_EINVAL;
+        }
+        if (rc == 0) rc = fmmbem_autotune(h, p_lo, p_hi, nullptr);
+        double total = 0.0;
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        if (rc == 0 && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)) rc = FMMBEM_EDEVICE;
+        if (rc == 0 && cudaMemsetAsync(h->xfix, 0, sizeof(double) * h->N * h->dof * h->nrhs, h->stream) != cudaSuccess)
+            rc = FMMBEM_EDEVICE;
+        for (int p = p_lo; p <= p_hi && rc == 0; ++p) {
+            float ms = 0.f;
+            rc = time_matvec(h, p, e0, e1, &ms);
+            total += ms / 3.0;
+        }
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+        if (rc < 0) {
+            fmmbem_destroy(h);
+            fmmbem_destroy(best);
+            return rc;
+        }
+        if (!best || total < best_ms) {
+            fmmbem_destroy(best);
+            best = h;
+            best_ms = total;
+            best_nc = ncrit_cand[i];
+        } else {
+            fmmbem_destroy(h);
+        }
+    }
+    *out = best;
+    if (ncrit_out) *ncrit_out = best_nc;
+    if (ms_out) *ms_out = best_ms;
+    return 0;
 }
 
 int fmmbem_set_p2p_variant(fmmbem_handle* h, int variant) {

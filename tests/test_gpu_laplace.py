@@ -264,14 +264,16 @@ def test_p2p_variants_agree(torch_cuda, sphere1280, ncrit):
 
 
 def test_autotune_keeps_results(torch_cuda, sphere1280):
-    """The autotuner only chooses between tensor-core and SIMT translations per order p: the
-    solve after tuning matches the oracle as before, and every choice is one of the four."""
+    """The autotuner only chooses among schedules of the same sums (the near-field schedule, and
+    tensor-core or SIMT translations per order p): the solve after tuning matches the oracle as
+    before, and every choice is one of the offered ones."""
     torch = torch_cuda
     s = sphere1280
     h = _h(torch, s["v"], s["t"], p_max=12)
     ch = h.autotune(3, 12)
     print("autotune choices", ch)
-    assert set(ch) == set(range(3, 13)) and all(c in (0, 1, 2, 3) for c in ch.values())
+    assert set(ch) == {0} | set(range(3, 13)) and ch[0] in (0, 1, 2, 3)
+    assert all(ch[p] in (0, 1, 2, 3) for p in range(3, 13))
     b = _dev(torch, s["b"])
     x = torch.zeros_like(b)
     r = h.solve(b, x, tol=1e-6, relax=True, p_initial=10, p_min=3)
@@ -279,3 +281,20 @@ def test_autotune_keeps_results(torch_cuda, sphere1280):
     assert rel(x.cpu().numpy(), s["x_lu"]) < 1e-5
     with pytest.raises(Exception):
         h.autotune(0, 5)
+
+
+def test_tuned_create_picks_a_candidate_leaf_capacity(torch_cuda, sphere1280):
+    """fmmbem_create_tuned builds the tree at each candidate leaf capacity and keeps the one
+    whose mat-vecs over [p_lo, p_hi] are fastest; the kept handle solves like any other."""
+    torch = torch_cuda
+    from paper_1506_05957_gb300 import FmmBem
+    s = sphere1280
+    h = FmmBem.tuned(s["v"], s["t"], ncrit_candidates=(40, 80, 150), p_lo=3, p_hi=10, gauss_k=4, theta=0.5,
+                     p_max=12)
+    print("tuned ncrit", h.tuned_ncrit, "summed mat-vec ms", h.tuned_ms)
+    assert h.tuned_ncrit in (40, 80, 150) and h.tuned_ms > 0.0
+    b = _dev(torch, s["b"])
+    x = torch.zeros_like(b)
+    r = h.solve(b, x, tol=1e-6, relax=True, p_initial=10, p_min=3)
+    assert r["converged"] and rel(x.cpu().numpy(), s["x_lu"]) < 1e-5
+    h.close()
