@@ -468,6 +468,29 @@ int fmmbem_set_wait_limit(fmmbem_handle* h, unsigned limit);
 int fmmbem_peak(int kind, int blocks, int64_t iters, double* ops, double* ms, void* stream);
 
 /*
+ * The hand-written device primitives of the tree build (Sec. 2.5: the Morton-ordered octree,
+ * its leaf classes and its list offsets), exported for callers that order their own points.
+ *
+ * fmmbem_sort_pairs_u64: stable least-significant-digit radix sort of n 64-bit keys (8-bit
+ * digits over bits [0, end_bit); end_bit 0 = 64), carrying one int32 value per key
+ * (vals_in/vals_out both NULL: keys only). keys_out/vals_out receive the keys in ascending
+ * order and each key's value; keys of equal value keep their input order. All four are
+ * device buffers of n elements on `stream` (NULL: the legacy default stream); inputs are
+ * left unchanged and must not alias the outputs. Scratch is stream-ordered
+ * (cudaMallocAsync). Synchronizes `stream` (it reads back the scatter's bounds flag).
+ * Errors: FMMBEM_EINVAL (n < 0 or n >= 2^30, end_bit outside [0, 64], aliasing, one value
+ * buffer without the other), FMMBEM_ENOMEM, FMMBEM_EDEVICE.
+ *
+ * fmmbem_scan_i32: prefix sum of n int32 values, out[i] = sum_{k<i} in[k] (inclusive = 0)
+ * or sum_{k<=i} in[k] (inclusive != 0), wrapping in 32-bit arithmetic; device buffers on
+ * `stream`, in == out allowed. Synchronizes `stream`. Errors: FMMBEM_EINVAL (n < 0),
+ * FMMBEM_ENOMEM, FMMBEM_EDEVICE.
+ */
+int fmmbem_sort_pairs_u64(const uint64_t* keys_in_dev, uint64_t* keys_out_dev, const int32_t* vals_in_dev,
+                          int32_t* vals_out_dev, int64_t n, int end_bit, void* stream);
+int fmmbem_scan_i32(const int32_t* in_dev, int32_t* out_dev, int64_t n, int inclusive, void* stream);
+
+/*
  * ---- Serving many solves at once.
  *
  * The paper solves one problem at a time. This is the request loop around its solver:

@@ -134,6 +134,8 @@ def lib():
         L.fmmbem_check_waits.argtypes = [_vp]
         L.fmmbem_set_wait_limit.argtypes = [_vp, ctypes.c_uint]
         L.fmmbem_peak.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int64, _dp, _dp, _vp]
+        L.fmmbem_sort_pairs_u64.argtypes = [_vp, _vp, _vp, _vp, ctypes.c_int64, ctypes.c_int, _vp]
+        L.fmmbem_scan_i32.argtypes = [_vp, _vp, ctypes.c_int64, ctypes.c_int, _vp]
         _lib = L
     return _lib
 
@@ -195,6 +197,40 @@ def fmmbem_peak(kind, iters, blocks=0, stream=None):
     ops, ms = ctypes.c_double(0.0), ctypes.c_double(0.0)
     _check(lib().fmmbem_peak(int(kind), int(blocks), int(iters), ctypes.byref(ops), ctypes.byref(ms), _vp(stream)))
     return ops.value, ms.value
+
+
+def _dev_typed(t, dtype, what):
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == dtype and t.is_contiguous()):
+        raise TypeError("expected a contiguous %s CUDA tensor for %s" % (dtype, what))
+    return _vp(t.data_ptr())
+
+
+def sort_pairs_u64(keys, values=None, end_bit=0, stream=None):
+    """fmmbem_sort_pairs_u64: (sorted keys, their values) of int64 CUDA tensors whose bits are the
+    unsigned 64-bit keys; values (int32, optional) follow their keys, equal keys keep their order."""
+    import torch
+    n = int(keys.numel())
+    kout = torch.empty_like(keys)
+    kp = _dev_typed(keys, torch.int64, "keys") if n else None
+    vout = torch.empty_like(values) if values is not None else None
+    vp = _dev_typed(values, torch.int32, "values") if (values is not None and n) else None
+    if values is not None and values.numel() != n:
+        raise ValueError("one value per key")
+    _check(lib().fmmbem_sort_pairs_u64(kp, _vp(kout.data_ptr()) if n else None, vp,
+                                       _vp(vout.data_ptr()) if (vp is not None) else None, n, int(end_bit), _vp(stream)))
+    return kout, vout
+
+
+def scan_i32(x, inclusive=False, out=None, stream=None):
+    """fmmbem_scan_i32: exclusive (or inclusive) prefix sum of an int32 CUDA tensor."""
+    import torch
+    n = int(x.numel())
+    out = torch.empty_like(x) if out is None else out
+    ip = _dev_typed(x, torch.int32, "input") if n else None
+    op = _dev_typed(out, torch.int32, "output") if n else None
+    _check(lib().fmmbem_scan_i32(ip, op, n, 1 if inclusive else 0, _vp(stream)))
+    return out
 
 
 class FmmBem:

@@ -144,6 +144,8 @@ struct fmmbem_handle {
     int* corr_col = nullptr;
     double* corr_sl = nullptr;  // single layer: 1 (Laplace) or 9 (Stokes) per entry
     double* corr_dl = nullptr;  // double layer / stresslet
+    float* corr_sl_f = nullptr;  // FP32 copies of both, read by the mixed-precision correction pass
+    float* corr_dl_f = nullptr;
     int64_t n_corr = 0;
 
     // octant translation tables: R_n^m((+-1/4, +-1/4, +-1/4)) for the 8 children
@@ -159,6 +161,7 @@ struct fmmbem_handle {
     double* xs = nullptr;     // [N*dof]
     double* ys = nullptr;     // [N*dof]
     double* ynear = nullptr;  // [N*dof]
+    double* ycorr = nullptr;  // [N*dof]: the correction rows' products of the work-item near field
 
     // Krylov work
     int kr_m = 0;

@@ -120,6 +120,67 @@ __device__ __forceinline__ void add_correction(int i, const int* cptr, const int
     }
 }
 
+// The correction rows of every target as their own pass of the mixed-precision near field:
+// yc[DOF i + a] = sum_e (C_e x_{col_e})_a with the FP32-rounded table and x rounded to FP32
+// (products and sums in FP32, like the P2P sums they are added to), written in FP64 in the
+// layout of the near-field output (DOF 4: a batch, vector c of the input at xs + c * bstride;
+// gridDim.y: the vectors of a Stokes batch, xsys apart). CR_LANES lanes share a row and each
+// takes U of its entries per pass (8; 4 for the 3x3 blocks) with every load issued before the
+// first product, so a row of up to CR_LANES * U entries costs three dependent loads (row
+// start, entry, input); a shuffle reduction adds the lanes' sums.
+constexpr int CR_LANES = 4;
+template <int DOF> struct CorrUnroll { static constexpr int U = DOF == 3 ? 4 : 8; };
+
+template <int DOF>
+__global__ void k_corr_rows(int n, const int* cptr, const int* ccol, const float* cval, const double* xs, double* yc,
+                            int64_t bstride, int64_t xsys) {
+    constexpr int U = CorrUnroll<DOF>::U, NV = DOF == 3 ? 9 : 1;
+    xs += blockIdx.y * xsys;
+    yc += blockIdx.y * xsys;
+    const int i = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / CR_LANES);
+    const int sub = threadIdx.x % CR_LANES;
+    float out[DOF];
+#pragma unroll
+    for (int a = 0; a < DOF; ++a) out[a] = 0.f;
+    if (i < n) {
+        const int e1 = cptr[i + 1];
+        for (int eb = cptr[i] + sub; eb < e1; eb += CR_LANES * U) {
+            int j[U];
+            float c[U][NV];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int e = eb + CR_LANES * u;
+                j[u] = e < e1 ? ccol[e] : -1;
+#pragma unroll
+                for (int v = 0; v < NV; ++v) c[u][v] = e < e1 ? cval[(int64_t)NV * e + v] : 0.f;
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                if (j[u] < 0) continue;
+                if (DOF == 1) {
+                    out[0] = fmaf(c[u][0], (float)xs[j[u]], out[0]);
+                } else if (DOF == 4) {
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) out[q] = fmaf(c[u][0], (float)xs[q * bstride + j[u]], out[q]);
+                } else {
+                    const float x0 = (float)xs[3 * j[u]], x1 = (float)xs[3 * j[u] + 1], x2 = (float)xs[3 * j[u] + 2];
+#pragma unroll
+                    for (int a = 0; a < 3; ++a)
+                        out[a] = fmaf(c[u][3 * a], x0, fmaf(c[u][3 * a + 1], x1, fmaf(c[u][3 * a + 2], x2, out[a])));
+                }
+            }
+        }
+    }
+    // every lane of the warp takes part (blockDim is a multiple of 32); rows past n add zeros
+#pragma unroll
+    for (int o = CR_LANES / 2; o >= 1; o >>= 1)
+#pragma unroll
+        for (int a = 0; a < DOF; ++a) out[a] += __shfl_xor_sync(0xffffffffu, out[a], o, CR_LANES);
+    if (i < n && sub == 0)
+#pragma unroll
+        for (int a = 0; a < DOF; ++a) yc[(int64_t)DOF * i + a] = (double)out[a];
+}
+
 // Near field: one block per target leaf. In FP32 the operands are leaf-relative:
 // target offsets from its leaf centre, source offsets from theirs, and the
 // leaf-to-leaf shift (FP64 difference of the centres) is added while staging, so
@@ -661,6 +722,26 @@ constexpr int PS_EMAX = 64;   // pair records per shared-memory chunk
 constexpr int PS_FOLD = 8;    // rounds between folds (32 terms per lane and target)
 static_assert(PS_TMAX <= 32, "the epilogue gives each target of a block one lane per warp");
 
+// Positions base + 32 h + lane (h < NS) of a warp's source stream (woff: the stream offsets of
+// the staged pair records, woff[ne] = s_end): rec[h] = the record holding position h (-1 past
+// the stream end) and g[h] = the position's offset inside that record's sources. The lane's
+// cursor only moves forward; the caller issues the loads.
+template <int NS>
+__device__ __forceinline__ void stream_slots(int base, int lane, int s_end, const int* woff, int& cur, int (&rec)[NS],
+                                             int (&g)[NS]) {
+#pragma unroll
+    for (int h = 0; h < NS; ++h) {
+        const int pos = base + 32 * h + lane;
+        rec[h] = -1;
+        g[h] = 0;
+        if (pos < s_end) {
+            while (woff[cur + 1] <= pos) ++cur;
+            rec[h] = cur;
+            g[h] = pos - woff[cur];
+        }
+    }
+}
+
 // Pair records are staged per warp, so the warps of a block never wait for one another
 // between the target load and the epilogue. Targets are stored in pairs: (x_a, x_b, y_a, y_b)
 // and (z_a, z_b).
@@ -769,8 +850,7 @@ __device__ __forceinline__ void ps_round_self(const float4* sXY, const float2* s
 __global__ void __launch_bounds__(32 * PS_WARPS, 7) k_p2p_lap_src(const int4* items, const int2* range, const int* pptr,
                                                                  const float4* prec, const int* poff, const int* plen,
                                                                  const float4* srcw, const float4* tgt, int K,
-                                                                 const int* cptr, const int* ccol, const double* cval,
-                                                                 const double* xs, double* ynear) {
+                                                                 const double* yc, double* ynear) {
     __shared__ PsShared sh;
     constexpr int RND = 32 * PS_SRC;  // stream positions per warp round
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -830,18 +910,20 @@ __global__ void __launch_bounds__(32 * PS_WARPS, 7) k_p2p_lap_src(const int4* it
             __syncwarp();
             const int s_beg = woff[0], s_end = woff[ne];
             int cur = 0;  // per-lane cursor: the pair record holding the lane's next position
+            // the records of the lane's positions first (the cursor walk), then every source
+            // load of the round back to back, so that their latencies overlap
             auto fetch = [&](int base, PsSrc (&u)[PS_SRC]) {
+                int rec[PS_SRC], g[PS_SRC];
+                stream_slots<PS_SRC>(base, lane, s_end, woff, cur, rec, g);
+                float4 rc[PS_SRC], v[PS_SRC];
+#pragma unroll
+                for (int h = 0; h < PS_SRC; ++h) rc[h] = wrec[max(rec[h], 0)];
+#pragma unroll
+                for (int h = 0; h < PS_SRC; ++h) v[h] = rec[h] >= 0 ? srcw[__float_as_int(rc[h].w) + g[h]] : far_src;
 #pragma unroll
                 for (int h = 0; h < PS_SRC; ++h) {
-                    const int pos = base + 32 * h + lane;
-                    float4 v = far_src;
-                    if (pos < s_end) {
-                        while (woff[cur + 1] <= pos) ++cur;
-                        const float4 rc = wrec[cur];
-                        v = srcw[__float_as_int(rc.w) + (pos - woff[cur])];
-                        v.x += rc.x; v.y += rc.y; v.z += rc.z;
-                    }
-                    u[h] = ps_src(v);
+                    if (rec[h] >= 0) { v[h].x += rc[h].x; v[h].y += rc[h].y; v[h].z += rc[h].z; }
+                    u[h] = ps_src(v[h]);
                 }
             };
             for (int base = s_beg + RND * warp; base < s_end; base += RND * PS_WARPS) {
@@ -874,9 +956,7 @@ __global__ void __launch_bounds__(32 * PS_WARPS, 7) k_p2p_lap_src(const int4* it
                 kahan_add(hi, lo, v.x);
                 kahan_add(hi, lo, -v.y);
             }
-            double out = (double)hi - (double)lo;
-            add_correction<1>(tb + i, cptr, ccol, cval, xs, &out);
-            ynear[tb + i] = out;
+            ynear[tb + i] = ((double)hi - (double)lo) + yc[tb + i];
         }
     }
 }
@@ -1002,12 +1082,11 @@ template <int OP>
 __global__ void __launch_bounds__(32 * PS_WARPS, VecLane<OP>::MINB) k_p2p_vec_src(const int4* items, const int2* range, const int* pptr,
                                                                  const float4* prec, const int* poff, const int* plen,
                                                                  const float4* srcw, const float4* tgt, int K,
-                                                                 const int* cptr, const int* ccol, const double* cval,
-                                                                 const double* xs, double* ynear, int64_t bstride,
-                                                                 int64_t ssys, int64_t xsys) {
+                                                                 const double* yc, double* ynear, int64_t ssys,
+                                                                 int64_t xsys) {
     constexpr int DOF = VecLane<OP>::DOF, TM = VecLane<OP>::TM;
-    srcw += blockIdx.y * ssys;  // vector blockIdx.y of a Stokes batch: its strengths, input and output
-    xs += blockIdx.y * xsys;
+    srcw += blockIdx.y * ssys;  // vector blockIdx.y of a Stokes batch: its strengths, corrections and output
+    yc += blockIdx.y * xsys;
     ynear += blockIdx.y * xsys;
     __shared__ VlShared<OP> sh;
     constexpr int RND = 32 * SS_SRC;
@@ -1106,19 +1185,22 @@ __global__ void __launch_bounds__(32 * PS_WARPS, VecLane<OP>::MINB) k_p2p_vec_sr
         for (int base = s_beg + RND * warp; base < s_end; base += RND * PS_WARPS) {
             VlSrc u[SS_SRC];
             int gp[SS_SRC];
+            // records first, then the round's source loads back to back (as k_p2p_lap_src)
+            int rec[SS_SRC], g[SS_SRC];
+            stream_slots<SS_SRC>(base, lane, s_end, woff, cur, rec, g);
+            float4 rc[SS_SRC], a[SS_SRC], b[SS_SRC];
+#pragma unroll
+            for (int h = 0; h < SS_SRC; ++h) rc[h] = wrec[max(rec[h], 0)];
 #pragma unroll
             for (int h = 0; h < SS_SRC; ++h) {
-                const int pos = base + 32 * h + lane;
-                float4 a = far_a, b = zero4;
-                if (pos < s_end) {
-                    while (woff[cur + 1] <= pos) ++cur;
-                    const float4 rc = wrec[cur];
-                    const int g = __float_as_int(rc.w) + (pos - woff[cur]);
-                    a = srcw[2 * g];
-                    a.x += rc.x; a.y += rc.y; a.z += rc.z;
-                    b = srcw[2 * g + 1];
-                }
-                u[h] = vl_src(a, b);
+                const int q = __float_as_int(rc[h].w) + g[h];
+                a[h] = rec[h] >= 0 ? srcw[2 * q] : far_a;
+                b[h] = rec[h] >= 0 ? srcw[2 * q + 1] : zero4;
+            }
+#pragma unroll
+            for (int h = 0; h < SS_SRC; ++h) {
+                if (rec[h] >= 0) { a[h].x += rc[h].x; a[h].y += rc[h].y; a[h].z += rc[h].z; }
+                u[h] = vl_src(a[h], b[h]);
                 gp[h] = -1;
             }
             round(u, gp, false);
@@ -1151,9 +1233,8 @@ __global__ void __launch_bounds__(32 * PS_WARPS, VecLane<OP>::MINB) k_p2p_vec_sr
             }
             out[a] = (double)hi - (double)lo;
         }
-        add_correction<DOF>(tb + i, cptr, ccol, cval, xs, out, bstride);
 #pragma unroll
-        for (int a = 0; a < DOF; ++a) ynear[DOF * (int64_t)(tb + i) + a] = out[a];
+        for (int a = 0; a < DOF; ++a) ynear[DOF * (int64_t)(tb + i) + a] = out[a] + yc[DOF * (int64_t)(tb + i) + a];
     }
 }
 
@@ -1270,24 +1351,36 @@ static int launch_items(fmmbem_handle* h) {
     const int4* it = h->p2p_items;
     const unsigned nb = (unsigned)h->n_p2p_items;
     if (nb == 0) return 0;
-    if (h->nrhs > 1 && h->kernel == FMMBEM_LAPLACE)
+    // the correction rows first, into h->ycorr; the item kernel adds one value per target
+    const int n = (int)h->N;
+    const unsigned gc = (unsigned)(((int64_t)n * CR_LANES + 255) / 256);
+    if (h->nrhs > 1 && h->kernel == FMMBEM_LAPLACE) {
+        k_corr_rows<4><<<gc, 256, 0, h->stream>>>(n, h->corr_ptr, h->corr_col, h->corr_sl_f, h->xin, h->ycorr, h->N, 0);
+        FMM_LAUNCHED();
         k_p2p_vec_src<LAP_B4><<<nb, 32 * PS_WARPS, 0, h->stream>>>(it, h->cell_range, h->p2p_ptr, h->p2p_rec, h->p2p_off,
-                                                                   h->p2p_len, h->src_w, h->tgt_rel, h->K, h->corr_ptr,
-                                                                   h->corr_col, h->corr_sl, h->xin, h->ynear, h->N, 0, 0);
-    else if (h->kernel == FMMBEM_LAPLACE && h->layer == FMMBEM_LAYER_DOUBLE)
+                                                                   h->p2p_len, h->src_w, h->tgt_rel, h->K, h->ycorr,
+                                                                   h->ynear, 0, 0);
+    } else if (h->kernel == FMMBEM_LAPLACE && h->layer == FMMBEM_LAYER_DOUBLE) {
+        k_corr_rows<1><<<gc, 256, 0, h->stream>>>(n, h->corr_ptr, h->corr_col, h->corr_dl_f, h->xin, h->ycorr, 0, 0);
+        FMM_LAUNCHED();
         k_p2p_vec_src<LAP_DL><<<nb, 32 * PS_WARPS, 0, h->stream>>>(it, h->cell_range, h->p2p_ptr, h->p2p_rec, h->p2p_off,
-                                                                   h->p2p_len, h->src_w, h->tgt_rel, h->K, h->corr_ptr,
-                                                                   h->corr_col, h->corr_dl, h->xin, h->ynear, 0, 0, 0);
-    else if (h->kernel == FMMBEM_LAPLACE)
+                                                                   h->p2p_len, h->src_w, h->tgt_rel, h->K, h->ycorr,
+                                                                   h->ynear, 0, 0);
+    } else if (h->kernel == FMMBEM_LAPLACE) {
+        k_corr_rows<1><<<gc, 256, 0, h->stream>>>(n, h->corr_ptr, h->corr_col, h->corr_sl_f, h->xin, h->ycorr, 0, 0);
+        FMM_LAUNCHED();
         k_p2p_lap_src<<<nb, 32 * PS_WARPS, 0, h->stream>>>(it, h->cell_range, h->p2p_ptr, h->p2p_rec, h->p2p_off,
-                                                          h->p2p_len, h->src_w, h->tgt_rel, h->K, h->corr_ptr,
-                                                          h->corr_col, h->corr_sl, h->xin, h->ynear);
-    else  // the Stokeslet: one launch for every vector of a batch (blockIdx.y)
+                                                          h->p2p_len, h->src_w, h->tgt_rel, h->K, h->ycorr, h->ynear);
+    } else {  // the Stokeslet: one launch for every vector of a batch (blockIdx.y)
+        k_corr_rows<3><<<dim3(gc, h->nsys), 256, 0, h->stream>>>(n, h->corr_ptr, h->corr_col, h->corr_sl_f, h->xin,
+                                                                 h->ycorr, 0, 3 * h->N);
+        FMM_LAUNCHED();
         k_p2p_vec_src<STK_SL><<<dim3(nb, h->nsys), 32 * PS_WARPS, 0, h->stream>>>(
-            it, h->cell_range, h->p2p_ptr, h->p2p_rec, h->p2p_off, h->p2p_len, h->src_w, h->tgt_rel, h->K, h->corr_ptr,
-            h->corr_col, h->corr_sl, h->xin, h->ynear, 0, 2 * h->NS, 3 * h->N);
+            it, h->cell_range, h->p2p_ptr, h->p2p_rec, h->p2p_off, h->p2p_len, h->src_w, h->tgt_rel, h->K, h->ycorr,
+            h->ynear, 2 * h->NS, 3 * h->N);
+    }
     FMM_LAUNCHED();
-    h->launches += 1;
+    h->launches += 2;
     return 0;
 }
 

@@ -605,6 +605,12 @@ __device__ void rule_sums(const double* P, const double4 nj, const double* c, co
     }
 }
 
+// Round FP64 values to FP32 (the mixed-precision correction pass reads the rounded table).
+__global__ void k_round_f32(const double* in, int64_t n, float* out) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+        out[e] = (float)in[e];
+}
+
 // Correction entries: self -> analytic single layer (double layer 0); near ->
 // (20-point rule) - (K-point rule), so that P2P's K-point sum plus the entry gives
 // the accurate integral.
@@ -1091,6 +1097,14 @@ int build_geometry_tree_lists(fmmbem_handle* h, const fmmbem_mesh* mesh) {
             k_corrections<<<(unsigned)((nnz + 127) / 128), 128, 0, st>>>(nnz, row, h->corr_col, h->tgt_d, h->nrm_d,
                                                                        h->verts, quad, K, quad + 4 * K, nq, stokes,
                                                                        h->corr_sl, h->corr_dl);
+            FMM_LAUNCHED();
+        }
+        FMM_TRY(dalloc(&h->corr_sl_f, (int64_t)per * nnz));
+        FMM_TRY(dalloc(&h->corr_dl_f, (int64_t)per * nnz));
+        if (nnz > 0) {
+            const int64_t m = (int64_t)per * nnz;
+            k_round_f32<<<(unsigned)std::min<int64_t>((m + 255) / 256, 4096), 256, 0, st>>>(h->corr_sl, m, h->corr_sl_f);
+            k_round_f32<<<(unsigned)std::min<int64_t>((m + 255) / 256, 4096), 256, 0, st>>>(h->corr_dl, m, h->corr_dl_f);
             FMM_LAUNCHED();
         }
         FMM_CU(cudaStreamSynchronize(st));

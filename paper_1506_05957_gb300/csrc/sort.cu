@@ -247,3 +247,36 @@ int exclusive_scan(const int* in, int* out, int64_t n, cudaStream_t st) { return
 int inclusive_scan(const int* in, int* out, int64_t n, cudaStream_t st) { return scan_i32(in, out, n, true, st); }
 
 }  // namespace fmmbem
+
+// The exported forms (stream-ordered scratch on the caller's stream; arguments checked first).
+extern "C" int fmmbem_sort_pairs_u64(const uint64_t* keys_in, uint64_t* keys_out, const int32_t* vals_in,
+                                     int32_t* vals_out, int64_t n, int end_bit, void* stream) {
+    if (n < 0 || end_bit < 0 || end_bit > 64 || (n > 0 && (!keys_in || !keys_out)) || ((vals_in == nullptr) != (vals_out == nullptr)) ||
+        (n > 0 && (keys_in == keys_out || (vals_in && vals_in == vals_out)))) {
+        fmmbem_set_error("sort_pairs_u64: need n >= 0, 0 <= end_bit <= 64, distinct input and output buffers, both or neither value buffer");
+        return FMMBEM_EINVAL;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaStream_t keep = fmm_alloc_stream();
+    fmm_alloc_stream() = st;
+    const int rc = fmmbem::radix_sort(keys_in, keys_out, vals_in, vals_out, n, end_bit, st);
+    fmm_alloc_stream() = keep;
+    return rc;
+}
+
+extern "C" int fmmbem_scan_i32(const int32_t* in, int32_t* out, int64_t n, int inclusive, void* stream) {
+    if (n < 0 || (n > 0 && (!in || !out))) {
+        fmmbem_set_error("scan_i32: need n >= 0 and device buffers");
+        return FMMBEM_EINVAL;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaStream_t keep = fmm_alloc_stream();
+    fmm_alloc_stream() = st;
+    int rc = inclusive ? fmmbem::inclusive_scan(in, out, n, st) : fmmbem::exclusive_scan(in, out, n, st);
+    if (rc == 0 && cudaStreamSynchronize(st) != cudaSuccess) {
+        fmmbem_set_error("scan_i32: %s", cudaGetErrorString(cudaGetLastError()));
+        rc = FMMBEM_EDEVICE;
+    }
+    fmm_alloc_stream() = keep;
+    return rc;
+}
