@@ -387,8 +387,9 @@ typedef struct {
     int64_t n_p2p_interactions;   /* sum over P2P pairs of targets x Gauss points */
     int64_t n_corrections;        /* entries of the near-singular/self correction table */
     int64_t n_m2l_tables;         /* distinct M2L operators (0: gather form only) */
-    int64_t n_m2l_tiles;          /* GEMM tiles over the M2L pairs */
+    int64_t n_m2l_tiles;          /* GEMM tiles over the M2L pairs (SIMT kernel: 64 pairs) */
     double setup_seconds;         /* wall time of fmmbem_create */
+    int64_t n_m2l_tiles_tc;       /* tensor-core tiles over the M2L pairs (128 rows) */
 } fmmbem_stats;
 
 int fmmbem_get_stats(const fmmbem_handle* h, fmmbem_stats* out);

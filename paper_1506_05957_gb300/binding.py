@@ -56,7 +56,7 @@ class fmmbem_stats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int64) for n in ("n_panels", "n_sources", "n_cells", "n_leaves", "n_levels",
                                                "n_m2l_pairs", "n_m2l_same_level", "n_p2p_pairs",
                                                "n_p2p_interactions", "n_corrections", "n_m2l_tables", "n_m2l_tiles")] + \
-               [("setup_seconds", ctypes.c_double)]
+               [("setup_seconds", ctypes.c_double), ("n_m2l_tiles_tc", ctypes.c_int64)]
 
 
 class fmmbem_profile(ctypes.Structure):

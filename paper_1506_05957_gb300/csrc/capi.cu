@@ -852,6 +852,7 @@ int fmmbem_get_stats(const fmmbem_handle* h, fmmbem_stats* s) {
     s->n_m2l_tables = h->n_tables;
     s->n_m2l_tiles = h->n_tiles;
     s->setup_seconds = h->setup_seconds;
+    s->n_m2l_tiles_tc = h->n_tiles_tc;
     return 0;
 }
 

@@ -182,6 +182,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_m2l_tc(int p, int prods, cons
     extern __shared__ __align__(1024) unsigned char smem[];
     const TcLayout lay = tc_layout(p, KC);
     const int R = 2 * ncoef(p);
+    const int R8 = (R + 7) & ~7;  // K extent the MMAs read: k-steps of 8 that start below R
     const int Np = lay.np, NST = lay.nst, NB = lay.nb;
     const int nch = (R + KC - 1) / KC;
     const uint32_t chunk_bytes = (uint32_t)Np * KC * 4;
@@ -303,6 +304,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_m2l_tc(int p, int prods, cons
                 const uint32_t acc = taddr + (uint32_t)b * buf_cols;
                 const uint32_t ah = smem_u32(xh(st)), al = smem_u32(xl(st)), bh = smem_u32(th(st)), bl = smem_u32(tl(st));
                 for (int ks = 0; ks < KC / 8; ++ks) {
+                    if (c * KC + 8 * ks >= R) break;  // the rest of the chunk lies past degree p
                     const uint32_t off = 256u * ks;
                     const uint64_t a_hi = smem_desc(ah + off, 128, Kc<KC>::SBO), b_hi = smem_desc(bh + off, 128, Kc<KC>::SBO);
                     const uint32_t first = (c == 0 && ks == 0) ? 0u : 1u;
@@ -339,47 +341,49 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_m2l_tc(int p, int prods, cons
         // ---------------- gather producers: rows 16 pw + 8 h + (lane & 7), k-quads (lane >> 3) + 4 e.
         // Software pipeline over three register slots (the loop is unrolled by three so the
         // slot indices are constants): while item i is stored from slot i % 3, the inputs of
-        // item i + 1 are in flight in slot (i + 1) % 3, the inputs of item i + 2 are issued into
-        // slot (i + 2) % 3 from its row tables (loaded one item earlier), and the row tables
-        // of item i + 3 then go into the freed slot i % 3. Item counters (tile, chunk, stage,
-        // phase) advance incrementally; signs and the order-p mask come from the CTA's tables.
+        // item i + 2 are issued into slot (i + 2) % 3. A row table belongs to a tile, not to an
+        // item: each lane keeps its two rows' entries for the tiles j .. j + 3 in registers (ti[0]
+        // = tile j of item i; item i + 2 lies at most two tiles ahead) and loads those of tile
+        // j + 3 when item i starts tile j, a whole tile before the gathers that use them. Item counters (tile,
+        // chunk, stage, phase) advance incrementally; signs and the order-p mask come from the
+        // CTA's tables.
         const int pw = warp - TC_PROD0, r7 = lane & 7, kq0 = lane >> 3;
         const int row0 = 16 * pw + r7;
         float4 d[3][2][Kc<KC>::E];
-        int f[3][2];
+        int ti[4][2];
         struct Ctr {
             int j, c;
             __device__ void next(int nch_) { if (++c == nch_) { c = 0; ++j; } }
         };
-        auto load_info = [&](const Ctr& t, int (&info)[2]) {
+        auto load_info = [&](int j, int (&info)[2]) {
 #pragma unroll
             for (int h = 0; h < 2; ++h)
-                info[h] = t.j < my_tiles ? src_info[(size_t)tile_of(t.j) * TC_ROWS + row0 + 8 * h] : -1;
+                info[h] = j < my_tiles ? src_info[(size_t)tile_of(j) * TC_ROWS + row0 + 8 * h] : -1;
         };
-        auto load_data = [&](const Ctr& t, const int (&info)[2], float4 (&v)[2][Kc<KC>::E]) {
+        // the row entries of tile t.j, which lies dj = t.j - (tile of item i) in {0, 1, 2} tiles ahead
+        auto load_data = [&](const Ctr& t, int dj, float4 (&v)[2][Kc<KC>::E]) {
 #pragma unroll
-            for (int h = 0; h < 2; ++h)
+            for (int h = 0; h < 2; ++h) {
+                const int info = dj == 0 ? ti[0][h] : (dj == 1 ? ti[1][h] : ti[2][h]);
 #pragma unroll
                 for (int e = 0; e < Kc<KC>::E; ++e) {
                     const int k = t.c * KC + 4 * (kq0 + 4 * e);
-                    v[h][e] = (t.j < my_tiles && info[h] >= 0)
-                                  ? *reinterpret_cast<const float4*>(M + (size_t)(info[h] >> 3) + k)
+                    v[h][e] = (t.j < my_tiles && info >= 0 && k < R)
+                                  ? *reinterpret_cast<const float4*>(M + (size_t)(info >> 3) + k)
                                   : make_float4(0.f, 0.f, 0.f, 0.f);
                 }
+            }
         };
-        Ctr ci{0, 0}, c2{0, 0}, c3{0, 0};  // items i, i + 2, i + 3
-        load_info(c2, f[0]);
-        c2.next(nch);
-        load_info(c2, f[1]);
-        c2.next(nch);
-        load_info(c2, f[2]);
-        c3 = c2;
-        c3.next(nch);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) load_info(q, ti[q]);
+        Ctr ci{0, 0}, c2{0, 0};  // items i and i + 2
         {
-            Ctr c0{0, 0}, c1{0, 0};
+            Ctr c1{0, 0};
             c1.next(nch);
-            load_data(c0, f[0], d[0]);
-            load_data(c1, f[1], d[1]);
+            load_data(ci, 0, d[0]);
+            load_data(c1, c1.j, d[1]);
+            c2 = c1;
+            c2.next(nch);
         }
         int st = 0, ph = 0;  // stage of item i and the number of earlier uses of that stage
         bool stop = false;
@@ -389,7 +393,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_m2l_tc(int p, int prods, cons
                 const int i = base + u;
                 if (i >= n_items || stop) break;
                 const int sa = u, sc = (u + 2) % 3;
-                load_data(c2, f[sc], d[sc]);
+                load_data(c2, c2.j - ci.j, d[sc]);
                 // warp-uniform decisions: the warp's lanes take every branch together
                 const bool okw = ph == 0 || mbar_wait_ab(empty(st), (uint32_t)((ph - 1) & 1), abort_flag);
                 if (!__all_sync(0xffffffffu, okw)) {
@@ -403,12 +407,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_m2l_tc(int p, int prods, cons
 #pragma unroll
                 for (int e = 0; e < Kc<KC>::E; ++e) {
                     const int kq = 4 * (kq0 + 4 * e);
+                    if (ci.c * KC + kq >= R8) continue;  // past the last 8-wide k-step any MMA reads
                     const int te = ci.c * Kc<KC>::KQ + kq0 + 4 * e;
                     const uint32_t sg = sgn_tab[te], zm = zm_tab[te];
 #pragma unroll
                     for (int h = 0; h < 2; ++h) {
                         const int row = row0 + 8 * h;
-                        const float4 x = apply_zero(apply_signs(d[sa][h][e], (sg >> (4 * (f[sa][h] & 7))) & 15u), zm);
+                        const float4 x = apply_zero(apply_signs(d[sa][h][e], (sg >> (4 * (ti[0][h] & 7))) & 15u), zm);
                         const float4 hi = make_float4(tf32_hi(x.x), tf32_hi(x.y), tf32_hi(x.z), tf32_hi(x.w));
                         *reinterpret_cast<float4*>(xh_s + cm_index<KC>(row, kq)) = hi;
                         if (prods == 3)
@@ -419,10 +424,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_m2l_tc(int p, int prods, cons
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 __syncwarp();
                 if (lane == 0) mbar_arrive(full(st));
-                load_info(c3, f[sa]);
                 ci.next(nch);
                 c2.next(nch);
-                c3.next(nch);
+                if (ci.c == 0) {  // item i + 1 starts tile ci.j: shift the row tables, fetch tile ci.j + 3
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        ti[0][h] = ti[1][h];
+                        ti[1][h] = ti[2][h];
+                        ti[2][h] = ti[3][h];
+                    }
+                    load_info(ci.j + 3, ti[3]);
+                }
                 if (++st == NST) { st = 0; ++ph; }
             }
         }
@@ -434,17 +446,20 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_m2l_tc(int p, int prods, cons
         const int eg = (warp - TC_EPI0) >> 2;  // group 0 or 1
         const int quad = warp & 3;             // TMEM lane quadrant of this warp
         float* E = epi + (warp - TC_EPI0) * 32 * EPI_LD;
+        // destination row table of this warp's 32 accumulator rows, one per lane (shuffled per
+        // pass); the next tile's entries are fetched before this tile's accumulator wait
+        auto dst_of = [&](int j) { return j < my_tiles ? dst_info[(size_t)tile_of(j) * TC_ROWS + 32 * quad + lane] : -1; };
+        int next_info = eg < EG ? dst_of(eg) : -1;
         for (int j = eg; eg < EG && j < my_tiles; j += EG) {
             const int b = j % NB, u = j / NB;
+            const int my_info = next_info;
+            next_info = dst_of(j + EG);
             const bool okw = mbar_wait_ab(acc_full(b), (uint32_t)(u & 1), abort_flag);
             if (!__all_sync(0xffffffffu, okw)) {
                 if (lane == 0) fail(5);
                 break;
             }
             asm volatile("tcgen05.fence::after_thread_sync;");
-            const int t = tile_of(j);
-            // destination row table of this warp's 32 accumulator rows, one per lane, shuffled per pass
-            const int my_info = dst_info[(size_t)t * TC_ROWS + 32 * quad + lane];
             for (int cb = 0; cb < R; cb += 32) {
                 uint32_t v[32];
                 const uint32_t a = taddr + (uint32_t)b * buf_cols + ((uint32_t)(32 * quad) << 16) + (uint32_t)cb;
