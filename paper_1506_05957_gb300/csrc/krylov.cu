@@ -126,17 +126,18 @@ __device__ __forceinline__ bool grid_barrier(unsigned* count, volatile unsigned*
     return s_ok != 0;
 }
 
-// FP64 throughput is scarce on this GPU (a few FP64 operations per clock per SM), so the
-// helpers below spend about one FP64 operation per vector element and little on reductions.
+// FP64 throughput is scarce on this GPU: two FP64 operations per clock per SM, so a warp-wide
+// FP64 instruction holds its sub-partition's FP64 unit for 64 clocks. The helpers below spend
+// about one FP64 operation per vector element, keep the reductions short (one entry per
+// vector per block) and leave scalar FP64 work to a single thread.
 
-// partial[j * gridDim.x + block] = sum over the block's rows of V_j w. One warp per vector:
-// its lanes stride over the block's rows with four independent accumulators (eight loads in
-// flight per lane), then one five-level shuffle reduction per vector. With with_self the
-// vector after the last V_j is w itself (entry nv is w.w), so ||w||^2 comes from the same
-// sweep. Fixed summation order: deterministic.
-// When the block has more warps than vectors, each vector's rows are cut into ns slices
-// (one warp each) and partial holds one entry per slice: partial[(j * ns + slice) * gridDim.x
-// + block]; arn_reduce sums over slices and blocks.
+// partial[j * nbk + bk] = sum over the block's rows of V_j w. One warp per vector: its lanes
+// stride over the block's rows with four independent accumulators (eight loads in flight per
+// lane), then one five-level shuffle reduction. With with_self the vector after the last V_j
+// is w itself (entry nv is w.w), so ||w||^2 comes from the same sweep. When the block has more
+// warps than vectors, each vector's rows are cut into ns slices (one warp each) whose sums are
+// added in shared memory (sred, one double per warp) before the block writes its entry.
+// Fixed summation order: deterministic.
 __device__ __forceinline__ int arn_slices(int nt) {
     const int nw = (int)(blockDim.x >> 5);
     return nw > nt ? nw / nt : 1;
@@ -144,7 +145,7 @@ __device__ __forceinline__ int arn_slices(int nt) {
 
 // nbk, bk: the blocks that share this system and this block's index among them.
 __device__ void arn_partials(const double* V, int64_t ldv, int nv, const double* w, int64_t i0, int64_t i1,
-                             double* partial, int nbk, int bk, bool with_self = false) {
+                             double* partial, int nbk, int bk, bool with_self, double* sred) {
     const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5, nw = (int)(blockDim.x >> 5);
     const int nt = nv + (with_self ? 1 : 0);
     const int ns = arn_slices(nt);
@@ -165,7 +166,20 @@ __device__ void arn_partials(const double* V, int64_t ldv, int nv, const double*
         double t = (s0 + s1) + (s2 + s3);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-        if (lane == 0) partial[(int64_t)item * nbk + bk] = t;
+        if (ns == 1) {
+            if (lane == 0) partial[(int64_t)j * nbk + bk] = t;
+        } else if (lane == 0) {
+            sred[item] = t;
+        }
+    }
+    if (ns > 1) {
+        __syncthreads();
+        if ((int)threadIdx.x < nt) {
+            const int j = threadIdx.x;
+            double t = sred[j * ns];
+            for (int sl = 1; sl < ns; ++sl) t += sred[j * ns + sl];
+            partial[(int64_t)j * nbk + bk] = t;
+        }
     }
 }
 
@@ -173,11 +187,9 @@ __device__ void arn_partials(const double* V, int64_t ldv, int nv, const double*
 // the same hs. With sq != nullptr, *sq = sum_{j < nsq} hs[j]^2, by one warp.
 __device__ void arn_reduce(const double* partial, int nv, int nbk, double* hs, int nsq = 0, double* sq = nullptr) {
     const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
-    const int ns = arn_slices(nv);
-    const int nb = nbk * ns;  // a vector's entries are contiguous: slices x blocks
     for (int j = wp; j < nv; j += (int)(blockDim.x >> 5)) {
         double t = 0.0;
-        for (int b = lane; b < nb; b += 32) t += partial[(int64_t)j * nb + b];
+        for (int b = lane; b < nbk; b += 32) t += partial[(int64_t)j * nbk + b];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
         if (lane == 0) hs[j] = t;
@@ -255,8 +267,10 @@ __global__ void __launch_bounds__(ARN_THREADS) k_arnoldi(double* V, int64_t n, i
     // a block's w rows are read and written by that block alone
     double* vk1 = V + (int64_t)(k + 1) * n;
     // phase 1: h = V^T w and ||w||^2
-    __shared__ double s_sq;
-    arn_partials(V, n, nv, w, i0, i1, partial, nbk, bk, true);
+    __shared__ double s_sq, s_scale;
+    __shared__ int s_direct;
+    __shared__ double sred[ARN_THREADS / 32];
+    arn_partials(V, n, nv, w, i0, i1, partial, nbk, bk, true, sred);
     // a barrier that gives up marks the step's norm NaN in the output: the host stops there
     // and reports the flag set in err
     if (!grid_barrier(bar_count, bar_gen, (unsigned)nbk, err, wait_limit)) {
@@ -264,16 +278,21 @@ __global__ void __launch_bounds__(ARN_THREADS) k_arnoldi(double* V, int64_t n, i
         return;
     }
     arn_reduce(partial, nv + 1, nbk, hs, nv, &s_sq);
-    const double ww = hs[nv];
-    const double nn2 = ww - s_sq;
+    // the scalar decisions in FP64 by one thread, broadcast through shared memory
+    if (threadIdx.x == 0) {
+        const double ww = hs[nv];
+        const double nn2 = ww - s_sq;
+        s_direct = nn2 > 0.5 * ww && nn2 > 0.0 && isfinite(nn2);
+        s_scale = s_direct ? 1.0 / sqrt(nn2) : 0.0;
+        if (bk == 0 && s_direct) out[2 * (ARN_MAXV + 1)] = nn2;
+    }
+    __syncthreads();
     if (bk == 0)
         for (int j = threadIdx.x; j < nv; j += blockDim.x) out[j] = hs[j];
-    if (nn2 > 0.5 * ww && nn2 > 0.0 && isfinite(nn2)) {
-        if (bk == 0) {
+    if (s_direct) {
+        if (bk == 0)
             for (int j = threadIdx.x; j < nv; j += blockDim.x) out[(ARN_MAXV + 1) + j] = 0.0;
-            if (threadIdx.x == 0) out[2 * (ARN_MAXV + 1)] = nn2;
-        }
-        arn_update(V, n, nv, hs, w, i0, i1, 1.0 / sqrt(nn2), vk1, xfix);
+        arn_update(V, n, nv, hs, w, i0, i1, s_scale, vk1, xfix);
         return;
     }
     // phase 2: reorthogonalize. The sweep that projects w1 = w - V h1 again also gives
@@ -285,21 +304,25 @@ __global__ void __launch_bounds__(ARN_THREADS) k_arnoldi(double* V, int64_t n, i
     arn_update(V, n, nv, h1, w, i0, i1, 0.0, nullptr, nullptr);
     __syncthreads();  // arn_partials reads rows of w that other threads of the block updated
     double* part2 = partial + parea;
-    arn_partials(V, n, nv, w, i0, i1, part2, nbk, bk, true);
+    arn_partials(V, n, nv, w, i0, i1, part2, nbk, bk, true, sred);
     if (!grid_barrier(bar_count, bar_gen, (unsigned)nbk, err, wait_limit)) {
         if (threadIdx.x == 0) out[2 * (ARN_MAXV + 1)] = __longlong_as_double(0x7ff8000000000000ll);
         return;
     }
     arn_reduce(part2, nv + 1, nbk, hs, nv, &s_sq);
-    const double w1w1 = hs[nv];
-    const double nrm2 = fmax(w1w1 - s_sq, 0.0);  // rounding below zero: w1 lies in the span (breakdown)
-    if (bk == 0) {
-        for (int j = threadIdx.x; j < nv; j += blockDim.x) out[(ARN_MAXV + 1) + j] = hs[j];
-        if (threadIdx.x == 0) out[2 * (ARN_MAXV + 1)] = nrm2;
+    if (threadIdx.x == 0) {
+        const double w1w1 = hs[nv];
+        const double nrm2 = fmax(w1w1 - s_sq, 0.0);  // rounding below zero: w1 lies in the span (breakdown)
+        const double hn = sqrt(nrm2);
+        s_direct = hn > 0.0 && isfinite(hn);
+        s_scale = s_direct ? 1.0 / hn : 0.0;
+        if (bk == 0) out[2 * (ARN_MAXV + 1)] = nrm2;
     }
-    const double hn = sqrt(nrm2);
-    if (hn > 0.0 && isfinite(hn)) {
-        arn_update(V, n, nv, hs, w, i0, i1, 1.0 / hn, vk1, xfix);
+    __syncthreads();
+    if (bk == 0)
+        for (int j = threadIdx.x; j < nv; j += blockDim.x) out[(ARN_MAXV + 1) + j] = hs[j];
+    if (s_direct) {
+        arn_update(V, n, nv, hs, w, i0, i1, s_scale, vk1, xfix);
     } else {
         arn_update(V, n, nv, hs, w, i0, i1, 0.0, nullptr, nullptr);
     }

@@ -72,19 +72,20 @@ __global__ void k_tc_tables(const double* Td, int ntab, int nr, int ld, int nch,
     }
 }
 
-// Persistent and warp-specialized: one CTA per SM takes tiles blockIdx.x, blockIdx.x +
-// gridDim.x, ...; its work items are (tile, K chunk) pairs in that order. Roles:
+// Persistent and warp-specialized: one CTA per SM takes work units blockIdx.x, blockIdx.x +
+// gridDim.x, ... (a unit is a tile, or with split-K a range of its K chunks); its work items
+// are (unit, K chunk) pairs in that order. Roles:
 //   warp 0      : bulk-copies the operator chunk of item i into smem stage i % NST;
-//   warp 1      : issues the MMAs of item i into TMEM accumulator (tile) % NB and commits;
+//   warp 1      : issues the MMAs of item i into TMEM accumulator (unit) % NB and commits;
 //   warps 2-9   : gather producers; each stages 16 rows of every item (rows of the
 //                 tile's pairs, reflection signs applied, split into TF32 hi/lo),
 //                 keeping the loads of the next item in flight while storing this one;
 //   warps 10-17 : two epilogue groups of four (one per TMEM lane quadrant); group g
-//                 drains the accumulators of tiles j = g mod 2 (all tiles by group 0
+//                 drains the accumulators of units j = g mod 2 (all units by group 0
 //                 when there is one accumulator) through a padded smem transpose into
 //                 row-contiguous float4 atomics.
 // mbarriers: full[s] (8 producer arrivals + the copy's transaction bytes), empty[s]
-// (MMA commit), acc_full[b] (commit after a tile's last chunk), acc_empty[b] (the
+// (MMA commit), acc_full[b] (commit after a unit's last chunk), acc_empty[b] (the
 // four warps of the draining group). Use k of a barrier completes phase k; a role
 // waits on phase k only before the use k + 1 that it gates can begin, so parities
 // never alias. Every wait is bounded: on timeout the CTA records an error code,
@@ -174,8 +175,8 @@ __device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
 
 // rinfo[t * 128 + r] = (row offset of pair row r of tile t in the expansion array) * 8 + reflection,
 // -1 past the tile's rows; one table for the sources (gather) and one for the targets (epilogue).
-template <int KC>
-__global__ void __launch_bounds__(TC_THREADS, 1) k_m2l_tc(int p, int prods, const int4* tiles, int ntiles,
+template <int KC, bool SPLIT>
+__global__ void __launch_bounds__(TC_THREADS, 1) k_m2l_tc(int p, int prods, const int4* tiles, int ntiles, int ksplit_arg,
                                                          const int* src_info, const int* dst_info, const float* tab,
                                                          size_t tab_stride, int rows_max, const float* M, float* L,
                                                          int* err) {
@@ -234,9 +235,21 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_m2l_tc(int p, int prods, cons
     asm volatile("tcgen05.fence::after_thread_sync;");
     const uint32_t taddr = *taddr_slot;
     const uint32_t buf_cols = (uint32_t)(512 / NB);
-    const int my_tiles = (int)blockIdx.x < ntiles ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
-    const int n_items = my_tiles * nch;
-    auto tile_of = [&](int j) { return (int)blockIdx.x + j * (int)gridDim.x; };
+    // Work units are (tile, range of K chunks): the nch chunks of a tile are cut into ksplit
+    // ranges (split-K for launches with fewer tiles than SMs; the epilogue adds each range's
+    // partial product like any other). Unit u covers tile u / ksplit, range u mod ksplit; the
+    // CTA takes units blockIdx.x, blockIdx.x + gridDim.x, ... and its items are (unit, chunk).
+    const int ksplit = SPLIT ? ksplit_arg : 1;  // the unsplit kernel has none of the unit arithmetic
+    const int nunits = ntiles * ksplit;
+    const int my_units = (int)blockIdx.x < nunits ? (nunits - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+    auto unit_of = [&](int j) { return (int)blockIdx.x + j * (int)gridDim.x; };
+    // (the divisions only run with split-K, and only when a role moves to its next unit)
+    auto tile_of = [&](int j) { return ksplit == 1 ? unit_of(j) : unit_of(j) / ksplit; };
+    auto c_begin = [&](int j) { return ksplit == 1 ? 0 : (unit_of(j) % ksplit) * nch / ksplit; };
+    auto c_end = [&](int j) { return ksplit == 1 ? nch : (unit_of(j) % ksplit + 1) * nch / ksplit; };
+    int n_items = ksplit == 1 ? my_units * nch : 0;
+    if (ksplit > 1)
+        for (int j = 0; j < my_units; ++j) n_items += c_end(j) - c_begin(j);
     auto fail = [&](int code) {
         atomicExch(err, code);
         *abort_flag = 1;
@@ -246,18 +259,18 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_m2l_tc(int p, int prods, cons
     if (warp == 0) {
         // ---------------- operator copies
         if (lane == 0) {
-            // the tile record of the next tile is loaded one tile ahead, and the next tile's
-            // operator chunks are prefetched into L2 when this tile starts, so neither the
+            // the tile record of the next unit is loaded one unit ahead, and the next unit's
+            // operator chunks are prefetched into L2 when this unit starts, so neither the
             // record load nor a DRAM miss sits between a free stage and its refill
             const uint32_t bytes = prods == 3 ? 2 * chunk_bytes : chunk_bytes;
-            int4 tile = my_tiles > 0 ? tiles[tile_of(0)] : make_int4(0, 0, 0, 0);
-            int4 next_tile = my_tiles > 1 ? tiles[tile_of(1)] : tile;
-            int4 next2_tile = my_tiles > 2 ? tiles[tile_of(2)] : next_tile;
-            int c = 0, st = 0, k = 0, j = 0;
+            int4 tile = my_units > 0 ? tiles[tile_of(0)] : make_int4(0, 0, 0, 0);
+            int4 next_tile = my_units > 1 ? tiles[tile_of(1)] : tile;
+            int4 next2_tile = my_units > 2 ? tiles[tile_of(2)] : next_tile;
+            int c0 = c_begin(0), c1 = c_end(0), c = c0, st = 0, k = 0, j = 0;
             for (int i = 0; i < n_items; ++i) {
-                if (c == 0 && j + 1 < my_tiles) {
+                if (c == c0 && j + 1 < my_units) {
                     const float* nt = tab + (size_t)next_tile.x * tab_stride;
-                    for (int cc = 0; cc < nch; ++cc) {
+                    for (int cc = c_begin(j + 1); cc < c_end(j + 1); ++cc) {
                         const float* q = nt + (size_t)cc * 2 * rows_max * KC;
                         asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(q), "r"(chunk_bytes) : "memory");
                         if (prods == 3)
@@ -281,12 +294,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_m2l_tc(int p, int prods, cons
                                  : "memory");
                 issued_tma = i + 1;
                 if (++st == NST) { st = 0; ++k; }
-                if (++c == nch) {
-                    c = 0;
+                if (++c == c1) {
                     ++j;
+                    c0 = c_begin(j);
+                    c1 = c_end(j);
+                    c = c0;
                     tile = next_tile;
                     next_tile = next2_tile;
-                    if (j + 2 < my_tiles) next2_tile = tiles[tile_of(j + 2)];
+                    if (j + 2 < my_units) next2_tile = tiles[tile_of(j + 2)];
                 }
             }
         }
@@ -296,9 +311,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_m2l_tc(int p, int prods, cons
             const int n1 = Np <= 256 ? Np : 256;
             const uint32_t id1 = idesc_tf32(TC_ROWS, n1);
             const uint32_t id2 = Np > 256 ? idesc_tf32(TC_ROWS, Np - 256) : 0u;
-            int st = 0, k = 0, c = 0, b = 0, u = 0;  // stage, stage use, chunk, accumulator, accumulator use
+            // stage, stage use, unit, chunk and the unit's chunk range, accumulator, accumulator use
+            int st = 0, k = 0, j = 0, c0 = c_begin(0), c1 = c_end(0), c = c0, b = 0, u = 0;
             for (int i = 0; i < n_items; ++i) {
-                if (c == 0 && u > 0 && !mbar_wait_ab(acc_empty(b), (uint32_t)((u - 1) & 1), abort_flag)) { fail(3); break; }
+                if (c == c0 && u > 0 && !mbar_wait_ab(acc_empty(b), (uint32_t)((u - 1) & 1), abort_flag)) { fail(3); break; }
                 if (!mbar_wait_ab(full(st), (uint32_t)(k & 1), abort_flag)) { fail(4); break; }
                 asm volatile("tcgen05.fence::after_thread_sync;");
                 const uint32_t acc = taddr + (uint32_t)b * buf_cols;
@@ -307,7 +323,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_m2l_tc(int p, int prods, cons
                     if (c * KC + 8 * ks >= R) break;  // the rest of the chunk lies past degree p
                     const uint32_t off = 256u * ks;
                     const uint64_t a_hi = smem_desc(ah + off, 128, Kc<KC>::SBO), b_hi = smem_desc(bh + off, 128, Kc<KC>::SBO);
-                    const uint32_t first = (c == 0 && ks == 0) ? 0u : 1u;
+                    const uint32_t first = (c == c0 && ks == 0) ? 0u : 1u;
                     mma_tf32(acc, a_hi, b_hi, id1, first);
                     if (prods == 3) {
                         mma_tf32(acc, a_hi, smem_desc(bl + off, 128, Kc<KC>::SBO), id1, 1u);
@@ -325,14 +341,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_m2l_tc(int p, int prods, cons
                 }
                 asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(empty(st))
                              : "memory");
-                if (c == nch - 1)
+                if (c == c1 - 1)
                     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                                      acc_full(b))
                                  : "memory");
                 issued_mma = i + 1;
                 if (++st == NST) { st = 0; ++k; }
-                if (++c == nch) {
-                    c = 0;
+                if (++c == c1) {
+                    ++j;
+                    c0 = c_begin(j);
+                    c1 = c_end(j);
+                    c = c0;
                     if (++b == NB) { b = 0; ++u; }
                 }
             }
@@ -341,24 +360,31 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_m2l_tc(int p, int prods, cons
         // ---------------- gather producers: rows 16 pw + 8 h + (lane & 7), k-quads (lane >> 3) + 4 e.
         // Software pipeline over three register slots (the loop is unrolled by three so the
         // slot indices are constants): while item i is stored from slot i % 3, the inputs of
-        // item i + 2 are issued into slot (i + 2) % 3. A row table belongs to a tile, not to an
-        // item: each lane keeps its two rows' entries for the tiles j .. j + 3 in registers (ti[0]
-        // = tile j of item i; item i + 2 lies at most two tiles ahead) and loads those of tile
-        // j + 3 when item i starts tile j, a whole tile before the gathers that use them. Item counters (tile,
-        // chunk, stage, phase) advance incrementally; signs and the order-p mask come from the
-        // CTA's tables.
+        // item i + 2 are issued into slot (i + 2) % 3. A row table belongs to a unit's tile, not
+        // to an item: each lane keeps its two rows' entries for the units j .. j + 3 in registers
+        // (ti[0] = unit j of item i; item i + 2 lies at most two units ahead) and loads those of
+        // unit j + 3 when item i starts unit j, a whole unit before the gathers that use them.
+        // Item counters (unit, chunk, stage, phase) advance incrementally; signs and the order-p
+        // mask come from the CTA's tables.
         const int pw = warp - TC_PROD0, r7 = lane & 7, kq0 = lane >> 3;
         const int row0 = 16 * pw + r7;
         float4 d[3][2][Kc<KC>::E];
         int ti[4][2];
         struct Ctr {
-            int j, c;
-            __device__ void next(int nch_) { if (++c == nch_) { c = 0; ++j; } }
+            int j, c, c1;  // unit, chunk, end of the unit's chunk range
+        };
+        // next item; true when it starts a new unit
+        auto adv = [&](Ctr& t) {
+            if (++t.c < t.c1) return false;
+            ++t.j;
+            t.c = c_begin(t.j);
+            t.c1 = c_end(t.j);
+            return true;
         };
         auto load_info = [&](int j, int (&info)[2]) {
 #pragma unroll
             for (int h = 0; h < 2; ++h)
-                info[h] = j < my_tiles ? src_info[(size_t)tile_of(j) * TC_ROWS + row0 + 8 * h] : -1;
+                info[h] = j < my_units ? src_info[(size_t)tile_of(j) * TC_ROWS + row0 + 8 * h] : -1;
         };
         // the row entries of tile t.j, which lies dj = t.j - (tile of item i) in {0, 1, 2} tiles ahead
         auto load_data = [&](const Ctr& t, int dj, float4 (&v)[2][Kc<KC>::E]) {
@@ -368,7 +394,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_m2l_tc(int p, int prods, cons
 #pragma unroll
                 for (int e = 0; e < Kc<KC>::E; ++e) {
                     const int k = t.c * KC + 4 * (kq0 + 4 * e);
-                    v[h][e] = (t.j < my_tiles && info >= 0 && k < R)
+                    v[h][e] = (t.j < my_units && info >= 0 && k < R)
                                   ? *reinterpret_cast<const float4*>(M + (size_t)(info >> 3) + k)
                                   : make_float4(0.f, 0.f, 0.f, 0.f);
                 }
@@ -376,14 +402,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_m2l_tc(int p, int prods, cons
         };
 #pragma unroll
         for (int q = 0; q < 4; ++q) load_info(q, ti[q]);
-        Ctr ci{0, 0}, c2{0, 0};  // items i and i + 2
+        Ctr ci{0, c_begin(0), c_end(0)};  // item i
+        Ctr c2 = ci;            // item i + 2
         {
-            Ctr c1{0, 0};
-            c1.next(nch);
+            Ctr c1 = ci;
+            adv(c1);
             load_data(ci, 0, d[0]);
             load_data(c1, c1.j, d[1]);
             c2 = c1;
-            c2.next(nch);
+            adv(c2);
         }
         int st = 0, ph = 0;  // stage of item i and the number of earlier uses of that stage
         bool stop = false;
@@ -424,9 +451,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_m2l_tc(int p, int prods, cons
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 __syncwarp();
                 if (lane == 0) mbar_arrive(full(st));
-                ci.next(nch);
-                c2.next(nch);
-                if (ci.c == 0) {  // item i + 1 starts tile ci.j: shift the row tables, fetch tile ci.j + 3
+                const bool new_unit = adv(ci);
+                adv(c2);
+                if (new_unit) {  // item i + 1 starts unit ci.j: shift the row tables, fetch unit ci.j + 3
 #pragma unroll
                     for (int h = 0; h < 2; ++h) {
                         ti[0][h] = ti[1][h];
@@ -448,9 +475,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_m2l_tc(int p, int prods, cons
         float* E = epi + (warp - TC_EPI0) * 32 * EPI_LD;
         // destination row table of this warp's 32 accumulator rows, one per lane (shuffled per
         // pass); the next tile's entries are fetched before this tile's accumulator wait
-        auto dst_of = [&](int j) { return j < my_tiles ? dst_info[(size_t)tile_of(j) * TC_ROWS + 32 * quad + lane] : -1; };
+        auto dst_of = [&](int j) { return j < my_units ? dst_info[(size_t)tile_of(j) * TC_ROWS + 32 * quad + lane] : -1; };
         int next_info = eg < EG ? dst_of(eg) : -1;
-        for (int j = eg; eg < EG && j < my_tiles; j += EG) {
+        for (int j = eg; eg < EG && j < my_units; j += EG) {
             const int b = j % NB, u = j / NB;
             const int my_info = next_info;
             next_info = dst_of(j + EG);
@@ -704,8 +731,13 @@ int build_m2l_tc(fmmbem_handle* h) {
     FMM_TRY(build_tree_tc(h, nr, rows_max, nch));
     size_t smax = 0;
     for (int q = 1; q <= pmax; ++q) smax = std::max(smax, m2l_tc_smem(h, q));
-    if (h->tc_kc == 16) FMM_CU(cudaFuncSetAttribute(k_m2l_tc<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smax));
-    else FMM_CU(cudaFuncSetAttribute(k_m2l_tc<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smax));
+    if (h->tc_kc == 16) {
+        FMM_CU(cudaFuncSetAttribute(k_m2l_tc<16, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smax));
+        FMM_CU(cudaFuncSetAttribute(k_m2l_tc<16, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smax));
+    } else {
+        FMM_CU(cudaFuncSetAttribute(k_m2l_tc<32, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smax));
+        FMM_CU(cudaFuncSetAttribute(k_m2l_tc<32, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smax));
+    }
     int dev = 0;
     FMM_CU(cudaGetDevice(&dev));
     FMM_CU(cudaDeviceGetAttribute(&h->n_sm, cudaDevAttrMultiProcessorCount, dev));
@@ -735,13 +767,17 @@ int tree_tc(fmmbem_handle* h, int p, int level, int which) {
     const int* src = h->tree_info + (which == 0 ? 0 : 2 * rw) + (size_t)t0 * TC_ROWS;
     const int* dst = h->tree_info + (which == 0 ? rw : 3 * rw) + (size_t)t0 * TC_ROWS;
     const int4* tiles = h->tree_tiles + (which == 0 ? 0 : h->n_tree_tiles) + t0;
-    const int grid = std::min(nt, h->n_sm);
+    // a level has few tiles (tens against 152 SMs): split each tile's K chunks over several
+    // CTAs so that more SMs share the level and each CTA's chain of chunks is shorter
+    const int nch = (2 * ncoef(p) + h->tc_kc - 1) / h->tc_kc;
+    const int ks = std::max(1, std::min(nch, h->n_sm / nt));
+    const int grid = std::min(nt * ks, h->n_sm);
     const size_t sm = m2l_tc_smem(h, p);
     if (h->tc_kc == 16)
-        k_m2l_tc<16><<<grid, TC_THREADS, sm, h->stream>>>(p, 3, tiles, nt, src, dst, h->tree_tab_tc, h->tc_stride,
+        k_m2l_tc<16, true><<<grid, TC_THREADS, sm, h->stream>>>(p, 3, tiles, nt, ks, src, dst, h->tree_tab_tc, h->tc_stride,
                                                          h->tc_rows_max, X, X, h->tc_err);
     else
-        k_m2l_tc<32><<<grid, TC_THREADS, sm, h->stream>>>(p, 3, tiles, nt, src, dst, h->tree_tab_tc, h->tc_stride,
+        k_m2l_tc<32, true><<<grid, TC_THREADS, sm, h->stream>>>(p, 3, tiles, nt, ks, src, dst, h->tree_tab_tc, h->tc_stride,
                                                          h->tc_rows_max, X, X, h->tc_err);
     FMM_LAUNCHED();
     return 0;
@@ -756,11 +792,11 @@ int m2l_tc(fmmbem_handle* h, int p) {
     const int prods = 3;
     if (grid <= 0) return 0;
     if (h->tc_kc == 16)
-        k_m2l_tc<16><<<grid, TC_THREADS, sm, h->stream>>>(p, prods, h->m2l_tiles_tc, h->n_tiles_tc, h->tc_src_info,
+        k_m2l_tc<16, false><<<grid, TC_THREADS, sm, h->stream>>>(p, prods, h->m2l_tiles_tc, h->n_tiles_tc, 1, h->tc_src_info,
                                                          h->tc_dst_info, h->tab_tc, h->tc_stride, h->tc_rows_max, M, L,
                                                          h->tc_err);
     else
-        k_m2l_tc<32><<<grid, TC_THREADS, sm, h->stream>>>(p, prods, h->m2l_tiles_tc, h->n_tiles_tc, h->tc_src_info,
+        k_m2l_tc<32, false><<<grid, TC_THREADS, sm, h->stream>>>(p, prods, h->m2l_tiles_tc, h->n_tiles_tc, 1, h->tc_src_info,
                                                          h->tc_dst_info, h->tab_tc, h->tc_stride, h->tc_rows_max, M, L,
                                                          h->tc_err);
     FMM_LAUNCHED();
