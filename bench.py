@@ -43,14 +43,15 @@ def parse():
     ap.add_argument("--ncrit", type=int, default=WORKLOAD["ncrit"])
     ap.add_argument("--no-compare", action="store_true", help="skip the FP64 comparison solves")
     ap.add_argument("--problem", default="laplace",
-                    choices=["laplace", "stokes", "serve", "laplace2", "sweeps", "batch", "rbc64", "peaks"],
+                    choices=["laplace", "stokes", "serve", "laplace2", "sweeps", "batch", "rbc64", "peaks", "matvec"],
                     help="laplace: the headline workload; stokes: Stokes flow past a sphere of 81920 panels; "
                          "serve: a Poisson stream of mixed solves through the serving runtime; "
                          "laplace2: second-kind Laplace solves on octahedron spheres of 8192-131072 panels; "
                          "sweeps: the paper's parameter studies (initial p, tolerance, p_min, red blood cell); "
                          "batch: four right-hand sides in one batched solve against four single solves; "
                          "rbc64: Stokes flow around 64 red blood cells (131072 panels); "
-                         "peaks: the peak rates the rooflines divide by (FP32, paired FP32, rsqrt, FP64, TF32 tensor)")
+                         "peaks: the peak rates the rooflines divide by (FP32, paired FP32, rsqrt, FP64, TF32 tensor); "
+                         "matvec: per-order pass times of single mat-vecs of the headline sphere")
     ap.add_argument("--quick", action="store_true",
                     help="sweeps: the same studies on small meshes with one timed run each (a check of the harness)")
     ap.add_argument("--requests", type=int, default=48, help="serve: number of requests")
@@ -58,6 +59,12 @@ def parse():
     ap.add_argument("--max-active", type=int, default=6, help="serve: concurrent solves")
     ap.add_argument("--no-autotune", action="store_true",
                     help="laplace: keep the default per-order tensor-core choices instead of fmmbem_autotune's")
+    ap.add_argument("--orders", default="3,4,5,6,7,8,9,10,11,12,16",
+                    help="matvec: comma-separated expansion orders")
+    ap.add_argument("--tree-tc-min", type=int, default=0,
+                    help="matvec: lowest order whose M2M/L2L run on the tensor cores (0: the library default)")
+    ap.add_argument("--capture", action="store_true",
+                    help="matvec: one mat-vec per order and nothing else (a fixed launch sequence for ncu)")
     ap.add_argument("--tune-ncrit", default="",
                     help="laplace: comma-separated leaf capacities; the handle is created by fmmbem_create_tuned "
                          "over them (the workload's ncrit stays the reported configuration's otherwise)")
@@ -1104,6 +1111,66 @@ def run_peaks(args, world, rank, local):
         print(json.dumps(line), flush=True)
 
 
+def run_matvec(args, world, rank, local):
+    """Single mat-vecs of the headline sphere (icosahedron refined --levels times, K = 4, theta 0.5,
+    mixed precision) at each order of --orders: the library's per-pass CUDA events with every
+    pass timed alone (near field before far field on one stream), averaged over 10 mat-vecs
+    after 3 untimed ones, with the M2L pairs' algorithmic rate and the near field's pair rate.
+    --capture runs one mat-vec per order and nothing else, the launch sequence an ncu capture
+    selects from (k_m2l_tc launch i is then the M2L of order i when the tree passes are off the
+    tensor cores, --tree-tc-min above the largest order)."""
+    import torch
+    from synth import icosphere
+    from paper_1506_05957_gb300 import FmmBem, FMMBEM_MIXED, build
+    build.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    v, t = icosphere(args.levels)
+    orders = [int(q) for q in args.orders.split(",") if q]
+    h = FmmBem(v, t, gauss_k=WORKLOAD["gauss_k"], ncrit=args.ncrit, theta=WORKLOAD["theta"], p_max=max(16, max(orders)),
+               precision=FMMBEM_MIXED)
+    if args.tree_tc_min > 0:
+        h.set_tc_thresholds(1, args.tree_tc_min)
+    g = torch.Generator(device=dev).manual_seed(0)
+    x = torch.randn(len(t), dtype=torch.float64, device=dev, generator=g)
+    y = torch.empty_like(x)
+    st = h.stats()
+    if args.capture:
+        for q in orders:
+            h.matvec(q, x, y)
+        torch.cuda.synchronize(dev)
+        h.check_waits()
+        if rank == 0:
+            print(json.dumps({"metric": "mat-vec launch sequence", "orders": orders, "panels": len(t),
+                              "n_m2l_tiles_tc": st["n_m2l_tiles_tc"]}), flush=True)
+        h.close()
+        return
+    rows = {}
+    reps = 10
+    for q in orders:
+        for _ in range(3):
+            h.matvec(q, x, y)
+        torch.cuda.synchronize(dev)
+        h.profile_enable(2)
+        for _ in range(reps):
+            h.matvec(q, x, y)
+        pr = h.profile()
+        h.profile_enable(False)
+        h.check_waits()
+        us = {k_: round(v_ / reps * 1e3, 1) for k_, v_ in pr["ms"].items() if k_ != "krylov"}
+        m2l_flops = 2.0 * (q + 1) ** 4 * st["n_m2l_pairs"]
+        rows[q] = dict(us, m2l_tflops=round(m2l_flops / (us["m2l"] * 1e-6) / 1e12, 2) if us["m2l"] > 0 else None,
+                       p2p_pairs_per_s=st["n_p2p_interactions"] / (us["p2p"] * 1e-6) if us["p2p"] > 0 else None)
+    if rank == 0:
+        print(json.dumps({"metric": "mat-vec pass times (us, each pass alone) per expansion order", "unit": "us",
+                          "config": {"workload": "laplace-sphere-ico%d-%d" % (args.levels, len(t)), "panels": len(t),
+                                     "gauss_k": WORKLOAD["gauss_k"], "theta": WORKLOAD["theta"], "ncrit": args.ncrit,
+                                     "precision": "mixed", "tree_tc_min": args.tree_tc_min or None},
+                          "n_m2l_pairs": st["n_m2l_pairs"], "n_m2l_tiles_tc": st["n_m2l_tiles_tc"],
+                          "n_p2p_interactions": st["n_p2p_interactions"], "orders": rows}), flush=True)
+    h.close()
+
+
 def main():
     args = parse()
     world, rank, local = dist_init(args)
@@ -1123,6 +1190,8 @@ def main():
         run_rbc64(args, world, rank, local)
     elif args.problem == "peaks":
         run_peaks(args, world, rank, local)
+    elif args.problem == "matvec":
+        run_matvec(args, world, rank, local)
     else:
         run_ours(args, world, rank, local)
     if world > 1:
