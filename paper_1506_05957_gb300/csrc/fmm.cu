@@ -1043,6 +1043,7 @@ int far_field_t(fmmbem_handle* h, int p) {
     prof_begin(h, FMMBEM_PASS_M2M);
     int nl = 0;
     const size_t sm_m2m = (size_t)(16 * NC + 8) * nco * 2 * sizeof(T);
+    if (m2l_tc_on) FMM_TRY(m2l_tc_zero(h));
     if (tree_tc_on) {
         FMM_TRY(tree_tc_zero(h, p));
         ++nl;

@@ -205,6 +205,7 @@ int build_m2l_tc(fmmbem_handle* h);
 int m2l_tc(fmmbem_handle* h, int p);
 int tree_tc(fmmbem_handle* h, int p, int level, int which);
 int tree_tc_zero(fmmbem_handle* h, int p);
+int m2l_tc_zero(fmmbem_handle* h);  // zero the local expansions the tensor-core M2L accumulates into
 // fmm.cu
 int far_field(fmmbem_handle* h, int p, bool fp64);
 int far_eval_add(fmmbem_handle* h, int p, bool fp64, double* y_sorted, double scale);

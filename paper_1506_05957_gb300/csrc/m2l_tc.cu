@@ -234,6 +234,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_m2l_tc(int p, int prods, cons
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
     const uint32_t taddr = *taddr_slot;
+    // everything above (barriers, sign tables, TMEM) may overlap the previous kernel of the
+    // stream; the expansions it writes are read and accumulated only after it has completed
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     const uint32_t buf_cols = (uint32_t)(512 / NB);
     // Work units are (tile, range of K chunks): the nch chunks of a tile are cut into ksplit
     // ranges (split-K for launches with fewer tiles than SMs; the epilogue adds each range's
@@ -755,6 +758,27 @@ int tree_tc_zero(fmmbem_handle* h, int p) {
     return 0;
 }
 
+// Launch of the tensor-core kernel with programmatic stream serialization: consecutive
+// tensor-core passes of a mat-vec (tree levels, M2L) overlap each launch's set-up with the
+// previous one's tail (the kernel waits for its predecessor before reading expansions).
+template <int KC, bool SPLIT>
+static cudaError_t launch_tc(int grid, size_t smem, cudaStream_t st, int p, int prods, const int4* tiles, int nt,
+                             int ks, const int* src, const int* dst, const float* tab, size_t stride, int rows_max,
+                             const float* M, float* L, int* err) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3(TC_THREADS);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_m2l_tc<KC, SPLIT>, p, prods, tiles, nt, ks, src, dst, tab, stride, rows_max, M, L,
+                              err);
+}
+
 // One level of M2M (which = 0: children of level l into their parents, zeroed beforehand
 // by tree_tc_zero) or L2L (which = 1: parents of level l into their children) on the
 // tensor cores.
@@ -774,32 +798,35 @@ int tree_tc(fmmbem_handle* h, int p, int level, int which) {
     const int grid = std::min(nt * ks, h->n_sm);
     const size_t sm = m2l_tc_smem(h, p);
     if (h->tc_kc == 16)
-        k_m2l_tc<16, true><<<grid, TC_THREADS, sm, h->stream>>>(p, 3, tiles, nt, ks, src, dst, h->tree_tab_tc, h->tc_stride,
-                                                         h->tc_rows_max, X, X, h->tc_err);
+        FMM_CU((launch_tc<16, true>(grid, sm, h->stream, p, 3, tiles, nt, ks, src, dst, h->tree_tab_tc, h->tc_stride,
+                                   h->tc_rows_max, X, X, h->tc_err)));
     else
-        k_m2l_tc<32, true><<<grid, TC_THREADS, sm, h->stream>>>(p, 3, tiles, nt, ks, src, dst, h->tree_tab_tc, h->tc_stride,
-                                                         h->tc_rows_max, X, X, h->tc_err);
-    FMM_LAUNCHED();
+        FMM_CU((launch_tc<32, true>(grid, sm, h->stream, p, 3, tiles, nt, ks, src, dst, h->tree_tab_tc, h->tc_stride,
+                                   h->tc_rows_max, X, X, h->tc_err)));
+    return 0;
+}
+
+// The local expansions are zeroed ahead of the upward pass (nothing reads or writes them until
+// the M2L), so that the M2L launch follows the last M2M level directly and its set-up overlaps
+// that level's tail.
+int m2l_tc_zero(fmmbem_handle* h) {
+    FMM_CU(cudaMemsetAsync(h->L, 0, sizeof(float) * h->esys * h->nsys, h->stream));
     return 0;
 }
 
 int m2l_tc(fmmbem_handle* h, int p) {
     float* L = reinterpret_cast<float*>(h->L);
     const float* M = reinterpret_cast<const float*>(h->M);
-    FMM_CU(cudaMemsetAsync(L, 0, sizeof(float) * h->esys * h->nsys, h->stream));
     const size_t sm = m2l_tc_smem(h, p);
     const int grid = std::min(h->n_tiles_tc, h->n_sm);  // persistent: one CTA per SM (512 TMEM columns each)
     const int prods = 3;
     if (grid <= 0) return 0;
     if (h->tc_kc == 16)
-        k_m2l_tc<16, false><<<grid, TC_THREADS, sm, h->stream>>>(p, prods, h->m2l_tiles_tc, h->n_tiles_tc, 1, h->tc_src_info,
-                                                         h->tc_dst_info, h->tab_tc, h->tc_stride, h->tc_rows_max, M, L,
-                                                         h->tc_err);
+        FMM_CU((launch_tc<16, false>(grid, sm, h->stream, p, prods, h->m2l_tiles_tc, h->n_tiles_tc, 1, h->tc_src_info,
+                                    h->tc_dst_info, h->tab_tc, h->tc_stride, h->tc_rows_max, M, L, h->tc_err)));
     else
-        k_m2l_tc<32, false><<<grid, TC_THREADS, sm, h->stream>>>(p, prods, h->m2l_tiles_tc, h->n_tiles_tc, 1, h->tc_src_info,
-                                                         h->tc_dst_info, h->tab_tc, h->tc_stride, h->tc_rows_max, M, L,
-                                                         h->tc_err);
-    FMM_LAUNCHED();
+        FMM_CU((launch_tc<32, false>(grid, sm, h->stream, p, prods, h->m2l_tiles_tc, h->n_tiles_tc, 1, h->tc_src_info,
+                                    h->tc_dst_info, h->tab_tc, h->tc_stride, h->tc_rows_max, M, L, h->tc_err)));
     return 0;
 }
 
