@@ -57,6 +57,8 @@ def parse():
     ap.add_argument("--requests", type=int, default=48, help="serve: number of requests")
     ap.add_argument("--rate", type=float, default=20.0, help="serve: mean arrival rate (requests/s)")
     ap.add_argument("--max-active", type=int, default=6, help="serve: concurrent solves")
+    ap.add_argument("--no-handle-cache", action="store_true",
+                    help="serve: destroy every request's handle (no reuse across requests on one mesh)")
     ap.add_argument("--no-autotune", action="store_true",
                     help="laplace: keep the default per-order tensor-core choices instead of fmmbem_autotune's")
     ap.add_argument("--orders", default="3,4,5,6,7,8,9,10,11,12,16",
@@ -1039,6 +1041,8 @@ def run_serve(args, world, rank, local):
     rng = np.random.default_rng(100 + rank)
     gaps = rng.exponential(1.0 / args.rate, len(reqs))
     srv = FmmBemServer(max_active=args.max_active)
+    if args.no_handle_cache:
+        srv.set_cache(0)
     # warm-up: one small solve of each operator (module load, first allocations)
     for kern, k, rhs_fn in ((FMMBEM_LAPLACE, 4, None), (FMMBEM_STOKES, 3, None)):
         from synth import icosphere
@@ -1059,6 +1063,7 @@ def run_serve(args, world, rank, local):
                                    p_min=3 if lap else 4, precision=prec), r))
     res = [(srv.wait(tk)[1], r) for tk, r in tickets]
     wall = time.perf_counter() - t0
+    reused = sum(int(i["handle_reused"]) for i, _ in res)
     srv.close()
     lat = np.array([i["latency_s"] for i, _ in res])
     ok = sum(1 for i, _ in res if i["status"] == 0)
@@ -1077,6 +1082,7 @@ def run_serve(args, world, rank, local):
                         "note": "true_res = ||b - A x|| / ||b|| at p_initial after the solve; tolerances below 1e-6 run "
                                 "refined (FP64 residuals around the mixed relaxed GMRES)"},
            "solves_per_s": len(reqs) * world / wall, "converged": ok,
+           "handle_cache": {"on": not args.no_handle_cache, "requests_on_cached_handles": reused},
            "mean_queue_s": float(np.mean([i["queue_s"] for i, _ in res])),
            "mean_setup_s": float(np.mean([i["setup_s"] for i, _ in res])),
            "mean_solve_s": float(np.mean([i["solve_s"] for i, _ in res])),
@@ -1084,7 +1090,8 @@ def run_serve(args, world, rank, local):
            "requests_detail": [{"shape": r["shape"], "kernel": r["kernel"], "panels": int(len(r["t"])), "tol": r["tol"],
                                 "status": int(i["status"]), "iters": int(i["iters"]), "true_res": float(i["true_res"]),
                                 "setup_s": round(float(i["setup_s"]), 4), "solve_s": round(float(i["solve_s"]), 4),
-                                "latency_s": round(float(i["latency_s"]), 4)} for i, r in res]}
+                                "latency_s": round(float(i["latency_s"]), 4), "reused": int(i["handle_reused"])}
+                               for i, r in res]}
     if rank == 0:
         print(json.dumps(out), flush=True)
 

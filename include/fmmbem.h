@@ -504,9 +504,17 @@ int fmmbem_scan_i32(const int32_t* in_dev, int32_t* out_dev, int64_t n, int incl
  *     hbm_budget (one request is always admitted when nothing else is running).
  * A smaller request that fits may therefore pass a larger one that does not.
  *
- * An admitted request is created, solved (fmmbem_solve_host) and destroyed on its worker's
- * own CUDA stream. The workers' mat-vecs interleave on the device, and each request's state
- * stays resident until its solve ends.
+ * An admitted request is created and solved (fmmbem_solve_host) on its worker's own CUDA
+ * stream. The workers' mat-vecs interleave on the device, and each request's state stays
+ * resident until its solve ends.
+ *
+ * Handle cache (the paper has no counterpart: requests on one geometry are the serving case
+ * of its repeated solves). The handle of a request that solved without error is kept idle
+ * instead of destroyed, up to fmmbem_server_set_cache's count (default 4 max_active). A later
+ * request on the same mesh (vertices and triangles equal byte for byte) with the same kernel,
+ * gauss_k, ncrit, theta and options takes the idle handle and skips fmmbem_create; its tree,
+ * lists, operators, correction rows and captured mat-vec graphs are reused. Idle handles count
+ * against hbm_budget: a request that does not fit evicts them, least recently used first.
  *
  * Handles are independent and the library keeps no shared mutable state in a handle's path,
  * so concurrent requests give the results they give alone, up to floating-point summation
@@ -520,10 +528,11 @@ typedef struct {
     int iters;             /* Arnoldi steps */
     double true_res;       /* ||b - A x|| / ||b|| after the solve */
     double queue_s;        /* submit -> admission */
-    double setup_s;        /* fmmbem_create */
-    double solve_s;        /* fmmbem_solve_host (copies included) and fmmbem_destroy */
+    double setup_s;        /* fmmbem_create (about 0 when the handle came from the cache) */
+    double solve_s;        /* fmmbem_solve_host (copies included) */
     double latency_s;      /* submit -> result ready */
-    int64_t device_bytes;  /* admission estimate */
+    int64_t device_bytes;  /* admission estimate (of the cached handle's request when reused) */
+    int32_t handle_reused; /* 1 when the request ran on a cached handle */
 } fmmbem_result;
 
 /* Conservative estimate of the device memory of a handle (bytes), -1 for bad arguments. */
@@ -543,10 +552,19 @@ int fmmbem_server_submit(fmmbem_server* s, const fmmbem_mesh* mesh, int kernel, 
                          const fmmbem_opts* opts, const double* rhs_host, double tol, int relax, int p_initial,
                          int p_min, double* x_host, int64_t* ticket);
 
+/* Keep at most max_handles idle handles (0 turns the cache off); extra idle handles are
+ * destroyed at once, least recently used first. Errors: FMMBEM_EINVAL (NULL server, negative
+ * count). */
+int fmmbem_server_set_cache(fmmbem_server* s, int max_handles);
+
+/* Requests served on a cached handle since the server was created (0 for NULL). */
+int64_t fmmbem_server_cache_hits(fmmbem_server* s);
+
 /* Block until the ticket's request has finished and return its result (each ticket once). */
 int fmmbem_server_wait(fmmbem_server* s, int64_t ticket, fmmbem_result* out);
 
-/* Finish every queued request, stop the workers and free the server. NULL is ignored. */
+/* Finish every queued request, stop the workers, destroy the cached handles and free the
+ * server. NULL is ignored. */
 int fmmbem_server_destroy(fmmbem_server* s);
 
 #ifdef __cplusplus

@@ -68,7 +68,8 @@ class fmmbem_profile(ctypes.Structure):
 class fmmbem_result(ctypes.Structure):
     _fields_ = [("ticket", ctypes.c_int64), ("status", ctypes.c_int), ("iters", ctypes.c_int),
                 ("true_res", ctypes.c_double), ("queue_s", ctypes.c_double), ("setup_s", ctypes.c_double),
-                ("solve_s", ctypes.c_double), ("latency_s", ctypes.c_double), ("device_bytes", ctypes.c_int64)]
+                ("solve_s", ctypes.c_double), ("latency_s", ctypes.c_double), ("device_bytes", ctypes.c_int64),
+                ("handle_reused", ctypes.c_int32)]
 
 
 _lib = None
@@ -109,6 +110,9 @@ def lib():
                                            ctypes.POINTER(ctypes.c_int64)]
         L.fmmbem_server_wait.argtypes = [_vp, ctypes.c_int64, ctypes.POINTER(fmmbem_result)]
         L.fmmbem_server_destroy.argtypes = [_vp]
+        L.fmmbem_server_set_cache.argtypes = [_vp, ctypes.c_int]
+        L.fmmbem_server_cache_hits.argtypes = [_vp]
+        L.fmmbem_server_cache_hits.restype = ctypes.c_int64
         L.fmmbem_matvec_direct.argtypes = [_vp, _vp, _vp]
         L.fmmbem_rhs.argtypes = [_vp, _vp, _vp]
         L.fmmbem_stokes_dl_apply.argtypes = [_vp, _vp, _vp]
@@ -435,6 +439,13 @@ class FmmBemServer:
         _check(lib().fmmbem_server_wait(self.s, int(ticket), ctypes.byref(r)))
         x = self._pending.pop(ticket)
         return x, {n: getattr(r, n) for n, _ in fmmbem_result._fields_}
+
+    def set_cache(self, max_handles):
+        """fmmbem_server_set_cache: keep at most max_handles idle handles (0: no cache)."""
+        _check(lib().fmmbem_server_set_cache(self.s, int(max_handles)))
+
+    def cache_hits(self):
+        return int(lib().fmmbem_server_cache_hits(self.s))
 
     def close(self):
         if getattr(self, "s", None):

@@ -12,7 +12,14 @@
 // mat-vecs are independent kernel streams that interleave on the device. When a solve
 // ends its memory returns to the budget and the next queued request is admitted.
 // fmmbem_server_wait blocks until a ticket's result (solution, iterations, timings) is in.
+//
+// Handles of finished requests are kept in an idle cache (least recently used first out,
+// up to fmmbem_server_set_cache's count and always inside the HBM budget): a later request
+// on the same mesh with the same operator and settings takes the cached handle (tree, lists,
+// operators, correction rows and captured mat-vec graphs) and skips fmmbem_create. The
+// cache is keyed by a hash of the mesh and settings and confirmed by comparing the mesh.
 #include <math.h>
+#include <string.h>
 #include <chrono>
 #include <condition_variable>
 #include <deque>
@@ -38,16 +45,62 @@ struct Request {
     int relax = 1, p_initial = 10, p_min = 3;
     double* x_host = nullptr;
     int64_t bytes = 0;  // admission estimate
+    uint64_t key = 0;   // hash of the mesh and the handle settings (the handle cache's key)
     clk::time_point t_submit;
     fmmbem_result res{};
     bool done = false;
 };
 
+// An idle handle of a finished request, with what it was created from.
+struct CacheEntry {
+    uint64_t key = 0;
+    std::vector<double> vertices;
+    std::vector<int32_t> triangles;
+    int kernel = 0, gauss_k = 0, ncrit = 0;
+    double theta = 0.0;
+    fmmbem_opts opts{};
+    fmmbem_handle* h = nullptr;
+    int64_t bytes = 0;
+    uint64_t last_use = 0;
+};
+
+// 64-bit FNV-1a over a byte range, continuing from h.
+uint64_t fnv1a(const void* data, size_t n, uint64_t h) {
+    const unsigned char* b = static_cast<const unsigned char*>(data);
+    for (size_t i = 0; i < n; ++i) {
+        h ^= b[i];
+        h *= 1099511628211ull;
+    }
+    return h;
+}
+
+// The settings that decide a handle's contents (the stream excluded).
+bool same_opts(const fmmbem_opts& a, const fmmbem_opts& b) {
+    return a.p_max == b.p_max && a.near_factor == b.near_factor && a.mu == b.mu && a.precision == b.precision &&
+           a.restart == b.restart && a.max_iter == b.max_iter && a.nrhs == b.nrhs && a.near_k == b.near_k;
+}
+
+uint64_t request_key(const Request& r) {
+    uint64_t h = 1469598103934665603ull;
+    h = fnv1a(r.vertices.data(), r.vertices.size() * sizeof(double), h);
+    h = fnv1a(r.triangles.data(), r.triangles.size() * sizeof(int32_t), h);
+    const int ints[] = {r.kernel, r.gauss_k, r.ncrit, r.opts.p_max, r.opts.precision, r.opts.restart,
+                        r.opts.max_iter, r.opts.nrhs, r.opts.near_k};
+    const double dbl[] = {r.theta, r.opts.near_factor, r.opts.mu};
+    h = fnv1a(ints, sizeof(ints), h);
+    return fnv1a(dbl, sizeof(dbl), h);
+}
+
+bool entry_matches(const CacheEntry& e, const Request& r) {
+    return e.key == r.key && e.kernel == r.kernel && e.gauss_k == r.gauss_k && e.ncrit == r.ncrit &&
+           e.theta == r.theta && same_opts(e.opts, r.opts) && e.vertices == r.vertices && e.triangles == r.triangles;
+}
+
 }  // namespace
 
 struct fmmbem_server {
     int device = 0;
-    int64_t budget = 0, in_use = 0;
+    int64_t budget = 0, in_use = 0;  // in_use counts running requests and cached handles
     int n_workers = 0;
     bool stop = false;
     int64_t next_ticket = 1;
@@ -56,44 +109,93 @@ struct fmmbem_server {
     std::deque<Request*> queue;
     std::map<int64_t, Request*> all;
     std::vector<std::thread> workers;
+    std::vector<cudaStream_t> streams;  // one per worker; they outlive every handle created on them
+    std::vector<CacheEntry*> idle;      // cached handles of finished requests
+    int max_cached = 0;
+    uint64_t use_clock = 0;
+    int64_t hits = 0;
 };
 
 namespace {
 
-void worker_main(fmmbem_server* s) {
+// Remove the least recently used idle entry (caller holds the lock); the caller destroys it.
+CacheEntry* pop_lru(fmmbem_server* s) {
+    if (s->idle.empty()) return nullptr;
+    size_t v = 0;
+    for (size_t i = 1; i < s->idle.size(); ++i)
+        if (s->idle[i]->last_use < s->idle[v]->last_use) v = i;
+    CacheEntry* e = s->idle[v];
+    s->idle.erase(s->idle.begin() + (long)v);
+    s->in_use -= e->bytes;
+    return e;
+}
+
+void destroy_entries(std::vector<CacheEntry*>& v) {
+    for (CacheEntry* e : v) {
+        fmmbem_destroy(e->h);
+        delete e;
+    }
+    v.clear();
+}
+
+void worker_main(fmmbem_server* s, int idx) {
     cudaSetDevice(s->device);
-    cudaStream_t st = nullptr;
-    cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    cudaStream_t st = s->streams[idx];
     for (;;) {
         Request* r = nullptr;
+        CacheEntry* hit = nullptr;
+        std::vector<CacheEntry*> evicted;
         {
             std::unique_lock<std::mutex> lock(s->mu);
             for (;;) {
                 if (s->stop && s->queue.empty()) break;
-                // the first queued request whose estimate fits in the remaining budget
-                for (auto it = s->queue.begin(); it != s->queue.end(); ++it) {
-                    if (s->in_use + (*it)->bytes <= s->budget || s->in_use == 0) {
+                // the first queued request that has a cached handle or whose estimate fits in the
+                // remaining budget once idle handles are given up
+                auto it = s->queue.begin();
+                for (; it != s->queue.end(); ++it) {
+                    for (size_t i = 0; i < s->idle.size(); ++i)
+                        if (entry_matches(*s->idle[i], **it)) {
+                            hit = s->idle[i];
+                            s->idle.erase(s->idle.begin() + (long)i);
+                            break;
+                        }
+                    if (hit) {
                         r = *it;
-                        s->queue.erase(it);
-                        break;
+                        r->bytes = hit->bytes;  // already counted in in_use
+                    } else {
+                        int64_t idle_bytes = 0;
+                        for (CacheEntry* e : s->idle) idle_bytes += e->bytes;
+                        if (s->in_use - idle_bytes + (*it)->bytes <= s->budget || s->in_use == idle_bytes) {
+                            r = *it;
+                            while (!s->idle.empty() && s->in_use + r->bytes > s->budget) evicted.push_back(pop_lru(s));
+                            s->in_use += r->bytes;
+                        }
                     }
+                    if (r) break;
                 }
-                if (r) break;
+                if (r) {
+                    s->queue.erase(it);
+                    break;
+                }
                 s->cv_work.wait(lock);
             }
             if (!r) break;
-            s->in_use += r->bytes;
         }
+        destroy_entries(evicted);
         const auto t_adm = clk::now();
         r->res.queue_s = std::chrono::duration<double>(t_adm - r->t_submit).count();
-        fmmbem_mesh mesh{(int64_t)(r->vertices.size() / 3), r->vertices.data(), (int64_t)(r->triangles.size() / 3),
-                         r->triangles.data()};
-        fmmbem_opts o = r->opts;
-        o.stream = st;
-        fmmbem_handle* h = nullptr;
-        int rc = fmmbem_create(&mesh, r->kernel, r->gauss_k, r->ncrit, r->theta, &o, &h);
+        fmmbem_handle* h = hit ? hit->h : nullptr;
+        int rc = 0;
+        if (!h) {
+            fmmbem_mesh mesh{(int64_t)(r->vertices.size() / 3), r->vertices.data(), (int64_t)(r->triangles.size() / 3),
+                             r->triangles.data()};
+            fmmbem_opts o = r->opts;
+            o.stream = st;
+            rc = fmmbem_create(&mesh, r->kernel, r->gauss_k, r->ncrit, r->theta, &o, &h);
+        }
         const auto t_set = clk::now();
         r->res.setup_s = std::chrono::duration<double>(t_set - t_adm).count();
+        r->res.handle_reused = hit ? 1 : 0;
         if (rc == 0) {
             int iters = 0;
             double true_res = 0.0;
@@ -101,25 +203,51 @@ void worker_main(fmmbem_server* s) {
                                    nullptr, nullptr, &true_res);
             r->res.iters = iters;
             r->res.true_res = true_res;
-            fmmbem_destroy(h);
         }
         const auto t_end = clk::now();
         r->res.solve_s = std::chrono::duration<double>(t_end - t_set).count();
         r->res.latency_s = std::chrono::duration<double>(t_end - r->t_submit).count();
         r->res.status = rc;
         r->res.device_bytes = r->bytes;
+        // a handle that solved cleanly goes to the idle cache; a failed one is destroyed
+        CacheEntry* keep = nullptr;
+        if (h && rc >= 0 && s->max_cached > 0) {
+            keep = hit ? hit : new CacheEntry();
+            if (!hit) {
+                keep->key = r->key;
+                keep->kernel = r->kernel;
+                keep->gauss_k = r->gauss_k;
+                keep->ncrit = r->ncrit;
+                keep->theta = r->theta;
+                keep->opts = r->opts;
+                keep->h = h;
+                keep->bytes = r->bytes;
+                keep->vertices.swap(r->vertices);
+                keep->triangles.swap(r->triangles);
+            }
+        } else if (h) {
+            fmmbem_destroy(h);
+            if (hit) delete hit;
+        }
         {
             std::lock_guard<std::mutex> lock(s->mu);
-            s->in_use -= r->bytes;
+            if (keep) {
+                keep->last_use = ++s->use_clock;
+                s->idle.push_back(keep);
+                while ((int)s->idle.size() > s->max_cached) evicted.push_back(pop_lru(s));
+            } else {
+                s->in_use -= r->bytes;
+            }
+            if (hit) ++s->hits;
             r->done = true;
             r->vertices.clear();
             r->triangles.clear();
             r->rhs.clear();
         }
+        destroy_entries(evicted);
         s->cv_done.notify_all();
         s->cv_work.notify_all();
     }
-    cudaStreamDestroy(st);
 }
 
 }  // namespace
@@ -159,9 +287,42 @@ int fmmbem_server_create(int max_active, int64_t hbm_budget, fmmbem_server** out
     }
     s->budget = hbm_budget;
     s->n_workers = max_active;
-    for (int i = 0; i < max_active; ++i) s->workers.emplace_back(worker_main, s);
+    s->max_cached = 4 * max_active;
+    for (int i = 0; i < max_active; ++i) {
+        cudaStream_t st = nullptr;
+        if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
+            for (cudaStream_t q : s->streams) cudaStreamDestroy(q);
+            delete s;
+            fmmbem_set_error("cannot create the workers' streams");
+            return FMMBEM_EDEVICE;
+        }
+        s->streams.push_back(st);
+    }
+    for (int i = 0; i < max_active; ++i) s->workers.emplace_back(worker_main, s, i);
     *out = s;
     return 0;
+}
+
+int fmmbem_server_set_cache(fmmbem_server* s, int max_handles) {
+    if (!s || max_handles < 0) {
+        fmmbem_set_error("bad cache size");
+        return FMMBEM_EINVAL;
+    }
+    std::vector<CacheEntry*> evicted;
+    {
+        std::lock_guard<std::mutex> lock(s->mu);
+        s->max_cached = max_handles;
+        while ((int)s->idle.size() > max_handles) evicted.push_back(pop_lru(s));
+    }
+    destroy_entries(evicted);
+    s->cv_work.notify_all();
+    return 0;
+}
+
+int64_t fmmbem_server_cache_hits(fmmbem_server* s) {
+    if (!s) return 0;
+    std::lock_guard<std::mutex> lock(s->mu);
+    return s->hits;
 }
 
 int fmmbem_server_submit(fmmbem_server* s, const fmmbem_mesh* mesh, int kernel, int gauss_k, int ncrit, double theta,
@@ -193,6 +354,8 @@ int fmmbem_server_submit(fmmbem_server* s, const fmmbem_mesh* mesh, int kernel, 
     r->p_min = p_min;
     r->x_host = x_host;
     r->bytes = fmmbem_estimate_bytes(mesh->n_panels, kernel, gauss_k, ncrit, &r->opts);
+    r->opts.stream = nullptr;  // each worker has its own
+    r->key = request_key(*r);
     r->t_submit = clk::now();
     {
         std::lock_guard<std::mutex> lock(s->mu);
@@ -233,6 +396,8 @@ int fmmbem_server_destroy(fmmbem_server* s) {
     s->cv_work.notify_all();
     for (auto& w : s->workers) w.join();
     for (auto& e : s->all) delete e.second;
+    destroy_entries(s->idle);  // before the streams the handles were created on
+    for (cudaStream_t st : s->streams) cudaStreamDestroy(st);
     delete s;
     return 0;
 }

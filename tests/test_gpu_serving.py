@@ -137,3 +137,54 @@ def test_mixed_requests_match_solo_solves(torch_cuda):
         print("served request", idx, "oracle residual", res, "reported", info["true_res"])
         # the FMM at p_initial differs from the dense operator by up to ~1e-6 at these sizes
         assert res <= 2 * r["tol"] + 2e-6
+
+
+def test_cached_handles_serve_repeated_meshes(torch_cuda):
+    """A request on a mesh and settings that an earlier request used runs on that request's
+    idle handle (no fmmbem_create) and gives the solution a fresh handle gives; other settings,
+    a full budget and a cache size of zero each force a new handle."""
+    import torch
+    from oracle import dense
+    from synth import icosphere, ellipsoid, point_charge_dirichlet
+    from paper_1506_05957_gb300 import FmmBem, FmmBemServer, fmmbem_estimate_bytes, FMMBEM_FP64
+    v, t = icosphere(3)
+    c = v[t].mean(axis=1)
+    rhs = [point_charge_dirichlet(c, np.array(z)) for z in ((0.0, 0.0, 3.0), (2.5, -1.0, 0.5), (0.0, 2.0, -2.0))]
+    est = fmmbem_estimate_bytes(len(t))
+    srv = FmmBemServer(max_active=1, hbm_budget=int(50 * est))
+    run = lambda b, **kw: srv.wait(srv.submit(v, t, b, tol=1e-6, **kw))
+    x0, i0 = run(rhs[0])
+    x1, i1 = run(rhs[1])
+    x2, i2 = run(rhs[2], p_max=12)  # another operator table size: a new handle
+    assert (i0["handle_reused"], i1["handle_reused"], i2["handle_reused"]) == (0, 1, 0)
+    assert i1["setup_s"] < 0.5 * i0["setup_s"]
+    assert srv.cache_hits() == 1
+    # the reused handle's solution against a fresh handle's and against the oracle
+    h = FmmBem(v, t, ncrit=150, theta=0.5, p_max=16)
+    xs = np.zeros_like(rhs[1])
+    h.solve_host(np.ascontiguousarray(rhs[1]), xs, tol=1e-6, relax=True, p_initial=10, p_min=3)
+    h.close()
+    hd = FmmBem(v, t, ncrit=150, theta=0.5, p_max=16, precision=FMMBEM_FP64)
+    d = torch.tensor(x1 - xs, dtype=torch.float64, device="cuda")
+    ad = torch.zeros_like(d)
+    hd.matvec_direct(d, ad)
+    hd.close()
+    assert float(torch.linalg.vector_norm(ad)) / np.linalg.norm(rhs[1]) <= 4e-6
+    M = dense.Mesh(v, t, k=4)
+    for x, b in ((x0, rhs[0]), (x1, rhs[1]), (x2, rhs[2])):
+        assert np.linalg.norm(M.laplace_apply(x) - b) / np.linalg.norm(b) <= 2e-6 + 2e-6
+    # cache size zero: the idle handles go, the next repeat is created again
+    srv.set_cache(0)
+    _, i3 = run(rhs[0])
+    assert i3["handle_reused"] == 0 and srv.cache_hits() == 1
+    srv.close()
+    # a budget for about one handle: a second mesh evicts the first's idle handle
+    ve, te = ellipsoid(3, (1.0, 0.8, 1.3))
+    ce = ve[te].mean(axis=1)
+    srv = FmmBemServer(max_active=1, hbm_budget=int(1.2 * max(est, fmmbem_estimate_bytes(len(te)))))
+    _, j0 = srv.wait(srv.submit(v, t, rhs[0], tol=1e-6))
+    _, j1 = srv.wait(srv.submit(ve, te, point_charge_dirichlet(ce, np.array((0.0, 0.0, 4.0))), tol=1e-6))
+    _, j2 = srv.wait(srv.submit(v, t, rhs[1], tol=1e-6))
+    assert (j0["handle_reused"], j1["handle_reused"], j2["handle_reused"]) == (0, 0, 0)
+    assert all(j["status"] == 0 for j in (j0, j1, j2))
+    srv.close()
