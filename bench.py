@@ -65,6 +65,10 @@ def parse():
                     help="matvec: comma-separated expansion orders")
     ap.add_argument("--tree-tc-min", type=int, default=0,
                     help="matvec: lowest order whose M2M/L2L run on the tensor cores (0: the library default)")
+    ap.add_argument("--operator", default="laplace", choices=["laplace", "laplace-dl", "stokes", "stokes-dl"],
+                    help="matvec: the operator (single or double layer; Stokes on the sphere with K = 3)")
+    ap.add_argument("--p2p-variant", type=int, default=3,
+                    help="matvec: near-field schedule (3 source lanes, 0 shared tiles)")
     ap.add_argument("--capture", action="store_true",
                     help="matvec: one mat-vec per order and nothing else (a fixed launch sequence for ncu)")
     ap.add_argument("--tune-ncrit", default="",
@@ -1128,18 +1132,23 @@ def run_matvec(args, world, rank, local):
     tensor cores, --tree-tc-min above the largest order)."""
     import torch
     from synth import icosphere
-    from paper_1506_05957_gb300 import FmmBem, FMMBEM_MIXED, build
+    from paper_1506_05957_gb300 import (FmmBem, FMMBEM_MIXED, FMMBEM_LAPLACE, FMMBEM_STOKES, FMMBEM_LAYER_DOUBLE,
+                                        build)
     build.build()
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     v, t = icosphere(args.levels)
     orders = [int(q) for q in args.orders.split(",") if q]
-    h = FmmBem(v, t, gauss_k=WORKLOAD["gauss_k"], ncrit=args.ncrit, theta=WORKLOAD["theta"], p_max=max(16, max(orders)),
-               precision=FMMBEM_MIXED)
+    stokes = args.operator.startswith("stokes")
+    h = FmmBem(v, t, kernel=FMMBEM_STOKES if stokes else FMMBEM_LAPLACE, gauss_k=3 if stokes else WORKLOAD["gauss_k"],
+               ncrit=args.ncrit, theta=WORKLOAD["theta"], p_max=max(16, max(orders)), precision=FMMBEM_MIXED)
+    if args.operator.endswith("-dl"):
+        h.set_layer(FMMBEM_LAYER_DOUBLE)
+    h.set_p2p_variant(args.p2p_variant)
     if args.tree_tc_min > 0:
         h.set_tc_thresholds(1, args.tree_tc_min)
     g = torch.Generator(device=dev).manual_seed(0)
-    x = torch.randn(len(t), dtype=torch.float64, device=dev, generator=g)
+    x = torch.randn(len(t) * (3 if stokes else 1), dtype=torch.float64, device=dev, generator=g)
     y = torch.empty_like(x)
     st = h.stats()
     if args.capture:
@@ -1165,14 +1174,15 @@ def run_matvec(args, world, rank, local):
         h.profile_enable(False)
         h.check_waits()
         us = {k_: round(v_ / reps * 1e3, 1) for k_, v_ in pr["ms"].items() if k_ != "krylov"}
-        m2l_flops = 2.0 * (q + 1) ** 4 * st["n_m2l_pairs"]
+        m2l_flops = 2.0 * (q + 1) ** 4 * st["n_m2l_pairs"] * (4 if stokes else 1)
         rows[q] = dict(us, m2l_tflops=round(m2l_flops / (us["m2l"] * 1e-6) / 1e12, 2) if us["m2l"] > 0 else None,
                        p2p_pairs_per_s=st["n_p2p_interactions"] / (us["p2p"] * 1e-6) if us["p2p"] > 0 else None)
     if rank == 0:
         print(json.dumps({"metric": "mat-vec pass times (us, each pass alone) per expansion order", "unit": "us",
-                          "config": {"workload": "laplace-sphere-ico%d-%d" % (args.levels, len(t)), "panels": len(t),
-                                     "gauss_k": WORKLOAD["gauss_k"], "theta": WORKLOAD["theta"], "ncrit": args.ncrit,
-                                     "precision": "mixed", "tree_tc_min": args.tree_tc_min or None},
+                          "config": {"workload": "%s-sphere-ico%d-%d" % (args.operator, args.levels, len(t)),
+                                     "panels": len(t), "gauss_k": 3 if stokes else WORKLOAD["gauss_k"],
+                                     "theta": WORKLOAD["theta"], "ncrit": args.ncrit, "precision": "mixed",
+                                     "p2p_variant": args.p2p_variant, "tree_tc_min": args.tree_tc_min or None},
                           "n_m2l_pairs": st["n_m2l_pairs"], "n_m2l_tiles_tc": st["n_m2l_tiles_tc"],
                           "n_p2p_interactions": st["n_p2p_interactions"], "orders": rows}), flush=True)
     h.close()

@@ -330,7 +330,7 @@ void fmmbem_destroy(fmmbem_handle* h) {
     if (h->stream2) cudaStreamSynchronize(h->stream2);
     if (h->istream) cudaStreamSynchronize(h->istream);
     fmm_alloc_stream() = h->stream;
-    void* bufs[] = {h->perm, h->body, h->body_acc, h->rf_r, h->rf_d, h->tgt_d, h->tgt_f, h->nrm_d, h->nrm_f, h->verts, h->src_d, h->src_f, h->src_rel, h->tgt_rel, h->src_w, h->cell_cs, h->cell_range, h->cell_rad,
+    void* bufs[] = {h->perm, h->body, h->body_acc, h->rf_r, h->rf_d, h->tgt_d, h->tgt_f, h->nrm_d, h->nrm_f, h->nrm_pt, h->verts, h->src_d, h->src_f, h->src_rel, h->tgt_rel, h->src_w, h->cell_cs, h->cell_range, h->cell_rad,
                     h->cell_child, h->cell_level, h->cell_parent, h->leaves, h->parents, h->leaf_class, h->m2l_ptr, h->m2l_src, h->p2p_ptr,
                     h->p2p_src, h->p2p_rec, h->p2p_off, h->p2p_len, h->p2p_items, h->p2p_cnt, h->p2p_toff, h->stage_ptr, h->stage_first, h->stage_bytes, h->corr_ptr, h->corr_col, h->corr_sl, h->corr_dl, h->corr_sl_f, h->corr_dl_f, h->oct_d, h->oct_f, h->M, h->L,
                     h->xs, h->ys, h->ynear, h->ycorr, h->m2l_pt, h->m2l_ps, h->m2l_refl, h->sign_f, h->sign_d, h->m2l_tiles, h->tab_d, h->tab_f, h->tab_tc, h->m2l_tiles_tc, h->tc_src_info, h->tc_dst_info, h->tree_tab_tc, h->tree_tiles, h->tree_info, h->tc_err, h->kerr, h->V, h->kw, h->xfix, h->kb, h->kx, h->kr, h->kpart, h->kh, h->kyv, h->arn_bar};

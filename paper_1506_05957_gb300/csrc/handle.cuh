@@ -53,6 +53,7 @@ struct fmmbem_handle {
     float4* tgt_f = nullptr;
     double4* nrm_d = nullptr;     // [N] unit normal (x,y,z, area)
     float4* nrm_f = nullptr;      // [N] the same in FP32 (mixed-precision double layer)
+    float4* nrm_pt = nullptr;     // [N K] Stokes: each Gauss point's panel normal in FP32 (stresslet near field)
     double* verts = nullptr;      // [N][9] panel vertices
     double4* src_d = nullptr;     // [NS] Gauss point (x,y,z, q_k S_j), panel-major
     float4* src_f = nullptr;

@@ -969,6 +969,9 @@ __global__ void __launch_bounds__(32 * PS_WARPS, 7) k_p2p_lap_src(const int4* it
 //   u += f / r + d (d.f) / r^3.
 // - Laplace double layer (eq. gauss:2nd-kind): v = q_k S_j x_j n_j; one accumulator per
 //   target, at most P2P_SRC_TMAX targets per item; per pair phi += (d.v) / r^3.
+// - Stresslet double layer (eq. stresslet): v = u = q_k S_J u_J, and a third float4 per Gauss
+//   point, the source panel's normal n; three accumulators per target, at most
+//   P2P_SRC_TMAX_STOKES targets per item; per pair u += -6 (d.u)(d.n) d / r^5.
 // Accumulators are folded every PS_FOLD rounds into compensated per-lane sums.
 constexpr int SS_SRC = 2;  // sources per lane per round
 
@@ -978,6 +981,7 @@ template <int OP> struct VecLane;
 template <> struct VecLane<STK_SL> { static constexpr int DOF = 3, TM = P2P_SRC_TMAX_STOKES, MINB = 7; };
 template <> struct VecLane<LAP_DL> { static constexpr int DOF = 1, TM = P2P_SRC_TMAX, MINB = 7; };
 template <> struct VecLane<LAP_B4> { static constexpr int DOF = 4, TM = P2P_SRC_TMAX_BATCH, MINB = 6; };
+template <> struct VecLane<STK_DL> { static constexpr int DOF = 3, TM = P2P_SRC_TMAX_STOKES, MINB = 6; };
 
 // Both pack per panel (one FP64-to-FP32 conversion per unknown, as k_pack_sources).
 __global__ void k_pack_sources_stokes(const float4* src_rel, const double* xs, int K, int64_t n, float4* out) {
@@ -1044,11 +1048,12 @@ template <int OP> struct VlShared {
 // position and strength components are repeated in both halves; sk0/sk1 drop the pair's
 // first/second target (the source lies on that target's own panel).
 struct VlSrc {
-    f32x2 x, y, z, v0, v1, v2, v3;
+    f32x2 x, y, z, v0, v1, v2, v3, n0, n1, n2;
 };
-__device__ __forceinline__ VlSrc vl_src(float4 a, float4 b) {
+__device__ __forceinline__ VlSrc vl_src(float4 a, float4 b, float4 c) {
     return {f2_pack(a.x, a.x), f2_pack(a.y, a.y), f2_pack(a.z, a.z), f2_pack(a.w, a.w),
-            f2_pack(b.x, b.x), f2_pack(b.y, b.y), f2_pack(b.z, b.z)};
+            f2_pack(b.x, b.x), f2_pack(b.y, b.y), f2_pack(b.z, b.z), f2_pack(c.x, c.x),
+            f2_pack(c.y, c.y), f2_pack(c.z, c.z)};
 }
 
 template <int OP>
@@ -1073,6 +1078,14 @@ __device__ __forceinline__ void vl_pair(f32x2 tx, f32x2 ty, f32x2 tz, const VlSr
         acc[0] = f2_fma(u.v0, ir, f2_fma(dx, df, acc[0]));
         acc[1] = f2_fma(u.v1, ir, f2_fma(dy, df, acc[1]));
         acc[2] = f2_fma(u.v2, ir, f2_fma(dz, df, acc[2]));
+    } else if (OP == STK_DL) {
+        // 6 d (d.u)(e.n) / r^5 with e = -d: f = -6 (d.u)(d.n) / r^5
+        const f32x2 dn = f2_fma(dx, u.n0, f2_fma(dy, u.n1, f2_mul(dz, u.n2)));
+        const f32x2 ir5 = f2_mul(ir3, f2_mul(ir, ir));
+        const f32x2 f = f2_mul(f2_mul(dv, dn), f2_mul(f2_pack(-6.f, -6.f), ir5));
+        acc[0] = f2_fma(dx, f, acc[0]);
+        acc[1] = f2_fma(dy, f, acc[1]);
+        acc[2] = f2_fma(dz, f, acc[2]);
     } else {
         acc[0] = f2_fma(dv, ir3, acc[0]);
     }
@@ -1081,9 +1094,9 @@ __device__ __forceinline__ void vl_pair(f32x2 tx, f32x2 ty, f32x2 tz, const VlSr
 template <int OP>
 __global__ void __launch_bounds__(32 * PS_WARPS, VecLane<OP>::MINB) k_p2p_vec_src(const int4* items, const int2* range, const int* pptr,
                                                                  const float4* prec, const int* poff, const int* plen,
-                                                                 const float4* srcw, const float4* tgt, int K,
-                                                                 const double* yc, double* ynear, int64_t ssys,
-                                                                 int64_t xsys) {
+                                                                 const float4* srcw, const float4* snrm,
+                                                                 const float4* tgt, int K, const double* yc,
+                                                                 double* ynear, int64_t ssys, int64_t xsys) {
     constexpr int DOF = VecLane<OP>::DOF, TM = VecLane<OP>::TM;
     srcw += blockIdx.y * ssys;  // vector blockIdx.y of a Stokes batch: its strengths, corrections and output
     yc += blockIdx.y * xsys;
@@ -1098,6 +1111,8 @@ __global__ void __launch_bounds__(32 * PS_WARPS, VecLane<OP>::MINB) k_p2p_vec_sr
     const int total = plen[cell];
     float2* sHL = &sh.hl[warp][0][0];
     const float4 far_a = make_float4(1e18f, 0.f, 0.f, 0.f), zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    // the third float4 of a source: its panel's normal (stresslet only)
+    auto nrm_of = [&](int q) { return OP == STK_DL ? snrm[q] : zero4; };
     // targets in pairs; an odd count is padded with a far-away target whose sums are never read
     for (int i = threadIdx.x; i < ((ntb + 1) & ~1); i += blockDim.x) {
         const float4 x = i < ntb ? tgt[tb + i] : make_float4(1e18f, 1e18f, 1e18f, 0.f);
@@ -1161,7 +1176,8 @@ __global__ void __launch_bounds__(32 * PS_WARPS, VecLane<OP>::MINB) k_p2p_vec_sr
 #pragma unroll
             for (int h = 0; h < SS_SRC; ++h) {
                 const int q = base + 32 * h + lane;
-                u[h] = vl_src(q < n ? srcw[2 * (g0 + q)] : far_a, q < n ? srcw[2 * (g0 + q) + 1] : zero4);
+                u[h] = vl_src(q < n ? srcw[2 * (g0 + q)] : far_a, q < n ? srcw[2 * (g0 + q) + 1] : zero4,
+                              q < n ? nrm_of(g0 + q) : zero4);
                 gp[h] = q < n ? (g0 + q) / K : -1;
             }
             round(u, gp, true);
@@ -1188,7 +1204,7 @@ __global__ void __launch_bounds__(32 * PS_WARPS, VecLane<OP>::MINB) k_p2p_vec_sr
             // records first, then the round's source loads back to back (as k_p2p_lap_src)
             int rec[SS_SRC], g[SS_SRC];
             stream_slots<SS_SRC>(base, lane, s_end, woff, cur, rec, g);
-            float4 rc[SS_SRC], a[SS_SRC], b[SS_SRC];
+            float4 rc[SS_SRC], a[SS_SRC], b[SS_SRC], c[SS_SRC];
 #pragma unroll
             for (int h = 0; h < SS_SRC; ++h) rc[h] = wrec[max(rec[h], 0)];
 #pragma unroll
@@ -1196,11 +1212,12 @@ __global__ void __launch_bounds__(32 * PS_WARPS, VecLane<OP>::MINB) k_p2p_vec_sr
                 const int q = __float_as_int(rc[h].w) + g[h];
                 a[h] = rec[h] >= 0 ? srcw[2 * q] : far_a;
                 b[h] = rec[h] >= 0 ? srcw[2 * q + 1] : zero4;
+                c[h] = rec[h] >= 0 ? nrm_of(q) : zero4;
             }
 #pragma unroll
             for (int h = 0; h < SS_SRC; ++h) {
                 if (rec[h] >= 0) { a[h].x += rc[h].x; a[h].y += rc[h].y; a[h].z += rc[h].z; }
-                u[h] = vl_src(a[h], b[h]);
+                u[h] = vl_src(a[h], b[h], c[h]);
                 gp[h] = -1;
             }
             round(u, gp, false);
@@ -1343,6 +1360,7 @@ int init_near_attrs() {
     FMM_CU(cudaFuncSetAttribute(k_p2p_vec_src<STK_SL>, cudaFuncAttributePreferredSharedMemoryCarveout, c));
     FMM_CU(cudaFuncSetAttribute(k_p2p_vec_src<LAP_DL>, cudaFuncAttributePreferredSharedMemoryCarveout, c));
     FMM_CU(cudaFuncSetAttribute(k_p2p_vec_src<LAP_B4>, cudaFuncAttributePreferredSharedMemoryCarveout, c));
+    FMM_CU(cudaFuncSetAttribute(k_p2p_vec_src<STK_DL>, cudaFuncAttributePreferredSharedMemoryCarveout, c));
     return 0;
 }
 
@@ -1358,26 +1376,32 @@ static int launch_items(fmmbem_handle* h) {
         k_corr_rows<4><<<gc, 256, 0, h->stream>>>(n, h->corr_ptr, h->corr_col, h->corr_sl_f, h->xin, h->ycorr, h->N, 0);
         FMM_LAUNCHED();
         k_p2p_vec_src<LAP_B4><<<nb, 32 * PS_WARPS, 0, h->stream>>>(it, h->cell_range, h->p2p_ptr, h->p2p_rec, h->p2p_off,
-                                                                   h->p2p_len, h->src_w, h->tgt_rel, h->K, h->ycorr,
-                                                                   h->ynear, 0, 0);
+                                                                   h->p2p_len, h->src_w, nullptr, h->tgt_rel, h->K,
+                                                                   h->ycorr, h->ynear, 0, 0);
     } else if (h->kernel == FMMBEM_LAPLACE && h->layer == FMMBEM_LAYER_DOUBLE) {
         k_corr_rows<1><<<gc, 256, 0, h->stream>>>(n, h->corr_ptr, h->corr_col, h->corr_dl_f, h->xin, h->ycorr, 0, 0);
         FMM_LAUNCHED();
         k_p2p_vec_src<LAP_DL><<<nb, 32 * PS_WARPS, 0, h->stream>>>(it, h->cell_range, h->p2p_ptr, h->p2p_rec, h->p2p_off,
-                                                                   h->p2p_len, h->src_w, h->tgt_rel, h->K, h->ycorr,
-                                                                   h->ynear, 0, 0);
+                                                                   h->p2p_len, h->src_w, nullptr, h->tgt_rel, h->K,
+                                                                   h->ycorr, h->ynear, 0, 0);
     } else if (h->kernel == FMMBEM_LAPLACE) {
         k_corr_rows<1><<<gc, 256, 0, h->stream>>>(n, h->corr_ptr, h->corr_col, h->corr_sl_f, h->xin, h->ycorr, 0, 0);
         FMM_LAUNCHED();
         k_p2p_lap_src<<<nb, 32 * PS_WARPS, 0, h->stream>>>(it, h->cell_range, h->p2p_ptr, h->p2p_rec, h->p2p_off,
                                                           h->p2p_len, h->src_w, h->tgt_rel, h->K, h->ycorr, h->ynear);
+    } else if (h->layer == FMMBEM_LAYER_DOUBLE) {  // the stresslet (one vector)
+        k_corr_rows<3><<<gc, 256, 0, h->stream>>>(n, h->corr_ptr, h->corr_col, h->corr_dl_f, h->xin, h->ycorr, 0, 0);
+        FMM_LAUNCHED();
+        k_p2p_vec_src<STK_DL><<<nb, 32 * PS_WARPS, 0, h->stream>>>(it, h->cell_range, h->p2p_ptr, h->p2p_rec, h->p2p_off,
+                                                                   h->p2p_len, h->src_w, h->nrm_pt, h->tgt_rel, h->K,
+                                                                   h->ycorr, h->ynear, 0, 0);
     } else {  // the Stokeslet: one launch for every vector of a batch (blockIdx.y)
         k_corr_rows<3><<<dim3(gc, h->nsys), 256, 0, h->stream>>>(n, h->corr_ptr, h->corr_col, h->corr_sl_f, h->xin,
                                                                  h->ycorr, 0, 3 * h->N);
         FMM_LAUNCHED();
         k_p2p_vec_src<STK_SL><<<dim3(nb, h->nsys), 32 * PS_WARPS, 0, h->stream>>>(
-            it, h->cell_range, h->p2p_ptr, h->p2p_rec, h->p2p_off, h->p2p_len, h->src_w, h->tgt_rel, h->K, h->ycorr,
-            h->ynear, 2 * h->NS, 3 * h->N);
+            it, h->cell_range, h->p2p_ptr, h->p2p_rec, h->p2p_off, h->p2p_len, h->src_w, nullptr, h->tgt_rel, h->K,
+            h->ycorr, h->ynear, 2 * h->NS, 3 * h->N);
     }
     FMM_LAUNCHED();
     h->launches += 2;
@@ -1397,9 +1421,13 @@ int near_field_on(fmmbem_handle* h, bool fp64) {
             h->launches += 1;
         }
     } else if (h->kernel == FMMBEM_STOKES && h->layer == FMMBEM_LAYER_DOUBLE) {
-        // the stresslet double layer: the shared-tile schedule with the FP64 3x3 correction rows
-        FMM_TRY((fp64 ? launch_p2p<double, STK_DL>(h, h->corr_dl) : launch_p2p<float, STK_DL>(h, h->corr_dl)));
-        h->launches += 1;
+        // the stresslet double layer: the work-item kernel (mixed precision), else the
+        // shared-tile schedule with the FP64 3x3 correction rows
+        if (items && h->nrm_pt) FMM_TRY(launch_items(h));
+        else {
+            FMM_TRY((fp64 ? launch_p2p<double, STK_DL>(h, h->corr_dl) : launch_p2p<float, STK_DL>(h, h->corr_dl)));
+            h->launches += 1;
+        }
     } else if (h->kernel == FMMBEM_LAPLACE && h->layer == FMMBEM_LAYER_DOUBLE) {
         if (items) FMM_TRY(launch_items(h));
         else {

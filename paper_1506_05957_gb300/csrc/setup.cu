@@ -605,6 +605,12 @@ __device__ void rule_sums(const double* P, const double4 nj, const double* c, co
     }
 }
 
+// The FP32 normal of each Gauss point's panel (sorted order: Gauss point g lies on panel g / K).
+__global__ void k_point_normals(const float4* nrm_f, int K, int64_t ns, float4* out) {
+    const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (g < ns) out[g] = nrm_f[g / K];
+}
+
 // Round FP64 values to FP32 (the mixed-precision correction pass reads the rounded table).
 __global__ void k_round_f32(const double* in, int64_t n, float* out) {
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
@@ -761,6 +767,11 @@ int build_geometry_tree_lists(fmmbem_handle* h, const fmmbem_mesh* mesh) {
     k_gather_sorted<<<gn, T, 0, st>>>(h->perm, n, dv, dt, cen, nrm, quad, K, h->tgt_d, h->tgt_f, h->nrm_d, h->nrm_f,
                                       h->verts, h->src_d, h->src_f);
     FMM_LAUNCHED();
+    if (h->kernel == FMMBEM_STOKES) {  // the stresslet near field reads each source's normal with it
+        FMM_TRY(dalloc(&h->nrm_pt, h->NS));
+        k_point_normals<<<(unsigned)((h->NS + T - 1) / T), T, 0, st>>>(h->nrm_f, K, h->NS, h->nrm_pt);
+        FMM_LAUNCHED();
+    }
 
     // ---- octree, level by level
     {

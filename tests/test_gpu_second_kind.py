@@ -211,6 +211,32 @@ def test_stokes_double_layer_direct_and_fmm(torch_cuda, stokes1280):
         assert rel(y.cpu().numpy(), ref) < 1e-5, p
 
 
+def test_stresslet_near_field_schedules_agree(torch_cuda, stokes1280):
+    """The stresslet's work-item near field (source lanes, three FP32 accumulators per target,
+    each source's panel normal read beside it) and the shared-tile schedule compute the same
+    FP32 sums; both stay within the mixed-precision bound of the oracle's dense operator, at
+    leaf capacities that give one-target and ragged work items."""
+    torch = torch_cuda
+    from paper_1506_05957_gb300 import FMMBEM_MIXED
+    s = stokes1280
+    x = np.random.default_rng(6).standard_normal(3 * len(s["t"]))
+    ref = s["A"] @ x
+    for ncrit in (20, 60, 300):
+        h = _stokes_dl(s["v"], s["t"], ncrit=ncrit, precision=FMMBEM_MIXED)
+        xd = _dev(torch, x)
+        ys = {}
+        for variant in (3, 0):
+            h.set_p2p_variant(variant)
+            for p in (8, 14):
+                y = torch.zeros_like(xd)
+                h.matvec(p, xd, y)
+                ys[(variant, p)] = y.cpu().numpy()
+        h.close()
+        assert rel(ys[(3, 14)], ref) < 1e-5, (ncrit, rel(ys[(3, 14)], ref))
+        for p in (8, 14):
+            assert rel(ys[(3, p)], ys[(0, p)]) < 2e-6, (ncrit, p, rel(ys[(3, p)], ys[(0, p)]))
+
+
 def test_stokes_second_kind_relaxed_solve(torch_cuda, stokes1280):
     """Velocity from the second-kind system for data of a rigid motion plus a smooth field:
     the GPU solution meets the oracle residual and equals the oracle's solution up to the
