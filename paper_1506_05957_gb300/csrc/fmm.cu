@@ -150,15 +150,24 @@ __global__ void __launch_bounds__(32 * P2M_WARPS) k_p2m(int p, const int* leaves
 // MODE 1: the double layer's dipoles (two float4 per Gauss point, the moment w n in .w of
 // the first and .x, .y of the second), scattered as in k_p2m_dl. MODE 2: a batch of four
 // vectors (strengths in .w of the first float4 and .x, .y, .z of the second), four
-// expansions per cell.
+// expansions per cell. MODE 3: the Stokeslet's four Laplace expansions (Sec. 2.5 for Stokes:
+// strengths w t_x, w t_y, w t_z packed as for the near field, and w t.(y - o), o the handle's
+// origin, formed here from the cell centre's offset to o and the point's position in the
+// leaf); the vector of a Stokes batch is blockIdx.y (its sources ssys float4 apart, its
+// expansions msys reals apart).
 constexpr int P2MP_WARPS = 4;
-template <int MODE> struct P2mSpl { static constexpr int v = MODE == 2 ? 2 : 4; };
+template <int MODE> struct P2mSpl { static constexpr int v = MODE >= 2 ? 2 : 4; };
 
 template <int MODE>
 __global__ void __launch_bounds__(32 * P2MP_WARPS) k_p2m_packed(int p, const int* leaves, const double4* cs,
-                                                               const int2* range, const float4* srcw, int K, float* M) {
+                                                               const int2* range, const float4* srcw, int K, float* M,
+                                                               double ox = 0.0, double oy = 0.0, double oz = 0.0,
+                                                               int64_t ssys = 0, size_t msys = 0) {
     constexpr bool DL = MODE == 1;
-    constexpr int NC = MODE == 2 ? 4 : 1;
+    constexpr bool QUAD = MODE >= 2;  // four strengths per point, four expansions per cell
+    constexpr int NC = QUAD ? 4 : 1;
+    srcw += blockIdx.y * ssys;
+    M += blockIdx.y * msys;
     constexpr int SPL = P2mSpl<MODE>::v;
     extern __shared__ unsigned char smem_raw[];
     float* acc = reinterpret_cast<float*>(smem_raw);  // [warps][NC][ncoef][2]
@@ -168,7 +177,14 @@ __global__ void __launch_bounds__(32 * P2MP_WARPS) k_p2m_packed(int p, const int
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int q = threadIdx.x; q < P2MP_WARPS * NC * nco * 2; q += blockDim.x) acc[q] = 0.f;
     __shared__ float s_inv;  // 1 / side: one FP64 division per block (FP64 is scarce on this GPU)
-    if (threadIdx.x == 0) s_inv = (float)(1.0 / cs[cell].w);
+    __shared__ float s_co[3];  // MODE 3: the cell centre minus the origin
+    if (threadIdx.x == 0) {
+        const double4 cc = cs[cell];
+        s_inv = (float)(1.0 / cc.w);
+        s_co[0] = (float)(cc.x - ox);
+        s_co[1] = (float)(cc.y - oy);
+        s_co[2] = (float)(cc.z - oz);
+    }
     __syncthreads();
     float* wacc = acc + warp * NC * nco * 2;
     const float inv_s = s_inv;
@@ -203,6 +219,11 @@ __global__ void __launch_bounds__(32 * P2MP_WARPS) k_p2m_packed(int p, const int
                     const float4 u = srcw[2 * s], u2 = srcw[2 * s + 1];
                     vx[h] = u.x * inv_s; vy[h] = u.y * inv_s; vz[h] = u.z * inv_s;
                     qb[h][0] = u.w; qb[h][1] = u2.x; qb[h][2] = u2.y; qb[h][3] = u2.z;
+                } else if (MODE == 3) {
+                    const float4 u = srcw[2 * s], u2 = srcw[2 * s + 1];
+                    vx[h] = u.x * inv_s; vy[h] = u.y * inv_s; vz[h] = u.z * inv_s;
+                    qb[h][0] = u.w; qb[h][1] = u2.x; qb[h][2] = u2.y;
+                    qb[h][3] = u.w * (s_co[0] + u.x) + u2.x * (s_co[1] + u.y) + u2.y * (s_co[2] + u.z);
                 } else if (DL) {
                     const float4 u = srcw[2 * s], u2 = srcw[2 * s + 1];
                     vx[h] = u.x * inv_s; vy[h] = u.y * inv_s; vz[h] = u.z * inv_s;
@@ -222,7 +243,7 @@ __global__ void __launch_bounds__(32 * P2MP_WARPS) k_p2m_packed(int p, const int
         for (int k = 0; k < NP; ++k) q2[k] = f2_pack(q[2 * k], q[2 * k + 1]);
         // R_n^m of the lane's points, held as pairs of points (re and im of points 2k, 2k + 1)
         auto emit = [&](int n, int m, const f32x2 (&Rre)[NP], const f32x2 (&Rim)[NP]) {
-            if (!DL && MODE != 2) {  // single layer: sum_h q_h R_h with paired multiply-adds
+            if (!DL && !QUAD) {  // single layer: sum_h q_h R_h with paired multiply-adds
                 f32x2 sre = f2_mul(q2[0], Rre[0]), sim = f2_mul(q2[0], Rim[0]);
 #pragma unroll
                 for (int k = 1; k < NP; ++k) {
@@ -254,7 +275,7 @@ __global__ void __launch_bounds__(32 * P2MP_WARPS) k_p2m_packed(int p, const int
                 if (m >= 1) add(0, n + 1, m - 1, t1);
                 add(0, n + 1, m + 1, mk(-t2.re, -t2.im));
                 if (m == 1) add(0, n + 1, 0, t3);
-            } else if (MODE == 2) {
+            } else if (QUAD) {
 #pragma unroll
                 for (int cc = 0; cc < 4; ++cc) {
                     cpx<float> t = mk(0.f, 0.f);
@@ -998,11 +1019,16 @@ int far_field_t(fmmbem_handle* h, int p) {
     // P2M
     prof_begin(h, FMMBEM_PASS_P2M);
     const size_t sm = (size_t)P2M_WARPS * NC * nco * 2 * sizeof(T);
-    if (std::is_same<T, float>::value && (NC == 1 || (h->nrhs > 1 && h->kernel == FMMBEM_LAPLACE))) {
+    const bool stokeslet = NC == 4 && h->kernel == FMMBEM_STOKES && h->layer != FMMBEM_LAYER_DOUBLE;
+    if (std::is_same<T, float>::value && (NC == 1 || (h->nrhs > 1 && h->kernel == FMMBEM_LAPLACE) || stokeslet)) {
         // mixed precision: the packed FP32 sources
         float* Mf = reinterpret_cast<float*>(h->M);
         const size_t smp = (size_t)P2MP_WARPS * NC * nco * 2 * sizeof(float);
-        if (h->nrhs > 1)
+        if (stokeslet)
+            k_p2m_packed<3><<<dim3(h->n_leaves, h->nsys), 32 * P2MP_WARPS, smp, st>>>(
+                p, h->leaves, h->cell_cs, h->cell_range, h->src_w, h->K, Mf, h->origin[0], h->origin[1], h->origin[2],
+                2 * h->NS, h->esys);
+        else if (h->nrhs > 1)
             k_p2m_packed<2><<<h->n_leaves, 32 * P2MP_WARPS, smp, st>>>(p, h->leaves, h->cell_cs, h->cell_range,
                                                                       h->src_w, h->K, Mf);
         else if (h->layer == FMMBEM_LAYER_DOUBLE)
