@@ -299,11 +299,11 @@ def run_ours(args, world, rank, local):
     if args.tune_ncrit:
         cand = [int(c) for c in args.tune_ncrit.split(",")]
         h = FmmBem.tuned(v, t, ncrit_candidates=cand, p_lo=W["p_min"], p_hi=W["p_initial"], gauss_k=W["gauss_k"],
-                         theta=W["theta"], p_max=16, restart=W["restart"], max_iter=100, precision=FMMBEM_MIXED,
+                         theta=W["theta"], p_max=W["p_initial"], restart=W["restart"], max_iter=100, precision=FMMBEM_MIXED,
                          stream=stream.cuda_stream)
         args.ncrit = h.tuned_ncrit
     else:
-        h = FmmBem(v, t, gauss_k=W["gauss_k"], ncrit=args.ncrit, theta=W["theta"], p_max=16, restart=W["restart"],
+        h = FmmBem(v, t, gauss_k=W["gauss_k"], ncrit=args.ncrit, theta=W["theta"], p_max=W["p_initial"], restart=W["restart"],
                    max_iter=100, precision=FMMBEM_MIXED, stream=stream.cuda_stream)
     stats = h.stats()
     phi_d = torch.tensor(phi, dtype=torch.float64, device=dev)
