@@ -501,19 +501,13 @@ __global__ void k_leaves(const int2* child, const int2* range, int ncells, int* 
 
 // ---------------------------------------------------------------- near-singular search
 // For sorted target panel i: every panel j with j == i or |c_i - c_j|^2 < f^2 2 S_j,
-// found by a depth-first walk that prunes cells farther than f sqrt(2 S_max). FP64 throughput
-// is scarce on this GPU, so each candidate panel's test takes its coordinate differences in
-// FP64 and the rest in FP32, which decides only outside a band of 1e-5 around the threshold
-// (the FP32 rounding of d^2 and of the threshold is below 1e-6 relative, whatever the
-// coordinates' size); inside the band the FP64 test decides, so the set found is exactly the
-// FP64 criterion's.
+// found by a depth-first walk that prunes cells farther than f sqrt(2 S_max).
 template <bool FILL>
 __global__ void k_near_search(const double4* tgt, int n, const double4* cs, const int2* child, const int2* range,
                               double f2, double r2max, int* count, const int* ptr, int* col, int* row) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const double4 ci = tgt[i];
-    const float f2x2 = (float)(2.0 * f2);
     int stack[8 * MAX_LEVELS + 8];
     int sp = 0;
     stack[sp++] = 0;
@@ -531,18 +525,8 @@ __global__ void k_near_search(const double4* tgt, int n, const double4* cs, cons
             const int2 r = range[c];
             for (int j = r.x; j < r.y; ++j) {
                 const double4 cj = tgt[j];
-                const float dx = (float)(ci.x - cj.x), dy = (float)(ci.y - cj.y), dz = (float)(ci.z - cj.z);
-                const float d2 = dx * dx + dy * dy + dz * dz, thr = f2x2 * (float)cj.w;
-                bool near;
-                if (d2 < thr * (1.f - 1e-5f)) {
-                    near = true;
-                } else if (d2 > thr * (1.f + 1e-5f)) {
-                    near = false;
-                } else {  // at the threshold: the FP64 test
-                    const double ddx = ci.x - cj.x, ddy = ci.y - cj.y, ddz = ci.z - cj.z;
-                    near = ddx * ddx + ddy * ddy + ddz * ddz < f2 * 2.0 * cj.w;
-                }
-                if (j == i || near) {
+                const double dx = ci.x - cj.x, dy = ci.y - cj.y, dz = ci.z - cj.z;
+                if (j == i || dx * dx + dy * dy + dz * dz < f2 * 2.0 * cj.w) {
                     if (FILL) { col[out + k] = j; row[out + k] = i; }
                     ++k;
                 }
