@@ -109,7 +109,7 @@ struct fmmbem_handle {
     float* tab_tc = nullptr;
     size_t tc_stride = 0;
     int tc_rows_max = 0;
-    int tc_kc = 32;               // K width of the tensor-core operand chunks (tables and kernel)
+    int tc_kc = 16;               // K width of the tensor-core operand chunks (tables and kernel)
     int4* m2l_tiles_tc = nullptr;
     int n_tiles_tc = 0;
     int* tc_src_info = nullptr;   // [n_tiles_tc][128]: source row offset * 8 + reflection (-1: empty row)

@@ -25,9 +25,11 @@ namespace fmmbem {
 namespace {
 
 constexpr int TC_ROWS = 128;  // rows per tile (MMA M)
-// K per staged chunk, a kernel template parameter: 32 for handles of one expansion per row
-// group (fewer, larger pipeline items), 16 when four or more expansions per pair make a
-// stage large (p = 16 Stokes: three 56 KB stages in flight instead of one of 112 KB).
+// K per staged chunk (a kernel template parameter): 16 for every handle. Against 32-wide
+// chunks a lone M2L at p <= 12 is a few percent slower, but p = 16 keeps three stages in flight
+// instead of one, the split tree levels get more K ranges, and at low p the CTA's smaller
+// footprint leaves room for a near-field block beside it: the concurrent solve is faster.
+constexpr int TC_KC = 16;
 template <int KC> struct Kc {
     static_assert(KC % 16 == 0, "a gather lane covers whole k-quads of 16-wide steps");
     static constexpr int KQ = KC / 4;           // k-quads (core matrices along K) per chunk
@@ -47,7 +49,7 @@ __device__ __forceinline__ float tf32_hi(float x) {
     return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
 }
 
-// Operator tables for this path: per operator, per 32-wide input chunk c, the hi and
+// Operator tables for this path: per operator, per KC-wide input chunk c, the hi and
 // lo parts of rows [0, rows_max) in the core-matrix layout:
 //   tab[g][c][h][cm_index<KC>(r, k mod KC)], h = 0 (hi) or 1 (lo).
 template <int KC>
@@ -96,7 +98,7 @@ constexpr int TC_THREADS = 32 * TC_WARPS;
 constexpr int TC_PROD0 = 2, TC_NPROD = 8, TC_EPI0 = 10;
 constexpr int EPI_LD = 33;  // padded row length of the epilogue transpose buffer
 constexpr int TC_SMEM_BUDGET = 222 * 1024;
-constexpr int TC_SIGN_TAB = 16 * 8;  // (K chunk, k-quad) entries: chunks of 32 reals up to 2 ncoef(P_MAX) <= 320
+constexpr int TC_SIGN_TAB = 16 * 8;  // k-quad entries: 512 reals cover 2 ncoef(P_MAX) <= 320
 
 struct TcLayout {
     int nst, nb, np, kc;
@@ -624,8 +626,7 @@ size_t m2l_tc_smem(const fmmbem_handle* h, int p) { return tc_layout(p, h->tc_kc
 // The operator tables in the handle's chunk layout.
 static void launch_tc_tables(const fmmbem_handle* h, unsigned grid, const double* Td, int ntab, int nr, int ld, int nch,
                              int rows_max, float* out, cudaStream_t st) {
-    if (h->tc_kc == 16) k_tc_tables<16><<<grid, 256, 0, st>>>(Td, ntab, nr, ld, nch, rows_max, out);
-    else k_tc_tables<32><<<grid, 256, 0, st>>>(Td, ntab, nr, ld, nch, rows_max, out);
+    k_tc_tables<TC_KC><<<grid, 256, 0, st>>>(Td, ntab, nr, ld, nch, rows_max, out);
 }
 
 // M2M and L2L of each level as tensor-core products: the pairs (parent at level l, child)
@@ -712,8 +713,7 @@ int build_m2l_tc(fmmbem_handle* h) {
     const int pmax = h->opts.p_max;
     const int nr = 2 * ncoef(pmax);
     const int rows_max = (nr + 15) & ~15;
-    // 16-wide chunks when a pair carries four or more expansions (their stages are large)
-    h->tc_kc = h->ncomp * h->nsys >= 4 ? 16 : 32;
+    h->tc_kc = TC_KC;
     const int nch = (nr + h->tc_kc - 1) / h->tc_kc;
     const size_t per_tab = (size_t)nch * 2 * rows_max * h->tc_kc;
     FMM_CU(fmm_malloc((void**)&h->tab_tc, sizeof(float) * per_tab * (size_t)h->n_tables));
@@ -734,13 +734,8 @@ int build_m2l_tc(fmmbem_handle* h) {
     FMM_TRY(build_tree_tc(h, nr, rows_max, nch));
     size_t smax = 0;
     for (int q = 1; q <= pmax; ++q) smax = std::max(smax, m2l_tc_smem(h, q));
-    if (h->tc_kc == 16) {
-        FMM_CU(cudaFuncSetAttribute(k_m2l_tc<16, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smax));
-        FMM_CU(cudaFuncSetAttribute(k_m2l_tc<16, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smax));
-    } else {
-        FMM_CU(cudaFuncSetAttribute(k_m2l_tc<32, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smax));
-        FMM_CU(cudaFuncSetAttribute(k_m2l_tc<32, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smax));
-    }
+    FMM_CU(cudaFuncSetAttribute(k_m2l_tc<TC_KC, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smax));
+    FMM_CU(cudaFuncSetAttribute(k_m2l_tc<TC_KC, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smax));
     int dev = 0;
     FMM_CU(cudaGetDevice(&dev));
     FMM_CU(cudaDeviceGetAttribute(&h->n_sm, cudaDevAttrMultiProcessorCount, dev));
@@ -797,11 +792,7 @@ int tree_tc(fmmbem_handle* h, int p, int level, int which) {
     const int ks = std::max(1, std::min(nch, h->n_sm / nt));
     const int grid = std::min(nt * ks, h->n_sm);
     const size_t sm = m2l_tc_smem(h, p);
-    if (h->tc_kc == 16)
-        FMM_CU((launch_tc<16, true>(grid, sm, h->stream, p, 3, tiles, nt, ks, src, dst, h->tree_tab_tc, h->tc_stride,
-                                   h->tc_rows_max, X, X, h->tc_err)));
-    else
-        FMM_CU((launch_tc<32, true>(grid, sm, h->stream, p, 3, tiles, nt, ks, src, dst, h->tree_tab_tc, h->tc_stride,
+    FMM_CU((launch_tc<TC_KC, true>(grid, sm, h->stream, p, 3, tiles, nt, ks, src, dst, h->tree_tab_tc, h->tc_stride,
                                    h->tc_rows_max, X, X, h->tc_err)));
     return 0;
 }
@@ -821,11 +812,7 @@ int m2l_tc(fmmbem_handle* h, int p) {
     const int grid = std::min(h->n_tiles_tc, h->n_sm);  // persistent: one CTA per SM (512 TMEM columns each)
     const int prods = 3;
     if (grid <= 0) return 0;
-    if (h->tc_kc == 16)
-        FMM_CU((launch_tc<16, false>(grid, sm, h->stream, p, prods, h->m2l_tiles_tc, h->n_tiles_tc, 1, h->tc_src_info,
-                                    h->tc_dst_info, h->tab_tc, h->tc_stride, h->tc_rows_max, M, L, h->tc_err)));
-    else
-        FMM_CU((launch_tc<32, false>(grid, sm, h->stream, p, prods, h->m2l_tiles_tc, h->n_tiles_tc, 1, h->tc_src_info,
+    FMM_CU((launch_tc<TC_KC, false>(grid, sm, h->stream, p, prods, h->m2l_tiles_tc, h->n_tiles_tc, 1, h->tc_src_info,
                                     h->tc_dst_info, h->tab_tc, h->tc_stride, h->tc_rows_max, M, L, h->tc_err)));
     return 0;
 }
