@@ -100,29 +100,55 @@ constexpr int EPI_LD = 33;  // padded row length of the epilogue transpose buffe
 constexpr int TC_SMEM_BUDGET = 222 * 1024;
 constexpr int TC_SIGN_TAB = 16 * 8;  // k-quad entries: 512 reals cover 2 ncoef(P_MAX) <= 320
 
+// Stages, accumulators and TMEM columns of one order. With atm (A in TMEM) a stage's gathered
+// rows (TF32 hi and lo, 2 kc columns) live in the last nst * 2 kc TMEM columns and shared
+// memory holds only the operator chunks; the accumulators take what is left.
 struct TcLayout {
-    int nst, nb, np, kc;
-    __host__ __device__ int stage_floats() const { return 2 * TC_ROWS * kc + 2 * np * kc; }
+    int nst, nb, np, kc, buf_cols;
+    bool atm;
+    __host__ __device__ int a_floats() const { return atm ? 0 : 2 * TC_ROWS * kc; }
+    __host__ __device__ int stage_floats() const { return a_floats() + 2 * np * kc; }
     __host__ __device__ int epi_floats() const { return 8 * 32 * EPI_LD; }
+    __host__ __device__ int a_col0() const { return 512 - nst * 2 * kc; }  // first A column (atm)
     __host__ __device__ size_t bytes() const {
         return (size_t)(nst * stage_floats() + epi_floats()) * sizeof(float) + 16 * 8 + 64 + 2 * TC_SIGN_TAB * 4;
     }
 };
 
-__host__ __device__ inline TcLayout tc_layout(int p, int kc) {
+__host__ __device__ inline TcLayout tc_layout(int p, int kc, bool atm) {
     TcLayout t;
     t.kc = kc;
+    t.atm = atm;
     const int R = 2 * ncoef(p);
     t.np = (R + 15) & ~15;
     t.nb = t.np <= 128 ? 4 : (t.np <= 256 ? 2 : 1);
+    t.buf_cols = 512 / t.nb;
     t.nst = 1;
     for (int n = 4; n >= 1; --n) {
         t.nst = n;
-        if ((size_t)(n * t.stage_floats() + t.epi_floats()) * sizeof(float) + 16 * 8 + 64 + 2 * TC_SIGN_TAB * 4 <=
-            (size_t)TC_SMEM_BUDGET)
-            break;
+        if (t.bytes() <= (size_t)TC_SMEM_BUDGET) break;
+    }
+    if (atm) {
+        // accumulators of 32-column multiples beside the A stages; fewer stages (down to two)
+        // when that keeps a second accumulator. The count stays 1, 2 or 4: with two epilogue
+        // groups, group g drains units j = g mod 2, and an even count keeps each accumulator
+        // with one group (whose waits then follow its phases in order).
+        t.buf_cols = (t.np + 31) & ~31;
+        auto nb_of = [&](int nst) { return (512 - nst * 2 * kc) / t.buf_cols; };
+        while (t.nst > 2 && nb_of(t.nst) < 2 && t.np <= 256) --t.nst;
+        const int nb = nb_of(t.nst);
+        t.nb = nb >= 4 ? 4 : (nb >= 2 ? 2 : nb);
     }
     return t;
+}
+
+// The TMEM-operand variant where it keeps as many accumulators as the shared-memory one (up
+// to two) and at least three stages where that one has them. Measured alone, p = 12: 277
+// against 303 us; p = 16: 747 against 806 us; p = 13, where two accumulators leave two
+// stages: 411 against 369 us (p = 13 and 14 keep the shared-memory variant).
+__host__ __device__ inline bool tc_atm_at(int p, int kc) {
+    const TcLayout a = tc_layout(p, kc, true), s = tc_layout(p, kc, false);
+    return a.nb >= 1 && a.nb >= (s.nb < 2 ? s.nb : 2) && a.nst >= (s.nst < 3 ? s.nst : 3);
 }
 
 // Reflection sign bits of a float4 of real coefficients (re_a, im_a, re_b, im_b),
@@ -177,13 +203,13 @@ __device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
 
 // rinfo[t * 128 + r] = (row offset of pair row r of tile t in the expansion array) * 8 + reflection,
 // -1 past the tile's rows; one table for the sources (gather) and one for the targets (epilogue).
-template <int KC, bool SPLIT>
+template <int KC, bool SPLIT, bool ATM>
 __global__ void __launch_bounds__(TC_THREADS, 1) k_m2l_tc(int p, int prods, const int4* tiles, int ntiles, int ksplit_arg,
                                                          const int* src_info, const int* dst_info, const float* tab,
                                                          size_t tab_stride, int rows_max, const float* M, float* L,
                                                          int* err) {
     extern __shared__ __align__(1024) unsigned char smem[];
-    const TcLayout lay = tc_layout(p, KC);
+    const TcLayout lay = tc_layout(p, KC, ATM);
     const int R = 2 * ncoef(p);
     const int R8 = (R + 7) & ~7;  // K extent the MMAs read: k-steps of 8 that start below R
     const int Np = lay.np, NST = lay.nst, NB = lay.nb;
@@ -205,8 +231,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_m2l_tc(int p, int prods, cons
     auto acc_empty = [&](int b) { return smem_u32(&bar[12 + b]); };
     auto xh = [&](int st) { return stage0 + st * sf; };
     auto xl = [&](int st) { return stage0 + st * sf + TC_ROWS * KC; };
-    auto th = [&](int st) { return stage0 + st * sf + 2 * TC_ROWS * KC; };
-    auto tl = [&](int st) { return stage0 + st * sf + 2 * TC_ROWS * KC + Np * KC; };
+    auto th = [&](int st) { return stage0 + st * sf + lay.a_floats(); };
+    auto tl = [&](int st) { return stage0 + st * sf + lay.a_floats() + Np * KC; };
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     for (int e = tid; e < TC_SIGN_TAB; e += blockDim.x) {
@@ -239,7 +265,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_m2l_tc(int p, int prods, cons
     // everything above (barriers, sign tables, TMEM) may overlap the previous kernel of the
     // stream; the expansions it writes are read and accumulated only after it has completed
     asm volatile("griddepcontrol.wait;" ::: "memory");
-    const uint32_t buf_cols = (uint32_t)(512 / NB);
+    const uint32_t buf_cols = (uint32_t)lay.buf_cols;
     // Work units are (tile, range of K chunks): the nch chunks of a tile are cut into ksplit
     // ranges (split-K for launches with fewer tiles than SMs; the epilogue adds each range's
     // partial product like any other). Unit u covers tile u / ksplit, range u mod ksplit; the
@@ -324,23 +350,31 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_m2l_tc(int p, int prods, cons
                 asm volatile("tcgen05.fence::after_thread_sync;");
                 const uint32_t acc = taddr + (uint32_t)b * buf_cols;
                 const uint32_t ah = smem_u32(xh(st)), al = smem_u32(xl(st)), bh = smem_u32(th(st)), bl = smem_u32(tl(st));
+                const uint32_t at = taddr + (uint32_t)(lay.a_col0() + st * 2 * KC);  // the stage's A columns (ATM)
+                // D (+)= A B^T with k-step ks of A's hi or lo part, from TMEM or shared memory
+                auto mma_a = [&](uint32_t d, bool lo, int ks, uint64_t bdesc, uint32_t id, uint32_t accum) {
+                    if constexpr (ATM)
+                        mma_tf32_ts(d, at + (lo ? (uint32_t)KC : 0u) + 8u * ks, bdesc, id, accum);
+                    else
+                        mma_tf32(d, smem_desc((lo ? al : ah) + 256u * ks, 128, Kc<KC>::SBO), bdesc, id, accum);
+                };
                 for (int ks = 0; ks < KC / 8; ++ks) {
                     if (c * KC + 8 * ks >= R) break;  // the rest of the chunk lies past degree p
                     const uint32_t off = 256u * ks;
-                    const uint64_t a_hi = smem_desc(ah + off, 128, Kc<KC>::SBO), b_hi = smem_desc(bh + off, 128, Kc<KC>::SBO);
+                    const uint64_t b_hi = smem_desc(bh + off, 128, Kc<KC>::SBO);
                     const uint32_t first = (c == c0 && ks == 0) ? 0u : 1u;
-                    mma_tf32(acc, a_hi, b_hi, id1, first);
+                    mma_a(acc, false, ks, b_hi, id1, first);
                     if (prods == 3) {
-                        mma_tf32(acc, a_hi, smem_desc(bl + off, 128, Kc<KC>::SBO), id1, 1u);
-                        mma_tf32(acc, smem_desc(al + off, 128, Kc<KC>::SBO), b_hi, id1, 1u);
+                        mma_a(acc, false, ks, smem_desc(bl + off, 128, Kc<KC>::SBO), id1, 1u);
+                        mma_a(acc, true, ks, b_hi, id1, 1u);
                     }
                     if (Np > 256) {
                         const uint32_t boff = 32u * Kc<KC>::SBO;  // operator rows 256.. start 32 row groups later
                         const uint64_t b2_hi = smem_desc(bh + off + boff, 128, Kc<KC>::SBO);
-                        mma_tf32(acc + 256, a_hi, b2_hi, id2, first);
+                        mma_a(acc + 256, false, ks, b2_hi, id2, first);
                         if (prods == 3) {
-                            mma_tf32(acc + 256, a_hi, smem_desc(bl + off + boff, 128, Kc<KC>::SBO), id2, 1u);
-                            mma_tf32(acc + 256, smem_desc(al + off, 128, Kc<KC>::SBO), b2_hi, id2, 1u);
+                            mma_a(acc + 256, false, ks, smem_desc(bl + off + boff, 128, Kc<KC>::SBO), id2, 1u);
+                            mma_a(acc + 256, true, ks, b2_hi, id2, 1u);
                         }
                     }
                 }
@@ -371,6 +405,100 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_m2l_tc(int p, int prods, cons
         // unit j + 3 when item i starts unit j, a whole unit before the gathers that use them.
         // Item counters (unit, chunk, stage, phase) advance incrementally; signs and the order-p
         // mask come from the CTA's tables.
+      if constexpr (ATM) {
+        // ---------------- gather producers, A operand in TMEM: warp w may write TMEM lanes
+        // 32 (w mod 4) .. + 31 only, so lane l of warp w gathers tile row 32 (w mod 4) + l, and
+        // the two warps of a quadrant take the chunk's columns 0-7 and 8-15. Each item stores
+        // the row's 8 TF32 hi values and 8 lo values with one tcgen05.st each. The software
+        // pipeline, row tables and counters are those of the shared-memory variant below.
+        const int pw = warp - TC_PROD0, qd = warp & 3, half = pw >> 2;
+        const int row = 32 * qd + lane;
+        const uint32_t ta_row = taddr + ((uint32_t)(32 * qd) << 16) + (uint32_t)(lay.a_col0() + 8 * half);
+        float4 d[3][2];
+        int ti[4] = {-1, -1, -1, -1};
+        struct Ctr {
+            int j, c, c1;
+        };
+        auto adv = [&](Ctr& t) {
+            if (++t.c < t.c1) return false;
+            ++t.j;
+            t.c = c_begin(t.j);
+            t.c1 = c_end(t.j);
+            return true;
+        };
+        auto load_info = [&](int j) { return j < my_units ? src_info[(size_t)tile_of(j) * TC_ROWS + row] : -1; };
+        auto load_data = [&](const Ctr& t, int dj, float4 (&v)[2]) {
+            const int info = dj == 0 ? ti[0] : (dj == 1 ? ti[1] : ti[2]);
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+                const int k = t.c * KC + 8 * half + 4 * e;
+                v[e] = (t.j < my_units && info >= 0 && k < R) ? *reinterpret_cast<const float4*>(M + (size_t)(info >> 3) + k)
+                                                               : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+        };
+#pragma unroll
+        for (int q = 0; q < 4; ++q) ti[q] = load_info(q);
+        Ctr ci{0, c_begin(0), c_end(0)};
+        Ctr c2 = ci;
+        {
+            Ctr c1 = ci;
+            adv(c1);
+            load_data(ci, 0, d[0]);
+            load_data(c1, c1.j, d[1]);
+            c2 = c1;
+            adv(c2);
+        }
+        int st = 0, ph = 0;
+        bool stop = false;
+        for (int base = 0; base < n_items && !stop; base += 3) {
+#pragma unroll
+            for (int u = 0; u < 3; ++u) {
+                const int i = base + u;
+                if (i >= n_items || stop) break;
+                const int sa = u, sc = (u + 2) % 3;
+                load_data(c2, c2.j - ci.j, d[sc]);
+                const bool okw = ph == 0 || mbar_wait_ab(empty(st), (uint32_t)((ph - 1) & 1), abort_flag);
+                if (!__all_sync(0xffffffffu, okw)) {
+                    if (lane == 0) fail(2);
+                    stop = true;
+                    break;
+                }
+                if (__any_sync(0xffffffffu, *abort_flag != 0)) { stop = true; break; }
+                uint32_t hv[8], lv[8];
+#pragma unroll
+                for (int e = 0; e < 2; ++e) {
+                    const int te = ((ci.c * KC + 8 * half) >> 2) + e;
+                    const uint32_t sg = sgn_tab[te], zm = zm_tab[te];
+                    const float4 x = apply_zero(apply_signs(d[sa][e], (sg >> (4 * (ti[0] & 7))) & 15u), zm);
+                    const float4 hi = make_float4(tf32_hi(x.x), tf32_hi(x.y), tf32_hi(x.z), tf32_hi(x.w));
+                    hv[4 * e + 0] = __float_as_uint(hi.x);
+                    hv[4 * e + 1] = __float_as_uint(hi.y);
+                    hv[4 * e + 2] = __float_as_uint(hi.z);
+                    hv[4 * e + 3] = __float_as_uint(hi.w);
+                    lv[4 * e + 0] = __float_as_uint(x.x - hi.x);
+                    lv[4 * e + 1] = __float_as_uint(x.y - hi.y);
+                    lv[4 * e + 2] = __float_as_uint(x.z - hi.z);
+                    lv[4 * e + 3] = __float_as_uint(x.w - hi.w);
+                }
+                const uint32_t ta = ta_row + (uint32_t)(st * 2 * KC);
+                tmem_st8(ta, hv);
+                if (prods == 3) tmem_st8(ta + KC, lv);
+                asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+                asm volatile("tcgen05.fence::before_thread_sync;");
+                __syncwarp();
+                if (lane == 0) mbar_arrive(full(st));
+                const bool new_unit = adv(ci);
+                adv(c2);
+                if (new_unit) {
+                    ti[0] = ti[1];
+                    ti[1] = ti[2];
+                    ti[2] = ti[3];
+                    ti[3] = load_info(ci.j + 3);
+                }
+                if (++st == NST) { st = 0; ++ph; }
+            }
+        }
+      } else {
         const int pw = warp - TC_PROD0, r7 = lane & 7, kq0 = lane >> 3;
         const int row0 = 16 * pw + r7;
         float4 d[3][2][Kc<KC>::E];
@@ -470,6 +598,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_m2l_tc(int p, int prods, cons
                 if (++st == NST) { st = 0; ++ph; }
             }
         }
+      }
     } else {
         // ---------------- epilogue groups
         // with one accumulator a single group drains every tile, so that each group waits
@@ -621,7 +750,10 @@ __global__ void k_zero_cells(const int* cells, int n, int nc, int R, float* X, s
 
 }  // namespace
 
-size_t m2l_tc_smem(const fmmbem_handle* h, int p) { return tc_layout(p, h->tc_kc).bytes(); }
+// Orders whose tensor-core passes keep the gathered rows in TMEM (tc_atm_at).
+static bool atm_at(const fmmbem_handle* h, int p) { return tc_atm_at(p, h->tc_kc); }
+
+size_t m2l_tc_smem(const fmmbem_handle* h, int p) { return tc_layout(p, h->tc_kc, atm_at(h, p)).bytes(); }
 
 // The operator tables in the handle's chunk layout.
 static void launch_tc_tables(const fmmbem_handle* h, unsigned grid, const double* Td, int ntab, int nr, int ld, int nch,
@@ -733,9 +865,12 @@ int build_m2l_tc(fmmbem_handle* h) {
     FMM_CU(cudaMemsetAsync(h->tc_err, 0, sizeof(int), h->stream));
     FMM_TRY(build_tree_tc(h, nr, rows_max, nch));
     size_t smax = 0;
-    for (int q = 1; q <= pmax; ++q) smax = std::max(smax, m2l_tc_smem(h, q));
-    FMM_CU(cudaFuncSetAttribute(k_m2l_tc<TC_KC, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smax));
-    FMM_CU(cudaFuncSetAttribute(k_m2l_tc<TC_KC, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smax));
+    for (int q = 1; q <= pmax; ++q)
+        smax = std::max({smax, tc_layout(q, h->tc_kc, false).bytes(), tc_layout(q, h->tc_kc, true).bytes()});
+    FMM_CU(cudaFuncSetAttribute(k_m2l_tc<TC_KC, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smax));
+    FMM_CU(cudaFuncSetAttribute(k_m2l_tc<TC_KC, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smax));
+    FMM_CU(cudaFuncSetAttribute(k_m2l_tc<TC_KC, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smax));
+    FMM_CU(cudaFuncSetAttribute(k_m2l_tc<TC_KC, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smax));
     int dev = 0;
     FMM_CU(cudaGetDevice(&dev));
     FMM_CU(cudaDeviceGetAttribute(&h->n_sm, cudaDevAttrMultiProcessorCount, dev));
@@ -756,10 +891,10 @@ int tree_tc_zero(fmmbem_handle* h, int p) {
 // Launch of the tensor-core kernel with programmatic stream serialization: consecutive
 // tensor-core passes of a mat-vec (tree levels, M2L) overlap each launch's set-up with the
 // previous one's tail (the kernel waits for its predecessor before reading expansions).
-template <int KC, bool SPLIT>
-static cudaError_t launch_tc(int grid, size_t smem, cudaStream_t st, int p, int prods, const int4* tiles, int nt,
-                             int ks, const int* src, const int* dst, const float* tab, size_t stride, int rows_max,
-                             const float* M, float* L, int* err) {
+template <int KC, bool SPLIT, bool ATM>
+static cudaError_t launch_tc1(int grid, size_t smem, cudaStream_t st, int p, int prods, const int4* tiles, int nt,
+                              int ks, const int* src, const int* dst, const float* tab, size_t stride, int rows_max,
+                              const float* M, float* L, int* err) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)grid);
     cfg.blockDim = dim3(TC_THREADS);
@@ -770,8 +905,19 @@ static cudaError_t launch_tc(int grid, size_t smem, cudaStream_t st, int p, int 
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_m2l_tc<KC, SPLIT>, p, prods, tiles, nt, ks, src, dst, tab, stride, rows_max, M, L,
-                              err);
+    return cudaLaunchKernelEx(&cfg, k_m2l_tc<KC, SPLIT, ATM>, p, prods, tiles, nt, ks, src, dst, tab, stride, rows_max,
+                              M, L, err);
+}
+
+template <bool SPLIT>
+static cudaError_t launch_tc(const fmmbem_handle* h, int grid, cudaStream_t st, int p, int prods, const int4* tiles,
+                             int nt, int ks, const int* src, const int* dst, const float* tab, size_t stride,
+                             int rows_max, const float* M, float* L, int* err) {
+    const size_t smem = m2l_tc_smem(h, p);
+    return atm_at(h, p) ? launch_tc1<TC_KC, SPLIT, true>(grid, smem, st, p, prods, tiles, nt, ks, src, dst, tab, stride,
+                                                          rows_max, M, L, err)
+                        : launch_tc1<TC_KC, SPLIT, false>(grid, smem, st, p, prods, tiles, nt, ks, src, dst, tab, stride,
+                                                           rows_max, M, L, err);
 }
 
 // One level of M2M (which = 0: children of level l into their parents, zeroed beforehand
@@ -791,9 +937,8 @@ int tree_tc(fmmbem_handle* h, int p, int level, int which) {
     const int nch = (2 * ncoef(p) + h->tc_kc - 1) / h->tc_kc;
     const int ks = std::max(1, std::min(nch, h->n_sm / nt));
     const int grid = std::min(nt * ks, h->n_sm);
-    const size_t sm = m2l_tc_smem(h, p);
-    FMM_CU((launch_tc<TC_KC, true>(grid, sm, h->stream, p, 3, tiles, nt, ks, src, dst, h->tree_tab_tc, h->tc_stride,
-                                   h->tc_rows_max, X, X, h->tc_err)));
+    FMM_CU((launch_tc<true>(h, grid, h->stream, p, 3, tiles, nt, ks, src, dst, h->tree_tab_tc, h->tc_stride,
+                            h->tc_rows_max, X, X, h->tc_err)));
     return 0;
 }
 
@@ -808,12 +953,11 @@ int m2l_tc_zero(fmmbem_handle* h) {
 int m2l_tc(fmmbem_handle* h, int p) {
     float* L = reinterpret_cast<float*>(h->L);
     const float* M = reinterpret_cast<const float*>(h->M);
-    const size_t sm = m2l_tc_smem(h, p);
     const int grid = std::min(h->n_tiles_tc, h->n_sm);  // persistent: one CTA per SM (512 TMEM columns each)
     const int prods = 3;
     if (grid <= 0) return 0;
-    FMM_CU((launch_tc<TC_KC, false>(grid, sm, h->stream, p, prods, h->m2l_tiles_tc, h->n_tiles_tc, 1, h->tc_src_info,
-                                    h->tc_dst_info, h->tab_tc, h->tc_stride, h->tc_rows_max, M, L, h->tc_err)));
+    FMM_CU((launch_tc<false>(h, grid, h->stream, p, prods, h->m2l_tiles_tc, h->n_tiles_tc, 1, h->tc_src_info,
+                             h->tc_dst_info, h->tab_tc, h->tc_stride, h->tc_rows_max, M, L, h->tc_err)));
     return 0;
 }
 
