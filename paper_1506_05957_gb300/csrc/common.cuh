@@ -131,6 +131,27 @@ void fmmbem_set_error(const char* fmt, ...);
         }                                                                                   \
     } while (0)
 
+// Programmatic dependent launch. A kernel launched by launch_pdl may be scheduled while its
+// predecessor in the stream drains; it calls pdl_wait() before anything else, which returns
+// once that predecessor has completed and its writes are visible (at once for a plain launch).
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+template <typename... KP, typename... A>
+inline cudaError_t launch_pdl(void (*kernel)(KP...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                              A&&... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, static_cast<A&&>(args)...);
+}
+
 #define FMM_TRY(expr)              \
     do {                           \
         int r_ = (expr);           \

@@ -572,6 +572,7 @@ constexpr int TREE_THREADS = 256;
 template <typename T, int NC>
 __global__ void __launch_bounds__(TREE_THREADS) k_m2m(int p, const int* parents, const double4* cs, const int2* child,
                                                       const T* oct, T* M, size_t msys) {
+    pdl_wait();
     M += blockIdx.y * msys;  // copy blockIdx.y of a Stokes batch
     extern __shared__ unsigned char smem_raw[];
     const int nco = ncoef(p);
@@ -713,6 +714,7 @@ __global__ void k_m2l(int p, const int* ptr, const int* srcl, const double4* cs,
 template <typename T, int NC>
 __global__ void __launch_bounds__(TREE_THREADS) k_l2l(int p, const int* parents, const double4* cs, const int2* child,
                                                       const T* oct, T* L, size_t msys) {
+    pdl_wait();
     L += blockIdx.y * msys;  // copy blockIdx.y of a Stokes batch
     extern __shared__ unsigned char smem_raw[];
     const int nco = ncoef(p);
@@ -1016,8 +1018,21 @@ int far_field_t(fmmbem_handle* h, int p) {
     if (std::is_same<T, float>::value) src = reinterpret_cast<const typename V4<T>::type*>(h->src_f);
     else src = reinterpret_cast<const typename V4<T>::type*>(h->src_d);
     const int nco = ncoef(p);
-    // P2M
+    // tensor-core tree translations in the mixed-precision M2L-TENSOR mode
+    const bool tree_tc_on = std::is_same<T, float>::value && h->m2l_mode == FMMBEM_M2L_TENSOR && h->m2l_tc_ready &&
+                            h->tree_tiles != nullptr && h->tree_tc_at[p];
+    const bool m2l_tc_on = std::is_same<T, float>::value && h->m2l_mode == FMMBEM_M2L_TENSOR && h->m2l_tc_ready &&
+                           h->m2l_tc_at[p];
+    // P2M (after the zeroing of what the tensor-core passes accumulate into: all local
+    // expansions, and the multipoles of the non-leaf cells, which P2M does not write), so that
+    // the first M2M level follows P2M directly and its launch overlaps P2M's tail
     prof_begin(h, FMMBEM_PASS_P2M);
+    int nz = 0;
+    if (m2l_tc_on) FMM_TRY(m2l_tc_zero(h));
+    if (tree_tc_on) {
+        FMM_TRY(tree_tc_zero(h, p));
+        ++nz;
+    }
     const size_t sm = (size_t)P2M_WARPS * NC * nco * 2 * sizeof(T);
     const bool stokeslet = NC == 4 && h->kernel == FMMBEM_STOKES && h->layer != FMMBEM_LAYER_DOUBLE;
     if (std::is_same<T, float>::value && (NC == 1 || (h->nrhs > 1 && h->kernel == FMMBEM_LAPLACE) || stokeslet)) {
@@ -1056,12 +1071,7 @@ int far_field_t(fmmbem_handle* h, int p) {
             (h->nrhs > 1 && !copies) ? h->N : 0, h->N * h->dof, h->esys);
     }
     FMM_LAUNCHED();
-    prof_end(h, FMMBEM_PASS_P2M, 1);
-    // tensor-core tree translations in the mixed-precision M2L-TENSOR mode
-    const bool tree_tc_on = std::is_same<T, float>::value && h->m2l_mode == FMMBEM_M2L_TENSOR && h->m2l_tc_ready &&
-                            h->tree_tiles != nullptr && h->tree_tc_at[p];
-    const bool m2l_tc_on = std::is_same<T, float>::value && h->m2l_mode == FMMBEM_M2L_TENSOR && h->m2l_tc_ready &&
-                           h->m2l_tc_at[p];
+    prof_end(h, FMMBEM_PASS_P2M, 1 + nz);
     // passes of this mat-vec that run on the tensor-core kernel (profiling attributes their time to it)
     h->tc_pass_bits = (tree_tc_on ? (1 << FMMBEM_PASS_M2M) | (1 << FMMBEM_PASS_L2L) : 0) |
                       (m2l_tc_on ? 1 << FMMBEM_PASS_M2L : 0);
@@ -1069,11 +1079,6 @@ int far_field_t(fmmbem_handle* h, int p) {
     prof_begin(h, FMMBEM_PASS_M2M);
     int nl = 0;
     const size_t sm_m2m = (size_t)(16 * NC + 8) * nco * 2 * sizeof(T);
-    if (m2l_tc_on) FMM_TRY(m2l_tc_zero(h));
-    if (tree_tc_on) {
-        FMM_TRY(tree_tc_zero(h, p));
-        ++nl;
-    }
     for (int l = h->n_levels - 2; l >= h->m2m_lmin; --l) {
         const int pb = h->parent_start[l], pe = h->parent_start[l + 1];
         if (pe == pb) continue;
@@ -1081,9 +1086,8 @@ int far_field_t(fmmbem_handle* h, int p) {
             FMM_TRY(tree_tc(h, p, l, 0));
             ++nl;
         } else {
-            k_m2m<T, NC><<<dim3(pe - pb, h->nsys), TREE_THREADS, sm_m2m, st>>>(p, h->parents + pb, h->cell_cs,
-                                                                             h->cell_child, oct, M, h->esys);
-            FMM_LAUNCHED();
+            FMM_CU(launch_pdl(k_m2m<T, NC>, dim3(pe - pb, h->nsys), dim3(TREE_THREADS), sm_m2m, st, p, h->parents + pb,
+                              h->cell_cs, h->cell_child, oct, M, h->esys));
             ++nl;
         }
     }
@@ -1110,14 +1114,13 @@ int far_field_t(fmmbem_handle* h, int p) {
         if (tree_tc_on) {
             FMM_TRY(tree_tc(h, p, l, 1));
         } else {
-            k_l2l<T, NC><<<dim3(pe - pb, h->nsys), TREE_THREADS, sm_l2l, st>>>(p, h->parents + pb, h->cell_cs,
-                                                                             h->cell_child, oct, L, h->esys);
-            FMM_LAUNCHED();
+            FMM_CU(launch_pdl(k_l2l<T, NC>, dim3(pe - pb, h->nsys), dim3(TREE_THREADS), sm_l2l, st, p, h->parents + pb,
+                              h->cell_cs, h->cell_child, oct, L, h->esys));
         }
         ++nl2;
     }
     prof_end(h, FMMBEM_PASS_L2L, nl2);
-    h->launches += 2 + nl + nl2;
+    h->launches += 2 + nz + nl + nl2;
     return 0;
 }
 

@@ -427,13 +427,20 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_m2l_tc(int p, int prods, cons
             return true;
         };
         auto load_info = [&](int j) { return j < my_units ? src_info[(size_t)tile_of(j) * TC_ROWS + row] : -1; };
+        // one 32-byte load per lane and item: rows start at multiples of 320 floats and k at
+        // multiples of 8, and the 8 reals stay inside the row's 320 (the ones past degree p
+        // are zeroed with the sign table's mask)
         auto load_data = [&](const Ctr& t, int dj, float4 (&v)[2]) {
             const int info = dj == 0 ? ti[0] : (dj == 1 ? ti[1] : ti[2]);
-#pragma unroll
-            for (int e = 0; e < 2; ++e) {
-                const int k = t.c * KC + 8 * half + 4 * e;
-                v[e] = (t.j < my_units && info >= 0 && k < R) ? *reinterpret_cast<const float4*>(M + (size_t)(info >> 3) + k)
-                                                               : make_float4(0.f, 0.f, 0.f, 0.f);
+            const int k = t.c * KC + 8 * half;
+            if (t.j < my_units && info >= 0 && k < R) {
+                asm volatile("ld.global.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                             : "=f"(v[0].x), "=f"(v[0].y), "=f"(v[0].z), "=f"(v[0].w), "=f"(v[1].x), "=f"(v[1].y),
+                               "=f"(v[1].z), "=f"(v[1].w)
+                             : "l"(M + (size_t)(info >> 3) + k));
+            } else {
+                v[0] = make_float4(0.f, 0.f, 0.f, 0.f);
+                v[1] = v[0];
             }
         };
 #pragma unroll
