@@ -229,7 +229,8 @@ static int matvec_launch(fmmbem_handle* h, int p, const double* xs, double* ys);
 // per order p; the graph is recaptured when the arithmetic or kernel selection changed.
 int matvec_sorted(fmmbem_handle* h, int p, const double* xs, double* ys) {
     const int mode = h->precision * 16 + h->m2l_mode + 4 * h->p2p_variant + 64 * (h->prof_on ? 1 : 0) + 128 * h->layer +
-                     256 * h->m2l_tc_at[p] + 512 * h->tree_tc_at[p] + 1024 * (h->prof_serial ? 1 : 0);
+                     256 * h->m2l_tc_at[p] + 512 * h->tree_tc_at[p] + 1024 * (h->prof_serial ? 1 : 0) +
+                     2048 * h->near_at;
     if (!h->use_graphs || xs != h->xfix || ys != h->kw || h->stream == nullptr)
         return matvec_launch(h, p, xs, ys);
     prof_harvest(h);
@@ -267,23 +268,36 @@ int matvec_sorted(fmmbem_handle* h, int p, const double* xs, double* ys) {
     return 0;
 }
 
+// Forks the pending near field onto the second stream when the far field reaches stage
+// (see near_at); ev_join follows it there.
+int near_release(fmmbem_handle* h, int stage) {
+    if (!h->near_pending || stage < h->near_at) return 0;
+    h->near_pending = false;
+    FMM_CU(cudaEventRecord(h->ev_fork, h->stream));
+    FMM_CU(cudaStreamWaitEvent(h->stream2, h->ev_fork, 0));
+    FMM_TRY(near_field(h, h->near_fp64, h->stream2));
+    FMM_CU(cudaEventRecord(h->ev_join, h->stream2));
+    return 0;
+}
+
 static int matvec_launch(fmmbem_handle* h, int p, const double* xs, double* ys) {
     const bool fp64 = h->precision == FMMBEM_FP64;
     h->xin = xs;
     prof_begin(h, FMMBEM_PASS_MATVEC);
-    // near field on the second stream, far field on the handle's stream, joined before L2P;
-    // in serial profiling the near field runs first on the handle's stream, so that every
-    // pass's events time its kernels alone (no wait for SMs held by the other field)
+    // near field on the second stream, released once P2M is queued (near_at), far field on the
+    // handle's stream, joined before L2P; in serial profiling the near field runs first on the
+    // handle's stream, so that every pass's events time its kernels alone (no wait for SMs held
+    // by the other field)
     if (!fp64) FMM_TRY(pack_sources(h));
     if (h->prof_on && h->prof_serial) {
         FMM_TRY(near_field(h, fp64, h->stream));
         FMM_TRY(far_field(h, p, fp64));
     } else {
-        FMM_CU(cudaEventRecord(h->ev_fork, h->stream));
-        FMM_CU(cudaStreamWaitEvent(h->stream2, h->ev_fork, 0));
-        FMM_TRY(near_field(h, fp64, h->stream2));
-        FMM_TRY(far_field(h, p, fp64));
-        FMM_CU(cudaEventRecord(h->ev_join, h->stream2));
+        h->near_pending = true;
+        h->near_fp64 = fp64;
+        FMM_TRY(near_release(h, 0));
+        FMM_TRY(far_field(h, p, fp64));  // releases the near field at stage near_at
+        FMM_TRY(near_release(h, 4));
         FMM_CU(cudaStreamWaitEvent(h->stream, h->ev_join, 0));
     }
     FMM_TRY(far_eval_add(h, p, fp64, ys, operator_scale(h)));

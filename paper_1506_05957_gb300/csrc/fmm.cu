@@ -1072,6 +1072,7 @@ int far_field_t(fmmbem_handle* h, int p) {
     }
     FMM_LAUNCHED();
     prof_end(h, FMMBEM_PASS_P2M, 1 + nz);
+    FMM_TRY(near_release(h, 1));
     // passes of this mat-vec that run on the tensor-core kernel (profiling attributes their time to it)
     h->tc_pass_bits = (tree_tc_on ? (1 << FMMBEM_PASS_M2M) | (1 << FMMBEM_PASS_L2L) : 0) |
                       (m2l_tc_on ? 1 << FMMBEM_PASS_M2L : 0);
@@ -1092,6 +1093,7 @@ int far_field_t(fmmbem_handle* h, int p) {
         }
     }
     prof_end(h, FMMBEM_PASS_M2M, nl);
+    FMM_TRY(near_release(h, 2));
     // M2L
     prof_begin(h, FMMBEM_PASS_M2L);
     if (m2l_tc_on) {
@@ -1104,6 +1106,7 @@ int far_field_t(fmmbem_handle* h, int p) {
         FMM_LAUNCHED();
     }
     prof_end(h, FMMBEM_PASS_M2L, 1);
+    FMM_TRY(near_release(h, 3));
     // L2L, top-down
     prof_begin(h, FMMBEM_PASS_L2L);
     int nl2 = 0;
