@@ -61,6 +61,9 @@ def parse():
                     help="serve: destroy every request's handle (no reuse across requests on one mesh)")
     ap.add_argument("--no-autotune", action="store_true",
                     help="laplace: keep the default per-order tensor-core choices instead of fmmbem_autotune's")
+    ap.add_argument("--krylov-loop", choices=["host", "device"], default="host",
+                    help="laplace: GMRES cycles driven from the host, one round trip per step, or run on the "
+                         "device as one graph per restart cycle (fmmbem_set_device_loop)")
     ap.add_argument("--orders", default="3,4,5,6,7,8,9,10,11,12,16",
                     help="matvec: comma-separated expansion orders")
     ap.add_argument("--tree-tc-min", type=int, default=0,
@@ -318,6 +321,8 @@ def run_ours(args, world, rank, local):
     x = torch.zeros_like(b)
     # per-order choice of tensor-core or SIMT translations (part of setup, untimed)
     tuned = None if args.no_autotune else h.autotune(W["p_min"], W["p_initial"])
+    if args.krylov_loop == "device":
+        h.set_device_loop(True)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     solve = lambda: h.solve(b, x, tol=W["tol"], relax=True, p_initial=W["p_initial"], p_min=W["p_min"])
 
@@ -450,7 +455,7 @@ def run_ours(args, world, rank, local):
            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
            "config": dict(W, workload="laplace-sphere-ico%d-%d" % (args.levels, n), ncrit=args.ncrit, panels=n,
                           parallelism="replicas" if world > 1 else "single",
-                          l2="flushed between steps (512 MB write)", precision="mixed"),
+                          l2="flushed between steps (512 MB write)", precision="mixed", krylov_loop=args.krylov_loop),
            "matvec_per_s": mv_per_s, "iters": iters, "p_hist": r["p_hist"], "true_residual": r["true_res"],
            "autotune": tuned,
            "gpu_launches": launches,

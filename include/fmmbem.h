@@ -206,6 +206,17 @@ int fmmbem_create_tuned(const fmmbem_mesh* mesh, int kernel, int gauss_k, int n_
  * Returns FMMBEM_EINVAL for any other value. */
 int fmmbem_set_p2p_variant(fmmbem_handle* h, int variant);
 
+/* Run each restart cycle of fmmbem_solve on the device (on = 1) instead of one host round
+ * trip per GMRES step (Sec. 2.4 and 2.6: the steps are the same). The cycle is one CUDA graph
+ * whose while node repeats the mat-vec at the step's order (a switch over the per-order
+ * mat-vecs), the Arnoldi step and the column update (Givens rotations, residual estimate,
+ * stopping tests and the next relaxed order), all on the device; the host reads the cycle's
+ * state once at its end. Built on the first solve after it is enabled or after the kernel
+ * selection of any order changed (that solve's capture must not run inside a stream
+ * capture). Applies to single right-hand-side solves in FMMBEM_MIXED and FMMBEM_FP64 without
+ * profiling; FMMBEM_EDEVICE from the solve if the graph cannot be built. Default off. */
+int fmmbem_set_device_loop(fmmbem_handle* h, int on);
+
 /* Which boundary-integral operator A the mat-vecs and solves of a handle apply
  * (eq. laplace_matrix; for Stokes eqs. stokes_bem_discretized and stresslet):
  *   SINGLE : A = V, V_ij = (1/4pi) int_j 1/r dS; the first-kind system for the unknown

@@ -95,6 +95,7 @@ def lib():
         L.fmmbem_matvec.argtypes = [_vp, ctypes.c_int, _vp, _vp]
         L.fmmbem_set_m2l_mode.argtypes = [_vp, ctypes.c_int]
         L.fmmbem_set_p2p_variant.argtypes = [_vp, ctypes.c_int]
+        L.fmmbem_set_device_loop.argtypes = [_vp, ctypes.c_int]
         L.fmmbem_set_layer.argtypes = [_vp, ctypes.c_int]
         L.fmmbem_solve_batch.argtypes = [_vp, _vp, ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, _vp,
                                          _vp, _vp, _vp]
@@ -337,6 +338,10 @@ class FmmBem:
 
     def set_p2p_variant(self, variant):
         _check(lib().fmmbem_set_p2p_variant(self.h, int(variant)))
+
+    def set_device_loop(self, on=True):
+        """Run each GMRES restart cycle as one device-resident graph (fmmbem_set_device_loop)."""
+        _check(lib().fmmbem_set_device_loop(self.h, 1 if on else 0))
 
     def set_m2l_mode(self, mode):
         _check(lib().fmmbem_set_m2l_mode(self.h, int(mode)))

@@ -227,6 +227,24 @@ static int matvec_launch(fmmbem_handle* h, int p, const double* xs, double* ys);
 
 // Mat-vecs of the solver (fixed buffers xfix -> kw, not profiling) replay one CUDA graph
 // per order p; the graph is recaptured when the arithmetic or kernel selection changed.
+uint64_t matvec_modes_key(const fmmbem_handle* h) {
+    uint64_t key = 1469598103934665603ull;
+    for (int q = 0; q <= h->opts.p_max; ++q) {
+        const int mode = h->precision * 16 + h->m2l_mode + 4 * h->p2p_variant + 128 * h->layer + 256 * h->m2l_tc_at[q] +
+                         512 * h->tree_tc_at[q] + 2048 * h->near_at;
+        key = (key ^ (uint64_t)mode) * 1099511628211ull;
+    }
+    return key;
+}
+
+int matvec_capture_body(fmmbem_handle* h, int p) {
+    const int64_t keep = h->launches;
+    const int rc = matvec_launch(h, p, h->xfix, h->kw);
+    h->dloop_mv_launches[p] = h->launches - keep;
+    h->launches = keep;
+    return rc;
+}
+
 int matvec_sorted(fmmbem_handle* h, int p, const double* xs, double* ys) {
     const int mode = h->precision * 16 + h->m2l_mode + 4 * h->p2p_variant + 64 * (h->prof_on ? 1 : 0) + 128 * h->layer +
                      256 * h->m2l_tc_at[p] + 512 * h->tree_tc_at[p] + 1024 * (h->prof_serial ? 1 : 0) +
@@ -362,6 +380,7 @@ void fmmbem_destroy(fmmbem_handle* h) {
     if (h->istream) cudaStreamDestroy(h->istream);
     if (h->ev_fork) cudaEventDestroy(h->ev_fork);
     if (h->ev_join) cudaEventDestroy(h->ev_join);
+    dloop_free(h);
     if (h->stream2) cudaStreamDestroy(h->stream2);
     prof_free(h);
     delete h;
@@ -722,6 +741,12 @@ int fmmbem_create_tuned(const fmmbem_mesh* mesh, int kernel, int gauss_k, int n_
 int fmmbem_set_p2p_variant(fmmbem_handle* h, int variant) {
     if (!h || variant < 0 || variant > 3) { fmmbem_set_error("bad P2P variant"); return FMMBEM_EINVAL; }
     h->p2p_variant = variant;
+    return 0;
+}
+
+int fmmbem_set_device_loop(fmmbem_handle* h, int on) {
+    if (!h || (on != 0 && on != 1)) { fmmbem_set_error("device loop: on must be 0 or 1"); return FMMBEM_EINVAL; }
+    h->dloop_on = on != 0;
     return 0;
 }
 

@@ -199,6 +199,16 @@ struct fmmbem_handle {
     cudaEvent_t ev[2 * FMMBEM_N_PASSES] = {};
     void* prof_state = nullptr;  // per-handle event pool and pending intervals (capi.cu)
     int64_t launches = 0;
+    // device-resident GMRES cycle (fmmbem_set_device_loop): one graph per restart cycle whose
+    // while node repeats mat-vec (a switch over the orders) -> Arnoldi step -> Givens step on
+    // the device until the cycle ends; built on first use for the handle's kernel selection
+    bool dloop_on = false;
+    cudaGraphExec_t dloop_exec = nullptr;
+    uint64_t dloop_key = 0;
+    void* dloop_state = nullptr;       // device cycle state
+    void* dloop_host = nullptr;        // pinned copy read back after each cycle
+    double* dloop_out = nullptr;       // the Arnoldi step's output (device)
+    int64_t dloop_mv_launches[FMMBEM_P_MAX + 1] = {};
 };
 
 namespace fmmbem {
@@ -241,6 +251,9 @@ int exclusive_scan(const int* in, int* out, int64_t n, cudaStream_t st);
 int inclusive_scan(const int* in, int* out, int64_t n, cudaStream_t st);
 // capi.cu
 int matvec_sorted(fmmbem_handle* h, int p, const double* xs, double* ys);
+int matvec_capture_body(fmmbem_handle* h, int p);  // the mat-vec xfix -> kw at order p onto h->stream
+uint64_t matvec_modes_key(const fmmbem_handle* h);  // kernel selection of every order's mat-vec
+void dloop_free(fmmbem_handle* h);
 void prof_begin(fmmbem_handle* h, int pass);
 void prof_end(fmmbem_handle* h, int pass, int launches);
 void prof_harvest(fmmbem_handle* h);

@@ -246,7 +246,8 @@ __device__ void arn_update(const double* V, int64_t n, int nv, const double* hs,
 __global__ void __launch_bounds__(ARN_THREADS) k_arnoldi(double* V, int64_t n, int k, double* w, double* xfix,
                                                          double* partial, unsigned* bar, double* out, int* err,
                                                          int nsys, int64_t vstride, int64_t wstride,
-                                                         unsigned active, unsigned wait_limit) {
+                                                         unsigned active, unsigned wait_limit, const int* kdev) {
+    if (kdev) k = *kdev;  // the device-resident cycle keeps the step index on the device
     __shared__ double hs[ARN_MAXV];
     __shared__ double h1[ARN_MAXV];
     const int nbk = (int)gridDim.x / nsys;
@@ -349,7 +350,7 @@ struct Kr {
     }
 };
 
-int relaxed_p_int(double eta, double rho_prev, int p_initial, int p_min) {
+__host__ __device__ int relaxed_p_int(double eta, double rho_prev, int p_initial, int p_min) {
     double eps = eta / (rho_prev < 1.0 ? rho_prev : 1.0);
     if (eps > 1.0) eps = 1.0;
     int p;
@@ -363,6 +364,100 @@ int relaxed_p_int(double eta, double rho_prev, int p_initial, int p_min) {
     if (p < p_min) p = p_min;
     if (p > p_initial) p = p_initial;
     return p;
+}
+
+// State of one device-resident GMRES cycle (the host loop's scalars, Hessenberg matrix,
+// rotations and per-step records), written by k_dloop_begin and advanced by k_dloop_step.
+struct KrylovDev {
+    int k, it, m, max_iter, p_initial, p_min, relax, status;  // status: 0 running, 1 converged, 2 NaN, 3 cycle or budget ended
+    int k_done, p_cur, pad0, pad1;
+    double rho, bnorm, tol, pad2;
+    double g[ARN_MAXV + 1], cs[ARN_MAXV], sn[ARN_MAXV];
+    double H[(ARN_MAXV + 1) * ARN_MAXV];  // (i, j) at i * ARN_MAXV + j
+    double res_c[ARN_MAXV];               // rho after each step of the cycle
+    int p_c[ARN_MAXV];                    // order of each step's mat-vec
+};
+
+__global__ void k_dloop_begin(KrylovDev* s, int it, int m, int max_iter, int p_initial, int p_min, int relax, double tol,
+                              double bnorm, double beta, double rho) {
+    for (int i = threadIdx.x; i < (ARN_MAXV + 1) * ARN_MAXV; i += blockDim.x) s->H[i] = 0.0;
+    for (int i = threadIdx.x; i <= ARN_MAXV; i += blockDim.x) s->g[i] = 0.0;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        s->k = 0;
+        s->it = it;
+        s->m = m;
+        s->max_iter = max_iter;
+        s->p_initial = p_initial;
+        s->p_min = p_min;
+        s->relax = relax;
+        s->status = 0;
+        s->k_done = 0;
+        s->rho = rho;
+        s->bnorm = bnorm;
+        s->tol = tol;
+        s->g[0] = beta;
+        s->p_cur = relax ? relaxed_p_int(tol, rho, p_initial, p_min) : p_initial;
+    }
+}
+
+// First node of the cycle graph: the switch takes the first step's order.
+__global__ void k_dloop_init(const KrylovDev* s, cudaGraphConditionalHandle hs) {
+    if (threadIdx.x == 0) cudaGraphSetConditional(hs, (unsigned)s->p_cur);
+}
+
+// After each Arnoldi step: the host loop's column update, done by one thread in the same
+// order and FP64 operations (Givens rotations, residual estimate, stopping tests, next order),
+// then the switch's next order and whether the while node runs again.
+__global__ void k_dloop_step(KrylovDev* s, const double* ao, cudaGraphConditionalHandle hw,
+                             cudaGraphConditionalHandle hs) {
+    if (threadIdx.x != 0) return;
+    const int k = s->k;
+    auto Hc = [&](int i, int j) -> double& { return s->H[i * ARN_MAXV + j]; };
+    s->p_c[k] = s->p_cur;
+    s->it += 1;
+    for (int i = 0; i <= k; ++i) Hc(i, k) = ao[i] + ao[(ARN_MAXV + 1) + i];
+    const double hn = sqrt(ao[2 * (ARN_MAXV + 1)]);
+    Hc(k + 1, k) = hn;
+    bool stop = false;
+    if (!isfinite(hn)) {
+        s->status = 2;
+        s->k_done = k;
+        stop = true;
+    } else {
+        for (int i = 0; i < k; ++i) {
+            const double t = s->cs[i] * Hc(i, k) + s->sn[i] * Hc(i + 1, k);
+            Hc(i + 1, k) = -s->sn[i] * Hc(i, k) + s->cs[i] * Hc(i + 1, k);
+            Hc(i, k) = t;
+        }
+        const double den = hypot(Hc(k, k), Hc(k + 1, k));
+        s->cs[k] = Hc(k, k) / den;
+        s->sn[k] = Hc(k + 1, k) / den;
+        Hc(k, k) = den;
+        Hc(k + 1, k) = 0.0;
+        s->g[k + 1] = -s->sn[k] * s->g[k];
+        s->g[k] = s->cs[k] * s->g[k];
+        const double rho = fabs(s->g[k + 1]) / s->bnorm;
+        s->rho = rho;
+        s->res_c[k] = rho;
+        s->k_done = k + 1;
+        if (!isfinite(rho)) {
+            s->status = 2;
+            stop = true;
+        } else if (rho <= s->tol || hn == 0.0) {  // converged, or the exact solution is in the space
+            s->status = 1;
+            stop = true;
+        } else if (s->it >= s->max_iter || k + 1 >= s->m) {
+            s->status = 3;
+            stop = true;
+        }
+        if (!stop) {
+            s->k = k + 1;
+            s->p_cur = s->relax ? relaxed_p_int(s->tol, rho, s->p_initial, s->p_min) : s->p_initial;
+            cudaGraphSetConditional(hs, (unsigned)s->p_cur);
+        }
+    }
+    cudaGraphSetConditional(hw, stop ? 0u : 1u);
 }
 
 }  // namespace
@@ -381,6 +476,167 @@ int arnoldi_threads(int64_t, int) { return ARN_THREADS; }
 
 int relaxed_p(double eta, double rho_prev, int p_initial, int p_min) {
     return relaxed_p_int(eta, rho_prev, p_initial, p_min);
+}
+
+void dloop_free(fmmbem_handle* h) {
+    if (h->dloop_exec) cudaGraphExecDestroy(h->dloop_exec);
+    if (h->dloop_state) cudaFree(h->dloop_state);
+    if (h->dloop_out) cudaFree(h->dloop_out);
+    if (h->dloop_host) cudaFreeHost(h->dloop_host);
+    h->dloop_exec = nullptr;
+    h->dloop_state = h->dloop_host = nullptr;
+    h->dloop_out = nullptr;
+}
+
+// The cycle graph: k_dloop_init, then a while node whose body is a switch over the orders
+// (body p: the mat-vec xfix -> kw at order p, as matvec_sorted's graph), the Arnoldi step
+// (its index read from the state) and k_dloop_step. Rebuilt when the kernel selection of
+// any order changed.
+static int dloop_build(fmmbem_handle* h) {
+    const uint64_t key = matvec_modes_key(h);
+    if (h->dloop_exec && h->dloop_key == key) return 0;
+    if (h->dloop_exec) {
+        cudaGraphExecDestroy(h->dloop_exec);
+        h->dloop_exec = nullptr;
+    }
+    if (!h->dloop_state) {
+        FMM_CU(cudaMalloc(&h->dloop_state, sizeof(KrylovDev)));
+        FMM_CU(cudaMalloc((void**)&h->dloop_out, sizeof(double) * (2 * (ARN_MAXV + 1) + 1)));
+        FMM_CU(cudaMallocHost(&h->dloop_host, sizeof(KrylovDev)));
+    }
+    cudaStream_t st = h->stream;
+    KrylovDev* state = reinterpret_cast<KrylovDev*>(h->dloop_state);
+    cudaGraph_t g = nullptr;
+    FMM_CU(cudaGraphCreate(&g, 0));
+    // every exit below destroys the graph under construction
+    auto fail_with = [&](cudaError_t e, const char* what) {
+        cudaGraph_t dummy = nullptr;
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone)
+            cudaStreamEndCapture(st, &dummy);
+        cudaGetLastError();
+        cudaGraphDestroy(g);
+        fmmbem_set_error("device loop: %s: %s", what, cudaGetErrorString(e));
+        return FMMBEM_EDEVICE;
+    };
+    cudaGraphConditionalHandle hw, hs;
+    cudaError_t e = cudaGraphConditionalHandleCreate(&hw, g, 1, cudaGraphCondAssignDefault);
+    if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&hs, g, 0, 0);
+    if (e != cudaSuccess) return fail_with(e, "conditional handles");
+    cudaGraph_t out = nullptr;
+    e = cudaStreamBeginCaptureToGraph(st, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return fail_with(e, "capture");
+    k_dloop_init<<<1, 32, 0, st>>>(state, hs);
+    e = cudaGetLastError();
+    cudaError_t e2 = cudaStreamEndCapture(st, &out);
+    if (e == cudaSuccess) e = e2;
+    if (e != cudaSuccess) return fail_with(e, "init node");
+    size_t nn = 0;
+    cudaGraphNode_t init = nullptr;
+    e = cudaGraphGetNodes(g, nullptr, &nn);
+    if (e != cudaSuccess || nn != 1) return fail_with(e, "init node count");
+    e = cudaGraphGetNodes(g, &init, &nn);
+    if (e != cudaSuccess) return fail_with(e, "init node");
+    cudaGraphNodeParams wp = {};
+    wp.type = cudaGraphNodeTypeConditional;
+    wp.conditional.handle = hw;
+    wp.conditional.type = cudaGraphCondTypeWhile;
+    wp.conditional.size = 1;
+    cudaGraphNode_t wn;
+    e = cudaGraphAddNode(&wn, g, &init, nullptr, 1, &wp);
+    if (e != cudaSuccess) return fail_with(e, "while node");
+    cudaGraph_t body = wp.conditional.phGraph_out[0];
+    cudaGraphNodeParams sp = {};
+    sp.type = cudaGraphNodeTypeConditional;
+    sp.conditional.handle = hs;
+    sp.conditional.type = cudaGraphCondTypeSwitch;
+    sp.conditional.size = (unsigned)h->opts.p_max + 1;
+    cudaGraphNode_t sn;
+    e = cudaGraphAddNode(&sn, body, nullptr, nullptr, 0, &sp);
+    if (e != cudaSuccess) return fail_with(e, "switch node");
+    for (int q = 1; q <= h->opts.p_max; ++q) {
+        e = cudaStreamBeginCaptureToGraph(st, sp.conditional.phGraph_out[q], nullptr, nullptr, 0,
+                                          cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return fail_with(e, "mat-vec capture");
+        const int rc = matvec_capture_body(h, q);
+        e = cudaStreamEndCapture(st, &out);
+        if (rc < 0) {
+            cudaGraphDestroy(g);
+            return rc;
+        }
+        if (e != cudaSuccess) return fail_with(e, "mat-vec body");
+    }
+    e = cudaStreamBeginCaptureToGraph(st, body, &sn, nullptr, 1, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return fail_with(e, "step capture");
+    {
+        double* dV = h->V;
+        int64_t nn64 = h->N * h->dof;
+        int kk = 0;
+        double* dw = h->kw;
+        double* dx = h->xfix;
+        double* dp = h->kpart;
+        unsigned* bar = h->arn_bar;
+        double* dout = h->dloop_out;
+        int* de = h->kerr;
+        int nsys = 1;
+        int64_t vstride = 0, wstride = 0;
+        unsigned active = 1u;
+        unsigned wl = h->wait_limit;
+        const int* kdev = &state->k;
+        void* args[] = {&dV, &nn64, &kk, &dw, &dx, &dp, &bar, &dout, &de, &nsys, &vstride, &wstride, &active, &wl, &kdev};
+        e = cudaLaunchCooperativeKernel((const void*)k_arnoldi, dim3(h->arn_blocks),
+                                        dim3(arnoldi_threads(nn64, h->arn_blocks)), args, 0, st);
+        if (e == cudaSuccess) {
+            k_dloop_step<<<1, 32, 0, st>>>(state, h->dloop_out, hw, hs);
+            e = cudaGetLastError();
+        }
+    }
+    e2 = cudaStreamEndCapture(st, &out);
+    if (e == cudaSuccess) e = e2;
+    if (e != cudaSuccess) return fail_with(e, "Arnoldi and step nodes");
+    e = cudaGraphInstantiate(&h->dloop_exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        h->dloop_exec = nullptr;
+        cudaGetLastError();
+        fmmbem_set_error("device loop: instantiate: %s", cudaGetErrorString(e));
+        return FMMBEM_EDEVICE;
+    }
+    h->dloop_key = key;
+    return 0;
+}
+
+// One restart cycle on the device: the state is set, the cycle graph runs until the cycle
+// converges, fails or ends, and the state comes back in one copy. Outputs as in the host loop.
+static int dloop_cycle(fmmbem_handle* h, int& it, int m, int max_iter, int relax, int p_initial, int p_min, double tol,
+                       double bnorm, double beta, double& rho, std::vector<double>& H, int m_max, std::vector<double>& g,
+                       int& k_done, int& status, bool& converged, int* p_hist, double* res_hist) {
+    FMM_TRY(dloop_build(h));
+    cudaStream_t st = h->stream;
+    KrylovDev* state = reinterpret_cast<KrylovDev*>(h->dloop_state);
+    k_dloop_begin<<<1, 256, 0, st>>>(state, it, m, max_iter, p_initial, p_min, relax, tol, bnorm, beta, rho);
+    FMM_LAUNCHED();
+    FMM_CU(cudaGraphLaunch(h->dloop_exec, st));
+    FMM_CU(cudaMemcpyAsync(h->dloop_host, state, sizeof(KrylovDev), cudaMemcpyDeviceToHost, st));
+    FMM_CU(cudaStreamSynchronize(st));
+    const KrylovDev* s = reinterpret_cast<const KrylovDev*>(h->dloop_host);
+    const int steps = s->it - it;
+    h->launches += 2;  // k_dloop_begin, k_dloop_init
+    for (int j = 0; j < steps; ++j) {
+        if (p_hist) p_hist[it + j] = s->p_c[j];
+        if (res_hist && j < s->k_done) res_hist[it + j + 1] = s->res_c[j];
+        h->launches += h->dloop_mv_launches[s->p_c[j]] + 2;
+    }
+    it = s->it;
+    k_done = s->k_done;
+    rho = s->rho;
+    for (int i = 0; i <= k_done && i <= m_max; ++i) {
+        g[i] = s->g[i];
+        for (int j = 0; j < k_done; ++j) H[(size_t)i * m_max + j] = s->H[i * ARN_MAXV + j];
+    }
+    if (s->status == 1) converged = true;
+    if (s->status == 2) status = FMMBEM_ENAN;
+    return 0;
 }
 
 static int gmres_solve_on(fmmbem_handle* h, const double* b, double tol, int relax, int p_initial, int p_min, double* x,
@@ -482,7 +738,12 @@ static int gmres_solve_on(fmmbem_handle* h, const double* b, double tol, int rel
         g[0] = beta;
         int k_done = 0;
         bool stop = false;
-        for (int k = 0; k < m; ++k) {
+        // the device-resident cycle (fmmbem_set_device_loop) runs the same steps on the device
+        const bool dloop = h->dloop_on && h->use_graphs && !h->prof_on && h->stream != nullptr && m <= ARN_MAXV;
+        if (dloop)
+            FMM_TRY(dloop_cycle(h, it, m, max_iter, relax, p_initial, p_min, tol, bnorm, beta, rho, H, m_max, g, k_done,
+                                status, converged, p_hist, res_hist));
+        for (int k = 0; k < m && !dloop; ++k) {
             const int p = relax ? relaxed_p_int(tol, rho, p_initial, p_min) : p_initial;
             // v_k is also in xfix, the fixed input of the per-order mat-vec graphs
             FMM_TRY(matvec_sorted(h, p, h->xfix, h->kw));
@@ -504,7 +765,8 @@ static int gmres_solve_on(fmmbem_handle* h, const double* b, double tol, int rel
                 int64_t vstride = 0, wstride = 0;
                 unsigned active = 1u;
                 unsigned wl = h->wait_limit;
-                void* args[] = {&dV, &nn, &kk, &dw, &dx, &dp, &bar, &dout, &de, &nsys, &vstride, &wstride, &active, &wl};
+                const int* kdev = nullptr;
+                void* args[] = {&dV, &nn, &kk, &dw, &dx, &dp, &bar, &dout, &de, &nsys, &vstride, &wstride, &active, &wl, &kdev};
                 FMM_CU(cudaLaunchCooperativeKernel((const void*)k_arnoldi, dim3(h->arn_blocks), dim3(arnoldi_threads(n, h->arn_blocks)), args, 0,
                                                    st));
                 h->launches += 1;
@@ -760,7 +1022,8 @@ static int gmres_batch_on(fmmbem_handle* h, const double* b, double tol, int rel
                 int nsys = nb;
                 int64_t vs = vstride, ws = n;
                 unsigned wl = h->wait_limit;
-                void* args[] = {&dV, &nn, &kk, &dw, &dx, &dp, &bar, &dout, &de, &nsys, &vs, &ws, &active, &wl};
+                const int* kdev = nullptr;
+                void* args[] = {&dV, &nn, &kk, &dw, &dx, &dp, &bar, &dout, &de, &nsys, &vs, &ws, &active, &wl, &kdev};
                 const int grid = (h->arn_blocks / nb) * nb;
                 FMM_CU(cudaLaunchCooperativeKernel((const void*)k_arnoldi, dim3(grid),
                                                    dim3(arnoldi_threads(n, grid)), args, 0, st));
