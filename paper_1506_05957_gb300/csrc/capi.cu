@@ -289,7 +289,10 @@ int matvec_sorted(fmmbem_handle* h, int p, const double* xs, double* ys) {
 // Forks the pending near field onto the second stream when the far field reaches stage
 // (see near_at); ev_join follows it there.
 int near_release(fmmbem_handle* h, int stage) {
-    if (!h->near_pending || stage < h->near_at) return 0;
+    // FP64 mat-vecs release it before their P2M, which is long (FP64 recurrences) and would
+    // otherwise run alone
+    const int at = h->near_fp64 ? 0 : h->near_at;
+    if (!h->near_pending || stage < at) return 0;
     h->near_pending = false;
     FMM_CU(cudaEventRecord(h->ev_fork, h->stream));
     FMM_CU(cudaStreamWaitEvent(h->stream2, h->ev_fork, 0));

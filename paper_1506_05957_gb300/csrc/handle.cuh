@@ -28,7 +28,8 @@ struct fmmbem_handle {
     // far-field pass before which a mat-vec releases its near field to the second stream
     // (0: P2M, 1: the first tree level, 2: M2L, 3: L2L); near_pending while not yet released.
     // After P2M: the first tensor-core tree level then finds SMs free, and the near-field blocks
-    // fill the room its CTAs leave (headline 9.97 against 10.05 ms released before P2M)
+    // fill the room its CTAs leave (headline 9.97 against 10.05 ms released before P2M); FP64
+    // mat-vecs release it before P2M
     int near_at = 1;
     bool near_pending = false, near_fp64 = false;
     cudaStream_t istream = nullptr;  // internal stream of fmmbem_solve
