@@ -62,7 +62,8 @@ def parse():
     ap.add_argument("--no-handle-cache", action="store_true",
                     help="serve: destroy every request's handle (no reuse across requests on one mesh)")
     ap.add_argument("--no-autotune", action="store_true",
-                    help="laplace: keep the default per-order tensor-core choices instead of fmmbem_autotune's")
+                    help="laplace, stokes, rbc64: keep the default per-order tensor-core choices instead of "
+                         "fmmbem_autotune's")
     ap.add_argument("--krylov-loop", choices=["host", "device"], default="host",
                     help="laplace: GMRES cycles driven from the host, one round trip per step, or run on the "
                          "device as one graph per restart cycle (fmmbem_set_device_loop)")
@@ -542,6 +543,7 @@ def run_stokes(args, world, rank, local):
     area = 0.5 * np.linalg.norm(np.cross(b_ - a_, c_ - a_), axis=1)
     h = FmmBem(v, t, kernel=FMMBEM_STOKES, gauss_k=W["gauss_k"], ncrit=args.ncrit, theta=W["theta"], p_max=16,
                restart=W["restart"], max_iter=100, precision=FMMBEM_MIXED, stream=stream.cuda_stream)
+    tuned = None if args.no_autotune else h.autotune(W["p_min"], W["p_initial"])  # untimed setup
     bU = torch.tensor(np.tile([1.0, 0.0, 0.0], len(t)), dtype=torch.float64, device=dev)
     # a smooth random field with its area-weighted normal flux removed: the single layer's range is
     # orthogonal to the normal field, so only flux-free data gives a solvable first-kind system
@@ -935,6 +937,8 @@ def run_rbc64(args, world, rank, local):
     area = 0.5 * np.linalg.norm(np.cross(p3[:, 1] - p3[:, 0], p3[:, 2] - p3[:, 0]), axis=1)
     h = FmmBem(v, t, kernel=FMMBEM_STOKES, gauss_k=3, ncrit=args.ncrit, theta=0.5, p_max=16, mu=1e-3, restart=50,
                max_iter=100, precision=FMMBEM_MIXED, stream=stream.cuda_stream)
+    # per-order choice of tensor-core or SIMT translations (part of setup, untimed)
+    tuned = None if args.no_autotune else h.autotune(4, 16)
     b = torch.tensor(np.tile([1.0, 0.0, 0.0], len(t)), dtype=torch.float64, device=dev)
     x = torch.zeros_like(b)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
@@ -987,6 +991,8 @@ def run_rbc64(args, world, rank, local):
     # relaxed GMRES in lockstep (fmmbem_solve_batch)
     hb = FmmBem(v, t, kernel=FMMBEM_STOKES, gauss_k=3, ncrit=args.ncrit, theta=0.5, p_max=16, mu=1e-3, restart=50,
                 max_iter=100, precision=FMMBEM_MIXED, stream=stream.cuda_stream, nrhs=8, body_of_panel=body)
+    if not args.no_autotune:
+        hb.autotune(4, 16)
     B8 = torch.tensor(np.concatenate([np.tile(U, len(t)) for U in dirs]), dtype=torch.float64, device=dev)
     X8 = torch.zeros_like(B8)
     hb.solve_batch(B8, X8, tol=1e-5, relax=True, p_initial=16, p_min=4)  # warm-up (captures the graphs)
