@@ -62,7 +62,7 @@ def parse():
     ap.add_argument("--no-handle-cache", action="store_true",
                     help="serve: destroy every request's handle (no reuse across requests on one mesh)")
     ap.add_argument("--no-autotune", action="store_true",
-                    help="laplace, stokes, rbc64: keep the default per-order tensor-core choices instead of "
+                    help="laplace, stokes, rbc64, batch: keep the default per-order tensor-core choices instead of "
                          "fmmbem_autotune's")
     ap.add_argument("--krylov-loop", choices=["host", "device"], default="host",
                     help="laplace: GMRES cycles driven from the host, one round trip per step, or run on the "
@@ -858,6 +858,9 @@ def run_batch(args, world, rank, local):
                     max_iter=100, precision=FMMBEM_MIXED, stream=stream.cuda_stream)
     batch = FmmBem(v, t, gauss_k=W["gauss_k"], ncrit=args.ncrit, theta=W["theta"], p_max=16, restart=W["restart"],
                    max_iter=100, precision=FMMBEM_MIXED, stream=stream.cuda_stream, nrhs=4)
+    if not args.no_autotune:  # per-order translation paths of both handles (untimed setup)
+        single.autotune(W["p_min"], W["p_initial"])
+        batch.autotune(W["p_min"], W["p_initial"])
     B = torch.empty(4 * n, dtype=torch.float64, device=dev)
     for q, z0 in enumerate(((0.0, 0.0, 3.0), (2.5, 0.5, 0.0), (-0.3, -2.2, 1.1), (1.2, 1.2, -2.0))):
         d = c - np.asarray(z0)
