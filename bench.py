@@ -62,7 +62,7 @@ def parse():
     ap.add_argument("--no-handle-cache", action="store_true",
                     help="serve: destroy every request's handle (no reuse across requests on one mesh)")
     ap.add_argument("--no-autotune", action="store_true",
-                    help="laplace, stokes, rbc64, batch: keep the default per-order tensor-core choices instead of "
+                    help="laplace, laplace2, stokes, rbc64, batch: keep the default per-order tensor-core choices instead of "
                          "fmmbem_autotune's")
     ap.add_argument("--krylov-loop", choices=["host", "device"], default="host",
                     help="laplace: GMRES cycles driven from the host, one round trip per step, or run on the "
@@ -636,6 +636,8 @@ def run_laplace2(args, world, rank, local):
         h.matvec(16, ones, b)  # b = V q with q = 1 (FP64 FMM at p = 16)
         h.set_layer(FMMBEM_LAYER_DOUBLE)
         h.set_precision(FMMBEM_MIXED)
+        if not args.no_autotune:  # per-order translation paths (untimed setup)
+            h.autotune(W["p_min"], W["p_initial"])
         return h, b, len(t)
 
     def timed(h, b, x, relax, steps):
